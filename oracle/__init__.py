@@ -1,0 +1,22 @@
+"""Plain FP64 CPU oracle for the RBM variational Monte Carlo hot path.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference arm of ``bench.py`` may import, call, link or run
+anything under ``oracle/``.  The product package never does, and the two share
+no code: the only thing both sides consume is the seeded input generators in
+``paper_2112_10526_gb300.inputs``, which hold none of the method's arithmetic.
+
+Layout:
+  nk_oracle.c  per-configuration definitions in C (ln psi, local energy,
+               log-derivatives, Philox4x64-10, chain initialisation,
+               Metropolis chains with forced-follow replay);
+  core.py      ctypes binding of the C part plus the sample statistics, force,
+               QGT, SR linear solves and update in numpy (Sec. 3.4, 3.6, 4.1,
+               App. B of the paper);
+  exact.py     exact enumeration over all basis states and exact
+               diagonalisation from Kronecker products of Pauli matrices.
+
+Parity pins are in tests/test_oracle_*.py.  Functions without an external
+pin say "parity unpinned" in their docstring.
+"""
+from .core import *  # noqa: F401,F403

@@ -1,0 +1,83 @@
+"""Seeded synthetic inputs shared by the tests, the bench and the oracle checks.
+
+This module holds no arithmetic of the method: it only draws parameters and
+configurations from numpy generators and lists lattice edges.  Both the CUDA
+path and the CPU oracle consume what it returns.
+
+Recipe (matching the workloads of the NetKet 3 paper, Secs. 8-10):
+  * parameters a, b, W ~ N(0, sigma^2) i.i.d. from
+    ``numpy.random.default_rng(seed).normal``, drawn in the order a (N),
+    b (M), W (M x N row-major); sigma = 0.01 unless stated;
+  * periodic chain of L sites: edges (i, i+1 mod L) for i = 0..L-1;
+  * periodic L x L square lattice: site i = x L + y, edges (i, right) then
+    (i, down) for every site in order, right = ((x+1) mod L) L + y,
+    down = x L + (y+1) mod L  (E = 2 L^2);
+  * random configurations: i.i.d. +-1 spins, or uniformly random S_z = 0
+    configurations (a random permutation of N/2 up and N/2 down spins).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def rbm_params(N: int, M: int, seed: int, sigma: float = 0.01) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    a = rng.normal(0.0, sigma, N)
+    b = rng.normal(0.0, sigma, M)
+    W = rng.normal(0.0, sigma, (M, N))
+    return np.concatenate([a, b, W.ravel()]).astype(np.float64)
+
+
+def chain_edges(L: int) -> np.ndarray:
+    return np.array([[i, (i + 1) % L] for i in range(L)], dtype=np.int32).reshape(-1, 2)
+
+
+def square_edges(L: int) -> np.ndarray:
+    out = []
+    for x in range(L):
+        for y in range(L):
+            i = x * L + y
+            out.append([i, ((x + 1) % L) * L + y])
+            out.append([i, x * L + (y + 1) % L])
+    return np.array(out, dtype=np.int32).reshape(-1, 2)
+
+
+def random_configs(B: int, N: int, seed: int, sz0: bool = False) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    if not sz0:
+        return (2 * rng.integers(0, 2, size=(B, N)) - 1).astype(np.int8)
+    base = np.array([1] * (N // 2) + [-1] * (N - N // 2), dtype=np.int8)
+    return np.stack([rng.permutation(base) for _ in range(B)]).astype(np.int8)
+
+
+def tfim_chain(L: int, J: float = 1.0, h: float = 1.0) -> dict:
+    return {"kind": "tfim", "J": J, "h": h, "marshall": False, "edges": chain_edges(L)}
+
+
+def tfim_square(L: int, J: float = 1.0, h: float = 3.04) -> dict:
+    return {"kind": "tfim", "J": J, "h": h, "marshall": False, "edges": square_edges(L)}
+
+
+def heis_square(L: int, J: float = 1.0, marshall: bool = True) -> dict:
+    return {"kind": "heis", "J": J, "h": 0.0, "marshall": marshall, "edges": square_edges(L)}
+
+
+def heis_chain(L: int, J: float = 1.0, marshall: bool = True) -> dict:
+    return {"kind": "heis", "J": J, "h": 0.0, "marshall": marshall, "edges": chain_edges(L)}
+
+
+# The five workloads (sizes from the paper's examples and benchmarks).
+WORKLOADS = {
+    "tfim1d_n16": dict(N=16, alpha=1, ham=lambda: tfim_chain(16, 1.0, 1.0), rule="local",
+                       chains=16, per_chain=64, discard=16, seed=1, diag_shift=0.01, lr=0.01,
+                       solver="cholesky"),
+    "heis2d_10x10": dict(N=100, alpha=2, ham=lambda: heis_square(10, 1.0, True), rule="exchange",
+                         chains=1024, per_chain=8, discard=16, seed=2, diag_shift=0.01, lr=0.01,
+                         solver="cholesky_samplespace"),
+    "tfim2d_20x20": dict(N=400, alpha=4, ham=lambda: tfim_square(20, 1.0, 3.04), rule="local",
+                         chains=16384, per_chain=1, discard=16, seed=3, diag_shift=0.01, lr=0.01,
+                         solver="cg"),
+    "heis2d_24x24": dict(N=576, alpha=8, ham=lambda: heis_square(24, 1.0, True), rule="exchange",
+                         chains=8192, per_chain=8, discard=16, seed=5, diag_shift=0.01, lr=0.01,
+                         solver="cg"),
+}
