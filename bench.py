@@ -1,0 +1,394 @@
+#!/usr/bin/env python
+"""Benchmark of one VMC + stochastic-reconfiguration step (the whole hot path).
+
+Workload (default): 10 x 10 periodic Heisenberg antiferromagnet with the
+Marshall sign folded in, real RBM alpha = 2 (M = 200, Np = 20300), spin-
+exchange Metropolis at S_z = 0 with 1024 chains x 8 samples (Ns = 8192),
+eps = 0.01, lr = 0.01, SR solved by an FP64 Cholesky of the Ns x Ns
+sample-space matrix.  A step = sampling (8 sweeps per chain), local energies,
+statistics, force, SR solve and update, all through nk_sr_step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|f64]
+    python bench.py --impl reference ...   # the CPU oracle on a bounded sample
+
+Multi-GPU runs (torchrun) are independent replicas: the VMC step has no
+data-parallel exchange on one GPU per box, so every rank runs its own chains
+and the line reports the units all ranks processed over the slowest rank's
+time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "VMC samples·sweeps/s & SR steps/s, mixed vs FP64 on 1 GB300; serve p50/p99"
+FP64_PEAK_TFLOPS = 1.25     # nominal GB300 FP64 rate (no tensor-core FP64 path is used)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x FMA x max clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "f64"])
+    ap.add_argument("--workload", default="heis2d_10x10")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip the other-precision timing")
+    ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+def workload(name):
+    from paper_2112_10526_gb300 import inputs as I
+    w = dict(I.WORKLOADS[name])
+    w["name"] = name
+    w["M"] = w["alpha"] * w["N"]
+    w["ham"] = w["ham"]()
+    return w
+
+
+# ----------------------------------------------------------- CPU oracle ----
+
+def oracle_sample(name, chains, steps):
+    """Time the oracle's SR step on `chains` chains of the workload (one host
+    thread), `steps` times.  Runs in a fresh process."""
+    import numpy as np
+    import oracle
+    from paper_2112_10526_gb300 import inputs as I
+    w = workload(name)
+    N, M = w["N"], w["M"]
+    p = I.rbm_params(N, M, w["seed"])
+    s = oracle.chain_init(N, chains, w["rule"], w["seed"], 0)
+    times = []
+    sweep0 = 0
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        r = oracle.sr_step(p, N, M, w["ham"], w["rule"], s, sweep0, 0, w["per_chain"], w["seed"], 0,
+                           diag_shift=w["diag_shift"], lr=w["lr"], solver="cg", cg_tol=1e-10,
+                           cg_maxiter=1000)
+        times.append(time.perf_counter() - t0)
+        p, s = r["params"], r["state"]
+        sweep0 += w["per_chain"]
+    return {"times": times, "energy": float(r["stats"]["mean"]), "cg_iters": int(r["cg_iters"])}
+
+
+def run_oracle_subprocess(name, chains, steps):
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample",
+                          f"{name}:{chains}:{steps}"], env=env, capture_output=True, text=True,
+                         check=True)
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def oracle_line_fields(name, chains, res):
+    w = workload(name)
+    scale = w["chains"] / chains
+    t = statistics.median(res["times"])
+    value = 1.0 / (t * scale)
+    return value, {
+        "value": value, "unit": "SR steps/s", "cores": 1, "kind": "oracle",
+        "sample": (f"{chains} of {w['chains']} chains x {w['per_chain']} samples, oracle CG solver "
+                   f"(x0 = 0, tol 1e-10), 1 host thread; median of {len(res['times'])} steps, "
+                   f"extrapolated linearly in the number of samples"),
+    }
+
+
+# --------------------------------------------------------------- clocks ----
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9:
+                    rows.append(f)
+            os.unlink(self.path)
+        except Exception:
+            return None
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for n, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------------- our path ----
+
+def setup(w, precision, rank, dev):
+    import torch
+    from paper_2112_10526_gb300 import inputs as I
+    from paper_2112_10526_gb300 import nk
+    N, M, C = w["N"], w["M"], w["chains"]
+    st = {"N": N, "M": M, "C": C, "ns": w["per_chain"]}
+    st["params"] = torch.from_numpy(I.rbm_params(N, M, w["seed"])).to(dev)
+    st["edges"] = torch.from_numpy(w["ham"]["edges"]).to(dev)
+    st["ham"] = nk.make_ham(w["ham"]["kind"], w["ham"]["J"], w["ham"].get("h", 0.0),
+                            w["ham"].get("marshall", False), st["edges"])
+    st["s"] = torch.empty((C, N), dtype=torch.int8, device=dev)
+    st["ctx"] = nk.Ctx(dev.index)
+    nk.nk_chains_init(st["ctx"], N, C, w["rule"], w["seed"], rank, st["s"])
+    st["chains"] = nk.make_chains(st["s"])
+    st["cfg"] = nk.make_cfg(w["rule"], precision, w["solver"], w["discard"], w["per_chain"],
+                            w["diag_shift"], w["lr"], w["seed"], stream_id=rank, cg_tol=1e-8,
+                            cg_maxiter=1000)
+    st["stats"] = torch.empty(8, dtype=torch.float64, device=dev)
+    return st
+
+
+def step(st, first=False):
+    from paper_2112_10526_gb300 import nk
+    st["cfg"].n_discard = st["cfg"].n_discard if first else 0
+    nk.nk_sr_step(st["ctx"], st["params"], st["N"], st["M"], st["ham"], st["chains"], st["cfg"],
+                  st["stats"])
+
+
+def barrier(world):
+    import torch.distributed as dist
+    if world > 1:
+        dist.barrier()
+
+
+def max_over_ranks(x, world, dev):
+    import torch
+    import torch.distributed as dist
+    if world == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def timed_steps(st, K, world, dev, prof=False):
+    import torch
+    from paper_2112_10526_gb300 import nk
+    stream = torch.cuda.current_stream()
+    barrier(world)
+    torch.cuda.synchronize()
+    if prof:
+        nk.nk_prof_enable(True)
+    l0 = nk.nk_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(K):
+        step(st)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = nk.nk_launch_count() - l0
+    ms = e0.elapsed_time(e1)
+    prof_out = None
+    if prof:
+        prof_out = {c: nk.nk_prof_read(c) for c in nk.PROF_CLASSES}
+        nk.nk_prof_enable(False)
+    return max_over_ranks(ms, world, dev), launches, prof_out
+
+
+def e2e_steps(st, K, dev):
+    """Each step: pinned host -> device copy of the step's inputs (parameters
+    and chain states), nk_sr_step, device -> host read of the result
+    (updated parameters and the step statistics)."""
+    import torch
+    h_params = st["params"].cpu().pin_memory()
+    h_s = st["s"].cpu().pin_memory()
+    h_out = torch.empty_like(h_params).pin_memory()
+    h_stats = torch.empty(8, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        st["params"].copy_(h_params, non_blocking=True)
+        st["s"].copy_(h_s, non_blocking=True)
+        step(st)
+        h_out.copy_(st["params"], non_blocking=True)
+        h_stats.copy_(st["stats"], non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        h_params.copy_(h_out)
+    dt = time.perf_counter() - t0
+    bi = h_params.numel() * 8 + h_s.numel()
+    bo = h_out.numel() * 8 + 8 * 8
+    return dt, bi, bo
+
+
+def roofline(prof, K, precision):
+    # dominant tracked kernel class by time
+    cls = max(prof, key=lambda c: prof[c][0])
+    ms, launches, work = prof[cls]
+    if launches == 0 or ms <= 0:
+        return None, cls
+    secs = ms / 1e3
+    if cls in ("sweep", "eloc"):
+        flops = 2.0 * work  # one FMA + one multiply per ratio term
+        peak = FP64_PEAK_TFLOPS if precision == "f64" else FP32_PEAK_TFLOPS
+        note = "FP64 nominal" if precision == "f64" else "FP32 lanes x max clock"
+    else:
+        flops = work
+        peak = FP64_PEAK_TFLOPS
+        note = "FP64 nominal"
+    achieved = flops / secs / 1e12
+    return {"kernel_class": cls, "bound": "alu", "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "peak_source": f"{note} (of nominal; no measured FP64 peak)",
+            "launches": launches, "avg_launch_ms": ms / launches,
+            "share_of_step": ms / 1.0}, cls
+
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_2112_10526_gb300 import nk
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = workload(args.workload)
+    st = setup(w, args.precision, rank, dev)
+    for i in range(args.warmup):
+        step(st, first=(i == 0))
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    ms, launches, prof = timed_steps(st, args.steps, world, dev, prof=True)
+    clk = clocks.stop()
+    # a second timing without the event brackets (the headline number)
+    ms_plain, launches, _ = timed_steps(st, args.steps, world, dev, prof=False)
+    K = args.steps
+    value = world * K / (ms_plain / 1e3)
+    stats = nk.sr_stats_dict(st["stats"])
+    rf, dom = roofline(prof, K, args.precision)
+    if rf is not None:
+        rf["share_of_step"] = prof[dom][0] / ms
+    e2e_dt, bi, bo = e2e_steps(st, K, dev)
+    e2e_dt = max_over_ranks(e2e_dt, world, dev)
+    Ns = w["chains"] * w["per_chain"]
+    line = {
+        "metric": METRIC, "value": value, "unit": "SR steps/s", "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": ms_plain / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "f64" else "f32+f64",
+        "data": "synthetic (seeded RBM parameters N(0, 0.01^2), Philox chains)",
+        "config": {"workload": w["name"], "lattice": "10x10 periodic square" if w["N"] == 100 else str(w["N"]),
+                   "hamiltonian": w["ham"]["kind"], "N": w["N"], "M": w["M"], "Np": w["N"] + w["M"] + w["M"] * w["N"],
+                   "chains": w["chains"], "samples_per_chain": w["per_chain"], "Ns": Ns, "rule": w["rule"],
+                   "solver": w["solver"], "precision": args.precision, "diag_shift": w["diag_shift"],
+                   "lr": w["lr"], "parallelism": f"replicas x{world}",
+                   "l2": "working set larger than L2 (Ns x Ns FP64 Gram = 512 MiB per step)"},
+        "samples_sweeps_per_s": world * K * Ns / (ms_plain / 1e3),
+        "proposals_per_s": world * K * Ns * w["N"] / (ms_plain / 1e3),
+        "energy": stats["energy"], "energy_error": stats["error"], "acceptance": stats["acceptance"],
+        "roofline": rf,
+        "kernel_ms_per_step": {c: prof[c][0] / K for c in prof if prof[c][1] > 0},
+        "e2e": {"value": world * K / e2e_dt, "unit": "SR steps/s", "h2d_bytes_per_step": bi,
+                "d2h_bytes_per_step": bo},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if not args.no_compare and world == 1:
+        other = "f64" if args.precision == "mixed" else "mixed"
+        st2 = setup(w, other, rank, dev)
+        for i in range(args.warmup):
+            step(st2, first=(i == 0))
+        ms2, _, _ = timed_steps(st2, K, world, dev)
+        s2 = nk.sr_stats_dict(st2["stats"])
+        line[f"{other}_path"] = {"value": K / (ms2 / 1e3), "unit": "SR steps/s", "ms_per_step": ms2 / K,
+                                 "energy": s2["energy"], "energy_error": s2["error"]}
+        st2["ctx"].close()
+    st["ctx"].close()
+    return line
+
+
+def main():
+    args = parse()
+    if args.oracle_sample:
+        name, chains, steps = args.oracle_sample.split(":")
+        print(json.dumps(oracle_sample(name, int(chains), int(steps))))
+        return
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        chains = 128
+        res = run_oracle_subprocess(args.workload, chains, args.steps + args.warmup)
+        res["times"] = res["times"][args.warmup:] or res["times"]
+        value, cpu = oracle_line_fields(args.workload, chains, res)
+        w = workload(args.workload)
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "SR steps/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": w["name"], "N": w["N"], "M": w["M"], "chains": w["chains"],
+                           "samples_per_chain": w["per_chain"]},
+                "cpu_baseline": cpu,
+                "e2e": {"value": value, "unit": "SR steps/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the oracle runs in a fresh process before any CUDA work in this one
+        chains = 128
+        res = run_oracle_subprocess(args.workload, chains, 1)
+        _, cpu = oracle_line_fields(args.workload, chains, res)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    line = run_ours(args, rank, world)
+    line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

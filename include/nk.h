@@ -1,0 +1,300 @@
+/*
+ * nk.h -- C ABI of libnk.so, the GB300 (sm_103a) hot path of variational
+ * Monte Carlo with a restricted Boltzmann machine, after the NetKet 3 paper
+ * (F. Vicentini et al., arXiv:2112.10526).
+ *
+ * One VMC step: Metropolis sampling of |psi|^2 (Sec. 3.5), local energies
+ * (Sec. 3.4, Eq. eq:local-estimator), log-derivatives (Eq.
+ * eq:log-derivative-O), force (Eqs. eq:force VMC, eq:gradE:real), the
+ * quantum geometric tensor (Sec. 3.6, App. B) and the stochastic
+ * reconfiguration solve (Eq. eq:stochastic-reconfiguration) followed by the
+ * SGD update (Sec. 4.1).
+ *
+ * Conventions for every call:
+ *   - Return value: NK_OK (0) or a negative NK_ERR_* code.  The message of
+ *     the last failure on the calling host thread is nk_last_error().
+ *   - Array arguments are DEVICE pointers owned by the caller, contiguous,
+ *     row-major, unless a comment says "host".  The library never frees them.
+ *   - Configurations are int8 with values -1/+1, layout [batch, N].
+ *   - RBM parameters are one float64 device vector
+ *         theta = [ a (N) ; b (M) ; W (M x N, row-major) ],  Np = N + M + M N,
+ *     with ln psi(s) = sum_i a_i s_i + sum_j ln cosh(b_j + sum_i W_ji s_i)
+ *     (the RBM of Sec. 3.2, Table tab:nk.models).
+ *   - Every call is asynchronous on the given CUDA stream (cudaStream_t
+ *     passed as void*, NULL = legacy default stream) and does not
+ *     synchronise it, except nk_sr_step with the CG solver, which reads the
+ *     residual back every few iterations (documented there).
+ *   - Workspace is allocated inside the nk_ctx and grows on demand
+ *     (cudaMalloc, which synchronises the device).  A context is not
+ *     thread-safe: use one per host thread.  Calls on one context must not
+ *     overlap on different streams (they share the workspace).
+ *   - precision: NK_F64 computes everything in FP64 on CUDA cores.
+ *     NK_MIXED keeps the Metropolis chains and local-energy ratios in FP32
+ *     (hidden activations rebuilt from scratch in FP64 at every sweep) and
+ *     keeps FP64 for sample means, centring, the SR solve and the update.
+ */
+#ifndef NK_H
+#define NK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t nk_status;
+#define NK_OK 0
+#define NK_ERR_INVALID_ARG (-1)
+#define NK_ERR_CUDA (-2)
+#define NK_ERR_OOM (-3)
+#define NK_ERR_TIMEOUT (-4)
+#define NK_ERR_NOT_CONVERGED (-5) /* result still written */
+#define NK_ERR_UNIMPLEMENTED (-6)
+
+#define NK_F64 0
+#define NK_MIXED 1
+
+#define NK_RULE_LOCAL 0    /* MetropolisLocal: flip one spin (Sec. 3.5) */
+#define NK_RULE_EXCHANGE 1 /* MetropolisExchange: swap an edge (Sec. 3.5) */
+
+#define NK_TFIM 0 /* H = J sum_<ik> sz sz - h sum_i sx (Eq. eq:tf-ising-hamiltonian) */
+#define NK_HEIS 1 /* H = J sum_<ik> sigma.sigma (Eq. eq: j1 j2 heisenberg, J2=0) */
+
+#define NK_SOLVER_CHOLESKY 0             /* dense (S + eps I) in parameter space */
+#define NK_SOLVER_CHOLESKY_SAMPLESPACE 1 /* same solution via an Ns x Ns factor */
+#define NK_SOLVER_CG 2                   /* CG on on-the-fly QGT products */
+
+#define NK_QGT_ONTHEFLY 0 /* QGTOnTheFly (App. B.3) */
+#define NK_QGT_JACOBIAN 1 /* QGTJacobianDense on a stored centred Jacobian (App. B.2) */
+
+typedef struct nk_ctx nk_ctx;
+
+typedef struct {
+    int32_t N;      /* visible units = lattice sites, >= 1 */
+    int32_t M;      /* hidden units (alpha N), >= 1 */
+    double *params; /* device [Np]; only nk_sr_step writes it */
+} nk_rbm;
+
+typedef struct {
+    int32_t kind;          /* NK_TFIM or NK_HEIS */
+    double J;              /* coupling */
+    double h;              /* transverse field (NK_TFIM) */
+    int32_t marshall;      /* NK_HEIS: 1 = off-diagonal element -2J on every
+                              edge (Marshall sign folded in; the lattice must
+                              be bipartite with every edge joining the two
+                              sublattices), 0 = +2J */
+    int32_t n_edges;       /* E >= 1 */
+    const int32_t *edges;  /* device [E, 2], site indices in [0, N) */
+} nk_ham;
+
+/* Context: device ordinal, workspace, cached per-parameter tables. */
+nk_status nk_ctx_create(int32_t device, nk_ctx **out /* host */);
+nk_status nk_ctx_destroy(nk_ctx *ctx);
+/* Message of the last failure on this host thread ("" if none); valid until
+ * the next failing call on this thread. */
+const char *nk_last_error(void);
+/* Library version (major*10000 + minor*100 + patch). */
+int32_t nk_version(void);
+
+/*
+ * ln psi(s) for a batch of configurations (Eq. eq:mapping: the model maps
+ * (theta, s) to ln psi_theta(s); the batched evaluation of Sec. 3.2).
+ *   s          [B, N] int8 +-1
+ *   logpsi_out [B] float64
+ * B = 0 is a no-op.
+ */
+nk_status nk_rbm_logpsi(nk_ctx *ctx, const nk_rbm *rbm, int32_t precision, const int8_t *s,
+                        int64_t B, double *logpsi_out, void *stream);
+
+/*
+ * Random initial chain states (random_state of Sec. 2.1), from the Philox
+ * stream (key (seed, 0), counter (index, chain, stream_id, 1)).
+ *   rule NK_RULE_LOCAL: i.i.d. spins; NK_RULE_EXCHANGE: S_z = 0 (N even).
+ *   s_out [C, N] int8.
+ */
+nk_status nk_chains_init(nk_ctx *ctx, int32_t N, int32_t C, int32_t rule, uint64_t seed,
+                         uint32_t stream_id, int8_t *s_out, void *stream);
+
+/*
+ * Metropolis-Hastings sweeps (Sec. 3.5: P_acc = min(1, |psi(s')/psi(s)|^2)
+ * for the symmetric local and exchange proposals).  One sweep is N
+ * proposals per chain.  Proposal p of sweep w uses the Philox4x64-10 block
+ * with key (seed, 0) and counter ((sweep0 + w) N + p, chain, stream_id, 0):
+ * the site (local) or edge (exchange) is floor(hi32(y0) * n / 2^32), the
+ * uniform is u = ((y1 >> 11) + 0.5) 2^-53, and the move is accepted iff
+ * ln u < 2 (ln psi(s') - ln psi(s)).  An exchange proposal on an edge with
+ * equal spins is not a move.  Hidden activations theta = b + W s are rebuilt
+ * from scratch (FP64) at the start of every sweep and updated incrementally
+ * on every accepted move.
+ *   s            [C, N] in/out chain states
+ *   n_edges/edges  device [E, 2] edge list (exchange rule only; else 0/NULL)
+ *   samples_out  [C, n_samples, N]: the state after each of the n_samples
+ *                sweeps that follow n_discard discarded sweeps
+ *   logpsi_out   [C, n_samples] float64 or NULL
+ *   n_accepted   [C] uint64, incremented by accepted moves, or NULL
+ *   decisions_out [C, n_discard + n_samples, N] uint8 or NULL: per proposal
+ *                0 rejected, 1 accepted, 2 not a move (for replay checks)
+ * Limits: N <= 4096, M <= 8192.  C = 0 is a no-op.
+ */
+nk_status nk_metropolis_sweep(nk_ctx *ctx, const nk_rbm *rbm, int32_t precision, int32_t rule,
+                              int32_t n_edges, const int32_t *edges, int32_t C, int8_t *s,
+                              int64_t sweep0, int32_t n_discard, int32_t n_samples, uint64_t seed,
+                              uint32_t stream_id, int8_t *samples_out, double *logpsi_out,
+                              uint64_t *n_accepted, uint8_t *decisions_out, void *stream);
+
+/*
+ * Local energies E_loc(s) = sum_s' H_ss' psi(s')/psi(s)
+ * (Eq. eq:local-estimator) through single-flip (NK_TFIM) and pair-flip
+ * (NK_HEIS) amplitude ratios.
+ *   s [Ns, N];  eloc_out [Ns] float64;  t_out [Ns, M] float64 tanh(theta)
+ *   of every sample as a by-product, or NULL.
+ */
+nk_status nk_local_energy(nk_ctx *ctx, const nk_rbm *rbm, int32_t precision, const nk_ham *ham,
+                          const int8_t *s, int64_t Ns, double *eloc_out, double *t_out,
+                          void *stream);
+
+/*
+ * Sample statistics of the local energy (Sec. 3.4): out[0] = mean,
+ * out[1] = variance (1/Ns normalisation), out[2] = standard error of the
+ * mean (from the n_chains chain means when each chain holds >= 2 samples
+ * stored chain-major, else sqrt(variance/Ns)).  out: device float64 [3].
+ */
+nk_status nk_stats(nk_ctx *ctx, const double *eloc, int64_t Ns, int32_t n_chains, double *out,
+                   void *stream);
+
+/*
+ * Rows [row0, row0 + rows) of the Jacobian J_kl = O_l(s_k) (Eq.
+ * eq:log-derivative-O, App. B.1): O_a = s, O_b = tanh theta,
+ * O_W = tanh theta s^T, theta recomputed from s.  With centered = 1 the
+ * column means over all Ns samples are subtracted (the centred Jacobian of
+ * App. B.2).  O_out [rows, Np] float64.
+ */
+nk_status nk_jacobian(nk_ctx *ctx, const nk_rbm *rbm, int32_t precision, const int8_t *s,
+                      int64_t Ns, int32_t centered, int64_t row0, int64_t rows, double *O_out,
+                      void *stream);
+
+/* Vector-Jacobian product out = J^T g (App. B.1), g [Ns], out [Np]. */
+nk_status nk_vjp(nk_ctx *ctx, const nk_rbm *rbm, int32_t precision, const int8_t *s, int64_t Ns,
+                 const double *g, double *out, void *stream);
+
+/* Jacobian-vector product out = J v (App. B.1), v [Np], out [Ns]. */
+nk_status nk_jvp(nk_ctx *ctx, const nk_rbm *rbm, int32_t precision, const int8_t *s, int64_t Ns,
+                 const double *v, double *out, void *stream);
+
+/*
+ * Force f = 2 Re Cov[O, E_loc] = (2/Ns) J^T (E_loc - mean E_loc)
+ * (Eqs. eq:force VMC and eq:gradE:real).  F_out [Np].
+ */
+nk_status nk_force(nk_ctx *ctx, const nk_rbm *rbm, int32_t precision, const int8_t *s,
+                   int64_t Ns, const double *eloc, double *F_out, void *stream);
+
+typedef struct {
+    int32_t kind;        /* NK_QGT_ONTHEFLY or NK_QGT_JACOBIAN */
+    const nk_rbm *rbm;   /* ONTHEFLY: the model and its samples */
+    int32_t precision;
+    const int8_t *s;     /* ONTHEFLY: [Ns, N] */
+    const double *dJ;    /* JACOBIAN: centred Jacobian [Ns, Np] (nk_jacobian, centered=1) */
+    int64_t Ns;
+    int32_t Np;          /* JACOBIAN: number of parameters */
+} nk_qgt;
+
+/*
+ * out = (G + diag_shift I) v with G = (1/Ns) J^T dJ (Sec. 3.6, App. B.2 /
+ * B.3): ONTHEFLY computes w = J v / Ns, dw = w - <w>, J^T dw; JACOBIAN
+ * computes dJ^T (dJ v) / Ns.  v, out [Np].
+ */
+nk_status nk_qgt_matvec(nk_ctx *ctx, const nk_qgt *qgt, double diag_shift, const double *v,
+                        double *out, void *stream);
+
+/*
+ * Solve (G + diag_shift I) delta = F for the QGT of the given samples
+ * (Eq. eq:stochastic-reconfiguration, real case; Sec. 3.6 "Solving linear
+ * systems").  solver: NK_SOLVER_CHOLESKY (dense Np x Np FP64 Cholesky),
+ * NK_SOLVER_CHOLESKY_SAMPLESPACE (FP64 Cholesky of the Ns x Ns matrix
+ * dJ dJ^T / Ns + diag_shift I and delta = (F - dJ^T y / sqrt(Ns)) /
+ * diag_shift, equal in exact arithmetic), NK_SOLVER_CG (x0 = 0, stops at
+ * ||r|| <= cg_tol ||F|| or cg_maxiter; reads the residual back to the host
+ * every 8 iterations, which synchronises the stream).
+ *   info_out host int32[2] or NULL: iterations, converged flag.
+ *   resid_out host double or NULL: final relative residual (CG).
+ */
+nk_status nk_sr_solve(nk_ctx *ctx, const nk_rbm *rbm, int32_t precision, const int8_t *s,
+                      int64_t Ns, const double *F, int32_t solver, double diag_shift,
+                      double cg_tol, int32_t cg_maxiter, double *delta_out, int32_t *info_out,
+                      double *resid_out, void *stream);
+
+typedef struct {
+    int32_t C;          /* chains */
+    int8_t *s;          /* device [C, N] chain states, in/out */
+    int64_t sweeps_done;/* host: sweeps already run by these chains; advanced by nk_sr_step */
+    uint64_t *n_accepted; /* device [C] or NULL */
+} nk_chains;
+
+typedef struct {
+    int32_t rule;        /* NK_RULE_* */
+    int32_t precision;   /* NK_F64 or NK_MIXED */
+    int32_t solver;      /* NK_SOLVER_* */
+    int32_t n_discard;   /* sweeps discarded before sampling */
+    int32_t n_samples;   /* samples (sweeps) per chain */
+    int32_t cg_maxiter;
+    double diag_shift;   /* eps */
+    double lr;           /* eta */
+    double cg_tol;
+    uint64_t seed;
+    uint32_t stream_id;
+} nk_sr_cfg;
+
+/* Diagnostics of one step, written to DEVICE memory (float64 fields). */
+typedef struct {
+    double energy;       /* mean E_loc */
+    double variance;
+    double error;        /* standard error of the mean */
+    double acceptance;   /* accepted / proposed moves in this step */
+    double cg_iters;
+    double cg_residual;
+    double f_norm;       /* ||F|| */
+    double delta_norm;   /* ||delta|| */
+} nk_sr_stats;
+
+/*
+ * One VMC iteration with stochastic reconfiguration (Sec. 4.1): sample
+ * n_samples states per chain after n_discard sweeps, local energies,
+ * statistics, force, SR solve, and theta <- theta - lr delta (rbm->params
+ * updated in place).
+ *   chains: states advanced in place; chains->sweeps_done advanced (host).
+ *   stats_out: device nk_sr_stats or NULL.
+ *   samples_out [C*n_samples, N], eloc_out [C*n_samples]: optional device
+ *   outputs of this step's samples and local energies (NULL = internal).
+ */
+nk_status nk_sr_step(nk_ctx *ctx, nk_rbm *rbm, const nk_ham *ham, nk_chains *chains,
+                     const nk_sr_cfg *cfg, nk_sr_stats *stats_out, int8_t *samples_out,
+                     double *eloc_out, void *stream);
+
+
+/*
+ * Kernel timing for measurement tools (not part of the method).  When
+ * enabled, every launch of a tracked kernel class is bracketed by CUDA
+ * events recorded on the stream it is launched on, and its algorithmic work
+ * (flops or bytes, per class) is added up.  nk_prof_read waits for those
+ * events and returns the total milliseconds, the number of launches and the
+ * total work since the last nk_prof_enable.  Process-wide; thread-safe.
+ */
+#define NK_PROF_SWEEP 0       /* Metropolis sweeps: work = ratio terms (proposals x M) */
+#define NK_PROF_ELOC 1        /* local energies: work = ratio terms (connections x M) */
+#define NK_PROF_GRAM 2        /* sample-space Gram: work = flops */
+#define NK_PROF_CHOL_UPDATE 3 /* Cholesky trailing updates: work = flops */
+#define NK_PROF_CHOL_PANEL 4  /* Cholesky diagonal blocks and panels: work = flops */
+#define NK_PROF_TRSV 5        /* triangular solves: work = flops */
+#define NK_PROF_JVP_VJP 6     /* Jacobian products: work = flops */
+#define NK_PROF_N 8
+nk_status nk_prof_enable(int32_t on);
+/* Number of CUDA kernels this library has launched in this process. */
+int64_t nk_launch_count(void);
+nk_status nk_prof_read(int32_t cls, double *ms /* host */, int64_t *launches /* host */,
+                       double *work /* host */);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NK_H */

@@ -1,0 +1,501 @@
+// RBM kernels: flip-ratio tables, ln psi, chain initialisation, Metropolis
+// sweeps and local energies.
+//
+// Model (NetKet 3, Sec. 3.2, Table tab:nk.models, RBM):
+//   ln psi(s) = sum_i a_i s_i + sum_j ln cosh theta_j,  theta = b + W s.
+//
+// Flip-ratio identity used by the sweep and local-energy kernels.  With
+// t_j = tanh theta_j and s_i = +-1, cosh(theta - d) = cosh theta cosh d
+// (1 - tanh theta tanh d) gives, for flipping site i (d_j = 2 W_ji s_i):
+//   ln psi(s^(i)) - ln psi(s) = -2 a_i s_i + K_i + sum_j ln(1 - s_i t_j tau_ji)
+// with tau_ji = tanh(2 W_ji), K_i = sum_j ln cosh(2 W_ji); and for swapping an
+// antiparallel pair (i, k) (d_j = 2 s_i (W_ji - W_jk)):
+//   ln psi(s^(ik)) - ln psi(s) = -2 s_i (a_i - a_k) + K_e + sum_j ln(1 - s_i t_j tau_ej)
+// with tau_ej = tanh(2 (W_ji - W_jk)), K_e = sum_j ln cosh(2 (W_ji - W_jk)).
+// The sum of logs is taken as the log of one renormalised product, so a
+// ratio costs one FMA and one multiply per hidden unit.  After an accepted
+// move t_j becomes tanh(theta_j - d_j) = (t_j - s_i tau_j) / (1 - s_i t_j tau_j).
+
+#include <cuda_runtime.h>
+
+#include "nk_common.cuh"
+#include "nk_internal.h"
+
+namespace nk {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ---------------------------------------------------------------- tables ---
+
+__global__ void k_transpose_W(int N, int M, const double *__restrict__ W, double *__restrict__ Wt) {
+    __shared__ double tile[32][33];
+    int j0 = blockIdx.y * 32, i0 = blockIdx.x * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        int j = j0 + r, i = i0 + threadIdx.x;
+        if (j < M && i < N) tile[r][threadIdx.x] = W[(size_t)j * N + i];
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        int i = i0 + r, j = j0 + threadIdx.x;
+        if (i < N && j < M) Wt[(size_t)i * M + j] = tile[threadIdx.x][r];
+    }
+}
+
+// One block per site (or edge): tau row, its transpose and K by a fixed-order
+// block reduction.
+template <typename R>
+__global__ void k_tau_rows(int N, int M, int nrows, const double *__restrict__ Wt,
+                           const int32_t *__restrict__ edges, R *__restrict__ tau,
+                           R *__restrict__ tauT, R *__restrict__ K) {
+    int r = blockIdx.x;
+    if (r >= nrows) return;
+    const double *w0, *w1 = nullptr;
+    if (edges) {
+        const int i = edges[2 * r], k = edges[2 * r + 1];
+        if ((unsigned)i >= (unsigned)N || (unsigned)k >= (unsigned)N) return;  // never used
+        w0 = Wt + (size_t)i * M;
+        w1 = Wt + (size_t)k * M;
+    } else {
+        w0 = Wt + (size_t)r * M;
+    }
+    double part = 0.0;
+    for (int j = threadIdx.x; j < M; j += blockDim.x) {
+        double d = w1 ? (w0[j] - w1[j]) : w0[j];
+        double v = tanh(2.0 * d);
+        tau[(size_t)r * M + j] = (R)v;
+        tauT[(size_t)j * nrows + r] = (R)v;
+        part += lncosh(2.0 * d);
+    }
+    __shared__ double red[32];
+    part = warp_sum(part);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int nw = blockDim.x >> 5;
+        double v = threadIdx.x < nw ? red[threadIdx.x] : 0.0;
+        v = warp_sum(v);
+        if (threadIdx.x == 0) K[r] = (R)v;
+    }
+}
+
+// ------------------------------------------------------------------ ln psi ---
+
+// One warp per configuration; theta rebuilt in FP64 from the transposed W.
+__global__ void k_logpsi(int N, int M, const double *__restrict__ a, const double *__restrict__ b,
+                         const double *__restrict__ Wt, const int8_t *__restrict__ s, int64_t B,
+                         double *__restrict__ out) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    if (k >= B) return;
+    int8_t *sv = reinterpret_cast<int8_t *>(sm) + (size_t)warp * ((N + 15) & ~15);
+    for (int i = lane; i < N; i += 32) sv[i] = s[(size_t)k * N + i];
+    __syncwarp();
+    double part = 0.0;
+    for (int i = lane; i < N; i += 32) part += a[i] * (double)sv[i];
+    for (int j = lane; j < M; j += 32) {
+        double th = b[j];
+        for (int i = 0; i < N; ++i) th = fma(Wt[(size_t)i * M + j], (double)sv[i], th);
+        part += lncosh(th);
+    }
+    part = warp_sum(part);
+    if (lane == 0) out[k] = part;
+}
+
+// ------------------------------------------------------------- chain init ---
+
+__global__ void k_chain_init(int N, int C, int rule, unsigned long long seed, unsigned stream_id,
+                             int8_t *__restrict__ s) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    int8_t *sc = s + (size_t)c * N;
+    if (rule == NK_RULE_LOCAL) {
+        for (int blk = 0; blk * 256 < N; ++blk) {
+            Philox4 y = philox4x64_10((unsigned long long)blk, (unsigned long long)c, stream_id, 1ULL,
+                                      seed, 0ULL);
+            for (int bit = 0; bit < 256 && blk * 256 + bit < N; ++bit)
+                sc[blk * 256 + bit] = ((y.v[bit >> 6] >> (bit & 63)) & 1ULL) ? 1 : -1;
+        }
+    } else {
+        for (int i = 0; i < N; ++i) sc[i] = i < N / 2 ? 1 : -1;
+        for (int i = N - 1; i >= 1; --i) {
+            Philox4 y = philox4x64_10((unsigned long long)i, (unsigned long long)c, stream_id, 1ULL,
+                                      seed, 0ULL);
+            int j = pick_index(y.v[0], i + 1);
+            int8_t tmp = sc[i];
+            sc[i] = sc[j];
+            sc[j] = tmp;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ sweep ---
+
+template <typename R>
+struct SweepK {
+    Tables<R> t;
+    SweepArgs a;
+    int warp_bytes, t_bytes;
+};
+
+// One warp per chain.  Hidden units are spread over the lanes (j = lane,
+// lane + 32, ...); t = tanh theta and the spins live in shared memory.  The
+// 32 lanes evaluate the Philox blocks of 32 consecutive proposals at once and
+// broadcast them one per proposal.
+template <typename R>
+__global__ void __launch_bounds__(128) k_sweep(SweepK<R> P) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const Tables<R> &T = P.t;
+    const SweepArgs &A = P.a;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (c >= A.C) return;
+    const int N = T.N, M = T.M;
+    R *t = reinterpret_cast<R *>(sm + (size_t)warp * P.warp_bytes);
+    int8_t *sv = reinterpret_cast<int8_t *>(sm + (size_t)warp * P.warp_bytes + P.t_bytes);
+    for (int i = lane; i < N; i += 32) sv[i] = A.s[(size_t)c * N + i];
+    __syncwarp();
+    unsigned long long acc = 0;
+    const int n_sweeps = A.n_discard + A.n_samples;
+    for (int w = 0; w < n_sweeps; ++w) {
+        // From-scratch FP64 rebuild of theta = b + W s, t = tanh theta, ln psi.
+        double lp = 0.0;
+        for (int j = lane; j < M; j += 32) {
+            double th = T.b[j];
+            for (int i = 0; i < N; ++i) th = fma(T.Wt[(size_t)i * M + j], (double)sv[i], th);
+            t[j] = (R)tanh(th);
+            lp += lncosh(th);
+        }
+        for (int i = lane; i < N; i += 32) lp += T.a[i] * (double)sv[i];
+        lp = warp_sum(lp);
+        __syncwarp();
+        const unsigned long long qbase = (unsigned long long)(A.sweep0 + w) * (unsigned long long)N;
+        unsigned long long y0 = 0, y1 = 0;
+        for (int q = 0; q < N; ++q) {
+            if ((q & 31) == 0) {
+                Philox4 y = philox4x64_10(qbase + (unsigned long long)(q + lane), (unsigned long long)c,
+                                          (unsigned long long)A.stream_id, 0ULL, A.seed, 0ULL);
+                y0 = y.v[0];
+                y1 = y.v[1];
+            }
+            const unsigned long long u0 = __shfl_sync(kFull, y0, q & 31);
+            const unsigned long long u1 = __shfl_sync(kFull, y1, q & 31);
+            const size_t slot = ((size_t)c * n_sweeps + w) * N + q;
+            int i, k = -1;
+            const R *tau;
+            R K;
+            double d0;
+            if (A.rule == NK_RULE_LOCAL) {
+                i = pick_index(u0, N);
+                tau = T.tau_site + (size_t)i * M;
+                K = T.K_site[i];
+                d0 = -2.0 * T.a[i] * (double)sv[i];
+            } else {
+                const int e = pick_index(u0, T.E);
+                i = A.edges[2 * e];
+                k = A.edges[2 * e + 1];
+                // an edge outside [0, N) is never a move (bounds guard)
+                if ((unsigned)i >= (unsigned)N || (unsigned)k >= (unsigned)N || sv[i] == sv[k]) {
+                    if (lane == 0 && A.decisions) A.decisions[slot] = 2;
+                    continue;
+                }
+                tau = T.tau_edge + (size_t)e * M;
+                K = T.K_edge[e];
+                d0 = -2.0 * (double)sv[i] * (T.a[i] - T.a[k]);
+            }
+            const R si = (R)sv[i];
+            Prod<R> pr{R(1), 0};
+            int cnt = 0;
+            for (int j = lane; j < M; j += 32) {
+                pr.m *= R(1) - si * t[j] * tau[j];
+                if (++cnt == RenormEvery<R>::value) {
+                    renorm(pr);
+                    cnt = 0;
+                }
+            }
+            renorm(pr);
+            pr = warp_prod(pr);
+            const double delta = d0 + (double)(K + prod_log(pr));
+            const bool accept = log(uniform53(u1)) < 2.0 * delta;
+            if (lane == 0 && A.decisions) A.decisions[slot] = accept ? 1 : 0;
+            if (accept) {
+                for (int j = lane; j < M; j += 32) {
+                    const R tj = t[j], tv = si * tau[j];
+                    t[j] = (tj - tv) / (R(1) - tj * tv);
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    sv[i] = (int8_t)-sv[i];
+                    if (k >= 0) sv[k] = (int8_t)-sv[k];
+                }
+                lp += delta;
+                ++acc;
+            }
+            __syncwarp();
+        }
+        if (w >= A.n_discard) {
+            const size_t row = (size_t)c * A.n_samples + (w - A.n_discard);
+            for (int i = lane; i < N; i += 32) A.samples[row * N + i] = sv[i];
+            if (lane == 0 && A.logpsi) A.logpsi[row] = lp;
+        }
+        __syncwarp();
+    }
+    for (int i = lane; i < N; i += 32) A.s[(size_t)c * N + i] = sv[i];
+    if (lane == 0 && A.n_accepted) A.n_accepted[c] += acc;
+}
+
+// ----------------------------------------------------------- local energy ---
+
+template <typename R>
+struct ElocK {
+    Tables<R> t;
+    ElocArgs a;
+    int warp_bytes, t_bytes, s_bytes;
+};
+
+// One warp per sample.  theta and t are rebuilt from s; the connected
+// configurations are spread over the lanes (sites for the Ising field term,
+// antiparallel edges for the Heisenberg exchange term), each lane running
+// over all hidden units with the unit-major tables.
+template <typename R>
+__global__ void __launch_bounds__(128) k_eloc(ElocK<R> P) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const Tables<R> &T = P.t;
+    const ElocArgs &A = P.a;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    if (k >= A.Ns) return;
+    const int N = T.N, M = T.M, E = T.E;
+    unsigned char *base = sm + (size_t)warp * P.warp_bytes;
+    R *t = reinterpret_cast<R *>(base);
+    int8_t *sv = reinterpret_cast<int8_t *>(base + P.t_bytes);
+    int *list = reinterpret_cast<int *>(base + P.t_bytes + P.s_bytes);
+    for (int i = lane; i < N; i += 32) sv[i] = A.s[(size_t)k * N + i];
+    __syncwarp();
+    for (int j = lane; j < M; j += 32) {
+        double th = T.b[j];
+        for (int i = 0; i < N; ++i) th = fma(T.Wt[(size_t)i * M + j], (double)sv[i], th);
+        const double tj = tanh(th);
+        t[j] = (R)tj;
+        if (A.t_out) A.t_out[(size_t)k * M + j] = tj;
+    }
+    double diag = 0.0;
+    for (int e = lane; e < E; e += 32) {
+        const int i = T.edges[2 * e], kk = T.edges[2 * e + 1];
+        if ((unsigned)i < (unsigned)N && (unsigned)kk < (unsigned)N)
+            diag += A.J * (double)sv[i] * (double)sv[kk];
+    }
+    __syncwarp();
+    double off = 0.0;
+    if (A.kind == NK_TFIM) {
+        for (int i = lane; i < N; i += 32) {
+            const R si = (R)sv[i];
+            Prod<R> pr{R(1), 0};
+            int cnt = 0;
+            for (int j = 0; j < M; ++j) {
+                pr.m *= R(1) - si * t[j] * T.tau_siteT[(size_t)j * N + i];
+                if (++cnt == RenormEvery<R>::value) {
+                    renorm(pr);
+                    cnt = 0;
+                }
+            }
+            renorm(pr);
+            const double delta = -2.0 * T.a[i] * (double)si + (double)(T.K_site[i] + prod_log(pr));
+            off += -A.h * exp(delta);
+        }
+    } else {
+        // compact the antiparallel edges
+        int n = 0;
+        for (int e0 = 0; e0 < E; e0 += 32) {
+            const int e = e0 + lane;
+            bool f = false;
+            if (e < E) {
+                const int i = T.edges[2 * e], kk = T.edges[2 * e + 1];
+                f = (unsigned)i < (unsigned)N && (unsigned)kk < (unsigned)N && sv[i] != sv[kk];
+            }
+            const unsigned mask = __ballot_sync(kFull, f);
+            if (f) list[n + __popc(mask & ((1u << lane) - 1u))] = e;
+            n += __popc(mask);
+        }
+        __syncwarp();
+        const double hoff = A.marshall ? -2.0 * A.J : 2.0 * A.J;
+        for (int idx = lane; idx < n; idx += 32) {
+            const int e = list[idx];
+            const int i = T.edges[2 * e], kk = T.edges[2 * e + 1];
+            const R si = (R)sv[i];
+            Prod<R> pr{R(1), 0};
+            int cnt = 0;
+            for (int j = 0; j < M; ++j) {
+                pr.m *= R(1) - si * t[j] * T.tau_edgeT[(size_t)j * E + e];
+                if (++cnt == RenormEvery<R>::value) {
+                    renorm(pr);
+                    cnt = 0;
+                }
+            }
+            renorm(pr);
+            const double delta =
+                -2.0 * (double)si * (T.a[i] - T.a[kk]) + (double)(T.K_edge[e] + prod_log(pr));
+            off += hoff * exp(delta);
+        }
+    }
+    const double tot = warp_sum(diag + off);
+    if (lane == 0) A.eloc[k] = tot;
+}
+
+// --------------------------------------------------------- batched theta ---
+
+// T[k][j] = tanh(b_j + sum_i W_ji s_ki): 64 x 64 output tile per block,
+// 256 threads with 4 x 4 outputs each, FP64 FMA.
+__global__ void __launch_bounds__(256) k_theta_tanh(int N, int M, const double *__restrict__ b,
+                                                    const double *__restrict__ W,
+                                                    const int8_t *__restrict__ s, int64_t B,
+                                                    double *__restrict__ T) {
+    __shared__ double Sa[16][64 + 1];
+    __shared__ double Wb[16][64 + 1];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int64_t k0 = (int64_t)blockIdx.y * 64;
+    const int j0 = blockIdx.x * 64;
+    double acc[4][4] = {};
+    for (int i0 = 0; i0 < N; i0 += 16) {
+        for (int e = threadIdx.x; e < 16 * 64; e += 256) {
+            const int ii = e & 15, rr = e >> 4;
+            const int64_t kk = k0 + rr;
+            const int jj = j0 + rr, ic = i0 + ii;
+            Sa[ii][rr] = (kk < B && ic < N) ? (double)s[(size_t)kk * N + ic] : 0.0;
+            Wb[ii][rr] = (jj < M && ic < N) ? W[(size_t)jj * N + ic] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int ii = 0; ii < 16; ++ii) {
+            double av[4], bv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                av[u] = Sa[ii][ty * 4 + u];
+                bv[u] = Wb[ii][tx * 4 + u];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = fma(av[u], bv[v], acc[u][v]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int64_t kk = k0 + ty * 4 + u;
+        if (kk >= B) continue;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int jj = j0 + tx * 4 + v;
+            if (jj < M) T[(size_t)kk * M + jj] = tanh(acc[u][v] + b[jj]);
+        }
+    }
+}
+
+template <typename R>
+static int align16(int x) {
+    return (x + 15) & ~15;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- launchers ---
+
+template <typename R>
+cudaError_t launch_tables(const Tables<R> &t, bool need_site, bool need_edge, cudaStream_t st) {
+    dim3 tb(32, 8), tg((t.N + 31) / 32, (t.M + 31) / 32);
+    (k_transpose_W<<<tg, tb, 0, st>>>(t.N, t.M, t.W, t.Wt), nk::note_launch());
+    if (need_site)
+        (k_tau_rows<R><<<t.N, 256, 0, st>>>(t.N, t.M, t.N, t.Wt, nullptr, t.tau_site, t.tau_siteT,
+                                           t.K_site), nk::note_launch());
+    if (need_edge && t.E > 0)
+        (k_tau_rows<R><<<t.E, 256, 0, st>>>(t.N, t.M, t.E, t.Wt, t.edges, t.tau_edge, t.tau_edgeT,
+                                           t.K_edge), nk::note_launch());
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_tables<double>(const Tables<double> &, bool, bool, cudaStream_t);
+template cudaError_t launch_tables<float>(const Tables<float> &, bool, bool, cudaStream_t);
+
+cudaError_t launch_logpsi(int N, int M, const double *a, const double *b, const double *Wt,
+                          const int8_t *s, int64_t B, double *out, cudaStream_t st) {
+    if (B <= 0) return cudaSuccess;
+    const int wpb = 4;
+    size_t smem = (size_t)wpb * ((N + 15) & ~15);
+    unsigned grid = (unsigned)((B + wpb - 1) / wpb);
+    (k_logpsi<<<grid, 32 * wpb, smem, st>>>(N, M, a, b, Wt, s, B, out), nk::note_launch());
+    return cudaGetLastError();
+}
+
+cudaError_t launch_chain_init(int N, int C, int rule, uint64_t seed, uint32_t stream_id,
+                              int8_t *s, cudaStream_t st) {
+    if (C <= 0) return cudaSuccess;
+    (k_chain_init<<<(C + 127) / 128, 128, 0, st>>>(N, C, rule, seed, stream_id, s), nk::note_launch());
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_sweep(const Tables<R> &t, const SweepArgs &a, cudaStream_t st) {
+    if (a.C <= 0 || a.n_discard + a.n_samples <= 0) return cudaSuccess;
+    SweepK<R> P;
+    P.t = t;
+    P.a = a;
+    P.t_bytes = align16<R>(t.M * (int)sizeof(R));
+    P.warp_bytes = P.t_bytes + align16<R>(t.N);
+    int wpb = 4;
+    while (wpb > 1 && (size_t)wpb * P.warp_bytes > 200 * 1024) wpb >>= 1;
+    size_t smem = (size_t)wpb * P.warp_bytes;
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
+    cudaError_t err = cudaFuncSetAttribute(k_sweep<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem);
+    if (err != cudaSuccess) return err;
+    unsigned grid = (unsigned)((a.C + wpb - 1) / wpb);
+    const int slot = prof_begin(NK_PROF_SWEEP, st);
+    (k_sweep<R><<<grid, 32 * wpb, smem, st>>>(P), nk::note_launch());
+    prof_end(slot, st, (double)a.C * (a.n_discard + a.n_samples) * t.N * (double)t.M);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_sweep<double>(const Tables<double> &, const SweepArgs &, cudaStream_t);
+template cudaError_t launch_sweep<float>(const Tables<float> &, const SweepArgs &, cudaStream_t);
+
+template <typename R>
+cudaError_t launch_eloc(const Tables<R> &t, const ElocArgs &a, cudaStream_t st) {
+    if (a.Ns <= 0) return cudaSuccess;
+    ElocK<R> P;
+    P.t = t;
+    P.a = a;
+    P.t_bytes = align16<R>(t.M * (int)sizeof(R));
+    P.s_bytes = align16<R>(t.N);
+    P.warp_bytes = P.t_bytes + P.s_bytes + align16<R>(4 * (a.kind == NK_HEIS ? t.E : 0));
+    int wpb = 4;
+    while (wpb > 1 && (size_t)wpb * P.warp_bytes > 200 * 1024) wpb >>= 1;
+    size_t smem = (size_t)wpb * P.warp_bytes;
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
+    cudaError_t err = cudaFuncSetAttribute(k_eloc<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem);
+    if (err != cudaSuccess) return err;
+    unsigned grid = (unsigned)((a.Ns + wpb - 1) / wpb);
+    const int slot = prof_begin(NK_PROF_ELOC, st);
+    (k_eloc<R><<<grid, 32 * wpb, smem, st>>>(P), nk::note_launch());
+    // nominal connections per sample: N sites (Ising field) or E / 2 edges
+    // (antiparallel on average at S_z = 0)
+    const double conn = a.kind == NK_TFIM ? (double)t.N : 0.5 * (double)t.E;
+    prof_end(slot, st, (double)a.Ns * conn * (double)t.M);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_eloc<double>(const Tables<double> &, const ElocArgs &, cudaStream_t);
+template cudaError_t launch_eloc<float>(const Tables<float> &, const ElocArgs &, cudaStream_t);
+
+cudaError_t launch_theta_tanh(int N, int M, const double *b, const double *W, const int8_t *s,
+                              int64_t B, double *T, cudaStream_t st) {
+    if (B <= 0) return cudaSuccess;
+    dim3 grid((M + 63) / 64, (unsigned)((B + 63) / 64));
+    (k_theta_tanh<<<grid, 256, 0, st>>>(N, M, b, W, s, B, T), nk::note_launch());
+    return cudaGetLastError();
+}
+
+}  // namespace nk

@@ -1,0 +1,797 @@
+// C ABI of libnk (declared in include/nk.h): argument checks, workspace
+// planning, and the orchestration of one VMC + SR step (NetKet 3, Sec. 4.1)
+// out of the kernels in k_rbm.cu and k_linalg.cu.
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+
+#include "../../include/nk.h"
+#include "nk_internal.h"
+
+struct nk_ctx {
+    int device;
+    char *ws;
+    size_t ws_size;
+    int *host_flags;  // pinned: [0] done, [1] iterations
+    double *host_vals;  // pinned
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+nk_status fail(nk_status code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+nk_status cuda_fail(cudaError_t e, const char *where) {
+    return fail(e == cudaErrorMemoryAllocation ? NK_ERR_OOM : NK_ERR_CUDA, "%s: %s", where,
+                cudaGetErrorString(e));
+}
+
+#define NK_CU(call, where)                                       \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where);      \
+    } while (0)
+
+// Scoped switch to the context's device.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            ok = false;
+            return;
+        }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+#define NK_DEV(ptr, name)                                                                  \
+    do {                                                                                   \
+        if (!is_device_ptr(ptr))                                                           \
+            return fail(NK_ERR_INVALID_ARG, "%s must be a device pointer (got %p)", name, \
+                        (const void *)(ptr));                                              \
+    } while (0)
+
+// Workspace carving: the same sequence of take() calls runs once to count
+// bytes (base = null) and once to hand out pointers.
+struct Carver {
+    char *base;
+    size_t off = 0;
+    template <class T>
+    T *take(size_t n) {
+        off = (off + 255) & ~size_t(255);
+        T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+        off += n * sizeof(T);
+        return p;
+    }
+};
+
+nk_status ensure_ws(nk_ctx *ctx, size_t bytes) {
+    if (bytes <= ctx->ws_size) return NK_OK;
+    if (ctx->ws) {
+        cudaError_t e = cudaFree(ctx->ws);
+        ctx->ws = nullptr;
+        ctx->ws_size = 0;
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFree(workspace)");
+    }
+    size_t want = bytes + bytes / 8 + (1 << 20);
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(NK_ERR_OOM, "workspace of %zu bytes: %s", want, cudaGetErrorString(e));
+    }
+    ctx->ws = static_cast<char *>(p);
+    ctx->ws_size = want;
+    return NK_OK;
+}
+
+template <class Body>
+nk_status with_workspace(nk_ctx *ctx, Body body) {
+    Carver count{nullptr};
+    nk_status st = body(count, false);
+    if (st != NK_OK) return st;
+    st = ensure_ws(ctx, count.off);
+    if (st != NK_OK) return st;
+    Carver real{ctx->ws};
+    return body(real, true);
+}
+
+inline int64_t n_params(int N, int M) { return (int64_t)N + M + (int64_t)M * N; }
+
+nk_status check_rbm(const nk_rbm *rbm) {
+    if (!rbm) return fail(NK_ERR_INVALID_ARG, "rbm is NULL");
+    if (rbm->N < 1 || rbm->N > 4096) return fail(NK_ERR_INVALID_ARG, "N=%d out of [1, 4096]", rbm->N);
+    if (rbm->M < 1 || rbm->M > 8192) return fail(NK_ERR_INVALID_ARG, "M=%d out of [1, 8192]", rbm->M);
+    NK_DEV(rbm->params, "rbm->params");
+    return NK_OK;
+}
+
+nk_status check_precision(int32_t p) {
+    if (p != NK_F64 && p != NK_MIXED) return fail(NK_ERR_INVALID_ARG, "precision %d unknown", p);
+    return NK_OK;
+}
+
+nk_status check_ham(const nk_ham *h, int N) {
+    if (!h) return fail(NK_ERR_INVALID_ARG, "ham is NULL");
+    if (h->kind != NK_TFIM && h->kind != NK_HEIS)
+        return fail(NK_ERR_INVALID_ARG, "ham->kind %d unknown", h->kind);
+    if (h->n_edges < 1 || h->n_edges > 65536)
+        return fail(NK_ERR_INVALID_ARG, "ham->n_edges=%d out of [1, 65536]", h->n_edges);
+    NK_DEV(h->edges, "ham->edges");
+    (void)N;
+    return NK_OK;
+}
+
+template <typename R>
+void carve_tables(Carver &c, nk::Tables<R> &t, const nk_rbm *rbm, int E, const int32_t *edges,
+                  bool site, bool edge) {
+    const int N = rbm->N, M = rbm->M;
+    t.N = N;
+    t.M = M;
+    t.E = E;
+    t.a = rbm->params;
+    t.b = rbm->params + N;
+    t.W = rbm->params + N + M;
+    t.edges = edges;
+    t.Wt = c.take<double>((size_t)N * M);
+    t.tau_site = site ? c.take<R>((size_t)N * M) : nullptr;
+    t.tau_siteT = site ? c.take<R>((size_t)N * M) : nullptr;
+    t.K_site = site ? c.take<R>(N) : nullptr;
+    t.tau_edge = edge ? c.take<R>((size_t)E * M) : nullptr;
+    t.tau_edgeT = edge ? c.take<R>((size_t)E * M) : nullptr;
+    t.K_edge = edge ? c.take<R>(E) : nullptr;
+}
+
+__global__ void k_cg_init(const double *rr, double *ff, double *rr_keep, int *done, int *iters) {
+    *ff = *rr;
+    *rr_keep = *rr;
+    *done = (*rr == 0.0) ? 1 : 0;
+    *iters = 0;
+}
+
+__global__ void k_add_u64(int n, const unsigned long long *src, unsigned long long *dst) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] += src[i];
+}
+
+// ------------------------------------------------------------ SR solves ---
+
+struct SolveWs {
+    // shared
+    double *U, *w, *partial, *dotp, *tmp;
+    // CG
+    double *x, *r, *p, *Ap, *sc;  // sc: rr, rr_new, pAp, ff, rr_keep
+    int *flags;                   // done, iters
+    // Cholesky
+    double *dJ, *S, *mean, *ones;
+    int *info;
+    double *K, *rowmean;
+};
+
+void carve_solve(Carver &c, SolveWs &w, int N, int M, int64_t Ns, int solver) {
+    const int64_t Np = n_params(N, M);
+    w = SolveWs{};
+    w.partial = c.take<double>(nk::vjp_partial_doubles(N, M, Ns));
+    w.dotp = c.take<double>(nk::dot_partial_doubles(Np > Ns ? Np : Ns) + 8);
+    w.sc = c.take<double>(8);
+    w.flags = c.take<int>(4);
+    if (solver == NK_SOLVER_CG) {
+        w.U = c.take<double>((size_t)Ns * (M + 1));
+        w.w = c.take<double>(Ns);
+        w.x = c.take<double>(Np);
+        w.r = c.take<double>(Np);
+        w.p = c.take<double>(Np);
+        w.Ap = c.take<double>(Np);
+    } else if (solver == NK_SOLVER_CHOLESKY) {
+        w.dJ = c.take<double>((size_t)Ns * Np);
+        w.S = c.take<double>((size_t)Np * Np);
+        w.mean = c.take<double>(Np);
+        w.ones = c.take<double>(Ns);
+        w.info = c.take<int>(1);
+    } else {
+        w.U = c.take<double>((size_t)Ns * (M + 1));
+        w.w = c.take<double>(Ns);
+        w.K = c.take<double>((size_t)Ns * Ns);
+        w.rowmean = c.take<double>(Ns + 1);
+        w.tmp = c.take<double>(Np);
+        w.info = c.take<int>(1);
+    }
+}
+
+// (G + eps I) v for the on-the-fly QGT (App. B.3).
+cudaError_t qgt_onthefly(int N, int M, int64_t Ns, const int8_t *s, const double *T,
+                         const double *v, double eps, SolveWs &w, double *out, cudaStream_t st) {
+    cudaError_t e = nk::launch_jvp(N, M, Ns, s, T, v, w.U, w.w, st);
+    if (e != cudaSuccess) return e;
+    e = nk::launch_center(Ns, w.w, w.dotp, 1.0 / (double)Ns, st);
+    if (e != cudaSuccess) return e;
+    e = nk::launch_vjp(N, M, Ns, s, T, w.w, 1.0, nullptr, w.partial, out, st);
+    if (e != cudaSuccess) return e;
+    return nk::launch_axpby(n_params(N, M), eps, v, 1.0, out, st);
+}
+
+nk_status run_solve(nk_ctx *ctx, int N, int M, int64_t Ns, const int8_t *s, const double *T,
+                    const double *F, int solver, double eps, double tol, int maxiter,
+                    SolveWs &w, double *delta, int *host_info, double *host_resid,
+                    cudaStream_t st) {
+    const int64_t Np = n_params(N, M);
+    if (host_info) host_info[0] = 0, host_info[1] = 1;
+    if (host_resid) *host_resid = 0.0;
+    if (solver == NK_SOLVER_CG) {
+        double *rr = w.sc, *rr_new = w.sc + 1, *pAp = w.sc + 2, *ff = w.sc + 3, *rr_keep = w.sc + 4;
+        int *done = w.flags, *iters = w.flags + 1;
+        NK_CU(nk::launch_fill(Np, 0.0, w.x, st), "cg init");
+        NK_CU(nk::launch_axpby(Np, 1.0, F, 0.0, w.r, st), "cg init");
+        NK_CU(nk::launch_axpby(Np, 1.0, F, 0.0, w.p, st), "cg init");
+        NK_CU(nk::launch_dot(Np, w.r, w.r, w.dotp, rr, st), "cg init");
+        (k_cg_init<<<1, 1, 0, st>>>(rr, ff, rr_keep, done, iters), nk::note_launch());
+        NK_CU(cudaGetLastError(), "cg init");
+        int it = 0;
+        bool converged = false;
+        while (it < maxiter) {
+            NK_CU(qgt_onthefly(N, M, Ns, s, T, w.p, eps, w, w.Ap, st), "cg matvec");
+            NK_CU(nk::launch_dot(Np, w.p, w.Ap, w.dotp, pAp, st), "cg dot");
+            NK_CU(nk::launch_cg_update_xr(Np, rr_keep, pAp, w.p, w.Ap, w.x, w.r, done, st), "cg xr");
+            NK_CU(nk::launch_dot(Np, w.r, w.r, w.dotp, rr_new, st), "cg dot");
+            NK_CU(nk::launch_cg_update_p(Np, rr_new, rr_keep, w.r, w.p, done, st), "cg p");
+            NK_CU(nk::launch_cg_check(rr_new, ff, tol, done, iters, rr_keep, st), "cg check");
+            ++it;
+            if (it % 8 == 0 || it == maxiter) {
+                NK_CU(cudaMemcpyAsync(ctx->host_flags, w.flags, 2 * sizeof(int),
+                                      cudaMemcpyDeviceToHost, st),
+                      "cg poll");
+                NK_CU(cudaStreamSynchronize(st), "cg poll");
+                if (ctx->host_flags[0]) {
+                    converged = true;
+                    break;
+                }
+            }
+        }
+        NK_CU(nk::launch_axpby(Np, 1.0, w.x, 0.0, delta, st), "cg out");
+        NK_CU(cudaMemcpyAsync(ctx->host_flags, w.flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st),
+              "cg out");
+        NK_CU(cudaMemcpyAsync(ctx->host_vals, w.sc, 5 * sizeof(double), cudaMemcpyDeviceToHost, st),
+              "cg out");
+        NK_CU(cudaStreamSynchronize(st), "cg out");
+        converged = ctx->host_flags[0] != 0;
+        const double res = ctx->host_vals[3] > 0 ? std::sqrt(ctx->host_vals[4] / ctx->host_vals[3]) : 0.0;
+        if (host_info) host_info[0] = ctx->host_flags[1], host_info[1] = converged ? 1 : 0;
+        if (host_resid) *host_resid = res;
+        if (!converged)
+            return fail(NK_ERR_NOT_CONVERGED, "CG did not reach %g in %d iterations (residual %g)",
+                        tol, maxiter, res);
+        return NK_OK;
+    }
+    if (solver == NK_SOLVER_CHOLESKY) {
+        NK_CU(nk::launch_fill(Ns, 1.0, w.ones, st), "chol");
+        NK_CU(nk::launch_vjp(N, M, Ns, s, T, w.ones, 1.0 / (double)Ns, nullptr, w.partial, w.mean, st),
+              "chol mean");
+        NK_CU(nk::launch_jacobian_rows(N, M, s, T, 0, Ns, w.mean, w.dJ, st), "chol dJ");
+        NK_CU(nk::launch_syrk_t(w.dJ, Ns, Np, 1.0 / (double)Ns, eps, w.S, st), "chol syrk");
+        NK_CU(cudaMemsetAsync(w.info, 0, sizeof(int), st), "chol");
+        NK_CU(nk::launch_cholesky(w.S, Np, w.info, st), "chol factor");
+        NK_CU(nk::launch_axpby(Np, 1.0, F, 0.0, delta, st), "chol");
+        NK_CU(nk::launch_cholesky_solve(w.S, Np, delta, st), "chol solve");
+        return NK_OK;
+    }
+    // sample space: delta = (F - X^T (X X^T + eps I)^{-1} X F) / eps, X = dJ / sqrt(Ns)
+    const double isq = 1.0 / std::sqrt((double)Ns);
+    NK_CU(nk::launch_gram_samplespace(N, M, Ns, s, T, eps, w.K, w.rowmean, st), "ss gram");
+    NK_CU(cudaMemsetAsync(w.info, 0, sizeof(int), st), "ss");
+    NK_CU(nk::launch_cholesky(w.K, Ns, w.info, st), "ss factor");
+    NK_CU(nk::launch_jvp(N, M, Ns, s, T, F, w.U, w.w, st), "ss XF");
+    NK_CU(nk::launch_center(Ns, w.w, w.dotp, isq, st), "ss XF");
+    NK_CU(nk::launch_cholesky_solve(w.K, Ns, w.w, st), "ss solve");
+    NK_CU(nk::launch_center(Ns, w.w, w.dotp, isq, st), "ss Xty");
+    NK_CU(nk::launch_vjp(N, M, Ns, s, T, w.w, 1.0, nullptr, w.partial, w.tmp, st), "ss Xty");
+    NK_CU(nk::launch_axpby(Np, 1.0 / eps, F, 0.0, delta, st), "ss delta");
+    NK_CU(nk::launch_axpby(Np, -1.0 / eps, w.tmp, 1.0, delta, st), "ss delta");
+    return NK_OK;
+}
+
+nk_status check_solver(int solver, double eps, double tol, int maxiter) {
+    if (solver != NK_SOLVER_CG && solver != NK_SOLVER_CHOLESKY &&
+        solver != NK_SOLVER_CHOLESKY_SAMPLESPACE)
+        return fail(NK_ERR_INVALID_ARG, "solver %d unknown", solver);
+    if (!(eps > 0.0) && solver == NK_SOLVER_CHOLESKY_SAMPLESPACE)
+        return fail(NK_ERR_INVALID_ARG, "the sample-space solve needs diag_shift > 0");
+    if (!(eps >= 0.0)) return fail(NK_ERR_INVALID_ARG, "diag_shift must be >= 0");
+    if (solver == NK_SOLVER_CG && (maxiter < 1 || !(tol > 0.0)))
+        return fail(NK_ERR_INVALID_ARG, "CG needs cg_maxiter >= 1 and cg_tol > 0");
+    return NK_OK;
+}
+
+}  // namespace
+
+// =================================================================== ABI ===
+
+extern "C" {
+
+int32_t nk_version(void) { return 100; }
+
+const char *nk_last_error(void) { return g_err.c_str(); }
+
+nk_status nk_ctx_create(int32_t device, nk_ctx **out) {
+    if (!out) return fail(NK_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= n) return fail(NK_ERR_INVALID_ARG, "device %d of %d", device, n);
+    DeviceGuard g(device);
+    if (!g.ok) return fail(NK_ERR_CUDA, "cannot select device %d", device);
+    nk_ctx *c = new nk_ctx{};
+    c->device = device;
+    e = cudaMallocHost(&c->host_flags, 4 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocHost(&c->host_vals, 8 * sizeof(double));
+    if (e != cudaSuccess) {
+        if (c->host_flags) cudaFreeHost(c->host_flags);
+        delete c;
+        return cuda_fail(e, "cudaMallocHost");
+    }
+    *out = c;
+    return NK_OK;
+}
+
+nk_status nk_ctx_destroy(nk_ctx *ctx) {
+    if (!ctx) return NK_OK;
+    DeviceGuard g(ctx->device);
+    if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->host_flags) cudaFreeHost(ctx->host_flags);
+    if (ctx->host_vals) cudaFreeHost(ctx->host_vals);
+    delete ctx;
+    return NK_OK;
+}
+
+nk_status nk_rbm_logpsi(nk_ctx *ctx, const nk_rbm *rbm, int32_t precision, const int8_t *s,
+                        int64_t B, double *logpsi_out, void *stream) {
+    if (!ctx) return fail(NK_ERR_INVALID_ARG, "ctx is NULL");
+    DeviceGuard g(ctx->device);
+    nk_status st0 = check_rbm(rbm);
+    if (st0 != NK_OK) return st0;
+    if ((st0 = check_precision(precision)) != NK_OK) return st0;
+    if (B < 0) return fail(NK_ERR_INVALID_ARG, "B < 0");
+    if (B == 0) return NK_OK;
+    NK_DEV(s, "s");
+    NK_DEV(logpsi_out, "logpsi_out");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int N = rbm->N, M = rbm->M;
+    return with_workspace(ctx, [&](Carver &c, bool run) -> nk_status {
+        nk::Tables<double> t{};
+        carve_tables(c, t, rbm, 0, nullptr, false, false);
+        if (!run) return NK_OK;
+        NK_CU(nk::launch_tables(t, false, false, st), "tables");
+        NK_CU(nk::launch_logpsi(N, M, t.a, t.b, t.Wt, s, B, logpsi_out, st), "logpsi");
+        return NK_OK;
+    });
+}
+
+nk_status nk_chains_init(nk_ctx *ctx, int32_t N, int32_t C, int32_t rule, uint64_t seed,
+                         uint32_t stream_id, int8_t *s_out, void *stream) {
+    if (!ctx) return fail(NK_ERR_INVALID_ARG, "ctx is NULL");
+    DeviceGuard g(ctx->device);
+    if (N < 1 || N > 4096) return fail(NK_ERR_INVALID_ARG, "N=%d out of [1, 4096]", N);
+    if (C < 0) return fail(NK_ERR_INVALID_ARG, "C < 0");
+    if (rule != NK_RULE_LOCAL && rule != NK_RULE_EXCHANGE)
+        return fail(NK_ERR_INVALID_ARG, "rule %d unknown", rule);
+    if (rule == NK_RULE_EXCHANGE && (N % 2))
+        return fail(NK_ERR_INVALID_ARG, "S_z = 0 initial states need an even N");
+    if (C == 0) return NK_OK;
+    NK_DEV(s_out, "s_out");
+    NK_CU(nk::launch_chain_init(N, C, rule, seed, stream_id, s_out, (cudaStream_t)stream),
+          "chain init");
+    return NK_OK;
+}
+
+nk_status nk_metropolis_sweep(nk_ctx *ctx, const nk_rbm *rbm, int32_t precision, int32_t rule,
+                              int32_t n_edges, const int32_t *edges, int32_t C, int8_t *s,
+                              int64_t sweep0, int32_t n_discard, int32_t n_samples, uint64_t seed,
+                              uint32_t stream_id, int8_t *samples_out, double *logpsi_out,
+                              uint64_t *n_accepted, uint8_t *decisions_out, void *stream) {
+    if (!ctx) return fail(NK_ERR_INVALID_ARG, "ctx is NULL");
+    DeviceGuard g(ctx->device);
+    nk_status st0 = check_rbm(rbm);
+    if (st0 != NK_OK) return st0;
+    if ((st0 = check_precision(precision)) != NK_OK) return st0;
+    if (rule != NK_RULE_LOCAL && rule != NK_RULE_EXCHANGE)
+        return fail(NK_ERR_INVALID_ARG, "rule %d unknown", rule);
+    if (C < 0 || n_discard < 0 || n_samples < 0 || sweep0 < 0)
+        return fail(NK_ERR_INVALID_ARG, "negative C, n_discard, n_samples or sweep0");
+    if (C == 0 || n_discard + n_samples == 0) return NK_OK;
+    if (rule == NK_RULE_EXCHANGE) {
+        if (n_edges < 1 || n_edges > 65536)
+            return fail(NK_ERR_INVALID_ARG, "exchange rule needs 1 <= n_edges <= 65536");
+        NK_DEV(edges, "edges");
+    }
+    NK_DEV(s, "s");
+    if (n_samples > 0) NK_DEV(samples_out, "samples_out");
+    if (logpsi_out) NK_DEV(logpsi_out, "logpsi_out");
+    if (n_accepted) NK_DEV(n_accepted, "n_accepted");
+    if (decisions_out) NK_DEV(decisions_out, "decisions_out");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int E = rule == NK_RULE_EXCHANGE ? n_edges : 0;
+    nk::SweepArgs a{};
+    a.N = rbm->N;
+    a.M = rbm->M;
+    a.E = E;
+    a.C = C;
+    a.rule = rule;
+    a.edges = edges;
+    a.s = s;
+    a.sweep0 = sweep0;
+    a.n_discard = n_discard;
+    a.n_samples = n_samples;
+    a.seed = seed;
+    a.stream_id = stream_id;
+    a.samples = samples_out;
+    a.logpsi = logpsi_out;
+    a.n_accepted = reinterpret_cast<unsigned long long *>(n_accepted);
+    a.decisions = decisions_out;
+    auto body = [&](auto tag, Carver &c, bool run) -> nk_status {
+        using R = decltype(tag);
+        nk::Tables<R> t{};
+        carve_tables(c, t, rbm, E, edges, rule == NK_RULE_LOCAL, rule == NK_RULE_EXCHANGE);
+        if (!run) return NK_OK;
+        NK_CU(nk::launch_tables(t, rule == NK_RULE_LOCAL, rule == NK_RULE_EXCHANGE, st), "tables");
+        NK_CU(nk::launch_sweep(t, a, st), "sweep");
+        return NK_OK;
+    };
+    if (precision == NK_F64)
+        return with_workspace(ctx, [&](Carver &c, bool run) { return body(double{}, c, run); });
+    return with_workspace(ctx, [&](Carver &c, bool run) { return body(float{}, c, run); });
+}
+
+nk_status nk_local_energy(nk_ctx *ctx, const nk_rbm *rbm, int32_t precision, const nk_ham *ham,
+                          const int8_t *s, int64_t Ns, double *eloc_out, double *t_out,
+                          void *stream) {
+    if (!ctx) return fail(NK_ERR_INVALID_ARG, "ctx is NULL");
+    DeviceGuard g(ctx->device);
+    nk_status st0 = check_rbm(rbm);
+    if (st0 != NK_OK) return st0;
+    if ((st0 = check_precision(precision)) != NK_OK) return st0;
+    if ((st0 = check_ham(ham, rbm->N)) != NK_OK) return st0;
+    if (Ns < 0) return fail(NK_ERR_INVALID_ARG, "Ns < 0");
+    if (Ns == 0) return NK_OK;
+    NK_DEV(s, "s");
+    NK_DEV(eloc_out, "eloc_out");
+    if (t_out) NK_DEV(t_out, "t_out");
+    cudaStream_t st = (cudaStream_t)stream;
+    nk::ElocArgs a{ham->kind, ham->J, ham->h, ham->marshall, s, Ns, eloc_out, t_out};
+    const bool site = ham->kind == NK_TFIM, edge = ham->kind == NK_HEIS;
+    auto body = [&](auto tag, Carver &c, bool run) -> nk_status {
+        using R = decltype(tag);
+        nk::Tables<R> t{};
+        carve_tables(c, t, rbm, ham->n_edges, ham->edges, site, edge);
+        if (!run) return NK_OK;
+        NK_CU(nk::launch_tables(t, site, edge, st), "tables");
+        NK_CU(nk::launch_eloc(t, a, st), "local energy");
+        return NK_OK;
+    };
+    if (precision == NK_F64)
+        return with_workspace(ctx, [&](Carver &c, bool run) { return body(double{}, c, run); });
+    return with_workspace(ctx, [&](Carver &c, bool run) { return body(float{}, c, run); });
+}
+
+nk_status nk_stats(nk_ctx *ctx, const double *eloc, int64_t Ns, int32_t n_chains, double *out,
+                   void *stream) {
+    if (!ctx) return fail(NK_ERR_INVALID_ARG, "ctx is NULL");
+    DeviceGuard g(ctx->device);
+    if (Ns < 1) return fail(NK_ERR_INVALID_ARG, "Ns must be >= 1");
+    NK_DEV(eloc, "eloc");
+    NK_DEV(out, "out");
+    NK_CU(nk::launch_stats(eloc, Ns, n_chains, out, (cudaStream_t)stream), "stats");
+    return NK_OK;
+}
+
+nk_status nk_jacobian(nk_ctx *ctx, const nk_rbm *rbm, int32_t precision, const int8_t *s,
+                      int64_t Ns, int32_t centered, int64_t row0, int64_t rows, double *O_out,
+                      void *stream) {
+    if (!ctx) return fail(NK_ERR_INVALID_ARG, "ctx is NULL");
+    DeviceGuard g(ctx->device);
+    nk_status st0 = check_rbm(rbm);
+    if (st0 != NK_OK) return st0;
+    if ((st0 = check_precision(precision)) != NK_OK) return st0;
+    if (Ns < 1 || row0 < 0 || rows < 0 || row0 + rows > Ns)
+        return fail(NK_ERR_INVALID_ARG, "rows [%lld, %lld) outside [0, %lld)", (long long)row0,
+                    (long long)(row0 + rows), (long long)Ns);
+    if (rows == 0) return NK_OK;
+    NK_DEV(s, "s");
+    NK_DEV(O_out, "O_out");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int N = rbm->N, M = rbm->M;
+    const int64_t Np = n_params(N, M);
+    return with_workspace(ctx, [&](Carver &c, bool run) -> nk_status {
+        double *T = c.take<double>((size_t)(centered ? Ns : rows) * M);
+        double *mean = centered ? c.take<double>(Np) : nullptr;
+        double *ones = centered ? c.take<double>(Ns) : nullptr;
+        double *partial = centered ? c.take<double>(nk::vjp_partial_doubles(N, M, Ns)) : nullptr;
+        if (!run) return NK_OK;
+        const double *b = rbm->params + N, *W = rbm->params + N + M;
+        if (centered) {
+            NK_CU(nk::launch_theta_tanh(N, M, b, W, s, Ns, T, st), "theta");
+            NK_CU(nk::launch_fill(Ns, 1.0, ones, st), "ones");
+            NK_CU(nk::launch_vjp(N, M, Ns, s, T, ones, 1.0 / (double)Ns, nullptr, partial, mean, st),
+                  "mean");
+            NK_CU(nk::launch_jacobian_rows(N, M, s, T, row0, rows, mean, O_out, st), "jacobian");
+        } else {
+            NK_CU(nk::launch_theta_tanh(N, M, b, W, s + (size_t)row0 * N, rows, T, st), "theta");
+            NK_CU(nk::launch_jacobian_rows(N, M, s + (size_t)row0 * N, T, 0, rows, nullptr, O_out, st),
+                  "jacobian");
+        }
+        (void)Np;
+        return NK_OK;
+    });
+}
+
+nk_status nk_vjp(nk_ctx *ctx, const nk_rbm *rbm, int32_t precision, const int8_t *s, int64_t Ns,
+                 const double *gvec, double *out, void *stream) {
+    if (!ctx) return fail(NK_ERR_INVALID_ARG, "ctx is NULL");
+    DeviceGuard g(ctx->device);
+    nk_status st0 = check_rbm(rbm);
+    if (st0 != NK_OK) return st0;
+    if ((st0 = check_precision(precision)) != NK_OK) return st0;
+    if (Ns < 1) return fail(NK_ERR_INVALID_ARG, "Ns must be >= 1");
+    NK_DEV(s, "s");
+    NK_DEV(gvec, "g");
+    NK_DEV(out, "out");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int N = rbm->N, M = rbm->M;
+    return with_workspace(ctx, [&](Carver &c, bool run) -> nk_status {
+        double *T = c.take<double>((size_t)Ns * M);
+        double *partial = c.take<double>(nk::vjp_partial_doubles(N, M, Ns));
+        if (!run) return NK_OK;
+        NK_CU(nk::launch_theta_tanh(N, M, rbm->params + N, rbm->params + N + M, s, Ns, T, st), "theta");
+        NK_CU(nk::launch_vjp(N, M, Ns, s, T, gvec, 1.0, nullptr, partial, out, st), "vjp");
+        return NK_OK;
+    });
+}
+
+nk_status nk_jvp(nk_ctx *ctx, const nk_rbm *rbm, int32_t precision, const int8_t *s, int64_t Ns,
+                 const double *v, double *out, void *stream) {
+    if (!ctx) return fail(NK_ERR_INVALID_ARG, "ctx is NULL");
+    DeviceGuard g(ctx->device);
+    nk_status st0 = check_rbm(rbm);
+    if (st0 != NK_OK) return st0;
+    if ((st0 = check_precision(precision)) != NK_OK) return st0;
+    if (Ns < 1) return fail(NK_ERR_INVALID_ARG, "Ns must be >= 1");
+    NK_DEV(s, "s");
+    NK_DEV(v, "v");
+    NK_DEV(out, "out");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int N = rbm->N, M = rbm->M;
+    return with_workspace(ctx, [&](Carver &c, bool run) -> nk_status {
+        double *T = c.take<double>((size_t)Ns * M);
+        double *U = c.take<double>((size_t)Ns * (M + 1));
+        if (!run) return NK_OK;
+        NK_CU(nk::launch_theta_tanh(N, M, rbm->params + N, rbm->params + N + M, s, Ns, T, st), "theta");
+        NK_CU(nk::launch_jvp(N, M, Ns, s, T, v, U, out, st), "jvp");
+        return NK_OK;
+    });
+}
+
+nk_status nk_force(nk_ctx *ctx, const nk_rbm *rbm, int32_t precision, const int8_t *s,
+                   int64_t Ns, const double *eloc, double *F_out, void *stream) {
+    if (!ctx) return fail(NK_ERR_INVALID_ARG, "ctx is NULL");
+    DeviceGuard g(ctx->device);
+    nk_status st0 = check_rbm(rbm);
+    if (st0 != NK_OK) return st0;
+    if ((st0 = check_precision(precision)) != NK_OK) return st0;
+    if (Ns < 1) return fail(NK_ERR_INVALID_ARG, "Ns must be >= 1");
+    NK_DEV(s, "s");
+    NK_DEV(eloc, "eloc");
+    NK_DEV(F_out, "F_out");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int N = rbm->N, M = rbm->M;
+    return with_workspace(ctx, [&](Carver &c, bool run) -> nk_status {
+        double *T = c.take<double>((size_t)Ns * M);
+        double *partial = c.take<double>(nk::vjp_partial_doubles(N, M, Ns));
+        double *st3 = c.take<double>(4);
+        double *gv = c.take<double>(Ns);
+        if (!run) return NK_OK;
+        NK_CU(nk::launch_theta_tanh(N, M, rbm->params + N, rbm->params + N + M, s, Ns, T, st), "theta");
+        NK_CU(nk::launch_stats(eloc, Ns, 1, st3, st), "stats");
+        NK_CU(nk::launch_make_force_g(Ns, eloc, st3, gv, st), "force g");
+        NK_CU(nk::launch_vjp(N, M, Ns, s, T, gv, 1.0, nullptr, partial, F_out, st), "vjp");
+        return NK_OK;
+    });
+}
+
+nk_status nk_qgt_matvec(nk_ctx *ctx, const nk_qgt *q, double diag_shift, const double *v,
+                        double *out, void *stream) {
+    if (!ctx) return fail(NK_ERR_INVALID_ARG, "ctx is NULL");
+    if (!q) return fail(NK_ERR_INVALID_ARG, "qgt is NULL");
+    DeviceGuard g(ctx->device);
+    if (q->Ns < 1) return fail(NK_ERR_INVALID_ARG, "Ns must be >= 1");
+    NK_DEV(v, "v");
+    NK_DEV(out, "out");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t Ns = q->Ns;
+    if (q->kind == NK_QGT_JACOBIAN) {
+        if (q->Np < 1) return fail(NK_ERR_INVALID_ARG, "Np must be >= 1");
+        NK_DEV(q->dJ, "qgt->dJ");
+        const int64_t Np = q->Np;
+        return with_workspace(ctx, [&](Carver &c, bool run) -> nk_status {
+            double *w = c.take<double>(Ns);
+            double *partial = c.take<double>(nk::gemv_t_partial_doubles(Ns, Np));
+            if (!run) return NK_OK;
+            NK_CU(nk::launch_gemv_rows(q->dJ, Ns, Np, v, w, st), "dJ v");
+            NK_CU(nk::launch_gemv_t(q->dJ, Ns, Np, w, 1.0 / (double)Ns, partial, out, st), "dJ^T w");
+            NK_CU(nk::launch_axpby(Np, diag_shift, v, 1.0, out, st), "shift");
+            return NK_OK;
+        });
+    }
+    if (q->kind != NK_QGT_ONTHEFLY) return fail(NK_ERR_INVALID_ARG, "qgt->kind %d unknown", q->kind);
+    nk_status st0 = check_rbm(q->rbm);
+    if (st0 != NK_OK) return st0;
+    if ((st0 = check_precision(q->precision)) != NK_OK) return st0;
+    NK_DEV(q->s, "qgt->s");
+    const nk_rbm *rbm = q->rbm;
+    const int N = rbm->N, M = rbm->M;
+    return with_workspace(ctx, [&](Carver &c, bool run) -> nk_status {
+        double *T = c.take<double>((size_t)Ns * M);
+        SolveWs w{};
+        w.partial = c.take<double>(nk::vjp_partial_doubles(N, M, Ns));
+        w.dotp = c.take<double>(nk::dot_partial_doubles(Ns) + 8);
+        w.U = c.take<double>((size_t)Ns * (M + 1));
+        w.w = c.take<double>(Ns);
+        if (!run) return NK_OK;
+        NK_CU(nk::launch_theta_tanh(N, M, rbm->params + N, rbm->params + N + M, q->s, Ns, T, st),
+              "theta");
+        NK_CU(qgt_onthefly(N, M, Ns, q->s, T, v, diag_shift, w, out, st), "qgt matvec");
+        return NK_OK;
+    });
+}
+
+nk_status nk_sr_solve(nk_ctx *ctx, const nk_rbm *rbm, int32_t precision, const int8_t *s,
+                      int64_t Ns, const double *F, int32_t solver, double diag_shift,
+                      double cg_tol, int32_t cg_maxiter, double *delta_out, int32_t *info_out,
+                      double *resid_out, void *stream) {
+    if (!ctx) return fail(NK_ERR_INVALID_ARG, "ctx is NULL");
+    DeviceGuard g(ctx->device);
+    nk_status st0 = check_rbm(rbm);
+    if (st0 != NK_OK) return st0;
+    if ((st0 = check_precision(precision)) != NK_OK) return st0;
+    if ((st0 = check_solver(solver, diag_shift, cg_tol, cg_maxiter)) != NK_OK) return st0;
+    if (Ns < 1) return fail(NK_ERR_INVALID_ARG, "Ns must be >= 1");
+    NK_DEV(s, "s");
+    NK_DEV(F, "F");
+    NK_DEV(delta_out, "delta_out");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int N = rbm->N, M = rbm->M;
+    return with_workspace(ctx, [&](Carver &c, bool run) -> nk_status {
+        double *T = c.take<double>((size_t)Ns * M);
+        SolveWs w;
+        carve_solve(c, w, N, M, Ns, solver);
+        if (!run) return NK_OK;
+        NK_CU(nk::launch_theta_tanh(N, M, rbm->params + N, rbm->params + N + M, s, Ns, T, st), "theta");
+        return run_solve(ctx, N, M, Ns, s, T, F, solver, diag_shift, cg_tol, cg_maxiter, w,
+                         delta_out, info_out, resid_out, st);
+    });
+}
+
+nk_status nk_sr_step(nk_ctx *ctx, nk_rbm *rbm, const nk_ham *ham, nk_chains *chains,
+                     const nk_sr_cfg *cfg, nk_sr_stats *stats_out, int8_t *samples_out,
+                     double *eloc_out, void *stream) {
+    if (!ctx) return fail(NK_ERR_INVALID_ARG, "ctx is NULL");
+    DeviceGuard g(ctx->device);
+    nk_status st0 = check_rbm(rbm);
+    if (st0 != NK_OK) return st0;
+    if (!cfg || !chains) return fail(NK_ERR_INVALID_ARG, "cfg or chains is NULL");
+    if ((st0 = check_precision(cfg->precision)) != NK_OK) return st0;
+    if ((st0 = check_ham(ham, rbm->N)) != NK_OK) return st0;
+    if ((st0 = check_solver(cfg->solver, cfg->diag_shift, cfg->cg_tol, cfg->cg_maxiter)) != NK_OK)
+        return st0;
+    if (cfg->rule != NK_RULE_LOCAL && cfg->rule != NK_RULE_EXCHANGE)
+        return fail(NK_ERR_INVALID_ARG, "rule %d unknown", cfg->rule);
+    if (chains->C < 1 || cfg->n_samples < 1 || cfg->n_discard < 0 || chains->sweeps_done < 0)
+        return fail(NK_ERR_INVALID_ARG, "need C >= 1, n_samples >= 1, n_discard >= 0");
+    NK_DEV(chains->s, "chains->s");
+    if (chains->n_accepted) NK_DEV(chains->n_accepted, "chains->n_accepted");
+    if (stats_out) NK_DEV(stats_out, "stats_out");
+    if (samples_out) NK_DEV(samples_out, "samples_out");
+    if (eloc_out) NK_DEV(eloc_out, "eloc_out");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int N = rbm->N, M = rbm->M, C = chains->C, E = ham->n_edges;
+    const int64_t Ns = (int64_t)C * cfg->n_samples, Np = n_params(N, M);
+    const bool site = cfg->rule == NK_RULE_LOCAL || ham->kind == NK_TFIM;
+    const bool edge = cfg->rule == NK_RULE_EXCHANGE || ham->kind == NK_HEIS;
+
+    auto body = [&](auto tag, Carver &c, bool run) -> nk_status {
+        using R = decltype(tag);
+        nk::Tables<R> t{};
+        carve_tables(c, t, rbm, E, ham->edges, site, edge);
+        int8_t *samples = samples_out ? samples_out : c.take<int8_t>((size_t)Ns * N);
+        double *eloc = eloc_out ? eloc_out : c.take<double>(Ns);
+        double *T = c.take<double>((size_t)Ns * M);
+        double *st3 = c.take<double>(4);
+        double *gv = c.take<double>(Ns);
+        double *F = c.take<double>(Np);
+        double *delta = c.take<double>(Np);
+        double *nrm = c.take<double>(2);
+        unsigned long long *acc = c.take<unsigned long long>(C);
+        SolveWs w;
+        carve_solve(c, w, N, M, Ns, cfg->solver);
+        if (!run) return NK_OK;
+        NK_CU(nk::launch_tables(t, site, edge, st), "tables");
+        NK_CU(cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * C, st), "memset");
+        nk::SweepArgs a{};
+        a.N = N;
+        a.M = M;
+        a.E = E;
+        a.C = C;
+        a.rule = cfg->rule;
+        a.edges = ham->edges;
+        a.s = chains->s;
+        a.sweep0 = chains->sweeps_done;
+        a.n_discard = cfg->n_discard;
+        a.n_samples = cfg->n_samples;
+        a.seed = cfg->seed;
+        a.stream_id = cfg->stream_id;
+        a.samples = samples;
+        a.logpsi = nullptr;
+        a.n_accepted = acc;
+        a.decisions = nullptr;
+        NK_CU(nk::launch_sweep(t, a, st), "sweep");
+        nk::ElocArgs ea{ham->kind, ham->J, ham->h, ham->marshall, samples, Ns, eloc, T};
+        NK_CU(nk::launch_eloc(t, ea, st), "local energy");
+        NK_CU(nk::launch_stats(eloc, Ns, C, st3, st), "stats");
+        NK_CU(nk::launch_make_force_g(Ns, eloc, st3, gv, st), "force g");
+        NK_CU(nk::launch_vjp(N, M, Ns, samples, T, gv, 1.0, nullptr, w.partial, F, st), "force");
+        int info[2] = {0, 0};
+        double resid = 0.0;
+        nk_status ss = run_solve(ctx, N, M, Ns, samples, T, F, cfg->solver, cfg->diag_shift,
+                                 cfg->cg_tol, cfg->cg_maxiter, w, delta, info, &resid, st);
+        if (ss != NK_OK && ss != NK_ERR_NOT_CONVERGED) return ss;
+        NK_CU(nk::launch_dot(Np, F, F, w.dotp, nrm, st), "norm");
+        NK_CU(nk::launch_dot(Np, delta, delta, w.dotp, nrm + 1, st), "norm");
+        NK_CU(nk::launch_sgd(Np, cfg->lr, delta, rbm->params, st), "update");
+        if (stats_out) {
+            const double nprop = (double)C * (cfg->n_discard + cfg->n_samples) * N;
+            const bool cg = cfg->solver == NK_SOLVER_CG;
+            NK_CU(nk::launch_write_sr_stats(st3, acc, C, nprop, cg ? w.sc + 3 : nrm, nrm + 1,
+                                            cg ? w.flags + 1 : nullptr, cg ? w.sc + 4 : nullptr,
+                                            stats_out, st),
+                  "stats out");
+        }
+        if (chains->n_accepted) {
+            (k_add_u64<<<(C + 255) / 256, 256, 0, st>>>(
+                C, acc, reinterpret_cast<unsigned long long *>(chains->n_accepted)), nk::note_launch());
+            NK_CU(cudaGetLastError(), "acc");
+        }
+        chains->sweeps_done += cfg->n_discard + cfg->n_samples;
+        return ss;
+    };
+    if (cfg->precision == NK_F64)
+        return with_workspace(ctx, [&](Carver &c, bool run) { return body(double{}, c, run); });
+    return with_workspace(ctx, [&](Carver &c, bool run) { return body(float{}, c, run); });
+}
+
+}  // extern "C"

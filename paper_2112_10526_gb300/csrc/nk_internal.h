@@ -1,0 +1,144 @@
+// Internal launch interface between the C ABI (nk_api.cu) and the kernel
+// translation units.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/nk.h"
+
+namespace nk {
+
+// Kernel timing hooks (prof.cu).  prof_begin returns a slot (or -1 when
+// timing is off); prof_end closes it and adds `work` to the class.
+int prof_begin(int cls, cudaStream_t st);
+// Process-wide count of kernel launches issued by the library.
+void note_launch(long long n = 1);
+void prof_end(int slot, cudaStream_t st, double work);
+
+// Per-parameter tables of the flip-ratio identity (see k_rbm.cu).  All
+// pointers are device workspace.  R = double (NK_F64) or float (NK_MIXED).
+template <typename R>
+struct Tables {
+    int N, M, E;
+    const double *a, *b, *W;  // views of the parameter vector
+    double *Wt;               // [N][M] transposed W (FP64, coalesced theta rebuild)
+    R *tau_site;              // [N][M]  tanh(2 W_ji)
+    R *tau_siteT;             // [M][N]
+    R *K_site;                // [N]     sum_j ln cosh(2 W_ji)
+    const int32_t *edges;     // [E][2]
+    R *tau_edge;              // [E][M]  tanh(2 (W_ji - W_jk))
+    R *tau_edgeT;             // [M][E]
+    R *K_edge;                // [E]
+};
+
+template <typename R>
+cudaError_t launch_tables(const Tables<R> &t, bool need_site, bool need_edge, cudaStream_t st);
+
+cudaError_t launch_logpsi(int N, int M, const double *a, const double *b, const double *Wt,
+                          const int8_t *s, int64_t B, double *out, cudaStream_t st);
+
+cudaError_t launch_chain_init(int N, int C, int rule, uint64_t seed, uint32_t stream_id,
+                              int8_t *s, cudaStream_t st);
+
+struct SweepArgs {
+    int N, M, E, C, rule;
+    const int32_t *edges;
+    int8_t *s;
+    int64_t sweep0;
+    int n_discard, n_samples;
+    uint64_t seed;
+    uint32_t stream_id;
+    int8_t *samples;
+    double *logpsi;
+    unsigned long long *n_accepted;
+    uint8_t *decisions;
+};
+
+template <typename R>
+cudaError_t launch_sweep(const Tables<R> &t, const SweepArgs &a, cudaStream_t st);
+
+struct ElocArgs {
+    int kind;
+    double J, h;
+    int marshall;
+    const int8_t *s;
+    int64_t Ns;
+    double *eloc;
+    double *t_out;  // [Ns][M] or null
+};
+
+template <typename R>
+cudaError_t launch_eloc(const Tables<R> &t, const ElocArgs &a, cudaStream_t st);
+
+// T[k][j] = tanh(b_j + sum_i W_ji s_ki) for a batch (FP64 tiled GEMM).
+cudaError_t launch_theta_tanh(int N, int M, const double *b, const double *W, const int8_t *s,
+                              int64_t B, double *T, cudaStream_t st);
+
+// ---- linear algebra (k_linalg.cu) -----------------------------------------
+
+cudaError_t launch_stats(const double *e, int64_t Ns, int n_chains, double *out, cudaStream_t st);
+
+// out = J^T g, with J given by samples s [Ns,N] and T = tanh theta [Ns,M].
+// partial: workspace of vjp_partial_doubles(...) doubles.
+size_t vjp_partial_doubles(int N, int M, int64_t Ns);
+cudaError_t launch_vjp(int N, int M, int64_t Ns, const int8_t *s, const double *T,
+                       const double *g, double g_scale, const double *g_shift, double *partial,
+                       double *out, cudaStream_t st);
+
+// out = J v.  U: workspace [Ns][M+1] doubles.
+cudaError_t launch_jvp(int N, int M, int64_t Ns, const int8_t *s, const double *T,
+                       const double *v, double *U, double *out, cudaStream_t st);
+
+cudaError_t launch_jacobian_rows(int N, int M, const int8_t *s, const double *T, int64_t row0,
+                                 int64_t rows, const double *mean, double *O, cudaStream_t st);
+
+// Dense QGT products on a stored centred Jacobian dJ [Ns][Np].
+cudaError_t launch_gemv_rows(const double *A, int64_t rows, int64_t cols, const double *x,
+                             double *y, cudaStream_t st);
+size_t gemv_t_partial_doubles(int64_t rows, int64_t cols);
+cudaError_t launch_gemv_t(const double *A, int64_t rows, int64_t cols, const double *x,
+                          double scale, double *partial, double *y, cudaStream_t st);
+
+// S = dJ^T dJ / Ns + eps I  [Np][Np] (lower triangle filled, full written).
+cudaError_t launch_syrk_t(const double *A, int64_t rows, int64_t cols, double scale, double eps,
+                          double *C, cudaStream_t st);
+
+// Sample-space Gram K = P (S S^T + T T^T + (T T^T) o (S S^T)) P / Ns + eps I.
+cudaError_t launch_gram_samplespace(int N, int M, int64_t Ns, const int8_t *s, const double *T,
+                                    double eps, double *K, double *rowmean, cudaStream_t st);
+
+// In-place lower Cholesky of an n x n matrix (lda = n); info: device int.
+cudaError_t launch_cholesky(double *A, int64_t n, int *info, cudaStream_t st);
+// Solve L L^T x = b in place (b -> x).
+cudaError_t launch_cholesky_solve(const double *L, int64_t n, double *b, cudaStream_t st);
+
+// vector helpers
+cudaError_t launch_axpby(int64_t n, double alpha, const double *x, double beta, double *y,
+                         cudaStream_t st);  // y = alpha x + beta y
+size_t dot_partial_doubles(int64_t n);
+cudaError_t launch_dot(int64_t n, const double *x, const double *y, double *partial, double *out,
+                       cudaStream_t st);
+cudaError_t launch_center(int64_t n, double *x, double *partial, double scale, cudaStream_t st);
+cudaError_t launch_fill(int64_t n, double v, double *x, cudaStream_t st);
+
+// CG step kernels (scalars live in device memory).
+cudaError_t launch_cg_update_xr(int64_t n, const double *rr, const double *pAp, const double *p,
+                                const double *Ap, double *x, double *r, const int *done,
+                                cudaStream_t st);
+cudaError_t launch_cg_update_p(int64_t n, const double *rr_new, const double *rr_old,
+                               const double *r, double *p, const int *done, cudaStream_t st);
+cudaError_t launch_cg_check(const double *rr, const double *ff, double tol, int *done,
+                            int *iters, double *rr_keep, cudaStream_t st);
+
+// params -= lr * delta; norms into stats.
+cudaError_t launch_sgd(int64_t n, double lr, const double *delta, double *params,
+                       cudaStream_t st);
+cudaError_t launch_make_force_g(int64_t Ns, const double *eloc, const double *stats,
+                                double *g, cudaStream_t st);
+cudaError_t launch_write_sr_stats(const double *stats3, const unsigned long long *acc, int C,
+                                  double n_proposals, const double *ff, const double *dd,
+                                  const int *cg_iters, const double *cg_rr, nk_sr_stats *out,
+                                  cudaStream_t st);
+
+}  // namespace nk

@@ -1,0 +1,332 @@
+"""Thin ctypes binding of libnk.so (include/nk.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and takes
+torch CUDA tensors for the device arrays; all arithmetic runs in the CUDA
+library.  There is no fallback: if libnk.so is missing or fails to load,
+``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libnk.so")
+
+NK_OK = 0
+NK_ERR_INVALID_ARG = -1
+NK_ERR_CUDA = -2
+NK_ERR_OOM = -3
+NK_ERR_TIMEOUT = -4
+NK_ERR_NOT_CONVERGED = -5
+NK_ERR_UNIMPLEMENTED = -6
+
+NK_F64, NK_MIXED = 0, 1
+NK_RULE_LOCAL, NK_RULE_EXCHANGE = 0, 1
+NK_TFIM, NK_HEIS = 0, 1
+NK_SOLVER_CHOLESKY, NK_SOLVER_CHOLESKY_SAMPLESPACE, NK_SOLVER_CG = 0, 1, 2
+NK_QGT_ONTHEFLY, NK_QGT_JACOBIAN = 0, 1
+
+PRECISION = {"f64": NK_F64, "mixed": NK_MIXED}
+RULE = {"local": NK_RULE_LOCAL, "exchange": NK_RULE_EXCHANGE}
+KIND = {"tfim": NK_TFIM, "heis": NK_HEIS}
+SOLVER = {"cholesky": NK_SOLVER_CHOLESKY, "cholesky_samplespace": NK_SOLVER_CHOLESKY_SAMPLESPACE,
+          "cg": NK_SOLVER_CG}
+
+
+class NkError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libnk error {code}: {msg}")
+        self.code = code
+
+
+class nk_rbm(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int32), ("M", ctypes.c_int32), ("params", ctypes.c_void_p)]
+
+
+class nk_ham(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("J", ctypes.c_double), ("h", ctypes.c_double),
+                ("marshall", ctypes.c_int32), ("n_edges", ctypes.c_int32), ("edges", ctypes.c_void_p)]
+
+
+class nk_qgt(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("rbm", ctypes.POINTER(nk_rbm)), ("precision", ctypes.c_int32),
+                ("s", ctypes.c_void_p), ("dJ", ctypes.c_void_p), ("Ns", ctypes.c_int64),
+                ("Np", ctypes.c_int32)]
+
+
+class nk_chains(ctypes.Structure):
+    _fields_ = [("C", ctypes.c_int32), ("s", ctypes.c_void_p), ("sweeps_done", ctypes.c_int64),
+                ("n_accepted", ctypes.c_void_p)]
+
+
+class nk_sr_cfg(ctypes.Structure):
+    _fields_ = [("rule", ctypes.c_int32), ("precision", ctypes.c_int32), ("solver", ctypes.c_int32),
+                ("n_discard", ctypes.c_int32), ("n_samples", ctypes.c_int32),
+                ("cg_maxiter", ctypes.c_int32), ("diag_shift", ctypes.c_double), ("lr", ctypes.c_double),
+                ("cg_tol", ctypes.c_double), ("seed", ctypes.c_uint64), ("stream_id", ctypes.c_uint32)]
+
+
+SR_STATS_FIELDS = ["energy", "variance", "error", "acceptance", "cg_iters", "cg_residual", "f_norm",
+                   "delta_norm"]
+
+_lib = None
+
+
+def lib():
+    """Load libnk.so (raises if it is missing: there is no CPU fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing; build it with "
+                           "`python -m paper_2112_10526_gb300.build`")
+    L = ctypes.CDLL(LIB_PATH)
+    P, i32, i64, u64, u32, f64 = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64,
+                                  ctypes.c_uint32, ctypes.c_double)
+    sig = {
+        "nk_ctx_create": [i32, ctypes.POINTER(P)],
+        "nk_ctx_destroy": [P],
+        "nk_rbm_logpsi": [P, ctypes.POINTER(nk_rbm), i32, P, i64, P, P],
+        "nk_chains_init": [P, i32, i32, i32, u64, u32, P, P],
+        "nk_metropolis_sweep": [P, ctypes.POINTER(nk_rbm), i32, i32, i32, P, i32, P, i64, i32, i32, u64,
+                                u32, P, P, P, P, P],
+        "nk_local_energy": [P, ctypes.POINTER(nk_rbm), i32, ctypes.POINTER(nk_ham), P, i64, P, P, P],
+        "nk_stats": [P, P, i64, i32, P, P],
+        "nk_jacobian": [P, ctypes.POINTER(nk_rbm), i32, P, i64, i32, i64, i64, P, P],
+        "nk_vjp": [P, ctypes.POINTER(nk_rbm), i32, P, i64, P, P, P],
+        "nk_jvp": [P, ctypes.POINTER(nk_rbm), i32, P, i64, P, P, P],
+        "nk_force": [P, ctypes.POINTER(nk_rbm), i32, P, i64, P, P, P],
+        "nk_qgt_matvec": [P, ctypes.POINTER(nk_qgt), f64, P, P, P],
+        "nk_sr_solve": [P, ctypes.POINTER(nk_rbm), i32, P, i64, P, i32, f64, f64, i32, P,
+                        ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double), P],
+        "nk_sr_step": [P, ctypes.POINTER(nk_rbm), ctypes.POINTER(nk_ham), ctypes.POINTER(nk_chains),
+                       ctypes.POINTER(nk_sr_cfg), P, P, P, P],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int32
+    L.nk_last_error.argtypes = []
+    L.nk_last_error.restype = ctypes.c_char_p
+    L.nk_version.argtypes = []
+    L.nk_version.restype = ctypes.c_int32
+    L.nk_prof_enable.argtypes = [i32]
+    L.nk_prof_enable.restype = ctypes.c_int32
+    L.nk_prof_read.argtypes = [i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
+                               ctypes.POINTER(ctypes.c_double)]
+    L.nk_prof_read.restype = ctypes.c_int32
+    L.nk_launch_count.argtypes = []
+    L.nk_launch_count.restype = ctypes.c_int64
+    _lib = L
+    return L
+
+
+def _check(code, allow=()):
+    if code != NK_OK and code not in allow:
+        raise NkError(code, lib().nk_last_error().decode())
+    return code
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _prec(p):
+    return PRECISION[p] if isinstance(p, str) else int(p)
+
+
+class Ctx:
+    """Owns one nk_ctx (device workspace); close() or use as a context manager."""
+
+    def __init__(self, device=None):
+        dev = torch.cuda.current_device() if device is None else int(device)
+        h = ctypes.c_void_p()
+        _check(lib().nk_ctx_create(dev, ctypes.byref(h)))
+        self.handle = h
+        self.device = dev
+
+    def close(self):
+        if self.handle:
+            lib().nk_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_rbm(params, N, M):
+    assert params.dtype == torch.float64 and params.is_cuda and params.numel() == N + M + M * N
+    return nk_rbm(N, M, params.data_ptr())
+
+
+def make_ham(kind, J, h, marshall, edges):
+    assert edges.dtype == torch.int32 and edges.is_cuda
+    e = edges.reshape(-1, 2)
+    return nk_ham(KIND[kind] if isinstance(kind, str) else int(kind), float(J), float(h), int(bool(marshall)),
+                  int(e.shape[0]), e.data_ptr())
+
+
+# ------------------------------------------------------------ entry points --
+
+def nk_rbm_logpsi(ctx, params, N, M, s, out, precision="f64", stream=None):
+    r = make_rbm(params, N, M)
+    _check(lib().nk_rbm_logpsi(ctx.handle, ctypes.byref(r), _prec(precision), _ptr(s), s.shape[0],
+                               _ptr(out), _stream(stream)))
+    return out
+
+
+def nk_chains_init(ctx, N, C, rule, seed, stream_id, s_out, stream=None):
+    _check(lib().nk_chains_init(ctx.handle, N, C, RULE[rule] if isinstance(rule, str) else rule, seed,
+                                stream_id, _ptr(s_out), _stream(stream)))
+    return s_out
+
+
+def nk_metropolis_sweep(ctx, params, N, M, rule, edges, s, sweep0, n_discard, n_samples, seed,
+                        stream_id, samples_out, logpsi_out=None, n_accepted=None, decisions_out=None,
+                        precision="f64", stream=None):
+    r = make_rbm(params, N, M)
+    ne = 0 if edges is None else int(edges.reshape(-1, 2).shape[0])
+    _check(lib().nk_metropolis_sweep(ctx.handle, ctypes.byref(r), _prec(precision),
+                                     RULE[rule] if isinstance(rule, str) else rule, ne, _ptr(edges),
+                                     s.shape[0], _ptr(s), sweep0, n_discard, n_samples, seed, stream_id,
+                                     _ptr(samples_out), _ptr(logpsi_out), _ptr(n_accepted),
+                                     _ptr(decisions_out), _stream(stream)))
+    return samples_out
+
+
+def nk_local_energy(ctx, params, N, M, ham, s, eloc_out, t_out=None, precision="f64", stream=None):
+    r = make_rbm(params, N, M)
+    _check(lib().nk_local_energy(ctx.handle, ctypes.byref(r), _prec(precision), ctypes.byref(ham),
+                                 _ptr(s), s.shape[0], _ptr(eloc_out), _ptr(t_out), _stream(stream)))
+    return eloc_out
+
+
+def nk_stats(ctx, eloc, n_chains, out, stream=None):
+    _check(lib().nk_stats(ctx.handle, _ptr(eloc), eloc.numel(), n_chains, _ptr(out), _stream(stream)))
+    return out
+
+
+def nk_jacobian(ctx, params, N, M, s, centered, row0, rows, O_out, precision="f64", stream=None):
+    r = make_rbm(params, N, M)
+    _check(lib().nk_jacobian(ctx.handle, ctypes.byref(r), _prec(precision), _ptr(s), s.shape[0],
+                             int(bool(centered)), row0, rows, _ptr(O_out), _stream(stream)))
+    return O_out
+
+
+def nk_vjp(ctx, params, N, M, s, g, out, precision="f64", stream=None):
+    r = make_rbm(params, N, M)
+    _check(lib().nk_vjp(ctx.handle, ctypes.byref(r), _prec(precision), _ptr(s), s.shape[0], _ptr(g),
+                        _ptr(out), _stream(stream)))
+    return out
+
+
+def nk_jvp(ctx, params, N, M, s, v, out, precision="f64", stream=None):
+    r = make_rbm(params, N, M)
+    _check(lib().nk_jvp(ctx.handle, ctypes.byref(r), _prec(precision), _ptr(s), s.shape[0], _ptr(v),
+                        _ptr(out), _stream(stream)))
+    return out
+
+
+def nk_force(ctx, params, N, M, s, eloc, F_out, precision="f64", stream=None):
+    r = make_rbm(params, N, M)
+    _check(lib().nk_force(ctx.handle, ctypes.byref(r), _prec(precision), _ptr(s), s.shape[0],
+                          _ptr(eloc), _ptr(F_out), _stream(stream)))
+    return F_out
+
+
+def nk_qgt_matvec(ctx, v, out, diag_shift, params=None, N=None, M=None, s=None, dJ=None,
+                  precision="f64", stream=None):
+    """On-the-fly QGT when `s` is given, stored centred Jacobian when `dJ` is."""
+    if dJ is not None:
+        q = nk_qgt(NK_QGT_JACOBIAN, None, 0, None, dJ.data_ptr(), dJ.shape[0], dJ.shape[1])
+        _check(lib().nk_qgt_matvec(ctx.handle, ctypes.byref(q), float(diag_shift), _ptr(v), _ptr(out),
+                                   _stream(stream)))
+        return out
+    r = make_rbm(params, N, M)
+    q = nk_qgt(NK_QGT_ONTHEFLY, ctypes.pointer(r), _prec(precision), s.data_ptr(), None, s.shape[0], 0)
+    _check(lib().nk_qgt_matvec(ctx.handle, ctypes.byref(q), float(diag_shift), _ptr(v), _ptr(out),
+                               _stream(stream)))
+    return out
+
+
+def nk_sr_solve(ctx, params, N, M, s, F, delta_out, solver="cg", diag_shift=0.01, cg_tol=1e-10,
+                cg_maxiter=1000, precision="f64", stream=None):
+    r = make_rbm(params, N, M)
+    info = (ctypes.c_int32 * 2)()
+    res = ctypes.c_double()
+    code = lib().nk_sr_solve(ctx.handle, ctypes.byref(r), _prec(precision), _ptr(s), s.shape[0], _ptr(F),
+                             SOLVER[solver] if isinstance(solver, str) else solver, float(diag_shift),
+                             float(cg_tol), int(cg_maxiter), _ptr(delta_out), info, ctypes.byref(res),
+                             _stream(stream))
+    _check(code, allow=(NK_ERR_NOT_CONVERGED,))
+    return {"iters": int(info[0]), "converged": bool(info[1]), "residual": res.value, "code": code}
+
+
+def nk_sr_step(ctx, params, N, M, ham, chains, cfg, stats_out=None, samples_out=None, eloc_out=None,
+               stream=None):
+    """`chains` is an nk_chains structure (its sweeps_done advances); `cfg` an nk_sr_cfg."""
+    r = make_rbm(params, N, M)
+    code = lib().nk_sr_step(ctx.handle, ctypes.byref(r), ctypes.byref(ham), ctypes.byref(chains),
+                            ctypes.byref(cfg), _ptr(stats_out), _ptr(samples_out), _ptr(eloc_out),
+                            _stream(stream))
+    _check(code, allow=(NK_ERR_NOT_CONVERGED,))
+    return code
+
+
+def sr_stats_dict(t):
+    """Read an nk_sr_stats device buffer (float64 [8]) into a dict."""
+    v = t.detach().cpu().tolist()
+    return dict(zip(SR_STATS_FIELDS, v))
+
+
+def make_cfg(rule, precision, solver, n_discard, n_samples, diag_shift, lr, seed, stream_id=0,
+             cg_tol=1e-10, cg_maxiter=1000):
+    return nk_sr_cfg(RULE[rule] if isinstance(rule, str) else rule, _prec(precision),
+                     SOLVER[solver] if isinstance(solver, str) else solver, int(n_discard), int(n_samples),
+                     int(cg_maxiter), float(diag_shift), float(lr), float(cg_tol), int(seed), int(stream_id))
+
+
+def make_chains(s, sweeps_done=0, n_accepted=None):
+    return nk_chains(int(s.shape[0]), s.data_ptr(), int(sweeps_done),
+                     None if n_accepted is None else n_accepted.data_ptr())
+
+
+PROF_CLASSES = {"sweep": 0, "eloc": 1, "gram": 2, "chol_update": 3, "chol_panel": 4, "trsv": 5,
+                "jvp_vjp": 6}
+
+
+def nk_prof_enable(on=True):
+    _check(lib().nk_prof_enable(int(bool(on))))
+
+
+def nk_prof_read(cls):
+    """(milliseconds, launches, work) of a tracked kernel class since nk_prof_enable."""
+    ms, n, w = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
+    c = PROF_CLASSES[cls] if isinstance(cls, str) else int(cls)
+    _check(lib().nk_prof_read(c, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(w)))
+    return ms.value, n.value, w.value
+
+
+def nk_launch_count():
+    return int(lib().nk_launch_count())
