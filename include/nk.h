@@ -155,6 +155,26 @@ nk_status nk_local_energy(nk_ctx *ctx, const nk_rbm *rbm, int32_t precision, con
                           void *stream);
 
 /*
+ * Local energies exactly as nk_local_energy, for callers that cannot let a
+ * library allocate device memory (their HBM is owned by another allocator,
+ * or they cannot afford cudaMalloc's device-wide synchronisation).  The paper
+ * has no counterpart; this is a property of the library, not of the method.
+ * No context and no allocation: the flip-ratio tables live in one fixed
+ * __device__ array of NK_NOALLOC_SCRATCH_BYTES compiled into libnk.so, held
+ * by every GPU that loads the library until the process exits.  Sizes whose
+ * tables do not fit (about 8 (3 N M + N) bytes for NK_TFIM, 8 (N M + 2 E M
+ * + E) for NK_HEIS in FP64, half the tau part in NK_MIXED) return
+ * NK_ERR_INVALID_ARG.  The first call on each device (with it current) looks
+ * up the array's device address; make it before any stream capture.  All
+ * calls share the array: calls that overlap on the GPU race, so serialise
+ * them.  Runs on the current device; arguments as nk_local_energy.
+ */
+#define NK_NOALLOC_SCRATCH_BYTES (8u << 20)
+nk_status nk_local_energy_noalloc(const nk_rbm *rbm, int32_t precision, const nk_ham *ham,
+                                  const int8_t *s, int64_t Ns, double *eloc_out, double *t_out,
+                                  void *stream);
+
+/*
  * Sample statistics of the local energy (Sec. 3.4): out[0] = mean,
  * out[1] = variance (1/Ns normalisation), out[2] = standard error of the
  * mean (from the n_chains chain means when each chain holds >= 2 samples

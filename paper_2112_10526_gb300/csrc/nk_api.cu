@@ -331,6 +331,11 @@ nk_status check_solver(int solver, double eps, double tol, int maxiter) {
 
 }  // namespace
 
+namespace nk {
+// Lets other translation units of the library report through nk_last_error.
+nk_status report_error(nk_status code, const char *msg) { return fail(code, "%s", msg); }
+}  // namespace nk
+
 // =================================================================== ABI ===
 
 extern "C" {

@@ -12,6 +12,8 @@ namespace nk {
 // Kernel timing hooks (prof.cu).  prof_begin returns a slot (or -1 when
 // timing is off); prof_end closes it and adds `work` to the class.
 int prof_begin(int cls, cudaStream_t st);
+// Sets the message returned by nk_last_error on this thread; returns code.
+nk_status report_error(nk_status code, const char *msg);
 // Process-wide count of kernel launches issued by the library.
 void note_launch(long long n = 1);
 void prof_end(int slot, cudaStream_t st, double work);

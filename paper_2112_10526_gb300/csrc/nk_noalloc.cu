@@ -1,0 +1,156 @@
+// nk_local_energy_noalloc: the local-energy entry point for callers that
+// cannot let a library allocate device memory.
+//
+// Who needs it: programs whose device memory is owned by another allocator
+// (a framework that reserves most of HBM up front, so a library cudaMalloc
+// fails or fragments that pool), and latency-critical loops that cannot
+// afford cudaMalloc / cudaFree, which synchronise the device and stall every
+// other stream.  nk_local_energy keeps its tables in a context workspace
+// that grows with cudaMalloc; this variant needs no context and keeps the
+// same tables in one fixed array compiled into the library instead.
+//
+// The array is a file-scope __device__ variable of kNoallocScratchBytes.
+// Every GPU that loads libnk.so holds it until the process exits.  Host code
+// cannot use the array's name as a device address (in host code it names a
+// host-side stand-in), so the device address is looked up once per device
+// with cudaGetSymbolAddress, on the first call made with that device
+// current, and cached.  Make that first call before any stream capture.
+//
+// All calls share the array and it keeps the last call's contents.  Every
+// table a call reads is fully written by that same call first, so nothing
+// has to start at zero.  Calls whose kernels overlap on the GPU (different
+// streams, or different host threads) race on the array: serialise them.
+
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <mutex>
+
+#include "../../include/nk.h"
+#include "nk_internal.h"
+
+namespace {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NK_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+char *g_scratch_dev[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device (set-up on the
+// first call per device).
+nk_status scratch_address(char **out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return nk::report_error(NK_ERR_CUDA, cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return nk::report_error(NK_ERR_INVALID_ARG, "device ordinal out of range");
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_scratch_dev[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            return nk::report_error(NK_ERR_CUDA, "cudaGetSymbolAddress(scratch) failed");
+        }
+        g_scratch_dev[dev] = static_cast<char *>(p);
+    }
+    *out = g_scratch_dev[dev];
+    return NK_OK;
+}
+
+bool on_device(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Bump carving of the scratch array (base == nullptr counts bytes only).
+struct Bump {
+    char *base;
+    size_t off = 0;
+    template <class T>
+    T *take(size_t n) {
+        off = (off + 255) & ~size_t(255);
+        T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+        off += n * sizeof(T);
+        return p;
+    }
+};
+
+template <typename R>
+size_t plan_tables(Bump &b, nk::Tables<R> &t, const nk_rbm *rbm, const nk_ham *ham) {
+    const int N = rbm->N, M = rbm->M, E = ham->n_edges;
+    const bool site = ham->kind == NK_TFIM, edge = ham->kind == NK_HEIS;
+    t.N = N;
+    t.M = M;
+    t.E = E;
+    t.a = rbm->params;
+    t.b = rbm->params + N;
+    t.W = rbm->params + N + M;
+    t.edges = ham->edges;
+    t.Wt = b.take<double>((size_t)N * M);
+    t.tau_site = site ? b.take<R>((size_t)N * M) : nullptr;
+    t.tau_siteT = site ? b.take<R>((size_t)N * M) : nullptr;
+    t.K_site = site ? b.take<R>(N) : nullptr;
+    t.tau_edge = edge ? b.take<R>((size_t)E * M) : nullptr;
+    t.tau_edgeT = edge ? b.take<R>((size_t)E * M) : nullptr;
+    t.K_edge = edge ? b.take<R>(E) : nullptr;
+    return b.off;
+}
+
+template <typename R>
+nk_status run(const nk_rbm *rbm, const nk_ham *ham, const int8_t *s, int64_t Ns, double *eloc,
+              double *t_out, cudaStream_t st) {
+    nk::Tables<R> t{};
+    Bump count{nullptr};
+    const size_t need = plan_tables(count, t, rbm, ham);
+    if (need > (size_t)NK_NOALLOC_SCRATCH_BYTES) {
+        char msg[256];
+        snprintf(msg, sizeof msg,
+                 "nk_local_energy_noalloc: these sizes need %zu bytes of tables; the fixed scratch "
+                 "holds %zu bytes (use nk_local_energy)",
+                 need, (size_t)NK_NOALLOC_SCRATCH_BYTES);
+        return nk::report_error(NK_ERR_INVALID_ARG, msg);
+    }
+    char *base = nullptr;
+    nk_status stt = scratch_address(&base);
+    if (stt != NK_OK) return stt;
+    Bump real{base};
+    plan_tables(real, t, rbm, ham);
+    const bool site = ham->kind == NK_TFIM, edge = ham->kind == NK_HEIS;
+    cudaError_t e = nk::launch_tables(t, site, edge, st);
+    if (e == cudaSuccess) {
+        nk::ElocArgs a{ham->kind, ham->J, ham->h, ham->marshall, s, Ns, eloc, t_out};
+        e = nk::launch_eloc(t, a, st);
+    }
+    if (e != cudaSuccess) return nk::report_error(NK_ERR_CUDA, cudaGetErrorString(e));
+    return NK_OK;
+}
+
+}  // namespace
+
+extern "C" nk_status nk_local_energy_noalloc(const nk_rbm *rbm, int32_t precision, const nk_ham *ham,
+                                             const int8_t *s, int64_t Ns, double *eloc_out,
+                                             double *t_out, void *stream) {
+    if (!rbm || !ham) return nk::report_error(NK_ERR_INVALID_ARG, "rbm or ham is NULL");
+    if (rbm->N < 1 || rbm->N > 4096 || rbm->M < 1 || rbm->M > 8192)
+        return nk::report_error(NK_ERR_INVALID_ARG, "N or M out of range");
+    if (precision != NK_F64 && precision != NK_MIXED)
+        return nk::report_error(NK_ERR_INVALID_ARG, "precision unknown");
+    if (ham->kind != NK_TFIM && ham->kind != NK_HEIS)
+        return nk::report_error(NK_ERR_INVALID_ARG, "ham->kind unknown");
+    if (ham->n_edges < 1 || ham->n_edges > 65536)
+        return nk::report_error(NK_ERR_INVALID_ARG, "ham->n_edges out of [1, 65536]");
+    if (Ns < 0) return nk::report_error(NK_ERR_INVALID_ARG, "Ns < 0");
+    if (Ns == 0) return NK_OK;
+    if (!on_device(rbm->params) || !on_device(ham->edges) || !on_device(s) || !on_device(eloc_out) ||
+        (t_out && !on_device(t_out)))
+        return nk::report_error(NK_ERR_INVALID_ARG, "arrays must be device pointers");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (precision == NK_F64) return run<double>(rbm, ham, s, Ns, eloc_out, t_out, st);
+    return run<float>(rbm, ham, s, Ns, eloc_out, t_out, st);
+}

@@ -94,6 +94,7 @@ def lib():
         "nk_metropolis_sweep": [P, ctypes.POINTER(nk_rbm), i32, i32, i32, P, i32, P, i64, i32, i32, u64,
                                 u32, P, P, P, P, P],
         "nk_local_energy": [P, ctypes.POINTER(nk_rbm), i32, ctypes.POINTER(nk_ham), P, i64, P, P, P],
+        "nk_local_energy_noalloc": [ctypes.POINTER(nk_rbm), i32, ctypes.POINTER(nk_ham), P, i64, P, P, P],
         "nk_stats": [P, P, i64, i32, P, P],
         "nk_jacobian": [P, ctypes.POINTER(nk_rbm), i32, P, i64, i32, i64, i64, P, P],
         "nk_vjp": [P, ctypes.POINTER(nk_rbm), i32, P, i64, P, P, P],
@@ -219,6 +220,15 @@ def nk_local_energy(ctx, params, N, M, ham, s, eloc_out, t_out=None, precision="
     r = make_rbm(params, N, M)
     _check(lib().nk_local_energy(ctx.handle, ctypes.byref(r), _prec(precision), ctypes.byref(ham),
                                  _ptr(s), s.shape[0], _ptr(eloc_out), _ptr(t_out), _stream(stream)))
+    return eloc_out
+
+
+def nk_local_energy_noalloc(params, N, M, ham, s, eloc_out, t_out=None, precision="f64", stream=None):
+    """nk_local_energy without a context or any device allocation (fixed
+    library scratch; see include/nk.h)."""
+    r = make_rbm(params, N, M)
+    _check(lib().nk_local_energy_noalloc(ctypes.byref(r), _prec(precision), ctypes.byref(ham), _ptr(s),
+                                         s.shape[0], _ptr(eloc_out), _ptr(t_out), _stream(stream)))
     return eloc_out
 
 
