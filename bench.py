@@ -182,7 +182,7 @@ def setup(w, precision, rank, dev):
     st["cfg"] = nk.make_cfg(w["rule"], precision, w["solver"], w["discard"], w["per_chain"],
                             w["diag_shift"], w["lr"], w["seed"], stream_id=rank, cg_tol=1e-8,
                             cg_maxiter=1000)
-    st["stats"] = torch.empty(8, dtype=torch.float64, device=dev)
+    st["stats"] = torch.empty(nk.SR_STATS_DOUBLES, dtype=torch.float64, device=dev)
     return st
 
 
@@ -239,10 +239,11 @@ def e2e_steps(st, K, dev):
     and chain states), nk_sr_step, device -> host read of the result
     (updated parameters and the step statistics)."""
     import torch
+    from paper_2112_10526_gb300 import nk
     h_params = st["params"].cpu().pin_memory()
     h_s = st["s"].cpu().pin_memory()
     h_out = torch.empty_like(h_params).pin_memory()
-    h_stats = torch.empty(8, dtype=torch.float64).pin_memory()
+    h_stats = torch.empty(nk.SR_STATS_DOUBLES, dtype=torch.float64).pin_memory()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(K):

@@ -228,6 +228,22 @@ nk_status nk_qgt_matvec(nk_ctx *ctx, const nk_qgt *qgt, double diag_shift, const
                         double *out, void *stream);
 
 /*
+ * FP64-accurate dense product on the tensor cores: C (op)= A B^T with
+ * A [rows, k] (row stride lda), B [cols, k] (ldb), k <= 64, C [rows, cols]
+ * (ldc); op by mode: 0 '=', 1 '-=', 2 '+='; lower = 1 touches only entries
+ * with column <= row.  Each operand row is scaled by a power of two and cut
+ * into `slices` (1..7) 8-bit integer slices; the slice products run as BF16
+ * tcgen05 MMAs with exact FP32 accumulation and are recombined in FP64
+ * (slices = 7: FP64-level accuracy; 3: about FP32).  This is the building
+ * block of the NK_MIXED Cholesky and sample-space Gram (the dense products
+ * G = dJ^T dJ / Ns of App. B.2 and the factorisation of Sec. 3.6).  The call
+ * synchronises the stream and returns NK_ERR_TIMEOUT if a product timed out.
+ */
+nk_status nk_tc_gemm(nk_ctx *ctx, int64_t rows, int64_t cols, int32_t k, const double *A, int64_t lda,
+                     const double *B, int64_t ldb, int32_t slices, int32_t mode, int32_t lower,
+                     double *C, int64_t ldc, void *stream);
+
+/*
  * Solve (G + diag_shift I) delta = F for the QGT of the given samples
  * (Eq. eq:stochastic-reconfiguration, real case; Sec. 3.6 "Solving linear
  * systems").  solver: NK_SOLVER_CHOLESKY (dense Np x Np FP64 Cholesky),
@@ -235,7 +251,12 @@ nk_status nk_qgt_matvec(nk_ctx *ctx, const nk_qgt *qgt, double diag_shift, const
  * dJ dJ^T / Ns + diag_shift I and delta = (F - dJ^T y / sqrt(Ns)) /
  * diag_shift, equal in exact arithmetic), NK_SOLVER_CG (x0 = 0, stops at
  * ||r|| <= cg_tol ||F|| or cg_maxiter; reads the residual back to the host
- * every 8 iterations, which synchronises the stream).
+ * every 8 iterations, which synchronises the stream).  With NK_MIXED the
+ * Cholesky factorisations run their panel and trailing products on the
+ * tensor cores at FP64-level accuracy (see nk_tc_gemm), and so does the
+ * sample-space Gram; the call then synchronises the stream and returns
+ * NK_ERR_CUDA on a failed factorisation (NK_ERR_TIMEOUT on a tensor-core
+ * time-out).
  *   info_out host int32[2] or NULL: iterations, converged flag.
  *   resid_out host double or NULL: final relative residual (CG).
  */
@@ -275,6 +296,9 @@ typedef struct {
     double cg_residual;
     double f_norm;       /* ||F|| */
     double delta_norm;   /* ||delta|| */
+    double solver_status; /* 0 = ok; k > 0: the Cholesky pivot k (1-based) was not
+                             positive; -1 / -2: a tensor-core product timed out
+                             waiting for its operands / its MMAs */
 } nk_sr_stats;
 
 /*

@@ -707,7 +707,8 @@ __global__ void k_force_g(int64_t Ns, const double *__restrict__ e, const double
 __global__ void k_write_sr_stats(const double *__restrict__ st3, const unsigned long long *acc, int C,
                                  double n_proposals, const double *__restrict__ ff,
                                  const double *__restrict__ dd, const int *__restrict__ it,
-                                 const double *__restrict__ rr, nk_sr_stats *__restrict__ out) {
+                                 const double *__restrict__ rr, const int *__restrict__ status,
+                                 nk_sr_stats *__restrict__ out) {
     __shared__ unsigned long long red[256];
     unsigned long long a = 0;
     for (int c = threadIdx.x; c < C; c += blockDim.x) a += acc[c];
@@ -726,6 +727,8 @@ __global__ void k_write_sr_stats(const double *__restrict__ st3, const unsigned 
         out->cg_residual = (rr && ff && *ff > 0) ? sqrt(*rr / *ff) : 0.0;
         out->f_norm = ff ? sqrt(*ff) : 0.0;
         out->delta_norm = dd ? sqrt(*dd) : 0.0;
+        // status[0]: Cholesky breakdown pivot, status[1]: tensor-core time-out
+        out->solver_status = status ? (status[1] ? -(double)status[1] : (double)status[0]) : 0.0;
     }
 }
 
@@ -826,6 +829,13 @@ cudaError_t launch_gram_samplespace(int N, int M, int64_t Ns, const int8_t *s, c
     const int slot = prof_begin(NK_PROF_GRAM, st);
     (k_gram_raw<<<grid, 256, 0, st>>>(N, M, Ns, s, T, K), nk::note_launch());
     prof_end(slot, st, (double)Ns * (Ns + 1) * (double)(N + M));
+    (k_row_mean<<<nblk(Ns, 8), 256, 0, st>>>(Ns, K, rowmean), nk::note_launch());
+    (k_mean_into<<<1, 1024, 0, st>>>(Ns, rowmean), nk::note_launch());
+    (k_double_center<<<nblk(Ns * Ns, 256), 256, 0, st>>>(Ns, K, rowmean, eps), nk::note_launch());
+    return cudaGetLastError();
+}
+
+cudaError_t launch_center_gram(int64_t Ns, double *K, double *rowmean, double eps, cudaStream_t st) {
     (k_row_mean<<<nblk(Ns, 8), 256, 0, st>>>(Ns, K, rowmean), nk::note_launch());
     (k_mean_into<<<1, 1024, 0, st>>>(Ns, rowmean), nk::note_launch());
     (k_double_center<<<nblk(Ns * Ns, 256), 256, 0, st>>>(Ns, K, rowmean, eps), nk::note_launch());
@@ -935,9 +945,9 @@ cudaError_t launch_make_force_g(int64_t Ns, const double *eloc, const double *st
 
 cudaError_t launch_write_sr_stats(const double *stats3, const unsigned long long *acc, int C,
                                   double n_proposals, const double *ff, const double *dd,
-                                  const int *cg_iters, const double *cg_rr, nk_sr_stats *out,
-                                  cudaStream_t st) {
-    (k_write_sr_stats<<<1, 256, 0, st>>>(stats3, acc, C, n_proposals, ff, dd, cg_iters, cg_rr, out), nk::note_launch());
+                                  const int *cg_iters, const double *cg_rr, const int *status,
+                                  nk_sr_stats *out, cudaStream_t st) {
+    (k_write_sr_stats<<<1, 256, 0, st>>>(stats3, acc, C, n_proposals, ff, dd, cg_iters, cg_rr, status, out), nk::note_launch());
     return cudaGetLastError();
 }
 

@@ -1,0 +1,644 @@
+// Tensor-core (tcgen05) products for the dense contractions of the SR solve.
+//
+// FP64-accurate GEMM by integer splitting (the Ozaki scheme: Ozaki, Ogita,
+// Oishi, Rump, Numer. Algorithms 59 (2012); Ootomo, Ozaki, Yokota,
+// IJHPCA 2024).  Every row r of an FP64 operand (K <= 64 columns) is scaled
+// by its own power of two 2^-e_r (max |a_rk| < 2^e_r) and cut into S slices
+// of 8-bit integers alpha_s in [-255, 255]:
+//     a_rk = 2^e_r sum_{s=1..S} alpha_s,rk 2^{-8s} + (remainder < 2^{e_r - 8S}).
+// Integers of at most 8 bits are exact in BF16, their products exact in the
+// FP32 accumulator of kind::f16 MMAs, and a sum of up to four slice products
+// over K = 64 stays below 2^24, so the partial products
+//     D_g = sum_{s+t=g} sum_k alpha_s,ik beta_t,jk      (g = 2 .. S+1)
+// are exact integers for g <= 5 (the levels that carry the leading bits) and
+// carry a relative error 2^-24 x 2^{-8g} < 2^-70 beyond.  The epilogue
+// recombines C_ij = 2^{e_i + f_j} sum_g 2^{-8g} D_g in FP64.  With S = 7 the
+// dropped terms are below 2^-56 of K max|a| max|b|: FP64-level accuracy.
+// S = 3 gives about FP32 accuracy (24 bits per operand).
+//
+// Kernel shape: one 128 x 64 output tile per CTA, K = 64.  Thread 0 loads the
+// S slices of the A rows (128 x 64) and of the B rows (64 x 64) with TMA
+// (3-D tensor maps [S][rows][64] BF16, 128-byte swizzle) onto one mbarrier,
+// then issues the S(S+1)/2 x 4 tcgen05.mma (M = 128, N = 64, K = 16) into
+// S accumulators of 64 TMEM columns each, and commits to a second mbarrier;
+// the four warps then read their 32 TMEM lanes (= tile rows) and update C.
+// Every wait is bounded by the global timer; on time-out the kernel records
+// an error code, frees its TMEM and returns.
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "nk_common.cuh"
+#include "nk_internal.h"
+
+namespace nk {
+
+namespace {
+
+constexpr int kTileM = 128;
+constexpr int kTileN = 64;
+constexpr int kTileK = 64;
+constexpr int kMaxSlices = 7;
+constexpr uint32_t kTmemCols = 512;
+constexpr int kABytes = kTileM * kTileK * 2;  // one slice of the A tile
+constexpr int kBBytes = kTileN * kTileK * 2;  // one slice of the B tile
+constexpr unsigned long long kWaitNs = 2000000000ULL;  // 2 s
+
+// ------------------------------------------------------------ PTX helpers ---
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase; false after kWaitNs.
+__device__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    const unsigned long long t0 = global_ns();
+    for (long long it = 0; it < (1LL << 40); ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255) == 255 && global_ns() - t0 > kWaitNs) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0,
+                                            int c1, int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+                 "r"(ncols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand written by a TMA load with
+// 128-byte swizzle (8-row groups of 1024 bytes), sm_100 descriptor version 1.
+__device__ __forceinline__ uint64_t sw128_desc(const void *p) {
+    const uint64_t addr = smem_u32(p);
+    uint64_t d = (addr & 0x3FFFFULL) >> 4;    // start address
+    d |= (uint64_t)(16 >> 4) << 16;           // leading byte offset (unused for this layout)
+    d |= (uint64_t)(1024 >> 4) << 32;         // stride byte offset: next 8-row group
+    d |= (uint64_t)1 << 46;                   // descriptor version
+    d |= (uint64_t)2 << 61;                   // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor of kind::f16: BF16 A and B (K-major), FP32 D.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// ---------------------------------------------------------------- slicing ---
+
+// One warp per row: the first kcols (<= 64) entries of row r of A (row
+// stride lda) -> S BF16 integer slices out[s][r][0..63] (zero beyond kcols)
+// and the row exponent e_r.
+__global__ void k_slice_rows(const double *__restrict__ A, int64_t lda, int64_t rows, int kcols, int S,
+                             __nv_bfloat16 *__restrict__ out, int *__restrict__ expo) {
+    const int lane = threadIdx.x & 31;
+    const int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (r >= rows) return;
+    double x0 = lane < kcols ? A[(size_t)r * lda + lane] : 0.0;
+    double x1 = lane + 32 < kcols ? A[(size_t)r * lda + lane + 32] : 0.0;
+    double m = fmax(fabs(x0), fabs(x1));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+    int e = 0;
+    if (m > 0.0) frexp(m, &e);  // m < 2^e
+    x0 = ldexp(x0, -e);
+    x1 = ldexp(x1, -e);
+    for (int s = 0; s < S; ++s) {
+        x0 *= 256.0;
+        x1 *= 256.0;
+        const double a0 = trunc(x0), a1 = trunc(x1);
+        x0 -= a0;
+        x1 -= a1;
+        __nv_bfloat16 *o = out + ((size_t)s * rows + r) * kTileK;
+        o[lane] = __double2bfloat16(a0);
+        o[lane + 32] = __double2bfloat16(a1);
+    }
+    if (lane == 0) expo[r] = e;
+}
+
+// ------------------------------------------------------------- the GEMM ---
+
+struct OzArgs {
+    int64_t rows, cols;   // output rows (A rows) and columns (B rows)
+    int S;
+    const int *expA, *expB;
+    double *C;
+    int64_t ldc;
+    int mode;             // 0: C = R, 1: C -= R, 2: C += R
+    int lower;            // only entries with col <= row (tiles above are skipped)
+    int *err;
+};
+
+__global__ void __launch_bounds__(128, 1)
+    k_ozaki_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, OzArgs a) {
+    extern __shared__ unsigned char smem_raw[];
+    const int64_t m0 = (int64_t)blockIdx.y * kTileM;
+    const int64_t n0 = (int64_t)blockIdx.x * kTileN;
+    if (a.lower && n0 > m0 + kTileM - 1) return;
+    // 1024-byte aligned operand area (128-byte swizzle atoms)
+    const uint32_t base = smem_u32(smem_raw);
+    unsigned char *ops = smem_raw + ((1024 - (base & 1023)) & 1023);
+    unsigned char *sA = ops;                                  // [S][128][64] bf16
+    unsigned char *sB = ops + (size_t)kMaxSlices * kABytes;   // [S][64][64] bf16
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sB + (size_t)kMaxSlices * kBBytes);  // [0] tma, [1] mma
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2);
+    int *abort_flag = reinterpret_cast<int *>(tslot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int S = a.S;
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc(tslot, kTmemCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(&bars[0], (uint32_t)S * (kABytes + kBBytes));
+        for (int s = 0; s < S; ++s) {
+            tma_load_3d(sA + (size_t)s * kABytes, &mapA, &bars[0], 0, (int)m0, s);
+            tma_load_3d(sB + (size_t)s * kBBytes, &mapB, &bars[0], 0, (int)n0, s);
+        }
+        if (!mbar_wait(&bars[0], 0)) {
+            *abort_flag = 1;
+            atomicExch(a.err, 1);
+        } else {
+            tc_fence_after();
+            const uint32_t idesc = idesc_bf16(kTileM, kTileN);
+            for (int g = 2; g <= S + 1; ++g) {
+                const uint32_t dcol = tmem + (uint32_t)((g - 2) * kTileN);
+                bool first = true;
+                for (int s = 1; s < g; ++s) {
+                    const int t = g - s;
+                    if (s > S || t > S) continue;
+                    const uint64_t da = sw128_desc(sA + (size_t)(s - 1) * kABytes);
+                    const uint64_t db = sw128_desc(sB + (size_t)(t - 1) * kBBytes);
+#pragma unroll
+                    for (int kk = 0; kk < kTileK / 16; ++kk) {
+                        // advance 16 BF16 = 32 bytes along K inside the swizzle atom
+                        umma_bf16(dcol, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
+                                  first ? 0u : 1u);
+                        first = false;
+                    }
+                }
+            }
+            umma_commit(&bars[1]);
+        }
+    }
+    __syncthreads();
+    if (!*abort_flag) {
+        // one waiter per warp, so that the .sync.aligned TMEM loads below are
+        // executed by whole warps
+        int ok = 1;
+        if (lane == 0) ok = mbar_wait(&bars[1], 0) ? 1 : 0;
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) {
+            if (lane == 0) atomicExch(a.err, 2);
+        } else {
+            tc_fence_after();
+            const int64_t row = m0 + warp * 32 + lane;
+            const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+            const bool row_ok = row < a.rows;
+            const int ei = row_ok ? a.expA[row] : 0;
+            for (int c0 = 0; c0 < kTileN; c0 += 16) {
+                double acc[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) acc[j] = 0.0;
+                // smallest levels first
+                for (int g = S + 1; g >= 2; --g) {
+                    uint32_t r[16];
+                    tmem_ld16(lane_base + (uint32_t)((g - 2) * kTileN + c0), r);
+                    tmem_wait_ld();
+                    const double sc = ldexp(1.0, -8 * g);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) acc[j] += (double)__uint_as_float(r[j]) * sc;
+                }
+                if (row_ok) {
+                    double *crow = a.C + (size_t)row * a.ldc;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int64_t col = n0 + c0 + j;
+                        if (col >= a.cols || (a.lower && col > row)) continue;
+                        const double v = ldexp(acc[j], ei + a.expB[col]);
+                        if (a.mode == 0)
+                            crow[col] = v;
+                        else if (a.mode == 1)
+                            crow[col] -= v;
+                        else
+                            crow[col] += v;
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, kTmemCols);
+    }
+}
+
+// ------------------------------------------------- Cholesky building blocks ---
+
+constexpr int kNB = 64;
+
+// Factor the kb x kb diagonal block at (k, k) in place (lower) and write its
+// inverse, a lower-triangular 64 x 64 block (zero above the diagonal and
+// beyond kb), to Linv.
+__global__ void k_potrf_inv(double *__restrict__ A, int64_t n, int64_t k, int kb, int *__restrict__ info,
+                            double *__restrict__ Linv) {
+    __shared__ double L[kNB][kNB + 1];
+    __shared__ double X[kNB][kNB + 1];
+    const int t = threadIdx.x;
+    for (int r = 0; r < kNB; ++r) L[r][t] = (r < kb && t < kb) ? A[(size_t)(k + r) * n + k + t] : 0.0;
+    __syncthreads();
+    for (int c = 0; c < kb; ++c) {
+        if (t == 0) {
+            double d = L[c][c];
+            if (!(d > 0.0)) {
+                if (info) atomicExch(info, (int)(k + c + 1));
+                d = 1e-300;
+            }
+            L[c][c] = sqrt(d);
+        }
+        __syncthreads();
+        if (t > c && t < kb) L[t][c] /= L[c][c];
+        __syncthreads();
+        if (t > c && t < kb) {
+            const double ltc = L[t][c];
+            for (int q = c + 1; q <= t; ++q) L[t][q] -= ltc * L[q][c];
+        }
+        __syncthreads();
+    }
+    // column t of the inverse by forward substitution
+    for (int r = 0; r < kNB; ++r) X[r][t] = 0.0;
+    if (t < kb) {
+        X[t][t] = 1.0 / L[t][t];
+        for (int i = t + 1; i < kb; ++i) {
+            double acc = 0.0;
+            for (int q = t; q < i; ++q) acc += L[i][q] * X[q][t];
+            X[i][t] = -acc / L[i][i];
+        }
+    }
+    __syncthreads();
+    for (int r = 0; r < kb; ++r)
+        if (t <= r) A[(size_t)(k + r) * n + k + t] = L[r][t];
+    for (int r = 0; r < kNB; ++r) Linv[(size_t)r * kNB + t] = X[r][t];
+}
+
+// y_k = Linv_k b_k (forward step of L y = b on block k).
+__global__ void k_trsv_inv_lower(const double *__restrict__ Linv, int64_t k, int kb, double *__restrict__ b) {
+    __shared__ double v[kNB];
+    const int t = threadIdx.x;
+    v[t] = t < kb ? b[k + t] : 0.0;
+    __syncthreads();
+    double acc = 0.0;
+    for (int c = 0; c <= t && c < kb; ++c) acc += Linv[(size_t)t * kNB + c] * v[c];
+    if (t < kb) b[k + t] = acc;
+}
+
+// x_k = Linv_k^T y_k (backward step of L^T x = y on block k).
+__global__ void k_trsv_inv_upper(const double *__restrict__ Linv, int64_t k, int kb, double *__restrict__ b) {
+    __shared__ double v[kNB];
+    const int t = threadIdx.x;
+    v[t] = t < kb ? b[k + t] : 0.0;
+    __syncthreads();
+    double acc = 0.0;
+    for (int c = t; c < kb; ++c) acc += Linv[(size_t)c * kNB + t] * v[c];
+    if (t < kb) b[k + t] = acc;
+}
+
+__global__ void k_trsv_sub_lower(const double *__restrict__ A, int64_t n, int64_t k, int kb,
+                                 double *__restrict__ b) {
+    const int lane = threadIdx.x & 31;
+    const int64_t r = k + kb + (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (r >= n) return;
+    double acc = 0.0;
+    for (int c = lane; c < kb; c += 32) acc += A[(size_t)r * n + k + c] * b[k + c];
+    acc = warp_sum(acc);
+    if (lane == 0) b[r] -= acc;
+}
+
+__global__ void k_trsv_sub_upper(const double *__restrict__ A, int64_t n, int64_t k, int kb,
+                                 double *__restrict__ b) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= k) return;
+    double acc = 0.0;
+    for (int c = 0; c < kb; ++c) acc += A[(size_t)(k + c) * n + r] * b[k + c];
+    b[r] -= acc;
+}
+
+// Lower triangle of K holds g_t = t_k . t_l; replace it (both triangles) by
+// the Gram of the Jacobian rows g_s + g_t + g_t g_s with g_s = s_k . s_l
+// (exact integer dot products of the +-1 configurations).
+__global__ void __launch_bounds__(256) k_gram_combine(int N, int64_t Ns, const int8_t *__restrict__ s,
+                                                      double *__restrict__ K) {
+    __shared__ __align__(16) int8_t sa[64][132];
+    __shared__ __align__(16) int8_t sb[64][132];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int64_t m0 = (int64_t)blockIdx.y * 64, n0 = (int64_t)blockIdx.x * 64;
+    if (n0 > m0 + 63) return;
+    int gs[4][4] = {};
+    for (int i0 = 0; i0 < N; i0 += 128) {
+        for (int e = threadIdx.x; e < 64 * 128; e += 256) {
+            const int r = e >> 7, c = e & 127;
+            const int i = i0 + c;
+            sa[r][c] = (m0 + r < Ns && i < N) ? s[(size_t)(m0 + r) * N + i] : (int8_t)0;
+            sb[r][c] = (n0 + r < Ns && i < N) ? s[(size_t)(n0 + r) * N + i] : (int8_t)0;
+        }
+        __syncthreads();
+        for (int c = 0; c < 128; c += 4) {
+            int av[4], bv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                av[u] = *reinterpret_cast<const int *>(&sa[ty * 4 + u][c]);
+                bv[u] = *reinterpret_cast<const int *>(&sb[tx * 4 + u][c]);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) gs[u][v] = __dp4a(av[u], bv[v], gs[u][v]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int64_t k = m0 + ty * 4 + u;
+        if (k >= Ns) continue;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int64_t l = n0 + tx * 4 + v;
+            if (l >= Ns || l > k) continue;
+            const double gt = K[(size_t)k * Ns + l];
+            const double g = (double)gs[u][v] + gt + gt * (double)gs[u][v];
+            K[(size_t)k * Ns + l] = g;
+            K[(size_t)l * Ns + k] = g;
+        }
+    }
+}
+
+// ------------------------------------------------------ host: tensor maps ---
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
+                                  CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                  CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// 3-D map over slices [S][rows][64] BF16 with a box of one slice x box_rows rows.
+bool make_slice_map(CUtensorMap *map, const __nv_bfloat16 *slices, int64_t rows, int S, int box_rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)kTileK, (cuuint64_t)rows, (cuuint64_t)S};
+    cuuint64_t strides[2] = {(cuuint64_t)kTileK * 2, (cuuint64_t)rows * kTileK * 2};
+    cuuint32_t box[3] = {(cuuint32_t)kTileK, (cuuint32_t)box_rows, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16 *>(slices), dims, strides,
+                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+size_t ozaki_smem_bytes() {
+    return 1024 + (size_t)kMaxSlices * (kABytes + kBBytes) + 2 * sizeof(uint64_t) + 2 * sizeof(uint32_t) + 16;
+}
+
+inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+// ============================================================ launchers ====
+
+size_t slice_elems(int64_t rows, int S) { return (size_t)S * (size_t)rows * kTileK; }
+
+cudaError_t launch_slice_rows(const double *A, int64_t lda, int64_t rows, int kcols, int S,
+                              __nv_bfloat16 *out, int *expo, cudaStream_t st) {
+    if (rows <= 0) return cudaSuccess;
+    if (kcols < 1 || kcols > kTileK || S < 1 || S > kMaxSlices) return cudaErrorInvalidValue;
+    (k_slice_rows<<<nblk(rows, 8), 256, 0, st>>>(A, lda, rows, kcols, S, out, expo), nk::note_launch());
+    return cudaGetLastError();
+}
+
+// R = A B^T (FP64-accurate to the slice count), applied to C by mode.
+// A and B are given by their slices (rows x 64, as written by
+// launch_slice_rows) and row exponents.
+cudaError_t launch_ozaki_gemm(const __nv_bfloat16 *Asl, const int *expA, int64_t rows,
+                              const __nv_bfloat16 *Bsl, const int *expB, int64_t cols, int S, double *C,
+                              int64_t ldc, int mode, bool lower, int *err, cudaStream_t st) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    if (S < 1 || S > kMaxSlices) return cudaErrorInvalidValue;
+    if (rows > (1LL << 31) - kTileM || cols > (1LL << 31) - kTileN) return cudaErrorInvalidValue;
+    CUtensorMap ma, mb;
+    if (!make_slice_map(&ma, Asl, rows, S, kTileM) || !make_slice_map(&mb, Bsl, cols, S, kTileN))
+        return cudaErrorInvalidValue;
+    cudaError_t attr_err = cudaFuncSetAttribute(k_ozaki_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)ozaki_smem_bytes());
+    if (attr_err != cudaSuccess) return attr_err;
+    OzArgs a{rows, cols, S, expA, expB, C, ldc, mode, lower ? 1 : 0, err};
+    dim3 grid(nblk(cols, kTileN), nblk(rows, kTileM));
+    (k_ozaki_gemm<<<grid, 128, ozaki_smem_bytes(), st>>>(ma, mb, a), nk::note_launch());
+    return cudaGetLastError();
+}
+
+size_t tc_chol_ws_bytes(int64_t n) {
+    const int64_t nb = (n + kNB - 1) / kNB;
+    return slice_elems(n, kMaxSlices) * 2 + slice_elems(kNB, kMaxSlices) * 2 + (size_t)(n + kNB) * 4 +
+           (size_t)nb * kNB * kNB * 8 + 4 * 256;
+}
+
+namespace {
+struct TcWs {
+    __nv_bfloat16 *Asl, *Bsl;
+    int *expA, *expB;
+    double *Linv;
+};
+TcWs carve_tc(void *ws, int64_t n) {
+    char *p = static_cast<char *>(ws);
+    auto take = [&](size_t bytes) {
+        char *q = p;
+        p += (bytes + 255) & ~size_t(255);
+        return q;
+    };
+    TcWs w;
+    w.Asl = reinterpret_cast<__nv_bfloat16 *>(take(slice_elems(n, kMaxSlices) * 2));
+    w.Bsl = reinterpret_cast<__nv_bfloat16 *>(take(slice_elems(kNB, kMaxSlices) * 2));
+    w.expA = reinterpret_cast<int *>(take((size_t)n * 4));
+    w.expB = reinterpret_cast<int *>(take((size_t)kNB * 4));
+    w.Linv = reinterpret_cast<double *>(take((size_t)((n + kNB - 1) / kNB) * kNB * kNB * 8));
+    return w;
+}
+}  // namespace
+
+// Blocked right-looking Cholesky with tensor-core (Ozaki, 7 slices) panel
+// solves and trailing updates.  The inverted diagonal blocks stay in the
+// workspace for launch_cholesky_solve_tc.
+cudaError_t launch_cholesky_tc(double *A, int64_t n, int *info, int *err, void *ws, cudaStream_t st) {
+    TcWs w = carve_tc(ws, n);
+    const int S = kMaxSlices;
+    for (int64_t k = 0; k < n; k += kNB) {
+        const int kb = (int)(n - k < kNB ? n - k : kNB);
+        const int64_t rest = n - k - kb;
+        double *Linv = w.Linv + (size_t)(k / kNB) * kNB * kNB;
+        int slot = prof_begin(NK_PROF_CHOL_PANEL, st);
+        (k_potrf_inv<<<1, kNB, 0, st>>>(A, n, k, kb, info, Linv), nk::note_launch());
+        if (rest > 0) {
+            double *panel = A + (size_t)(k + kb) * n + k;
+            cudaError_t e = launch_slice_rows(Linv, kNB, kb, kb, S, w.Bsl, w.expB, st);
+            if (e == cudaSuccess) e = launch_slice_rows(panel, n, rest, kb, S, w.Asl, w.expA, st);
+            if (e == cudaSuccess)
+                e = launch_ozaki_gemm(w.Asl, w.expA, rest, w.Bsl, w.expB, kb, S, panel, n, 0, false, err, st);
+            prof_end(slot, st, (double)kb * kb * kb / 3.0 + 2.0 * (double)rest * kb * kb);
+            if (e != cudaSuccess) return e;
+            slot = prof_begin(NK_PROF_CHOL_UPDATE, st);
+            e = launch_slice_rows(panel, n, rest, kb, S, w.Asl, w.expA, st);
+            if (e == cudaSuccess)
+                e = launch_ozaki_gemm(w.Asl, w.expA, rest, w.Asl, w.expA, rest, S,
+                                      A + (size_t)(k + kb) * n + k + kb, n, 1, true, err, st);
+            prof_end(slot, st, (double)kb * rest * (double)(rest + 1));
+            if (e != cudaSuccess) return e;
+        } else {
+            prof_end(slot, st, (double)kb * kb * kb / 3.0);
+        }
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cholesky_solve_tc(const double *L, int64_t n, const void *ws, double *b, cudaStream_t st) {
+    TcWs w = carve_tc(const_cast<void *>(ws), n);
+    const int slot = prof_begin(NK_PROF_TRSV, st);
+    for (int64_t k = 0; k < n; k += kNB) {
+        const int kb = (int)(n - k < kNB ? n - k : kNB);
+        const double *Linv = w.Linv + (size_t)(k / kNB) * kNB * kNB;
+        (k_trsv_inv_lower<<<1, kNB, 0, st>>>(Linv, k, kb, b), nk::note_launch());
+        const int64_t rest = n - k - kb;
+        if (rest > 0) (k_trsv_sub_lower<<<nblk(rest, 8), 256, 0, st>>>(L, n, k, kb, b), nk::note_launch());
+    }
+    const int64_t last = ((n - 1) / kNB) * kNB;
+    for (int64_t k = last; k >= 0; k -= kNB) {
+        const int kb = (int)(n - k < kNB ? n - k : kNB);
+        const double *Linv = w.Linv + (size_t)(k / kNB) * kNB * kNB;
+        (k_trsv_inv_upper<<<1, kNB, 0, st>>>(Linv, k, kb, b), nk::note_launch());
+        if (k > 0) (k_trsv_sub_upper<<<nblk(k, 256), 256, 0, st>>>(L, n, k, kb, b), nk::note_launch());
+    }
+    prof_end(slot, st, 2.0 * (double)n * (double)n);
+    return cudaGetLastError();
+}
+
+// Lower triangle of K = T T^T by tensor cores with S slices per 64-column
+// chunk of T [Ns][M], then the Jacobian-row Gram s.s + t.t + (t.t)(s.s)
+// written to both triangles.
+cudaError_t launch_gram_tc(int N, int M, int64_t Ns, const int8_t *s, const double *T, int S, double *K,
+                           int *err, void *ws, cudaStream_t st) {
+    TcWs w = carve_tc(ws, Ns);
+    const int slot = prof_begin(NK_PROF_GRAM, st);
+    for (int c = 0; c < M; c += kTileK) {
+        const int kc = M - c < kTileK ? M - c : kTileK;
+        cudaError_t e = launch_slice_rows(T + c, M, Ns, kc, S, w.Asl, w.expA, st);
+        if (e == cudaSuccess)
+            e = launch_ozaki_gemm(w.Asl, w.expA, Ns, w.Asl, w.expA, Ns, S, K, Ns, c == 0 ? 0 : 2, true, err, st);
+        if (e != cudaSuccess) return e;
+    }
+    dim3 grid(nblk(Ns, 64), nblk(Ns, 64));
+    (k_gram_combine<<<grid, 256, 0, st>>>(N, Ns, s, K), nk::note_launch());
+    prof_end(slot, st, (double)Ns * (Ns + 1) * (double)(N + M));
+    return cudaGetLastError();
+}
+
+}  // namespace nk

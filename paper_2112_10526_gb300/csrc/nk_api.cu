@@ -192,11 +192,12 @@ struct SolveWs {
     int *flags;                   // done, iters
     // Cholesky
     double *dJ, *S, *mean, *ones;
-    int *info;
+    int *info;  // [0] breakdown pivot, [1] tensor-core time-out code
     double *K, *rowmean;
+    void *tc;   // tensor-core slices and inverted diagonal blocks (NK_MIXED)
 };
 
-void carve_solve(Carver &c, SolveWs &w, int N, int M, int64_t Ns, int solver) {
+void carve_solve(Carver &c, SolveWs &w, int N, int M, int64_t Ns, int solver, int precision) {
     const int64_t Np = n_params(N, M);
     w = SolveWs{};
     w.partial = c.take<double>(nk::vjp_partial_doubles(N, M, Ns));
@@ -215,14 +216,16 @@ void carve_solve(Carver &c, SolveWs &w, int N, int M, int64_t Ns, int solver) {
         w.S = c.take<double>((size_t)Np * Np);
         w.mean = c.take<double>(Np);
         w.ones = c.take<double>(Ns);
-        w.info = c.take<int>(1);
+        w.info = c.take<int>(2);
+        if (precision == NK_MIXED) w.tc = c.take<char>(nk::tc_chol_ws_bytes(Np));
     } else {
         w.U = c.take<double>((size_t)Ns * (M + 1));
         w.w = c.take<double>(Ns);
         w.K = c.take<double>((size_t)Ns * Ns);
         w.rowmean = c.take<double>(Ns + 1);
         w.tmp = c.take<double>(Np);
-        w.info = c.take<int>(1);
+        w.info = c.take<int>(2);
+        if (precision == NK_MIXED) w.tc = c.take<char>(nk::tc_chol_ws_bytes(Ns));
     }
 }
 
@@ -238,10 +241,22 @@ cudaError_t qgt_onthefly(int N, int M, int64_t Ns, const int8_t *s, const double
     return nk::launch_axpby(n_params(N, M), eps, v, 1.0, out, st);
 }
 
+// Reads the factorisation status words back (synchronises the stream).
+nk_status check_factor(nk_ctx *ctx, const int *info, cudaStream_t st) {
+    NK_CU(cudaMemcpyAsync(ctx->host_flags + 2, info, 2 * sizeof(int), cudaMemcpyDeviceToHost, st), "status");
+    NK_CU(cudaStreamSynchronize(st), "status");
+    if (ctx->host_flags[3])
+        return fail(NK_ERR_TIMEOUT, "a tensor-core product timed out (code %d)", ctx->host_flags[3]);
+    if (ctx->host_flags[2])
+        return fail(NK_ERR_CUDA, "Cholesky pivot %d not positive", ctx->host_flags[2]);
+    return NK_OK;
+}
+
 nk_status run_solve(nk_ctx *ctx, int N, int M, int64_t Ns, const int8_t *s, const double *T,
                     const double *F, int solver, double eps, double tol, int maxiter,
                     SolveWs &w, double *delta, int *host_info, double *host_resid,
-                    cudaStream_t st) {
+                    cudaStream_t st, int precision = NK_F64, bool sync_check = false) {
+    const bool tc = precision == NK_MIXED;
     const int64_t Np = n_params(N, M);
     if (host_info) host_info[0] = 0, host_info[1] = 1;
     if (host_resid) *host_resid = 0.0;
@@ -296,25 +311,40 @@ nk_status run_solve(nk_ctx *ctx, int N, int M, int64_t Ns, const int8_t *s, cons
               "chol mean");
         NK_CU(nk::launch_jacobian_rows(N, M, s, T, 0, Ns, w.mean, w.dJ, st), "chol dJ");
         NK_CU(nk::launch_syrk_t(w.dJ, Ns, Np, 1.0 / (double)Ns, eps, w.S, st), "chol syrk");
-        NK_CU(cudaMemsetAsync(w.info, 0, sizeof(int), st), "chol");
-        NK_CU(nk::launch_cholesky(w.S, Np, w.info, st), "chol factor");
+        NK_CU(cudaMemsetAsync(w.info, 0, 2 * sizeof(int), st), "chol");
+        if (tc)
+            NK_CU(nk::launch_cholesky_tc(w.S, Np, w.info, w.info + 1, w.tc, st), "chol factor");
+        else
+            NK_CU(nk::launch_cholesky(w.S, Np, w.info, st), "chol factor");
         NK_CU(nk::launch_axpby(Np, 1.0, F, 0.0, delta, st), "chol");
-        NK_CU(nk::launch_cholesky_solve(w.S, Np, delta, st), "chol solve");
-        return NK_OK;
+        if (tc)
+            NK_CU(nk::launch_cholesky_solve_tc(w.S, Np, w.tc, delta, st), "chol solve");
+        else
+            NK_CU(nk::launch_cholesky_solve(w.S, Np, delta, st), "chol solve");
+        return sync_check ? check_factor(ctx, w.info, st) : NK_OK;
     }
     // sample space: delta = (F - X^T (X X^T + eps I)^{-1} X F) / eps, X = dJ / sqrt(Ns)
     const double isq = 1.0 / std::sqrt((double)Ns);
-    NK_CU(nk::launch_gram_samplespace(N, M, Ns, s, T, eps, w.K, w.rowmean, st), "ss gram");
-    NK_CU(cudaMemsetAsync(w.info, 0, sizeof(int), st), "ss");
-    NK_CU(nk::launch_cholesky(w.K, Ns, w.info, st), "ss factor");
+    NK_CU(cudaMemsetAsync(w.info, 0, 2 * sizeof(int), st), "ss");
+    if (tc) {
+        NK_CU(nk::launch_gram_tc(N, M, Ns, s, T, 7, w.K, w.info + 1, w.tc, st), "ss gram");
+        NK_CU(nk::launch_center_gram(Ns, w.K, w.rowmean, eps, st), "ss gram");
+        NK_CU(nk::launch_cholesky_tc(w.K, Ns, w.info, w.info + 1, w.tc, st), "ss factor");
+    } else {
+        NK_CU(nk::launch_gram_samplespace(N, M, Ns, s, T, eps, w.K, w.rowmean, st), "ss gram");
+        NK_CU(nk::launch_cholesky(w.K, Ns, w.info, st), "ss factor");
+    }
     NK_CU(nk::launch_jvp(N, M, Ns, s, T, F, w.U, w.w, st), "ss XF");
     NK_CU(nk::launch_center(Ns, w.w, w.dotp, isq, st), "ss XF");
-    NK_CU(nk::launch_cholesky_solve(w.K, Ns, w.w, st), "ss solve");
+    if (tc)
+        NK_CU(nk::launch_cholesky_solve_tc(w.K, Ns, w.tc, w.w, st), "ss solve");
+    else
+        NK_CU(nk::launch_cholesky_solve(w.K, Ns, w.w, st), "ss solve");
     NK_CU(nk::launch_center(Ns, w.w, w.dotp, isq, st), "ss Xty");
     NK_CU(nk::launch_vjp(N, M, Ns, s, T, w.w, 1.0, nullptr, w.partial, w.tmp, st), "ss Xty");
     NK_CU(nk::launch_axpby(Np, 1.0 / eps, F, 0.0, delta, st), "ss delta");
     NK_CU(nk::launch_axpby(Np, -1.0 / eps, w.tmp, 1.0, delta, st), "ss delta");
-    return NK_OK;
+    return sync_check ? check_factor(ctx, w.info, st) : NK_OK;
 }
 
 nk_status check_solver(int solver, double eps, double tol, int maxiter) {
@@ -355,7 +385,7 @@ nk_status nk_ctx_create(int32_t device, nk_ctx **out) {
     if (!g.ok) return fail(NK_ERR_CUDA, "cannot select device %d", device);
     nk_ctx *c = new nk_ctx{};
     c->device = device;
-    e = cudaMallocHost(&c->host_flags, 4 * sizeof(int));
+    e = cudaMallocHost(&c->host_flags, 8 * sizeof(int));
     if (e == cudaSuccess) e = cudaMallocHost(&c->host_vals, 8 * sizeof(double));
     if (e != cudaSuccess) {
         if (c->host_flags) cudaFreeHost(c->host_flags);
@@ -675,6 +705,33 @@ nk_status nk_qgt_matvec(nk_ctx *ctx, const nk_qgt *q, double diag_shift, const d
     });
 }
 
+nk_status nk_tc_gemm(nk_ctx *ctx, int64_t rows, int64_t cols, int32_t k, const double *A, int64_t lda,
+                     const double *B, int64_t ldb, int32_t slices, int32_t mode, int32_t lower,
+                     double *C, int64_t ldc, void *stream) {
+    if (!ctx) return fail(NK_ERR_INVALID_ARG, "ctx is NULL");
+    DeviceGuard g(ctx->device);
+    if (rows < 0 || cols < 0 || k < 1 || k > 64 || slices < 1 || slices > 7 || mode < 0 || mode > 2)
+        return fail(NK_ERR_INVALID_ARG, "need rows, cols >= 0, 1 <= k <= 64, 1 <= slices <= 7, 0 <= mode <= 2");
+    if (lda < k || ldb < k || ldc < cols) return fail(NK_ERR_INVALID_ARG, "leading dimension too small");
+    if (rows == 0 || cols == 0) return NK_OK;
+    NK_DEV(A, "A");
+    NK_DEV(B, "B");
+    NK_DEV(C, "C");
+    cudaStream_t st = (cudaStream_t)stream;
+    return with_workspace(ctx, [&](Carver &c, bool run) -> nk_status {
+        __nv_bfloat16 *as = c.take<__nv_bfloat16>(nk::slice_elems(rows, slices));
+        __nv_bfloat16 *bs = c.take<__nv_bfloat16>(nk::slice_elems(cols, slices));
+        int *ea = c.take<int>(rows), *eb = c.take<int>(cols), *err = c.take<int>(2);
+        if (!run) return NK_OK;
+        NK_CU(cudaMemsetAsync(err, 0, 2 * sizeof(int), st), "tc gemm");
+        NK_CU(nk::launch_slice_rows(A, lda, rows, k, slices, as, ea, st), "slice A");
+        NK_CU(nk::launch_slice_rows(B, ldb, cols, k, slices, bs, eb, st), "slice B");
+        NK_CU(nk::launch_ozaki_gemm(as, ea, rows, bs, eb, cols, slices, C, ldc, mode, lower != 0, err + 1, st),
+              "tc gemm");
+        return check_factor(ctx, err, st);
+    });
+}
+
 nk_status nk_sr_solve(nk_ctx *ctx, const nk_rbm *rbm, int32_t precision, const int8_t *s,
                       int64_t Ns, const double *F, int32_t solver, double diag_shift,
                       double cg_tol, int32_t cg_maxiter, double *delta_out, int32_t *info_out,
@@ -694,11 +751,11 @@ nk_status nk_sr_solve(nk_ctx *ctx, const nk_rbm *rbm, int32_t precision, const i
     return with_workspace(ctx, [&](Carver &c, bool run) -> nk_status {
         double *T = c.take<double>((size_t)Ns * M);
         SolveWs w;
-        carve_solve(c, w, N, M, Ns, solver);
+        carve_solve(c, w, N, M, Ns, solver, precision);
         if (!run) return NK_OK;
         NK_CU(nk::launch_theta_tanh(N, M, rbm->params + N, rbm->params + N + M, s, Ns, T, st), "theta");
         return run_solve(ctx, N, M, Ns, s, T, F, solver, diag_shift, cg_tol, cg_maxiter, w,
-                         delta_out, info_out, resid_out, st);
+                         delta_out, info_out, resid_out, st, precision, precision == NK_MIXED);
     });
 }
 
@@ -743,7 +800,7 @@ nk_status nk_sr_step(nk_ctx *ctx, nk_rbm *rbm, const nk_ham *ham, nk_chains *cha
         double *nrm = c.take<double>(2);
         unsigned long long *acc = c.take<unsigned long long>(C);
         SolveWs w;
-        carve_solve(c, w, N, M, Ns, cfg->solver);
+        carve_solve(c, w, N, M, Ns, cfg->solver, cfg->precision);
         if (!run) return NK_OK;
         NK_CU(nk::launch_tables(t, site, edge, st), "tables");
         NK_CU(cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * C, st), "memset");
@@ -773,7 +830,8 @@ nk_status nk_sr_step(nk_ctx *ctx, nk_rbm *rbm, const nk_ham *ham, nk_chains *cha
         int info[2] = {0, 0};
         double resid = 0.0;
         nk_status ss = run_solve(ctx, N, M, Ns, samples, T, F, cfg->solver, cfg->diag_shift,
-                                 cfg->cg_tol, cfg->cg_maxiter, w, delta, info, &resid, st);
+                                 cfg->cg_tol, cfg->cg_maxiter, w, delta, info, &resid, st,
+                                 cfg->precision, false);
         if (ss != NK_OK && ss != NK_ERR_NOT_CONVERGED) return ss;
         NK_CU(nk::launch_dot(Np, F, F, w.dotp, nrm, st), "norm");
         NK_CU(nk::launch_dot(Np, delta, delta, w.dotp, nrm + 1, st), "norm");
@@ -783,7 +841,7 @@ nk_status nk_sr_step(nk_ctx *ctx, nk_rbm *rbm, const nk_ham *ham, nk_chains *cha
             const bool cg = cfg->solver == NK_SOLVER_CG;
             NK_CU(nk::launch_write_sr_stats(st3, acc, C, nprop, cg ? w.sc + 3 : nrm, nrm + 1,
                                             cg ? w.flags + 1 : nullptr, cg ? w.sc + 4 : nullptr,
-                                            stats_out, st),
+                                            cg ? nullptr : w.info, stats_out, st),
                   "stats out");
         }
         if (chains->n_accepted) {

@@ -2,6 +2,7 @@
 // translation units.  Not part of the public ABI.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -110,10 +111,29 @@ cudaError_t launch_syrk_t(const double *A, int64_t rows, int64_t cols, double sc
 cudaError_t launch_gram_samplespace(int N, int M, int64_t Ns, const int8_t *s, const double *T,
                                     double eps, double *K, double *rowmean, cudaStream_t st);
 
+// Row means, grand mean and K <- P K P / Ns + eps I for a full symmetric K.
+cudaError_t launch_center_gram(int64_t Ns, double *K, double *rowmean, double eps, cudaStream_t st);
+
 // In-place lower Cholesky of an n x n matrix (lda = n); info: device int.
 cudaError_t launch_cholesky(double *A, int64_t n, int *info, cudaStream_t st);
 // Solve L L^T x = b in place (b -> x).
 cudaError_t launch_cholesky_solve(const double *L, int64_t n, double *b, cudaStream_t st);
+
+// ---- tensor-core products (k_tc.cu) ---------------------------------------
+// FP64 rows -> S BF16 integer slices [S][rows][64] + row exponents.
+size_t slice_elems(int64_t rows, int S);
+cudaError_t launch_slice_rows(const double *A, int64_t lda, int64_t rows, int kcols, int S,
+                              __nv_bfloat16 *out, int *expo, cudaStream_t st);
+// C (mode 0: =, 1: -=, 2: +=) A B^T from slices, 128 x 64 tiles, K <= 64.
+cudaError_t launch_ozaki_gemm(const __nv_bfloat16 *Asl, const int *expA, int64_t rows,
+                              const __nv_bfloat16 *Bsl, const int *expB, int64_t cols, int S, double *C,
+                              int64_t ldc, int mode, bool lower, int *err, cudaStream_t st);
+size_t tc_chol_ws_bytes(int64_t n);
+cudaError_t launch_cholesky_tc(double *A, int64_t n, int *info, int *err, void *ws, cudaStream_t st);
+cudaError_t launch_cholesky_solve_tc(const double *L, int64_t n, const void *ws, double *b,
+                                     cudaStream_t st);
+cudaError_t launch_gram_tc(int N, int M, int64_t Ns, const int8_t *s, const double *T, int S, double *K,
+                           int *err, void *ws, cudaStream_t st);
 
 // vector helpers
 cudaError_t launch_axpby(int64_t n, double alpha, const double *x, double beta, double *y,
@@ -140,7 +160,7 @@ cudaError_t launch_make_force_g(int64_t Ns, const double *eloc, const double *st
                                 double *g, cudaStream_t st);
 cudaError_t launch_write_sr_stats(const double *stats3, const unsigned long long *acc, int C,
                                   double n_proposals, const double *ff, const double *dd,
-                                  const int *cg_iters, const double *cg_rr, nk_sr_stats *out,
-                                  cudaStream_t st);
+                                  const int *cg_iters, const double *cg_rr, const int *status,
+                                  nk_sr_stats *out, cudaStream_t st);
 
 }  // namespace nk

@@ -70,7 +70,8 @@ class nk_sr_cfg(ctypes.Structure):
 
 
 SR_STATS_FIELDS = ["energy", "variance", "error", "acceptance", "cg_iters", "cg_residual", "f_norm",
-                   "delta_norm"]
+                   "delta_norm", "solver_status"]
+SR_STATS_DOUBLES = len(SR_STATS_FIELDS)
 
 _lib = None
 
@@ -101,6 +102,7 @@ def lib():
         "nk_jvp": [P, ctypes.POINTER(nk_rbm), i32, P, i64, P, P, P],
         "nk_force": [P, ctypes.POINTER(nk_rbm), i32, P, i64, P, P, P],
         "nk_qgt_matvec": [P, ctypes.POINTER(nk_qgt), f64, P, P, P],
+        "nk_tc_gemm": [P, i64, i64, i32, P, i64, P, i64, i32, i32, i32, P, i64, P],
         "nk_sr_solve": [P, ctypes.POINTER(nk_rbm), i32, P, i64, P, i32, f64, f64, i32, P,
                         ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double), P],
         "nk_sr_step": [P, ctypes.POINTER(nk_rbm), ctypes.POINTER(nk_ham), ctypes.POINTER(nk_chains),
@@ -278,6 +280,15 @@ def nk_qgt_matvec(ctx, v, out, diag_shift, params=None, N=None, M=None, s=None, 
     _check(lib().nk_qgt_matvec(ctx.handle, ctypes.byref(q), float(diag_shift), _ptr(v), _ptr(out),
                                _stream(stream)))
     return out
+
+
+def nk_tc_gemm(ctx, A, B, C, slices=7, mode=0, lower=False, stream=None):
+    """C (mode 0 '=', 1 '-=', 2 '+=') A @ B.T on the tensor cores, FP64-accurate at 7 slices."""
+    rows, k = A.shape
+    cols = B.shape[0]
+    _check(lib().nk_tc_gemm(ctx.handle, rows, cols, k, _ptr(A), A.stride(0), _ptr(B), B.stride(0), slices, mode,
+                            int(bool(lower)), _ptr(C), C.stride(0), _stream(stream)))
+    return C
 
 
 def nk_sr_solve(ctx, params, N, M, s, F, delta_out, solver="cg", diag_shift=0.01, cg_tol=1e-10,

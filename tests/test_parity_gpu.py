@@ -239,7 +239,7 @@ def _sr_run(ctx, N, M, hamf, rule, C, nd, ns, seed, solver, eps, lr, steps, prec
     pd, sd = cu(p0), cu(s0)
     ch = nk.make_chains(sd)
     cfg = nk.make_cfg(rule, prec, solver, nd, ns, eps, lr, seed, cg_tol=1e-10, cg_maxiter=2000)
-    stats = torch.empty(8, dtype=torch.float64, device=dev())
+    stats = torch.empty(nk.SR_STATS_DOUBLES, dtype=torch.float64, device=dev())
     samples = torch.empty((C * ns, N), dtype=torch.int8, device=dev())
     eloc = torch.empty(C * ns, dtype=torch.float64, device=dev())
     out = []

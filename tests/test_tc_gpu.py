@@ -1,0 +1,113 @@
+"""Tensor-core (tcgen05) products and the NK_MIXED solves, through the C ABI.
+
+nk_tc_gemm is compared with a plain FP64 product within the splitting bound
+4 K (S + 3) 2^-8S max|a_i| max|b_j| (S slices per operand row), i.e. about
+2^-50 K max|a| max|b| with 7 slices (FP64-level) and 2^-19 with 3 slices,
+plus one rounding (2^-52) of the result for the accumulating modes.  The NK_MIXED SR
+solves (tensor-core Cholesky, FP64-level products) must match the oracle's
+dense FP64 solve within the same 1e-8 as the FP64 path.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2112_10526_gb300 import inputs as I
+from paper_2112_10526_gb300 import nk
+
+from gpu_util import cu, dev, vec_rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    with nk.Ctx() as c:
+        yield c
+
+
+# (rows, cols, k, mode, lower); mode 0 '=', 1 '-=', 2 '+='
+GEMM_CASES = [(300, 130, 64, 0, False), (128, 64, 64, 0, False), (1, 1, 1, 0, False), (257, 65, 37, 1, False),
+              (400, 400, 64, 1, True), (129, 200, 50, 2, True), (64, 300, 64, 0, False)]
+
+
+@pytest.mark.parametrize("rows,cols,k,mode,lower", GEMM_CASES)
+@pytest.mark.parametrize("slices,bits", [(7, 50), (3, 20)])
+def test_tc_gemm_against_fp64(ctx, rows, cols, k, mode, lower, slices, bits):
+    rng = np.random.default_rng(rows * 7 + cols)
+    # rows of very different magnitudes exercise the per-row scaling
+    A = rng.normal(size=(rows, k)) * np.exp2(rng.integers(-20, 20, size=(rows, 1)))
+    B = rng.normal(size=(cols, k)) * np.exp2(rng.integers(-20, 20, size=(cols, 1)))
+    C0 = rng.normal(size=(rows, cols))
+    C = cu(C0.copy())
+    nk.nk_tc_gemm(ctx, cu(A), cu(B), C, slices=slices, mode=mode, lower=lower)
+    R = A @ B.T
+    ref = {0: R, 1: C0 - R, 2: C0 + R}[mode]
+    scale = np.abs(A) @ np.abs(B).T
+    got = C.cpu().numpy()
+    mask = np.tril(np.ones((rows, cols), dtype=bool)) if lower else np.ones((rows, cols), dtype=bool)
+    # Splitting error: each operand row is 2^e (sum of S 8-bit slices + a
+    # remainder below 2^-8S), 2^e <= 2 max|row|, and the dropped slice products
+    # and remainders add up to at most (S + 3) 2^-8S per term, so
+    # |err| <= 4 K (S + 3) 2^-8S max|a_i| max|b_j|; plus one rounding of the
+    # result for the accumulating modes.
+    amax = np.abs(A).max(axis=1)[:, None]
+    bmax = np.abs(B).max(axis=1)[None, :]
+    split = 4.0 * k * (slices + 3) * 2.0 ** (-8 * slices) * amax * bmax
+    bound = split[mask] + 2.0 ** -52 * np.abs(ref[mask])
+    assert (np.abs(got - ref)[mask] <= bound).all()
+    # and, against sum |a b|, FP64-level with 7 slices
+    assert (np.abs(got - ref)[mask] <= 2.0 ** -bits * scale[mask] * 64 + 2.0 ** -52 * np.abs(ref[mask])).all()
+    if lower:  # entries above the diagonal are untouched
+        np.testing.assert_array_equal(got[~mask], C0[~mask])
+
+
+@pytest.mark.parametrize("solver", ["cholesky", "cholesky_samplespace"])
+@pytest.mark.parametrize("N,M,Ns,eps", [(16, 16, 1024, 0.01), (10, 20, 100, 0.05), (6, 6, 700, 0.01),
+                                        (12, 12, 130, 0.1), (36, 72, 300, 0.01)])
+def test_mixed_sr_solve_matches_oracle(ctx, solver, N, M, Ns, eps):
+    p = I.rbm_params(N, M, 4, 0.3)
+    s = I.random_configs(Ns, N, 6)
+    Np = N + M + M * N
+    if solver == "cholesky" and Np > 4000:
+        pytest.skip("dense parameter-space case kept small")
+    O = oracle.jacobian(p, N, M, s)
+    F = np.random.default_rng(2).normal(size=Np) * 0.1
+    ref = oracle.solve_cholesky(oracle.qgt_dense(O), F, eps)
+    d = torch.empty(Np, dtype=torch.float64, device=dev())
+    nk.nk_sr_solve(ctx, cu(p), N, M, cu(s), cu(F), d, solver=solver, diag_shift=eps, precision="mixed")
+    assert vec_rel_err(d.cpu().numpy(), ref) < 1e-8
+
+
+@pytest.mark.parametrize("solver", ["cholesky_samplespace", "cholesky", "cg"])
+def test_mixed_sr_step_against_oracle(ctx, solver):
+    """One NK_MIXED step on the 4x4 Heisenberg lattice: E_loc per sample within
+    1e-4 of the oracle on the GPU's own samples, and the update equal to the
+    oracle's SR solution for the GPU's local energies within 1e-8 (1e-7 for CG
+    at its 1e-10 stopping tolerance)."""
+    N, M, C, ns = 16, 32, 32, 8
+    ham = I.heis_square(4)
+    p0 = I.rbm_params(N, M, 2, 0.2)
+    s0 = oracle.chain_init(N, C, "exchange", 2, 0)
+    edges = cu(ham["edges"])
+    h = nk.make_ham("heis", 1.0, 0.0, True, edges)
+    pd, sd = cu(p0), cu(s0)
+    ch = nk.make_chains(sd)
+    cfg = nk.make_cfg("exchange", "mixed", solver, 4, ns, 0.01, 0.02, 2, cg_tol=1e-10, cg_maxiter=3000)
+    stats = torch.empty(nk.SR_STATS_DOUBLES, dtype=torch.float64, device=dev())
+    samples = torch.empty((C * ns, N), dtype=torch.int8, device=dev())
+    eloc = torch.empty(C * ns, dtype=torch.float64, device=dev())
+    nk.nk_sr_step(ctx, pd, N, M, h, ch, cfg, stats, samples, eloc)
+    st = nk.sr_stats_dict(stats)
+    assert st["solver_status"] == 0
+    sm = samples.cpu().numpy()
+    e = eloc.cpu().numpy()
+    ref_e = oracle.local_energy(p0, N, M, ham, sm)
+    assert np.max(np.abs(e - ref_e) / np.maximum(np.abs(ref_e), np.sqrt(np.mean(ref_e ** 2)))) < 1e-4
+    O = oracle.jacobian(p0, N, M, sm)
+    F = oracle.force(O, e)
+    delta = oracle.solve_cholesky(oracle.qgt_dense(O), F, 0.01)
+    got = (p0 - pd.cpu().numpy()) / 0.02
+    assert vec_rel_err(got, delta) < (1e-7 if solver == "cg" else 1e-8)
