@@ -164,32 +164,91 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 
 // One warp per row: the first kcols (<= 64) entries of row r of A (row
 // stride lda) -> S BF16 integer slices out[s][r][0..63] (zero beyond kcols)
-// and the row exponent e_r.
+// and the row exponent e_r (max |a_rk| < 2^e_r).  The slices are the bytes,
+// from the top, of the fixed-point magnitude floor(|a| 2^(8S - e_r)), with the
+// sign of a: exactly the digits of repeated multiply-by-256-and-truncate,
+// taken from the FP64 bit pattern with integer shifts only.
+__device__ __forceinline__ void split_bits(double x, int &biased, unsigned long long &mant, bool &neg) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    neg = (b >> 63) != 0;
+    biased = (int)((b >> 52) & 0x7FF);
+    mant = b & 0xFFFFFFFFFFFFFULL;
+    if (biased != 0) mant |= 1ULL << 52;
+    else biased = 1;  // subnormal: value = mant 2^(1 - 1075)
+}
+
 __global__ void k_slice_rows(const double *__restrict__ A, int64_t lda, int64_t rows, int kcols, int S,
                              __nv_bfloat16 *__restrict__ out, int *__restrict__ expo) {
     const int lane = threadIdx.x & 31;
     const int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (r >= rows) return;
-    double x0 = lane < kcols ? A[(size_t)r * lda + lane] : 0.0;
-    double x1 = lane + 32 < kcols ? A[(size_t)r * lda + lane + 32] : 0.0;
-    double m = fmax(fabs(x0), fabs(x1));
+    const double x0 = lane < kcols ? A[(size_t)r * lda + lane] : 0.0;
+    const double x1 = lane + 32 < kcols ? A[(size_t)r * lda + lane + 32] : 0.0;
+    int b0, b1;
+    unsigned long long m0, m1;
+    bool n0, n1;
+    split_bits(x0, b0, m0, n0);
+    split_bits(x1, b1, m1, n1);
+    // |x| < 2^(biased - 1022) for nonzero x; the row exponent is the largest
+    int ex = -100000;
+    if (m0) ex = b0 - 1022;
+    if (m1) ex = max(ex, b1 - 1022);
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
-    int e = 0;
-    if (m > 0.0) frexp(m, &e);  // m < 2^e
-    x0 = ldexp(x0, -e);
-    x1 = ldexp(x1, -e);
-    for (int s = 0; s < S; ++s) {
-        x0 *= 256.0;
-        x1 *= 256.0;
-        const double a0 = trunc(x0), a1 = trunc(x1);
-        x0 -= a0;
-        x1 -= a1;
-        __nv_bfloat16 *o = out + ((size_t)s * rows + r) * kTileK;
-        o[lane] = __double2bfloat16(a0);
-        o[lane + 32] = __double2bfloat16(a1);
+    for (int off = 16; off > 0; off >>= 1) ex = max(ex, __shfl_xor_sync(0xffffffffu, ex, off));
+    const int e = ex == -100000 ? 0 : ex;
+    // fixed point Y = floor(|x| 2^(8S - e)) = mant 2^(biased - 1075 + 8S - e) < 2^(8S)
+    auto fixp = [&](int biased, unsigned long long mant) -> unsigned long long {
+        if (!mant) return 0ULL;
+        const int sh = biased - 1075 + 8 * S - e;
+        if (sh >= 0) return mant << sh;  // sh <= 3 here
+        if (sh <= -64) return 0ULL;
+        return mant >> (-sh);
+    };
+    const unsigned long long y0 = fixp(b0, m0), y1 = fixp(b1, m1);
+    for (int q = 0; q < S; ++q) {
+        const int sh = 8 * (S - 1 - q);
+        const int d0 = (int)((y0 >> sh) & 0xFFULL), d1 = (int)((y1 >> sh) & 0xFFULL);
+        __nv_bfloat16 *o = out + ((size_t)q * rows + r) * kTileK;
+        o[lane] = __int2bfloat16_rn(n0 ? -d0 : d0);
+        o[lane + 32] = __int2bfloat16_rn(n1 ? -d1 : d1);
     }
     if (lane == 0) expo[r] = e;
+}
+
+// Value V 2^sc as an FP64 bit pattern built with integer operations (round
+// to nearest even); V is the exact 128-bit fixed-point recombination of the
+// slice products.
+__device__ __forceinline__ double fixed_to_double(__int128 V, int sc) {
+    if (V == 0) return 0.0;
+    const bool neg = V < 0;
+    const unsigned __int128 mag = neg ? (unsigned __int128)(-V) : (unsigned __int128)V;
+    const unsigned long long h = (unsigned long long)(mag >> 64), l = (unsigned long long)mag;
+    int p = h ? 127 - __clzll(h) : 63 - __clzll(l);  // index of the leading one
+    unsigned long long mant;
+    if (p <= 52) {
+        mant = l << (52 - p);
+    } else {
+        const int sh = p - 52;
+        const unsigned __int128 q = mag >> sh;
+        mant = (unsigned long long)q;
+        const unsigned __int128 rem = mag - (q << sh);
+        const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
+        if (rem > half || (rem == half && (mant & 1ULL))) {
+            ++mant;
+            if (mant == (1ULL << 53)) {
+                mant >>= 1;
+                ++p;
+            }
+        }
+    }
+    const int E = p + sc + 1023;
+    if (E <= 0 || E >= 2047) {  // outside the normal range: FP64 fallback
+        const double d = (double)h * 18446744073709551616.0 + (double)l;
+        return ldexp(neg ? -d : d, sc);
+    }
+    const unsigned long long bits = (neg ? (1ULL << 63) : 0ULL) | ((unsigned long long)E << 52) |
+                                    (mant & 0xFFFFFFFFFFFFFULL);
+    return __longlong_as_double((long long)bits);
 }
 
 // ------------------------------------------------------------- the GEMM ---
@@ -205,7 +264,10 @@ struct OzArgs {
     int *err;
 };
 
-__global__ void __launch_bounds__(128, 1)
+constexpr int kOzThreads = 256;
+constexpr int kOutLd = kTileN + 1;  // staged output tile [128][65] doubles
+
+__global__ void __launch_bounds__(kOzThreads, 1)
     k_ozaki_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, OzArgs a) {
     extern __shared__ unsigned char smem_raw[];
     const int64_t m0 = (int64_t)blockIdx.y * kTileM;
@@ -274,40 +336,76 @@ __global__ void __launch_bounds__(128, 1)
         if (lane == 0) ok = mbar_wait(&bars[1], 0) ? 1 : 0;
         ok = __shfl_sync(0xffffffffu, ok, 0);
         if (!ok) {
-            if (lane == 0) atomicExch(a.err, 2);
+            if (lane == 0) {
+                atomicExch(a.err, 2);
+                *abort_flag = 2;
+            }
         } else {
             tc_fence_after();
-            const int64_t row = m0 + warp * 32 + lane;
-            const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-            const bool row_ok = row < a.rows;
-            const int ei = row_ok ? a.expA[row] : 0;
-            for (int c0 = 0; c0 < kTileN; c0 += 16) {
-                double acc[16];
+            // Warp w reads TMEM lanes 32 (w % 4) .. +31 (= tile rows) and the
+            // column half w / 4; results go to a staged tile in the operand
+            // area, which the MMAs no longer read.
+            const int rloc = (warp & 3) * 32 + lane;
+            const int64_t row = m0 + rloc;
+            const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+            const int ei = row < a.rows ? a.expA[row] : 0;
+            double *tile = reinterpret_cast<double *>(sA);
+            for (int c0 = (warp >> 2) * 32; c0 < (warp >> 2) * 32 + 32; c0 += 16) {
+                // V = sum_g D_g 2^(8 (8 - g)) = hi 2^32 + lo, exactly, in integers
+                long long hi[16], lo[16];
 #pragma unroll
-                for (int j = 0; j < 16; ++j) acc[j] = 0.0;
-                // smallest levels first
-                for (int g = S + 1; g >= 2; --g) {
+                for (int j = 0; j < 16; ++j) hi[j] = lo[j] = 0;
+                for (int g = 2; g <= S + 1; ++g) {
                     uint32_t r[16];
                     tmem_ld16(lane_base + (uint32_t)((g - 2) * kTileN + c0), r);
                     tmem_wait_ld();
-                    const double sc = ldexp(1.0, -8 * g);
+                    if (g <= 4) {
+                        const int sh = 8 * (4 - g);
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) acc[j] += (double)__uint_as_float(r[j]) * sc;
-                }
-                if (row_ok) {
-                    double *crow = a.C + (size_t)row * a.ldc;
+                        for (int j = 0; j < 16; ++j)
+                            hi[j] += (long long)__float2int_rn(__uint_as_float(r[j])) << sh;
+                    } else {
+                        const int sh = 8 * (8 - g);
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int64_t col = n0 + c0 + j;
-                        if (col >= a.cols || (a.lower && col > row)) continue;
-                        const double v = ldexp(acc[j], ei + a.expB[col]);
-                        if (a.mode == 0)
-                            crow[col] = v;
-                        else if (a.mode == 1)
-                            crow[col] -= v;
-                        else
-                            crow[col] += v;
+                        for (int j = 0; j < 16; ++j)
+                            lo[j] += (long long)__float2int_rn(__uint_as_float(r[j])) << sh;
                     }
+                }
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int64_t col = n0 + c0 + j;
+                    const int fj = col < a.cols ? a.expB[col] : 0;
+                    const __int128 V = ((__int128)hi[j] << 32) + (__int128)lo[j];
+                    tile[rloc * kOutLd + c0 + j] = fixed_to_double(V, ei + fj - 64);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (!*abort_flag) {
+        // coalesced update of C: consecutive threads take consecutive columns
+        const double *tile = reinterpret_cast<const double *>(sA);
+        const int cx = threadIdx.x & 63, ry = threadIdx.x >> 6;
+        const int64_t col = n0 + cx;
+        constexpr int kStep = kOzThreads / 64, kBatch = 8;
+        if (col < a.cols) {
+            for (int rb = ry; rb < kTileM; rb += kStep * kBatch) {
+                // all loads of a batch first, so that they are in flight together
+                double cv[kBatch];
+                bool on[kBatch];
+#pragma unroll
+                for (int u = 0; u < kBatch; ++u) {
+                    const int rl = rb + kStep * u;
+                    const int64_t row = m0 + rl;
+                    on[u] = rl < kTileM && row < a.rows && !(a.lower && col > row);
+                    cv[u] = (on[u] && a.mode != 0) ? a.C[(size_t)row * a.ldc + col] : 0.0;
+                }
+#pragma unroll
+                for (int u = 0; u < kBatch; ++u) {
+                    if (!on[u]) continue;
+                    const int rl = rb + kStep * u;
+                    const double v = tile[rl * kOutLd + cx];
+                    a.C[(size_t)(m0 + rl) * a.ldc + col] = a.mode == 0 ? v : (a.mode == 1 ? cv[u] - v : cv[u] + v);
                 }
             }
         }
@@ -326,47 +424,68 @@ constexpr int kNB = 64;
 
 // Factor the kb x kb diagonal block at (k, k) in place (lower) and write its
 // inverse, a lower-triangular 64 x 64 block (zero above the diagonal and
-// beyond kb), to Linv.
-__global__ void k_potrf_inv(double *__restrict__ A, int64_t n, int64_t k, int kb, int *__restrict__ info,
-                            double *__restrict__ Linv) {
-    __shared__ double L[kNB][kNB + 1];
-    __shared__ double X[kNB][kNB + 1];
+// beyond kb), to Linv.  256 threads; per column one thread takes the square
+// root and its reciprocal, the others scale and update with independent
+// FMAs.  The inverse is built right-looking (row k of X = L^-1 is final once
+// scaled; it is then eliminated from the rows below).
+constexpr int kPotrfThreads = 256;
+constexpr int kLd = kNB + 1;
+
+__global__ void __launch_bounds__(kPotrfThreads) k_potrf_inv(double *__restrict__ A, int64_t n, int64_t k, int kb,
+                                                             int *__restrict__ info, double *__restrict__ Linv) {
+    extern __shared__ double psm[];
+    double *L = psm;                 // [64][65]
+    double *X = psm + kNB * kLd;     // [64][65]
+    double *rd = X + kNB * kLd;      // [64] reciprocal diagonal
     const int t = threadIdx.x;
-    for (int r = 0; r < kNB; ++r) L[r][t] = (r < kb && t < kb) ? A[(size_t)(k + r) * n + k + t] : 0.0;
+    for (int e = t; e < kNB * kNB; e += kPotrfThreads) {
+        const int r = e >> 6, c = e & 63;
+        L[r * kLd + c] = (r < kb && c < kb) ? A[(size_t)(k + r) * n + k + c] : 0.0;
+        X[r * kLd + c] = (r == c) ? 1.0 : 0.0;
+    }
     __syncthreads();
+    const int ry = t >> 6, cx = t & 63;
     for (int c = 0; c < kb; ++c) {
         if (t == 0) {
-            double d = L[c][c];
+            double d = L[c * kLd + c];
             if (!(d > 0.0)) {
                 if (info) atomicExch(info, (int)(k + c + 1));
                 d = 1e-300;
             }
-            L[c][c] = sqrt(d);
+            const double lcc = sqrt(d);
+            L[c * kLd + c] = lcc;
+            rd[c] = 1.0 / lcc;
         }
         __syncthreads();
-        if (t > c && t < kb) L[t][c] /= L[c][c];
+        const double inv = rd[c];
+        for (int r = c + 1 + t; r < kb; r += kPotrfThreads) L[r * kLd + c] *= inv;
         __syncthreads();
-        if (t > c && t < kb) {
-            const double ltc = L[t][c];
-            for (int q = c + 1; q <= t; ++q) L[t][q] -= ltc * L[q][c];
+        const int q = c + 1 + cx;
+        if (q < kb) {
+            const double lqc = L[q * kLd + c];
+            for (int r = q + ((ry - (q - c - 1)) & 3); r < kb; r += 4) L[r * kLd + q] -= L[r * kLd + c] * lqc;
+        }
+        __syncthreads();  // the next pivot reads this update
+    }
+    for (int kk = 0; kk < kb; ++kk) {
+        const double inv = rd[kk];
+        if (t <= kk) X[kk * kLd + t] *= inv;
+        __syncthreads();
+        // rows i > kk, columns j <= kk:  X[i][j] -= L[i][kk] X[kk][j]
+        if (cx <= kk) {
+            const double xk = X[kk * kLd + cx];
+            for (int i = kk + 1 + ry; i < kb; i += 4) X[i * kLd + cx] -= L[i * kLd + kk] * xk;
         }
         __syncthreads();
     }
-    // column t of the inverse by forward substitution
-    for (int r = 0; r < kNB; ++r) X[r][t] = 0.0;
-    if (t < kb) {
-        X[t][t] = 1.0 / L[t][t];
-        for (int i = t + 1; i < kb; ++i) {
-            double acc = 0.0;
-            for (int q = t; q < i; ++q) acc += L[i][q] * X[q][t];
-            X[i][t] = -acc / L[i][i];
-        }
+    for (int e = t; e < kNB * kNB; e += kPotrfThreads) {
+        const int r = e >> 6, c = e & 63;
+        if (r < kb && c <= r) A[(size_t)(k + r) * n + k + c] = L[r * kLd + c];
+        Linv[(size_t)r * kNB + c] = (r < kb && c <= r) ? X[r * kLd + c] : 0.0;
     }
-    __syncthreads();
-    for (int r = 0; r < kb; ++r)
-        if (t <= r) A[(size_t)(k + r) * n + k + t] = L[r][t];
-    for (int r = 0; r < kNB; ++r) Linv[(size_t)r * kNB + t] = X[r][t];
 }
+
+constexpr size_t kPotrfSmem = (size_t)(2 * kNB * kLd + kNB) * sizeof(double);
 
 // y_k = Linv_k b_k (forward step of L y = b on block k).
 __global__ void k_trsv_inv_lower(const double *__restrict__ Linv, int64_t k, int kb, double *__restrict__ b) {
@@ -533,7 +652,7 @@ cudaError_t launch_ozaki_gemm(const __nv_bfloat16 *Asl, const int *expA, int64_t
     if (attr_err != cudaSuccess) return attr_err;
     OzArgs a{rows, cols, S, expA, expB, C, ldc, mode, lower ? 1 : 0, err};
     dim3 grid(nblk(cols, kTileN), nblk(rows, kTileM));
-    (k_ozaki_gemm<<<grid, 128, ozaki_smem_bytes(), st>>>(ma, mb, a), nk::note_launch());
+    (k_ozaki_gemm<<<grid, kOzThreads, ozaki_smem_bytes(), st>>>(ma, mb, a), nk::note_launch());
     return cudaGetLastError();
 }
 
@@ -572,12 +691,14 @@ TcWs carve_tc(void *ws, int64_t n) {
 cudaError_t launch_cholesky_tc(double *A, int64_t n, int *info, int *err, void *ws, cudaStream_t st) {
     TcWs w = carve_tc(ws, n);
     const int S = kMaxSlices;
+    cudaError_t ae = cudaFuncSetAttribute(k_potrf_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPotrfSmem);
+    if (ae != cudaSuccess) return ae;
     for (int64_t k = 0; k < n; k += kNB) {
         const int kb = (int)(n - k < kNB ? n - k : kNB);
         const int64_t rest = n - k - kb;
         double *Linv = w.Linv + (size_t)(k / kNB) * kNB * kNB;
         int slot = prof_begin(NK_PROF_CHOL_PANEL, st);
-        (k_potrf_inv<<<1, kNB, 0, st>>>(A, n, k, kb, info, Linv), nk::note_launch());
+        (k_potrf_inv<<<1, kPotrfThreads, kPotrfSmem, st>>>(A, n, k, kb, info, Linv), nk::note_launch());
         if (rest > 0) {
             double *panel = A + (size_t)(k + kb) * n + k;
             cudaError_t e = launch_slice_rows(Linv, kNB, kb, kb, S, w.Bsl, w.expB, st);
