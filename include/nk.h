@@ -327,7 +327,8 @@ nk_status nk_sr_step(nk_ctx *ctx, nk_rbm *rbm, const nk_ham *ham, nk_chains *cha
 #define NK_PROF_SWEEP 0       /* Metropolis sweeps: work = ratio terms (proposals x M) */
 #define NK_PROF_ELOC 1        /* local energies: work = ratio terms (connections x M) */
 #define NK_PROF_GRAM 2        /* sample-space Gram: work = flops */
-#define NK_PROF_CHOL_UPDATE 3 /* Cholesky trailing updates: work = flops */
+#define NK_PROF_CHOL_UPDATE 3 /* Cholesky trailing updates: work = flops (NK_F64: FP64
+                                 flops; NK_MIXED: BF16 tensor-core MMA flops executed) */
 #define NK_PROF_CHOL_PANEL 4  /* Cholesky diagonal blocks and panels: work = flops */
 #define NK_PROF_TRSV 5        /* triangular solves: work = flops */
 #define NK_PROF_JVP_VJP 6     /* Jacobian products: work = flops */

@@ -215,39 +215,54 @@ __global__ void k_slice_rows(const double *__restrict__ A, int64_t lda, int64_t 
     if (lane == 0) expo[r] = e;
 }
 
-// Value V 2^sc as an FP64 bit pattern built with integer operations (round
-// to nearest even); V is the exact 128-bit fixed-point recombination of the
-// slice products.
-__device__ __forceinline__ double fixed_to_double(__int128 V, int sc) {
-    if (V == 0) return 0.0;
-    const bool neg = V < 0;
-    const unsigned __int128 mag = neg ? (unsigned __int128)(-V) : (unsigned __int128)V;
-    const unsigned long long h = (unsigned long long)(mag >> 64), l = (unsigned long long)mag;
-    int p = h ? 127 - __clzll(h) : 63 - __clzll(l);  // index of the leading one
-    unsigned long long mant;
-    if (p <= 52) {
-        mant = l << (52 - p);
+// The value (hi 2^32 + lo) 2^sc as an FP64 bit pattern, rounded to nearest
+// even, built with 64-bit integer operations (|hi| < 2^43, |lo| < 2^52: the
+// exact fixed-point recombination of the slice products).  lo's upper half is
+// carried into hi first, so that the magnitude is Hm 2^32 + Lm with
+// 0 <= Lm < 2^32 and Hm < 2^44.
+__device__ __forceinline__ double fixed_to_double(long long hi, long long lo, int sc) {
+    long long H = hi + (lo >> 32);
+    unsigned long long Lw = (unsigned long long)lo & 0xFFFFFFFFULL;
+    const bool neg = H < 0;
+    unsigned long long Hm, Lm;
+    if (neg) {  // |V| = (-H) 2^32 - Lw
+        Hm = (unsigned long long)(-H) - (Lw ? 1ULL : 0ULL);
+        Lm = Lw ? (0x100000000ULL - Lw) : 0ULL;
     } else {
-        const int sh = p - 52;
-        const unsigned __int128 q = mag >> sh;
-        mant = (unsigned long long)q;
-        const unsigned __int128 rem = mag - (q << sh);
-        const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
-        if (rem > half || (rem == half && (mant & 1ULL))) {
-            ++mant;
-            if (mant == (1ULL << 53)) {
-                mant >>= 1;
-                ++p;
+        Hm = (unsigned long long)H;
+        Lm = Lw;
+    }
+    unsigned long long mant;
+    int p;  // position of the leading one of the magnitude
+    if (Hm == 0) {
+        if (Lm == 0) return 0.0;
+        p = 63 - __clzll((long long)Lm);
+        mant = Lm << (52 - p);
+    } else {
+        const int b = 64 - __clzll((long long)Hm);  // bit length of Hm, <= 44
+        p = b + 31;
+        if (b <= 21) {
+            mant = ((Hm << 32) | Lm) << (21 - b);  // exact, < 2^53
+        } else {
+            const int sr = b - 21;  // 1 .. 23 low bits of Lm to drop
+            mant = (Hm << (32 - sr)) | (Lm >> sr);
+            const unsigned long long rem = Lm & ((1ULL << sr) - 1ULL), half = 1ULL << (sr - 1);
+            if (rem > half || (rem == half && (mant & 1ULL))) {
+                ++mant;
+                if (mant == (1ULL << 53)) {
+                    mant >>= 1;
+                    ++p;
+                }
             }
         }
     }
     const int E = p + sc + 1023;
     if (E <= 0 || E >= 2047) {  // outside the normal range: FP64 fallback
-        const double d = (double)h * 18446744073709551616.0 + (double)l;
+        const double d = (double)Hm * 4294967296.0 + (double)Lm;
         return ldexp(neg ? -d : d, sc);
     }
-    const unsigned long long bits = (neg ? (1ULL << 63) : 0ULL) | ((unsigned long long)E << 52) |
-                                    (mant & 0xFFFFFFFFFFFFFULL);
+    const unsigned long long bits =
+        (neg ? (1ULL << 63) : 0ULL) | ((unsigned long long)E << 52) | (mant & 0xFFFFFFFFFFFFFULL);
     return __longlong_as_double((long long)bits);
 }
 
@@ -375,8 +390,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                 for (int j = 0; j < 16; ++j) {
                     const int64_t col = n0 + c0 + j;
                     const int fj = col < a.cols ? a.expB[col] : 0;
-                    const __int128 V = ((__int128)hi[j] << 32) + (__int128)lo[j];
-                    tile[rloc * kOutLd + c0 + j] = fixed_to_double(V, ei + fj - 64);
+                    tile[rloc * kOutLd + c0 + j] = fixed_to_double(hi[j], lo[j], ei + fj - 64);
                 }
             }
         }
@@ -601,12 +615,14 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-// 3-D map over slices [S][rows][64] BF16 with a box of one slice x box_rows rows.
-bool make_slice_map(CUtensorMap *map, const __nv_bfloat16 *slices, int64_t rows, int S, int box_rows) {
+// 3-D map over slices [S][rows][64] BF16 (consecutive slices stride_rows rows
+// apart) with a box of one slice x box_rows rows.
+bool make_slice_map(CUtensorMap *map, const __nv_bfloat16 *slices, int64_t rows, int S, int box_rows,
+                    int64_t stride_rows) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
     cuuint64_t dims[3] = {(cuuint64_t)kTileK, (cuuint64_t)rows, (cuuint64_t)S};
-    cuuint64_t strides[2] = {(cuuint64_t)kTileK * 2, (cuuint64_t)rows * kTileK * 2};
+    cuuint64_t strides[2] = {(cuuint64_t)kTileK * 2, (cuuint64_t)stride_rows * kTileK * 2};
     cuuint32_t box[3] = {(cuuint32_t)kTileK, (cuuint32_t)box_rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16 *>(slices), dims, strides,
@@ -638,14 +654,15 @@ cudaError_t launch_slice_rows(const double *A, int64_t lda, int64_t rows, int kc
 // R = A B^T (FP64-accurate to the slice count), applied to C by mode.
 // A and B are given by their slices (rows x 64, as written by
 // launch_slice_rows) and row exponents.
-cudaError_t launch_ozaki_gemm(const __nv_bfloat16 *Asl, const int *expA, int64_t rows,
-                              const __nv_bfloat16 *Bsl, const int *expB, int64_t cols, int S, double *C,
-                              int64_t ldc, int mode, bool lower, int *err, cudaStream_t st) {
+cudaError_t launch_ozaki_gemm_strided(const __nv_bfloat16 *Asl, const int *expA, int64_t rows, int64_t a_stride,
+                                      const __nv_bfloat16 *Bsl, const int *expB, int64_t cols, int64_t b_stride,
+                                      int S, double *C, int64_t ldc, int mode, bool lower, int *err,
+                                      cudaStream_t st) {
     if (rows <= 0 || cols <= 0) return cudaSuccess;
     if (S < 1 || S > kMaxSlices) return cudaErrorInvalidValue;
     if (rows > (1LL << 31) - kTileM || cols > (1LL << 31) - kTileN) return cudaErrorInvalidValue;
     CUtensorMap ma, mb;
-    if (!make_slice_map(&ma, Asl, rows, S, kTileM) || !make_slice_map(&mb, Bsl, cols, S, kTileN))
+    if (!make_slice_map(&ma, Asl, rows, S, kTileM, a_stride) || !make_slice_map(&mb, Bsl, cols, S, kTileN, b_stride))
         return cudaErrorInvalidValue;
     cudaError_t attr_err = cudaFuncSetAttribute(k_ozaki_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                 (int)ozaki_smem_bytes());
@@ -656,16 +673,34 @@ cudaError_t launch_ozaki_gemm(const __nv_bfloat16 *Asl, const int *expA, int64_t
     return cudaGetLastError();
 }
 
+// BF16 MMA flops a launch executes: active tiles x S(S+1)/2 slice products x
+// 2 x 128 x 64 x 64.
+double ozaki_mma_flops(int64_t rows, int64_t cols, int S, bool lower) {
+    const int64_t tm = (rows + kTileM - 1) / kTileM, tn = (cols + kTileN - 1) / kTileN;
+    int64_t tiles = 0;
+    for (int64_t i = 0; i < tm; ++i) {
+        const int64_t m0 = i * kTileM;
+        tiles += lower ? (m0 + kTileM - 1) / kTileN + 1 < tn ? (m0 + kTileM - 1) / kTileN + 1 : tn : tn;
+    }
+    return (double)tiles * (S * (S + 1) / 2) * 2.0 * kTileM * kTileN * kTileK;
+}
+
+cudaError_t launch_ozaki_gemm(const __nv_bfloat16 *Asl, const int *expA, int64_t rows,
+                              const __nv_bfloat16 *Bsl, const int *expB, int64_t cols, int S, double *C,
+                              int64_t ldc, int mode, bool lower, int *err, cudaStream_t st) {
+    return launch_ozaki_gemm_strided(Asl, expA, rows, rows, Bsl, expB, cols, cols, S, C, ldc, mode, lower, err, st);
+}
+
 size_t tc_chol_ws_bytes(int64_t n) {
     const int64_t nb = (n + kNB - 1) / kNB;
-    return slice_elems(n, kMaxSlices) * 2 + slice_elems(kNB, kMaxSlices) * 2 + (size_t)(n + kNB) * 4 +
-           (size_t)nb * kNB * kNB * 8 + 4 * 256;
+    return 2 * slice_elems(n, kMaxSlices) * 2 + slice_elems(kNB, kMaxSlices) * 2 + (size_t)(2 * n + kNB) * 4 +
+           (size_t)nb * kNB * kNB * 8 + 8 * 256;
 }
 
 namespace {
 struct TcWs {
-    __nv_bfloat16 *Asl, *Bsl;
-    int *expA, *expB;
+    __nv_bfloat16 *Asl, *Bsl, *Asl2;
+    int *expA, *expB, *expA2;
     double *Linv;
 };
 TcWs carve_tc(void *ws, int64_t n) {
@@ -681,41 +716,94 @@ TcWs carve_tc(void *ws, int64_t n) {
     w.expA = reinterpret_cast<int *>(take((size_t)n * 4));
     w.expB = reinterpret_cast<int *>(take((size_t)kNB * 4));
     w.Linv = reinterpret_cast<double *>(take((size_t)((n + kNB - 1) / kNB) * kNB * kNB * 8));
+    w.Asl2 = reinterpret_cast<__nv_bfloat16 *>(take(slice_elems(n, kMaxSlices) * 2));
+    w.expA2 = reinterpret_cast<int *>(take((size_t)n * 4));
     return w;
 }
 }  // namespace
 
 // Blocked right-looking Cholesky with tensor-core (Ozaki, 7 slices) panel
-// solves and trailing updates.  The inverted diagonal blocks stay in the
-// workspace for launch_cholesky_solve_tc.
-cudaError_t launch_cholesky_tc(double *A, int64_t n, int *info, int *err, void *ws, cudaStream_t st) {
+// solves and trailing updates, and a look-ahead of one panel: after panel k
+// the main stream first updates only block column k + 1 ("narrow" update),
+// then the side stream factors panel k + 1 (diagonal block, its inverse, the
+// panel product and its slices) while the main stream applies panel k to the
+// rest of the trailing matrix ("wide" update).  Panel slices alternate
+// between two buffers.  The inverted diagonal blocks stay in the workspace
+// for launch_cholesky_solve_tc.
+namespace {
+
+// Factor panel k (columns k0 .. k0 + kb - 1) whose block column is up to date:
+// diagonal block + inverse, L_panel = A_panel L_kk^-T, slices of L_panel.
+cudaError_t panel_step(double *A, int64_t n, int64_t k0, int *info, int *err, TcWs &w, __nv_bfloat16 *Lsl,
+                       int *Lexp, cudaStream_t st) {
+    const int S = kMaxSlices;
+    const int kb = (int)(n - k0 < kNB ? n - k0 : kNB);
+    const int64_t rest = n - k0 - kb;
+    double *Linv = w.Linv + (size_t)(k0 / kNB) * kNB * kNB;
+    const int slot = prof_begin(NK_PROF_CHOL_PANEL, st);
+    (k_potrf_inv<<<1, kPotrfThreads, kPotrfSmem, st>>>(A, n, k0, kb, info, Linv), nk::note_launch());
+    cudaError_t e = cudaSuccess;
+    if (rest > 0) {
+        double *panel = A + (size_t)(k0 + kb) * n + k0;
+        e = launch_slice_rows(Linv, kNB, kb, kb, S, w.Bsl, w.expB, st);
+        if (e == cudaSuccess) e = launch_slice_rows(panel, n, rest, kb, S, Lsl, Lexp, st);
+        if (e == cudaSuccess)
+            e = launch_ozaki_gemm(Lsl, Lexp, rest, w.Bsl, w.expB, kb, S, panel, n, 0, false, err, st);
+        if (e == cudaSuccess) e = launch_slice_rows(panel, n, rest, kb, S, Lsl, Lexp, st);
+    }
+    prof_end(slot, st, (double)kb * kb * kb / 3.0 + 2.0 * (double)rest * kb * kb);
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_cholesky_tc(double *A, int64_t n, int *info, int *err, void *ws, cudaStream_t st,
+                               cudaStream_t side, cudaEvent_t ev_narrow, cudaEvent_t ev_panel) {
     TcWs w = carve_tc(ws, n);
     const int S = kMaxSlices;
-    cudaError_t ae = cudaFuncSetAttribute(k_potrf_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPotrfSmem);
-    if (ae != cudaSuccess) return ae;
-    for (int64_t k = 0; k < n; k += kNB) {
-        const int kb = (int)(n - k < kNB ? n - k : kNB);
-        const int64_t rest = n - k - kb;
-        double *Linv = w.Linv + (size_t)(k / kNB) * kNB * kNB;
-        int slot = prof_begin(NK_PROF_CHOL_PANEL, st);
-        (k_potrf_inv<<<1, kPotrfThreads, kPotrfSmem, st>>>(A, n, k, kb, info, Linv), nk::note_launch());
-        if (rest > 0) {
-            double *panel = A + (size_t)(k + kb) * n + k;
-            cudaError_t e = launch_slice_rows(Linv, kNB, kb, kb, S, w.Bsl, w.expB, st);
-            if (e == cudaSuccess) e = launch_slice_rows(panel, n, rest, kb, S, w.Asl, w.expA, st);
-            if (e == cudaSuccess)
-                e = launch_ozaki_gemm(w.Asl, w.expA, rest, w.Bsl, w.expB, kb, S, panel, n, 0, false, err, st);
-            prof_end(slot, st, (double)kb * kb * kb / 3.0 + 2.0 * (double)rest * kb * kb);
+    cudaError_t e = cudaFuncSetAttribute(k_potrf_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPotrfSmem);
+    if (e != cudaSuccess) return e;
+    __nv_bfloat16 *buf[2] = {w.Asl, w.Asl2};
+    int *bexp[2] = {w.expA, w.expA2};
+    const int64_t nb = (n + kNB - 1) / kNB;
+    e = panel_step(A, n, 0, info, err, w, buf[0], bexp[0], st);
+    if (e != cudaSuccess) return e;
+    for (int64_t k = 0; k + 1 < nb; ++k) {
+        const int64_t k0 = k * kNB;
+        const int64_t rest = n - k0 - kNB;         // rows of panel k below its diagonal block
+        const int kb1 = (int)(rest < kNB ? rest : kNB);  // width of block column k + 1
+        __nv_bfloat16 *Lk = buf[k & 1];
+        int *Le = bexp[k & 1];
+        double *C1 = A + (size_t)(k0 + kNB) * n + (k0 + kNB);
+        int slot = prof_begin(NK_PROF_CHOL_UPDATE, st);
+        // narrow: block column k + 1 (all rows below panel k)
+        e = launch_ozaki_gemm_strided(Lk, Le, rest, rest, Lk, Le, kb1, rest, S, C1, n, 1, true, err, st);
+        prof_end(slot, st, ozaki_mma_flops(rest, kb1, S, true));
+        if (e != cudaSuccess) return e;
+        if (side) {
+            e = cudaEventRecord(ev_narrow, st);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(side, ev_narrow, 0);
             if (e != cudaSuccess) return e;
+        }
+        cudaStream_t ps = side ? side : st;
+        e = panel_step(A, n, k0 + kNB, info, err, w, buf[(k + 1) & 1], bexp[(k + 1) & 1], ps);
+        if (e != cudaSuccess) return e;
+        if (side) {
+            e = cudaEventRecord(ev_panel, side);
+            if (e != cudaSuccess) return e;
+        }
+        // wide: everything right of block column k + 1
+        const int64_t rest2 = rest - kb1;
+        if (rest2 > 0) {
             slot = prof_begin(NK_PROF_CHOL_UPDATE, st);
-            e = launch_slice_rows(panel, n, rest, kb, S, w.Asl, w.expA, st);
-            if (e == cudaSuccess)
-                e = launch_ozaki_gemm(w.Asl, w.expA, rest, w.Asl, w.expA, rest, S,
-                                      A + (size_t)(k + kb) * n + k + kb, n, 1, true, err, st);
-            prof_end(slot, st, (double)kb * rest * (double)(rest + 1));
+            e = launch_ozaki_gemm_strided(Lk + (size_t)kb1 * kTileK, Le + kb1, rest2, rest, Lk + (size_t)kb1 * kTileK,
+                                          Le + kb1, rest2, rest, S, C1 + (size_t)kb1 * n + kb1, n, 1, true, err, st);
+            prof_end(slot, st, ozaki_mma_flops(rest2, rest2, S, true));
             if (e != cudaSuccess) return e;
-        } else {
-            prof_end(slot, st, (double)kb * kb * kb / 3.0);
+        }
+        if (side) {
+            e = cudaStreamWaitEvent(st, ev_panel, 0);
+            if (e != cudaSuccess) return e;
         }
     }
     return cudaGetLastError();

@@ -18,6 +18,8 @@ struct nk_ctx {
     size_t ws_size;
     int *host_flags;  // pinned: [0] done, [1] iterations
     double *host_vals;  // pinned
+    cudaStream_t side;  // high-priority stream for the Cholesky look-ahead
+    cudaEvent_t ev[2];
 };
 
 namespace {
@@ -313,7 +315,8 @@ nk_status run_solve(nk_ctx *ctx, int N, int M, int64_t Ns, const int8_t *s, cons
         NK_CU(nk::launch_syrk_t(w.dJ, Ns, Np, 1.0 / (double)Ns, eps, w.S, st), "chol syrk");
         NK_CU(cudaMemsetAsync(w.info, 0, 2 * sizeof(int), st), "chol");
         if (tc)
-            NK_CU(nk::launch_cholesky_tc(w.S, Np, w.info, w.info + 1, w.tc, st), "chol factor");
+            NK_CU(nk::launch_cholesky_tc(w.S, Np, w.info, w.info + 1, w.tc, st, ctx->side, ctx->ev[0], ctx->ev[1]),
+                  "chol factor");
         else
             NK_CU(nk::launch_cholesky(w.S, Np, w.info, st), "chol factor");
         NK_CU(nk::launch_axpby(Np, 1.0, F, 0.0, delta, st), "chol");
@@ -329,7 +332,8 @@ nk_status run_solve(nk_ctx *ctx, int N, int M, int64_t Ns, const int8_t *s, cons
     if (tc) {
         NK_CU(nk::launch_gram_tc(N, M, Ns, s, T, 7, w.K, w.info + 1, w.tc, st), "ss gram");
         NK_CU(nk::launch_center_gram(Ns, w.K, w.rowmean, eps, st), "ss gram");
-        NK_CU(nk::launch_cholesky_tc(w.K, Ns, w.info, w.info + 1, w.tc, st), "ss factor");
+        NK_CU(nk::launch_cholesky_tc(w.K, Ns, w.info, w.info + 1, w.tc, st, ctx->side, ctx->ev[0], ctx->ev[1]),
+              "ss factor");
     } else {
         NK_CU(nk::launch_gram_samplespace(N, M, Ns, s, T, eps, w.K, w.rowmean, st), "ss gram");
         NK_CU(nk::launch_cholesky(w.K, Ns, w.info, st), "ss factor");
@@ -387,10 +391,18 @@ nk_status nk_ctx_create(int32_t device, nk_ctx **out) {
     c->device = device;
     e = cudaMallocHost(&c->host_flags, 8 * sizeof(int));
     if (e == cudaSuccess) e = cudaMallocHost(&c->host_vals, 8 * sizeof(double));
+    int lo_prio = 0, hi_prio = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, hi_prio);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev[0], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev[1], cudaEventDisableTiming);
     if (e != cudaSuccess) {
         if (c->host_flags) cudaFreeHost(c->host_flags);
+        if (c->host_vals) cudaFreeHost(c->host_vals);
+        if (c->side) cudaStreamDestroy(c->side);
+        if (c->ev[0]) cudaEventDestroy(c->ev[0]);
         delete c;
-        return cuda_fail(e, "cudaMallocHost");
+        return cuda_fail(e, "context resources");
     }
     *out = c;
     return NK_OK;
@@ -402,6 +414,9 @@ nk_status nk_ctx_destroy(nk_ctx *ctx) {
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->host_flags) cudaFreeHost(ctx->host_flags);
     if (ctx->host_vals) cudaFreeHost(ctx->host_vals);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
+    if (ctx->ev[0]) cudaEventDestroy(ctx->ev[0]);
+    if (ctx->ev[1]) cudaEventDestroy(ctx->ev[1]);
     delete ctx;
     return NK_OK;
 }

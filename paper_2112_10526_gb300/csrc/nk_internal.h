@@ -129,7 +129,10 @@ cudaError_t launch_ozaki_gemm(const __nv_bfloat16 *Asl, const int *expA, int64_t
                               const __nv_bfloat16 *Bsl, const int *expB, int64_t cols, int S, double *C,
                               int64_t ldc, int mode, bool lower, int *err, cudaStream_t st);
 size_t tc_chol_ws_bytes(int64_t n);
-cudaError_t launch_cholesky_tc(double *A, int64_t n, int *info, int *err, void *ws, cudaStream_t st);
+// side / events: a second stream for the panel look-ahead (null: one stream).
+cudaError_t launch_cholesky_tc(double *A, int64_t n, int *info, int *err, void *ws, cudaStream_t st,
+                               cudaStream_t side = nullptr, cudaEvent_t ev_narrow = nullptr,
+                               cudaEvent_t ev_panel = nullptr);
 cudaError_t launch_cholesky_solve_tc(const double *L, int64_t n, const void *ws, double *b,
                                      cudaStream_t st);
 cudaError_t launch_gram_tc(int N, int M, int64_t Ns, const int8_t *s, const double *T, int S, double *K,
