@@ -29,9 +29,13 @@
  *     thread-safe: use one per host thread.  Calls on one context must not
  *     overlap on different streams (they share the workspace).
  *   - precision: NK_F64 computes everything in FP64 on CUDA cores.
- *     NK_MIXED keeps the Metropolis chains and local-energy ratios in FP32
- *     (hidden activations rebuilt from scratch in FP64 at every sweep) and
- *     keeps FP64 for sample means, centring, the SR solve and the update.
+ *     NK_MIXED keeps the Metropolis chains and local-energy ratios in FP32,
+ *     rebuilds the hidden activations from scratch at every sweep with an
+ *     FP64-exact tensor-core product (configurations x W cut into 7 BF16
+ *     integer slices, FP32 accumulation), runs the Jacobian products on the
+ *     tensor cores (4 slices in CG matvecs, 7 where the sample-space solve
+ *     needs FP64-level products) and keeps FP64 for sample means, centring,
+ *     the SR factorisation (tensor-core products at FP64 level) and update.
  */
 #ifndef NK_H
 #define NK_H
@@ -96,6 +100,13 @@ nk_status nk_ctx_destroy(nk_ctx *ctx);
 const char *nk_last_error(void);
 /* Library version (major*10000 + minor*100 + patch). */
 int32_t nk_version(void);
+/*
+ * Sticky status of the context's tensor-core products (NK_MIXED paths):
+ * waits for the context's work on `stream` and returns in *code 0, or the
+ * code of the first tensor-core wait that timed out since the last call
+ * (1-5; the results of that call are invalid).  Resets the word.
+ */
+nk_status nk_ctx_error(nk_ctx *ctx, int32_t *code /* host */, void *stream);
 
 /*
  * ln psi(s) for a batch of configurations (Eq. eq:mapping: the model maps

@@ -104,6 +104,24 @@ __global__ void k_logpsi(int N, int M, const double *__restrict__ a, const doubl
     if (lane == 0) out[k] = part;
 }
 
+// ln psi from a precomputed theta [B][M]: one warp per configuration.
+__global__ void k_logpsi_theta(int N, int M, const double *__restrict__ a, const double *__restrict__ theta,
+                               const int8_t *__restrict__ s, int64_t B, double *__restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (k >= B) return;
+    double part = 0.0;
+    for (int i = lane; i < N; i += 32) part += a[i] * (double)s[(size_t)k * N + i];
+    for (int j = lane; j < M; j += 32) part += lncosh(theta[(size_t)k * M + j]);
+    part = warp_sum(part);
+    if (lane == 0) out[k] = part;
+}
+
+__global__ void k_tanh_inplace(int64_t n, double *__restrict__ x) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] = tanh(x[i]);
+}
+
 // ------------------------------------------------------------- chain init ---
 
 __global__ void k_chain_init(int N, int C, int rule, unsigned long long seed, unsigned stream_id,
@@ -160,11 +178,17 @@ __global__ void __launch_bounds__(128) k_sweep(SweepK<R> P) {
     unsigned long long acc = 0;
     const int n_sweeps = A.n_discard + A.n_samples;
     for (int w = 0; w < n_sweeps; ++w) {
-        // From-scratch FP64 rebuild of theta = b + W s, t = tanh theta, ln psi.
+        // From-scratch FP64 theta = b + W s (rebuilt here, or given by the
+        // tensor-core product), t = tanh theta, ln psi.
         double lp = 0.0;
         for (int j = lane; j < M; j += 32) {
-            double th = T.b[j];
-            for (int i = 0; i < N; ++i) th = fma(T.Wt[(size_t)i * M + j], (double)sv[i], th);
+            double th;
+            if (A.theta_in) {
+                th = A.theta_in[(size_t)c * M + j];
+            } else {
+                th = T.b[j];
+                for (int i = 0; i < N; ++i) th = fma(T.Wt[(size_t)i * M + j], (double)sv[i], th);
+            }
             t[j] = (R)tanh(th);
             lp += lncosh(th);
         }
@@ -182,7 +206,7 @@ __global__ void __launch_bounds__(128) k_sweep(SweepK<R> P) {
             }
             const unsigned long long u0 = __shfl_sync(kFull, y0, q & 31);
             const unsigned long long u1 = __shfl_sync(kFull, y1, q & 31);
-            const size_t slot = ((size_t)c * n_sweeps + w) * N + q;
+            const size_t slot = ((size_t)c * A.dec_stride + A.dec_offset + w) * N + q;
             int i, k = -1;
             const R *tau;
             R K;
@@ -236,7 +260,7 @@ __global__ void __launch_bounds__(128) k_sweep(SweepK<R> P) {
             __syncwarp();
         }
         if (w >= A.n_discard) {
-            const size_t row = (size_t)c * A.n_samples + (w - A.n_discard);
+            const size_t row = (size_t)c * A.out_stride + A.out_offset + (w - A.n_discard);
             for (int i = lane; i < N; i += 32) A.samples[row * N + i] = sv[i];
             if (lane == 0 && A.logpsi) A.logpsi[row] = lp;
         }
@@ -275,8 +299,13 @@ __global__ void __launch_bounds__(128) k_eloc(ElocK<R> P) {
     for (int i = lane; i < N; i += 32) sv[i] = A.s[(size_t)k * N + i];
     __syncwarp();
     for (int j = lane; j < M; j += 32) {
-        double th = T.b[j];
-        for (int i = 0; i < N; ++i) th = fma(T.Wt[(size_t)i * M + j], (double)sv[i], th);
+        double th;
+        if (A.theta_in) {
+            th = A.theta_in[(size_t)k * M + j];
+        } else {
+            th = T.b[j];
+            for (int i = 0; i < N; ++i) th = fma(T.Wt[(size_t)i * M + j], (double)sv[i], th);
+        }
         const double tj = tanh(th);
         t[j] = (R)tj;
         if (A.t_out) A.t_out[(size_t)k * M + j] = tj;
@@ -429,6 +458,19 @@ cudaError_t launch_logpsi(int N, int M, const double *a, const double *b, const 
     return cudaGetLastError();
 }
 
+cudaError_t launch_logpsi_theta(int N, int M, const double *a, const double *theta, const int8_t *s, int64_t B,
+                                double *out, cudaStream_t st) {
+    if (B <= 0) return cudaSuccess;
+    (k_logpsi_theta<<<(unsigned)((B + 7) / 8), 256, 0, st>>>(N, M, a, theta, s, B, out), nk::note_launch());
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tanh_inplace(int64_t n, double *x, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    (k_tanh_inplace<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, x), nk::note_launch());
+    return cudaGetLastError();
+}
+
 cudaError_t launch_chain_init(int N, int C, int rule, uint64_t seed, uint32_t stream_id,
                               int8_t *s, cudaStream_t st) {
     if (C <= 0) return cudaSuccess;
@@ -442,6 +484,14 @@ cudaError_t launch_sweep(const Tables<R> &t, const SweepArgs &a, cudaStream_t st
     SweepK<R> P;
     P.t = t;
     P.a = a;
+    if (P.a.out_stride <= 0) {
+        P.a.out_stride = a.n_samples;
+        P.a.out_offset = 0;
+    }
+    if (P.a.dec_stride <= 0) {
+        P.a.dec_stride = a.n_discard + a.n_samples;
+        P.a.dec_offset = 0;
+    }
     P.t_bytes = align16<R>(t.M * (int)sizeof(R));
     P.warp_bytes = P.t_bytes + align16<R>(t.N);
     int wpb = 4;

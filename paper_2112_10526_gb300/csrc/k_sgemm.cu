@@ -1,0 +1,548 @@
+// Tensor-core products with the spin configurations as one operand.
+//
+// The three dense contractions of the RBM path all multiply the +-1
+// configuration matrix by a real matrix (NetKet 3, Sec. 3.2 model
+// evaluation; App. B.1 Jacobian products):
+//   theta = S W^T + b           (batched hidden activations, [Ns][M])
+//   J v   via U = S' V'^T       (S' = [S, 1], V' = [[V_W, v_b], [v_a, 0]])
+//   J^T g via P^T = S'^T (T'o g) (T' = [T, 1])
+// +-1 and 1 are exact in BF16.  The real operand B is cut, row by row with one
+// power-of-two exponent per row, into SB slices of 8-bit integers (as in
+// k_tc.cu).  Every slice level t then needs one MMA chain,
+//   D_t[m][n] = sum_k a_mk beta_t,nk,
+// whose FP32 accumulation is exact: |D_t| <= K 255 < 2^24 for K <= 65792.
+// The epilogue recombines sum_t D_t 2^{-8t} 2^{f_n} in integers and writes
+// FP64.  With SB = 7 the products are exact up to the 2^-56 truncation of B
+// (FP64-level: the batched theta rebuild); with SB = 3 up to 2^-24 (the
+// NK_MIXED Jacobian products).
+//
+// Kernel: 128 x 64 output tile per CTA, K in chunks of 64 through a
+// 3-stage TMA / mbarrier ring (thread 0 produces, thread 32 issues
+// tcgen05.mma M=128 N=64 K=16 into SB TMEM accumulators), then all four warps
+// drain TMEM through the same integer assembly and a staged, coalesced
+// store.  Every wait is bounded by the global timer.
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "nk_common.cuh"
+#include "nk_internal.h"
+#include "tc_ptx.cuh"
+
+namespace nk {
+
+namespace {
+
+constexpr int kBM = 128, kBN = 64, kBK = 64;
+constexpr int kStages = 3;
+constexpr int kMaxSB = 7;
+constexpr int kSgThreads = 128;
+constexpr int kAB = kBM * kBK * 2;             // A tile, bytes
+constexpr int kBB = kBN * kBK * 2;             // one B slice tile, bytes
+constexpr int kStageBytes = kAB + kMaxSB * kBB;  // 72 KB
+constexpr int kSgOutLd = kBN + 1;
+
+struct SgArgs {
+    int64_t rows, cols;
+    int kchunks, SB;
+    const int *expB;      // [cols]
+    double *C;
+    int64_t ldc;
+    int mode;             // 0: C = R (+ bias), 1: C -= R, 2: C += R
+    const double *bias;   // [cols] or null
+    int *err;
+};
+
+__global__ void __launch_bounds__(kSgThreads, 1)
+    k_sgemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, SgArgs a) {
+    extern __shared__ unsigned char smem_raw[];
+    const uint32_t base = smem_u32(smem_raw);
+    unsigned char *ops = smem_raw + ((1024 - (base & 1023)) & 1023);
+    uint64_t *full = reinterpret_cast<uint64_t *>(ops + (size_t)kStages * kStageBytes);
+    uint64_t *empty = full + kStages;
+    uint64_t *done = empty + kStages;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
+    int *abort_flag = reinterpret_cast<int *>(tslot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t m0 = (int64_t)blockIdx.y * kBM, n0 = (int64_t)blockIdx.x * kBN;
+    const int SB = a.SB, KC = a.kchunks;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(done, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc(tslot, 512);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (threadIdx.x == 0) {
+        // TMA producer
+        const uint32_t tx = (uint32_t)(kAB + SB * kBB);
+        for (int kc = 0; kc < KC; ++kc) {
+            const int s = kc % kStages;
+            if (kc >= kStages && !mbar_wait(&empty[s], (uint32_t)(((kc / kStages) - 1) & 1))) {
+                *abort_flag = 1;
+                atomicExch(a.err, 3);
+                break;
+            }
+            unsigned char *sp = ops + (size_t)s * kStageBytes;
+            mbar_expect_tx(&full[s], tx);
+            tma_load_2d(sp, &mapA, &full[s], kc * kBK, (int)m0);
+            for (int t = 0; t < SB; ++t) tma_load_3d(sp + kAB + t * kBB, &mapB, &full[s], kc * kBK, (int)n0, t);
+        }
+    } else if (threadIdx.x == 32) {
+        // MMA issuer
+        const uint32_t idesc = idesc_bf16(kBM, kBN);
+        bool ok = true;
+        for (int kc = 0; kc < KC; ++kc) {
+            const int s = kc % kStages;
+            if (!mbar_wait(&full[s], (uint32_t)((kc / kStages) & 1))) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            unsigned char *sp = ops + (size_t)s * kStageBytes;
+            const uint64_t da = sw128_desc(sp);
+            for (int t = 0; t < SB; ++t) {
+                const uint64_t db = sw128_desc(sp + kAB + t * kBB);
+#pragma unroll
+                for (int kk = 0; kk < kBK / 16; ++kk)
+                    umma_bf16(tmem + (uint32_t)(t * kBN), da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
+                              (kc > 0 || kk > 0) ? 1u : 0u);
+            }
+            umma_commit(&empty[s]);
+        }
+        if (!ok) {
+            *abort_flag = 1;
+            atomicExch(a.err, 4);
+        }
+        umma_commit(done);
+    }
+    __syncthreads();
+    double *tile = reinterpret_cast<double *>(ops);
+    if (!*abort_flag) {
+        int ok = 1;
+        if (lane == 0) ok = mbar_wait(done, 0) ? 1 : 0;
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) {
+            if (lane == 0) {
+                atomicExch(a.err, 5);
+                *abort_flag = 2;
+            }
+        } else {
+            tc_fence_after();
+            const int rloc = warp * 32 + lane;
+            const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+            for (int c0 = 0; c0 < kBN; c0 += 16) {
+                // V = sum_t D_t 2^(8 (7 - t)) = hi 2^32 + lo
+                long long hi[16], lo[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) hi[j] = lo[j] = 0;
+                for (int t = 1; t <= SB; ++t) {
+                    uint32_t r[16];
+                    tmem_ld16(lane_base + (uint32_t)((t - 1) * kBN + c0), r);
+                    tmem_wait_ld();
+                    if (t <= 3) {
+                        const int sh = 8 * (3 - t);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) hi[j] += (long long)__float2int_rn(__uint_as_float(r[j])) << sh;
+                    } else {
+                        const int sh = 8 * (7 - t);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) lo[j] += (long long)__float2int_rn(__uint_as_float(r[j])) << sh;
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int64_t col = n0 + c0 + j;
+                    const int fn = col < a.cols ? a.expB[col] : 0;
+                    tile[rloc * kSgOutLd + c0 + j] = fixed_to_double(hi[j], lo[j], fn - 56);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (!*abort_flag) {
+        const int cx = threadIdx.x & 63, ry = threadIdx.x >> 6;
+        const int64_t col = n0 + cx;
+        constexpr int kStep = kSgThreads / 64, kBatch = 8;
+        if (col < a.cols) {
+            const double bcol = (a.bias && a.mode == 0) ? a.bias[col] : 0.0;
+            for (int rb = ry; rb < kBM; rb += kStep * kBatch) {
+                double cv[kBatch];
+                bool on[kBatch];
+#pragma unroll
+                for (int u = 0; u < kBatch; ++u) {
+                    const int rl = rb + kStep * u;
+                    on[u] = rl < kBM && m0 + rl < a.rows;
+                    cv[u] = (on[u] && a.mode != 0) ? a.C[(size_t)(m0 + rl) * a.ldc + col] : 0.0;
+                }
+#pragma unroll
+                for (int u = 0; u < kBatch; ++u) {
+                    if (!on[u]) continue;
+                    const int rl = rb + kStep * u;
+                    const double v = tile[rl * kSgOutLd + cx];
+                    a.C[(size_t)(m0 + rl) * a.ldc + col] =
+                        a.mode == 0 ? v + bcol : (a.mode == 1 ? cv[u] - v : cv[u] + v);
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+}
+
+size_t sgemm_smem_bytes() {
+    return 1024 + (size_t)kStages * kStageBytes + (2 * kStages + 1) * sizeof(uint64_t) + 16;
+}
+
+// ------------------------------------------------------- operand staging ---
+
+// S [B][N] int8 -> BF16 [B][ld]; column N holds 1.0 when augment, the rest of
+// the padding 0.
+__global__ void k_pm1_rows(const int8_t *__restrict__ s, int64_t B, int N, int augment, int64_t ld,
+                           __nv_bfloat16 *__restrict__ out) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= B * ld) return;
+    const int64_t k = idx / ld;
+    const int i = (int)(idx % ld);
+    float v = 0.f;
+    if (i < N)
+        v = (float)s[(size_t)k * N + i];
+    else if (augment && i == N)
+        v = 1.f;
+    out[idx] = __float2bfloat16_rn(v);
+}
+
+// S^T with a row of ones: out [N+1][ld] (row i, column k) = s_ki (i < N) or 1.
+__global__ void k_pm1_cols(const int8_t *__restrict__ s, int64_t Ns, int N, int64_t ld,
+                           __nv_bfloat16 *__restrict__ out) {
+    __shared__ int8_t tile[32][33];
+    const int64_t k0 = (int64_t)blockIdx.x * 32;
+    const int i0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int64_t k = k0 + r;
+        const int i = i0 + threadIdx.x;
+        tile[r][threadIdx.x] = (k < Ns && i < N) ? s[(size_t)k * N + i] : (int8_t)0;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int i = i0 + r;
+        const int64_t k = k0 + threadIdx.x;
+        if (i > N || k >= ld) continue;
+        float v = 0.f;
+        if (k < Ns) v = i < N ? (float)tile[threadIdx.x][r] : 1.f;
+        out[(size_t)i * ld + k] = __float2bfloat16_rn(v);
+    }
+}
+
+// Largest binary exponent of |x| (frexp convention, |x| < 2^e); -100000 for 0.
+__device__ __forceinline__ int exp_of(double x) {
+    int b;
+    unsigned long long m;
+    bool n;
+    split_bits(x, b, m, n);
+    return m ? b - 1022 : -100000;
+}
+
+// Slice one value with row exponent e into SB bytes (sign applied).
+__device__ __forceinline__ void slice_value(double x, int e, int SB, __nv_bfloat16 *out, int64_t plane) {
+    int b;
+    unsigned long long m;
+    bool neg;
+    split_bits(x, b, m, neg);
+    unsigned long long y = 0;
+    if (m) {
+        const int sh = b - 1075 + 8 * SB - e;
+        y = sh >= 0 ? (m << sh) : (sh <= -64 ? 0ULL : m >> (-sh));
+    }
+    for (int t = 0; t < SB; ++t) {
+        const int d = (int)((y >> (8 * (SB - 1 - t))) & 0xFFULL);
+        out[(size_t)t * plane] = __int2bfloat16_rn(neg ? -d : d);
+    }
+}
+
+// Rows of a row-major FP64 matrix (row r, column k: X[r * ldx + k] for k < K;
+// with augment, column K holds aug[r] and the operand has K + 1 columns) ->
+// SB slices [SB][rows][ld] with one exponent per row.  One block per row.
+__global__ void k_slice_long_rows(const double *__restrict__ X, int64_t ldx, int64_t rows, int64_t K,
+                                  const double *__restrict__ aug, int SB, int64_t ld,
+                                  __nv_bfloat16 *__restrict__ out, int *__restrict__ expo) {
+    const int64_t r = blockIdx.x;
+    if (r >= rows) return;
+    const int64_t Ke = aug ? K + 1 : K;
+    auto val = [&](int64_t k) -> double { return k < K ? X[(size_t)r * ldx + k] : aug[r]; };
+    int ex = -100000;
+    for (int64_t k = threadIdx.x; k < Ke; k += blockDim.x) ex = max(ex, exp_of(val(k)));
+    __shared__ int red[32];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) ex = max(ex, __shfl_xor_sync(0xffffffffu, ex, off));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ex;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : -100000;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, off));
+        if (threadIdx.x == 0) red[0] = v;
+    }
+    __syncthreads();
+    const int e = red[0] == -100000 ? 0 : red[0];
+    const int64_t plane = rows * ld;
+    for (int64_t k = threadIdx.x; k < ld; k += blockDim.x) {
+        const double x = k < Ke ? val(k) : 0.0;
+        slice_value(x, e, SB, out + (size_t)r * ld + k, plane);
+    }
+    if (threadIdx.x == 0) expo[r] = e;
+}
+
+__global__ void k_fill_int(int64_t n, int v, int *__restrict__ x) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] = v;
+}
+
+// Exponent of every row j <= M of (T' o g)^T: max over samples k of
+// |t'_kj g'_k|, t'_kM = 1, g'_k = scale (g_k - shift).  Blocks of 32 rows x
+// 256 samples, combined with atomicMax (-100000 marks an all-zero row).
+__global__ void k_tg_colexp(const double *__restrict__ T, const double *__restrict__ g, double scale,
+                            const double *__restrict__ shift, int64_t Ns, int M, int *__restrict__ expo) {
+    const int j = blockIdx.x * 32 + threadIdx.x;
+    const int64_t k0 = (int64_t)blockIdx.y * 256;
+    const double sh = shift ? *shift : 0.0;
+    int ex = -100000;
+    if (j <= M) {
+        for (int64_t k = k0 + threadIdx.y; k < k0 + 256 && k < Ns; k += blockDim.y) {
+            const double gk = scale * (g[k] - sh);
+            ex = max(ex, exp_of((j < M ? T[(size_t)k * M + j] : 1.0) * gk));
+        }
+    }
+    __shared__ int red[8][32];
+    red[threadIdx.y][threadIdx.x] = ex;
+    __syncthreads();
+    if (threadIdx.y == 0 && j <= M) {
+        for (int y = 1; y < (int)blockDim.y; ++y) ex = max(ex, red[y][threadIdx.x]);
+        if (ex != -100000) atomicMax(&expo[j], ex);
+    }
+}
+
+// (T' o g)^T sliced: out [SB][M+1][ld], row j, column k, through 32 x 32 tiles.
+__global__ void k_tg_slice(const double *__restrict__ T, const double *__restrict__ g, double scale,
+                           const double *__restrict__ shift, int64_t Ns, int M, int SB, int64_t ld,
+                           const int *__restrict__ expo, __nv_bfloat16 *__restrict__ out) {
+    __shared__ double tile[32][33];
+    const int64_t k0 = (int64_t)blockIdx.x * 32;
+    const int j0 = blockIdx.y * 32;
+    const double sh = shift ? *shift : 0.0;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int64_t k = k0 + r;
+        const int j = j0 + threadIdx.x;
+        double v = 0.0;
+        if (k < Ns && j <= M) v = (j < M ? T[(size_t)k * M + j] : 1.0) * (scale * (g[k] - sh));
+        tile[r][threadIdx.x] = v;
+    }
+    __syncthreads();
+    const int64_t plane = (int64_t)(M + 1) * ld;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int j = j0 + r;
+        const int64_t k = k0 + threadIdx.x;
+        if (j > M || k >= ld) continue;
+        const int e = expo[j] == -100000 ? 0 : expo[j];
+        slice_value(k < Ns ? tile[threadIdx.x][r] : 0.0, e, SB, out + (size_t)j * ld + k, plane);
+    }
+}
+
+// P^T [N+1][M+1] (row i, column j) -> J^T g in the parameter layout.
+__global__ void k_scatter_vjp(int N, int M, const double *__restrict__ PT, double *__restrict__ out) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t tot = (int64_t)(N + 1) * (M + 1);
+    if (idx >= tot) return;
+    const int i = (int)(idx / (M + 1)), j = (int)(idx % (M + 1));
+    const double v = PT[idx];
+    if (i == N && j == M) return;
+    if (j == M)
+        out[i] = v;
+    else if (i == N)
+        out[N + j] = v;
+    else
+        out[N + M + (size_t)j * N + i] = v;
+}
+
+// V' [(M+1)][(N+1)] from the parameter-shaped vector v: row j < M is
+// [V_W[j][0..N-1], v_b[j]], row M is [v_a, 0].
+__global__ void k_build_vaug(int N, int M, const double *__restrict__ v, double *__restrict__ Vp) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t tot = (int64_t)(M + 1) * (N + 1);
+    if (idx >= tot) return;
+    const int j = (int)(idx / (N + 1)), i = (int)(idx % (N + 1));
+    double x;
+    if (j < M)
+        x = i < N ? v[N + M + (size_t)j * N + i] : v[N + j];
+    else
+        x = i < N ? v[i] : 0.0;
+    Vp[idx] = x;
+}
+
+inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+inline int64_t pad8(int64_t x) { return (x + 7) / 8 * 8; }
+
+bool make_rows_map(CUtensorMap *map, const __nv_bfloat16 *p, int64_t rows, int64_t K, int64_t ld, int box_rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(p), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool make_sliced_map(CUtensorMap *map, const __nv_bfloat16 *p, int64_t rows, int64_t K, int64_t ld, int SB,
+                     int box_rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)SB};
+    cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)rows * ld * 2};
+    cuuint32_t box[3] = {(cuuint32_t)kBK, (cuuint32_t)box_rows, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16 *>(p), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// C (mode) A B^T + bias: A BF16 [rows][ldA] (K used), B slices [SB][cols][ldB].
+cudaError_t sgemm(const __nv_bfloat16 *A, int64_t rows, int64_t ldA, const __nv_bfloat16 *Bsl, const int *expB,
+                  int64_t cols, int64_t ldB, int64_t K, int SB, double *C, int64_t ldc, int mode,
+                  const double *bias, int *err, cudaStream_t st) {
+    if (rows <= 0 || cols <= 0 || K <= 0) return cudaSuccess;
+    if (SB < 1 || SB > kMaxSB || rows > (1LL << 31) - kBM || cols > (1LL << 31) - kBN) return cudaErrorInvalidValue;
+    CUtensorMap ma, mb;
+    if (!make_rows_map(&ma, A, rows, K, ldA, kBM) || !make_sliced_map(&mb, Bsl, cols, K, ldB, SB, kBN))
+        return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k_sgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sgemm_smem_bytes());
+    if (e != cudaSuccess) return e;
+    SgArgs a{rows, cols, (int)((K + kBK - 1) / kBK), SB, expB, C, ldc, mode, bias, err};
+    dim3 grid(nblk(cols, kBN), nblk(rows, kBM));
+    (k_sgemm<<<grid, kSgThreads, sgemm_smem_bytes(), st>>>(ma, mb, a), nk::note_launch());
+    return cudaGetLastError();
+}
+
+double sgemm_flops(int64_t rows, int64_t cols, int64_t K, int SB) {
+    return 2.0 * (double)((rows + kBM - 1) / kBM * kBM) * (double)((cols + kBN - 1) / kBN * kBN) *
+           (double)((K + kBK - 1) / kBK * kBK) * SB;
+}
+
+}  // namespace
+
+// ============================================================ launchers ====
+
+size_t tc_theta_ws_bytes(int N, int M, int64_t B) {
+    const int64_t ld = pad8(N);
+    return ((size_t)B * ld * 2 + 255) / 256 * 256 + ((size_t)kMaxSB * M * ld * 2 + 255) / 256 * 256 +
+           ((size_t)M * 4 + 255) / 256 * 256 + 256;
+}
+
+// theta [B][M] = S W^T + b with W sliced 7 ways: exact up to 2^-56 of max|W_j|.
+cudaError_t launch_theta_tc(int N, int M, const double *b, const double *W, const int8_t *s, int64_t B,
+                            double *theta, int *err, void *ws, cudaStream_t st) {
+    if (B <= 0) return cudaSuccess;
+    const int64_t ld = pad8(N);
+    char *p = static_cast<char *>(ws);
+    auto take = [&](size_t bytes) {
+        char *q = p;
+        p += (bytes + 255) / 256 * 256;
+        return q;
+    };
+    auto *As = reinterpret_cast<__nv_bfloat16 *>(take((size_t)B * ld * 2));
+    auto *Ws = reinterpret_cast<__nv_bfloat16 *>(take((size_t)kMaxSB * M * ld * 2));
+    auto *ew = reinterpret_cast<int *>(take((size_t)M * 4));
+    (k_pm1_rows<<<nblk(B * ld, 256), 256, 0, st>>>(s, B, N, 0, ld, As), nk::note_launch());
+    (k_slice_long_rows<<<M, 128, 0, st>>>(W, N, M, N, nullptr, kMaxSB, ld, Ws, ew), nk::note_launch());
+    const int slot = prof_begin(NK_PROF_JVP_VJP, st);
+    cudaError_t e = sgemm(As, B, ld, Ws, ew, M, ld, N, kMaxSB, theta, M, 0, b, err, st);
+    prof_end(slot, st, sgemm_flops(B, M, N, kMaxSB));
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+size_t tc_jvp_ws_bytes(int N, int M, int64_t Ns) {
+    const int64_t ld = pad8(N + 1);
+    return ((size_t)Ns * ld * 2 + 255) / 256 * 256 + ((size_t)kMaxSB * (M + 1) * ld * 2 + 255) / 256 * 256 +
+           ((size_t)(M + 1) * (N + 1) * 8 + 255) / 256 * 256 + ((size_t)(M + 1) * 4 + 255) / 256 * 256 +
+           ((size_t)Ns * (M + 1) * 8 + 255) / 256 * 256 + 256;
+}
+
+// out = J v with V' cut into SB slices: U' = S' V'^T, w = rowdot(T', U').
+cudaError_t launch_jvp_tc(int N, int M, int64_t Ns, const int8_t *s, const double *T, const double *v,
+                          double *out, int SB, int *err, void *ws, cudaStream_t st) {
+    const int64_t ld = pad8(N + 1);
+    char *p = static_cast<char *>(ws);
+    auto take = [&](size_t bytes) {
+        char *q = p;
+        p += (bytes + 255) / 256 * 256;
+        return q;
+    };
+    auto *As = reinterpret_cast<__nv_bfloat16 *>(take((size_t)Ns * ld * 2));
+    auto *Vs = reinterpret_cast<__nv_bfloat16 *>(take((size_t)kMaxSB * (M + 1) * ld * 2));
+    auto *Vp = reinterpret_cast<double *>(take((size_t)(M + 1) * (N + 1) * 8));
+    auto *ev = reinterpret_cast<int *>(take((size_t)(M + 1) * 4));
+    auto *U = reinterpret_cast<double *>(take((size_t)Ns * (M + 1) * 8));
+    const int64_t tot = (int64_t)(M + 1) * (N + 1);
+    (k_pm1_rows<<<nblk(Ns * ld, 256), 256, 0, st>>>(s, Ns, N, 1, ld, As), nk::note_launch());
+    (k_build_vaug<<<nblk(tot, 256), 256, 0, st>>>(N, M, v, Vp), nk::note_launch());
+    (k_slice_long_rows<<<M + 1, 128, 0, st>>>(Vp, N + 1, M + 1, N + 1, nullptr, SB, ld, Vs, ev), nk::note_launch());
+    const int slot = prof_begin(NK_PROF_JVP_VJP, st);
+    cudaError_t e = sgemm(As, Ns, ld, Vs, ev, M + 1, ld, N + 1, SB, U, M + 1, 0, nullptr, err, st);
+    prof_end(slot, st, sgemm_flops(Ns, M + 1, N + 1, SB));
+    if (e != cudaSuccess) return e;
+    return launch_rowdot_aug(M, Ns, T, U, out, st);
+}
+
+size_t tc_vjp_ws_bytes(int N, int M, int64_t Ns) {
+    const int64_t ld = pad8(Ns);
+    return ((size_t)(N + 1) * ld * 2 + 255) / 256 * 256 + ((size_t)kMaxSB * (M + 1) * ld * 2 + 255) / 256 * 256 +
+           ((size_t)(M + 1) * 4 + 255) / 256 * 256 + ((size_t)(N + 1) * (M + 1) * 8 + 255) / 256 * 256 + 256;
+}
+
+// out = J^T g' with g' = scale (g - shift), (T' o g')^T cut into SB slices.
+cudaError_t launch_vjp_tc(int N, int M, int64_t Ns, const int8_t *s, const double *T, const double *g,
+                          double scale, const double *shift, double *out, int SB, int *err, void *ws,
+                          cudaStream_t st) {
+    const int64_t ld = pad8(Ns);
+    char *p = static_cast<char *>(ws);
+    auto take = [&](size_t bytes) {
+        char *q = p;
+        p += (bytes + 255) / 256 * 256;
+        return q;
+    };
+    auto *St = reinterpret_cast<__nv_bfloat16 *>(take((size_t)(N + 1) * ld * 2));
+    auto *Gs = reinterpret_cast<__nv_bfloat16 *>(take((size_t)kMaxSB * (M + 1) * ld * 2));
+    auto *eg = reinterpret_cast<int *>(take((size_t)(M + 1) * 4));
+    auto *PT = reinterpret_cast<double *>(take((size_t)(N + 1) * (M + 1) * 8));
+    dim3 tb(32, 8);
+    (k_pm1_cols<<<dim3(nblk(ld, 32), nblk(N + 1, 32)), tb, 0, st>>>(s, Ns, N, ld, St), nk::note_launch());
+    (k_fill_int<<<nblk(M + 1, 256), 256, 0, st>>>(M + 1, -100000, eg), nk::note_launch());
+    (k_tg_colexp<<<dim3(nblk(M + 1, 32), nblk(Ns, 256)), dim3(32, 8), 0, st>>>(T, g, scale, shift, Ns, M, eg),
+     nk::note_launch());
+    (k_tg_slice<<<dim3(nblk(ld, 32), nblk(M + 1, 32)), tb, 0, st>>>(T, g, scale, shift, Ns, M, SB, ld, eg, Gs),
+     nk::note_launch());
+    const int slot = prof_begin(NK_PROF_JVP_VJP, st);
+    cudaError_t e = sgemm(St, N + 1, ld, Gs, eg, M + 1, ld, Ns, SB, PT, M + 1, 0, nullptr, err, st);
+    prof_end(slot, st, sgemm_flops(N + 1, M + 1, Ns, SB));
+    if (e != cudaSuccess) return e;
+    const int64_t tot = (int64_t)(N + 1) * (M + 1);
+    (k_scatter_vjp<<<nblk(tot, 256), 256, 0, st>>>(N, M, PT, out), nk::note_launch());
+    return cudaGetLastError();
+}
+
+}  // namespace nk

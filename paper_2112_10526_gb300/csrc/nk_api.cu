@@ -20,6 +20,7 @@ struct nk_ctx {
     double *host_vals;  // pinned
     cudaStream_t side;  // high-priority stream for the Cholesky look-ahead
     cudaEvent_t ev[2];
+    int *tc_err;        // device: sticky code of the first tensor-core time-out
 };
 
 namespace {
@@ -197,7 +198,14 @@ struct SolveWs {
     int *info;  // [0] breakdown pivot, [1] tensor-core time-out code
     double *K, *rowmean;
     void *tc;   // tensor-core slices and inverted diagonal blocks (NK_MIXED)
+    void *tcm;  // tensor-core Jacobian-product workspace (NK_MIXED)
+    int *tcerr; // sticky tensor-core error word of the context
 };
+
+size_t tcm_bytes(int N, int M, int64_t B) {
+    size_t a = nk::tc_jvp_ws_bytes(N, M, B), b = nk::tc_vjp_ws_bytes(N, M, B), c = nk::tc_theta_ws_bytes(N, M, B);
+    return a > b ? (a > c ? a : c) : (b > c ? b : c);
+}
 
 void carve_solve(Carver &c, SolveWs &w, int N, int M, int64_t Ns, int solver, int precision) {
     const int64_t Np = n_params(N, M);
@@ -206,6 +214,7 @@ void carve_solve(Carver &c, SolveWs &w, int N, int M, int64_t Ns, int solver, in
     w.dotp = c.take<double>(nk::dot_partial_doubles(Np > Ns ? Np : Ns) + 8);
     w.sc = c.take<double>(8);
     w.flags = c.take<int>(4);
+    if (precision == NK_MIXED) w.tcm = c.take<char>(tcm_bytes(N, M, Ns));
     if (solver == NK_SOLVER_CG) {
         w.U = c.take<double>((size_t)Ns * (M + 1));
         w.w = c.take<double>(Ns);
@@ -232,13 +241,33 @@ void carve_solve(Carver &c, SolveWs &w, int N, int M, int64_t Ns, int solver, in
 }
 
 // (G + eps I) v for the on-the-fly QGT (App. B.3).
+// Slices per operand row of the NK_MIXED Jacobian products: 4 in CG matvecs
+// (2^-32 of the row maximum), 7 (FP64 level) where the sample-space solve
+// subtracts nearly equal vectors.
+constexpr int kMatvecSlices = 4, kExactSlices = 7;
+
+cudaError_t jvp_any(int N, int M, int64_t Ns, const int8_t *s, const double *T, const double *v, SolveWs &w,
+                    double *out, int precision, int slices, cudaStream_t st) {
+    if (precision == NK_MIXED) return nk::launch_jvp_tc(N, M, Ns, s, T, v, out, slices, w.tcerr, w.tcm, st);
+    return nk::launch_jvp(N, M, Ns, s, T, v, w.U, out, st);
+}
+
+cudaError_t vjp_any(int N, int M, int64_t Ns, const int8_t *s, const double *T, const double *g, double scale,
+                    const double *shift, SolveWs &w, double *out, int precision, int slices, cudaStream_t st) {
+    if (precision == NK_MIXED)
+        return nk::launch_vjp_tc(N, M, Ns, s, T, g, scale, shift, out, slices, w.tcerr, w.tcm, st);
+    return nk::launch_vjp(N, M, Ns, s, T, g, scale, shift, w.partial, out, st);
+}
+
+// (G + eps I) v for the on-the-fly QGT (App. B.3).
 cudaError_t qgt_onthefly(int N, int M, int64_t Ns, const int8_t *s, const double *T,
-                         const double *v, double eps, SolveWs &w, double *out, cudaStream_t st) {
-    cudaError_t e = nk::launch_jvp(N, M, Ns, s, T, v, w.U, w.w, st);
+                         const double *v, double eps, SolveWs &w, double *out, cudaStream_t st,
+                         int precision = NK_F64) {
+    cudaError_t e = jvp_any(N, M, Ns, s, T, v, w, w.w, precision, kMatvecSlices, st);
     if (e != cudaSuccess) return e;
     e = nk::launch_center(Ns, w.w, w.dotp, 1.0 / (double)Ns, st);
     if (e != cudaSuccess) return e;
-    e = nk::launch_vjp(N, M, Ns, s, T, w.w, 1.0, nullptr, w.partial, out, st);
+    e = vjp_any(N, M, Ns, s, T, w.w, 1.0, nullptr, w, out, precision, kMatvecSlices, st);
     if (e != cudaSuccess) return e;
     return nk::launch_axpby(n_params(N, M), eps, v, 1.0, out, st);
 }
@@ -274,7 +303,7 @@ nk_status run_solve(nk_ctx *ctx, int N, int M, int64_t Ns, const int8_t *s, cons
         int it = 0;
         bool converged = false;
         while (it < maxiter) {
-            NK_CU(qgt_onthefly(N, M, Ns, s, T, w.p, eps, w, w.Ap, st), "cg matvec");
+            NK_CU(qgt_onthefly(N, M, Ns, s, T, w.p, eps, w, w.Ap, st, precision), "cg matvec");
             NK_CU(nk::launch_dot(Np, w.p, w.Ap, w.dotp, pAp, st), "cg dot");
             NK_CU(nk::launch_cg_update_xr(Np, rr_keep, pAp, w.p, w.Ap, w.x, w.r, done, st), "cg xr");
             NK_CU(nk::launch_dot(Np, w.r, w.r, w.dotp, rr_new, st), "cg dot");
@@ -338,17 +367,59 @@ nk_status run_solve(nk_ctx *ctx, int N, int M, int64_t Ns, const int8_t *s, cons
         NK_CU(nk::launch_gram_samplespace(N, M, Ns, s, T, eps, w.K, w.rowmean, st), "ss gram");
         NK_CU(nk::launch_cholesky(w.K, Ns, w.info, st), "ss factor");
     }
-    NK_CU(nk::launch_jvp(N, M, Ns, s, T, F, w.U, w.w, st), "ss XF");
+    NK_CU(jvp_any(N, M, Ns, s, T, F, w, w.w, precision, kExactSlices, st), "ss XF");
     NK_CU(nk::launch_center(Ns, w.w, w.dotp, isq, st), "ss XF");
     if (tc)
         NK_CU(nk::launch_cholesky_solve_tc(w.K, Ns, w.tc, w.w, st), "ss solve");
     else
         NK_CU(nk::launch_cholesky_solve(w.K, Ns, w.w, st), "ss solve");
     NK_CU(nk::launch_center(Ns, w.w, w.dotp, isq, st), "ss Xty");
-    NK_CU(nk::launch_vjp(N, M, Ns, s, T, w.w, 1.0, nullptr, w.partial, w.tmp, st), "ss Xty");
+    NK_CU(vjp_any(N, M, Ns, s, T, w.w, 1.0, nullptr, w, w.tmp, precision, kExactSlices, st), "ss Xty");
     NK_CU(nk::launch_axpby(Np, 1.0 / eps, F, 0.0, delta, st), "ss delta");
     NK_CU(nk::launch_axpby(Np, -1.0 / eps, w.tmp, 1.0, delta, st), "ss delta");
     return sync_check ? check_factor(ctx, w.info, st) : NK_OK;
+}
+
+// Metropolis sweeps.  NK_F64 rebuilds theta inside the sweep kernel; NK_MIXED
+// runs one sweep per launch, each preceded by the FP64-exact tensor-core
+// theta of all chains.
+template <typename R>
+nk_status run_sweeps(nk_ctx *ctx, const nk::Tables<R> &t, const nk::SweepArgs &a, bool mixed, double *theta,
+                     void *tcm, cudaStream_t st) {
+    if (!mixed) {
+        NK_CU(nk::launch_sweep(t, a, st), "sweep");
+        return NK_OK;
+    }
+    const int total = a.n_discard + a.n_samples;
+    for (int w = 0; w < total; ++w) {
+        NK_CU(nk::launch_theta_tc(t.N, t.M, t.b, t.W, a.s, a.C, theta, ctx->tc_err, tcm, st), "theta");
+        nk::SweepArgs b = a;
+        b.sweep0 = a.sweep0 + w;
+        b.n_discard = w < a.n_discard ? 1 : 0;
+        b.n_samples = w < a.n_discard ? 0 : 1;
+        b.theta_in = theta;
+        b.out_stride = a.n_samples;
+        b.out_offset = w < a.n_discard ? 0 : w - a.n_discard;
+        b.dec_stride = total;
+        b.dec_offset = w;
+        NK_CU(nk::launch_sweep(t, b, st), "sweep");
+    }
+    return NK_OK;
+}
+
+// T = tanh(theta) of a batch: FP64 CUDA-core GEMM (NK_F64) or the FP64-exact
+// tensor-core product (NK_MIXED, needs tcm).
+nk_status batch_T(nk_ctx *ctx, const nk_rbm *rbm, const int8_t *s, int64_t B, double *T, bool mixed, void *tcm,
+                  cudaStream_t st) {
+    const int N = rbm->N, M = rbm->M;
+    const double *b = rbm->params + N, *W = rbm->params + N + M;
+    if (!mixed) {
+        NK_CU(nk::launch_theta_tanh(N, M, b, W, s, B, T, st), "theta");
+        return NK_OK;
+    }
+    NK_CU(nk::launch_theta_tc(N, M, b, W, s, B, T, ctx->tc_err, tcm, st), "theta");
+    NK_CU(nk::launch_tanh_inplace(B * M, T, st), "tanh");
+    return NK_OK;
 }
 
 nk_status check_solver(int solver, double eps, double tol, int maxiter) {
@@ -376,6 +447,17 @@ extern "C" {
 
 int32_t nk_version(void) { return 100; }
 
+nk_status nk_ctx_error(nk_ctx *ctx, int32_t *code, void *stream) {
+    if (!ctx || !code) return fail(NK_ERR_INVALID_ARG, "ctx or code is NULL");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    NK_CU(cudaMemcpyAsync(ctx->host_flags + 4, ctx->tc_err, sizeof(int), cudaMemcpyDeviceToHost, st), "ctx error");
+    NK_CU(cudaMemsetAsync(ctx->tc_err, 0, sizeof(int), st), "ctx error");
+    NK_CU(cudaStreamSynchronize(st), "ctx error");
+    *code = ctx->host_flags[4];
+    return NK_OK;
+}
+
 const char *nk_last_error(void) { return g_err.c_str(); }
 
 nk_status nk_ctx_create(int32_t device, nk_ctx **out) {
@@ -396,6 +478,8 @@ nk_status nk_ctx_create(int32_t device, nk_ctx **out) {
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, hi_prio);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev[0], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev[1], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc(&c->tc_err, 256);
+    if (e == cudaSuccess) e = cudaMemset(c->tc_err, 0, 256);
     if (e != cudaSuccess) {
         if (c->host_flags) cudaFreeHost(c->host_flags);
         if (c->host_vals) cudaFreeHost(c->host_vals);
@@ -417,6 +501,7 @@ nk_status nk_ctx_destroy(nk_ctx *ctx) {
     if (ctx->side) cudaStreamDestroy(ctx->side);
     if (ctx->ev[0]) cudaEventDestroy(ctx->ev[0]);
     if (ctx->ev[1]) cudaEventDestroy(ctx->ev[1]);
+    if (ctx->tc_err) cudaFree(ctx->tc_err);
     delete ctx;
     return NK_OK;
 }
@@ -437,7 +522,15 @@ nk_status nk_rbm_logpsi(nk_ctx *ctx, const nk_rbm *rbm, int32_t precision, const
     return with_workspace(ctx, [&](Carver &c, bool run) -> nk_status {
         nk::Tables<double> t{};
         carve_tables(c, t, rbm, 0, nullptr, false, false);
+        const bool mixed = precision == NK_MIXED;
+        double *theta = mixed ? c.take<double>((size_t)B * M) : nullptr;
+        void *tcm = mixed ? c.take<char>(nk::tc_theta_ws_bytes(N, M, B)) : nullptr;
         if (!run) return NK_OK;
+        if (mixed) {
+            NK_CU(nk::launch_theta_tc(N, M, t.b, t.W, s, B, theta, ctx->tc_err, tcm, st), "theta");
+            NK_CU(nk::launch_logpsi_theta(N, M, t.a, theta, s, B, logpsi_out, st), "logpsi");
+            return NK_OK;
+        }
         NK_CU(nk::launch_tables(t, false, false, st), "tables");
         NK_CU(nk::launch_logpsi(N, M, t.a, t.b, t.Wt, s, B, logpsi_out, st), "logpsi");
         return NK_OK;
@@ -509,10 +602,12 @@ nk_status nk_metropolis_sweep(nk_ctx *ctx, const nk_rbm *rbm, int32_t precision,
         using R = decltype(tag);
         nk::Tables<R> t{};
         carve_tables(c, t, rbm, E, edges, rule == NK_RULE_LOCAL, rule == NK_RULE_EXCHANGE);
+        const bool mixed = precision == NK_MIXED;
+        double *theta = mixed ? c.take<double>((size_t)C * rbm->M) : nullptr;
+        void *tcm = mixed ? c.take<char>(nk::tc_theta_ws_bytes(rbm->N, rbm->M, C)) : nullptr;
         if (!run) return NK_OK;
         NK_CU(nk::launch_tables(t, rule == NK_RULE_LOCAL, rule == NK_RULE_EXCHANGE, st), "tables");
-        NK_CU(nk::launch_sweep(t, a, st), "sweep");
-        return NK_OK;
+        return run_sweeps(ctx, t, a, mixed, theta, tcm, st);
     };
     if (precision == NK_F64)
         return with_workspace(ctx, [&](Carver &c, bool run) { return body(double{}, c, run); });
@@ -540,9 +635,17 @@ nk_status nk_local_energy(nk_ctx *ctx, const nk_rbm *rbm, int32_t precision, con
         using R = decltype(tag);
         nk::Tables<R> t{};
         carve_tables(c, t, rbm, ham->n_edges, ham->edges, site, edge);
+        const bool mixed = precision == NK_MIXED;
+        double *theta = mixed ? c.take<double>((size_t)Ns * rbm->M) : nullptr;
+        void *tcm = mixed ? c.take<char>(nk::tc_theta_ws_bytes(rbm->N, rbm->M, Ns)) : nullptr;
         if (!run) return NK_OK;
         NK_CU(nk::launch_tables(t, site, edge, st), "tables");
-        NK_CU(nk::launch_eloc(t, a, st), "local energy");
+        nk::ElocArgs am = a;
+        if (mixed) {
+            NK_CU(nk::launch_theta_tc(rbm->N, rbm->M, t.b, t.W, s, Ns, theta, ctx->tc_err, tcm, st), "theta");
+            am.theta_in = theta;
+        }
+        NK_CU(nk::launch_eloc(t, am, st), "local energy");
         return NK_OK;
     };
     if (precision == NK_F64)
@@ -616,10 +719,15 @@ nk_status nk_vjp(nk_ctx *ctx, const nk_rbm *rbm, int32_t precision, const int8_t
     const int N = rbm->N, M = rbm->M;
     return with_workspace(ctx, [&](Carver &c, bool run) -> nk_status {
         double *T = c.take<double>((size_t)Ns * M);
-        double *partial = c.take<double>(nk::vjp_partial_doubles(N, M, Ns));
+        SolveWs w{};
+        w.partial = c.take<double>(nk::vjp_partial_doubles(N, M, Ns));
+        const bool mixed = precision == NK_MIXED;
+        w.tcm = mixed ? c.take<char>(tcm_bytes(N, M, Ns)) : nullptr;
+        w.tcerr = ctx->tc_err;
         if (!run) return NK_OK;
-        NK_CU(nk::launch_theta_tanh(N, M, rbm->params + N, rbm->params + N + M, s, Ns, T, st), "theta");
-        NK_CU(nk::launch_vjp(N, M, Ns, s, T, gvec, 1.0, nullptr, partial, out, st), "vjp");
+        nk_status bt = batch_T(ctx, rbm, s, Ns, T, mixed, w.tcm, st);
+        if (bt != NK_OK) return bt;
+        NK_CU(vjp_any(N, M, Ns, s, T, gvec, 1.0, nullptr, w, out, precision, kMatvecSlices, st), "vjp");
         return NK_OK;
     });
 }
@@ -639,10 +747,15 @@ nk_status nk_jvp(nk_ctx *ctx, const nk_rbm *rbm, int32_t precision, const int8_t
     const int N = rbm->N, M = rbm->M;
     return with_workspace(ctx, [&](Carver &c, bool run) -> nk_status {
         double *T = c.take<double>((size_t)Ns * M);
-        double *U = c.take<double>((size_t)Ns * (M + 1));
+        SolveWs w{};
+        w.U = c.take<double>((size_t)Ns * (M + 1));
+        const bool mixed = precision == NK_MIXED;
+        w.tcm = mixed ? c.take<char>(tcm_bytes(N, M, Ns)) : nullptr;
+        w.tcerr = ctx->tc_err;
         if (!run) return NK_OK;
-        NK_CU(nk::launch_theta_tanh(N, M, rbm->params + N, rbm->params + N + M, s, Ns, T, st), "theta");
-        NK_CU(nk::launch_jvp(N, M, Ns, s, T, v, U, out, st), "jvp");
+        nk_status bt = batch_T(ctx, rbm, s, Ns, T, mixed, w.tcm, st);
+        if (bt != NK_OK) return bt;
+        NK_CU(jvp_any(N, M, Ns, s, T, v, w, out, precision, kMatvecSlices, st), "jvp");
         return NK_OK;
     });
 }
@@ -662,14 +775,19 @@ nk_status nk_force(nk_ctx *ctx, const nk_rbm *rbm, int32_t precision, const int8
     const int N = rbm->N, M = rbm->M;
     return with_workspace(ctx, [&](Carver &c, bool run) -> nk_status {
         double *T = c.take<double>((size_t)Ns * M);
-        double *partial = c.take<double>(nk::vjp_partial_doubles(N, M, Ns));
+        SolveWs w{};
+        w.partial = c.take<double>(nk::vjp_partial_doubles(N, M, Ns));
         double *st3 = c.take<double>(4);
         double *gv = c.take<double>(Ns);
+        const bool mixed = precision == NK_MIXED;
+        w.tcm = mixed ? c.take<char>(tcm_bytes(N, M, Ns)) : nullptr;
+        w.tcerr = ctx->tc_err;
         if (!run) return NK_OK;
-        NK_CU(nk::launch_theta_tanh(N, M, rbm->params + N, rbm->params + N + M, s, Ns, T, st), "theta");
+        nk_status bt = batch_T(ctx, rbm, s, Ns, T, mixed, w.tcm, st);
+        if (bt != NK_OK) return bt;
         NK_CU(nk::launch_stats(eloc, Ns, 1, st3, st), "stats");
         NK_CU(nk::launch_make_force_g(Ns, eloc, st3, gv, st), "force g");
-        NK_CU(nk::launch_vjp(N, M, Ns, s, T, gv, 1.0, nullptr, partial, F_out, st), "vjp");
+        NK_CU(vjp_any(N, M, Ns, s, T, gv, 1.0, nullptr, w, F_out, precision, kExactSlices, st), "vjp");
         return NK_OK;
     });
 }
@@ -712,10 +830,13 @@ nk_status nk_qgt_matvec(nk_ctx *ctx, const nk_qgt *q, double diag_shift, const d
         w.dotp = c.take<double>(nk::dot_partial_doubles(Ns) + 8);
         w.U = c.take<double>((size_t)Ns * (M + 1));
         w.w = c.take<double>(Ns);
+        const bool mixed = q->precision == NK_MIXED;
+        w.tcm = mixed ? c.take<char>(tcm_bytes(N, M, Ns)) : nullptr;
+        w.tcerr = ctx->tc_err;
         if (!run) return NK_OK;
-        NK_CU(nk::launch_theta_tanh(N, M, rbm->params + N, rbm->params + N + M, q->s, Ns, T, st),
-              "theta");
-        NK_CU(qgt_onthefly(N, M, Ns, q->s, T, v, diag_shift, w, out, st), "qgt matvec");
+        nk_status bt = batch_T(ctx, rbm, q->s, Ns, T, mixed, w.tcm, st);
+        if (bt != NK_OK) return bt;
+        NK_CU(qgt_onthefly(N, M, Ns, q->s, T, v, diag_shift, w, out, st, q->precision), "qgt matvec");
         return NK_OK;
     });
 }
@@ -767,8 +888,10 @@ nk_status nk_sr_solve(nk_ctx *ctx, const nk_rbm *rbm, int32_t precision, const i
         double *T = c.take<double>((size_t)Ns * M);
         SolveWs w;
         carve_solve(c, w, N, M, Ns, solver, precision);
+        w.tcerr = ctx->tc_err;
         if (!run) return NK_OK;
-        NK_CU(nk::launch_theta_tanh(N, M, rbm->params + N, rbm->params + N + M, s, Ns, T, st), "theta");
+        nk_status bt = batch_T(ctx, rbm, s, Ns, T, precision == NK_MIXED, w.tcm, st);
+        if (bt != NK_OK) return bt;
         return run_solve(ctx, N, M, Ns, s, T, F, solver, diag_shift, cg_tol, cg_maxiter, w,
                          delta_out, info_out, resid_out, st, precision, precision == NK_MIXED);
     });
@@ -816,6 +939,11 @@ nk_status nk_sr_step(nk_ctx *ctx, nk_rbm *rbm, const nk_ham *ham, nk_chains *cha
         unsigned long long *acc = c.take<unsigned long long>(C);
         SolveWs w;
         carve_solve(c, w, N, M, Ns, cfg->solver, cfg->precision);
+        w.tcerr = ctx->tc_err;
+        const bool mixed = cfg->precision == NK_MIXED;
+        const int64_t TB = Ns > C ? Ns : C;
+        double *theta = mixed ? c.take<double>((size_t)TB * M) : nullptr;
+        void *tcm = mixed ? c.take<char>(tcm_bytes(N, M, TB)) : nullptr;
         if (!run) return NK_OK;
         NK_CU(nk::launch_tables(t, site, edge, st), "tables");
         NK_CU(cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * C, st), "memset");
@@ -836,12 +964,15 @@ nk_status nk_sr_step(nk_ctx *ctx, nk_rbm *rbm, const nk_ham *ham, nk_chains *cha
         a.logpsi = nullptr;
         a.n_accepted = acc;
         a.decisions = nullptr;
-        NK_CU(nk::launch_sweep(t, a, st), "sweep");
-        nk::ElocArgs ea{ham->kind, ham->J, ham->h, ham->marshall, samples, Ns, eloc, T};
+        nk_status sw = run_sweeps(ctx, t, a, mixed, theta, tcm, st);
+        if (sw != NK_OK) return sw;
+        if (mixed)
+            NK_CU(nk::launch_theta_tc(N, M, t.b, t.W, samples, Ns, theta, ctx->tc_err, tcm, st), "theta");
+        nk::ElocArgs ea{ham->kind, ham->J, ham->h, ham->marshall, samples, Ns, eloc, T, theta};
         NK_CU(nk::launch_eloc(t, ea, st), "local energy");
         NK_CU(nk::launch_stats(eloc, Ns, C, st3, st), "stats");
         NK_CU(nk::launch_make_force_g(Ns, eloc, st3, gv, st), "force g");
-        NK_CU(nk::launch_vjp(N, M, Ns, samples, T, gv, 1.0, nullptr, w.partial, F, st), "force");
+        NK_CU(vjp_any(N, M, Ns, samples, T, gv, 1.0, nullptr, w, F, cfg->precision, kExactSlices, st), "force");
         int info[2] = {0, 0};
         double resid = 0.0;
         nk_status ss = run_solve(ctx, N, M, Ns, samples, T, F, cfg->solver, cfg->diag_shift,

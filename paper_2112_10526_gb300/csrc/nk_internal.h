@@ -41,6 +41,10 @@ cudaError_t launch_tables(const Tables<R> &t, bool need_site, bool need_edge, cu
 cudaError_t launch_logpsi(int N, int M, const double *a, const double *b, const double *Wt,
                           const int8_t *s, int64_t B, double *out, cudaStream_t st);
 
+cudaError_t launch_logpsi_theta(int N, int M, const double *a, const double *theta, const int8_t *s, int64_t B,
+                                double *out, cudaStream_t st);
+cudaError_t launch_tanh_inplace(int64_t n, double *x, cudaStream_t st);
+
 cudaError_t launch_chain_init(int N, int C, int rule, uint64_t seed, uint32_t stream_id,
                               int8_t *s, cudaStream_t st);
 
@@ -56,6 +60,12 @@ struct SweepArgs {
     double *logpsi;
     unsigned long long *n_accepted;
     uint8_t *decisions;
+    // Optional, for one-sweep launches: theta of every chain at the start of
+    // the sweep ([C][M], FP64) instead of the in-kernel rebuild; the output
+    // rows are c * out_stride + out_offset + sample, the decision rows
+    // c * dec_stride + dec_offset + sweep.
+    const double *theta_in;
+    int out_stride, out_offset, dec_stride, dec_offset;
 };
 
 template <typename R>
@@ -68,7 +78,8 @@ struct ElocArgs {
     const int8_t *s;
     int64_t Ns;
     double *eloc;
-    double *t_out;  // [Ns][M] or null
+    double *t_out;            // [Ns][M] or null
+    const double *theta_in;   // [Ns][M] precomputed theta, or null (rebuilt in the kernel)
 };
 
 template <typename R>
@@ -137,6 +148,21 @@ cudaError_t launch_cholesky_solve_tc(const double *L, int64_t n, const void *ws,
                                      cudaStream_t st);
 cudaError_t launch_gram_tc(int N, int M, int64_t Ns, const int8_t *s, const double *T, int S, double *K,
                            int *err, void *ws, cudaStream_t st);
+
+cudaError_t launch_rowdot_aug(int M, int64_t Ns, const double *T, const double *U, double *out,
+                              cudaStream_t st);
+
+// ---- tensor-core products with the configurations (k_sgemm.cu) -------------
+size_t tc_theta_ws_bytes(int N, int M, int64_t B);
+cudaError_t launch_theta_tc(int N, int M, const double *b, const double *W, const int8_t *s, int64_t B,
+                            double *theta, int *err, void *ws, cudaStream_t st);
+size_t tc_jvp_ws_bytes(int N, int M, int64_t Ns);
+cudaError_t launch_jvp_tc(int N, int M, int64_t Ns, const int8_t *s, const double *T, const double *v,
+                          double *out, int SB, int *err, void *ws, cudaStream_t st);
+size_t tc_vjp_ws_bytes(int N, int M, int64_t Ns);
+cudaError_t launch_vjp_tc(int N, int M, int64_t Ns, const int8_t *s, const double *T, const double *g,
+                          double scale, const double *shift, double *out, int SB, int *err, void *ws,
+                          cudaStream_t st);
 
 // vector helpers
 cudaError_t launch_axpby(int64_t n, double alpha, const double *x, double beta, double *y,

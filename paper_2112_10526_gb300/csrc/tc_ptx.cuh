@@ -1,0 +1,243 @@
+// Internal: PTX wrappers for tcgen05 / TMA / mbarrier, exact integer-to-FP64
+// assembly, and host-side tensor-map encoding, shared by the tensor-core
+// translation units.  Everything is in an anonymous namespace (one copy per
+// translation unit).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+
+namespace nk {
+namespace {
+
+constexpr unsigned long long kWaitNs = 2000000000ULL;  // 2 s bound on every wait
+constexpr int kSliceK = 64;  // K extent of one slice row (128 bytes of BF16)
+
+// ------------------------------------------------------------ PTX helpers ---
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase; false after kWaitNs.
+__device__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    const unsigned long long t0 = global_ns();
+    for (long long it = 0; it < (1LL << 40); ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255) == 255 && global_ns() - t0 > kWaitNs) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0,
+                                            int c1, int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+                 "r"(ncols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand written by a TMA load with
+// 128-byte swizzle (8-row groups of 1024 bytes), sm_100 descriptor version 1.
+__device__ __forceinline__ uint64_t sw128_desc(const void *p) {
+    const uint64_t addr = smem_u32(p);
+    uint64_t d = (addr & 0x3FFFFULL) >> 4;    // start address
+    d |= (uint64_t)(16 >> 4) << 16;           // leading byte offset (unused for this layout)
+    d |= (uint64_t)(1024 >> 4) << 32;         // stride byte offset: next 8-row group
+    d |= (uint64_t)1 << 46;                   // descriptor version
+    d |= (uint64_t)2 << 61;                   // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor of kind::f16: BF16 A and B (K-major), FP32 D.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void split_bits(double x, int &biased, unsigned long long &mant, bool &neg) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    neg = (b >> 63) != 0;
+    biased = (int)((b >> 52) & 0x7FF);
+    mant = b & 0xFFFFFFFFFFFFFULL;
+    if (biased != 0) mant |= 1ULL << 52;
+    else biased = 1;  // subnormal: value = mant 2^(1 - 1075)
+}
+
+// The value (hi 2^32 + lo) 2^sc as an FP64 bit pattern, rounded to nearest
+// even, built with 64-bit integer operations (|hi| < 2^43, |lo| < 2^52: the
+// exact fixed-point recombination of the slice products).  lo's upper half is
+// carried into hi first, so that the magnitude is Hm 2^32 + Lm with
+// 0 <= Lm < 2^32 and Hm < 2^44.
+__device__ __forceinline__ double fixed_to_double(long long hi, long long lo, int sc) {
+    long long H = hi + (lo >> 32);
+    unsigned long long Lw = (unsigned long long)lo & 0xFFFFFFFFULL;
+    const bool neg = H < 0;
+    unsigned long long Hm, Lm;
+    if (neg) {  // |V| = (-H) 2^32 - Lw
+        Hm = (unsigned long long)(-H) - (Lw ? 1ULL : 0ULL);
+        Lm = Lw ? (0x100000000ULL - Lw) : 0ULL;
+    } else {
+        Hm = (unsigned long long)H;
+        Lm = Lw;
+    }
+    unsigned long long mant;
+    int p;  // position of the leading one of the magnitude
+    if (Hm == 0) {
+        if (Lm == 0) return 0.0;
+        p = 63 - __clzll((long long)Lm);
+        mant = Lm << (52 - p);
+    } else {
+        const int b = 64 - __clzll((long long)Hm);  // bit length of Hm, <= 44
+        p = b + 31;
+        if (b <= 21) {
+            mant = ((Hm << 32) | Lm) << (21 - b);  // exact, < 2^53
+        } else {
+            const int sr = b - 21;  // 1 .. 23 low bits of Lm to drop
+            mant = (Hm << (32 - sr)) | (Lm >> sr);
+            const unsigned long long rem = Lm & ((1ULL << sr) - 1ULL), half = 1ULL << (sr - 1);
+            if (rem > half || (rem == half && (mant & 1ULL))) {
+                ++mant;
+                if (mant == (1ULL << 53)) {
+                    mant >>= 1;
+                    ++p;
+                }
+            }
+        }
+    }
+    const int E = p + sc + 1023;
+    if (E <= 0 || E >= 2047) {  // outside the normal range: FP64 fallback
+        const double d = (double)Hm * 4294967296.0 + (double)Lm;
+        return ldexp(neg ? -d : d, sc);
+    }
+    const unsigned long long bits =
+        (neg ? (1ULL << 63) : 0ULL) | ((unsigned long long)E << 52) | (mant & 0xFFFFFFFFFFFFFULL);
+    return __longlong_as_double((long long)bits);
+}
+
+// ------------------------------------------------------ host: tensor maps ---
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
+                                  CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                  CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// 3-D map over slices [S][rows][64] BF16 (consecutive slices stride_rows rows
+// apart) with a box of one slice x box_rows rows.
+bool make_slice_map(CUtensorMap *map, const __nv_bfloat16 *slices, int64_t rows, int S, int box_rows,
+                    int64_t stride_rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)kSliceK, (cuuint64_t)rows, (cuuint64_t)S};
+    cuuint64_t strides[2] = {(cuuint64_t)kSliceK * 2, (cuuint64_t)stride_rows * kSliceK * 2};
+    cuuint32_t box[3] = {(cuuint32_t)kSliceK, (cuuint32_t)box_rows, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16 *>(slices), dims, strides,
+                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+
+}  // namespace
+}  // namespace nk

@@ -102,6 +102,7 @@ def lib():
         "nk_jvp": [P, ctypes.POINTER(nk_rbm), i32, P, i64, P, P, P],
         "nk_force": [P, ctypes.POINTER(nk_rbm), i32, P, i64, P, P, P],
         "nk_qgt_matvec": [P, ctypes.POINTER(nk_qgt), f64, P, P, P],
+        "nk_ctx_error": [P, ctypes.POINTER(ctypes.c_int32), P],
         "nk_tc_gemm": [P, i64, i64, i32, P, i64, P, i64, i32, i32, i32, P, i64, P],
         "nk_sr_solve": [P, ctypes.POINTER(nk_rbm), i32, P, i64, P, i32, f64, f64, i32, P,
                         ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double), P],
@@ -280,6 +281,13 @@ def nk_qgt_matvec(ctx, v, out, diag_shift, params=None, N=None, M=None, s=None, 
     _check(lib().nk_qgt_matvec(ctx.handle, ctypes.byref(q), float(diag_shift), _ptr(v), _ptr(out),
                                _stream(stream)))
     return out
+
+
+def nk_ctx_error(ctx, stream=None):
+    """Sticky tensor-core time-out code of the context (0 = none); resets it."""
+    code = ctypes.c_int32()
+    _check(lib().nk_ctx_error(ctx.handle, ctypes.byref(code), _stream(stream)))
+    return int(code.value)
 
 
 def nk_tc_gemm(ctx, A, B, C, slices=7, mode=0, lower=False, stream=None):
