@@ -57,6 +57,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the other-precision timing")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--serve", type=int, default=128,
+                    help="requests of the serving run added to the line (0: none)")
+    ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-budget-gb", type=float, default=64.0)
     return ap.parse_args()
 
 
@@ -363,6 +367,69 @@ def run_ours(args, rank, world):
     return line
 
 
+# ---------------------------------------------------------------- serving ----
+
+def run_serve(n_requests, slots, budget_gb, device=0):
+    """Serving workload: closed-loop capacity first (all requests queued at
+    once), then Poisson arrivals at 0.8 x that rate; latency = submit ->
+    completion as the server records it."""
+    import threading
+    import numpy as np
+    from paper_2112_10526_gb300 import inputs as I
+    from paper_2112_10526_gb300 import nk
+    specs = I.serve_requests(n_requests, seed=4)
+
+    def make(spec):
+        cfg = nk.make_cfg(spec["rule"], "mixed", spec["solver"], 8, spec["per_chain"], 0.01, 0.01, spec["seed"],
+                          stream_id=spec["index"], cg_tol=1e-8, cg_maxiter=200)
+        p = I.rbm_params(spec["N"], spec["M"], spec["seed"])
+        return nk.make_request("sr_step", spec["N"], spec["M"], p, spec["ham"], spec["chains"], cfg)
+
+    reqs = [make(sp) for sp in specs]
+    budget = int(budget_gb * (1 << 30))
+    # closed loop
+    with nk.Server(device, budget, slots) as srv:
+        t0 = time.perf_counter()
+        ids = [srv.submit(r) for r in reqs]
+        res = [srv.wait(i) for i in ids]
+        closed = time.perf_counter() - t0
+        st_closed = srv.stats()
+    capacity = n_requests / closed
+    rate = 0.8 * capacity
+    arrivals = I.poisson_arrivals(n_requests, rate, seed=4)
+    with nk.Server(device, budget, slots) as srv:
+        ids = [None] * n_requests
+        t0 = time.perf_counter()
+
+        def feeder():
+            for k, at in enumerate(arrivals):
+                delay = at - (time.perf_counter() - t0)
+                if delay > 0:
+                    time.sleep(delay)
+                ids[k] = srv.submit(reqs[k])
+
+        th = threading.Thread(target=feeder)
+        th.start()
+        th.join()
+        res_open = [srv.wait(i) for i in ids]
+        makespan = time.perf_counter() - t0
+        st_open = srv.stats()
+    lat = np.array([r["latency_ms"] for r in res_open])
+    failed = sum(1 for r in res_open if r["status"] != 0)
+    codes = {}
+    for r in list(res) + list(res_open):
+        if r["status"] != 0:
+            codes[str(r["status"])] = codes.get(str(r["status"]), 0) + 1
+    return {"requests": n_requests, "slots": slots, "hbm_budget_gb": budget_gb,
+            "closed_loop_req_per_s": capacity, "arrival_rate_req_per_s": rate,
+            "req_per_s": n_requests / makespan, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+            "failed": failed + st_closed["failed"], "failure_codes": codes,
+            "failures": [(r["status"], r["message"]) for r in list(res) + list(res_open) if r["status"] != 0][:4],
+            "mix": "Ising chains N in {16..256}, Heisenberg L in {4..16}, alpha in {1,2,4}, "
+                   "1024 chains x U{1..16} samples, NK_MIXED, Cholesky if Np <= 1024 else CG (<= 200 it)"}
+
+
 def main():
     args = parse()
     if args.oracle_sample:
@@ -402,6 +469,9 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     line = run_ours(args, rank, world)
     line["cpu_baseline"] = cpu
+    if args.serve > 0 and world == 1:
+        line["serve"] = run_serve(args.serve, args.serve_slots, args.serve_budget_gb,
+                                  int(os.environ.get("LOCAL_RANK", "0")))
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

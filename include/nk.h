@@ -327,6 +327,70 @@ nk_status nk_sr_step(nk_ctx *ctx, nk_rbm *rbm, const nk_ham *ham, nk_chains *cha
                      double *eloc_out, void *stream);
 
 
+/* ------------------------------------------------------------- serving ---
+ * A persistent request loop on one GPU for VMC expectation values and SR
+ * steps (the serving use of this library; the paper has no counterpart).
+ * Requests for different lattices, RBM widths and sample counts arrive from
+ * any host thread and wait in a FIFO; a scheduler thread admits the head
+ * request as soon as a worker slot is free and the HBM budget has room for
+ * the request's device state plus the growth of the slot's workspace
+ * (nk_request_bytes: a plan-only pass of the same entry points).  Each slot
+ * has its own context and stream, so admitted requests run concurrently and
+ * their kernels overlap, while new requests keep being admitted as slots and
+ * memory free up.  A request's parameters, chains, samples and solver
+ * workspace stay on the device until it completes.  Each request draws from
+ * its own Philox stream (cfg.seed, cfg.stream_id) and every reduction has a
+ * fixed order, so its result does not depend on what runs beside it.
+ */
+#define NK_REQ_EXPECT 0  /* sample + local energies + statistics */
+#define NK_REQ_SR_STEP 1 /* the same + force + SR solve + update (nk_sr_step) */
+
+typedef struct nk_server nk_server;
+
+typedef struct {
+    int32_t kind;            /* NK_REQ_* */
+    int32_t N, M;
+    const double *params;    /* HOST [Np], copied by nk_server_submit */
+    int32_t ham_kind;        /* NK_TFIM / NK_HEIS */
+    double J, h;
+    int32_t marshall;
+    int32_t n_edges;
+    const int32_t *edges;    /* HOST [E, 2], copied by nk_server_submit */
+    int32_t n_chains;        /* chains start from nk_chains_init(cfg.seed, cfg.stream_id) */
+    nk_sr_cfg cfg;           /* rule, precision, solver, sweeps, eps, lr, RNG stream */
+} nk_request;
+
+typedef struct {
+    int32_t status;          /* NK_OK or the request's NK_ERR_* code */
+    int32_t slot;            /* worker slot that ran it */
+    double energy, variance, error, acceptance, cg_iters, solver_status;
+    double queue_ms;         /* submit -> admission */
+    double run_ms;           /* admission -> completion */
+    double latency_ms;       /* submit -> completion */
+    size_t device_bytes;     /* HBM reserved at admission */
+    char message[128];       /* the failing entry point's message, or "" */
+} nk_result;
+
+typedef struct {
+    int64_t submitted, completed, failed, inflight, queued;
+    size_t hbm_in_use, hbm_budget;
+    double p50_ms, p99_ms;   /* latency quantiles over completed requests */
+} nk_server_stats;
+
+nk_status nk_server_create(int32_t device, size_t hbm_budget, int32_t slots, nk_server **out /* host */);
+/* params_out: HOST [Np] buffer that receives the updated parameters of an
+ * NK_REQ_SR_STEP (written before the request is marked done), or NULL. */
+nk_status nk_server_submit(nk_server *srv, const nk_request *req, double *params_out, uint64_t *id /* host */);
+nk_status nk_server_poll(nk_server *srv, uint64_t id, int32_t *done /* host */, nk_result *out /* host */);
+nk_status nk_server_wait(nk_server *srv, uint64_t id, nk_result *out /* host */);
+nk_status nk_server_stats_get(nk_server *srv, nk_server_stats *out /* host */);
+/* Drops queued requests, waits for those in flight, frees everything. */
+nk_status nk_server_destroy(nk_server *srv);
+/* HBM estimate used for admission: the request's device state plus the
+ * context workspace its entry points would allocate (planned bytes + 1/8
+ * + 1 MiB, the allocation rule of every context).  0 if the plan fails. */
+size_t nk_request_bytes(const nk_request *req);
+
 /*
  * Kernel timing for measurement tools (not part of the method).  When
  * enabled, every launch of a tracked kernel class is bracketed by CUDA

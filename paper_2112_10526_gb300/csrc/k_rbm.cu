@@ -149,6 +149,85 @@ __global__ void k_chain_init(int N, int C, int rule, unsigned long long seed, un
     }
 }
 
+// ------------------------------------------------------ ratio products ---
+
+// prod over j = j0, j0 + step, ... < M of (1 - si t_j tau[j * tstride]) as
+// mantissa x 2^exp.  Four independent running products (each renormalised
+// every RenormEvery factors) keep several loads and multiplies in flight.
+template <typename R>
+__device__ __forceinline__ Prod<R> strided_product(const R *__restrict__ t, const R *__restrict__ tau, size_t tstride,
+                                                   R si, int j0, int step, int M) {
+    R m0 = R(1), m1 = R(1), m2 = R(1), m3 = R(1);
+    int e = 0, cnt = 0;
+    int j = j0;
+    for (; j + 3 * step < M; j += 4 * step) {
+        m0 *= R(1) - si * t[j] * tau[(size_t)j * tstride];
+        m1 *= R(1) - si * t[j + step] * tau[(size_t)(j + step) * tstride];
+        m2 *= R(1) - si * t[j + 2 * step] * tau[(size_t)(j + 2 * step) * tstride];
+        m3 *= R(1) - si * t[j + 3 * step] * tau[(size_t)(j + 3 * step) * tstride];
+        if (++cnt == RenormEvery<R>::value) {
+            Prod<R> q0{m0, 0}, q1{m1, 0}, q2{m2, 0}, q3{m3, 0};
+            renorm(q0);
+            renorm(q1);
+            renorm(q2);
+            renorm(q3);
+            m0 = q0.m;
+            m1 = q1.m;
+            m2 = q2.m;
+            m3 = q3.m;
+            e += q0.e + q1.e + q2.e + q3.e;
+            cnt = 0;
+        }
+    }
+    for (; j < M; j += step) m0 *= R(1) - si * t[j] * tau[(size_t)j * tstride];
+    Prod<R> p{m0, e};
+    renorm(p);
+    p.m *= m1;
+    renorm(p);
+    p.m *= m2;
+    renorm(p);
+    p.m *= m3;
+    renorm(p);
+    return p;
+}
+
+// Lanes over hidden units, four consecutive units per lane (16-byte loads of
+// t and tau): prod over this lane's units of (1 - si t_j tau_j).  Needs
+// M % 4 == 0 and 16-byte aligned rows.
+__device__ __forceinline__ Prod<float> lane_product4(const float *__restrict__ t, const float *__restrict__ tau,
+                                                     float si, int lane, int M) {
+    float m0 = 1.f, m1 = 1.f;
+    int e = 0, cnt = 0;
+    for (int j = 4 * lane; j < M; j += 128) {
+        const float4 tv = *reinterpret_cast<const float4 *>(t + j);
+        const float4 uv = __ldg(reinterpret_cast<const float4 *>(tau + j));
+        m0 *= fmaf(-si * tv.x, uv.x, 1.f) * fmaf(-si * tv.y, uv.y, 1.f);
+        m1 *= fmaf(-si * tv.z, uv.z, 1.f) * fmaf(-si * tv.w, uv.w, 1.f);
+        if (++cnt == 4) {
+            int k0, k1;
+            m0 = frexpf(m0, &k0);
+            m1 = frexpf(m1, &k1);
+            e += k0 + k1;
+            cnt = 0;
+        }
+    }
+    Prod<float> p{m0, e};
+    renorm(p);
+    p.m *= m1;
+    renorm(p);
+    return p;
+}
+
+template <typename R>
+__device__ __forceinline__ Prod<R> unit_lanes_product(const R *t, const R *tau, R si, int lane, int M, bool vec4) {
+    return strided_product<R>(t, tau, 1, si, lane, 32, M);
+}
+template <>
+__device__ __forceinline__ Prod<float> unit_lanes_product<float>(const float *t, const float *tau, float si, int lane,
+                                                                 int M, bool vec4) {
+    return vec4 ? lane_product4(t, tau, si, lane, M) : strided_product<float>(t, tau, 1, si, lane, 32, M);
+}
+
 // ------------------------------------------------------------------ sweep ---
 
 template <typename R>
@@ -156,6 +235,7 @@ struct SweepK {
     Tables<R> t;
     SweepArgs a;
     int warp_bytes, t_bytes;
+    bool vec4;  // FP32 with M % 4 == 0: 16-byte loads in the ratio products
 };
 
 // One warp per chain.  Hidden units are spread over the lanes (j = lane,
@@ -230,16 +310,7 @@ __global__ void __launch_bounds__(128) k_sweep(SweepK<R> P) {
                 d0 = -2.0 * (double)sv[i] * (T.a[i] - T.a[k]);
             }
             const R si = (R)sv[i];
-            Prod<R> pr{R(1), 0};
-            int cnt = 0;
-            for (int j = lane; j < M; j += 32) {
-                pr.m *= R(1) - si * t[j] * tau[j];
-                if (++cnt == RenormEvery<R>::value) {
-                    renorm(pr);
-                    cnt = 0;
-                }
-            }
-            renorm(pr);
+            Prod<R> pr = unit_lanes_product<R>(t, tau, si, lane, M, P.vec4);
             pr = warp_prod(pr);
             const double delta = d0 + (double)(K + prod_log(pr));
             const bool accept = log(uniform53(u1)) < 2.0 * delta;
@@ -277,7 +348,12 @@ struct ElocK {
     Tables<R> t;
     ElocArgs a;
     int warp_bytes, t_bytes, s_bytes;
+    int units;  // 1: lanes over hidden units (large M), 0: lanes over connections
 };
+
+// Hidden-unit count from which the local energy spreads the units over the
+// lanes (one warp reduction per connection) instead of the connections.
+constexpr int kUnitsMappingM = 1024;
 
 // One warp per sample.  theta and t are rebuilt from s; the connected
 // configurations are spread over the lanes (sites for the Ising field term,
@@ -318,19 +394,20 @@ __global__ void __launch_bounds__(128) k_eloc(ElocK<R> P) {
     }
     __syncwarp();
     double off = 0.0;
-    if (A.kind == NK_TFIM) {
+    if (A.kind == NK_TFIM && P.units) {
+        // large M: lanes over hidden units, one warp reduction per site
+        for (int i = 0; i < N; ++i) {
+            const R si = (R)sv[i];
+            Prod<R> pr = strided_product<R>(t, T.tau_site + (size_t)i * M, 1, si, lane, 32, M);
+            pr = warp_prod(pr);
+            const double delta = -2.0 * T.a[i] * (double)si + (double)(T.K_site[i] + prod_log(pr));
+            if (lane == 0) off += -A.h * exp(delta);
+        }
+    } else if (A.kind == NK_TFIM) {
+        // small M: lanes over sites, each over all hidden units
         for (int i = lane; i < N; i += 32) {
             const R si = (R)sv[i];
-            Prod<R> pr{R(1), 0};
-            int cnt = 0;
-            for (int j = 0; j < M; ++j) {
-                pr.m *= R(1) - si * t[j] * T.tau_siteT[(size_t)j * N + i];
-                if (++cnt == RenormEvery<R>::value) {
-                    renorm(pr);
-                    cnt = 0;
-                }
-            }
-            renorm(pr);
+            Prod<R> pr = strided_product<R>(t, T.tau_siteT + i, (size_t)N, si, 0, 1, M);
             const double delta = -2.0 * T.a[i] * (double)si + (double)(T.K_site[i] + prod_log(pr));
             off += -A.h * exp(delta);
         }
@@ -350,27 +427,162 @@ __global__ void __launch_bounds__(128) k_eloc(ElocK<R> P) {
         }
         __syncwarp();
         const double hoff = A.marshall ? -2.0 * A.J : 2.0 * A.J;
-        for (int idx = lane; idx < n; idx += 32) {
-            const int e = list[idx];
-            const int i = T.edges[2 * e], kk = T.edges[2 * e + 1];
-            const R si = (R)sv[i];
-            Prod<R> pr{R(1), 0};
-            int cnt = 0;
-            for (int j = 0; j < M; ++j) {
-                pr.m *= R(1) - si * t[j] * T.tau_edgeT[(size_t)j * E + e];
-                if (++cnt == RenormEvery<R>::value) {
-                    renorm(pr);
-                    cnt = 0;
-                }
+        if (P.units) {
+            for (int idx = 0; idx < n; ++idx) {
+                const int e = list[idx];
+                const int i = T.edges[2 * e], kk = T.edges[2 * e + 1];
+                const R si = (R)sv[i];
+                Prod<R> pr = strided_product<R>(t, T.tau_edge + (size_t)e * M, 1, si, lane, 32, M);
+                pr = warp_prod(pr);
+                const double delta =
+                    -2.0 * (double)si * (T.a[i] - T.a[kk]) + (double)(T.K_edge[e] + prod_log(pr));
+                if (lane == 0) off += hoff * exp(delta);
             }
-            renorm(pr);
-            const double delta =
-                -2.0 * (double)si * (T.a[i] - T.a[kk]) + (double)(T.K_edge[e] + prod_log(pr));
-            off += hoff * exp(delta);
+        } else {
+            for (int idx = lane; idx < n; idx += 32) {
+                const int e = list[idx];
+                const int i = T.edges[2 * e], kk = T.edges[2 * e + 1];
+                const R si = (R)sv[i];
+                Prod<R> pr = strided_product<R>(t, T.tau_edgeT + e, (size_t)E, si, 0, 1, M);
+                const double delta =
+                    -2.0 * (double)si * (T.a[i] - T.a[kk]) + (double)(T.K_edge[e] + prod_log(pr));
+                off += hoff * exp(delta);
+            }
         }
     }
     const double tot = warp_sum(diag + off);
     if (lane == 0) A.eloc[k] = tot;
+}
+
+// ------------------------------------------- sample-batched local energy ---
+// Large M (NK_MIXED, theta given): one CTA of kEW warps holds tanh(theta) of
+// kEG samples in shared memory; every warp takes connections (sites, or
+// edges) in turn, loads each tau row once (16-byte loads, lanes over units)
+// and applies it to all kEG samples, so the tau traffic per ratio term drops
+// kEG-fold.  One warp reduction per (connection, sample).
+constexpr int kEG = 8, kEW = 8;
+
+struct ElocBK {
+    Tables<float> t;
+    ElocArgs a;
+    int t_ld, s_ld;
+};
+
+__global__ void __launch_bounds__(kEW * 32) k_eloc_batched(ElocBK P) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const Tables<float> &T = P.t;
+    const ElocArgs &A = P.a;
+    const int N = T.N, M = T.M, E = T.E;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t k0 = (int64_t)blockIdx.x * kEG;
+    const int G = (int)(A.Ns - k0 < kEG ? A.Ns - k0 : kEG);
+    float *t = reinterpret_cast<float *>(sm);                                    // [kEG][t_ld]
+    int8_t *sv = reinterpret_cast<int8_t *>(sm + (size_t)kEG * P.t_ld * 4);      // [kEG][s_ld]
+    double *part = reinterpret_cast<double *>(sm + (size_t)kEG * P.t_ld * 4 + (size_t)kEG * P.s_ld);  // [kEW][kEG]
+    double *diag = part + kEW * kEG;                                              // [kEG]
+    for (int x = threadIdx.x; x < kEG * N; x += blockDim.x) {
+        const int g = x / N, i = x % N;
+        sv[g * P.s_ld + i] = g < G ? A.s[(size_t)(k0 + g) * N + i] : (int8_t)1;
+    }
+    for (int x = threadIdx.x; x < kEG * M; x += blockDim.x) {
+        const int g = x / M, j = x % M;
+        float tv = 0.f;
+        if (g < G) {
+            const double tj = tanh(A.theta_in[(size_t)(k0 + g) * M + j]);
+            tv = (float)tj;
+            if (A.t_out) A.t_out[(size_t)(k0 + g) * M + j] = tj;
+        }
+        t[g * P.t_ld + j] = tv;
+    }
+    __syncthreads();
+    // diagonal part: warp g sums J s_i s_k over the edges of sample g
+    if (warp < G) {
+        double d = 0.0;
+        const int8_t *s = sv + warp * P.s_ld;
+        for (int e = lane; e < E; e += 32) {
+            const int i = T.edges[2 * e], kk = T.edges[2 * e + 1];
+            if ((unsigned)i < (unsigned)N && (unsigned)kk < (unsigned)N) d += A.J * (double)s[i] * (double)s[kk];
+        }
+        d = warp_sum(d);
+        if (lane == 0) diag[warp] = d;
+    }
+    double off[kEG];
+#pragma unroll
+    for (int g = 0; g < kEG; ++g) off[g] = 0.0;
+    const bool tfim = A.kind == NK_TFIM;
+    const int nconn = tfim ? N : E;
+    const double hoff = A.marshall ? -2.0 * A.J : 2.0 * A.J;
+    for (int c = warp; c < nconn; c += kEW) {
+        int i, kk = -1;
+        const float *tau;
+        float K;
+        if (tfim) {
+            i = c;
+            tau = T.tau_site + (size_t)c * M;
+            K = T.K_site[c];
+        } else {
+            i = T.edges[2 * c];
+            kk = T.edges[2 * c + 1];
+            if ((unsigned)i >= (unsigned)N || (unsigned)kk >= (unsigned)N) continue;
+            tau = T.tau_edge + (size_t)c * M;
+            K = T.K_edge[c];
+        }
+        unsigned active = 0;
+#pragma unroll
+        for (int g = 0; g < kEG; ++g)
+            if (g < G && (tfim || sv[g * P.s_ld + i] != sv[g * P.s_ld + kk])) active |= 1u << g;
+        if (!active) continue;
+        float m[kEG];
+        int ex[kEG];
+        float sg[kEG];
+#pragma unroll
+        for (int g = 0; g < kEG; ++g) {
+            m[g] = 1.f;
+            ex[g] = 0;
+            sg[g] = (float)sv[g * P.s_ld + i];
+        }
+        int cnt = 0;
+        for (int j = 4 * lane; j < M; j += 128) {
+            const float4 uv = __ldg(reinterpret_cast<const float4 *>(tau + j));
+#pragma unroll
+            for (int g = 0; g < kEG; ++g) {
+                if (!(active & (1u << g))) continue;
+                const float4 tv = *reinterpret_cast<const float4 *>(t + g * P.t_ld + j);
+                const float ns = -sg[g];
+                m[g] *= fmaf(ns * tv.x, uv.x, 1.f) * fmaf(ns * tv.y, uv.y, 1.f) * fmaf(ns * tv.z, uv.z, 1.f) *
+                        fmaf(ns * tv.w, uv.w, 1.f);
+            }
+            if (++cnt == 2) {
+#pragma unroll
+                for (int g = 0; g < kEG; ++g) {
+                    int k;
+                    m[g] = frexpf(m[g], &k);
+                    ex[g] += k;
+                }
+                cnt = 0;
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < kEG; ++g) {
+            if (!(active & (1u << g))) continue;
+            Prod<float> p{m[g], ex[g]};
+            renorm(p);
+            p = warp_prod(p);
+            double d0 = tfim ? -2.0 * T.a[i] * (double)sg[g] : -2.0 * (double)sg[g] * (T.a[i] - T.a[kk]);
+            const double delta = d0 + (double)(K + prod_log(p));
+            off[g] += (tfim ? -A.h : hoff) * exp(delta);
+        }
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int g = 0; g < kEG; ++g) part[warp * kEG + g] = off[g];
+    }
+    __syncthreads();
+    if (threadIdx.x < G) {
+        double tot = diag[threadIdx.x];
+        for (int w = 0; w < kEW; ++w) tot += part[w * kEG + threadIdx.x];
+        A.eloc[k0 + threadIdx.x] = tot;
+    }
 }
 
 // --------------------------------------------------------- batched theta ---
@@ -494,12 +706,12 @@ cudaError_t launch_sweep(const Tables<R> &t, const SweepArgs &a, cudaStream_t st
     }
     P.t_bytes = align16<R>(t.M * (int)sizeof(R));
     P.warp_bytes = P.t_bytes + align16<R>(t.N);
+    P.vec4 = sizeof(R) == 4 && (t.M % 4) == 0;
     int wpb = 4;
     while (wpb > 1 && (size_t)wpb * P.warp_bytes > 200 * 1024) wpb >>= 1;
     size_t smem = (size_t)wpb * P.warp_bytes;
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
-    cudaError_t err = cudaFuncSetAttribute(k_sweep<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smem);
+    cudaError_t err = nk::allow_max_dynamic_smem((const void *)k_sweep<R>);
     if (err != cudaSuccess) return err;
     unsigned grid = (unsigned)((a.C + wpb - 1) / wpb);
     const int slot = prof_begin(NK_PROF_SWEEP, st);
@@ -512,11 +724,39 @@ template cudaError_t launch_sweep<double>(const Tables<double> &, const SweepArg
 template cudaError_t launch_sweep<float>(const Tables<float> &, const SweepArgs &, cudaStream_t);
 
 template <typename R>
+cudaError_t launch_eloc_batched(const Tables<R> &, const ElocArgs &, cudaStream_t) {
+    return cudaErrorNotSupported;
+}
+
+template <>
+cudaError_t launch_eloc_batched<float>(const Tables<float> &t, const ElocArgs &a, cudaStream_t st) {
+    ElocBK P;
+    P.t = t;
+    P.a = a;
+    P.t_ld = (t.M + 3) / 4 * 4;
+    P.s_ld = (t.N + 15) / 16 * 16;
+    const size_t smem = (size_t)kEG * P.t_ld * 4 + (size_t)kEG * P.s_ld + (size_t)(kEW * kEG + kEG) * 8;
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
+    cudaError_t err = nk::allow_max_dynamic_smem((const void *)k_eloc_batched);
+    if (err != cudaSuccess) return err;
+    const unsigned grid = (unsigned)((a.Ns + kEG - 1) / kEG);
+    const int slot = prof_begin(NK_PROF_ELOC, st);
+    (k_eloc_batched<<<grid, kEW * 32, smem, st>>>(P), nk::note_launch());
+    const double conn = a.kind == NK_TFIM ? (double)t.N : 0.5 * (double)t.E;
+    prof_end(slot, st, (double)a.Ns * conn * (double)t.M);
+    return cudaGetLastError();
+}
+
+template <typename R>
 cudaError_t launch_eloc(const Tables<R> &t, const ElocArgs &a, cudaStream_t st) {
     if (a.Ns <= 0) return cudaSuccess;
+    if (sizeof(R) == 4 && a.theta_in && t.M >= kUnitsMappingM && (t.M % 4) == 0 &&
+        (size_t)kEG * ((t.M + 3) / 4 * 4) * 4 + (size_t)kEG * ((t.N + 15) / 16 * 16) + 1024 <= 227 * 1024)
+        return launch_eloc_batched<R>(t, a, st);
     ElocK<R> P;
     P.t = t;
     P.a = a;
+    P.units = t.M >= kUnitsMappingM ? 1 : 0;
     P.t_bytes = align16<R>(t.M * (int)sizeof(R));
     P.s_bytes = align16<R>(t.N);
     P.warp_bytes = P.t_bytes + P.s_bytes + align16<R>(4 * (a.kind == NK_HEIS ? t.E : 0));
@@ -524,8 +764,7 @@ cudaError_t launch_eloc(const Tables<R> &t, const ElocArgs &a, cudaStream_t st) 
     while (wpb > 1 && (size_t)wpb * P.warp_bytes > 200 * 1024) wpb >>= 1;
     size_t smem = (size_t)wpb * P.warp_bytes;
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
-    cudaError_t err = cudaFuncSetAttribute(k_eloc<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smem);
+    cudaError_t err = nk::allow_max_dynamic_smem((const void *)k_eloc<R>);
     if (err != cudaSuccess) return err;
     unsigned grid = (unsigned)((a.Ns + wpb - 1) / wpb);
     const int slot = prof_begin(NK_PROF_ELOC, st);

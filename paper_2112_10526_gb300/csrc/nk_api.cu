@@ -12,16 +12,6 @@
 #include "../../include/nk.h"
 #include "nk_internal.h"
 
-struct nk_ctx {
-    int device;
-    char *ws;
-    size_t ws_size;
-    int *host_flags;  // pinned: [0] done, [1] iterations
-    double *host_vals;  // pinned
-    cudaStream_t side;  // high-priority stream for the Cholesky look-ahead
-    cudaEvent_t ev[2];
-    int *tc_err;        // device: sticky code of the first tensor-core time-out
-};
 
 namespace {
 
@@ -65,7 +55,12 @@ struct DeviceGuard {
     }
 };
 
+// Plan-only mode (this thread): entry points check arguments, count their
+// workspace into ctx->plan_bytes and return without touching the device.
+thread_local bool g_plan_only = false;
+
 bool is_device_ptr(const void *p) {
+    if (g_plan_only) return p != nullptr;
     if (!p) return false;
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -121,6 +116,10 @@ nk_status with_workspace(nk_ctx *ctx, Body body) {
     Carver count{nullptr};
     nk_status st = body(count, false);
     if (st != NK_OK) return st;
+    if (g_plan_only) {
+        ctx->plan_bytes = count.off > ctx->plan_bytes ? count.off : ctx->plan_bytes;
+        return NK_OK;
+    }
     st = ensure_ws(ctx, count.off);
     if (st != NK_OK) return st;
     Carver real{ctx->ws};
@@ -439,6 +438,7 @@ nk_status check_solver(int solver, double eps, double tol, int maxiter) {
 namespace nk {
 // Lets other translation units of the library report through nk_last_error.
 nk_status report_error(nk_status code, const char *msg) { return fail(code, "%s", msg); }
+void set_plan_only(bool on) { g_plan_only = on; }
 }  // namespace nk
 
 // =================================================================== ABI ===

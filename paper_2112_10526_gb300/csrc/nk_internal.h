@@ -8,7 +8,23 @@
 
 #include "../../include/nk.h"
 
+// The context behind the opaque nk_ctx handle.
+struct nk_ctx {
+    int device;
+    char *ws;
+    size_t ws_size;
+    int *host_flags;    // pinned: [0] done, [1] iterations, [2..3] factor status, [4] tc error
+    double *host_vals;  // pinned
+    cudaStream_t side;  // high-priority stream for the Cholesky look-ahead
+    cudaEvent_t ev[2];
+    int *tc_err;        // device: sticky code of the first tensor-core time-out
+    size_t plan_bytes;  // workspace counted by plan-only calls
+};
+
 namespace nk {
+
+// Plan-only mode for the calling thread (see nk_api.cu).
+void set_plan_only(bool on);
 
 // Kernel timing hooks (prof.cu).  prof_begin returns a slot (or -1 when
 // timing is off); prof_end closes it and adds `work` to the class.
@@ -17,6 +33,12 @@ int prof_begin(int cls, cudaStream_t st);
 nk_status report_error(nk_status code, const char *msg);
 // Process-wide count of kernel launches issued by the library.
 void note_launch(long long n = 1);
+// Raises the dynamic shared-memory limit of a kernel to the device's opt-in
+// maximum, once per (kernel, device).  The limit is process-wide state, so a
+// per-launch value would race between host threads launching the same kernel
+// with different sizes; a constant maximum does not (occupancy follows the
+// size given at launch, not this limit).
+cudaError_t allow_max_dynamic_smem(const void *func);
 void prof_end(int slot, cudaStream_t st, double work);
 
 // Per-parameter tables of the flip-ratio identity (see k_rbm.cu).  All

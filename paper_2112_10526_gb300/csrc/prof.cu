@@ -4,6 +4,7 @@
 
 #include <atomic>
 #include <mutex>
+#include <utility>
 #include <vector>
 
 #include "../../include/nk.h"
@@ -29,6 +30,24 @@ std::atomic<long long> g_launches{0};
 namespace nk {
 
 void note_launch(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+cudaError_t allow_max_dynamic_smem(const void *func) {
+    static std::mutex mu;
+    static std::vector<std::pair<const void *, int>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto &d : done)
+        if (d.first == func && d.second == dev) return cudaSuccess;
+    int optin = 0;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e != cudaSuccess) return e;
+    done.emplace_back(func, dev);
+    return cudaSuccess;
+}
 
 int prof_begin(int cls, cudaStream_t st) {
     std::lock_guard<std::mutex> lk(g_mu);

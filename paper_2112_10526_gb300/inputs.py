@@ -81,3 +81,36 @@ WORKLOADS = {
                          chains=8192, per_chain=8, discard=16, seed=5, diag_shift=0.01, lr=0.01,
                          solver="cg"),
 }
+
+
+def serve_requests(n: int = 512, seed: int = 4) -> list:
+    """Seeded serving mix (each request: local-energy expectation + one SR
+    step): lattice uniform over the periodic Ising chains N in {16, 32, 64,
+    128, 256} (J = h = 1) and the Marshall-signed Heisenberg squares L in
+    {4, 6, 8, 12, 16}; alpha uniform in {1, 2, 4}; 1024 chains x U{1..16}
+    samples; parameters seeded 40000 + r; dense Cholesky when Np <= 1024,
+    else CG."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for r in range(n):
+        lat = int(rng.integers(0, 10))
+        alpha = int(rng.choice([1, 2, 4]))
+        per_chain = int(rng.integers(1, 17))
+        if lat < 5:
+            N = [16, 32, 64, 128, 256][lat]
+            ham, rule = tfim_chain(N, 1.0, 1.0), "local"
+        else:
+            L = [4, 6, 8, 12, 16][lat - 5]
+            N = L * L
+            ham, rule = heis_square(L, 1.0, True), "exchange"
+        M = alpha * N
+        Np = N + M + M * N
+        out.append(dict(index=r, N=N, M=M, alpha=alpha, ham=ham, rule=rule, chains=1024, per_chain=per_chain,
+                        seed=40000 + r, solver="cholesky" if Np <= 1024 else "cg"))
+    return out
+
+
+def poisson_arrivals(n: int, rate: float, seed: int = 4) -> np.ndarray:
+    """Arrival times (s) of a Poisson process of the given rate."""
+    rng = np.random.default_rng(seed)
+    return np.cumsum(rng.exponential(1.0 / rate, size=n))

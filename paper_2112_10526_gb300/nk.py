@@ -69,6 +69,30 @@ class nk_sr_cfg(ctypes.Structure):
                 ("cg_tol", ctypes.c_double), ("seed", ctypes.c_uint64), ("stream_id", ctypes.c_uint32)]
 
 
+NK_REQ_EXPECT, NK_REQ_SR_STEP = 0, 1
+
+
+class nk_request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("N", ctypes.c_int32), ("M", ctypes.c_int32),
+                ("params", ctypes.c_void_p), ("ham_kind", ctypes.c_int32), ("J", ctypes.c_double),
+                ("h", ctypes.c_double), ("marshall", ctypes.c_int32), ("n_edges", ctypes.c_int32),
+                ("edges", ctypes.c_void_p), ("n_chains", ctypes.c_int32), ("cfg", nk_sr_cfg)]
+
+
+class nk_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("slot", ctypes.c_int32), ("energy", ctypes.c_double),
+                ("variance", ctypes.c_double), ("error", ctypes.c_double), ("acceptance", ctypes.c_double),
+                ("cg_iters", ctypes.c_double), ("solver_status", ctypes.c_double), ("queue_ms", ctypes.c_double),
+                ("run_ms", ctypes.c_double), ("latency_ms", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
+                ("message", ctypes.c_char * 128)]
+
+
+class nk_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("inflight", ctypes.c_int64), ("queued", ctypes.c_int64), ("hbm_in_use", ctypes.c_size_t),
+                ("hbm_budget", ctypes.c_size_t), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double)]
+
+
 SR_STATS_FIELDS = ["energy", "variance", "error", "acceptance", "cg_iters", "cg_residual", "f_norm",
                    "delta_norm", "solver_status"]
 SR_STATS_DOUBLES = len(SR_STATS_FIELDS)
@@ -103,6 +127,12 @@ def lib():
         "nk_force": [P, ctypes.POINTER(nk_rbm), i32, P, i64, P, P, P],
         "nk_qgt_matvec": [P, ctypes.POINTER(nk_qgt), f64, P, P, P],
         "nk_ctx_error": [P, ctypes.POINTER(ctypes.c_int32), P],
+        "nk_server_create": [i32, ctypes.c_size_t, i32, ctypes.POINTER(P)],
+        "nk_server_submit": [P, ctypes.POINTER(nk_request), P, ctypes.POINTER(ctypes.c_uint64)],
+        "nk_server_poll": [P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(nk_result)],
+        "nk_server_wait": [P, ctypes.c_uint64, ctypes.POINTER(nk_result)],
+        "nk_server_stats_get": [P, ctypes.POINTER(nk_server_stats)],
+        "nk_server_destroy": [P],
         "nk_tc_gemm": [P, i64, i64, i32, P, i64, P, i64, i32, i32, i32, P, i64, P],
         "nk_sr_solve": [P, ctypes.POINTER(nk_rbm), i32, P, i64, P, i32, f64, f64, i32, P,
                         ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double), P],
@@ -124,6 +154,8 @@ def lib():
     L.nk_prof_read.restype = ctypes.c_int32
     L.nk_launch_count.argtypes = []
     L.nk_launch_count.restype = ctypes.c_int64
+    L.nk_request_bytes.argtypes = [ctypes.POINTER(nk_request)]
+    L.nk_request_bytes.restype = ctypes.c_size_t
     _lib = L
     return L
 
@@ -359,3 +391,94 @@ def nk_prof_read(cls):
 
 def nk_launch_count():
     return int(lib().nk_launch_count())
+
+
+# ------------------------------------------------------------------ serving --
+
+def make_request(kind, N, M, params, ham, n_chains, cfg):
+    """An nk_request for host arrays: params float64 [Np], ham dict with int32
+    edges [E, 2] (numpy).  The arrays must stay alive until submission."""
+    import numpy as np
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    e = np.ascontiguousarray(ham["edges"], dtype=np.int32).reshape(-1, 2)
+    req = nk_request(NK_REQ_SR_STEP if kind in ("sr_step", NK_REQ_SR_STEP) else NK_REQ_EXPECT, int(N), int(M),
+                     p.ctypes.data, KIND[ham["kind"]], float(ham["J"]), float(ham.get("h", 0.0)),
+                     int(bool(ham.get("marshall", False))), int(e.shape[0]), e.ctypes.data, int(n_chains), cfg)
+    req._keep = (p, e)
+    return req
+
+
+def nk_request_bytes(req):
+    return int(lib().nk_request_bytes(ctypes.byref(req)))
+
+
+def nk_server_create(device, hbm_budget, slots):
+    h = ctypes.c_void_p()
+    _check(lib().nk_server_create(int(device), int(hbm_budget), int(slots), ctypes.byref(h)))
+    return h
+
+
+def nk_server_submit(srv, req, params_out=None):
+    rid = ctypes.c_uint64()
+    out = None if params_out is None else params_out.ctypes.data_as(ctypes.c_void_p)
+    _check(lib().nk_server_submit(srv, ctypes.byref(req), out, ctypes.byref(rid)))
+    return int(rid.value)
+
+
+def _result_dict(r):
+    d = {f: getattr(r, f) for f, _ in nk_result._fields_}
+    d["message"] = d["message"].decode(errors="replace")
+    return d
+
+
+def nk_server_poll(srv, rid):
+    done = ctypes.c_int32()
+    r = nk_result()
+    _check(lib().nk_server_poll(srv, ctypes.c_uint64(rid), ctypes.byref(done), ctypes.byref(r)))
+    return _result_dict(r) if done.value else None
+
+
+def nk_server_wait(srv, rid):
+    r = nk_result()
+    _check(lib().nk_server_wait(srv, ctypes.c_uint64(rid), ctypes.byref(r)))
+    return _result_dict(r)
+
+
+def nk_server_stats_get(srv):
+    st = nk_server_stats()
+    _check(lib().nk_server_stats_get(srv, ctypes.byref(st)))
+    return {f: getattr(st, f) for f, _ in nk_server_stats._fields_}
+
+
+def nk_server_destroy(srv):
+    _check(lib().nk_server_destroy(srv))
+
+
+class Server:
+    """Thin owner of an nk_server handle."""
+
+    def __init__(self, device=0, hbm_budget=32 << 30, slots=8):
+        self.handle = nk_server_create(device, hbm_budget, slots)
+
+    def submit(self, req, params_out=None):
+        return nk_server_submit(self.handle, req, params_out)
+
+    def wait(self, rid):
+        return nk_server_wait(self.handle, rid)
+
+    def poll(self, rid):
+        return nk_server_poll(self.handle, rid)
+
+    def stats(self):
+        return nk_server_stats_get(self.handle)
+
+    def close(self):
+        if self.handle:
+            nk_server_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -68,3 +68,25 @@ def test_null_arguments_rejected_without_touching_a_device(libnk):
         assert code in (-1, -2) and not out.value
     else:
         libnk.nk_ctx_destroy(out)
+
+
+def test_request_bytes_plan_only_without_gpu(libnk):
+    """The admission estimate is a plan-only pass: it needs no GPU, grows
+    with the sample count and counts the Ns x Ns factor of the sample-space
+    solve."""
+    import numpy as np
+    from paper_2112_10526_gb300 import inputs as I
+    from paper_2112_10526_gb300 import nk
+
+    def req(ns, solver):
+        N, M = 100, 200
+        cfg = nk.make_cfg("exchange", "mixed", solver, 0, ns, 0.01, 0.01, 1)
+        return nk.make_request("sr_step", N, M, I.rbm_params(N, M, 1), I.heis_square(10), 1024, cfg)
+
+    a = nk.nk_request_bytes(req(1, "cg"))
+    b = nk.nk_request_bytes(req(8, "cg"))
+    c = nk.nk_request_bytes(req(8, "cholesky_samplespace"))
+    if a == 0:
+        pytest.skip("no CUDA driver to create the planning context")
+    assert b > a > 0
+    assert c >= b + 8192 * 8192 * 8

@@ -305,3 +305,32 @@ def test_invalid_arguments_are_rejected(ctx):
     assert ei.value.code == nk.NK_ERR_INVALID_ARG
     with pytest.raises(nk.NkError):
         nk.nk_chains_init(ctx, 5, 3, "exchange", 1, 0, torch.empty((3, 5), dtype=torch.int8, device=dev()))
+
+
+def test_sr_trajectory_config1_50_iterations(ctx):
+    """Tutorial workload, 50 VMC + SR iterations on the FP64 path (periodic TFIM
+    chain N = 16, J = h = 1, alpha = 1, 16 chains x 64 samples, 16 discarded
+    sweeps, eps = lr = 0.01, dense Cholesky): the energy trajectory equals the
+    oracle's on the same Philox streams to 1e-8 relative, and every energy
+    respects the variational bound E >= E0 - 4 sigma with E0 = -2/sin(pi/32)."""
+    from oracle import exact
+    N = M = 16
+    steps = 50
+    p0, s0, ham, out = _sr_run(ctx, N, M, lambda: I.tfim_chain(16), "local", 16, 16, 64, 1, "cholesky",
+                               0.01, 0.01, steps)
+    e0 = exact.tfim_free_fermion_e0(16)
+    p, s, sweep0 = p0, s0, 0
+    for it in range(steps):
+        nd = 16 if it == 0 else 0
+        ref = oracle.sr_step(p, N, M, ham, "local", s, sweep0, nd, 64, 1, 0, diag_shift=0.01, lr=0.01,
+                             solver="cholesky")
+        sweep0 += nd + 64
+        g = out[it]["stats"]
+        assert abs(g["energy"] - ref["stats"]["mean"]) <= 1e-8 * abs(ref["stats"]["mean"])
+        assert g["energy"] >= e0 - 4 * g["error"]
+        p, s = ref["params"], ref["state"]
+        np.testing.assert_array_equal(out[it]["state"], s)
+    # the optimisation moves down towards E0
+    first = np.mean([o["stats"]["energy"] for o in out[:5]])
+    last = np.mean([o["stats"]["energy"] for o in out[-5:]])
+    assert last < first
