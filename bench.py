@@ -427,7 +427,7 @@ def run_serve(n_requests, slots, budget_gb, device=0):
             "failed": failed + st_closed["failed"], "failure_codes": codes,
             "failures": [(r["status"], r["message"]) for r in list(res) + list(res_open) if r["status"] != 0][:4],
             "mix": "Ising chains N in {16..256}, Heisenberg L in {4..16}, alpha in {1,2,4}, "
-                   "1024 chains x U{1..16} samples, NK_MIXED, Cholesky if Np <= 1024 else CG (<= 200 it)"}
+                   "1024 chains x U{1..16} samples, NK_MIXED, Cholesky if Np <= 4096 else CG (<= 200 it)"}
 
 
 def main():

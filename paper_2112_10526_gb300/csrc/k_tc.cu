@@ -16,19 +16,20 @@
 // dropped terms are below 2^-56 of K max|a| max|b|: FP64-level accuracy.
 // S = 3 gives about FP32 accuracy (24 bits per operand).
 //
-// Kernel shape: one 128 x 64 output tile per CTA, K = 64.  Thread 0 loads the
-// S slices of the A rows (128 x 64) and of the B rows (64 x 64) with TMA
-// (3-D tensor maps [S][rows][64] BF16, 128-byte swizzle) onto one mbarrier,
-// then issues the S(S+1)/2 x 4 tcgen05.mma (M = 128, N = 64, K = 16) into
-// S accumulators of 64 TMEM columns each, and commits to a second mbarrier;
-// the four warps then read their 32 TMEM lanes (= tile rows) and update C.
-// Every wait is bounded by the global timer; on time-out the kernel records
-// an error code, frees its TMEM and returns.
+// Kernel shape: a persistent CTA per SM walks a range of 128 x 32 output
+// tiles (K = 64): TMA brings the S slices of the A rows (once per tile row)
+// and of the B rows (3-D tensor maps [S][rows][64] BF16, 128-byte swizzle),
+// one thread issues the S(S+1)/2 x 4 tcgen05.mma (M = 128, N = 32, K = 16)
+// into S accumulators of 32 TMEM columns, double-buffered, and eight warps
+// drain the other buffer and update C.  Every wait is bounded by the global
+// timer; on time-out the kernel records an error code, lets its copies and
+// MMAs in flight finish, frees its TMEM and returns.
 
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "nk_common.cuh"
@@ -40,12 +41,10 @@ namespace nk {
 namespace {
 
 constexpr int kTileM = 128;
-constexpr int kTileN = 64;
 constexpr int kTileK = 64;
 constexpr int kMaxSlices = 7;
 constexpr uint32_t kTmemCols = 512;
 constexpr int kABytes = kTileM * kTileK * 2;  // one slice of the A tile
-constexpr int kBBytes = kTileN * kTileK * 2;  // one slice of the B tile
 
 // ---------------------------------------------------------------- slicing ---
 
@@ -94,6 +93,24 @@ __global__ void k_slice_rows(const double *__restrict__ A, int64_t lda, int64_t 
 }
 
 // ------------------------------------------------------------- the GEMM ---
+//
+// Warp-specialised kernel over output strips: a CTA owns up to kChunk
+// consecutive 128 x 32 tiles of one tile row (a 128 x 256 strip), keeps the
+// S slices of its 128 A rows resident, and pipelines the tiles:
+//   warp 0 (one thread): TMA producer, A slices once, B slices per tile into
+//     one of two buffers;
+//   warp 1 (one thread): MMA issuer, S(S+1)/2 slice products x 4 K-steps per
+//     tile into one of two TMEM accumulator sets (S x 32 columns each), so
+//     that the MMAs of tile i+1 run while tile i is drained;
+//   warps 2-17: epilogue; warp w owns tile rows 32 (w % 4) .. +31 (its TMEM
+//     lane quarter) and 8 columns, loads its C entries a tile ahead, and
+//     turns the S accumulators into FP64 by exact integer recombination
+//     before writing C back.
+// Strips (lower triangle only when `lower`) are numbered row by row.  CTAs
+// are short-lived on purpose: kernels of a higher-priority stream (the
+// Cholesky look-ahead) get SMs as strips retire.  mbarriers hand buffers
+// between the roles; every wait is bounded by the global timer and gives up
+// when another role of the CTA has aborted.
 
 struct OzArgs {
     int64_t rows, cols;   // output rows (A rows) and columns (B rows)
@@ -104,31 +121,88 @@ struct OzArgs {
     int mode;             // 0: C = R, 1: C -= R, 2: C += R
     int lower;            // only entries with col <= row (tiles above are skipped)
     int *err;
+    int64_t n_nb;         // tile columns
 };
 
-constexpr int kOzThreads = 256;
-constexpr int kOutLd = kTileN + 1;  // staged output tile [128][65] doubles
+constexpr int kPN = 32;                      // tile columns
+constexpr int kChunk = 8;                    // tiles per strip
+constexpr int kPEpiWarps = 16;
+constexpr int kPThreads = 64 + 32 * kPEpiWarps;        // producer, MMA issuer, epilogue warps
+constexpr int kPColsPerWarp = kPN / (kPEpiWarps / 4);  // 8
+constexpr int kPBBytes = kPN * kTileK * 2;   // one slice of the B tile (4 KB)
+constexpr uint32_t kPAccCols = 256;          // TMEM columns per accumulator set
 
-__global__ void __launch_bounds__(kOzThreads, 1)
+__host__ __device__ inline int64_t oz_row_tiles(int64_t n_nb, bool lower, int64_t mb) {
+    if (!lower) return n_nb;
+    const int64_t last = (mb * kTileM + kTileM - 1) / kPN + 1;
+    return last < n_nb ? last : n_nb;
+}
+
+__host__ __device__ inline int64_t oz_row_strips(int64_t n_nb, bool lower, int64_t mb) {
+    return (oz_row_tiles(n_nb, lower, mb) + kChunk - 1) / kChunk;
+}
+
+// The S(S+1)/2 x 4 MMAs of one tile: level g = s + t (2 .. S+1) collects the
+// products of A slice s and B slice t in TMEM columns dbase + (g - 2) 32.
+// SS > 0 fixes S at compile time (fully unrolled issue).
+template <int SS>
+__device__ __forceinline__ void issue_tile(uint32_t dbase, const uint64_t (&da)[kMaxSlices],
+                                           const uint64_t (&db)[kMaxSlices], uint32_t idesc, int S_rt) {
+    const int S = SS > 0 ? SS : S_rt;
+#pragma unroll
+    for (int g = 2; g <= (SS > 0 ? SS : kMaxSlices) + 1; ++g) {
+        if (g > S + 1) break;
+        const uint32_t dcol = dbase + (uint32_t)((g - 2) * kPN);
+        uint32_t acc = 0;
+#pragma unroll
+        for (int sa = 1; sa < g; ++sa) {
+            const int sb = g - sa;
+            if (sa > S || sb > S) continue;
+#pragma unroll
+            for (int kk = 0; kk < kTileK / 16; ++kk) {
+                // advance 16 BF16 = 32 bytes along K inside the swizzle atom
+                umma_bf16(dcol, da[sa - 1] + (uint64_t)(kk * 2), db[sb - 1] + (uint64_t)(kk * 2), idesc, acc);
+                acc = 1;
+            }
+        }
+    }
+}
+
+template <int SS>
+__global__ void __launch_bounds__(kPThreads, 1)
     k_ozaki_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, OzArgs a) {
     extern __shared__ unsigned char smem_raw[];
-    const int64_t m0 = (int64_t)blockIdx.y * kTileM;
-    const int64_t n0 = (int64_t)blockIdx.x * kTileN;
-    if (a.lower && n0 > m0 + kTileM - 1) return;
-    // 1024-byte aligned operand area (128-byte swizzle atoms)
     const uint32_t base = smem_u32(smem_raw);
     unsigned char *ops = smem_raw + ((1024 - (base & 1023)) & 1023);
-    unsigned char *sA = ops;                                  // [S][128][64] bf16
-    unsigned char *sB = ops + (size_t)kMaxSlices * kABytes;   // [S][64][64] bf16
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sB + (size_t)kMaxSlices * kBBytes);  // [0] tma, [1] mma
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2);
-    int *abort_flag = reinterpret_cast<int *>(tslot + 1);
+    unsigned char *sA = ops;                                            // [S][128][64] bf16
+    unsigned char *sB = ops + (size_t)kMaxSlices * kABytes;             // [2][S][32][64] bf16
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sB + (size_t)2 * kMaxSlices * kPBBytes);
+    uint64_t *a_full = bars, *b_full = bars + 2, *b_empty = bars + 4;
+    uint64_t *acc_full = bars + 6, *acc_empty = bars + 8;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 10);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tslot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int S = a.S;
+    const int S = SS > 0 ? SS : a.S;
+    // strip -> tile row mb, first tile column nb0, tile count
+    int64_t mb = 0, rem = blockIdx.x;
+    for (;;) {
+        const int64_t ns = oz_row_strips(a.n_nb, a.lower != 0, mb);
+        if (rem < ns) break;
+        rem -= ns;
+        ++mb;
+    }
+    const int64_t nb0 = rem * kChunk, in_row = oz_row_tiles(a.n_nb, a.lower != 0, mb);
+    const int count = (int)(in_row - nb0 < kChunk ? in_row - nb0 : kChunk);
+    const int64_t m0 = mb * kTileM;
 
     if (threadIdx.x == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
+        mbar_init(a_full, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&b_full[b], 1);
+            mbar_init(&b_empty[b], 1);
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], kPEpiWarps);
+        }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -137,118 +211,150 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
+    auto fail = [&](int code) {
+        *abort_flag = 1;
+        atomicExch(a.err, code);
+    };
 
-    if (threadIdx.x == 0) {
-        mbar_expect_tx(&bars[0], (uint32_t)S * (kABytes + kBBytes));
-        for (int s = 0; s < S; ++s) {
-            tma_load_3d(sA + (size_t)s * kABytes, &mapA, &bars[0], 0, (int)m0, s);
-            tma_load_3d(sB + (size_t)s * kBBytes, &mapB, &bars[0], 0, (int)n0, s);
+    if (warp == 0 && lane == 0) {
+        // ---------------------------------------------------------- producer
+        uint32_t fills0 = 0, fills1 = 0;  // loads issued into B buffer 0 / 1
+        mbar_expect_tx(a_full, (uint32_t)S * kABytes);
+        for (int s = 0; s < S; ++s) tma_load_3d(sA + (size_t)s * kABytes, &mapA, a_full, 0, (int)m0, s);
+        for (int i = 0; i < count && !*abort_flag; ++i) {
+            const int b = i & 1;
+            const uint32_t fills = b ? fills1 : fills0;
+            if (fills > 0 && !mbar_wait_or_abort(&b_empty[b], (fills - 1) & 1, abort_flag)) {
+                fail(12);
+                break;
+            }
+            mbar_expect_tx(&b_full[b], (uint32_t)S * kPBBytes);
+            for (int s = 0; s < S; ++s)
+                tma_load_3d(sB + (size_t)(b * kMaxSlices + s) * kPBBytes, &mapB, &b_full[b], 0,
+                            (int)((nb0 + i) * kPN), s);
+            if (b)
+                ++fills1;
+            else
+                ++fills0;
         }
-        if (!mbar_wait(&bars[0], 0)) {
-            *abort_flag = 1;
-            atomicExch(a.err, 1);
-        } else {
-            tc_fence_after();
-            const uint32_t idesc = idesc_bf16(kTileM, kTileN);
-            for (int g = 2; g <= S + 1; ++g) {
-                const uint32_t dcol = tmem + (uint32_t)((g - 2) * kTileN);
-                bool first = true;
-                for (int s = 1; s < g; ++s) {
-                    const int t = g - s;
-                    if (s > S || t > S) continue;
-                    const uint64_t da = sw128_desc(sA + (size_t)(s - 1) * kABytes);
-                    const uint64_t db = sw128_desc(sB + (size_t)(t - 1) * kBBytes);
+        if (*abort_flag) {
+            // let the copies in flight land before the CTA exits
+            mbar_wait(a_full, 0);
+            if (fills0 > 0) mbar_wait(&b_full[0], (fills0 - 1) & 1);
+            if (fills1 > 0) mbar_wait(&b_full[1], (fills1 - 1) & 1);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ------------------------------------------------------- MMA issuer
+        int issued = 0;
+        const uint32_t idesc = idesc_bf16(kTileM, kPN);
+        uint64_t da[kMaxSlices], db0[kMaxSlices], db1[kMaxSlices];
 #pragma unroll
-                    for (int kk = 0; kk < kTileK / 16; ++kk) {
-                        // advance 16 BF16 = 32 bytes along K inside the swizzle atom
-                        umma_bf16(dcol, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
-                                  first ? 0u : 1u);
-                        first = false;
+        for (int s = 0; s < kMaxSlices; ++s) {
+            da[s] = sw128_desc(sA + (size_t)s * kABytes);
+            db0[s] = sw128_desc(sB + (size_t)s * kPBBytes);
+            db1[s] = sw128_desc(sB + (size_t)(kMaxSlices + s) * kPBBytes);
+        }
+        if (!mbar_wait_or_abort(a_full, 0, abort_flag)) fail(13);
+        for (int i = 0; i < count && !*abort_flag; ++i) {
+            const int b = i & 1;
+            const uint32_t use = (uint32_t)(i >> 1);
+            if (!mbar_wait_or_abort(&b_full[b], use & 1, abort_flag)) {
+                fail(14);
+                break;
+            }
+            if (use > 0 && !mbar_wait_or_abort(&acc_empty[b], (use - 1) & 1, abort_flag)) {
+                fail(15);
+                break;
+            }
+            tc_fence_after();
+            if (b)
+                issue_tile<SS>(tmem + kPAccCols, da, db1, idesc, S);
+            else
+                issue_tile<SS>(tmem, da, db0, idesc, S);
+            umma_commit(&acc_full[b]);
+            umma_commit(&b_empty[b]);
+            ++issued;
+        }
+        if (*abort_flag && issued > 0) {
+            // the MMAs in flight must finish before the TMEM is released
+            const int last = issued - 1;
+            mbar_wait(&acc_full[last & 1], (uint32_t)(last >> 1) & 1);
+        }
+    } else if (warp >= 2) {
+        // --------------------------------------------------------- epilogue
+        const int q = warp & 3;                 // TMEM lane quarter = tile rows 32q .. 32q + 31
+        const int c0 = ((warp - 2) >> 2) * kPColsPerWarp;  // the warp's 8 tile columns
+        const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+        const int64_t row = m0 + q * 32 + lane;
+        const bool row_ok = row < a.rows;
+        const int ei = row_ok ? a.expA[row] : 0;
+        double *crow = a.C + (size_t)(row_ok ? row : 0) * a.ldc;
+        auto on = [&](int64_t col) { return row_ok && col < a.cols && !(a.lower && col > row); };
+        auto load_c = [&](int i, double (&cv)[kPColsPerWarp]) {
+            const int64_t col0 = (nb0 + i) * kPN + c0;
+#pragma unroll
+            for (int j = 0; j < kPColsPerWarp; ++j)
+                cv[j] = (a.mode != 0 && on(col0 + j)) ? crow[col0 + j] : 0.0;
+        };
+        // column exponents (lane & 7 holds column c0 + (lane & 7)), broadcast by shuffles
+        auto load_f = [&](int i) {
+            const int64_t col = (nb0 + i) * kPN + c0 + (lane & 7);
+            return col < a.cols ? a.expB[col] : 0;
+        };
+        double cv[kPColsPerWarp], cn[kPColsPerWarp];
+        load_c(0, cv);
+        int fj_next = load_f(0);
+        for (int i = 0; i < count; ++i) {
+            const int b = i & 1;
+            const uint32_t use = (uint32_t)(i >> 1);
+            const int fj_lane = fj_next;
+            // the next tile's C and exponents are in flight during this tile
+            if (i + 1 < count) {
+                load_c(i + 1, cn);
+                fj_next = load_f(i + 1);
+            }
+            int ok = 1;
+            if (lane == 0) ok = mbar_wait_or_abort(&acc_full[b], use & 1, abort_flag) ? 1 : 0;
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) {
+                if (lane == 0) fail(16);
+                break;
+            }
+            tc_fence_after();
+            const int64_t col0 = (nb0 + i) * kPN + c0;
+#pragma unroll
+            for (int c4 = 0; c4 < kPColsPerWarp; c4 += 4) {
+                uint32_t r[kMaxSlices][4];
+#pragma unroll
+                for (int gi = 0; gi < kMaxSlices; ++gi)
+                    if (gi < S)
+                        tmem_ld4(tmem + (uint32_t)b * kPAccCols + lane_base + (uint32_t)(gi * kPN + c0 + c4), r[gi]);
+                tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    int d[kMaxSlices];
+#pragma unroll
+                    for (int gi = 0; gi < kMaxSlices; ++gi)
+                        d[gi] = gi < S ? __float2int_rn(__uint_as_float(r[gi][j])) : 0;
+                    // V = sum_g D_g 2^(8 (8 - g)) = hi 2^32 + lo exactly: levels g = 2 .. 4
+                    // weigh 2^(8 (4 - g)) in hi, g = 5 .. 8 weigh 2^(8 (8 - g)) in lo
+                    const long long hi = (long long)d[0] * 65536 + (long long)d[1] * 256 + d[2];
+                    const long long lo =
+                        (long long)d[3] * 16777216 + (long long)d[4] * 65536 + (long long)d[5] * 256 + d[6];
+                    const int sc = ei + __shfl_sync(0xffffffffu, fj_lane, c4 + j) - 64;
+                    const double v = fixed_to_double_sat(hi, lo, sc);
+                    const int64_t col = col0 + c4 + j;
+                    if (on(col)) {
+                        const double c = cv[c4 + j];
+                        crow[col] = a.mode == 0 ? v : (a.mode == 1 ? c - v : c + v);
                     }
                 }
             }
-            umma_commit(&bars[1]);
-        }
-    }
-    __syncthreads();
-    if (!*abort_flag) {
-        // one waiter per warp, so that the .sync.aligned TMEM loads below are
-        // executed by whole warps
-        int ok = 1;
-        if (lane == 0) ok = mbar_wait(&bars[1], 0) ? 1 : 0;
-        ok = __shfl_sync(0xffffffffu, ok, 0);
-        if (!ok) {
-            if (lane == 0) {
-                atomicExch(a.err, 2);
-                *abort_flag = 2;
-            }
-        } else {
-            tc_fence_after();
-            // Warp w reads TMEM lanes 32 (w % 4) .. +31 (= tile rows) and the
-            // column half w / 4; results go to a staged tile in the operand
-            // area, which the MMAs no longer read.
-            const int rloc = (warp & 3) * 32 + lane;
-            const int64_t row = m0 + rloc;
-            const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-            const int ei = row < a.rows ? a.expA[row] : 0;
-            double *tile = reinterpret_cast<double *>(sA);
-            for (int c0 = (warp >> 2) * 32; c0 < (warp >> 2) * 32 + 32; c0 += 16) {
-                // V = sum_g D_g 2^(8 (8 - g)) = hi 2^32 + lo, exactly, in integers
-                long long hi[16], lo[16];
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[b]);
 #pragma unroll
-                for (int j = 0; j < 16; ++j) hi[j] = lo[j] = 0;
-                for (int g = 2; g <= S + 1; ++g) {
-                    uint32_t r[16];
-                    tmem_ld16(lane_base + (uint32_t)((g - 2) * kTileN + c0), r);
-                    tmem_wait_ld();
-                    if (g <= 4) {
-                        const int sh = 8 * (4 - g);
-#pragma unroll
-                        for (int j = 0; j < 16; ++j)
-                            hi[j] += (long long)__float2int_rn(__uint_as_float(r[j])) << sh;
-                    } else {
-                        const int sh = 8 * (8 - g);
-#pragma unroll
-                        for (int j = 0; j < 16; ++j)
-                            lo[j] += (long long)__float2int_rn(__uint_as_float(r[j])) << sh;
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int64_t col = n0 + c0 + j;
-                    const int fj = col < a.cols ? a.expB[col] : 0;
-                    tile[rloc * kOutLd + c0 + j] = fixed_to_double(hi[j], lo[j], ei + fj - 64);
-                }
-            }
-        }
-    }
-    __syncthreads();
-    if (!*abort_flag) {
-        // coalesced update of C: consecutive threads take consecutive columns
-        const double *tile = reinterpret_cast<const double *>(sA);
-        const int cx = threadIdx.x & 63, ry = threadIdx.x >> 6;
-        const int64_t col = n0 + cx;
-        constexpr int kStep = kOzThreads / 64, kBatch = 8;
-        if (col < a.cols) {
-            for (int rb = ry; rb < kTileM; rb += kStep * kBatch) {
-                // all loads of a batch first, so that they are in flight together
-                double cv[kBatch];
-                bool on[kBatch];
-#pragma unroll
-                for (int u = 0; u < kBatch; ++u) {
-                    const int rl = rb + kStep * u;
-                    const int64_t row = m0 + rl;
-                    on[u] = rl < kTileM && row < a.rows && !(a.lower && col > row);
-                    cv[u] = (on[u] && a.mode != 0) ? a.C[(size_t)row * a.ldc + col] : 0.0;
-                }
-#pragma unroll
-                for (int u = 0; u < kBatch; ++u) {
-                    if (!on[u]) continue;
-                    const int rl = rb + kStep * u;
-                    const double v = tile[rl * kOutLd + cx];
-                    a.C[(size_t)(m0 + rl) * a.ldc + col] = a.mode == 0 ? v : (a.mode == 1 ? cv[u] - v : cv[u] + v);
-                }
-            }
+            for (int j = 0; j < kPColsPerWarp; ++j) cv[j] = cn[j];
         }
     }
     tc_fence_before();
@@ -263,111 +369,275 @@ __global__ void __launch_bounds__(kOzThreads, 1)
 
 constexpr int kNB = 64;
 
-// Factor the kb x kb diagonal block at (k, k) in place (lower) and write its
-// inverse, a lower-triangular 64 x 64 block (zero above the diagonal and
-// beyond kb), to Linv.  256 threads; per column one thread takes the square
-// root and its reciprocal, the others scale and update with independent
-// FMAs.  The inverse is built right-looking (row k of X = L^-1 is final once
-// scaled; it is then eliminated from the rows below).
+// Factor the kb x kb diagonal block at (k, k) in place (lower).  One CTA of
+// 256 threads holds the block in shared memory and runs the right-looking
+// elimination on unscaled columns: for pivot column c every entry (r, q),
+// c < q <= r, takes a_rq -= a_rc (a_qc / d_c) with d_c the current pivot,
+// which needs one barrier per column.  Thread 0 updates (c+1, c+1) first and
+// then forms the next pivot's reciprocal square root, so the pivots cost no
+// extra barrier.  The stored factor is l_rc = a_rc / sqrt(d_c), l_cc =
+// sqrt(d_c).  FP64 throughput bounds it: kb^3 / 6 FMAs on one SM.
 constexpr int kPotrfThreads = 256;
 constexpr int kLd = kNB + 1;
 
-__global__ void __launch_bounds__(kPotrfThreads) k_potrf_inv(double *__restrict__ A, int64_t n, int64_t k, int kb,
-                                                             int *__restrict__ info, double *__restrict__ Linv) {
-    extern __shared__ double psm[];
-    double *L = psm;                 // [64][65]
-    double *X = psm + kNB * kLd;     // [64][65]
-    double *rd = X + kNB * kLd;      // [64] reciprocal diagonal
+__global__ void __launch_bounds__(kPotrfThreads) k_potrf64(double *__restrict__ A, int64_t n, int64_t k, int kb,
+                                                           int *__restrict__ info) {
+    __shared__ double L[kNB * kLd];
+    __shared__ double rdiag[kNB];  // 1 / d_c
+    __shared__ double rsq[kNB];    // 1 / sqrt(d_c)
+    __shared__ double sq[kNB];     // sqrt(d_c)
     const int t = threadIdx.x;
     for (int e = t; e < kNB * kNB; e += kPotrfThreads) {
         const int r = e >> 6, c = e & 63;
-        L[r * kLd + c] = (r < kb && c < kb) ? A[(size_t)(k + r) * n + k + c] : 0.0;
-        X[r * kLd + c] = (r == c) ? 1.0 : 0.0;
+        L[r * kLd + c] = (r < kb && c <= r) ? A[(size_t)(k + r) * n + k + c] : 0.0;
     }
+    auto pivot = [&](int c) {
+        double d = L[c * kLd + c];
+        if (!(d > 0.0)) {
+            if (info) atomicExch(info, (int)(k + c + 1));
+            d = 1e-300;
+        }
+        const double r = rsqrt(d);
+        rsq[c] = r;
+        rdiag[c] = r * r;
+        sq[c] = d * r;
+    };
+    __syncthreads();
+    if (t == 0 && kb > 0) pivot(0);
     __syncthreads();
     const int ry = t >> 6, cx = t & 63;
     for (int c = 0; c < kb; ++c) {
-        if (t == 0) {
-            double d = L[c * kLd + c];
-            if (!(d > 0.0)) {
-                if (info) atomicExch(info, (int)(k + c + 1));
-                d = 1e-300;
-            }
-            const double lcc = sqrt(d);
-            L[c * kLd + c] = lcc;
-            rd[c] = 1.0 / lcc;
-        }
-        __syncthreads();
-        const double inv = rd[c];
-        for (int r = c + 1 + t; r < kb; r += kPotrfThreads) L[r * kLd + c] *= inv;
-        __syncthreads();
         const int q = c + 1 + cx;
         if (q < kb) {
-            const double lqc = L[q * kLd + c];
-            for (int r = q + ((ry - (q - c - 1)) & 3); r < kb; r += 4) L[r * kLd + q] -= L[r * kLd + c] * lqc;
+            const double m = L[q * kLd + c] * rdiag[c];
+            // thread 0 (cx = 0, ry = 0) starts at (c + 1, c + 1)
+            for (int r = q + ((ry - (q - c - 1)) & 3); r < kb; r += 4)
+                L[r * kLd + q] = fma(-L[r * kLd + c], m, L[r * kLd + q]);
         }
-        __syncthreads();  // the next pivot reads this update
-    }
-    for (int kk = 0; kk < kb; ++kk) {
-        const double inv = rd[kk];
-        if (t <= kk) X[kk * kLd + t] *= inv;
-        __syncthreads();
-        // rows i > kk, columns j <= kk:  X[i][j] -= L[i][kk] X[kk][j]
-        if (cx <= kk) {
-            const double xk = X[kk * kLd + cx];
-            for (int i = kk + 1 + ry; i < kb; i += 4) X[i * kLd + cx] -= L[i * kLd + kk] * xk;
-        }
+        if (t == 0 && c + 1 < kb) pivot(c + 1);
         __syncthreads();
     }
     for (int e = t; e < kNB * kNB; e += kPotrfThreads) {
         const int r = e >> 6, c = e & 63;
-        if (r < kb && c <= r) A[(size_t)(k + r) * n + k + c] = L[r * kLd + c];
-        Linv[(size_t)r * kNB + c] = (r < kb && c <= r) ? X[r * kLd + c] : 0.0;
+        if (r < kb && c <= r) A[(size_t)(k + r) * n + k + c] = r == c ? sq[c] : L[r * kLd + c] * rsq[c];
     }
 }
 
-constexpr size_t kPotrfSmem = (size_t)(2 * kNB * kLd + kNB) * sizeof(double);
+// Linv = L^-1 for the factored kb x kb diagonal block at (k, k): a lower-
+// triangular 64 x 64 block, zero above the diagonal and beyond kb.  Column j
+// of the inverse solves L x = e_j by forward substitution; one warp per
+// column (16 CTAs x 4 warps), lanes holding rows lane and lane + 32, x_i
+// broadcast by shuffle and eliminated from the rows below with one FMA per
+// lane, so the 64 columns run on 16 SMs at once.
+constexpr int kTrtriWarps = 4;
 
-// y_k = Linv_k b_k (forward step of L y = b on block k).
-__global__ void k_trsv_inv_lower(const double *__restrict__ Linv, int64_t k, int kb, double *__restrict__ b) {
-    __shared__ double v[kNB];
-    const int t = threadIdx.x;
-    v[t] = t < kb ? b[k + t] : 0.0;
+__global__ void __launch_bounds__(32 * kTrtriWarps) k_trtri64(const double *__restrict__ A, int64_t n, int64_t k,
+                                                              int kb, double *__restrict__ Linv) {
+    __shared__ double L[kNB * kLd];
+    __shared__ double rd[kNB];
+    const int t = threadIdx.x, lane = t & 31;
+    for (int e = t; e < kNB * kNB; e += 32 * kTrtriWarps) {
+        const int r = e >> 6, c = e & 63;
+        L[r * kLd + c] = (r < kb && c <= r) ? A[(size_t)(k + r) * n + k + c] : 0.0;
+    }
+    if (t < kNB) rd[t] = t < kb ? 1.0 / A[(size_t)(k + t) * n + k + t] : 0.0;
     __syncthreads();
-    double acc = 0.0;
-    for (int c = 0; c <= t && c < kb; ++c) acc += Linv[(size_t)t * kNB + c] * v[c];
-    if (t < kb) b[k + t] = acc;
+    const int j = blockIdx.x * kTrtriWarps + (t >> 5);
+    double acc0 = lane == j ? 1.0 : 0.0, acc1 = lane + 32 == j ? 1.0 : 0.0;
+    double x0 = 0.0, x1 = 0.0;
+    for (int i = j; i < kb; ++i) {  // warp-uniform bounds
+        const double ai = i < 32 ? __shfl_sync(0xffffffffu, acc0, i) : __shfl_sync(0xffffffffu, acc1, i - 32);
+        const double x = ai * rd[i];
+        if (lane == (i & 31)) {
+            if (i < 32)
+                x0 = x;
+            else
+                x1 = x;
+        }
+        acc0 = fma(-L[lane * kLd + i], x, acc0);
+        acc1 = fma(-L[(lane + 32) * kLd + i], x, acc1);
+    }
+    Linv[(size_t)lane * kNB + j] = x0;
+    Linv[(size_t)(lane + 32) * kNB + j] = x1;
 }
 
-// x_k = Linv_k^T y_k (backward step of L^T x = y on block k).
-__global__ void k_trsv_inv_upper(const double *__restrict__ Linv, int64_t k, int kb, double *__restrict__ b) {
-    __shared__ double v[kNB];
-    const int t = threadIdx.x;
-    v[t] = t < kb ? b[k + t] : 0.0;
+// ---------------------------------------------- triangular solves with L ---
+//
+// One cooperative launch per direction.  CTA b owns block rows b, b + G, ...
+// (64 rows each) in solve order.  For its block row i it streams the blocks
+// L_ij of the rows already solved (flag[j] set), accumulating L_ij y_j with
+// coalesced row loads, then applies the inverted diagonal block and
+// publishes y_i with a release store of flag[i].  Every block row waits only
+// on rows that come earlier in solve order, and a CTA takes its rows in that
+// order, so with all CTAs resident (cooperative launch) every wait ends; each
+// wait is still bounded by the global timer and records error 6 (forward) or
+// 7 (backward) before the CTA returns.
+constexpr int kTrsvThreads = 256;
+
+__device__ __forceinline__ int ld_acquire_flag(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_flag(int *p, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Thread 0 advances `ready` (shared) past every consecutive block whose flag
+// holds `want`, stepping by `dir`, waiting while the next needed block is not
+// ready; false on time-out.
+__device__ bool advance_ready(const int *flags, int want, int dir, int stop, int *ready, int *err, int code) {
+    __shared__ int ok;
+    __syncthreads();  // every thread has read the previous `ready`
+    if (threadIdx.x == 0) {
+        ok = 1;
+        int r = *ready;
+        const unsigned long long t0 = global_ns();
+        if (r != stop) {
+            for (long long it = 0;; ++it) {
+                if (ld_acquire_flag(flags + r) == want) break;
+                if ((it & 63) == 63 && global_ns() - t0 > kWaitNs) {
+                    atomicExch(err, code);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+            if (ok) {
+                r += dir;
+                while (r != stop && ld_acquire_flag(flags + r) == want) r += dir;
+            }
+        }
+        *ready = r;
+    }
     __syncthreads();
-    double acc = 0.0;
-    for (int c = t; c < kb; ++c) acc += Linv[(size_t)c * kNB + t] * v[c];
-    if (t < kb) b[k + t] = acc;
+    return ok != 0;
 }
 
-__global__ void k_trsv_sub_lower(const double *__restrict__ A, int64_t n, int64_t k, int kb,
-                                 double *__restrict__ b) {
-    const int lane = threadIdx.x & 31;
-    const int64_t r = k + kb + (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (r >= n) return;
-    double acc = 0.0;
-    for (int c = lane; c < kb; c += 32) acc += A[(size_t)r * n + k + c] * b[k + c];
-    acc = warp_sum(acc);
-    if (lane == 0) b[r] -= acc;
+// L y = b: b is overwritten by y.  flags[nb] must be zero; set to 1.
+__global__ void __launch_bounds__(kTrsvThreads) k_trsv_fwd(const double *__restrict__ L, int64_t n,
+                                                           const double *__restrict__ Linv, double *b, int *flags,
+                                                           int *err) {
+    __shared__ double inv[kNB * kNB];
+    __shared__ double acc[kNB];
+    __shared__ int ready;
+    const int nb = (int)((n + kNB - 1) / kNB);
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    for (int i = blockIdx.x; i < nb; i += gridDim.x) {
+        const int64_t r0 = (int64_t)i * kNB;
+        const int kb = (int)(n - r0 < kNB ? n - r0 : kNB);
+        for (int e = t; e < kNB * kNB; e += kTrsvThreads) inv[e] = Linv[(size_t)i * kNB * kNB + e];
+        if (t == 0) ready = 0;
+        __syncthreads();
+        // warp w: rows 8w .. 8w + 7 of the block; lanes: columns lane, lane + 32
+        double part[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) part[u] = 0.0;
+        int j = 0;
+        while (j < i) {
+            if (!advance_ready(flags, 1, 1, i, &ready, err, 6)) return;
+            const int upto = ready;
+            for (; j < upto; ++j) {
+                const int64_t c0 = (int64_t)j * kNB;  // j < i: a full block
+                const double y0 = __ldcg(b + c0 + lane), y1 = __ldcg(b + c0 + lane + 32);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int r = warp * 8 + u;
+                    if (r < kb) {
+                        const double *row = L + (size_t)(r0 + r) * n + c0;
+                        part[u] = fma(row[lane], y0, fma(row[lane + 32], y1, part[u]));
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const double sum = warp_sum(part[u]);
+            const int r = warp * 8 + u;
+            if (lane == 0) acc[r] = r < kb ? __ldcg(b + r0 + r) - sum : 0.0;
+        }
+        __syncthreads();
+        // y_i = Linv_i acc: four threads per row, 16 columns each
+        {
+            const int r = t >> 2, q = t & 3;
+            double y = 0.0;
+#pragma unroll
+            for (int c = q * 16; c < q * 16 + 16; ++c) y = fma(inv[r * kNB + c], acc[c], y);
+            y += __shfl_xor_sync(0xffffffffu, y, 1);
+            y += __shfl_xor_sync(0xffffffffu, y, 2);
+            if (q == 0 && r < kb) b[r0 + r] = y;
+        }
+        __syncthreads();
+        if (t == 0) {
+            __threadfence();
+            st_release_flag(flags + i, 1);
+        }
+    }
 }
 
-__global__ void k_trsv_sub_upper(const double *__restrict__ A, int64_t n, int64_t k, int kb,
-                                 double *__restrict__ b) {
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= k) return;
-    double acc = 0.0;
-    for (int c = 0; c < kb; ++c) acc += A[(size_t)(k + c) * n + r] * b[k + c];
-    b[r] -= acc;
+// L^T x = y: b (holding y) is overwritten by x.  flags[nb] must hold 1; set
+// to 2.  Block rows are solved from the last to the first.
+__global__ void __launch_bounds__(kTrsvThreads) k_trsv_bwd(const double *__restrict__ L, int64_t n,
+                                                           const double *__restrict__ Linv, double *b, int *flags,
+                                                           int *err) {
+    __shared__ double inv[kNB * kNB];
+    __shared__ double part_s[kTrsvThreads / 32][kNB];
+    __shared__ double acc[kNB];
+    __shared__ int ready;
+    const int nb = (int)((n + kNB - 1) / kNB);
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    for (int ii = blockIdx.x; ii < nb; ii += gridDim.x) {
+        const int i = nb - 1 - ii;
+        const int64_t c0 = (int64_t)i * kNB;
+        const int kb = (int)(n - c0 < kNB ? n - c0 : kNB);
+        for (int e = t; e < kNB * kNB; e += kTrsvThreads) inv[e] = Linv[(size_t)i * kNB * kNB + e];
+        if (t == 0) ready = nb - 1;
+        __syncthreads();
+        // lanes: columns lane, lane + 32 of block column i; warp w: rows w, w + 8, ... of block row j
+        double p0 = 0.0, p1 = 0.0;
+        const bool v0 = lane < kb, v1 = lane + 32 < kb;
+        int j = nb - 1;
+        while (j > i) {
+            if (!advance_ready(flags, 2, -1, i, &ready, err, 7)) return;
+            const int downto = ready;
+            for (; j > downto; --j) {
+                const int64_t r0 = (int64_t)j * kNB;
+                const int kr = (int)(n - r0 < kNB ? n - r0 : kNB);
+                for (int r = warp; r < kr; r += kTrsvThreads / 32) {
+                    const double x = __ldcg(b + r0 + r);
+                    const double *row = L + (size_t)(r0 + r) * n + c0;
+                    if (v0) p0 = fma(row[lane], x, p0);
+                    if (v1) p1 = fma(row[lane + 32], x, p1);
+                }
+            }
+        }
+        part_s[warp][lane] = p0;
+        part_s[warp][lane + 32] = p1;
+        __syncthreads();
+        if (t < kNB) {
+            double sum = 0.0;
+#pragma unroll
+            for (int w = 0; w < kTrsvThreads / 32; ++w) sum += part_s[w][t];
+            acc[t] = t < kb ? __ldcg(b + c0 + t) - sum : 0.0;
+        }
+        __syncthreads();
+        // x_i = Linv_i^T acc: four threads per column, 16 rows each
+        {
+            const int c = t >> 2, q = t & 3;
+            double x = 0.0;
+#pragma unroll
+            for (int r = q * 16; r < q * 16 + 16; ++r) x = fma(inv[r * kNB + c], acc[r], x);
+            x += __shfl_xor_sync(0xffffffffu, x, 1);
+            x += __shfl_xor_sync(0xffffffffu, x, 2);
+            if (q == 0 && c < kb) b[c0 + c] = x;
+        }
+        __syncthreads();
+        if (t == 0) {
+            __threadfence();
+            st_release_flag(flags + i, 2);
+        }
+    }
 }
 
 // Lower triangle of K holds g_t = t_k . t_l; replace it (both triangles) by
@@ -420,7 +690,7 @@ __global__ void __launch_bounds__(256) k_gram_combine(int N, int64_t Ns, const i
 }
 
 size_t ozaki_smem_bytes() {
-    return 1024 + (size_t)kMaxSlices * (kABytes + kBBytes) + 2 * sizeof(uint64_t) + 2 * sizeof(uint32_t) + 16;
+    return 1024 + (size_t)kMaxSlices * kABytes + (size_t)2 * kMaxSlices * kPBBytes + 10 * sizeof(uint64_t) + 16;
 }
 
 inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -448,29 +718,33 @@ cudaError_t launch_ozaki_gemm_strided(const __nv_bfloat16 *Asl, const int *expA,
                                       cudaStream_t st) {
     if (rows <= 0 || cols <= 0) return cudaSuccess;
     if (S < 1 || S > kMaxSlices) return cudaErrorInvalidValue;
-    if (rows > (1LL << 31) - kTileM || cols > (1LL << 31) - kTileN) return cudaErrorInvalidValue;
+    if (rows > (1LL << 31) - kTileM || cols > (1LL << 31) - kPN) return cudaErrorInvalidValue;
     CUtensorMap ma, mb;
-    if (!make_slice_map(&ma, Asl, rows, S, kTileM, a_stride) || !make_slice_map(&mb, Bsl, cols, S, kTileN, b_stride))
+    if (!make_slice_map(&ma, Asl, rows, S, kTileM, a_stride) || !make_slice_map(&mb, Bsl, cols, S, kPN, b_stride))
         return cudaErrorInvalidValue;
-    cudaError_t attr_err = cudaFuncSetAttribute(k_ozaki_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                (int)ozaki_smem_bytes());
-    if (attr_err != cudaSuccess) return attr_err;
-    OzArgs a{rows, cols, S, expA, expB, C, ldc, mode, lower ? 1 : 0, err};
-    dim3 grid(nblk(cols, kTileN), nblk(rows, kTileM));
-    (k_ozaki_gemm<<<grid, kOzThreads, ozaki_smem_bytes(), st>>>(ma, mb, a), nk::note_launch());
+    const void *kern = S == kMaxSlices ? (const void *)k_ozaki_gemm<kMaxSlices> : (const void *)k_ozaki_gemm<0>;
+    cudaError_t e = nk::allow_max_dynamic_smem(kern);
+    if (e != cudaSuccess) return e;
+    OzArgs a{rows, cols, S, expA, expB, C, ldc, mode, lower ? 1 : 0, err, (cols + kPN - 1) / kPN};
+    const int64_t n_mb = (rows + kTileM - 1) / kTileM;
+    int64_t strips = 0;
+    for (int64_t m = 0; m < n_mb; ++m) strips += oz_row_strips(a.n_nb, lower, m);
+    if (strips > (1LL << 31) - 1) return cudaErrorInvalidValue;
+    if (S == kMaxSlices)
+        (k_ozaki_gemm<kMaxSlices><<<(unsigned)strips, kPThreads, ozaki_smem_bytes(), st>>>(ma, mb, a),
+         nk::note_launch());
+    else
+        (k_ozaki_gemm<0><<<(unsigned)strips, kPThreads, ozaki_smem_bytes(), st>>>(ma, mb, a), nk::note_launch());
     return cudaGetLastError();
 }
 
 // BF16 MMA flops a launch executes: active tiles x S(S+1)/2 slice products x
-// 2 x 128 x 64 x 64.
+// 2 x 128 x 32 x 64.
 double ozaki_mma_flops(int64_t rows, int64_t cols, int S, bool lower) {
-    const int64_t tm = (rows + kTileM - 1) / kTileM, tn = (cols + kTileN - 1) / kTileN;
+    const int64_t tm = (rows + kTileM - 1) / kTileM, tn = (cols + kPN - 1) / kPN;
     int64_t tiles = 0;
-    for (int64_t i = 0; i < tm; ++i) {
-        const int64_t m0 = i * kTileM;
-        tiles += lower ? (m0 + kTileM - 1) / kTileN + 1 < tn ? (m0 + kTileM - 1) / kTileN + 1 : tn : tn;
-    }
-    return (double)tiles * (S * (S + 1) / 2) * 2.0 * kTileM * kTileN * kTileK;
+    for (int64_t i = 0; i < tm; ++i) tiles += oz_row_tiles(tn, lower, i);
+    return (double)tiles * (S * (S + 1) / 2) * 2.0 * kTileM * kPN * kTileK;
 }
 
 cudaError_t launch_ozaki_gemm(const __nv_bfloat16 *Asl, const int *expA, int64_t rows,
@@ -482,7 +756,7 @@ cudaError_t launch_ozaki_gemm(const __nv_bfloat16 *Asl, const int *expA, int64_t
 size_t tc_chol_ws_bytes(int64_t n) {
     const int64_t nb = (n + kNB - 1) / kNB;
     return 2 * slice_elems(n, kMaxSlices) * 2 + slice_elems(kNB, kMaxSlices) * 2 + (size_t)(2 * n + kNB) * 4 +
-           (size_t)nb * kNB * kNB * 8 + 8 * 256;
+           (size_t)nb * kNB * kNB * 8 + (size_t)nb * 4 + 9 * 256;
 }
 
 namespace {
@@ -490,6 +764,7 @@ struct TcWs {
     __nv_bfloat16 *Asl, *Bsl, *Asl2;
     int *expA, *expB, *expA2;
     double *Linv;
+    int *flags;  // [nb] block-row flags of the triangular solves
 };
 TcWs carve_tc(void *ws, int64_t n) {
     char *p = static_cast<char *>(ws);
@@ -506,6 +781,7 @@ TcWs carve_tc(void *ws, int64_t n) {
     w.Linv = reinterpret_cast<double *>(take((size_t)((n + kNB - 1) / kNB) * kNB * kNB * 8));
     w.Asl2 = reinterpret_cast<__nv_bfloat16 *>(take(slice_elems(n, kMaxSlices) * 2));
     w.expA2 = reinterpret_cast<int *>(take((size_t)n * 4));
+    w.flags = reinterpret_cast<int *>(take((size_t)((n + kNB - 1) / kNB) * 4));
     return w;
 }
 }  // namespace
@@ -529,7 +805,8 @@ cudaError_t panel_step(double *A, int64_t n, int64_t k0, int *info, int *err, Tc
     const int64_t rest = n - k0 - kb;
     double *Linv = w.Linv + (size_t)(k0 / kNB) * kNB * kNB;
     const int slot = prof_begin(NK_PROF_CHOL_PANEL, st);
-    (k_potrf_inv<<<1, kPotrfThreads, kPotrfSmem, st>>>(A, n, k0, kb, info, Linv), nk::note_launch());
+    (k_potrf64<<<1, kPotrfThreads, 0, st>>>(A, n, k0, kb, info), nk::note_launch());
+    (k_trtri64<<<kNB / kTrtriWarps, 32 * kTrtriWarps, 0, st>>>(A, n, k0, kb, Linv), nk::note_launch());
     cudaError_t e = cudaSuccess;
     if (rest > 0) {
         double *panel = A + (size_t)(k0 + kb) * n + k0;
@@ -549,8 +826,7 @@ cudaError_t launch_cholesky_tc(double *A, int64_t n, int *info, int *err, void *
                                cudaStream_t side, cudaEvent_t ev_narrow, cudaEvent_t ev_panel) {
     TcWs w = carve_tc(ws, n);
     const int S = kMaxSlices;
-    cudaError_t e = cudaFuncSetAttribute(k_potrf_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPotrfSmem);
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
     __nv_bfloat16 *buf[2] = {w.Asl, w.Asl2};
     int *bexp[2] = {w.expA, w.expA2};
     const int64_t nb = (n + kNB - 1) / kNB;
@@ -597,25 +873,34 @@ cudaError_t launch_cholesky_tc(double *A, int64_t n, int *info, int *err, void *
     return cudaGetLastError();
 }
 
-cudaError_t launch_cholesky_solve_tc(const double *L, int64_t n, const void *ws, double *b, cudaStream_t st) {
+cudaError_t launch_cholesky_solve_tc(const double *L, int64_t n, const void *ws, double *b, int *err,
+                                     cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
     TcWs w = carve_tc(const_cast<void *>(ws), n);
+    const int nb = (int)((n + kNB - 1) / kNB);
+    int dev = 0, sms = 0, per_sm_f = 0, per_sm_b = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_f, k_trsv_fwd, kTrsvThreads, 0);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, k_trsv_bwd, kTrsvThreads, 0);
+    if (e != cudaSuccess) return e;
+    // at most one CTA per SM: the resident grid needs no more, and blocks
+    // rows then spread over the SMs' load bandwidth
+    const int gf = std::min(nb, sms * std::min(per_sm_f, 1)), gb = std::min(nb, sms * std::min(per_sm_b, 1));
+    if (gf < 1 || gb < 1) return cudaErrorLaunchOutOfResources;
     const int slot = prof_begin(NK_PROF_TRSV, st);
-    for (int64_t k = 0; k < n; k += kNB) {
-        const int kb = (int)(n - k < kNB ? n - k : kNB);
-        const double *Linv = w.Linv + (size_t)(k / kNB) * kNB * kNB;
-        (k_trsv_inv_lower<<<1, kNB, 0, st>>>(Linv, k, kb, b), nk::note_launch());
-        const int64_t rest = n - k - kb;
-        if (rest > 0) (k_trsv_sub_lower<<<nblk(rest, 8), 256, 0, st>>>(L, n, k, kb, b), nk::note_launch());
-    }
-    const int64_t last = ((n - 1) / kNB) * kNB;
-    for (int64_t k = last; k >= 0; k -= kNB) {
-        const int kb = (int)(n - k < kNB ? n - k : kNB);
-        const double *Linv = w.Linv + (size_t)(k / kNB) * kNB * kNB;
-        (k_trsv_inv_upper<<<1, kNB, 0, st>>>(Linv, k, kb, b), nk::note_launch());
-        if (k > 0) (k_trsv_sub_upper<<<nblk(k, 256), 256, 0, st>>>(L, n, k, kb, b), nk::note_launch());
-    }
+    e = cudaMemsetAsync(w.flags, 0, (size_t)nb * 4, st);
+    if (e != cudaSuccess) return e;
+    const double *Linv = w.Linv;
+    int *flags = w.flags;
+    void *args[] = {(void *)&L, (void *)&n, (void *)&Linv, (void *)&b, (void *)&flags, (void *)&err};
+    e = cudaLaunchCooperativeKernel((const void *)k_trsv_fwd, dim3(gf), dim3(kTrsvThreads), args, 0, st);
+    nk::note_launch();
+    if (e != cudaSuccess) return e;
+    e = cudaLaunchCooperativeKernel((const void *)k_trsv_bwd, dim3(gb), dim3(kTrsvThreads), args, 0, st);
+    nk::note_launch();
     prof_end(slot, st, 2.0 * (double)n * (double)n);
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 // Lower triangle of K = T T^T by tensor cores with S slices per 64-column

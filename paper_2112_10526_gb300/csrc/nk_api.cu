@@ -349,7 +349,7 @@ nk_status run_solve(nk_ctx *ctx, int N, int M, int64_t Ns, const int8_t *s, cons
             NK_CU(nk::launch_cholesky(w.S, Np, w.info, st), "chol factor");
         NK_CU(nk::launch_axpby(Np, 1.0, F, 0.0, delta, st), "chol");
         if (tc)
-            NK_CU(nk::launch_cholesky_solve_tc(w.S, Np, w.tc, delta, st), "chol solve");
+            NK_CU(nk::launch_cholesky_solve_tc(w.S, Np, w.tc, delta, w.info + 1, st), "chol solve");
         else
             NK_CU(nk::launch_cholesky_solve(w.S, Np, delta, st), "chol solve");
         return sync_check ? check_factor(ctx, w.info, st) : NK_OK;
@@ -369,7 +369,7 @@ nk_status run_solve(nk_ctx *ctx, int N, int M, int64_t Ns, const int8_t *s, cons
     NK_CU(jvp_any(N, M, Ns, s, T, F, w, w.w, precision, kExactSlices, st), "ss XF");
     NK_CU(nk::launch_center(Ns, w.w, w.dotp, isq, st), "ss XF");
     if (tc)
-        NK_CU(nk::launch_cholesky_solve_tc(w.K, Ns, w.tc, w.w, st), "ss solve");
+        NK_CU(nk::launch_cholesky_solve_tc(w.K, Ns, w.tc, w.w, w.info + 1, st), "ss solve");
     else
         NK_CU(nk::launch_cholesky_solve(w.K, Ns, w.w, st), "ss solve");
     NK_CU(nk::launch_center(Ns, w.w, w.dotp, isq, st), "ss Xty");

@@ -166,7 +166,9 @@ size_t tc_chol_ws_bytes(int64_t n);
 cudaError_t launch_cholesky_tc(double *A, int64_t n, int *info, int *err, void *ws, cudaStream_t st,
                                cudaStream_t side = nullptr, cudaEvent_t ev_narrow = nullptr,
                                cudaEvent_t ev_panel = nullptr);
-cudaError_t launch_cholesky_solve_tc(const double *L, int64_t n, const void *ws, double *b,
+// Forward and backward solves with the factor of launch_cholesky_tc (one
+// cooperative launch each); err receives 6 / 7 if a block-row wait timed out.
+cudaError_t launch_cholesky_solve_tc(const double *L, int64_t n, const void *ws, double *b, int *err,
                                      cudaStream_t st);
 cudaError_t launch_gram_tc(int N, int M, int64_t Ns, const int8_t *s, const double *T, int S, double *K,
                            int *err, void *ws, cudaStream_t st);

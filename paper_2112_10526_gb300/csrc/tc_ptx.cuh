@@ -128,6 +128,36 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
         : "r"(taddr));
 }
 
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&r)[4]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Bounded wait that also gives up as soon as *abort is set (by another role
+// of the same CTA); false on time-out or abort.
+__device__ bool mbar_wait_or_abort(uint64_t *bar, uint32_t parity, const volatile int *abort) {
+    const unsigned long long t0 = global_ns();
+    for (long long it = 0; it < (1LL << 40); ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255) == 255) {
+            if (*abort) return false;
+            if (global_ns() - t0 > kWaitNs) return false;
+        }
+    }
+    return false;
+}
+
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 
@@ -147,6 +177,60 @@ __device__ __forceinline__ void split_bits(double x, int &biased, unsigned long 
     if (biased != 0) mant |= 1ULL << 52;
     else biased = 1;  // subnormal: value = mant 2^(1 - 1075)
 }
+
+__host__ __device__ __forceinline__ int clz64_any(unsigned long long x) {
+#ifdef __CUDA_ARCH__
+    return __clzll((long long)x);
+#else
+    return x ? __builtin_clzll(x) : 64;
+#endif
+}
+
+// Branch-free variant of fixed_to_double with the same result (round to
+// nearest even of V = hi 2^32 + lo, |V| < 2^75, times 2^sc): selects instead
+// of branches so that the conversions of neighbouring elements interleave.
+// The 64-bit window W = floor(|V| / 2^k) keeps all of |V| when it fits
+// (k = 0), else exactly 64 bits with the k <= 11 dropped bits kept as a
+// sticky flag; W is left-justified and rounded at bit 11.
+__host__ __device__ __forceinline__ unsigned long long fixed_to_bits(long long hi, long long lo, int sc, bool &ok,
+                                                                   int &E) {
+    const long long H = hi + (lo >> 32);
+    const unsigned int Lw = (unsigned int)(unsigned long long)lo;
+    const bool neg = H < 0;
+    const unsigned int s32 = neg ? 0xFFFFFFFFu : 0u;
+    const unsigned int Lm = (Lw ^ s32) + (neg ? 1u : 0u);
+    const unsigned long long Hm =
+        ((unsigned long long)H ^ (neg ? ~0ULL : 0ULL)) + ((neg && Lw == 0u) ? 1ULL : 0ULL);
+    const int bl = 64 - clz64_any(Hm);  // bit length of Hm, 0 .. 43
+    const int k = bl > 32 ? bl - 32 : 0;
+    const unsigned long long W = (Hm << (32 - k)) | (unsigned long long)(Lm >> k);
+    const bool sticky = (Lm & ((1u << k) - 1u)) != 0u;
+    const int z = k > 0 ? 0 : (bl > 0 ? 32 - bl : clz64_any((unsigned long long)Lm));  // leading zeros of W
+    const unsigned long long N = z < 64 ? W << z : 0ULL;
+    unsigned long long mant = N >> 11;
+    const unsigned int rb = (unsigned int)(N & 0x7FFULL);
+    const bool up = rb > 0x400u || (rb == 0x400u && (sticky || (mant & 1ULL)));
+    mant += up ? 1ULL : 0ULL;
+    const bool carry = (mant >> 53) != 0ULL;
+    mant = carry ? (mant >> 1) : mant;
+    E = (63 - z) + k + (carry ? 1 : 0) + sc + 1023;
+    ok = W == 0ULL || (E > 0 && E < 2047);
+    const unsigned long long bits =
+        (neg ? (1ULL << 63) : 0ULL) | ((unsigned long long)(E & 0x7FF) << 52) | (mant & 0xFFFFFFFFFFFFFULL);
+    return W == 0ULL ? 0ULL : bits;
+}
+
+// fixed_to_bits as a double, saturating outside the normal range: results
+// below 2^-1022 in magnitude become a signed zero, at or above 2^1024 an
+// infinity.
+__device__ __forceinline__ double fixed_to_double_sat(long long hi, long long lo, int sc) {
+    bool ok;
+    int E;
+    unsigned long long bits = fixed_to_bits(hi, lo, sc, ok, E);
+    if (!ok) bits = (bits & (1ULL << 63)) | (E > 0 ? 0x7FF0000000000000ULL : 0ULL);
+    return __longlong_as_double((long long)bits);
+}
+
 
 // The value (hi 2^32 + lo) 2^sc as an FP64 bit pattern, rounded to nearest
 // even, built with 64-bit integer operations (|hi| < 2^43, |lo| < 2^52: the

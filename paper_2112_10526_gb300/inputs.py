@@ -88,7 +88,7 @@ def serve_requests(n: int = 512, seed: int = 4) -> list:
     step): lattice uniform over the periodic Ising chains N in {16, 32, 64,
     128, 256} (J = h = 1) and the Marshall-signed Heisenberg squares L in
     {4, 6, 8, 12, 16}; alpha uniform in {1, 2, 4}; 1024 chains x U{1..16}
-    samples; parameters seeded 40000 + r; dense Cholesky when Np <= 1024,
+    samples; parameters seeded 40000 + r; dense Cholesky when Np <= 4096,
     else CG."""
     rng = np.random.default_rng(seed)
     out = []
@@ -106,7 +106,7 @@ def serve_requests(n: int = 512, seed: int = 4) -> list:
         M = alpha * N
         Np = N + M + M * N
         out.append(dict(index=r, N=N, M=M, alpha=alpha, ham=ham, rule=rule, chains=1024, per_chain=per_chain,
-                        seed=40000 + r, solver="cholesky" if Np <= 1024 else "cg"))
+                        seed=40000 + r, solver="cholesky" if Np <= 4096 else "cg"))
     return out
 
 
