@@ -804,19 +804,26 @@ cudaError_t panel_step(double *A, int64_t n, int64_t k0, int *info, int *err, Tc
     const int kb = (int)(n - k0 < kNB ? n - k0 : kNB);
     const int64_t rest = n - k0 - kb;
     double *Linv = w.Linv + (size_t)(k0 / kNB) * kNB * kNB;
-    const int slot = prof_begin(NK_PROF_CHOL_PANEL, st);
+    // timing classes: the FP64 diagonal-block kernels and the slicing count
+    // as the panel, the tensor-core panel product with the trailing updates
+    int slot = prof_begin(NK_PROF_CHOL_PANEL, st);
     (k_potrf64<<<1, kPotrfThreads, 0, st>>>(A, n, k0, kb, info), nk::note_launch());
     (k_trtri64<<<kNB / kTrtriWarps, 32 * kTrtriWarps, 0, st>>>(A, n, k0, kb, Linv), nk::note_launch());
     cudaError_t e = cudaSuccess;
+    double *panel = A + (size_t)(k0 + kb) * n + k0;
     if (rest > 0) {
-        double *panel = A + (size_t)(k0 + kb) * n + k0;
         e = launch_slice_rows(Linv, kNB, kb, kb, S, w.Bsl, w.expB, st);
         if (e == cudaSuccess) e = launch_slice_rows(panel, n, rest, kb, S, Lsl, Lexp, st);
-        if (e == cudaSuccess)
-            e = launch_ozaki_gemm(Lsl, Lexp, rest, w.Bsl, w.expB, kb, S, panel, n, 0, false, err, st);
-        if (e == cudaSuccess) e = launch_slice_rows(panel, n, rest, kb, S, Lsl, Lexp, st);
     }
-    prof_end(slot, st, (double)kb * kb * kb / 3.0 + 2.0 * (double)rest * kb * kb);
+    prof_end(slot, st, 2.0 * (double)kb * kb * kb / 3.0);
+    if (rest > 0 && e == cudaSuccess) {
+        slot = prof_begin(NK_PROF_CHOL_UPDATE, st);
+        e = launch_ozaki_gemm(Lsl, Lexp, rest, w.Bsl, w.expB, kb, S, panel, n, 0, false, err, st);
+        prof_end(slot, st, ozaki_mma_flops(rest, kb, S, false));
+        slot = prof_begin(NK_PROF_CHOL_PANEL, st);
+        if (e == cudaSuccess) e = launch_slice_rows(panel, n, rest, kb, S, Lsl, Lexp, st);
+        prof_end(slot, st, 0.0);
+    }
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
