@@ -207,6 +207,12 @@ def step(st, first=False):
                   st["stats"])
 
 
+def replica_value(world, K, ms_max):
+    """Whole-job SR steps/s of `world` independent replicas that each ran K
+    steps, from the slowest rank's time (ms): weak scaling."""
+    return world * K / (ms_max / 1e3)
+
+
 def barrier(world):
     import torch.distributed as dist
     if world > 1:
@@ -323,7 +329,7 @@ def run_ours(args, rank, world):
     # a second timing without the event brackets (the headline number)
     ms_plain, launches, _ = timed_steps(st, args.steps, world, dev, prof=False)
     K = args.steps
-    value = world * K / (ms_plain / 1e3)
+    value = replica_value(world, K, ms_plain)
     stats = nk.sr_stats_dict(st["stats"])
     rf, dom = roofline(prof, K, args.precision)
     if rf is not None:

@@ -3,10 +3,10 @@
  * Monte Carlo with a restricted Boltzmann machine, after the NetKet 3 paper
  * (F. Vicentini et al., arXiv:2112.10526).
  *
- * One VMC step: Metropolis sampling of |psi|^2 (Sec. 3.5), local energies
- * (Sec. 3.4, Eq. eq:local-estimator), log-derivatives (Eq.
+ * One VMC step: Metropolis sampling of |psi|^2 (Sec. 3.4), local energies
+ * (Sec. 3.3, Eq. eq:local-estimator), log-derivatives (Eq.
  * eq:log-derivative-O), force (Eqs. eq:force VMC, eq:gradE:real), the
- * quantum geometric tensor (Sec. 3.6, App. B) and the stochastic
+ * quantum geometric tensor (Sec. 3.5, App. B) and the stochastic
  * reconfiguration solve (Eq. eq:stochastic-reconfiguration) followed by the
  * SGD update (Sec. 4.1).
  *
@@ -59,8 +59,8 @@ typedef int32_t nk_status;
 #define NK_F64 0
 #define NK_MIXED 1
 
-#define NK_RULE_LOCAL 0    /* MetropolisLocal: flip one spin (Sec. 3.5) */
-#define NK_RULE_EXCHANGE 1 /* MetropolisExchange: swap an edge (Sec. 3.5) */
+#define NK_RULE_LOCAL 0    /* MetropolisLocal: flip one spin (Sec. 3.4) */
+#define NK_RULE_EXCHANGE 1 /* MetropolisExchange: swap an edge (Sec. 3.4) */
 
 #define NK_TFIM 0 /* H = J sum_<ik> sz sz - h sum_i sx (Eq. eq:tf-ising-hamiltonian) */
 #define NK_HEIS 1 /* H = J sum_<ik> sigma.sigma (Eq. eq: j1 j2 heisenberg, J2=0) */
@@ -128,7 +128,7 @@ nk_status nk_chains_init(nk_ctx *ctx, int32_t N, int32_t C, int32_t rule, uint64
                          uint32_t stream_id, int8_t *s_out, void *stream);
 
 /*
- * Metropolis-Hastings sweeps (Sec. 3.5: P_acc = min(1, |psi(s')/psi(s)|^2)
+ * Metropolis-Hastings sweeps (Sec. 3.4: P_acc = min(1, |psi(s')/psi(s)|^2)
  * for the symmetric local and exchange proposals).  One sweep is N
  * proposals per chain.  Proposal p of sweep w uses the Philox4x64-10 block
  * with key (seed, 0) and counter ((sweep0 + w) N + p, chain, stream_id, 0):
@@ -186,7 +186,7 @@ nk_status nk_local_energy_noalloc(const nk_rbm *rbm, int32_t precision, const nk
                                   void *stream);
 
 /*
- * Sample statistics of the local energy (Sec. 3.4): out[0] = mean,
+ * Sample statistics of the local energy (Sec. 3.3): out[0] = mean,
  * out[1] = variance (1/Ns normalisation), out[2] = standard error of the
  * mean (from the n_chains chain means when each chain holds >= 2 samples
  * stored chain-major, else sqrt(variance/Ns)).  out: device float64 [3].
@@ -231,7 +231,7 @@ typedef struct {
 } nk_qgt;
 
 /*
- * out = (G + diag_shift I) v with G = (1/Ns) J^T dJ (Sec. 3.6, App. B.2 /
+ * out = (G + diag_shift I) v with G = (1/Ns) J^T dJ (Sec. 3.5, App. B.2 /
  * B.3): ONTHEFLY computes w = J v / Ns, dw = w - <w>, J^T dw; JACOBIAN
  * computes dJ^T (dJ v) / Ns.  v, out [Np].
  */
@@ -247,7 +247,7 @@ nk_status nk_qgt_matvec(nk_ctx *ctx, const nk_qgt *qgt, double diag_shift, const
  * tcgen05 MMAs with exact FP32 accumulation and are recombined in FP64
  * (slices = 7: FP64-level accuracy; 3: about FP32).  This is the building
  * block of the NK_MIXED Cholesky and sample-space Gram (the dense products
- * G = dJ^T dJ / Ns of App. B.2 and the factorisation of Sec. 3.6).  The call
+ * G = dJ^T dJ / Ns of App. B.2 and the factorisation of Sec. 3.5).  The call
  * synchronises the stream and returns NK_ERR_TIMEOUT if a product timed out.
  */
 nk_status nk_tc_gemm(nk_ctx *ctx, int64_t rows, int64_t cols, int32_t k, const double *A, int64_t lda,
@@ -256,7 +256,7 @@ nk_status nk_tc_gemm(nk_ctx *ctx, int64_t rows, int64_t cols, int32_t k, const d
 
 /*
  * Solve (G + diag_shift I) delta = F for the QGT of the given samples
- * (Eq. eq:stochastic-reconfiguration, real case; Sec. 3.6 "Solving linear
+ * (Eq. eq:stochastic-reconfiguration, real case; Sec. 3.5 "Solving linear
  * systems").  solver: NK_SOLVER_CHOLESKY (dense Np x Np FP64 Cholesky),
  * NK_SOLVER_CHOLESKY_SAMPLESPACE (FP64 Cholesky of the Ns x Ns matrix
  * dJ dJ^T / Ns + diag_shift I and delta = (F - dJ^T y / sqrt(Ns)) /

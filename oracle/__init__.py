@@ -11,7 +11,7 @@ Layout:
                log-derivatives, Philox4x64-10, chain initialisation,
                Metropolis chains with forced-follow replay);
   core.py      ctypes binding of the C part plus the sample statistics, force,
-               QGT, SR linear solves and update in numpy (Sec. 3.4, 3.6, 4.1,
+               QGT, SR linear solves and update in numpy (Sec. 3.3, 3.5, 4.1,
                App. B of the paper);
   exact.py     exact enumeration over all basis states and exact
                diagonalisation from Kronecker products of Pauli matrices.

@@ -138,7 +138,7 @@ def chain_init(N, C, rule, seed, stream=0):
 
 def metropolis(params, N, M, rule, edges, s, sweep0, n_discard, n_samples, seed, stream=0,
                forced=None):
-    """Metropolis-Hastings chains (Sec. 3.5).  Returns a dict with the new chain
+    """Metropolis-Hastings chains (Sec. 3.4).  Returns a dict with the new chain
     states, samples [C, n_samples, N], ln psi of each sample, the oracle's own
     decisions and margins per proposal, and accepted-move counts.
 
@@ -169,7 +169,7 @@ def metropolis(params, N, M, rule, edges, s, sweep0, n_discard, n_samples, seed,
 # ---------------------------------------------------------------------------
 
 def stats(eloc, n_chains=None):
-    """Monte Carlo mean of the local energy (Sec. 3.4, "the required classical
+    """Monte Carlo mean of the local energy (Sec. 3.3, "the required classical
     expectation values are then estimated by averaging over a sequence"):
     mean = (1/N_s) sum_k E_k, variance = (1/N_s) sum_k (E_k - mean)^2.
 
@@ -210,7 +210,7 @@ def qgt_dense(O):
 
 def qgt_matvec_onthefly(O, v, diag_shift=0.0):
     """QGTOnTheFly product (App. B.3): w = (1/N_s) J v;  dw = w - <w>;
-    G v = J^T dw;  plus the diagonal shift eps v (Sec. 3.6)."""
+    G v = J^T dw;  plus the diagonal shift eps v (Sec. 3.5)."""
     O = np.asarray(O, dtype=np.float64)
     v = np.asarray(v, dtype=np.float64)
     ns = O.shape[0]
@@ -221,7 +221,7 @@ def qgt_matvec_onthefly(O, v, diag_shift=0.0):
 
 def solve_cholesky(S, F, diag_shift):
     """(S + eps I) delta = F by a dense Cholesky factor and two triangular
-    solves (Sec. 3.6 "Solving linear systems", direct solver; Eq.
+    solves (Sec. 3.5 "Solving linear systems", direct solver; Eq.
     eq:stochastic-reconfiguration, real case)."""
     A = np.asarray(S, dtype=np.float64) + diag_shift * np.eye(S.shape[0])
     L = np.linalg.cholesky(A)
@@ -246,7 +246,7 @@ def _backward_subst(U, b):
 
 
 def solve_cg(matvec, F, tol=1e-10, maxiter=1000):
-    """Conjugate gradients on (S + eps I) delta = F with x0 = 0 (Sec. 3.6,
+    """Conjugate gradients on (S + eps I) delta = F with x0 = 0 (Sec. 3.5,
     iterative solver).  Stops when ||r|| <= tol ||F||.  Returns (x, iters,
     relative residual)."""
     F = np.asarray(F, dtype=np.float64)

@@ -175,7 +175,7 @@ class ExactState:
         return (O.T * self.p) @ O - np.outer(mo, mo)
 
     def sample(self, n, seed):
-        """ExactSampler of Sec. 3.5: i.i.d. draws from |psi|^2 (indices into
+        """ExactSampler of Sec. 3.4: i.i.d. draws from |psi|^2 (indices into
         self.configs)."""
         rng = np.random.default_rng(seed)
         return rng.choice(self.p.size, size=n, p=self.p)

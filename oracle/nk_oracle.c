@@ -91,12 +91,12 @@ static double oc_log_ratio(int N, int M, const double *params, const int8_t *s,
 
 /*
  * Local energy E_loc(s) = sum_{s'} H_{s s'} psi(s')/psi(s)
- * (Sec. 3.4 "Estimating observables", Eq. "eq:local-estimator").
+ * (Sec. 3.3 "Estimating observables", Eq. "eq:local-estimator").
  *
  * kind 0, transverse-field Ising (Sec. 9, Eq. "eq:tf-ising-hamiltonian"):
  *     H = J sum_<ik> sz_i sz_k - h sum_i sx_i
  *     diagonal: J sum_e s_i s_k;  connected: s^(i) (site i flipped), H = -h.
- * kind 1, Heisenberg in Pauli matrices (Sec. 8, Eq. "eq: j1 j2 heisenberg"
+ * kind 1, Heisenberg in Pauli matrices (Sec. 7, Eq. "eq: j1 j2 heisenberg"
  * with J2 = 0):
  *     H = J sum_<ik> (sx sx + sy sy + sz sz)
  *     diagonal: J sum_e s_i s_k;  connected: for each edge with s_i != s_k,
@@ -138,7 +138,7 @@ void oc_local_energy(int N, int M, const double *params, int kind, double J,
 
 /*
  * Log-derivatives O_k(s) = d ln psi(s) / d theta_k
- * (Sec. 3.4, Eq. "eq:log-derivative-O"), written out for the RBM:
+ * (Sec. 3.3, Eq. "eq:log-derivative-O"), written out for the RBM:
  *     O_{a_i} = s_i,  O_{b_j} = tanh(theta_j),  O_{W_ji} = tanh(theta_j) s_i.
  * Output O: [B, Np] with Np = N + M + M N, the parameter layout above.
  */
@@ -251,12 +251,12 @@ void oc_chain_init(int N, int C, int rule, uint64_t seed, uint32_t stream,
 }
 
 /*
- * Metropolis-Hastings chains on |psi|^2 (Sec. 3.5 "Monte Carlo samplers",
+ * Metropolis-Hastings chains on |psi|^2 (Sec. 3.4 "Monte Carlo samplers",
  * the acceptance probability P_acc = min(1, P(s')/P(s)) for a symmetric
  * proposal).
  *
  * One sweep is N proposals (the paper's "N_sites intermediate updates" per
- * sample in Sec. 8).  Proposal p of sweep w of this call has global index
+ * sample in Sec. 7).  Proposal p of sweep w of this call has global index
  * q = (sweep0 + w) N + p and uses the Philox block (q, chain, stream, 0):
  *   rule 0 (MetropolisLocal): flip site i = pick(y0, N);
  *   rule 1 (MetropolisExchange): swap the spins of edge e = pick(y0, E); if

@@ -1,7 +1,7 @@
 // FP64 linear algebra of the VMC step: sample statistics, Jacobian products
 // (vjp / jvp, App. B.1), the stored centred Jacobian, QGT products and
 // Gram matrices (App. B.2 / B.3), blocked Cholesky and triangular solves
-// (Sec. 3.6, direct solver), and the CG / SGD vector kernels.
+// (Sec. 3.5, direct solver), and the CG / SGD vector kernels.
 //
 // Every reduction runs in a fixed order (split-K partials summed in split
 // order, tree reductions with a fixed shape), so results are bitwise

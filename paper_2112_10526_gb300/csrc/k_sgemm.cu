@@ -13,8 +13,8 @@
 // whose FP32 accumulation is exact: |D_t| <= K 255 < 2^24 for K <= 65792.
 // The epilogue recombines sum_t D_t 2^{-8t} 2^{f_n} in integers and writes
 // FP64.  With SB = 7 the products are exact up to the 2^-56 truncation of B
-// (FP64-level: the batched theta rebuild); with SB = 3 up to 2^-24 (the
-// NK_MIXED Jacobian products).
+// (FP64-level: the batched theta rebuild, the force and the sample-space
+// solve products); with SB = 4 up to 2^-32 (the NK_MIXED QGT products of CG).
 //
 // Kernel: 128 x 64 output tile per CTA, K in chunks of 64 through a
 // 3-stage TMA / mbarrier ring (thread 0 produces, thread 32 issues

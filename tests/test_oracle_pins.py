@@ -400,7 +400,7 @@ def test_metropolis_forced_follow_and_decisions():
 
 def test_mc_energy_within_error_of_exact():
     """The MC estimate of <H> from the oracle's chains lies within 4 sigma of
-    the exact expectation (Sec. 3.4)."""
+    the exact expectation (Sec. 3.3)."""
     N, M = 10, 10
     ham = I.tfim_chain(N, 1.0, 1.0)
     p = I.rbm_params(N, M, 14, 0.3)

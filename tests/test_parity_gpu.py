@@ -334,3 +334,40 @@ def test_sr_trajectory_config1_50_iterations(ctx):
     first = np.mean([o["stats"]["energy"] for o in out[:5]])
     last = np.mean([o["stats"]["energy"] for o in out[-5:]])
     assert last < first
+
+
+@pytest.mark.parametrize("prec", ["f64", "mixed"])
+def test_metropolis_full_size_sampled_chains(ctx, prec):
+    """The sweep configuration of the 10 x 10 Heisenberg workload (1024
+    exchange chains, 16 discarded + 8 sampled sweeps, N = 100, M = 200,
+    sigma = 0.01) run in full on the GPU; the first 48 chains are replayed by
+    the oracle (chains are independent: the Philox counter holds the chain
+    index)."""
+    N, M, C, nd, ns = 100, 200, 1024, 16, 8
+    p = I.rbm_params(N, M, 2)
+    edges = I.square_edges(10)
+    s0 = oracle.chain_init(N, C, "exchange", 2, 0)
+    st = cu(s0)
+    samples = torch.empty((C, ns, N), dtype=torch.int8, device=dev())
+    lp = torch.empty((C, ns), dtype=torch.float64, device=dev())
+    nacc = torch.zeros(C, dtype=torch.int64, device=dev())
+    dec = torch.empty((C, nd + ns, N), dtype=torch.uint8, device=dev())
+    nk.nk_metropolis_sweep(ctx, cu(p), N, M, "exchange", cu(edges), st, 0, nd, ns, 2, 0, samples, lp, nacc,
+                           dec, precision=prec)
+    K = 48
+    g_dec = dec.cpu().numpy()[:K]
+    ref = oracle.metropolis(p, N, M, "exchange", edges, s0[:K], 0, nd, ns, 2, 0, forced=g_dec)
+    mism = ref["decisions"] != g_dec
+    if prec == "f64":
+        allowed = ref["margin"] < 1e-9
+    else:
+        lu = _lnu(2, 0, K, N, nd + ns, 0)
+        two_d = lu + np.where(ref["decisions"] == 1, 1, -1) * ref["margin"]
+        allowed = ref["margin"] < 1e-4 * np.maximum(1.0, np.abs(two_d))
+    assert not (mism & ~allowed).any()
+    np.testing.assert_array_equal(samples.cpu().numpy()[:K], ref["samples"])
+    np.testing.assert_array_equal(st.cpu().numpy()[:K], ref["state"])
+    assert rel_err(lp.cpu().numpy()[:K], ref["logpsi"]) < (1e-10 if prec == "f64" else 1e-4)
+    # every chain keeps S_z = 0 and the accept counts match the decisions
+    assert (st.cpu().numpy().astype(np.int64).sum(axis=1) == 0).all()
+    np.testing.assert_array_equal(nacc.cpu().numpy(), (dec.cpu().numpy() == 1).sum(axis=(1, 2)))

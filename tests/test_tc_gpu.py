@@ -160,3 +160,27 @@ def test_mixed_cg_solve(ctx, N, M, Ns, eps):
                           cg_maxiter=5000, precision="mixed")
     assert info["converged"]
     assert vec_rel_err(d.cpu().numpy(), ref) < 1e-6
+
+
+def test_samplespace_solve_full_size(ctx):
+    """The sample-space solve at the size the 10 x 10 Heisenberg step runs it
+    (Ns = 8192, N = 100, M = 200, Np = 20300, eps = 0.01), NK_MIXED against
+    NK_F64 on the GPU and both against the SR system itself, applied with the
+    oracle's FP64 Jacobian: ||(S + eps I) delta - F|| / ||F||."""
+    N, M, Ns, eps = 100, 200, 8192, 0.01
+    p = I.rbm_params(N, M, 2, 0.05)
+    s = I.random_configs(Ns, N, 12, sz0=True)
+    Np = N + M + M * N
+    F = np.random.default_rng(5).normal(size=Np) * 0.1
+    out = {}
+    for prec in ("f64", "mixed"):
+        d = torch.empty(Np, dtype=torch.float64, device=dev())
+        nk.nk_sr_solve(ctx, cu(p), N, M, cu(s), cu(F), d, solver="cholesky_samplespace", diag_shift=eps,
+                       precision=prec)
+        out[prec] = d.cpu().numpy()
+    assert nk.nk_ctx_error(ctx) == 0
+    O = oracle.jacobian(p, N, M, s)
+    res = {k: np.linalg.norm(oracle.qgt_matvec_onthefly(O, v, eps) - F) / np.linalg.norm(F) for k, v in out.items()}
+    assert res["f64"] < 1e-9, res
+    assert res["mixed"] < 1e-9, res
+    assert vec_rel_err(out["mixed"], out["f64"]) < 1e-8
