@@ -257,6 +257,8 @@ __global__ void __launch_bounds__(128) k_sweep(SweepK<R> P) {
     __syncwarp();
     unsigned long long acc = 0;
     const int n_sweeps = A.n_discard + A.n_samples;
+    constexpr bool kF32 = sizeof(R) == 4;
+    using Acc = R;  // precision of the accept arithmetic
     for (int w = 0; w < n_sweeps; ++w) {
         // From-scratch FP64 theta = b + W s (rebuilt here, or given by the
         // tensor-core product), t = tanh theta, ln psi.
@@ -269,51 +271,77 @@ __global__ void __launch_bounds__(128) k_sweep(SweepK<R> P) {
                 th = T.b[j];
                 for (int i = 0; i < N; ++i) th = fma(T.Wt[(size_t)i * M + j], (double)sv[i], th);
             }
-            t[j] = (R)tanh(th);
-            lp += lncosh(th);
+            if (kF32) {
+                // FP32 path: t and the ln cosh terms in FP32 lanes (the FP64
+                // pipe of this part runs at 1/64 of the FP32 rate)
+                const float thf = (float)th;
+                t[j] = (R)tanhf(thf);
+                lp += (double)lncosh(thf);
+            } else {
+                t[j] = (R)tanh(th);
+                lp += lncosh(th);
+            }
         }
         for (int i = lane; i < N; i += 32) lp += T.a[i] * (double)sv[i];
         lp = warp_sum(lp);
         __syncwarp();
         const unsigned long long qbase = (unsigned long long)(A.sweep0 + w) * (unsigned long long)N;
-        unsigned long long y0 = 0, y1 = 0;
+        // Lane l prepares proposal q0 + l of each batch of 32: its Philox
+        // block, ln u, the site / edge, K and the visible-bias difference, so
+        // that a proposal only broadcasts them.
+        // The FP32 path takes the accept decision in FP32 (ln u and the
+        // ratio), the FP64 path in FP64.
+        int b_i = 0, b_k = -1, b_row = 0, b_ok = 1;
+        R b_K = R(0);
+        Acc b_aa = Acc(0), b_lu = Acc(0);
         for (int q = 0; q < N; ++q) {
             if ((q & 31) == 0) {
                 Philox4 y = philox4x64_10(qbase + (unsigned long long)(q + lane), (unsigned long long)c,
                                           (unsigned long long)A.stream_id, 0ULL, A.seed, 0ULL);
-                y0 = y.v[0];
-                y1 = y.v[1];
+                if (kF32)
+                    b_lu = (Acc)logf((float)uniform53(y.v[1]));
+                else
+                    b_lu = (Acc)log(uniform53(y.v[1]));
+                if (A.rule == NK_RULE_LOCAL) {
+                    b_i = pick_index(y.v[0], N);
+                    b_k = -1;
+                    b_row = b_i;
+                    b_K = T.K_site[b_i];
+                    b_aa = (Acc)T.a[b_i];
+                } else {
+                    const int e = pick_index(y.v[0], T.E);
+                    const int i0 = A.edges[2 * e], k0 = A.edges[2 * e + 1];
+                    // an edge outside [0, N) is never a move (bounds guard)
+                    b_ok = (unsigned)i0 < (unsigned)N && (unsigned)k0 < (unsigned)N;
+                    b_i = b_ok ? i0 : 0;
+                    b_k = b_ok ? k0 : 0;
+                    b_row = e;
+                    b_K = T.K_edge[e];
+                    b_aa = b_ok ? (Acc)(T.a[b_i] - T.a[b_k]) : Acc(0);
+                }
             }
-            const unsigned long long u0 = __shfl_sync(kFull, y0, q & 31);
-            const unsigned long long u1 = __shfl_sync(kFull, y1, q & 31);
+            const int src = q & 31;
+            const int i = __shfl_sync(kFull, b_i, src), k = __shfl_sync(kFull, b_k, src);
+            const int row = __shfl_sync(kFull, b_row, src);
+            const R K = __shfl_sync(kFull, b_K, src);
+            const Acc aa = __shfl_sync(kFull, b_aa, src), lu = __shfl_sync(kFull, b_lu, src);
             const size_t slot = ((size_t)c * A.dec_stride + A.dec_offset + w) * N + q;
-            int i, k = -1;
             const R *tau;
-            R K;
-            double d0;
             if (A.rule == NK_RULE_LOCAL) {
-                i = pick_index(u0, N);
-                tau = T.tau_site + (size_t)i * M;
-                K = T.K_site[i];
-                d0 = -2.0 * T.a[i] * (double)sv[i];
+                tau = T.tau_site + (size_t)row * M;
             } else {
-                const int e = pick_index(u0, T.E);
-                i = A.edges[2 * e];
-                k = A.edges[2 * e + 1];
-                // an edge outside [0, N) is never a move (bounds guard)
-                if ((unsigned)i >= (unsigned)N || (unsigned)k >= (unsigned)N || sv[i] == sv[k]) {
+                if (!__shfl_sync(kFull, b_ok, src) || sv[i] == sv[k]) {
                     if (lane == 0 && A.decisions) A.decisions[slot] = 2;
                     continue;
                 }
-                tau = T.tau_edge + (size_t)e * M;
-                K = T.K_edge[e];
-                d0 = -2.0 * (double)sv[i] * (T.a[i] - T.a[k]);
+                tau = T.tau_edge + (size_t)row * M;
             }
+            const Acc d0 = Acc(-2) * aa * (Acc)sv[i];
             const R si = (R)sv[i];
             Prod<R> pr = unit_lanes_product<R>(t, tau, si, lane, M, P.vec4);
-            pr = warp_prod(pr);
-            const double delta = d0 + (double)(K + prod_log(pr));
-            const bool accept = log(uniform53(u1)) < 2.0 * delta;
+            pr = warp_prod_normalised(pr);
+            const Acc delta = d0 + (Acc)(K + prod_log(pr));
+            const bool accept = lu < Acc(2) * delta;
             if (lane == 0 && A.decisions) A.decisions[slot] = accept ? 1 : 0;
             if (accept) {
                 for (int j = lane; j < M; j += 32) {
@@ -325,7 +353,7 @@ __global__ void __launch_bounds__(128) k_sweep(SweepK<R> P) {
                     sv[i] = (int8_t)-sv[i];
                     if (k >= 0) sv[k] = (int8_t)-sv[k];
                 }
-                lp += delta;
+                lp += (double)delta;
                 ++acc;
             }
             __syncwarp();

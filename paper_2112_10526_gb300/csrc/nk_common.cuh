@@ -135,6 +135,21 @@ __device__ __forceinline__ Prod<R> warp_prod(Prod<R> p) {
     return p;
 }
 
+// Same product as warp_prod, renormalised once at the end: when every lane's
+// partial mantissa lies in [1/2, 1) the running products stay >= 2^-32, far
+// from underflow, and scaling by powers of two does not change the rounding
+// of a product, so the result is bit-identical.
+template <typename R>
+__device__ __forceinline__ Prod<R> warp_prod_normalised(Prod<R> p) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        p.m *= __shfl_xor_sync(0xffffffffu, p.m, off);
+        p.e += __shfl_xor_sync(0xffffffffu, p.e, off);
+    }
+    renorm(p);
+    return p;
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
