@@ -293,8 +293,8 @@ def roofline(prof, K, precision):
         peak = FP64_PEAK_TFLOPS if precision == "f64" else FP32_PEAK_TFLOPS
         note = ("FP64 pipe, nominal 1.25 TFLOP/s (of nominal)" if precision == "f64"
                 else "FP32 lanes: 152 SMs x 128 x 2 x 2.07 GHz (of nominal)")
-    elif cls == "chol_update" and precision == "mixed":
-        # executed BF16 tcgen05 MMA flops (7-slice FP64 emulation) vs the measured bf16 peak
+    elif cls in ("chol_update", "gram", "jvp_vjp") and precision == "mixed":
+        # executed BF16 tcgen05 MMA flops (sliced FP64-accurate products) vs the measured bf16 peak
         flops = work
         peaks, src = measured_peaks()
         peak = peaks["bf16_tflops_sustained"]

@@ -401,7 +401,8 @@ size_t nk_request_bytes(const nk_request *req);
  */
 #define NK_PROF_SWEEP 0       /* Metropolis sweeps: work = ratio terms (proposals x M) */
 #define NK_PROF_ELOC 1        /* local energies: work = ratio terms (connections x M) */
-#define NK_PROF_GRAM 2        /* sample-space Gram: work = flops */
+#define NK_PROF_GRAM 2        /* sample-space Gram: work = flops (NK_MIXED: BF16 tensor-core
+                                 MMA flops executed) */
 #define NK_PROF_CHOL_UPDATE 3 /* Cholesky products: NK_F64 trailing updates, work = FP64
                                  flops; NK_MIXED every tensor-core product of the
                                  factorisation (trailing updates and panel solves),
@@ -411,7 +412,8 @@ size_t nk_request_bytes(const nk_request *req);
                                  inverses and the operand slicing, work = FP64 flops
                                  of the diagonal blocks */
 #define NK_PROF_TRSV 5        /* triangular solves: work = flops */
-#define NK_PROF_JVP_VJP 6     /* Jacobian products: work = flops */
+#define NK_PROF_JVP_VJP 6     /* Jacobian products and the batched theta: work = flops
+                                 (NK_MIXED: BF16 tensor-core MMA flops executed) */
 #define NK_PROF_N 8
 nk_status nk_prof_enable(int32_t on);
 /* Number of CUDA kernels this library has launched in this process. */

@@ -381,15 +381,24 @@ __global__ void k_mean_into(int64_t n, double *__restrict__ r) {
     }
 }
 
-__global__ void k_double_center(int64_t n, double *__restrict__ K, const double *__restrict__ r,
-                                double eps) {
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= n * n) return;
-    const int64_t k = idx / n, l = idx % n;
-    double v = (K[idx] - r[k] - r[l] + r[n]) / (double)n;
-    if (k == l) v += eps;
-    K[idx] = v;
+// K_kl <- (K_kl - r_k - r_l + rbar) / n (+ eps on the diagonal), written
+// as fma(K_kl - r_l, 1/n, (rbar - r_k) / n): two FP64 operations per entry
+// (the FP64 pipe bounds this kernel, not HBM).  Rows in blockIdx.y (grid-
+// stride), 256 columns per block in blockIdx.x; lower_only leaves the part
+// above the diagonal untouched.
+__global__ void k_double_center(int64_t n, double *__restrict__ K, const double *__restrict__ r, double inv_n,
+                                double eps, int lower_only) {
+    const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t k = blockIdx.y; k < n; k += gridDim.y) {
+        if (lower_only && (int64_t)blockIdx.x * blockDim.x > k) continue;  // block-uniform
+        if (l >= n || (lower_only && l > k)) continue;
+        const double bk = (r[n] - r[k]) * inv_n;
+        double v = fma(K[(size_t)k * n + l] - r[l], inv_n, bk);
+        if (k == l) v += eps;
+        K[(size_t)k * n + l] = v;
+    }
 }
+
 
 // ------------------------------------------------------------- Cholesky ---
 
@@ -734,6 +743,11 @@ __global__ void k_write_sr_stats(const double *__restrict__ st3, const unsigned 
 
 inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+void launch_double_center(int64_t n, double *K, const double *r, double eps, bool lower_only, cudaStream_t st) {
+    const dim3 grid(nblk(n, 256), (unsigned)(n < 65535 ? n : 65535));
+    (k_double_center<<<grid, 256, 0, st>>>(n, K, r, 1.0 / (double)n, eps, lower_only ? 1 : 0), nk::note_launch());
+}
+
 }  // namespace
 
 // ============================================================ launchers ====
@@ -837,14 +851,15 @@ cudaError_t launch_gram_samplespace(int N, int M, int64_t Ns, const int8_t *s, c
     prof_end(slot, st, (double)Ns * (Ns + 1) * (double)(N + M));
     (k_row_mean<<<nblk(Ns, 8), 256, 0, st>>>(Ns, K, rowmean), nk::note_launch());
     (k_mean_into<<<1, 1024, 0, st>>>(Ns, rowmean), nk::note_launch());
-    (k_double_center<<<nblk(Ns * Ns, 256), 256, 0, st>>>(Ns, K, rowmean, eps), nk::note_launch());
+    launch_double_center(Ns, K, rowmean, eps, false, st);
     return cudaGetLastError();
 }
 
+// The tensor-core Cholesky reads only the lower triangle.
 cudaError_t launch_center_gram(int64_t Ns, double *K, double *rowmean, double eps, cudaStream_t st) {
     (k_row_mean<<<nblk(Ns, 8), 256, 0, st>>>(Ns, K, rowmean), nk::note_launch());
     (k_mean_into<<<1, 1024, 0, st>>>(Ns, rowmean), nk::note_launch());
-    (k_double_center<<<nblk(Ns * Ns, 256), 256, 0, st>>>(Ns, K, rowmean, eps), nk::note_launch());
+    launch_double_center(Ns, K, rowmean, eps, true, st);
     return cudaGetLastError();
 }
 

@@ -370,26 +370,34 @@ __global__ void __launch_bounds__(kPThreads, 1)
 constexpr int kNB = 64;
 
 // Factor the kb x kb diagonal block at (k, k) in place (lower).  One CTA of
-// 256 threads holds the block in shared memory and runs the right-looking
-// elimination on unscaled columns: for pivot column c every entry (r, q),
-// c < q <= r, takes a_rq -= a_rc (a_qc / d_c) with d_c the current pivot,
-// which needs one barrier per column.  Thread 0 updates (c+1, c+1) first and
-// then forms the next pivot's reciprocal square root, so the pivots cost no
-// extra barrier.  The stored factor is l_rc = a_rc / sqrt(d_c), l_cc =
-// sqrt(d_c).  FP64 throughput bounds it: kb^3 / 6 FMAs on one SM.
+// 256 threads holds the block in shared memory.  Column c: scale it by
+// 1/sqrt(d_c) (l_cc = sqrt(d_c)), then update the trailing triangle
+// a_rq -= l_rc l_qc, c < q <= r.  This part's FP64 pipe serialises warp
+// instructions whatever their active lanes, so the update is packed: a table
+// lists the entries (r, q) of the 64 x 64 lower triangle by column q
+// descending, the trailing triangle of column c is its first
+// (63 - c)(64 - c)/2 entries, and the threads take them densely.  The
+// thread that updates (c+1, c+1) forms the next pivot.  Two barriers per
+// column; kb^3/6 FMAs.
 constexpr int kPotrfThreads = 256;
 constexpr int kLd = kNB + 1;
+constexpr int kTriEntries = kNB * (kNB - 1) / 2 + 0;  // (r, q) with 1 <= q <= r <= 63: 2016
 
 __global__ void __launch_bounds__(kPotrfThreads) k_potrf64(double *__restrict__ A, int64_t n, int64_t k, int kb,
                                                            int *__restrict__ info) {
     __shared__ double L[kNB * kLd];
-    __shared__ double rdiag[kNB];  // 1 / d_c
+    __shared__ uint16_t tab[kTriEntries];
     __shared__ double rsq[kNB];    // 1 / sqrt(d_c)
     __shared__ double sq[kNB];     // sqrt(d_c)
     const int t = threadIdx.x;
     for (int e = t; e < kNB * kNB; e += kPotrfThreads) {
         const int r = e >> 6, c = e & 63;
         L[r * kLd + c] = (r < kb && c <= r) ? A[(size_t)(k + r) * n + k + c] : 0.0;
+    }
+    // column q (1 .. 63) owns entries [(63 - q)(64 - q)/2, +64 - q): rows q .. 63
+    if (t >= 1 && t < kNB) {
+        const int q = t, s0 = (63 - q) * (64 - q) / 2;
+        for (int r = q; r < kNB; ++r) tab[s0 + r - q] = (uint16_t)((r << 8) | q);
     }
     auto pivot = [&](int c) {
         double d = L[c * kLd + c];
@@ -399,37 +407,38 @@ __global__ void __launch_bounds__(kPotrfThreads) k_potrf64(double *__restrict__ 
         }
         const double r = rsqrt(d);
         rsq[c] = r;
-        rdiag[c] = r * r;
         sq[c] = d * r;
     };
     __syncthreads();
     if (t == 0 && kb > 0) pivot(0);
     __syncthreads();
-    const int ry = t >> 6, cx = t & 63;
     for (int c = 0; c < kb; ++c) {
-        const int q = c + 1 + cx;
-        if (q < kb) {
-            const double m = L[q * kLd + c] * rdiag[c];
-            // thread 0 (cx = 0, ry = 0) starts at (c + 1, c + 1)
-            for (int r = q + ((ry - (q - c - 1)) & 3); r < kb; r += 4)
-                L[r * kLd + q] = fma(-L[r * kLd + c], m, L[r * kLd + q]);
+        // scale column c
+        if (t < kNB && t >= c && t < kb) L[t * kLd + c] = t == c ? sq[c] : L[t * kLd + c] * rsq[c];
+        __syncthreads();
+        // packed trailing update
+        const int P = (63 - c) * (64 - c) / 2;
+        for (int e = t; e < P; e += kPotrfThreads) {
+            const int rq = tab[e], r = rq >> 8, q = rq & 255;
+            L[r * kLd + q] = fma(-L[r * kLd + c], L[q * kLd + c], L[r * kLd + q]);
         }
-        if (t == 0 && c + 1 < kb) pivot(c + 1);
+        // entry (c+1, c+1) is the first of column c+1: index (62 - c)(63 - c)/2
+        if (c + 1 < kb && t == ((62 - c) * (63 - c) / 2) % kPotrfThreads) pivot(c + 1);
         __syncthreads();
     }
     for (int e = t; e < kNB * kNB; e += kPotrfThreads) {
         const int r = e >> 6, c = e & 63;
-        if (r < kb && c <= r) A[(size_t)(k + r) * n + k + c] = r == c ? sq[c] : L[r * kLd + c] * rsq[c];
+        if (r < kb && c <= r) A[(size_t)(k + r) * n + k + c] = L[r * kLd + c];
     }
 }
 
 // Linv = L^-1 for the factored kb x kb diagonal block at (k, k): a lower-
 // triangular 64 x 64 block, zero above the diagonal and beyond kb.  Column j
 // of the inverse solves L x = e_j by forward substitution; one warp per
-// column (16 CTAs x 4 warps), lanes holding rows lane and lane + 32, x_i
-// broadcast by shuffle and eliminated from the rows below with one FMA per
-// lane, so the 64 columns run on 16 SMs at once.
-constexpr int kTrtriWarps = 4;
+// column (64 CTAs of one warp: this part's FP64 pipe serialises the warps
+// of an SM), lanes holding rows lane and lane + 32, x_i broadcast by shuffle
+// and eliminated from the rows below with one FMA per lane.
+constexpr int kTrtriWarps = 1;
 
 __global__ void __launch_bounds__(32 * kTrtriWarps) k_trtri64(const double *__restrict__ A, int64_t n, int64_t k,
                                                               int kb, double *__restrict__ Linv) {
@@ -440,7 +449,7 @@ __global__ void __launch_bounds__(32 * kTrtriWarps) k_trtri64(const double *__re
         const int r = e >> 6, c = e & 63;
         L[r * kLd + c] = (r < kb && c <= r) ? A[(size_t)(k + r) * n + k + c] : 0.0;
     }
-    if (t < kNB) rd[t] = t < kb ? 1.0 / A[(size_t)(k + t) * n + k + t] : 0.0;
+    for (int i = t; i < kNB; i += 32 * kTrtriWarps) rd[i] = i < kb ? 1.0 / A[(size_t)(k + i) * n + k + i] : 0.0;
     __syncthreads();
     const int j = blockIdx.x * kTrtriWarps + (t >> 5);
     double acc0 = lane == j ? 1.0 : 0.0, acc1 = lane + 32 == j ? 1.0 : 0.0;
@@ -926,7 +935,7 @@ cudaError_t launch_gram_tc(int N, int M, int64_t Ns, const int8_t *s, const doub
     }
     dim3 grid(nblk(Ns, 64), nblk(Ns, 64));
     (k_gram_combine<<<grid, 256, 0, st>>>(N, Ns, s, K), nk::note_launch());
-    prof_end(slot, st, (double)Ns * (Ns + 1) * (double)(N + M));
+    prof_end(slot, st, (double)((M + kTileK - 1) / kTileK) * ozaki_mma_flops(Ns, Ns, S, true));
     return cudaGetLastError();
 }
 
