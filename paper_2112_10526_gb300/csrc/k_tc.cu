@@ -506,12 +506,11 @@ __device__ bool advance_ready(const int *flags, int want, int dir, int stop, int
         if (r != stop) {
             for (long long it = 0;; ++it) {
                 if (ld_acquire_flag(flags + r) == want) break;
-                if ((it & 63) == 63 && global_ns() - t0 > kWaitNs) {
+                if ((it & 255) == 255 && global_ns() - t0 > kWaitNs) {
                     atomicExch(err, code);
                     ok = 0;
                     break;
                 }
-                __nanosleep(64);
             }
             if (ok) {
                 r += dir;
@@ -545,8 +544,26 @@ __global__ void __launch_bounds__(kTrsvThreads) k_trsv_fwd(const double *__restr
         for (int u = 0; u < 8; ++u) part[u] = 0.0;
         int j = 0;
         while (j < i) {
+            // block j is the next one needed: its L entries are loaded before
+            // the wait for y_j, so that only FMAs follow the flag
+            double p0[8], p1[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int r = warp * 8 + u;
+                const double *row = L + (size_t)(r0 + (r < kb ? r : 0)) * n + (int64_t)j * kNB;
+                p0[u] = row[lane];
+                p1[u] = row[lane + 32];
+            }
             if (!advance_ready(flags, 1, 1, i, &ready, err, 6)) return;
             const int upto = ready;
+            {
+                const int64_t c0 = (int64_t)j * kNB;
+                const double y0 = __ldcg(b + c0 + lane), y1 = __ldcg(b + c0 + lane + 32);
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (warp * 8 + u < kb) part[u] = fma(p0[u], y0, fma(p1[u], y1, part[u]));
+                ++j;
+            }
             for (; j < upto; ++j) {
                 const int64_t c0 = (int64_t)j * kNB;  // j < i: a full block
                 const double y0 = __ldcg(b + c0 + lane), y1 = __ldcg(b + c0 + lane + 32);
@@ -608,8 +625,35 @@ __global__ void __launch_bounds__(kTrsvThreads) k_trsv_bwd(const double *__restr
         const bool v0 = lane < kb, v1 = lane + 32 < kb;
         int j = nb - 1;
         while (j > i) {
+            // block j is the next one needed: load its L entries before the wait
+            double q0[8], q1[8];
+            {
+                const int64_t r0 = (int64_t)j * kNB;
+                const int kr = (int)(n - r0 < kNB ? n - r0 : kNB);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int r = warp + 8 * u;
+                    const double *row = L + (size_t)(r0 + (r < kr ? r : 0)) * n + c0;
+                    q0[u] = v0 ? row[lane] : 0.0;
+                    q1[u] = v1 ? row[lane + 32] : 0.0;
+                }
+            }
             if (!advance_ready(flags, 2, -1, i, &ready, err, 7)) return;
             const int downto = ready;
+            {
+                const int64_t r0 = (int64_t)j * kNB;
+                const int kr = (int)(n - r0 < kNB ? n - r0 : kNB);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int r = warp + 8 * u;
+                    if (r < kr) {
+                        const double x = __ldcg(b + r0 + r);
+                        p0 = fma(q0[u], x, p0);
+                        p1 = fma(q1[u], x, p1);
+                    }
+                }
+                --j;
+            }
             for (; j > downto; --j) {
                 const int64_t r0 = (int64_t)j * kNB;
                 const int kr = (int)(n - r0 < kNB ? n - r0 : kNB);
