@@ -386,17 +386,22 @@ __global__ void k_mean_into(int64_t n, double *__restrict__ r) {
 // (the FP64 pipe bounds this kernel, not HBM).  Rows in blockIdx.y (grid-
 // stride), 256 columns per block in blockIdx.x; lower_only leaves the part
 // above the diagonal untouched.
-__global__ void k_double_center(int64_t n, double *__restrict__ K, const double *__restrict__ r, double inv_n,
-                                double eps, int lower_only) {
+__global__ void k_double_center(int64_t n, double *__restrict__ K, const double *__restrict__ r,
+                                const double *__restrict__ bk, double inv_n, double eps, int lower_only) {
     const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     for (int64_t k = blockIdx.y; k < n; k += gridDim.y) {
         if (lower_only && (int64_t)blockIdx.x * blockDim.x > k) continue;  // block-uniform
         if (l >= n || (lower_only && l > k)) continue;
-        const double bk = (r[n] - r[k]) * inv_n;
-        double v = fma(K[(size_t)k * n + l] - r[l], inv_n, bk);
+        double v = fma(K[(size_t)k * n + l] - r[l], inv_n, bk[k]);
         if (k == l) v += eps;
         K[(size_t)k * n + l] = v;
     }
+}
+
+// bk[k] = (rbar - r_k) / n, the per-row part of the double centring.
+__global__ void k_center_rows(int64_t n, const double *__restrict__ r, double inv_n, double *__restrict__ bk) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) bk[k] = (r[n] - r[k]) * inv_n;
 }
 
 
@@ -743,9 +748,14 @@ __global__ void k_write_sr_stats(const double *__restrict__ st3, const unsigned 
 
 inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-void launch_double_center(int64_t n, double *K, const double *r, double eps, bool lower_only, cudaStream_t st) {
+// r holds n + 1 row means (the last the grand mean) followed by room for n
+// per-row coefficients.
+void launch_double_center(int64_t n, double *K, double *r, double eps, bool lower_only, cudaStream_t st) {
+    double *bk = r + n + 1;
+    (k_center_rows<<<nblk(n, 256), 256, 0, st>>>(n, r, 1.0 / (double)n, bk), nk::note_launch());
     const dim3 grid(nblk(n, 256), (unsigned)(n < 65535 ? n : 65535));
-    (k_double_center<<<grid, 256, 0, st>>>(n, K, r, 1.0 / (double)n, eps, lower_only ? 1 : 0), nk::note_launch());
+    (k_double_center<<<grid, 256, 0, st>>>(n, K, r, bk, 1.0 / (double)n, eps, lower_only ? 1 : 0),
+     nk::note_launch());
 }
 
 }  // namespace

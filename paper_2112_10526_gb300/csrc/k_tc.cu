@@ -445,13 +445,15 @@ __global__ void __launch_bounds__(32 * kTrtriWarps) k_trtri64(const double *__re
     __shared__ double L[kNB * kLd];
     __shared__ double rd[kNB];
     const int t = threadIdx.x, lane = t & 31;
-    for (int e = t; e < kNB * kNB; e += 32 * kTrtriWarps) {
-        const int r = e >> 6, c = e & 63;
+    const int j = blockIdx.x * kTrtriWarps + (t >> 5);
+    // column j of the inverse reads only rows and columns j .. 63 of L
+    const int j0 = blockIdx.x * kTrtriWarps, w0 = kNB - j0;
+    for (int e = t; e < w0 * w0; e += 32 * kTrtriWarps) {
+        const int r = j0 + e / w0, c = j0 + e % w0;
         L[r * kLd + c] = (r < kb && c <= r) ? A[(size_t)(k + r) * n + k + c] : 0.0;
     }
-    for (int i = t; i < kNB; i += 32 * kTrtriWarps) rd[i] = i < kb ? 1.0 / A[(size_t)(k + i) * n + k + i] : 0.0;
+    for (int i = j0 + t; i < kNB; i += 32 * kTrtriWarps) rd[i] = i < kb ? 1.0 / A[(size_t)(k + i) * n + k + i] : 0.0;
     __syncthreads();
-    const int j = blockIdx.x * kTrtriWarps + (t >> 5);
     double acc0 = lane == j ? 1.0 : 0.0, acc1 = lane + 32 == j ? 1.0 : 0.0;
     double x0 = 0.0, x1 = 0.0;
     for (int i = j; i < kb; ++i) {  // warp-uniform bounds
@@ -463,8 +465,9 @@ __global__ void __launch_bounds__(32 * kTrtriWarps) k_trtri64(const double *__re
             else
                 x1 = x;
         }
-        acc0 = fma(-L[lane * kLd + i], x, acc0);
-        acc1 = fma(-L[(lane + 32) * kLd + i], x, acc1);
+        // rows above j0 were not loaded and never feed x
+        acc0 = fma(lane >= j0 ? -L[lane * kLd + i] : 0.0, x, acc0);
+        acc1 = fma(lane + 32 >= j0 ? -L[(lane + 32) * kLd + i] : 0.0, x, acc1);
     }
     Linv[(size_t)lane * kNB + j] = x0;
     Linv[(size_t)(lane + 32) * kNB + j] = x1;

@@ -232,7 +232,7 @@ void carve_solve(Carver &c, SolveWs &w, int N, int M, int64_t Ns, int solver, in
         w.U = c.take<double>((size_t)Ns * (M + 1));
         w.w = c.take<double>(Ns);
         w.K = c.take<double>((size_t)Ns * Ns);
-        w.rowmean = c.take<double>(Ns + 1);
+        w.rowmean = c.take<double>(2 * Ns + 1);  // row means, grand mean, centring coefficients
         w.tmp = c.take<double>(Np);
         w.info = c.take<int>(2);
         if (precision == NK_MIXED) w.tc = c.take<char>(nk::tc_chol_ws_bytes(Ns));

@@ -140,11 +140,13 @@ cudaError_t launch_gemv_t(const double *A, int64_t rows, int64_t cols, const dou
 cudaError_t launch_syrk_t(const double *A, int64_t rows, int64_t cols, double scale, double eps,
                           double *C, cudaStream_t st);
 
-// Sample-space Gram K = P (S S^T + T T^T + (T T^T) o (S S^T)) P / Ns + eps I.
+// Sample-space Gram K = P (S S^T + T T^T + (T T^T) o (S S^T)) P / Ns + eps I
+// (rowmean: 2 Ns + 1 doubles of scratch).
 cudaError_t launch_gram_samplespace(int N, int M, int64_t Ns, const int8_t *s, const double *T,
                                     double eps, double *K, double *rowmean, cudaStream_t st);
 
-// Row means, grand mean and K <- P K P / Ns + eps I for a full symmetric K.
+// Row means, grand mean and K <- P K P / Ns + eps I for a full symmetric K
+// (lower triangle written); rowmean holds 2 Ns + 1 doubles of scratch.
 cudaError_t launch_center_gram(int64_t Ns, double *K, double *rowmean, double eps, cudaStream_t st);
 
 // In-place lower Cholesky of an n x n matrix (lda = n); info: device int.
