@@ -280,6 +280,27 @@ def e2e_steps(st, K, dev):
     return dt, bi, bo
 
 
+# DRAM bytes (read + write) of k_ozaki_gemm per 128 x 32 output tile with 7
+# slices, from the ncu capture summarised in
+# profiles/k_ozaki_gemm_wide_update_heis2d_10x10.md (8064 x 8064 lower
+# update: 472.76 MB over 8064 tiles).  Valid while the kernel's source is the
+# one captured: the hash covers the GEMM section of k_tc.cu and tc_ptx.cuh.
+OZAKI_TRAFFIC = {"bytes_per_tile": 58625.8, "source_sha256_prefix": "63abab51bffdae6d"}
+OZAKI_TILE_FLOPS = 28 * 4 * 2.0 * 128 * 32 * 16  # executed BF16 flops per tile (7 slices)
+
+
+def ozaki_source_hash():
+    import hashlib
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2112_10526_gb300", "csrc")
+    try:
+        s = open(os.path.join(here, "k_tc.cu")).read()
+        a = s.index("// ------------------------------------------------------------- the GEMM ---")
+        b = s.index("// ------------------------------------------------- Cholesky building blocks ---")
+        return hashlib.sha256((s[a:b] + open(os.path.join(here, "tc_ptx.cuh")).read()).encode()).hexdigest()
+    except (OSError, ValueError):
+        return ""
+
+
 def roofline(prof, K, precision):
     # dominant tracked kernel class by time
     cls = max(prof, key=lambda c: prof[c][0])
@@ -305,8 +326,13 @@ def roofline(prof, K, precision):
         peak = FP64_PEAK_TFLOPS
         note = "FP64 pipe, nominal 1.25 TFLOP/s (of nominal; no measured FP64 peak)"
     achieved = flops / secs / 1e12
+    traffic = None
+    if cls == "chol_update" and precision == "mixed" and \
+            ozaki_source_hash().startswith(OZAKI_TRAFFIC["source_sha256_prefix"]):
+        # bytes per launch, like achieved: the class's tiles x the captured bytes per tile
+        traffic = work / OZAKI_TILE_FLOPS * OZAKI_TRAFFIC["bytes_per_tile"] / launches
     return {"kernel_class": cls, "bound": bound, "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic, "traffic_unit": "DRAM bytes per launch",
             "peak_source": note, "launches": launches, "avg_launch_ms": ms / launches,
             "share_of_step": ms / 1.0}, cls
 
