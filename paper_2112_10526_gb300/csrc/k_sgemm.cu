@@ -35,41 +35,52 @@ namespace nk {
 namespace {
 
 constexpr int kBM = 128, kBN = 64, kBK = 64;
-constexpr int kStages = 3;
 constexpr int kMaxSB = 7;
 constexpr int kSgThreads = 128;
 constexpr int kAB = kBM * kBK * 2;             // A tile, bytes
 constexpr int kBB = kBN * kBK * 2;             // one B slice tile, bytes
-constexpr int kStageBytes = kAB + kMaxSB * kBB;  // 72 KB
 constexpr int kSgOutLd = kBN + 1;
 
 struct SgArgs {
     int64_t rows, cols;
     int kchunks, SB;
+    int kc_split;         // K-chunks per split (blockIdx.z)
+    int nstages, stage_bytes;
+    uint32_t tmem_cols;
     const int *expB;      // [cols]
-    double *C;
-    int64_t ldc;
-    int mode;             // 0: C = R (+ bias), 1: C -= R, 2: C += R
+    double *C;            // modes 0-2: output (+ blockIdx.z * split_stride); mode 3: row partials
+    int64_t ldc, split_stride;
+    int mode;             // 0: C = R (+ bias), 1: C -= R, 2: C += R, 3: C[row][bx] = sum_col R t'
     const double *bias;   // [cols] or null
+    const double *T;      // mode 3: T [rows][Mt]; t'_col = T[col] for col < Mt, 1 at col = Mt
+    int Mt;
     int *err;
 };
 
-__global__ void __launch_bounds__(kSgThreads, 1)
+// Smem: nstages x (A tile + SB B-slice tiles), reused by the staged output
+// tile after the MMAs.  With SB <= 4 two stages and 256 TMEM columns let two
+// CTAs share an SM, so that one CTA's epilogue overlaps the other's MMAs.
+__global__ void __launch_bounds__(kSgThreads, 2)
     k_sgemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, SgArgs a) {
     extern __shared__ unsigned char smem_raw[];
     const uint32_t base = smem_u32(smem_raw);
     unsigned char *ops = smem_raw + ((1024 - (base & 1023)) & 1023);
-    uint64_t *full = reinterpret_cast<uint64_t *>(ops + (size_t)kStages * kStageBytes);
-    uint64_t *empty = full + kStages;
-    uint64_t *done = empty + kStages;
+    const size_t ops_bytes = (size_t)a.nstages * a.stage_bytes > (size_t)kBM * kSgOutLd * 8
+                                 ? (size_t)a.nstages * a.stage_bytes
+                                 : (size_t)kBM * kSgOutLd * 8;
+    uint64_t *full = reinterpret_cast<uint64_t *>(ops + ops_bytes);
+    uint64_t *empty = full + 4;
+    uint64_t *done = empty + 4;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
     int *abort_flag = reinterpret_cast<int *>(tslot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t m0 = (int64_t)blockIdx.y * kBM, n0 = (int64_t)blockIdx.x * kBN;
-    const int SB = a.SB, KC = a.kchunks;
+    const int SB = a.SB, NS = a.nstages;
+    const int kc0 = (int)blockIdx.z * a.kc_split;
+    const int kc1 = kc0 + a.kc_split < a.kchunks ? kc0 + a.kc_split : a.kchunks;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) {
+        for (int s = 0; s < NS; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
@@ -77,7 +88,7 @@ __global__ void __launch_bounds__(kSgThreads, 1)
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) tmem_alloc(tslot, 512);
+    if (warp == 0) tmem_alloc(tslot, a.tmem_cols);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -86,14 +97,14 @@ __global__ void __launch_bounds__(kSgThreads, 1)
     if (threadIdx.x == 0) {
         // TMA producer
         const uint32_t tx = (uint32_t)(kAB + SB * kBB);
-        for (int kc = 0; kc < KC; ++kc) {
-            const int s = kc % kStages;
-            if (kc >= kStages && !mbar_wait(&empty[s], (uint32_t)(((kc / kStages) - 1) & 1))) {
+        for (int kc = kc0; kc < kc1; ++kc) {
+            const int i = kc - kc0, s = i % NS;
+            if (i >= NS && !mbar_wait(&empty[s], (uint32_t)(((i / NS) - 1) & 1))) {
                 *abort_flag = 1;
                 atomicExch(a.err, 3);
                 break;
             }
-            unsigned char *sp = ops + (size_t)s * kStageBytes;
+            unsigned char *sp = ops + (size_t)s * a.stage_bytes;
             mbar_expect_tx(&full[s], tx);
             tma_load_2d(sp, &mapA, &full[s], kc * kBK, (int)m0);
             for (int t = 0; t < SB; ++t) tma_load_3d(sp + kAB + t * kBB, &mapB, &full[s], kc * kBK, (int)n0, t);
@@ -102,21 +113,21 @@ __global__ void __launch_bounds__(kSgThreads, 1)
         // MMA issuer
         const uint32_t idesc = idesc_bf16(kBM, kBN);
         bool ok = true;
-        for (int kc = 0; kc < KC; ++kc) {
-            const int s = kc % kStages;
-            if (!mbar_wait(&full[s], (uint32_t)((kc / kStages) & 1))) {
+        for (int kc = kc0; kc < kc1; ++kc) {
+            const int i = kc - kc0, s = i % NS;
+            if (!mbar_wait(&full[s], (uint32_t)((i / NS) & 1))) {
                 ok = false;
                 break;
             }
             tc_fence_after();
-            unsigned char *sp = ops + (size_t)s * kStageBytes;
+            unsigned char *sp = ops + (size_t)s * a.stage_bytes;
             const uint64_t da = sw128_desc(sp);
             for (int t = 0; t < SB; ++t) {
                 const uint64_t db = sw128_desc(sp + kAB + t * kBB);
 #pragma unroll
                 for (int kk = 0; kk < kBK / 16; ++kk)
                     umma_bf16(tmem + (uint32_t)(t * kBN), da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
-                              (kc > 0 || kk > 0) ? 1u : 0u);
+                              (i > 0 || kk > 0) ? 1u : 0u);
             }
             umma_commit(&empty[s]);
         }
@@ -128,6 +139,8 @@ __global__ void __launch_bounds__(kSgThreads, 1)
     }
     __syncthreads();
     double *tile = reinterpret_cast<double *>(ops);
+    const int rloc = warp * 32 + lane;
+    const int64_t row = m0 + rloc;
     if (!*abort_flag) {
         int ok = 1;
         if (lane == 0) ok = mbar_wait(done, 0) ? 1 : 0;
@@ -139,38 +152,52 @@ __global__ void __launch_bounds__(kSgThreads, 1)
             }
         } else {
             tc_fence_after();
-            const int rloc = warp * 32 + lane;
             const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-            for (int c0 = 0; c0 < kBN; c0 += 16) {
-                // V = sum_t D_t 2^(8 (7 - t)) = hi 2^32 + lo
-                long long hi[16], lo[16];
+            const bool row_ok = row < a.rows;
+            const double *trow = (a.mode == 3 && row_ok) ? a.T + (size_t)row * a.Mt : nullptr;
+            double racc = 0.0;
+#pragma unroll 1
+            for (int c8 = 0; c8 < kBN; c8 += 8) {
+                // column exponents of this chunk (lane & 7) and, for the fused
+                // row product, the chunk's t' values, loaded before the TMEM drain
+                const int64_t fcol = n0 + c8 + (lane & 7);
+                const int fj_lane = fcol < a.cols ? a.expB[fcol] : 0;
+                double tv[8];
+                if (a.mode == 3) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j) hi[j] = lo[j] = 0;
-                for (int t = 1; t <= SB; ++t) {
-                    uint32_t r[16];
-                    tmem_ld16(lane_base + (uint32_t)((t - 1) * kBN + c0), r);
-                    tmem_wait_ld();
-                    if (t <= 3) {
-                        const int sh = 8 * (3 - t);
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) hi[j] += (long long)__float2int_rn(__uint_as_float(r[j])) << sh;
-                    } else {
-                        const int sh = 8 * (7 - t);
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) lo[j] += (long long)__float2int_rn(__uint_as_float(r[j])) << sh;
+                    for (int j = 0; j < 8; ++j) {
+                        const int64_t col = n0 + c8 + j;
+                        tv[j] = trow == nullptr ? 0.0 : (col < a.Mt ? trow[col] : (col == a.Mt ? 1.0 : 0.0));
                     }
                 }
+                uint32_t r[kMaxSB][8];
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int64_t col = n0 + c0 + j;
-                    const int fn = col < a.cols ? a.expB[col] : 0;
-                    tile[rloc * kSgOutLd + c0 + j] = fixed_to_double(hi[j], lo[j], fn - 56);
+                for (int t = 0; t < kMaxSB; ++t)
+                    if (t < SB) tmem_ld8(lane_base + (uint32_t)(t * kBN + c8), r[t]);
+                tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    int d[kMaxSB];
+#pragma unroll
+                    for (int t = 0; t < kMaxSB; ++t) d[t] = t < SB ? __float2int_rn(__uint_as_float(r[t][j])) : 0;
+                    // V = sum_t D_t 2^(8 (7 - t)) = hi 2^32 + lo: slices 1 .. 3 in hi, 4 .. 7 in lo
+                    const long long hi = (long long)d[0] * 65536 + (long long)d[1] * 256 + d[2];
+                    const long long lo =
+                        (long long)d[3] * 16777216 + (long long)d[4] * 65536 + (long long)d[5] * 256 + d[6];
+                    const int fn = __shfl_sync(0xffffffffu, fj_lane, j);
+                    const double v = fixed_to_double_sat(hi, lo, fn - 56);
+                    if (a.mode == 3)
+                        racc = fma(v, tv[j], racc);
+                    else
+                        tile[rloc * kSgOutLd + c8 + j] = v;
                 }
             }
+            if (a.mode == 3 && row_ok) a.C[(size_t)row * a.ldc + blockIdx.x] = racc;
         }
     }
     __syncthreads();
-    if (!*abort_flag) {
+    if (!*abort_flag && a.mode != 3) {
+        double *C = a.C + (size_t)blockIdx.z * a.split_stride;
         const int cx = threadIdx.x & 63, ry = threadIdx.x >> 6;
         const int64_t col = n0 + cx;
         constexpr int kStep = kSgThreads / 64, kBatch = 8;
@@ -183,15 +210,14 @@ __global__ void __launch_bounds__(kSgThreads, 1)
                 for (int u = 0; u < kBatch; ++u) {
                     const int rl = rb + kStep * u;
                     on[u] = rl < kBM && m0 + rl < a.rows;
-                    cv[u] = (on[u] && a.mode != 0) ? a.C[(size_t)(m0 + rl) * a.ldc + col] : 0.0;
+                    cv[u] = (on[u] && a.mode != 0) ? C[(size_t)(m0 + rl) * a.ldc + col] : 0.0;
                 }
 #pragma unroll
                 for (int u = 0; u < kBatch; ++u) {
                     if (!on[u]) continue;
                     const int rl = rb + kStep * u;
                     const double v = tile[rl * kSgOutLd + cx];
-                    a.C[(size_t)(m0 + rl) * a.ldc + col] =
-                        a.mode == 0 ? v + bcol : (a.mode == 1 ? cv[u] - v : cv[u] + v);
+                    C[(size_t)(m0 + rl) * a.ldc + col] = a.mode == 0 ? v + bcol : (a.mode == 1 ? cv[u] - v : cv[u] + v);
                 }
             }
         }
@@ -200,12 +226,16 @@ __global__ void __launch_bounds__(kSgThreads, 1)
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        tmem_dealloc(tmem, 512);
+        tmem_dealloc(tmem, a.tmem_cols);
     }
 }
 
-size_t sgemm_smem_bytes() {
-    return 1024 + (size_t)kStages * kStageBytes + (2 * kStages + 1) * sizeof(uint64_t) + 16;
+int sgemm_stages(int SB) { return SB <= 4 ? 2 : 3; }
+
+size_t sgemm_smem_bytes(int SB) {
+    const size_t st = (size_t)sgemm_stages(SB) * (kAB + SB * kBB);
+    const size_t tile = (size_t)kBM * kSgOutLd * 8;
+    return 1024 + (st > tile ? st : tile) + 9 * sizeof(uint64_t) + 16;
 }
 
 // ------------------------------------------------------- operand staging ---
@@ -363,12 +393,23 @@ __global__ void k_tg_slice(const double *__restrict__ T, const double *__restric
 }
 
 // P^T [N+1][M+1] (row i, column j) -> J^T g in the parameter layout.
-__global__ void k_scatter_vjp(int N, int M, const double *__restrict__ PT, double *__restrict__ out) {
+// w[row] = sum over the ntc column tiles of P[row][t], in tile order.
+__global__ void k_rowsum_partials(int64_t rows, int ntc, const double *__restrict__ P, double *__restrict__ w) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    double acc = 0.0;
+    for (int t = 0; t < ntc; ++t) acc += P[(size_t)r * ntc + t];
+    w[r] = acc;
+}
+
+// PT holds ks K-split partial products [ks][(N+1)][(M+1)], summed in order.
+__global__ void k_scatter_vjp(int N, int M, int ks, const double *__restrict__ PT, double *__restrict__ out) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t tot = (int64_t)(N + 1) * (M + 1);
     if (idx >= tot) return;
     const int i = (int)(idx / (M + 1)), j = (int)(idx % (M + 1));
-    const double v = PT[idx];
+    double v = PT[idx];
+    for (int z = 1; z < ks; ++z) v += PT[(size_t)z * tot + idx];
     if (i == N && j == M) return;
     if (j == M)
         out[i] = v;
@@ -422,19 +463,29 @@ bool make_sliced_map(CUtensorMap *map, const __nv_bfloat16 *p, int64_t rows, int
 }
 
 // C (mode) A B^T + bias: A BF16 [rows][ldA] (K used), B slices [SB][cols][ldB].
+// ksplit > 1 (mode 0 only): split z of the K range writes C + z split_stride.
+// mode 3: C [rows][ldc >= col tiles] receives, per 64-column tile, the row
+// products sum_col R[row][col] t'_col with t' = [T[row][0 .. Mt-1], 1, 0 ...].
 cudaError_t sgemm(const __nv_bfloat16 *A, int64_t rows, int64_t ldA, const __nv_bfloat16 *Bsl, const int *expB,
                   int64_t cols, int64_t ldB, int64_t K, int SB, double *C, int64_t ldc, int mode,
-                  const double *bias, int *err, cudaStream_t st) {
+                  const double *bias, int *err, cudaStream_t st, const double *T = nullptr, int Mt = 0,
+                  int ksplit = 1, int64_t split_stride = 0) {
     if (rows <= 0 || cols <= 0 || K <= 0) return cudaSuccess;
     if (SB < 1 || SB > kMaxSB || rows > (1LL << 31) - kBM || cols > (1LL << 31) - kBN) return cudaErrorInvalidValue;
+    if (ksplit < 1 || (ksplit > 1 && mode != 0) || (mode == 3 && T == nullptr)) return cudaErrorInvalidValue;
     CUtensorMap ma, mb;
     if (!make_rows_map(&ma, A, rows, K, ldA, kBM) || !make_sliced_map(&mb, Bsl, cols, K, ldB, SB, kBN))
         return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(k_sgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sgemm_smem_bytes());
+    cudaError_t e = nk::allow_max_dynamic_smem((const void *)k_sgemm);
     if (e != cudaSuccess) return e;
-    SgArgs a{rows, cols, (int)((K + kBK - 1) / kBK), SB, expB, C, ldc, mode, bias, err};
-    dim3 grid(nblk(cols, kBN), nblk(rows, kBM));
-    (k_sgemm<<<grid, kSgThreads, sgemm_smem_bytes(), st>>>(ma, mb, a), nk::note_launch());
+    const int kchunks = (int)((K + kBK - 1) / kBK);
+    const int kc_split = (kchunks + ksplit - 1) / ksplit;
+    uint32_t tcols = 32;
+    while (tcols < (uint32_t)(SB * kBN)) tcols <<= 1;
+    SgArgs a{rows, cols, kchunks, SB, kc_split, sgemm_stages(SB), kAB + SB * kBB, tcols, expB, C, ldc,
+             split_stride, mode, bias, T, Mt, err};
+    dim3 grid(nblk(cols, kBN), nblk(rows, kBM), (unsigned)((kchunks + kc_split - 1) / kc_split));
+    (k_sgemm<<<grid, kSgThreads, sgemm_smem_bytes(SB), st>>>(ma, mb, a), nk::note_launch());
     return cudaGetLastError();
 }
 
@@ -476,13 +527,14 @@ cudaError_t launch_theta_tc(int N, int M, const double *b, const double *W, cons
 }
 
 size_t tc_jvp_ws_bytes(int N, int M, int64_t Ns) {
-    const int64_t ld = pad8(N + 1);
+    const int64_t ld = pad8(N + 1), ntc = (M + 1 + kBN - 1) / kBN;
     return ((size_t)Ns * ld * 2 + 255) / 256 * 256 + ((size_t)kMaxSB * (M + 1) * ld * 2 + 255) / 256 * 256 +
            ((size_t)(M + 1) * (N + 1) * 8 + 255) / 256 * 256 + ((size_t)(M + 1) * 4 + 255) / 256 * 256 +
-           ((size_t)Ns * (M + 1) * 8 + 255) / 256 * 256 + 256;
+           ((size_t)Ns * ntc * 8 + 255) / 256 * 256 + 256;
 }
 
-// out = J v with V' cut into SB slices: U' = S' V'^T, w = rowdot(T', U').
+// out = J v with V' cut into SB slices: w = rowdot(T', S' V'^T), the row
+// products taken in the S-GEMM epilogue per 64-column tile and summed after.
 cudaError_t launch_jvp_tc(int N, int M, int64_t Ns, const int8_t *s, const double *T, const double *v,
                           double *out, int SB, int *err, void *ws, cudaStream_t st) {
     const int64_t ld = pad8(N + 1);
@@ -496,22 +548,27 @@ cudaError_t launch_jvp_tc(int N, int M, int64_t Ns, const int8_t *s, const doubl
     auto *Vs = reinterpret_cast<__nv_bfloat16 *>(take((size_t)kMaxSB * (M + 1) * ld * 2));
     auto *Vp = reinterpret_cast<double *>(take((size_t)(M + 1) * (N + 1) * 8));
     auto *ev = reinterpret_cast<int *>(take((size_t)(M + 1) * 4));
-    auto *U = reinterpret_cast<double *>(take((size_t)Ns * (M + 1) * 8));
+    const int ntc = (M + 1 + kBN - 1) / kBN;
+    auto *P = reinterpret_cast<double *>(take((size_t)Ns * ntc * 8));
     const int64_t tot = (int64_t)(M + 1) * (N + 1);
     (k_pm1_rows<<<nblk(Ns * ld, 256), 256, 0, st>>>(s, Ns, N, 1, ld, As), nk::note_launch());
     (k_build_vaug<<<nblk(tot, 256), 256, 0, st>>>(N, M, v, Vp), nk::note_launch());
     (k_slice_long_rows<<<M + 1, 128, 0, st>>>(Vp, N + 1, M + 1, N + 1, nullptr, SB, ld, Vs, ev), nk::note_launch());
     const int slot = prof_begin(NK_PROF_JVP_VJP, st);
-    cudaError_t e = sgemm(As, Ns, ld, Vs, ev, M + 1, ld, N + 1, SB, U, M + 1, 0, nullptr, err, st);
+    cudaError_t e = sgemm(As, Ns, ld, Vs, ev, M + 1, ld, N + 1, SB, P, ntc, 3, nullptr, err, st, T, M);
     prof_end(slot, st, sgemm_flops(Ns, M + 1, N + 1, SB));
     if (e != cudaSuccess) return e;
-    return launch_rowdot_aug(M, Ns, T, U, out, st);
+    (k_rowsum_partials<<<nblk(Ns, 256), 256, 0, st>>>(Ns, ntc, P, out), nk::note_launch());
+    return cudaGetLastError();
 }
+
+constexpr int kMaxKSplit = 8;
 
 size_t tc_vjp_ws_bytes(int N, int M, int64_t Ns) {
     const int64_t ld = pad8(Ns);
     return ((size_t)(N + 1) * ld * 2 + 255) / 256 * 256 + ((size_t)kMaxSB * (M + 1) * ld * 2 + 255) / 256 * 256 +
-           ((size_t)(M + 1) * 4 + 255) / 256 * 256 + ((size_t)(N + 1) * (M + 1) * 8 + 255) / 256 * 256 + 256;
+           ((size_t)(M + 1) * 4 + 255) / 256 * 256 +
+           ((size_t)kMaxKSplit * (N + 1) * (M + 1) * 8 + 255) / 256 * 256 + 256;
 }
 
 // out = J^T g' with g' = scale (g - shift), (T' o g')^T cut into SB slices.
@@ -528,7 +585,7 @@ cudaError_t launch_vjp_tc(int N, int M, int64_t Ns, const int8_t *s, const doubl
     auto *St = reinterpret_cast<__nv_bfloat16 *>(take((size_t)(N + 1) * ld * 2));
     auto *Gs = reinterpret_cast<__nv_bfloat16 *>(take((size_t)kMaxSB * (M + 1) * ld * 2));
     auto *eg = reinterpret_cast<int *>(take((size_t)(M + 1) * 4));
-    auto *PT = reinterpret_cast<double *>(take((size_t)(N + 1) * (M + 1) * 8));
+    auto *PT = reinterpret_cast<double *>(take((size_t)kMaxKSplit * (N + 1) * (M + 1) * 8));
     dim3 tb(32, 8);
     (k_pm1_cols<<<dim3(nblk(ld, 32), nblk(N + 1, 32)), tb, 0, st>>>(s, Ns, N, ld, St), nk::note_launch());
     (k_fill_int<<<nblk(M + 1, 256), 256, 0, st>>>(M + 1, -100000, eg), nk::note_launch());
@@ -536,12 +593,25 @@ cudaError_t launch_vjp_tc(int N, int M, int64_t Ns, const int8_t *s, const doubl
      nk::note_launch());
     (k_tg_slice<<<dim3(nblk(ld, 32), nblk(M + 1, 32)), tb, 0, st>>>(T, g, scale, shift, Ns, M, SB, ld, eg, Gs),
      nk::note_launch());
+    // split the long K = Ns range until the grid covers the SMs twice
+    // (every split keeps >= 4 chunks; each split's FP32 levels stay exact)
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int64_t tiles = (int64_t)nblk(M + 1, kBN) * nblk(N + 1, kBM), kchunks = (Ns + kBK - 1) / kBK;
+    int ks = (int)((2 * (int64_t)sms + tiles - 1) / tiles);
+    if (ks > kMaxKSplit) ks = kMaxKSplit;
+    if (ks > kchunks / 4) ks = (int)(kchunks / 4);
+    if (ks < 1) ks = 1;
+    const int kc_split = (int)((kchunks + ks - 1) / ks);
+    ks = (int)((kchunks + kc_split - 1) / kc_split);  // splits the kernel launches
+    const int64_t tot = (int64_t)(N + 1) * (M + 1);
     const int slot = prof_begin(NK_PROF_JVP_VJP, st);
-    cudaError_t e = sgemm(St, N + 1, ld, Gs, eg, M + 1, ld, Ns, SB, PT, M + 1, 0, nullptr, err, st);
+    e = sgemm(St, N + 1, ld, Gs, eg, M + 1, ld, Ns, SB, PT, M + 1, 0, nullptr, err, st, nullptr, 0, ks, tot);
     prof_end(slot, st, sgemm_flops(N + 1, M + 1, Ns, SB));
     if (e != cudaSuccess) return e;
-    const int64_t tot = (int64_t)(N + 1) * (M + 1);
-    (k_scatter_vjp<<<nblk(tot, 256), 256, 0, st>>>(N, M, PT, out), nk::note_launch());
+    (k_scatter_vjp<<<nblk(tot, 256), 256, 0, st>>>(N, M, ks, PT, out), nk::note_launch());
     return cudaGetLastError();
 }
 
