@@ -344,9 +344,27 @@ __global__ void __launch_bounds__(128) k_sweep(SweepK<R> P) {
             const bool accept = lu < Acc(2) * delta;
             if (lane == 0 && A.decisions) A.decisions[slot] = accept ? 1 : 0;
             if (accept) {
-                for (int j = lane; j < M; j += 32) {
-                    const R tj = t[j], tv = si * tau[j];
-                    t[j] = (tj - tv) / (R(1) - tj * tv);
+                if (kF32 && P.vec4) {
+                    // FP32 path: 16-byte accesses, fast division (t is rebuilt
+                    // exactly from theta after every sweep)
+                    float *tf = reinterpret_cast<float *>(t);
+                    const float *uf = reinterpret_cast<const float *>(tau);
+                    const float sf = (float)si;
+                    for (int j = 4 * lane; j < M; j += 128) {
+                        float4 tv = *reinterpret_cast<const float4 *>(tf + j);
+                        const float4 uv = __ldg(reinterpret_cast<const float4 *>(uf + j));
+                        const float v0 = sf * uv.x, v1 = sf * uv.y, v2 = sf * uv.z, v3 = sf * uv.w;
+                        tv.x = __fdividef(tv.x - v0, fmaf(-tv.x, v0, 1.f));
+                        tv.y = __fdividef(tv.y - v1, fmaf(-tv.y, v1, 1.f));
+                        tv.z = __fdividef(tv.z - v2, fmaf(-tv.z, v2, 1.f));
+                        tv.w = __fdividef(tv.w - v3, fmaf(-tv.w, v3, 1.f));
+                        *reinterpret_cast<float4 *>(tf + j) = tv;
+                    }
+                } else {
+                    for (int j = lane; j < M; j += 32) {
+                        const R tj = t[j], tv = si * tau[j];
+                        t[j] = (tj - tv) / (R(1) - tj * tv);
+                    }
                 }
                 __syncwarp();
                 if (lane == 0) {
