@@ -552,26 +552,31 @@ __global__ void __launch_bounds__(kEW * 32) k_eloc_batched(ElocBK P) {
         d = warp_sum(d);
         if (lane == 0) diag[warp] = d;
     }
-    double off[kEG];
+    // FP32 path: ratios, exponentials and the per-warp partial sums in FP32
+    // lanes (each warp adds about nconn / kEW terms); the diagonal part and
+    // the final sum stay in FP64.
+    float off[kEG];
 #pragma unroll
-    for (int g = 0; g < kEG; ++g) off[g] = 0.0;
+    for (int g = 0; g < kEG; ++g) off[g] = 0.f;
     const bool tfim = A.kind == NK_TFIM;
     const int nconn = tfim ? N : E;
-    const double hoff = A.marshall ? -2.0 * A.J : 2.0 * A.J;
+    const float hoff = (float)(A.marshall ? -2.0 * A.J : 2.0 * A.J), hfield = (float)(-A.h);
     for (int c = warp; c < nconn; c += kEW) {
         int i, kk = -1;
         const float *tau;
-        float K;
+        float K, aa;
         if (tfim) {
             i = c;
             tau = T.tau_site + (size_t)c * M;
             K = T.K_site[c];
+            aa = (float)T.a[i];
         } else {
             i = T.edges[2 * c];
             kk = T.edges[2 * c + 1];
             if ((unsigned)i >= (unsigned)N || (unsigned)kk >= (unsigned)N) continue;
             tau = T.tau_edge + (size_t)c * M;
             K = T.K_edge[c];
+            aa = (float)(T.a[i] - T.a[kk]);
         }
         unsigned active = 0;
 #pragma unroll
@@ -613,15 +618,14 @@ __global__ void __launch_bounds__(kEW * 32) k_eloc_batched(ElocBK P) {
             if (!(active & (1u << g))) continue;
             Prod<float> p{m[g], ex[g]};
             renorm(p);
-            p = warp_prod(p);
-            double d0 = tfim ? -2.0 * T.a[i] * (double)sg[g] : -2.0 * (double)sg[g] * (T.a[i] - T.a[kk]);
-            const double delta = d0 + (double)(K + prod_log(p));
-            off[g] += (tfim ? -A.h : hoff) * exp(delta);
+            p = warp_prod_normalised(p);
+            const float delta = -2.f * aa * sg[g] + (K + prod_log(p));
+            off[g] = fmaf(tfim ? hfield : hoff, expf(delta), off[g]);
         }
     }
     if (lane == 0) {
 #pragma unroll
-        for (int g = 0; g < kEG; ++g) part[warp * kEG + g] = off[g];
+        for (int g = 0; g < kEG; ++g) part[warp * kEG + g] = (double)off[g];
     }
     __syncthreads();
     if (threadIdx.x < G) {
