@@ -506,7 +506,7 @@ __global__ void __launch_bounds__(128) k_eloc(ElocK<R> P) {
 // edges) in turn, loads each tau row once (16-byte loads, lanes over units)
 // and applies it to all kEG samples, so the tau traffic per ratio term drops
 // kEG-fold.  One warp reduction per (connection, sample).
-constexpr int kEG = 8, kEW = 8;
+constexpr int kEG = 8, kEW = 16;
 
 struct ElocBK {
     Tables<float> t;
@@ -773,6 +773,11 @@ cudaError_t launch_sweep(const Tables<R> &t, const SweepArgs &a, cudaStream_t st
 template cudaError_t launch_sweep<double>(const Tables<double> &, const SweepArgs &, cudaStream_t);
 template cudaError_t launch_sweep<float>(const Tables<float> &, const SweepArgs &, cudaStream_t);
 
+size_t eloc_batched_smem(int N, int M) {
+    const size_t t_ld = (size_t)(M + 3) / 4 * 4, s_ld = (size_t)(N + 15) / 16 * 16;
+    return (size_t)kEG * t_ld * 4 + (size_t)kEG * s_ld + (size_t)(kEW * kEG + kEG) * 8;
+}
+
 template <typename R>
 cudaError_t launch_eloc_batched(const Tables<R> &, const ElocArgs &, cudaStream_t) {
     return cudaErrorNotSupported;
@@ -785,7 +790,7 @@ cudaError_t launch_eloc_batched<float>(const Tables<float> &t, const ElocArgs &a
     P.a = a;
     P.t_ld = (t.M + 3) / 4 * 4;
     P.s_ld = (t.N + 15) / 16 * 16;
-    const size_t smem = (size_t)kEG * P.t_ld * 4 + (size_t)kEG * P.s_ld + (size_t)(kEW * kEG + kEG) * 8;
+    const size_t smem = eloc_batched_smem(t.N, t.M);
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
     cudaError_t err = nk::allow_max_dynamic_smem((const void *)k_eloc_batched);
     if (err != cudaSuccess) return err;
@@ -801,7 +806,7 @@ template <typename R>
 cudaError_t launch_eloc(const Tables<R> &t, const ElocArgs &a, cudaStream_t st) {
     if (a.Ns <= 0) return cudaSuccess;
     if (sizeof(R) == 4 && a.theta_in && t.M >= kUnitsMappingM && (t.M % 4) == 0 &&
-        (size_t)kEG * ((t.M + 3) / 4 * 4) * 4 + (size_t)kEG * ((t.N + 15) / 16 * 16) + 1024 <= 227 * 1024)
+        eloc_batched_smem(t.N, t.M) <= 227 * 1024)
         return launch_eloc_batched<R>(t, a, st);
     ElocK<R> P;
     P.t = t;
