@@ -345,16 +345,28 @@ __global__ void k_fill_int(int64_t n, int v, int *__restrict__ x) {
 // Exponent of every row j <= M of (T' o g)^T: max over samples k of
 // |t'_kj g'_k|, t'_kM = 1, g'_k = scale (g_k - shift).  Blocks of 32 rows x
 // 256 samples, combined with atomicMax (-100000 marks an all-zero row).
-__global__ void k_tg_colexp(const double *__restrict__ T, const double *__restrict__ g, double scale,
-                            const double *__restrict__ shift, int64_t Ns, int M, int *__restrict__ expo) {
+// g'_k = scale (g_k - shift) and its exponent (|g'_k| < 2^ge_k).
+__global__ void k_scale_g(int64_t Ns, const double *__restrict__ g, double scale, const double *__restrict__ shift,
+                          double *__restrict__ gp, int *__restrict__ ge) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= Ns) return;
+    const double v = scale * (g[k] - (shift ? *shift : 0.0));
+    gp[k] = v;
+    ge[k] = exp_of(v);
+}
+
+// Column exponents of T' o g' (column j of (T' o g')^T): an upper bound
+// max_k (exp(T'_kj) + exp(g'_k)) of the exact exponent, at most one above it,
+// taken with integer operations only.
+__global__ void k_tg_colexp(const double *__restrict__ T, const int *__restrict__ ge, int64_t Ns, int M,
+                            int *__restrict__ expo) {
     const int j = blockIdx.x * 32 + threadIdx.x;
     const int64_t k0 = (int64_t)blockIdx.y * 256;
-    const double sh = shift ? *shift : 0.0;
     int ex = -100000;
     if (j <= M) {
         for (int64_t k = k0 + threadIdx.y; k < k0 + 256 && k < Ns; k += blockDim.y) {
-            const double gk = scale * (g[k] - sh);
-            ex = max(ex, exp_of((j < M ? T[(size_t)k * M + j] : 1.0) * gk));
+            const int et = j < M ? exp_of(T[(size_t)k * M + j]) : 1, eg = ge[k];
+            if (et != -100000 && eg != -100000) ex = max(ex, et + eg);
         }
     }
     __shared__ int red[8][32];
@@ -366,19 +378,17 @@ __global__ void k_tg_colexp(const double *__restrict__ T, const double *__restri
     }
 }
 
-// (T' o g)^T sliced: out [SB][M+1][ld], row j, column k, through 32 x 32 tiles.
-__global__ void k_tg_slice(const double *__restrict__ T, const double *__restrict__ g, double scale,
-                           const double *__restrict__ shift, int64_t Ns, int M, int SB, int64_t ld,
-                           const int *__restrict__ expo, __nv_bfloat16 *__restrict__ out) {
+// (T' o g')^T sliced: out [SB][M+1][ld], row j, column k, through 32 x 32 tiles.
+__global__ void k_tg_slice(const double *__restrict__ T, const double *__restrict__ gp, int64_t Ns, int M, int SB,
+                           int64_t ld, const int *__restrict__ expo, __nv_bfloat16 *__restrict__ out) {
     __shared__ double tile[32][33];
     const int64_t k0 = (int64_t)blockIdx.x * 32;
     const int j0 = blockIdx.y * 32;
-    const double sh = shift ? *shift : 0.0;
     for (int r = threadIdx.y; r < 32; r += blockDim.y) {
         const int64_t k = k0 + r;
         const int j = j0 + threadIdx.x;
         double v = 0.0;
-        if (k < Ns && j <= M) v = (j < M ? T[(size_t)k * M + j] : 1.0) * (scale * (g[k] - sh));
+        if (k < Ns && j <= M) v = (j < M ? T[(size_t)k * M + j] : 1.0) * gp[k];
         tile[r][threadIdx.x] = v;
     }
     __syncthreads();
@@ -568,7 +578,8 @@ size_t tc_vjp_ws_bytes(int N, int M, int64_t Ns) {
     const int64_t ld = pad8(Ns);
     return ((size_t)(N + 1) * ld * 2 + 255) / 256 * 256 + ((size_t)kMaxSB * (M + 1) * ld * 2 + 255) / 256 * 256 +
            ((size_t)(M + 1) * 4 + 255) / 256 * 256 +
-           ((size_t)kMaxKSplit * (N + 1) * (M + 1) * 8 + 255) / 256 * 256 + 256;
+           ((size_t)kMaxKSplit * (N + 1) * (M + 1) * 8 + 255) / 256 * 256 + ((size_t)Ns * 8 + 255) / 256 * 256 +
+           ((size_t)Ns * 4 + 255) / 256 * 256 + 256;
 }
 
 // out = J^T g' with g' = scale (g - shift), (T' o g')^T cut into SB slices.
@@ -586,12 +597,15 @@ cudaError_t launch_vjp_tc(int N, int M, int64_t Ns, const int8_t *s, const doubl
     auto *Gs = reinterpret_cast<__nv_bfloat16 *>(take((size_t)kMaxSB * (M + 1) * ld * 2));
     auto *eg = reinterpret_cast<int *>(take((size_t)(M + 1) * 4));
     auto *PT = reinterpret_cast<double *>(take((size_t)kMaxKSplit * (N + 1) * (M + 1) * 8));
+    auto *gp = reinterpret_cast<double *>(take((size_t)Ns * 8));
+    auto *ge = reinterpret_cast<int *>(take((size_t)Ns * 4));
     dim3 tb(32, 8);
     (k_pm1_cols<<<dim3(nblk(ld, 32), nblk(N + 1, 32)), tb, 0, st>>>(s, Ns, N, ld, St), nk::note_launch());
     (k_fill_int<<<nblk(M + 1, 256), 256, 0, st>>>(M + 1, -100000, eg), nk::note_launch());
-    (k_tg_colexp<<<dim3(nblk(M + 1, 32), nblk(Ns, 256)), dim3(32, 8), 0, st>>>(T, g, scale, shift, Ns, M, eg),
+    (k_scale_g<<<nblk(Ns, 256), 256, 0, st>>>(Ns, g, scale, shift, gp, ge), nk::note_launch());
+    (k_tg_colexp<<<dim3(nblk(M + 1, 32), nblk(Ns, 256)), dim3(32, 8), 0, st>>>(T, ge, Ns, M, eg),
      nk::note_launch());
-    (k_tg_slice<<<dim3(nblk(ld, 32), nblk(M + 1, 32)), tb, 0, st>>>(T, g, scale, shift, Ns, M, SB, ld, eg, Gs),
+    (k_tg_slice<<<dim3(nblk(ld, 32), nblk(M + 1, 32)), tb, 0, st>>>(T, gp, Ns, M, SB, ld, eg, Gs),
      nk::note_launch());
     // split the long K = Ns range until the grid covers the SMs twice
     // (every split keeps >= 4 chunks; each split's FP32 levels stay exact)
