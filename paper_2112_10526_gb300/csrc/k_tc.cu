@@ -435,10 +435,11 @@ __global__ void __launch_bounds__(kPotrfThreads) k_potrf64(double *__restrict__ 
 // Linv = L^-1 for the factored kb x kb diagonal block at (k, k): a lower-
 // triangular 64 x 64 block, zero above the diagonal and beyond kb.  Column j
 // of the inverse solves L x = e_j by forward substitution; one warp per
-// column (64 CTAs of one warp: this part's FP64 pipe serialises the warps
-// of an SM), lanes holding rows lane and lane + 32, x_i broadcast by shuffle
-// and eliminated from the rows below with one FMA per lane.
-constexpr int kTrtriWarps = 1;
+// column (16 CTAs of 4 warps, one per SM sub-partition, each CTA staging
+// only the rows and columns its columns read), lanes holding rows lane and
+// lane + 32, x_i broadcast by shuffle and eliminated from the rows below
+// with one FMA per lane.
+constexpr int kTrtriWarps = 4;
 
 __global__ void __launch_bounds__(32 * kTrtriWarps) k_trtri64(const double *__restrict__ A, int64_t n, int64_t k,
                                                               int kb, double *__restrict__ Linv) {
