@@ -197,19 +197,31 @@ __device__ __forceinline__ Prod<R> strided_product(const R *__restrict__ t, cons
 __device__ __forceinline__ Prod<float> lane_product4(const float *__restrict__ t, const float *__restrict__ tau,
                                                      float si, int lane, int M) {
     float m0 = 1.f, m1 = 1.f;
-    int e = 0, cnt = 0;
-    for (int j = 4 * lane; j < M; j += 128) {
+    int e = 0;
+    int j = 4 * lane;
+    // groups of four 16-byte loads in flight (large M reads the tau row from L2),
+    // renormalised after each group as before
+    for (; j + 3 * 128 < M; j += 4 * 128) {
+        float4 uv[4], tv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) uv[u] = __ldg(reinterpret_cast<const float4 *>(tau + j + u * 128));
+#pragma unroll
+        for (int u = 0; u < 4; ++u) tv[u] = *reinterpret_cast<const float4 *>(t + j + u * 128);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            m0 *= fmaf(-si * tv[u].x, uv[u].x, 1.f) * fmaf(-si * tv[u].y, uv[u].y, 1.f);
+            m1 *= fmaf(-si * tv[u].z, uv[u].z, 1.f) * fmaf(-si * tv[u].w, uv[u].w, 1.f);
+        }
+        int k0, k1;
+        m0 = frexpf(m0, &k0);
+        m1 = frexpf(m1, &k1);
+        e += k0 + k1;
+    }
+    for (; j < M; j += 128) {
         const float4 tv = *reinterpret_cast<const float4 *>(t + j);
         const float4 uv = __ldg(reinterpret_cast<const float4 *>(tau + j));
         m0 *= fmaf(-si * tv.x, uv.x, 1.f) * fmaf(-si * tv.y, uv.y, 1.f);
         m1 *= fmaf(-si * tv.z, uv.z, 1.f) * fmaf(-si * tv.w, uv.w, 1.f);
-        if (++cnt == 4) {
-            int k0, k1;
-            m0 = frexpf(m0, &k0);
-            m1 = frexpf(m1, &k1);
-            e += k0 + k1;
-            cnt = 0;
-        }
     }
     Prod<float> p{m0, e};
     renorm(p);
