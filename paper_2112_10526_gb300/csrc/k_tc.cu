@@ -144,25 +144,29 @@ __host__ __device__ inline int64_t oz_row_strips(int64_t n_nb, bool lower, int64
 
 // The S(S+1)/2 x 4 MMAs of one tile: level g = s + t (2 .. S+1) collects the
 // products of A slice s and B slice t in TMEM columns dbase + (g - 2) 32.
-// SS > 0 fixes S at compile time (fully unrolled issue).
+// Consecutive MMAs go to different levels (K-step outermost, then the
+// product index within a level, then the level), so that they do not wait on
+// one another's accumulator.  SS > 0 fixes S at compile time.
 template <int SS>
 __device__ __forceinline__ void issue_tile(uint32_t dbase, const uint64_t (&da)[kMaxSlices],
                                            const uint64_t (&db)[kMaxSlices], uint32_t idesc, int S_rt) {
     const int S = SS > 0 ? SS : S_rt;
+    constexpr int kG = (SS > 0 ? SS : kMaxSlices);
 #pragma unroll
-    for (int g = 2; g <= (SS > 0 ? SS : kMaxSlices) + 1; ++g) {
-        if (g > S + 1) break;
-        const uint32_t dcol = dbase + (uint32_t)((g - 2) * kPN);
-        uint32_t acc = 0;
+    for (int kk = 0; kk < kTileK / 16; ++kk) {
 #pragma unroll
-        for (int sa = 1; sa < g; ++sa) {
-            const int sb = g - sa;
-            if (sa > S || sb > S) continue;
+        for (int p = 0; p < kG; ++p) {
 #pragma unroll
-            for (int kk = 0; kk < kTileK / 16; ++kk) {
-                // advance 16 BF16 = 32 bytes along K inside the swizzle atom
-                umma_bf16(dcol, da[sa - 1] + (uint64_t)(kk * 2), db[sb - 1] + (uint64_t)(kk * 2), idesc, acc);
-                acc = 1;
+            for (int g = 2; g <= kG + 1; ++g) {
+                if (g > S + 1) continue;
+                // products of level g: sa = lo .. hi with sb = g - sa in [1, S]
+                const int lo = g - S > 1 ? g - S : 1, hi = g - 1 < S ? g - 1 : S;
+                const int sa = lo + p;
+                if (sa > hi) continue;
+                const int sb = g - sa;
+                const uint32_t acc = (kk > 0 || p > 0) ? 1u : 0u;
+                umma_bf16(dbase + (uint32_t)((g - 2) * kPN), da[sa - 1] + (uint64_t)(kk * 2),
+                          db[sb - 1] + (uint64_t)(kk * 2), idesc, acc);
             }
         }
     }
