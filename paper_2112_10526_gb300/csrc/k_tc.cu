@@ -92,6 +92,66 @@ __global__ void k_slice_rows(const double *__restrict__ A, int64_t lda, int64_t 
     if (lane == 0) expo[r] = e;
 }
 
+// Columns p of rows r0 .. r0 + kr - 1 (kr <= 64) of X [.][ldx] -> S BF16
+// integer slices out[s][p][0..63] (zero beyond kr) with the column exponent
+// expo[p] (max over those rows): the transposed counterpart of k_slice_rows,
+// same digits.  One block per 32 columns, staged through shared memory.
+__global__ void __launch_bounds__(256) k_slice_cols(const double *__restrict__ X, int64_t ldx, int64_t r0, int kr,
+                                                    int64_t ncols, int S, __nv_bfloat16 *__restrict__ out,
+                                                    int *__restrict__ expo) {
+    __shared__ double tile[kTileK][33];
+    __shared__ int ex[32];
+    const int tid = threadIdx.x;
+    const int64_t p0 = (int64_t)blockIdx.x * 32;
+    for (int idx = tid; idx < kTileK * 32; idx += 256) {
+        const int r = idx >> 5, c = idx & 31;
+        tile[r][c] = (r < kr && p0 + c < ncols) ? X[(size_t)(r0 + r) * ldx + p0 + c] : 0.0;
+    }
+    __syncthreads();
+    if (tid < 32) {
+        int e = -100000;
+        for (int r = 0; r < kTileK; ++r) {
+            int b;
+            unsigned long long m;
+            bool n;
+            split_bits(tile[r][tid], b, m, n);
+            if (m) e = max(e, b - 1022);
+        }
+        e = e == -100000 ? 0 : e;
+        ex[tid] = e;
+        if (p0 + tid < ncols) expo[p0 + tid] = e;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < kTileK * 32; idx += 256) {
+        const int c = idx >> 6, r = idx & 63;
+        if (p0 + c >= ncols) continue;
+        int b;
+        unsigned long long m;
+        bool n;
+        split_bits(tile[r][c], b, m, n);
+        unsigned long long y = 0;
+        if (m) {
+            const int sh = b - 1075 + 8 * S - ex[c];
+            y = sh >= 0 ? (m << sh) : (sh <= -64 ? 0ULL : (m >> (-sh)));
+        }
+        for (int q = 0; q < S; ++q) {
+            const int d = (int)((y >> (8 * (S - 1 - q))) & 0xFFULL);
+            out[((size_t)q * ncols + p0 + c) * kTileK + r] = __int2bfloat16_rn(n ? -d : d);
+        }
+    }
+}
+
+// C <- scale C + eps I on the lower triangle.
+__global__ void k_scale_shift_lower(double *__restrict__ C, int64_t n, double scale, double eps) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t i = blockIdx.y; i < n; i += gridDim.y) {
+        if (j > i || j >= n) continue;
+        double v = C[(size_t)i * n + j] * scale;
+        if (i == j) v += eps;
+        C[(size_t)i * n + j] = v;
+    }
+}
+
 // ------------------------------------------------------------- the GEMM ---
 //
 // Warp-specialised kernel over output strips: a CTA owns up to kChunk
@@ -974,6 +1034,29 @@ cudaError_t launch_cholesky_solve_tc(const double *L, int64_t n, const void *ws,
 // Lower triangle of K = T T^T by tensor cores with S slices per 64-column
 // chunk of T [Ns][M], then the Jacobian-row Gram s.s + t.t + (t.t)(s.s)
 // written to both triangles.
+// Lower triangle of C = scale X^T X + eps I for X [rows][ncols] (row stride
+// ncols): 64 rows of X per tensor-core pass, each sliced by columns (one
+// exponent per column and pass) and accumulated in FP64.
+cudaError_t launch_gram_cols_tc(const double *X, int64_t rows, int64_t ncols, double scale, double eps, double *C,
+                                int *err, void *ws, cudaStream_t st) {
+    if (rows <= 0 || ncols <= 0) return cudaSuccess;
+    TcWs w = carve_tc(ws, ncols);
+    const int S = kMaxSlices;
+    const int slot = prof_begin(NK_PROF_GRAM, st);
+    cudaError_t e = cudaSuccess;
+    for (int64_t r0 = 0; r0 < rows && e == cudaSuccess; r0 += kTileK) {
+        const int kr = (int)(rows - r0 < kTileK ? rows - r0 : kTileK);
+        (k_slice_cols<<<nblk(ncols, 32), 256, 0, st>>>(X, ncols, r0, kr, ncols, S, w.Asl, w.expA), nk::note_launch());
+        e = launch_ozaki_gemm(w.Asl, w.expA, ncols, w.Asl, w.expA, ncols, S, C, ncols, r0 == 0 ? 0 : 2, true, err, st);
+    }
+    if (e == cudaSuccess) {
+        const dim3 grid(nblk(ncols, 256), (unsigned)(ncols < 65535 ? ncols : 65535));
+        (k_scale_shift_lower<<<grid, 256, 0, st>>>(C, ncols, scale, eps), nk::note_launch());
+    }
+    prof_end(slot, st, (double)((rows + kTileK - 1) / kTileK) * ozaki_mma_flops(ncols, ncols, S, true));
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
 cudaError_t launch_gram_tc(int N, int M, int64_t Ns, const int8_t *s, const double *T, int S, double *K,
                            int *err, void *ws, cudaStream_t st) {
     TcWs w = carve_tc(ws, Ns);

@@ -340,8 +340,12 @@ nk_status run_solve(nk_ctx *ctx, int N, int M, int64_t Ns, const int8_t *s, cons
         NK_CU(nk::launch_vjp(N, M, Ns, s, T, w.ones, 1.0 / (double)Ns, nullptr, w.partial, w.mean, st),
               "chol mean");
         NK_CU(nk::launch_jacobian_rows(N, M, s, T, 0, Ns, w.mean, w.dJ, st), "chol dJ");
-        NK_CU(nk::launch_syrk_t(w.dJ, Ns, Np, 1.0 / (double)Ns, eps, w.S, st), "chol syrk");
         NK_CU(cudaMemsetAsync(w.info, 0, 2 * sizeof(int), st), "chol");
+        if (tc)
+            NK_CU(nk::launch_gram_cols_tc(w.dJ, Ns, Np, 1.0 / (double)Ns, eps, w.S, w.info + 1, w.tc, st),
+                  "chol gram");
+        else
+            NK_CU(nk::launch_syrk_t(w.dJ, Ns, Np, 1.0 / (double)Ns, eps, w.S, st), "chol syrk");
         if (tc)
             NK_CU(nk::launch_cholesky_tc(w.S, Np, w.info, w.info + 1, w.tc, st, ctx->side, ctx->ev[0], ctx->ev[1]),
                   "chol factor");

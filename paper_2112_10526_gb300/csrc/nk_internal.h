@@ -174,6 +174,10 @@ cudaError_t launch_cholesky_solve_tc(const double *L, int64_t n, const void *ws,
                                      cudaStream_t st);
 cudaError_t launch_gram_tc(int N, int M, int64_t Ns, const int8_t *s, const double *T, int S, double *K,
                            int *err, void *ws, cudaStream_t st);
+// Lower triangle of C = scale X^T X + eps I (X [rows][ncols]) by 7-slice
+// tensor-core products, 64 rows of X per pass; ws as for launch_cholesky_tc(ncols).
+cudaError_t launch_gram_cols_tc(const double *X, int64_t rows, int64_t ncols, double scale, double eps, double *C,
+                                int *err, void *ws, cudaStream_t st);
 
 cudaError_t launch_rowdot_aug(int M, int64_t Ns, const double *T, const double *U, double *out,
                               cudaStream_t st);
