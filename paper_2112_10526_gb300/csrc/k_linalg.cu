@@ -800,11 +800,6 @@ cudaError_t launch_jvp(int N, int M, int64_t Ns, const int8_t *s, const double *
     return cudaGetLastError();
 }
 
-cudaError_t launch_rowdot_aug(int M, int64_t Ns, const double *T, const double *U, double *out,
-                              cudaStream_t st) {
-    (k_rowdot_aug<<<nblk(Ns, 8), 256, 0, st>>>(M, Ns, T, U, out), nk::note_launch());
-    return cudaGetLastError();
-}
 
 cudaError_t launch_jacobian_rows(int N, int M, const int8_t *s, const double *T, int64_t row0,
                                  int64_t rows, const double *mean, double *O, cudaStream_t st) {

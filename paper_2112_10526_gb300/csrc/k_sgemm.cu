@@ -4,7 +4,7 @@
 // configuration matrix by a real matrix (NetKet 3, Sec. 3.2 model
 // evaluation; App. B.1 Jacobian products):
 //   theta = S W^T + b           (batched hidden activations, [Ns][M])
-//   J v   via U = S' V'^T       (S' = [S, 1], V' = [[V_W, v_b], [v_a, 0]])
+//   J v   = rowdot(T', S' V'^T)  (S' = [S, 1], V' = [[V_W, v_b], [v_a, 0]])
 //   J^T g via P^T = S'^T (T'o g) (T' = [T, 1])
 // +-1 and 1 are exact in BF16.  The real operand B is cut, row by row with one
 // power-of-two exponent per row, into SB slices of 8-bit integers (as in
@@ -16,11 +16,16 @@
 // (FP64-level: the batched theta rebuild, the force and the sample-space
 // solve products); with SB = 4 up to 2^-32 (the NK_MIXED QGT products of CG).
 //
-// Kernel: 128 x 64 output tile per CTA, K in chunks of 64 through a
-// 3-stage TMA / mbarrier ring (thread 0 produces, thread 32 issues
-// tcgen05.mma M=128 N=64 K=16 into SB TMEM accumulators), then all four warps
-// drain TMEM through the same integer assembly and a staged, coalesced
-// store.  Every wait is bounded by the global timer.
+// Kernel: 128 x 64 output tile per CTA, K in chunks of 64 through a TMA /
+// mbarrier ring (3 stages; 2 for SB <= 4, so that two CTAs share an SM and
+// one drains while the other multiplies).  Thread 0 produces, thread 32
+// issues tcgen05.mma M=128 N=64 K=16 into SB TMEM accumulators, then the
+// four warps drain TMEM through the integer recombination.  Outputs: a
+// staged, coalesced store (C =, -=, += R; a long K range may be split over
+// blockIdx.z into partial outputs summed afterwards), or, for J v, the row
+// products with t' = [t, 1] taken in the epilogue (one partial per row and
+// 64-column tile), so that the Ns x (M+1) product never reaches HBM.
+// Every wait is bounded by the global timer.
 
 #include <cuda.h>
 #include <cuda_bf16.h>

@@ -179,8 +179,6 @@ cudaError_t launch_gram_tc(int N, int M, int64_t Ns, const int8_t *s, const doub
 cudaError_t launch_gram_cols_tc(const double *X, int64_t rows, int64_t ncols, double scale, double eps, double *C,
                                 int *err, void *ws, cudaStream_t st);
 
-cudaError_t launch_rowdot_aug(int M, int64_t Ns, const double *T, const double *U, double *out,
-                              cudaStream_t st);
 
 // ---- tensor-core products with the configurations (k_sgemm.cu) -------------
 size_t tc_theta_ws_bytes(int N, int M, int64_t B);
