@@ -337,6 +337,34 @@ def roofline(prof, K, precision):
             "share_of_step": ms / 1.0}, cls
 
 
+def rooflines_by_class(prof, step_ms, precision):
+    """Every tracked kernel class against the roofline that bounds it (the
+    same conventions as the dominant-class roofline)."""
+    peaks, src = measured_peaks()
+    out = {}
+    for cls, (ms, launches, work) in prof.items():
+        if launches == 0 or ms <= 0:
+            continue
+        secs = ms / 1e3
+        if cls in ("sweep", "eloc"):
+            val, unit, bound = 2.0 * work / secs / 1e12, "TFLOP/s", "alu"
+            peak = FP64_PEAK_TFLOPS if precision == "f64" else FP32_PEAK_TFLOPS
+            note = "FP64 pipe, nominal" if precision == "f64" else "FP32 lanes, nominal"
+        elif cls in ("chol_update", "gram", "jvp_vjp") and precision == "mixed":
+            val, unit, bound = work / secs / 1e12, "TFLOP/s", "tensor"
+            peak, note = peaks["bf16_tflops_sustained"], f"bf16 dense, sustained ({src})"
+        elif cls == "trsv":
+            # two solves read the lower factor once each: n^2 / 2 x 8 bytes per solve, work = 2 n^2
+            val, unit, bound = (work / 2.0) * 8.0 / secs / 1e9, "GB/s", "hbm"
+            peak, note = peaks["hbm_gbs"], f"HBM copy ({src})"
+        else:
+            val, unit, bound = work / secs / 1e12, "TFLOP/s", "alu"
+            peak, note = FP64_PEAK_TFLOPS, "FP64 pipe, nominal"
+        out[cls] = {"bound": bound, "achieved": val, "peak": peak, "unit": unit, "frac": val / peak,
+                    "ms_per_step": ms, "share_of_step": ms / step_ms, "launches": launches, "peak_source": note}
+    return out
+
+
 def run_ours(args, rank, world):
     import torch
     from paper_2112_10526_gb300 import nk
@@ -360,6 +388,8 @@ def run_ours(args, rank, world):
     rf, dom = roofline(prof, K, args.precision)
     if rf is not None:
         rf["share_of_step"] = prof[dom][0] / ms
+    by_class = rooflines_by_class({c: (v[0] / K, v[1] / K, v[2] / K) for c, v in prof.items()}, ms / K,
+                                  args.precision)
     e2e_dt, bi, bo = e2e_steps(st, K, dev)
     e2e_dt = max_over_ranks(e2e_dt, world, dev)
     Ns = w["chains"] * w["per_chain"]
@@ -379,6 +409,7 @@ def run_ours(args, rank, world):
         "proposals_per_s": world * K * Ns * w["N"] / (ms_plain / 1e3),
         "energy": stats["energy"], "energy_error": stats["error"], "acceptance": stats["acceptance"],
         "roofline": rf,
+        "rooflines_by_class": by_class,
         "kernel_ms_per_step": {c: prof[c][0] / K for c in prof if prof[c][1] > 0},
         "e2e": {"value": world * K / e2e_dt, "unit": "SR steps/s", "h2d_bytes_per_step": bi,
                 "d2h_bytes_per_step": bo},
