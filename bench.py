@@ -207,6 +207,23 @@ def step(st, first=False):
                   st["stats"])
 
 
+def lattice_text(N):
+    L = int(round(N ** 0.5))
+    return f"{L}x{L} periodic square" if L * L == N else f"{N}-site periodic chain"
+
+
+def l2_text(solver, Ns, M, Np):
+    """Which per-step array outgrows the 129 MB L2 between timed steps."""
+    if solver == "cholesky_samplespace":
+        what, nbytes = "Ns x Ns FP64 Gram", Ns * Ns * 8
+    elif solver == "cholesky":
+        what, nbytes = "Np x Np FP64 QGT", Np * Np * 8
+    else:
+        what, nbytes = "Ns x M FP64 tanh(theta), read per CG product", Ns * M * 8
+    side = "larger" if nbytes > 129e6 else "SMALLER"
+    return f"working set {side} than L2 ({what} = {nbytes / 2**20:.0f} MiB per step)"
+
+
 def replica_value(world, K, ms_max):
     """Whole-job SR steps/s of `world` independent replicas that each ran K
     steps, from the slowest rank's time (ms): weak scaling."""
@@ -399,12 +416,12 @@ def run_ours(args, rank, world):
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "f64" else "f32+f64",
         "data": "synthetic (seeded RBM parameters N(0, 0.01^2), Philox chains)",
-        "config": {"workload": w["name"], "lattice": "10x10 periodic square" if w["N"] == 100 else str(w["N"]),
+        "config": {"workload": w["name"], "lattice": lattice_text(w["N"]),
                    "hamiltonian": w["ham"]["kind"], "N": w["N"], "M": w["M"], "Np": w["N"] + w["M"] + w["M"] * w["N"],
                    "chains": w["chains"], "samples_per_chain": w["per_chain"], "Ns": Ns, "rule": w["rule"],
                    "solver": w["solver"], "precision": args.precision, "diag_shift": w["diag_shift"],
                    "lr": w["lr"], "parallelism": f"replicas x{world}",
-                   "l2": "working set larger than L2 (Ns x Ns FP64 Gram = 512 MiB per step)"},
+                   "l2": l2_text(w["solver"], Ns, w["M"], w["N"] + w["M"] + w["M"] * w["N"])},
         "samples_sweeps_per_s": world * K * Ns / (ms_plain / 1e3),
         "proposals_per_s": world * K * Ns * w["N"] / (ms_plain / 1e3),
         "energy": stats["energy"], "energy_error": stats["error"], "acceptance": stats["acceptance"],

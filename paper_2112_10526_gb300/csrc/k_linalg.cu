@@ -421,7 +421,7 @@ __global__ void k_potrf_diag(double *__restrict__ A, int64_t n, int64_t k, int k
         if (t == 0) {
             double d = L[c][c];
             if (!(d > 0.0)) {
-                if (info) atomicExch(info, (int)(k + c + 1));
+                if (info) atomicCAS(info, 0, (int)(k + c + 1));  // the first failure
                 d = 1e-300;
             }
             L[c][c] = sqrt(d);

@@ -19,7 +19,8 @@
 // Kernel: 128 x 64 output tile per CTA, K in chunks of 64 through a TMA /
 // mbarrier ring (3 stages; 2 for SB <= 4, so that two CTAs share an SM and
 // one drains while the other multiplies).  Thread 0 produces, thread 32
-// issues tcgen05.mma M=128 N=64 K=16 into SB TMEM accumulators, then the
+// issues tcgen05.mma M=128 K=16 into SB TMEM accumulators of 64 columns,
+// with the slices side by side as one B operand (N = 64 SB up to 256), then the
 // four warps drain TMEM through the integer recombination.  Outputs: a
 // staged, coalesced store (C =, -=, += R; a long K range may be split over
 // blockIdx.z into partial outputs summed afterwards), or, for J v, the row
@@ -116,7 +117,11 @@ __global__ void __launch_bounds__(kSgThreads, 2)
         }
     } else if (threadIdx.x == 32) {
         // MMA issuer
-        const uint32_t idesc = idesc_bf16(kBM, kBN);
+        // the SB slice tiles of a stage lie back to back ([SB][64][64] BF16), so
+        // slices 0 .. 3 form one operand of 64 min(SB, 4) rows for one MMA into
+        // TMEM columns 0 .. 64 min(SB, 4) - 1, and slices 4 .. SB-1 a second one
+        const int nlo = SB < 4 ? SB : 4, nhi = SB - nlo;
+        const uint32_t idesc_lo = idesc_bf16(kBM, kBN * nlo), idesc_hi = idesc_bf16(kBM, kBN * (nhi > 0 ? nhi : 1));
         bool ok = true;
         for (int kc = kc0; kc < kc1; ++kc) {
             const int i = kc - kc0, s = i % NS;
@@ -126,13 +131,14 @@ __global__ void __launch_bounds__(kSgThreads, 2)
             }
             tc_fence_after();
             unsigned char *sp = ops + (size_t)s * a.stage_bytes;
-            const uint64_t da = sw128_desc(sp);
-            for (int t = 0; t < SB; ++t) {
-                const uint64_t db = sw128_desc(sp + kAB + t * kBB);
+            const uint64_t da = sw128_desc(sp), dlo = sw128_desc(sp + kAB), dhi = sw128_desc(sp + kAB + 4 * kBB);
 #pragma unroll
-                for (int kk = 0; kk < kBK / 16; ++kk)
-                    umma_bf16(tmem + (uint32_t)(t * kBN), da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
-                              (i > 0 || kk > 0) ? 1u : 0u);
+            for (int kk = 0; kk < kBK / 16; ++kk) {
+                const uint32_t acc = (i > 0 || kk > 0) ? 1u : 0u;
+                umma_bf16(tmem, da + (uint64_t)(kk * 2), dlo + (uint64_t)(kk * 2), idesc_lo, acc);
+                if (nhi > 0)
+                    umma_bf16(tmem + (uint32_t)(4 * kBN), da + (uint64_t)(kk * 2), dhi + (uint64_t)(kk * 2), idesc_hi,
+                              acc);
             }
             umma_commit(&empty[s]);
         }
@@ -185,12 +191,9 @@ __global__ void __launch_bounds__(kSgThreads, 2)
                     int d[kMaxSB];
 #pragma unroll
                     for (int t = 0; t < kMaxSB; ++t) d[t] = t < SB ? __float2int_rn(__uint_as_float(r[t][j])) : 0;
-                    // V = sum_t D_t 2^(8 (7 - t)) = hi 2^32 + lo: slices 1 .. 3 in hi, 4 .. 7 in lo
-                    const long long hi = (long long)d[0] * 65536 + (long long)d[1] * 256 + d[2];
-                    const long long lo =
-                        (long long)d[3] * 16777216 + (long long)d[4] * 65536 + (long long)d[5] * 256 + d[6];
+                    // V 2^(f_n - 56) with V = sum_t D_t 2^(8 (7 - t))
                     const int fn = __shfl_sync(0xffffffffu, fj_lane, j);
-                    const double v = fixed_to_double_sat(hi, lo, fn - 56);
+                    const double v = window_to_double(sgemm_window10(d), fn - 46);
                     if (a.mode == 3)
                         racc = fma(v, tv[j], racc);
                     else

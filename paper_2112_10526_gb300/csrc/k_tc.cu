@@ -16,14 +16,15 @@
 // dropped terms are below 2^-56 of K max|a| max|b|: FP64-level accuracy.
 // S = 3 gives about FP32 accuracy (24 bits per operand).
 //
-// Kernel shape: a persistent CTA per SM walks a range of 128 x 32 output
-// tiles (K = 64): TMA brings the S slices of the A rows (once per tile row)
-// and of the B rows (3-D tensor maps [S][rows][64] BF16, 128-byte swizzle),
-// one thread issues the S(S+1)/2 x 4 tcgen05.mma (M = 128, N = 32, K = 16)
-// into S accumulators of 32 TMEM columns, double-buffered, and eight warps
-// drain the other buffer and update C.  Every wait is bounded by the global
-// timer; on time-out the kernel records an error code, lets its copies and
-// MMAs in flight finish, frees its TMEM and returns.
+// Kernel shape: a CTA per strip of up to eight 128 x 32 output tiles (K =
+// 64): TMA brings the S slices of the A rows (once per strip) and of the B
+// rows (3-D tensor maps [S][rows][64] BF16, 128-byte swizzle), one thread
+// issues S x 4 tcgen05.mma (M = 128, K = 16, A slice s against B slices
+// 1 .. S+1-s side by side: N = 32 (S+1-s)) into S accumulators of 32 TMEM
+// columns, double-buffered, and sixteen warps drain the other buffer and
+// update C.  Every wait is bounded by the global timer; on time-out the
+// kernel records an error code, lets its copies and MMAs in flight finish,
+// frees its TMEM and returns.
 
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -154,13 +155,14 @@ __global__ void k_scale_shift_lower(double *__restrict__ C, int64_t n, double sc
 
 // ------------------------------------------------------------- the GEMM ---
 //
-// Warp-specialised kernel over output strips: a CTA owns up to kChunk
-// consecutive 128 x 32 tiles of one tile row (a 128 x 256 strip), keeps the
+// Warp-specialised kernel over output strips: a CTA owns up to `chunk` (<= 8)
+// consecutive 128 x 32 tiles of one tile row (a 128 x 256 strip at most), keeps the
 // S slices of its 128 A rows resident, and pipelines the tiles:
 //   warp 0 (one thread): TMA producer, A slices once, B slices per tile into
 //     one of two buffers;
-//   warp 1 (one thread): MMA issuer, S(S+1)/2 slice products x 4 K-steps per
-//     tile into one of two TMEM accumulator sets (S x 32 columns each), so
+//   warp 1 (one thread): MMA issuer, S MMAs (one per A slice, against the
+//     B slices side by side) x 4 K-steps per tile into one of two TMEM
+//     accumulator sets (S x 32 columns each), so
 //     that the MMAs of tile i+1 run while tile i is drained;
 //   warps 2-17: epilogue; warp w owns tile rows 32 (w % 4) .. +31 (its TMEM
 //     lane quarter) and 8 columns, loads its C entries a tile ahead, and
@@ -182,10 +184,11 @@ struct OzArgs {
     int lower;            // only entries with col <= row (tiles above are skipped)
     int *err;
     int64_t n_nb;         // tile columns
+    int chunk;            // tiles per strip, 1 .. kMaxChunk
 };
 
 constexpr int kPN = 32;                      // tile columns
-constexpr int kChunk = 8;                    // tiles per strip
+constexpr int kMaxChunk = 8;                 // tiles per strip at most
 constexpr int kPEpiWarps = 16;
 constexpr int kPThreads = 64 + 32 * kPEpiWarps;        // producer, MMA issuer, epilogue warps
 constexpr int kPColsPerWarp = kPN / (kPEpiWarps / 4);  // 8
@@ -198,36 +201,32 @@ __host__ __device__ inline int64_t oz_row_tiles(int64_t n_nb, bool lower, int64_
     return last < n_nb ? last : n_nb;
 }
 
-__host__ __device__ inline int64_t oz_row_strips(int64_t n_nb, bool lower, int64_t mb) {
-    return (oz_row_tiles(n_nb, lower, mb) + kChunk - 1) / kChunk;
+__host__ __device__ inline int64_t oz_row_strips(int64_t n_nb, bool lower, int64_t mb, int chunk) {
+    return (oz_row_tiles(n_nb, lower, mb) + chunk - 1) / chunk;
 }
 
-// The S(S+1)/2 x 4 MMAs of one tile: level g = s + t (2 .. S+1) collects the
-// products of A slice s and B slice t in TMEM columns dbase + (g - 2) 32.
-// Consecutive MMAs go to different levels (K-step outermost, then the
-// product index within a level, then the level), so that they do not wait on
-// one another's accumulator.  SS > 0 fixes S at compile time.
+// The MMAs of one tile: level g = s + t (2 .. S+1) collects the products of
+// A slice s and B slice t in TMEM columns dbase + (g - 2) 32.  The B slices
+// of a tile lie back to back in shared memory ([S][32][64], 128-byte rows),
+// so B slices 1 .. S+1-s read as one operand of 32 (S+1-s) rows, and a single
+// MMA of that width adds A slice s times all of them to the contiguous levels
+// s+1 .. S+1.  S MMAs per K-step (instead of S(S+1)/2 of width 32) read each
+// A slice once; the first one of a tile (s = 1, K-step 0) initialises every
+// level.  SS > 0 fixes S at compile time.
 template <int SS>
-__device__ __forceinline__ void issue_tile(uint32_t dbase, const uint64_t (&da)[kMaxSlices],
-                                           const uint64_t (&db)[kMaxSlices], uint32_t idesc, int S_rt) {
+__device__ __forceinline__ void issue_tile(uint32_t dbase, uint64_t da, uint64_t db,
+                                           const uint32_t (&idesc)[kMaxSlices], int S_rt) {
     const int S = SS > 0 ? SS : S_rt;
-    constexpr int kG = (SS > 0 ? SS : kMaxSlices);
-#pragma unroll
+    constexpr int kS = (SS > 0 ? SS : kMaxSlices);
+#pragma unroll 1
     for (int kk = 0; kk < kTileK / 16; ++kk) {
 #pragma unroll
-        for (int p = 0; p < kG; ++p) {
-#pragma unroll
-            for (int g = 2; g <= kG + 1; ++g) {
-                if (g > S + 1) continue;
-                // products of level g: sa = lo .. hi with sb = g - sa in [1, S]
-                const int lo = g - S > 1 ? g - S : 1, hi = g - 1 < S ? g - 1 : S;
-                const int sa = lo + p;
-                if (sa > hi) continue;
-                const int sb = g - sa;
-                const uint32_t acc = (kk > 0 || p > 0) ? 1u : 0u;
-                umma_bf16(dbase + (uint32_t)((g - 2) * kPN), da[sa - 1] + (uint64_t)(kk * 2),
-                          db[sb - 1] + (uint64_t)(kk * 2), idesc, acc);
-            }
+        for (int sa = 1; sa <= kS; ++sa) {
+            if (sa > S) continue;
+            const uint32_t acc = (kk > 0 || sa > 1) ? 1u : 0u;
+            // A slice sa starts (sa - 1) kABytes after slice 1 (descriptor address field in 16-byte units)
+            umma_bf16(dbase + (uint32_t)((sa - 1) * kPN), da + (uint64_t)((sa - 1) * (kABytes >> 4) + kk * 2),
+                      db + (uint64_t)(kk * 2), idesc[sa - 1], acc);
         }
     }
 }
@@ -240,7 +239,8 @@ __global__ void __launch_bounds__(kPThreads, 1)
     unsigned char *ops = smem_raw + ((1024 - (base & 1023)) & 1023);
     unsigned char *sA = ops;                                            // [S][128][64] bf16
     unsigned char *sB = ops + (size_t)kMaxSlices * kABytes;             // [2][S][32][64] bf16
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sB + (size_t)2 * kMaxSlices * kPBBytes);
+    unsigned char *sE = sB + (size_t)2 * kMaxSlices * kPBBytes;         // [16 warps][32][8] fp64
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sE + (size_t)kPEpiWarps * 32 * kPColsPerWarp * 8);
     uint64_t *a_full = bars, *b_full = bars + 2, *b_empty = bars + 4;
     uint64_t *acc_full = bars + 6, *acc_empty = bars + 8;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 10);
@@ -250,13 +250,13 @@ __global__ void __launch_bounds__(kPThreads, 1)
     // strip -> tile row mb, first tile column nb0, tile count
     int64_t mb = 0, rem = blockIdx.x;
     for (;;) {
-        const int64_t ns = oz_row_strips(a.n_nb, a.lower != 0, mb);
+        const int64_t ns = oz_row_strips(a.n_nb, a.lower != 0, mb, a.chunk);
         if (rem < ns) break;
         rem -= ns;
         ++mb;
     }
-    const int64_t nb0 = rem * kChunk, in_row = oz_row_tiles(a.n_nb, a.lower != 0, mb);
-    const int count = (int)(in_row - nb0 < kChunk ? in_row - nb0 : kChunk);
+    const int64_t nb0 = rem * a.chunk, in_row = oz_row_tiles(a.n_nb, a.lower != 0, mb);
+    const int count = (int)(in_row - nb0 < a.chunk ? in_row - nb0 : a.chunk);
     const int64_t m0 = mb * kTileM;
 
     if (threadIdx.x == 0) {
@@ -310,14 +310,11 @@ __global__ void __launch_bounds__(kPThreads, 1)
     } else if (warp == 1 && lane == 0) {
         // ------------------------------------------------------- MMA issuer
         int issued = 0;
-        const uint32_t idesc = idesc_bf16(kTileM, kPN);
-        uint64_t da[kMaxSlices], db0[kMaxSlices], db1[kMaxSlices];
+        uint32_t idesc[kMaxSlices];  // A slice s + 1 meets B slices 1 .. S - s: N = 32 (S - s)
 #pragma unroll
-        for (int s = 0; s < kMaxSlices; ++s) {
-            da[s] = sw128_desc(sA + (size_t)s * kABytes);
-            db0[s] = sw128_desc(sB + (size_t)s * kPBBytes);
-            db1[s] = sw128_desc(sB + (size_t)(kMaxSlices + s) * kPBBytes);
-        }
+        for (int s = 0; s < kMaxSlices; ++s) idesc[s] = idesc_bf16(kTileM, kPN * (S - s > 0 ? S - s : 1));
+        const uint64_t da = sw128_desc(sA), db0 = sw128_desc(sB),
+                       db1 = sw128_desc(sB + (size_t)kMaxSlices * kPBBytes);
         if (!mbar_wait_or_abort(a_full, 0, abort_flag)) fail(13);
         for (int i = 0; i < count && !*abort_flag; ++i) {
             const int b = i & 1;
@@ -346,37 +343,54 @@ __global__ void __launch_bounds__(kPThreads, 1)
         }
     } else if (warp >= 2) {
         // --------------------------------------------------------- epilogue
+        // Lane l turns TMEM lane 32q + l (tile row 32q + l) into FP64 for the
+        // warp's 8 columns and parks the values in its shared block
+        // [32 rows][8 columns] (column index XOR (row / 2) mod 8: conflict-free
+        // for both access patterns); C is then read and written with lane l on
+        // row 4k + l / 8, column l mod 8 (k = 0 .. 7), 64-byte row segments.
         const int q = warp & 3;                 // TMEM lane quarter = tile rows 32q .. 32q + 31
         const int c0 = ((warp - 2) >> 2) * kPColsPerWarp;  // the warp's 8 tile columns
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+        double *stage = reinterpret_cast<double *>(sE) + (warp - 2) * 32 * kPColsPerWarp;
         const int64_t row = m0 + q * 32 + lane;
-        const bool row_ok = row < a.rows;
-        const int ei = row_ok ? a.expA[row] : 0;
-        double *crow = a.C + (size_t)(row_ok ? row : 0) * a.ldc;
-        auto on = [&](int64_t col) { return row_ok && col < a.cols && !(a.lower && col > row); };
-        auto load_c = [&](int i, double (&cv)[kPColsPerWarp]) {
-            const int64_t col0 = (nb0 + i) * kPN + c0;
+        const int ei = row < a.rows ? a.expA[row] : 0;
+        const int rr = lane >> 3, cc = lane & 7;
+        const int64_t row_c = m0 + q * 32 + rr;  // + 4k: the rows this lane reads and writes in C
+        auto on = [&](int64_t r, int64_t col) { return r < a.rows && col < a.cols && !(a.lower && col > r); };
+        auto load_c = [&](int i, double (&cv)[8]) {
+            const int64_t col = (nb0 + i) * kPN + c0 + cc;
 #pragma unroll
-            for (int j = 0; j < kPColsPerWarp; ++j)
-                cv[j] = (a.mode != 0 && on(col0 + j)) ? crow[col0 + j] : 0.0;
+            for (int k = 0; k < 8; ++k) {
+                const int64_t r = row_c + 4 * k;
+                cv[k] = (a.mode != 0 && on(r, col)) ? a.C[(size_t)r * a.ldc + col] : 0.0;
+            }
         };
         // column exponents (lane & 7 holds column c0 + (lane & 7)), broadcast by shuffles
         auto load_f = [&](int i) {
-            const int64_t col = (nb0 + i) * kPN + c0 + (lane & 7);
+            const int64_t col = (nb0 + i) * kPN + c0 + cc;
             return col < a.cols ? a.expB[col] : 0;
         };
-        double cv[kPColsPerWarp], cn[kPColsPerWarp];
-        load_c(0, cv);
-        int fj_next = load_f(0);
+        const long long flip = a.mode == 1 ? (long long)0x8000000000000000ULL : 0LL;
+        if (a.mode != 0) {
+            // the strip's C entries (at most 128 x 256 FP64 per CTA) into L2 up
+            // front, so that the per-tile loads below wait on L2, not on HBM
+            for (int i = 0; i < count; ++i) {
+                const int64_t col = (nb0 + i) * kPN + c0 + cc;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int64_t r = row_c + 4 * k;
+                    if (on(r, col)) prefetch_l2(a.C + (size_t)r * a.ldc + col);
+                }
+            }
+        }
         for (int i = 0; i < count; ++i) {
             const int b = i & 1;
             const uint32_t use = (uint32_t)(i >> 1);
-            const int fj_lane = fj_next;
-            // the next tile's C and exponents are in flight during this tile
-            if (i + 1 < count) {
-                load_c(i + 1, cn);
-                fj_next = load_f(i + 1);
-            }
+            // this tile's C entries and column exponents are in flight while
+            // the accumulators fill and drain; C is needed only at the end
+            double cv[8];
+            load_c(i, cv);
+            const int fj_lane = load_f(i);
             int ok = 1;
             if (lane == 0) ok = mbar_wait_or_abort(&acc_full[b], use & 1, abort_flag) ? 1 : 0;
             ok = __shfl_sync(0xffffffffu, ok, 0);
@@ -385,40 +399,41 @@ __global__ void __launch_bounds__(kPThreads, 1)
                 break;
             }
             tc_fence_after();
-            const int64_t col0 = (nb0 + i) * kPN + c0;
-#pragma unroll
-            for (int c4 = 0; c4 < kPColsPerWarp; c4 += 4) {
-                uint32_t r[kMaxSlices][4];
+#pragma unroll 1
+            for (int c4 = 0; c4 < kPColsPerWarp; c4 += 2) {
+                uint32_t r[kMaxSlices][2];
 #pragma unroll
                 for (int gi = 0; gi < kMaxSlices; ++gi)
                     if (gi < S)
-                        tmem_ld4(tmem + (uint32_t)b * kPAccCols + lane_base + (uint32_t)(gi * kPN + c0 + c4), r[gi]);
+                        tmem_ld2(tmem + (uint32_t)b * kPAccCols + lane_base + (uint32_t)(gi * kPN + c0 + c4), r[gi]);
                 tmem_wait_ld();
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
+                for (int j = 0; j < 2; ++j) {
                     int d[kMaxSlices];
 #pragma unroll
                     for (int gi = 0; gi < kMaxSlices; ++gi)
                         d[gi] = gi < S ? __float2int_rn(__uint_as_float(r[gi][j])) : 0;
-                    // V = sum_g D_g 2^(8 (8 - g)) = hi 2^32 + lo exactly: levels g = 2 .. 4
-                    // weigh 2^(8 (4 - g)) in hi, g = 5 .. 8 weigh 2^(8 (8 - g)) in lo
-                    const long long hi = (long long)d[0] * 65536 + (long long)d[1] * 256 + d[2];
-                    const long long lo =
-                        (long long)d[3] * 16777216 + (long long)d[4] * 65536 + (long long)d[5] * 256 + d[6];
+                    // V 2^sc with V = sum_g D_g 2^(8 (8 - g)); C - R as C + (-R)
                     const int sc = ei + __shfl_sync(0xffffffffu, fj_lane, c4 + j) - 64;
-                    const double v = fixed_to_double_sat(hi, lo, sc);
-                    const int64_t col = col0 + c4 + j;
-                    if (on(col)) {
-                        const double c = cv[c4 + j];
-                        crow[col] = a.mode == 0 ? v : (a.mode == 1 ? c - v : c + v);
-                    }
+                    const double v = __longlong_as_double(
+                        __double_as_longlong(window_to_double(ozaki_window8(d), sc + 8)) ^ flip);
+                    const int c = c4 + j;
+                    stage[lane * 8 + (c ^ ((lane >> 1) & 7))] = v;
                 }
             }
+            // the accumulators are drained: hand the buffer back before the C traffic
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[b]);
+            const int64_t col = (nb0 + i) * kPN + c0 + cc;
 #pragma unroll
-            for (int j = 0; j < kPColsPerWarp; ++j) cv[j] = cn[j];
+            for (int k = 0; k < 8; ++k) {
+                const int rl = 4 * k + rr;
+                const double v = stage[rl * 8 + (cc ^ ((rl >> 1) & 7))];
+                const int64_t r = row_c + 4 * k;
+                if (on(r, col)) a.C[(size_t)r * a.ldc + col] = cv[k] + v;  // C reads as 0 in mode 0
+            }
+            __syncwarp();
         }
     }
     tc_fence_before();
@@ -434,60 +449,98 @@ __global__ void __launch_bounds__(kPThreads, 1)
 constexpr int kNB = 64;
 
 // Factor the kb x kb diagonal block at (k, k) in place (lower).  One CTA of
-// 256 threads holds the block in shared memory.  Column c: scale it by
-// 1/sqrt(d_c) (l_cc = sqrt(d_c)), then update the trailing triangle
-// a_rq -= l_rc l_qc, c < q <= r.  This part's FP64 pipe serialises warp
-// instructions whatever their active lanes, so the update is packed: a table
-// lists the entries (r, q) of the 64 x 64 lower triangle by column q
-// descending, the trailing triangle of column c is its first
-// (63 - c)(64 - c)/2 entries, and the threads take them densely.  The
-// thread that updates (c+1, c+1) forms the next pivot.  Two barriers per
-// column; kb^3/6 FMAs.
+// 256 threads holds the block in shared memory (continued by the identity
+// beyond kb) and factors it column by column with a look-ahead of one:
+//   * warp 0 carries the dependency chain (lanes hold rows lane and
+//     lane + 32): it updates column c+1 with the finished column c in
+//     registers, broadcasts the pivot d_{c+1} by shuffle, and scales column
+//     c+1 by d_{c+1}^-1/2;
+//   * meanwhile six warps (none on warp 0's SM sub-partition) apply column c
+//     to the columns right of c+1: a_rq -= l_rc l_qc, c+2 <= q <= r, over a
+//     packed table of the lower triangle ordered by column q descending
+//     (entries with q >= x are its first (64 - x)(65 - x)/2), four entries
+//     per thread at a time so that their FMA chains overlap.
+// One barrier per column; kb^3/6 FMAs.  On this part a dependent FP64
+// operation takes tens of cycles and an FP64 reciprocal square root hundreds
+// (pairing columns to share one did not pay: the longer FP64 sequence per
+// pair cost more), so the chain per column is one FMA, one shuffle, one
+// rsqrt and one multiply, with the positivity test done on the bit pattern.
 constexpr int kPotrfThreads = 256;
 constexpr int kLd = kNB + 1;
 constexpr int kTriEntries = kNB * (kNB - 1) / 2 + 0;  // (r, q) with 1 <= q <= r <= 63: 2016
+
+__host__ __device__ constexpr int tri_from(int x) {  // packed entries with column q >= x (1 <= x <= 64)
+    return (64 - x) * (65 - x) / 2;
+}
+
+__device__ __forceinline__ bool positive_finite(double x) {  // integer compares, off the FP64 pipe
+    const long long bits = __double_as_longlong(x);
+    return bits > 0 && bits < 0x7FF0000000000000LL;
+}
 
 __global__ void __launch_bounds__(kPotrfThreads) k_potrf64(double *__restrict__ A, int64_t n, int64_t k, int kb,
                                                            int *__restrict__ info) {
     __shared__ double L[kNB * kLd];
     __shared__ uint16_t tab[kTriEntries];
-    __shared__ double rsq[kNB];    // 1 / sqrt(d_c)
-    __shared__ double sq[kNB];     // sqrt(d_c)
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     for (int e = t; e < kNB * kNB; e += kPotrfThreads) {
         const int r = e >> 6, c = e & 63;
-        L[r * kLd + c] = (r < kb && c <= r) ? A[(size_t)(k + r) * n + k + c] : 0.0;
+        L[r * kLd + c] = (r < kb && c <= r) ? A[(size_t)(k + r) * n + k + c] : (r == c ? 1.0 : 0.0);
     }
     // column q (1 .. 63) owns entries [(63 - q)(64 - q)/2, +64 - q): rows q .. 63
     if (t >= 1 && t < kNB) {
         const int q = t, s0 = (63 - q) * (64 - q) / 2;
         for (int r = q; r < kNB; ++r) tab[s0 + r - q] = (uint16_t)((r << 8) | q);
     }
-    auto pivot = [&](int c) {
-        double d = L[c * kLd + c];
-        if (!(d > 0.0)) {
-            if (info) atomicExch(info, (int)(k + c + 1));
+    const int r0 = lane, r1 = lane + 32;
+    // warp 0: pivot of column c from d (its updated diagonal) and the scaling
+    // of the column's rows below, held as v0 (row r0) and v1 (row r1)
+    auto pivot_scale = [&](int c, double d, double v0, double v1) {
+        if (!positive_finite(d)) {
+            if (lane == 0 && info && c < kb) atomicCAS(info, 0, (int)(k + c + 1));  // the first failure
             d = 1e-300;
         }
-        const double r = rsqrt(d);
-        rsq[c] = r;
-        sq[c] = d * r;
+        const double rs = rsqrt(d);
+        if (r0 >= c) L[r0 * kLd + c] = r0 == c ? d * rs : v0 * rs;
+        if (r1 >= c) L[r1 * kLd + c] = r1 == c ? d * rs : v1 * rs;
     };
     __syncthreads();
-    if (t == 0 && kb > 0) pivot(0);
+    if (warp == 0) pivot_scale(0, L[0], L[r0 * kLd], L[r1 * kLd]);
     __syncthreads();
-    for (int c = 0; c < kb; ++c) {
-        // scale column c
-        if (t < kNB && t >= c && t < kb) L[t * kLd + c] = t == c ? sq[c] : L[t * kLd + c] * rsq[c];
-        __syncthreads();
-        // packed trailing update
-        const int P = (63 - c) * (64 - c) / 2;
-        for (int e = t; e < P; e += kPotrfThreads) {
-            const int rq = tab[e], r = rq >> 8, q = rq & 255;
-            L[r * kLd + q] = fma(-L[r * kLd + c], L[q * kLd + c], L[r * kLd + q]);
+    // bulk workers: warps 1-3 and 5-7
+    const int bulk_rank = warp == 0 || warp == 4 ? -1 : (warp < 4 ? warp - 1 : warp - 2) * 32 + lane;
+    constexpr int kBulkThreads = 6 * 32;
+    for (int c = 0; c + 1 < kNB; ++c) {
+        if (warp == 0) {
+            // column c+1 by the finished column c, in registers
+            const double lq = L[(c + 1) * kLd + c];
+            const double v0 = r0 > c ? fma(-L[r0 * kLd + c], lq, L[r0 * kLd + c + 1]) : 0.0;
+            const double v1 = r1 > c ? fma(-L[r1 * kLd + c], lq, L[r1 * kLd + c + 1]) : 0.0;
+            const double d = c + 1 < 32 ? __shfl_sync(0xffffffffu, v0, c + 1) : __shfl_sync(0xffffffffu, v1, c - 31);
+            pivot_scale(c + 1, d, v0, v1);
+        } else if (bulk_rank >= 0) {
+            // four entries at a time, loads first: their FMA chains overlap (a
+            // store could alias the next loads as far as the compiler knows)
+            const int ne = tri_from(c + 2);
+            for (int e0 = bulk_rank; e0 < ne; e0 += 4 * kBulkThreads) {
+                int at[4];
+                double acc[4], x[4], y[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int e = e0 + u * kBulkThreads;
+                    const int rq = e < ne ? tab[e] : ((63 << 8) | 63), r = rq >> 8, q = rq & 255;
+                    at[u] = e < ne ? r * kLd + q : -1;
+                    acc[u] = L[r * kLd + q];
+                    x[u] = L[r * kLd + c];
+                    y[u] = L[q * kLd + c];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc[u] = fma(-x[u], y[u], acc[u]);
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (at[u] >= 0) L[at[u]] = acc[u];
+            }
         }
-        // entry (c+1, c+1) is the first of column c+1: index (62 - c)(63 - c)/2
-        if (c + 1 < kb && t == ((62 - c) * (63 - c) / 2) % kPotrfThreads) pivot(c + 1);
         __syncthreads();
     }
     for (int e = t; e < kNB * kNB; e += kPotrfThreads) {
@@ -497,45 +550,50 @@ __global__ void __launch_bounds__(kPotrfThreads) k_potrf64(double *__restrict__ 
 }
 
 // Linv = L^-1 for the factored kb x kb diagonal block at (k, k): a lower-
-// triangular 64 x 64 block, zero above the diagonal and beyond kb.  Column j
-// of the inverse solves L x = e_j by forward substitution; one warp per
-// column (16 CTAs of 4 warps, one per SM sub-partition, each CTA staging
-// only the rows and columns its columns read), lanes holding rows lane and
-// lane + 32, x_i broadcast by shuffle and eliminated from the rows below
-// with one FMA per lane.
+// triangular 64 x 64 block, zero above the diagonal and beyond kb.  With
+// L = D U (D = diag(l_ii), U unit lower), column j of L^-1 is U^-1 e_j / l_jj.
+// One warp per column (16 CTAs of 4 warps, one per SM sub-partition, each CTA
+// staging only the rows and columns its columns read, rows divided by their
+// diagonal on load): lanes hold rows lane and lane + 32, and the forward
+// substitution takes per step one shuffle of y_i and one FMA per lane (two
+// while rows below 32 are still open).  A dependent FP64 operation costs
+// about as much as a shuffle on this part, so the unit diagonal keeps the
+// division off the chain.
 constexpr int kTrtriWarps = 4;
 
 __global__ void __launch_bounds__(32 * kTrtriWarps) k_trtri64(const double *__restrict__ A, int64_t n, int64_t k,
                                                               int kb, double *__restrict__ Linv) {
-    __shared__ double L[kNB * kLd];
+    __shared__ double U[kNB * kLd];
     __shared__ double rd[kNB];
     const int t = threadIdx.x, lane = t & 31;
     const int j = blockIdx.x * kTrtriWarps + (t >> 5);
     // column j of the inverse reads only rows and columns j .. 63 of L
     const int j0 = blockIdx.x * kTrtriWarps, w0 = kNB - j0;
+    for (int i = j0 + t; i < kNB; i += 32 * kTrtriWarps) rd[i] = i < kb ? 1.0 / A[(size_t)(k + i) * n + k + i] : 1.0;
+    __syncthreads();
     for (int e = t; e < w0 * w0; e += 32 * kTrtriWarps) {
         const int r = j0 + e / w0, c = j0 + e % w0;
-        L[r * kLd + c] = (r < kb && c <= r) ? A[(size_t)(k + r) * n + k + c] : 0.0;
+        U[r * kLd + c] = (r < kb && c < r) ? A[(size_t)(k + r) * n + k + c] * rd[r] : 0.0;
     }
-    for (int i = j0 + t; i < kNB; i += 32 * kTrtriWarps) rd[i] = i < kb ? 1.0 / A[(size_t)(k + i) * n + k + i] : 0.0;
     __syncthreads();
+    // y = U^-1 e_j: y_i is final when step i begins; then row r -= u_ri y_i
     double acc0 = lane == j ? 1.0 : 0.0, acc1 = lane + 32 == j ? 1.0 : 0.0;
-    double x0 = 0.0, x1 = 0.0;
-    for (int i = j; i < kb; ++i) {  // warp-uniform bounds
-        const double ai = i < 32 ? __shfl_sync(0xffffffffu, acc0, i) : __shfl_sync(0xffffffffu, acc1, i - 32);
-        const double x = ai * rd[i];
-        if (lane == (i & 31)) {
-            if (i < 32)
-                x0 = x;
-            else
-                x1 = x;
-        }
-        // rows above j0 were not loaded and never feed x
-        acc0 = fma(lane >= j0 ? -L[lane * kLd + i] : 0.0, x, acc0);
-        acc1 = fma(lane + 32 >= j0 ? -L[(lane + 32) * kLd + i] : 0.0, x, acc1);
+    double y0 = 0.0, y1 = 0.0;
+    int i = j;
+    for (; i < 32; ++i) {  // warp-uniform bounds; rows above j0 were not staged and stay 0
+        const double yi = __shfl_sync(0xffffffffu, acc0, i);
+        if (lane == i) y0 = yi;
+        acc0 = fma(lane >= j0 ? -U[lane * kLd + i] : 0.0, yi, acc0);
+        acc1 = fma(-U[(lane + 32) * kLd + i], yi, acc1);
     }
-    Linv[(size_t)lane * kNB + j] = x0;
-    Linv[(size_t)(lane + 32) * kNB + j] = x1;
+    for (; i < kNB; ++i) {
+        const double yi = __shfl_sync(0xffffffffu, acc1, i - 32);
+        if (lane == i - 32) y1 = yi;
+        acc1 = fma(lane + 32 >= j0 ? -U[(lane + 32) * kLd + i] : 0.0, yi, acc1);
+    }
+    const double s = j < kb ? rd[j] : 0.0;
+    Linv[(size_t)lane * kNB + j] = lane < kb ? y0 * s : 0.0;
+    Linv[(size_t)(lane + 32) * kNB + j] = lane + 32 < kb ? y1 * s : 0.0;
 }
 
 // ---------------------------------------------- triangular solves with L ---
@@ -811,7 +869,8 @@ __global__ void __launch_bounds__(256) k_gram_combine(int N, int64_t Ns, const i
 }
 
 size_t ozaki_smem_bytes() {
-    return 1024 + (size_t)kMaxSlices * kABytes + (size_t)2 * kMaxSlices * kPBBytes + 10 * sizeof(uint64_t) + 16;
+    return 1024 + (size_t)kMaxSlices * kABytes + (size_t)2 * kMaxSlices * kPBBytes +
+           (size_t)kPEpiWarps * 32 * kPColsPerWarp * sizeof(double) + 10 * sizeof(uint64_t) + 16;
 }
 
 inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -846,10 +905,21 @@ cudaError_t launch_ozaki_gemm_strided(const __nv_bfloat16 *Asl, const int *expA,
     const void *kern = S == kMaxSlices ? (const void *)k_ozaki_gemm<kMaxSlices> : (const void *)k_ozaki_gemm<0>;
     cudaError_t e = nk::allow_max_dynamic_smem(kern);
     if (e != cudaSuccess) return e;
-    OzArgs a{rows, cols, S, expA, expB, C, ldc, mode, lower ? 1 : 0, err, (cols + kPN - 1) / kPN};
+    OzArgs a{rows, cols, S, expA, expB, C, ldc, mode, lower ? 1 : 0, err, (cols + kPN - 1) / kPN, 1};
     const int64_t n_mb = (rows + kTileM - 1) / kTileM;
+    // strips of up to 8 tiles amortise a CTA's A slices over its tiles; a
+    // product with few tiles per SM (the panel solve and the narrow update of
+    // the Cholesky, on its critical path) takes one tile per CTA instead
+    int64_t tiles = 0;
+    for (int64_t m = 0; m < n_mb; ++m) tiles += oz_row_tiles(a.n_nb, lower, m);
+    int dev = 0, sms = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int64_t per_sm = sms > 0 ? tiles / sms : kMaxChunk;
+    a.chunk = (int)(per_sm < 1 ? 1 : (per_sm > kMaxChunk ? kMaxChunk : per_sm));
     int64_t strips = 0;
-    for (int64_t m = 0; m < n_mb; ++m) strips += oz_row_strips(a.n_nb, lower, m);
+    for (int64_t m = 0; m < n_mb; ++m) strips += oz_row_strips(a.n_nb, lower, m, a.chunk);
     if (strips > (1LL << 31) - 1) return cudaErrorInvalidValue;
     if (S == kMaxSlices)
         (k_ozaki_gemm<kMaxSlices><<<(unsigned)strips, kPThreads, ozaki_smem_bytes(), st>>>(ma, mb, a),
@@ -951,13 +1021,23 @@ cudaError_t panel_step(double *A, int64_t n, int64_t k0, int *info, int *err, Tc
 }  // namespace
 
 cudaError_t launch_cholesky_tc(double *A, int64_t n, int *info, int *err, void *ws, cudaStream_t st,
-                               cudaStream_t side, cudaEvent_t ev_narrow, cudaEvent_t ev_panel) {
+                               cudaStream_t side, cudaEvent_t ev_wide, cudaEvent_t ev_panel) {
+    // Step k, with panel k factored and sliced:
+    //   side stream: the narrow update (block column k+1 by panel k), then
+    //     panel k+1 (factor, invert, solve, slice);
+    //   main stream: the wide update (everything right of block column k+1).
+    // The side stream waits for the previous wide update (block column k+1
+    // must have received it, and panel k+1's slice buffer is the one that
+    // update read); the main stream waits for panel k+1 before the next wide
+    // update.  A step then takes max(wide, narrow + panel).
     TcWs w = carve_tc(ws, n);
     const int S = kMaxSlices;
     cudaError_t e = cudaSuccess;
     __nv_bfloat16 *buf[2] = {w.Asl, w.Asl2};
     int *bexp[2] = {w.expA, w.expA2};
     const int64_t nb = (n + kNB - 1) / kNB;
+    const bool two = side != nullptr;
+    cudaStream_t ps = two ? side : st;
     e = panel_step(A, n, 0, info, err, w, buf[0], bexp[0], st);
     if (e != cudaSuccess) return e;
     for (int64_t k = 0; k + 1 < nb; ++k) {
@@ -967,20 +1047,19 @@ cudaError_t launch_cholesky_tc(double *A, int64_t n, int *info, int *err, void *
         __nv_bfloat16 *Lk = buf[k & 1];
         int *Le = bexp[k & 1];
         double *C1 = A + (size_t)(k0 + kNB) * n + (k0 + kNB);
-        int slot = prof_begin(NK_PROF_CHOL_UPDATE, st);
-        // narrow: block column k + 1 (all rows below panel k)
-        e = launch_ozaki_gemm_strided(Lk, Le, rest, rest, Lk, Le, kb1, rest, S, C1, n, 1, true, err, st);
-        prof_end(slot, st, ozaki_mma_flops(rest, kb1, S, true));
-        if (e != cudaSuccess) return e;
-        if (side) {
-            e = cudaEventRecord(ev_narrow, st);
-            if (e == cudaSuccess) e = cudaStreamWaitEvent(side, ev_narrow, 0);
+        if (two) {
+            e = cudaEventRecord(ev_wide, st);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(side, ev_wide, 0);
             if (e != cudaSuccess) return e;
         }
-        cudaStream_t ps = side ? side : st;
+        // narrow: block column k + 1 (all rows below panel k)
+        int slot = prof_begin(NK_PROF_CHOL_UPDATE, ps);
+        e = launch_ozaki_gemm_strided(Lk, Le, rest, rest, Lk, Le, kb1, rest, S, C1, n, 1, true, err, ps);
+        prof_end(slot, ps, ozaki_mma_flops(rest, kb1, S, true));
+        if (e != cudaSuccess) return e;
         e = panel_step(A, n, k0 + kNB, info, err, w, buf[(k + 1) & 1], bexp[(k + 1) & 1], ps);
         if (e != cudaSuccess) return e;
-        if (side) {
+        if (two) {
             e = cudaEventRecord(ev_panel, side);
             if (e != cudaSuccess) return e;
         }
@@ -993,7 +1072,7 @@ cudaError_t launch_cholesky_tc(double *A, int64_t n, int *info, int *err, void *
             prof_end(slot, st, ozaki_mma_flops(rest2, rest2, S, true));
             if (e != cudaSuccess) return e;
         }
-        if (side) {
+        if (two) {
             e = cudaStreamWaitEvent(st, ev_panel, 0);
             if (e != cudaSuccess) return e;
         }

@@ -159,14 +159,14 @@ cudaError_t launch_cholesky_solve(const double *L, int64_t n, double *b, cudaStr
 size_t slice_elems(int64_t rows, int S);
 cudaError_t launch_slice_rows(const double *A, int64_t lda, int64_t rows, int kcols, int S,
                               __nv_bfloat16 *out, int *expo, cudaStream_t st);
-// C (mode 0: =, 1: -=, 2: +=) A B^T from slices, 128 x 64 tiles, K <= 64.
+// C (mode 0: =, 1: -=, 2: +=) A B^T from slices, 128 x 32 tiles, K <= 64.
 cudaError_t launch_ozaki_gemm(const __nv_bfloat16 *Asl, const int *expA, int64_t rows,
                               const __nv_bfloat16 *Bsl, const int *expB, int64_t cols, int S, double *C,
                               int64_t ldc, int mode, bool lower, int *err, cudaStream_t st);
 size_t tc_chol_ws_bytes(int64_t n);
 // side / events: a second stream for the panel look-ahead (null: one stream).
 cudaError_t launch_cholesky_tc(double *A, int64_t n, int *info, int *err, void *ws, cudaStream_t st,
-                               cudaStream_t side = nullptr, cudaEvent_t ev_narrow = nullptr,
+                               cudaStream_t side = nullptr, cudaEvent_t ev_wide = nullptr,
                                cudaEvent_t ev_panel = nullptr);
 // Forward and backward solves with the factor of launch_cholesky_tc (one
 // cooperative launch each); err receives 6 / 7 if a block-row wait timed out.

@@ -134,10 +134,18 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
                  : "r"(taddr));
 }
 
+__device__ __forceinline__ void tmem_ld2(uint32_t taddr, uint32_t (&r)[2]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(taddr));
+}
+
 __device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&r)[4]) {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
                  : "r"(taddr));
+}
+
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
@@ -186,101 +194,63 @@ __host__ __device__ __forceinline__ int clz64_any(unsigned long long x) {
 #endif
 }
 
-// Branch-free variant of fixed_to_double with the same result (round to
-// nearest even of V = hi 2^32 + lo, |V| < 2^75, times 2^sc): selects instead
-// of branches so that the conversions of neighbouring elements interleave.
-// The 64-bit window W = floor(|V| / 2^k) keeps all of |V| when it fits
-// (k = 0), else exactly 64 bits with the k <= 11 dropped bits kept as a
-// sticky flag; W is left-justified and rounded at bit 11.
-__host__ __device__ __forceinline__ unsigned long long fixed_to_bits(long long hi, long long lo, int sc, bool &ok,
-                                                                   int &E) {
-    const long long H = hi + (lo >> 32);
-    const unsigned int Lw = (unsigned int)(unsigned long long)lo;
-    const bool neg = H < 0;
-    const unsigned int s32 = neg ? 0xFFFFFFFFu : 0u;
-    const unsigned int Lm = (Lw ^ s32) + (neg ? 1u : 0u);
-    const unsigned long long Hm =
-        ((unsigned long long)H ^ (neg ? ~0ULL : 0ULL)) + ((neg && Lw == 0u) ? 1ULL : 0ULL);
-    const int bl = 64 - clz64_any(Hm);  // bit length of Hm, 0 .. 43
-    const int k = bl > 32 ? bl - 32 : 0;
-    const unsigned long long W = (Hm << (32 - k)) | (unsigned long long)(Lm >> k);
-    const bool sticky = (Lm & ((1u << k) - 1u)) != 0u;
-    const int z = k > 0 ? 0 : (bl > 0 ? 32 - bl : clz64_any((unsigned long long)Lm));  // leading zeros of W
-    const unsigned long long N = z < 64 ? W << z : 0ULL;
-    unsigned long long mant = N >> 11;
-    const unsigned int rb = (unsigned int)(N & 0x7FFULL);
-    const bool up = rb > 0x400u || (rb == 0x400u && (sticky || (mant & 1ULL)));
-    mant += up ? 1ULL : 0ULL;
-    const bool carry = (mant >> 53) != 0ULL;
-    mant = carry ? (mant >> 1) : mant;
-    E = (63 - z) + k + (carry ? 1 : 0) + sc + 1023;
-    ok = W == 0ULL || (E > 0 && E < 2047);
-    const unsigned long long bits =
-        (neg ? (1ULL << 63) : 0ULL) | ((unsigned long long)(E & 0x7FF) << 52) | (mant & 0xFFFFFFFFFFFFFULL);
-    return W == 0ULL ? 0ULL : bits;
+// The tensor-core epilogues turn the exact FP32 levels D of a sliced product
+// into one signed 64-bit window of the fixed-point value V = sum D 2^(8 k),
+// then round the window to FP64.  The window drops only the lowest bits of V
+// (8 or 10), fewer than the slicing itself leaves undetermined, so the result
+// is the FP64 value of V within one rounding plus 2^(bits dropped) units of
+// V's last place.  Power-of-two multiply-adds build it in a few 64-bit
+// integer instructions.
+
+// floor(V / 2^8) for the Ozaki levels V = sum_{g=2..8} D_g 2^(8 (8 - g)),
+// d[g - 2] = D_g.  With |D_g| <= (g - 1) 64 255^2 (K = 64, 8-bit slices) the
+// window is below 2^62.01 in magnitude.
+__host__ __device__ __forceinline__ long long ozaki_window8(const int (&d)[7]) {
+    long long w = (long long)(d[5] + (d[6] >> 8));  // D_7 + floor(D_8 / 2^8)
+    w += (long long)d[4] * 256;
+    w += (long long)d[3] * 65536;
+    w += (long long)d[2] * 16777216;
+    w += (long long)d[1] * 4294967296LL;
+    w += (long long)d[0] * 1099511627776LL;
+    return w;
 }
 
-// fixed_to_bits as a double, saturating outside the normal range: results
-// below 2^-1022 in magnitude become a signed zero, at or above 2^1024 an
-// infinity.
-__device__ __forceinline__ double fixed_to_double_sat(long long hi, long long lo, int sc) {
-    bool ok;
-    int E;
-    unsigned long long bits = fixed_to_bits(hi, lo, sc, ok, E);
-    if (!ok) bits = (bits & (1ULL << 63)) | (E > 0 ? 0x7FF0000000000000ULL : 0ULL);
-    return __longlong_as_double((long long)bits);
+// floor(V / 2^10) for the S-GEMM levels V = sum_{t=1..7} D_t 2^(8 (7 - t)),
+// d[t - 1] = D_t (0 beyond the slices in use).  With |D_t| < 2^24 (K <= 65792,
+// a +-1 operand against 8-bit slices) the window is below 2^62.01.
+__host__ __device__ __forceinline__ long long sgemm_window10(const int (&d)[7]) {
+    long long w = ((long long)d[5] * 256 + d[6]) >> 10;  // floor((D_6 2^8 + D_7) / 2^10)
+    w += (long long)d[4] * 64;
+    w += (long long)d[3] * 16384;
+    w += (long long)d[2] * 4194304;
+    w += (long long)d[1] * 1073741824LL;
+    w += (long long)d[0] * 274877906944LL;
+    return w;
 }
 
-
-// The value (hi 2^32 + lo) 2^sc as an FP64 bit pattern, rounded to nearest
-// even, built with 64-bit integer operations (|hi| < 2^43, |lo| < 2^52: the
-// exact fixed-point recombination of the slice products).  lo's upper half is
-// carried into hi first, so that the magnitude is Hm 2^32 + Lm with
-// 0 <= Lm < 2^32 and Hm < 2^44.
-__device__ __forceinline__ double fixed_to_double(long long hi, long long lo, int sc) {
-    long long H = hi + (lo >> 32);
-    unsigned long long Lw = (unsigned long long)lo & 0xFFFFFFFFULL;
-    const bool neg = H < 0;
-    unsigned long long Hm, Lm;
-    if (neg) {  // |V| = (-H) 2^32 - Lw
-        Hm = (unsigned long long)(-H) - (Lw ? 1ULL : 0ULL);
-        Lm = Lw ? (0x100000000ULL - Lw) : 0ULL;
-    } else {
-        Hm = (unsigned long long)H;
-        Lm = Lw;
-    }
-    unsigned long long mant;
-    int p;  // position of the leading one of the magnitude
-    if (Hm == 0) {
-        if (Lm == 0) return 0.0;
-        p = 63 - __clzll((long long)Lm);
-        mant = Lm << (52 - p);
-    } else {
-        const int b = 64 - __clzll((long long)Hm);  // bit length of Hm, <= 44
-        p = b + 31;
-        if (b <= 21) {
-            mant = ((Hm << 32) | Lm) << (21 - b);  // exact, < 2^53
-        } else {
-            const int sr = b - 21;  // 1 .. 23 low bits of Lm to drop
-            mant = (Hm << (32 - sr)) | (Lm >> sr);
-            const unsigned long long rem = Lm & ((1ULL << sr) - 1ULL), half = 1ULL << (sr - 1);
-            if (rem > half || (rem == half && (mant & 1ULL))) {
-                ++mant;
-                if (mant == (1ULL << 53)) {
-                    mant >>= 1;
-                    ++p;
-                }
-            }
-        }
-    }
-    const int E = p + sc + 1023;
-    if (E <= 0 || E >= 2047) {  // outside the normal range: FP64 fallback
-        const double d = (double)Hm * 4294967296.0 + (double)Lm;
-        return ldexp(neg ? -d : d, sc);
-    }
-    const unsigned long long bits =
-        (neg ? (1ULL << 63) : 0ULL) | ((unsigned long long)E << 52) | (mant & 0xFFFFFFFFFFFFFULL);
-    return __longlong_as_double((long long)bits);
+// x 2^sc for |x| < 2^63 as FP64, rounded to nearest with ties away from zero,
+// from integer operations: normalise |x| to a leading one at bit 63, round at
+// bit 10, and add the 53-bit result (implicit bit included) to (exponent - 1)
+// 2^52, so that a rounding carry lifts the exponent.  Results below 2^-1022
+// in magnitude become a signed zero, at or above 2^1024 an infinity.
+__host__ __device__ __forceinline__ double window_to_double(long long x, int sc) {
+    const unsigned long long sgn = (unsigned long long)x & 0x8000000000000000ULL;
+    const unsigned long long m = sgn ? 0ULL - (unsigned long long)x : (unsigned long long)x;
+    const int z = clz64_any(m);                             // 1 .. 64
+    const unsigned long long n = m << (z & 63);             // leading one at bit 63 (m != 0)
+    const unsigned long long r = ((n >> 10) + 1ULL) >> 1;   // in [2^52, 2^53]
+    const int eb = 1086 - z + sc;                           // biased exponent of the leading one
+    const int ef = eb + (int)(r >> 53);                     // ... after the rounding carry
+    unsigned long long bits = sgn | (((unsigned long long)(eb - 1) << 52) + r);  // mod 2^64
+    bits = ef > 2046 ? (sgn | 0x7FF0000000000000ULL) : bits;
+    bits = (m == 0ULL || ef < 1) ? sgn : bits;
+    double v;
+#ifdef __CUDA_ARCH__
+    v = __longlong_as_double((long long)bits);
+#else
+    __builtin_memcpy(&v, &bits, 8);
+#endif
+    return v;
 }
 
 // ------------------------------------------------------ host: tensor maps ---

@@ -1,7 +1,14 @@
-"""The integer-to-FP64 rounding of the tensor-core epilogues (fixed_to_bits in
-tc_ptx.cuh: V = hi 2^32 + lo, |V| < 2^75, times 2^sc) against exact round-to-
-nearest-even of the 128-bit integer, on the host.  The routine is
-__host__ __device__; the test compiles it with g++ from the header itself."""
+"""The integer-to-FP64 step of the tensor-core epilogues (tc_ptx.cuh), on the
+host, against exact 128-bit integer arithmetic:
+
+* ozaki_window8 / sgemm_window10 are floor(V / 2^8) and floor(V / 2^10) of
+  the fixed-point recombination V of the slice levels, for levels up to the
+  bounds the kernels guarantee;
+* window_to_double(x, sc) is x 2^sc rounded to nearest with ties away from
+  zero, a signed zero below 2^-1022 and an infinity from 2^1024 on.
+
+The routines are __host__ __device__; the test compiles them with g++ from
+the header itself."""
 import os
 import re
 import shutil
@@ -23,52 +30,102 @@ HARNESS = r"""
 #define __device__
 #define __forceinline__ inline
 %s
-static double ref_round(__int128 V, int sc) {
-    __int128 av = V < 0 ? -V : V;
-    if (av == 0) return 0.0;
-    int p = 0; __int128 t = av; while (t >>= 1) p++;
-    double r;
-    if (p <= 52) r = (double)(long long)av;
-    else {
-        int sh = p - 52; __int128 q = av >> sh, rem = av - (q << sh), half = ((__int128)1) << (sh - 1);
-        unsigned long long m = (unsigned long long)q; if (rem > half || (rem == half && (m & 1))) m++;
-        r = ldexp((double)m, sh);
-    }
-    r = ldexp(r, sc);
-    return V < 0 ? -r : r;
+typedef __int128 i128;
+static i128 floor_shift(i128 v, int s) {  // floor(v / 2^s), written without >>
+    const i128 p = (i128)1 << s;
+    i128 q = v / p;
+    if (v %% p != 0 && v < 0) q -= 1;
+    return q;
 }
+// x 2^sc, ties away from zero, flushed / saturated like the kernels
+static double ref_round(long long x, int sc) {
+    const bool neg = x < 0;
+    unsigned long long m = neg ? 0ULL - (unsigned long long)x : (unsigned long long)x;
+    if (m == 0) return neg ? -0.0 : 0.0;
+    int bl = 0; for (unsigned long long t = m; t; t >>= 1) ++bl;
+    unsigned long long q = m; int sh = 0;
+    if (bl > 53) {
+        sh = bl - 53;
+        const unsigned long long rem = m & ((1ULL << sh) - 1), half = 1ULL << (sh - 1);
+        q = m >> sh;
+        if (rem >= half) ++q;
+    }
+    int qbl = 0; for (unsigned long long t = q; t; t >>= 1) ++qbl;
+    const int e = qbl - 1 + sh + sc;  // exponent of the leading one after rounding
+    double r;
+    if (e < -1022) r = 0.0;
+    else if (e > 1023) r = INFINITY;
+    else r = ldexp((double)q, sh + sc);
+    return neg ? -r : r;
+}
+static bool same(double a, double b) { return memcmp(&a, &b, 8) == 0; }
 int main() {
     std::mt19937_64 g(11);
     long bad = 0, n = 0;
-    auto rnd = [&](int bits) { long long v = (long long)(g() >> (64 - bits)); return (g() & 1) ? -v : v; };
-    for (long it = 0; it < 3000000; ++it) {
-        long long hi, lo;
-        switch (it %% 7) {
-            case 0: hi = rnd(43); lo = rnd(51); break;
-            case 1: hi = 0; lo = rnd(1 + g() %% 50); break;
-            case 2: hi = rnd(1 + g() %% 42); lo = rnd(1 + g() %% 50); break;
-            case 3: hi = (long long)(g() %% 5) - 2; lo = rnd(33); break;
-            case 4: hi = rnd(31); lo = ((long long)(g() %% 3) - 1) << 32; break;
-            case 5: hi = rnd(43); lo = ((long long)(g() & 0xFFF)) << (g() %% 40); if (g() & 1) lo = -lo; break;
-            default: {  // exact ties of the 53-bit rounding
-                const int b = 54 + (int)(g() %% 20);
-                __int128 V = ((__int128)((g() | 1ULL) >> 11) << (b - 53)) | ((__int128)1 << (b - 54));
-                if (g() & 1) V = -V;
-                hi = (long long)(V >> 32); lo = (long long)(V - ((__int128)hi << 32));
-            }
+    auto rnd_bound = [&](long long bound) {  // uniform-ish in [-bound, bound], often near the ends
+        long long v;
+        switch (g() %% 4) {
+            case 0: v = bound; break;
+            case 1: v = bound - (long long)(g() %% 1000); break;
+            case 2: v = (long long)(g() %% (unsigned long long)(bound + 1)); break;
+            default: v = (long long)(g() >> (64 - 1 - (int)(g() %% 24)));
         }
-        const int sc = (int)(g() %% 200) - 100;
-        const __int128 V = ((__int128)hi << 32) + lo;
-        bool ok; int E;
-        const unsigned long long bits = fixed_to_bits(hi, lo, sc, ok, E);
-        if (!ok) continue;
+        if (v > bound) v = bound;
+        return (g() & 1) ? -v : v;
+    };
+    // 1. the Ozaki window: |D_g| <= (g - 1) 64 255^2
+    for (long it = 0; it < 1000000; ++it) {
+        int d[7];
+        for (int i = 0; i < 7; ++i) d[i] = (int)rnd_bound((long long)(i + 1) * 64 * 255 * 255);
+        i128 V = 0;
+        for (int i = 0; i < 7; ++i) V += (i128)d[i] << (8 * (6 - i));
         ++n;
-        double got; memcpy(&got, &bits, 8);
-        const double ref = ref_round(V, sc);
-        if (got != ref) { if (bad < 5) printf("mismatch hi=%%lld lo=%%lld sc=%%d\n", hi, lo, sc); ++bad; }
+        if ((i128)ozaki_window8(d) != floor_shift(V, 8)) { if (bad < 5) printf("ozaki window %%ld\n", it); ++bad; }
+    }
+    // 2. the S-GEMM window: |D_t| <= 255 x 65792 < 2^24
+    for (long it = 0; it < 1000000; ++it) {
+        int d[7];
+        const int SB = 1 + (int)(g() %% 7);
+        for (int i = 0; i < 7; ++i) d[i] = i < SB ? (int)rnd_bound(255LL * 65792) : 0;
+        i128 V = 0;
+        for (int i = 0; i < 7; ++i) V += (i128)d[i] << (8 * (6 - i));
+        ++n;
+        if ((i128)sgemm_window10(d) != floor_shift(V, 10)) { if (bad < 5) printf("sgemm window %%ld\n", it); ++bad; }
+    }
+    // 3. the rounding: random bit lengths, exact ties, carries into the next
+    //    binade, and scales across both ends of the exponent range
+    for (long it = 0; it < 3000000; ++it) {
+        long long x;
+        const int kind = (int)(it %% 5);
+        const int bl = 1 + (int)(g() %% 63);
+        unsigned long long m = (g() >> (64 - bl)) | (1ULL << (bl - 1));
+        if (kind == 1 && bl > 54) {  // an exact tie at the 53-bit rounding
+            const int sh = bl - 53;
+            m = (m >> sh << sh) | (1ULL << (sh - 1));
+            m &= ~((1ULL << (sh - 1)) - 1);
+            m |= 1ULL << (sh - 1);
+        } else if (kind == 2 && bl > 53) {  // all ones: rounds up to the next power of two
+            m = (bl == 64) ? ~0ULL >> 1 : ((1ULL << bl) - 1);
+        } else if (kind == 3) {
+            m = (unsigned long long)(g() %% 3);
+        }
+        m &= ~(1ULL << 63);
+        x = (g() & 1) ? -(long long)m : (long long)m;
+        int sc;
+        switch (g() %% 3) {
+            case 0: sc = (int)(g() %% 200) - 100; break;
+            case 1: sc = -1085 + (int)(g() %% 80); break;   // near the flush to zero
+            default: sc = 960 + (int)(g() %% 80);           // near the saturation
+        }
+        ++n;
+        const double got = window_to_double(x, sc), ref = ref_round(x, sc);
+        if (!same(got, ref) && !(m == 0 && got == 0.0 && ref == 0.0)) {
+            if (bad < 5) printf("round x=%%lld sc=%%d got %%a ref %%a\n", x, sc, got, ref);
+            ++bad;
+        }
     }
     printf("checked %%ld bad %%ld\n", n, bad);
-    return bad != 0 || n < 2000000;
+    return bad != 0 || n < 4000000;
 }
 """
 
@@ -76,12 +133,12 @@ int main() {
 def _extract():
     src = open(HEADER).read()
     a = src.index("__host__ __device__ __forceinline__ int clz64_any")
-    b = src.index("\n}\n", src.index("fixed_to_bits(")) + 3
+    b = src.index("\n}\n", src.index("double window_to_double(")) + 3
     return src[a:b]
 
 
 @pytest.mark.skipif(shutil.which("g++") is None, reason="needs g++")
-def test_fixed_to_bits_rounds_like_exact_int128():
+def test_epilogue_windows_and_rounding_match_exact_int128():
     with tempfile.TemporaryDirectory() as d:
         cpp = os.path.join(d, "f2b.cpp")
         exe = os.path.join(d, "f2b")
