@@ -600,143 +600,117 @@ __global__ void __launch_bounds__(32 * kTrtriWarps) k_trtri64(const double *__re
 //
 // One cooperative launch per direction.  CTA b owns block rows b, b + G, ...
 // (64 rows each) in solve order.  For its block row i it streams the blocks
-// L_ij of the rows already solved (flag[j] set), accumulating L_ij y_j with
-// coalesced row loads, then applies the inverted diagonal block and
-// publishes y_i with a release store of flag[i].  Every block row waits only
-// on rows that come earlier in solve order, and a CTA takes its rows in that
+// L_ij of the rows already solved, accumulating L_ij y_j with coalesced row
+// loads, then applies the inverted diagonal block and writes y_i.  There are
+// no flags: the solved vector starts filled with a NaN sentinel (all bytes
+// 0xFF, a pattern FP64 arithmetic does not produce), and each warp waits on
+// the values themselves, so that the wait and the load of y_j are one L2
+// access on the chain of dependent block rows.  Every block row waits only on
+// rows that come earlier in solve order, and a CTA takes its rows in that
 // order, so with all CTAs resident (cooperative launch) every wait ends; each
 // wait is still bounded by the global timer and records error 6 (forward) or
-// 7 (backward) before the CTA returns.
+// 7 (backward), after which the CTA finishes its row without waiting again.
 constexpr int kTrsvThreads = 256;
+constexpr unsigned long long kSolveSentinel = 0xFFFFFFFFFFFFFFFFULL;
 
-__device__ __forceinline__ int ld_acquire_flag(const int *p) {
-    int v;
-    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
+__device__ __forceinline__ double ld_relaxed_f64(const double *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return __longlong_as_double((long long)v);
 }
 
-__device__ __forceinline__ void st_release_flag(int *p, int v) {
-    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Thread 0 advances `ready` (shared) past every consecutive block whose flag
-// holds `want`, stepping by `dir`, waiting while the next needed block is not
-// ready; false on time-out.
-__device__ bool advance_ready(const int *flags, int want, int dir, int stop, int *ready, int *err, int code) {
-    __shared__ int ok;
-    __syncthreads();  // every thread has read the previous `ready`
-    if (threadIdx.x == 0) {
-        ok = 1;
-        int r = *ready;
-        const unsigned long long t0 = global_ns();
-        if (r != stop) {
-            for (long long it = 0;; ++it) {
-                if (ld_acquire_flag(flags + r) == want) break;
-                if ((it & 255) == 255 && global_ns() - t0 > kWaitNs) {
-                    atomicExch(err, code);
-                    ok = 0;
-                    break;
-                }
-            }
-            if (ok) {
-                r += dir;
-                while (r != stop && ld_acquire_flag(flags + r) == want) r += dir;
-            }
+// The warp waits until both y[lane] and y[lane + 32] hold solved values
+// (lanes past `valid` read nothing and give 0); false on time-out.
+__device__ bool wait_solved(const double *y, int lane, int valid, double &a, double &b, int *err, int code) {
+    const unsigned long long t0 = global_ns();
+    for (long long it = 0;; ++it) {
+        a = lane < valid ? ld_relaxed_f64(y + lane) : 0.0;
+        b = lane + 32 < valid ? ld_relaxed_f64(y + lane + 32) : 0.0;
+        const bool ok = (unsigned long long)__double_as_longlong(a) != kSolveSentinel &&
+                        (unsigned long long)__double_as_longlong(b) != kSolveSentinel;
+        if (__all_sync(0xffffffffu, ok)) return true;
+        if ((it & 63) == 63 && global_ns() - t0 > kWaitNs) {
+            if (lane == 0) atomicExch(err, code);
+            return false;
         }
-        *ready = r;
     }
-    __syncthreads();
-    return ok != 0;
 }
 
-// L y = b: b is overwritten by y.  flags[nb] must be zero; set to 1.
+// L y = b: y (sentinel-filled) receives the solution; b is read and refilled
+// with the sentinel for the backward solve.
 __global__ void __launch_bounds__(kTrsvThreads) k_trsv_fwd(const double *__restrict__ L, int64_t n,
-                                                           const double *__restrict__ Linv, double *b, int *flags,
+                                                           const double *__restrict__ Linv, double *b, double *y,
                                                            int *err) {
     __shared__ double inv[kNB * kNB];
     __shared__ double acc[kNB];
-    __shared__ int ready;
     const int nb = (int)((n + kNB - 1) / kNB);
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     for (int i = blockIdx.x; i < nb; i += gridDim.x) {
         const int64_t r0 = (int64_t)i * kNB;
         const int kb = (int)(n - r0 < kNB ? n - r0 : kNB);
         for (int e = t; e < kNB * kNB; e += kTrsvThreads) inv[e] = Linv[(size_t)i * kNB * kNB + e];
-        if (t == 0) ready = 0;
-        __syncthreads();
         // warp w: rows 8w .. 8w + 7 of the block; lanes: columns lane, lane + 32
-        double part[8];
+        double part[8], bi[8];  // bi: the right-hand side of the warp's rows, read early
 #pragma unroll
-        for (int u = 0; u < 8; ++u) part[u] = 0.0;
-        int j = 0;
-        while (j < i) {
-            // block j is the next one needed: its L entries are loaded before
-            // the wait for y_j, so that only FMAs follow the flag
+        for (int u = 0; u < 8; ++u) {
+            part[u] = 0.0;
+            bi[u] = (lane == 0 && warp * 8 + u < kb) ? b[r0 + warp * 8 + u] : 0.0;
+        }
+        bool live = true;
+        for (int j = 0; j < i && live; ++j) {
+            const int64_t c0 = (int64_t)j * kNB;  // j < i: a full block
+            // the block's L entries are in flight while the warp waits for y_j
             double p0[8], p1[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const int r = warp * 8 + u;
-                const double *row = L + (size_t)(r0 + (r < kb ? r : 0)) * n + (int64_t)j * kNB;
+                const double *row = L + (size_t)(r0 + (r < kb ? r : 0)) * n + c0;
                 p0[u] = row[lane];
                 p1[u] = row[lane + 32];
             }
-            if (!advance_ready(flags, 1, 1, i, &ready, err, 6)) return;
-            const int upto = ready;
-            {
-                const int64_t c0 = (int64_t)j * kNB;
-                const double y0 = __ldcg(b + c0 + lane), y1 = __ldcg(b + c0 + lane + 32);
+            double y0, y1;
+            live = wait_solved(y + c0, lane, kNB, y0, y1, err, 6);
 #pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    if (warp * 8 + u < kb) part[u] = fma(p0[u], y0, fma(p1[u], y1, part[u]));
-                ++j;
-            }
-            for (; j < upto; ++j) {
-                const int64_t c0 = (int64_t)j * kNB;  // j < i: a full block
-                const double y0 = __ldcg(b + c0 + lane), y1 = __ldcg(b + c0 + lane + 32);
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int r = warp * 8 + u;
-                    if (r < kb) {
-                        const double *row = L + (size_t)(r0 + r) * n + c0;
-                        part[u] = fma(row[lane], y0, fma(row[lane + 32], y1, part[u]));
-                    }
-                }
-            }
+            for (int u = 0; u < 8; ++u)
+                if (warp * 8 + u < kb) part[u] = fma(p0[u], y0, fma(p1[u], y1, part[u]));
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const double sum = warp_sum(part[u]);
             const int r = warp * 8 + u;
-            if (lane == 0) acc[r] = r < kb ? __ldcg(b + r0 + r) - sum : 0.0;
+            if (lane == 0) {
+                acc[r] = r < kb ? bi[u] - sum : 0.0;
+                if (r < kb) b[r0 + r] = __longlong_as_double((long long)kSolveSentinel);
+            }
         }
         __syncthreads();
-        // y_i = Linv_i acc: four threads per row, 16 columns each
+        // y_i = Linv_i acc: four threads per row, 16 columns each, in two
+        // independent FMA chains (a dependent FP64 FMA costs tens of cycles)
         {
             const int r = t >> 2, q = t & 3;
-            double y = 0.0;
+            double ya = 0.0, yb = 0.0;
 #pragma unroll
-            for (int c = q * 16; c < q * 16 + 16; ++c) y = fma(inv[r * kNB + c], acc[c], y);
-            y += __shfl_xor_sync(0xffffffffu, y, 1);
-            y += __shfl_xor_sync(0xffffffffu, y, 2);
-            if (q == 0 && r < kb) b[r0 + r] = y;
+            for (int c = q * 16; c < q * 16 + 16; c += 2) {
+                ya = fma(inv[r * kNB + c], acc[c], ya);
+                yb = fma(inv[r * kNB + c + 1], acc[c + 1], yb);
+            }
+            double v = ya + yb;
+            v += __shfl_xor_sync(0xffffffffu, v, 1);
+            v += __shfl_xor_sync(0xffffffffu, v, 2);
+            if (q == 0 && r < kb) __stcg(y + r0 + r, v);
         }
-        __syncthreads();
-        if (t == 0) {
-            __threadfence();
-            st_release_flag(flags + i, 1);
-        }
+        __syncthreads();  // inv and acc are reused by the CTA's next row
     }
 }
 
-// L^T x = y: b (holding y) is overwritten by x.  flags[nb] must hold 1; set
-// to 2.  Block rows are solved from the last to the first.
+// L^T x = y: y holds the forward solution; x goes to b (sentinel-filled by
+// the forward solve).  Block rows are solved from the last to the first.
 __global__ void __launch_bounds__(kTrsvThreads) k_trsv_bwd(const double *__restrict__ L, int64_t n,
-                                                           const double *__restrict__ Linv, double *b, int *flags,
-                                                           int *err) {
+                                                           const double *__restrict__ Linv, double *b,
+                                                           const double *y, int *err) {
     __shared__ double inv[kNB * kNB];
     __shared__ double part_s[kTrsvThreads / 32][kNB];
     __shared__ double acc[kNB];
-    __shared__ int ready;
     const int nb = (int)((n + kNB - 1) / kNB);
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     for (int ii = blockIdx.x; ii < nb; ii += gridDim.x) {
@@ -744,52 +718,38 @@ __global__ void __launch_bounds__(kTrsvThreads) k_trsv_bwd(const double *__restr
         const int64_t c0 = (int64_t)i * kNB;
         const int kb = (int)(n - c0 < kNB ? n - c0 : kNB);
         for (int e = t; e < kNB * kNB; e += kTrsvThreads) inv[e] = Linv[(size_t)i * kNB * kNB + e];
-        if (t == 0) ready = nb - 1;
-        __syncthreads();
         // lanes: columns lane, lane + 32 of block column i; warp w: rows w, w + 8, ... of block row j
         double p0 = 0.0, p1 = 0.0;
         const bool v0 = lane < kb, v1 = lane + 32 < kb;
-        int j = nb - 1;
-        while (j > i) {
-            // block j is the next one needed: load its L entries before the wait
+        const double yi = t < kb ? y[c0 + t] : 0.0;  // the right-hand side, read early (threads < 64 use it)
+        bool live = true;
+        for (int j = nb - 1; j > i && live; --j) {
+            const int64_t r0 = (int64_t)j * kNB;
+            const int kr = (int)(n - r0 < kNB ? n - r0 : kNB);
+            // the block's L entries are in flight while the warp waits for x_j
             double q0[8], q1[8];
-            {
-                const int64_t r0 = (int64_t)j * kNB;
-                const int kr = (int)(n - r0 < kNB ? n - r0 : kNB);
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int r = warp + 8 * u;
-                    const double *row = L + (size_t)(r0 + (r < kr ? r : 0)) * n + c0;
-                    q0[u] = v0 ? row[lane] : 0.0;
-                    q1[u] = v1 ? row[lane + 32] : 0.0;
-                }
+            for (int u = 0; u < 8; ++u) {
+                const int r = warp + 8 * u;
+                const double *row = L + (size_t)(r0 + (r < kr ? r : 0)) * n + c0;
+                q0[u] = v0 ? row[lane] : 0.0;
+                q1[u] = v1 ? row[lane + 32] : 0.0;
             }
-            if (!advance_ready(flags, 2, -1, i, &ready, err, 7)) return;
-            const int downto = ready;
-            {
-                const int64_t r0 = (int64_t)j * kNB;
-                const int kr = (int)(n - r0 < kNB ? n - r0 : kNB);
+            double xa, xb;  // x_j: lane holds rows lane, lane + 32 of block j
+            live = wait_solved(b + r0, lane, kr, xa, xb, err, 7);
+            // four independent chains per column, summed after
+            double a0[4] = {0.0, 0.0, 0.0, 0.0}, a1[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int r = warp + 8 * u;
-                    if (r < kr) {
-                        const double x = __ldcg(b + r0 + r);
-                        p0 = fma(q0[u], x, p0);
-                        p1 = fma(q1[u], x, p1);
-                    }
-                }
-                --j;
-            }
-            for (; j > downto; --j) {
-                const int64_t r0 = (int64_t)j * kNB;
-                const int kr = (int)(n - r0 < kNB ? n - r0 : kNB);
-                for (int r = warp; r < kr; r += kTrsvThreads / 32) {
-                    const double x = __ldcg(b + r0 + r);
-                    const double *row = L + (size_t)(r0 + r) * n + c0;
-                    if (v0) p0 = fma(row[lane], x, p0);
-                    if (v1) p1 = fma(row[lane + 32], x, p1);
+            for (int u = 0; u < 8; ++u) {
+                const int r = warp + 8 * u;  // < 64: its x is in lane r (xa) or r - 32 (xb)
+                const double xr = r < 32 ? __shfl_sync(0xffffffffu, xa, r) : __shfl_sync(0xffffffffu, xb, r - 32);
+                if (r < kr) {
+                    a0[u & 3] = fma(q0[u], xr, a0[u & 3]);
+                    a1[u & 3] = fma(q1[u], xr, a1[u & 3]);
                 }
             }
+            p0 += (a0[0] + a0[1]) + (a0[2] + a0[3]);
+            p1 += (a1[0] + a1[1]) + (a1[2] + a1[3]);
         }
         part_s[warp][lane] = p0;
         part_s[warp][lane + 32] = p1;
@@ -798,24 +758,25 @@ __global__ void __launch_bounds__(kTrsvThreads) k_trsv_bwd(const double *__restr
             double sum = 0.0;
 #pragma unroll
             for (int w = 0; w < kTrsvThreads / 32; ++w) sum += part_s[w][t];
-            acc[t] = t < kb ? __ldcg(b + c0 + t) - sum : 0.0;
+            acc[t] = t < kb ? yi - sum : 0.0;
         }
         __syncthreads();
-        // x_i = Linv_i^T acc: four threads per column, 16 rows each
+        // x_i = Linv_i^T acc: four threads per column, 16 rows each, in two
+        // independent FMA chains
         {
             const int c = t >> 2, q = t & 3;
-            double x = 0.0;
+            double xa = 0.0, xb = 0.0;
 #pragma unroll
-            for (int r = q * 16; r < q * 16 + 16; ++r) x = fma(inv[r * kNB + c], acc[r], x);
+            for (int r = q * 16; r < q * 16 + 16; r += 2) {
+                xa = fma(inv[r * kNB + c], acc[r], xa);
+                xb = fma(inv[(r + 1) * kNB + c], acc[r + 1], xb);
+            }
+            double x = xa + xb;
             x += __shfl_xor_sync(0xffffffffu, x, 1);
             x += __shfl_xor_sync(0xffffffffu, x, 2);
-            if (q == 0 && c < kb) b[c0 + c] = x;
+            if (q == 0 && c < kb) __stcg(b + c0 + c, x);
         }
-        __syncthreads();
-        if (t == 0) {
-            __threadfence();
-            st_release_flag(flags + i, 2);
-        }
+        __syncthreads();  // inv, part_s and acc are reused by the CTA's next row
     }
 }
 
@@ -947,7 +908,7 @@ cudaError_t launch_ozaki_gemm(const __nv_bfloat16 *Asl, const int *expA, int64_t
 size_t tc_chol_ws_bytes(int64_t n) {
     const int64_t nb = (n + kNB - 1) / kNB;
     return 2 * slice_elems(n, kMaxSlices) * 2 + slice_elems(kNB, kMaxSlices) * 2 + (size_t)(2 * n + kNB) * 4 +
-           (size_t)nb * kNB * kNB * 8 + (size_t)nb * 4 + 9 * 256;
+           (size_t)nb * kNB * kNB * 8 + (size_t)n * 8 + 9 * 256;
 }
 
 namespace {
@@ -955,7 +916,7 @@ struct TcWs {
     __nv_bfloat16 *Asl, *Bsl, *Asl2;
     int *expA, *expB, *expA2;
     double *Linv;
-    int *flags;  // [nb] block-row flags of the triangular solves
+    double *y;   // [n] forward-solve vector of the triangular solves
 };
 TcWs carve_tc(void *ws, int64_t n) {
     char *p = static_cast<char *>(ws);
@@ -972,19 +933,19 @@ TcWs carve_tc(void *ws, int64_t n) {
     w.Linv = reinterpret_cast<double *>(take((size_t)((n + kNB - 1) / kNB) * kNB * kNB * 8));
     w.Asl2 = reinterpret_cast<__nv_bfloat16 *>(take(slice_elems(n, kMaxSlices) * 2));
     w.expA2 = reinterpret_cast<int *>(take((size_t)n * 4));
-    w.flags = reinterpret_cast<int *>(take((size_t)((n + kNB - 1) / kNB) * 4));
+    w.y = reinterpret_cast<double *>(take((size_t)n * 8));
     return w;
 }
 }  // namespace
 
 // Blocked right-looking Cholesky with tensor-core (Ozaki, 7 slices) panel
 // solves and trailing updates, and a look-ahead of one panel: after panel k
-// the main stream first updates only block column k + 1 ("narrow" update),
-// then the side stream factors panel k + 1 (diagonal block, its inverse, the
-// panel product and its slices) while the main stream applies panel k to the
-// rest of the trailing matrix ("wide" update).  Panel slices alternate
-// between two buffers.  The inverted diagonal blocks stay in the workspace
-// for launch_cholesky_solve_tc.
+// the side stream updates block column k + 1 alone (the "narrow" update) and
+// factors panel k + 1 (diagonal block, its inverse, the panel product and its
+// slices), while the main stream applies panel k to the rest of the trailing
+// matrix (the "wide" update).  Panel slices alternate between two buffers.
+// The inverted diagonal blocks stay in the workspace for
+// launch_cholesky_solve_tc.
 namespace {
 
 // Factor panel k (columns k0 .. k0 + kb - 1) whose block column is up to date:
@@ -1096,11 +1057,11 @@ cudaError_t launch_cholesky_solve_tc(const double *L, int64_t n, const void *ws,
     const int gf = std::min(nb, sms * std::min(per_sm_f, 1)), gb = std::min(nb, sms * std::min(per_sm_b, 1));
     if (gf < 1 || gb < 1) return cudaErrorLaunchOutOfResources;
     const int slot = prof_begin(NK_PROF_TRSV, st);
-    e = cudaMemsetAsync(w.flags, 0, (size_t)nb * 4, st);
+    e = cudaMemsetAsync(w.y, 0xFF, (size_t)n * 8, st);  // the sentinel of unsolved entries
     if (e != cudaSuccess) return e;
     const double *Linv = w.Linv;
-    int *flags = w.flags;
-    void *args[] = {(void *)&L, (void *)&n, (void *)&Linv, (void *)&b, (void *)&flags, (void *)&err};
+    double *y = w.y;
+    void *args[] = {(void *)&L, (void *)&n, (void *)&Linv, (void *)&b, (void *)&y, (void *)&err};
     e = cudaLaunchCooperativeKernel((const void *)k_trsv_fwd, dim3(gf), dim3(kTrsvThreads), args, 0, st);
     nk::note_launch();
     if (e != cudaSuccess) return e;
