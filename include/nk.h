@@ -420,6 +420,16 @@ nk_status nk_prof_enable(int32_t on);
 int64_t nk_launch_count(void);
 nk_status nk_prof_read(int32_t cls, double *ms /* host */, int64_t *launches /* host */,
                        double *work /* host */);
+/* The bracketed launches since the last nk_prof_enable, in the order they
+ * were enqueued: for entry i (i < max) the class cls[i] and the start and
+ * end times t0_ms[i], t1_ms[i] in milliseconds from the start of the first
+ * entry (all streams on one clock: the events' device timestamps).  Waits
+ * for the events.  *n_out receives the number of entries (which may exceed
+ * max; only the first max are written).  All pointers HOST; cls, t0_ms and
+ * t1_ms may be NULL when max is 0.  NK_ERR_INVALID_ARG for a NULL n_out or
+ * a NULL array with max > 0. */
+nk_status nk_prof_trace(int32_t max, int32_t *cls /* host */, double *t0_ms /* host */, double *t1_ms /* host */,
+                        int32_t *n_out /* host */);
 
 #ifdef __cplusplus
 }

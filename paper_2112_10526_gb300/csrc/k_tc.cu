@@ -184,7 +184,8 @@ struct OzArgs {
     int lower;            // only entries with col <= row (tiles above are skipped)
     int *err;
     int64_t n_nb;         // tile columns
-    int chunk;            // tiles per strip, 1 .. kMaxChunk
+    int chunk;            // tiles per strip: 1, 2, 4 or 8
+    int chunk_log2;
 };
 
 constexpr int kPN = 32;                      // tile columns
@@ -201,8 +202,10 @@ __host__ __device__ inline int64_t oz_row_tiles(int64_t n_nb, bool lower, int64_
     return last < n_nb ? last : n_nb;
 }
 
-__host__ __device__ inline int64_t oz_row_strips(int64_t n_nb, bool lower, int64_t mb, int chunk) {
-    return (oz_row_tiles(n_nb, lower, mb) + chunk - 1) / chunk;
+// strips of tile row mb (a power-of-two chunk: every CTA walks the rows before
+// its own, so the step is a shift, not a 64-bit division)
+__host__ __device__ inline int64_t oz_row_strips(int64_t n_nb, bool lower, int64_t mb, int chunk_log2) {
+    return (oz_row_tiles(n_nb, lower, mb) + ((int64_t)1 << chunk_log2) - 1) >> chunk_log2;
 }
 
 // The MMAs of one tile: level g = s + t (2 .. S+1) collects the products of
@@ -247,15 +250,33 @@ __global__ void __launch_bounds__(kPThreads, 1)
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tslot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int S = SS > 0 ? SS : a.S;
-    // strip -> tile row mb, first tile column nb0, tile count
+    // strip -> tile row mb, first tile column nb0, tile count: every warp scans
+    // the strips per tile row, 32 rows per round (inclusive prefix by
+    // shuffles), and takes the first row whose prefix passes blockIdx.x
     int64_t mb = 0, rem = blockIdx.x;
-    for (;;) {
-        const int64_t ns = oz_row_strips(a.n_nb, a.lower != 0, mb, a.chunk);
-        if (rem < ns) break;
-        rem -= ns;
-        ++mb;
+    {
+        const int64_t n_mb = (a.rows + kTileM - 1) / kTileM;
+        for (int64_t base = 0; base < n_mb; base += 32) {
+            const int64_t m = base + lane;
+            const int64_t ns = m < n_mb ? oz_row_strips(a.n_nb, a.lower != 0, m, a.chunk_log2) : 0;
+            int64_t incl = ns;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int64_t v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const int64_t total = __shfl_sync(0xffffffffu, incl, 31);
+            if (rem < total) {  // warp-uniform
+                const int l = __ffs(__ballot_sync(0xffffffffu, rem < incl)) - 1;
+                mb = base + l;
+                rem -= __shfl_sync(0xffffffffu, incl - ns, l);
+                break;
+            }
+            rem -= total;
+            mb = base + 32;
+        }
     }
-    const int64_t nb0 = rem * a.chunk, in_row = oz_row_tiles(a.n_nb, a.lower != 0, mb);
+    const int64_t nb0 = rem << a.chunk_log2, in_row = oz_row_tiles(a.n_nb, a.lower != 0, mb);
     const int count = (int)(in_row - nb0 < a.chunk ? in_row - nb0 : a.chunk);
     const int64_t m0 = mb * kTileM;
 
@@ -866,7 +887,7 @@ cudaError_t launch_ozaki_gemm_strided(const __nv_bfloat16 *Asl, const int *expA,
     const void *kern = S == kMaxSlices ? (const void *)k_ozaki_gemm<kMaxSlices> : (const void *)k_ozaki_gemm<0>;
     cudaError_t e = nk::allow_max_dynamic_smem(kern);
     if (e != cudaSuccess) return e;
-    OzArgs a{rows, cols, S, expA, expB, C, ldc, mode, lower ? 1 : 0, err, (cols + kPN - 1) / kPN, 1};
+    OzArgs a{rows, cols, S, expA, expB, C, ldc, mode, lower ? 1 : 0, err, (cols + kPN - 1) / kPN, 1, 0};
     const int64_t n_mb = (rows + kTileM - 1) / kTileM;
     // strips of up to 8 tiles amortise a CTA's A slices over its tiles; a
     // product with few tiles per SM (the panel solve and the narrow update of
@@ -878,9 +899,12 @@ cudaError_t launch_ozaki_gemm_strided(const __nv_bfloat16 *Asl, const int *expA,
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     const int64_t per_sm = sms > 0 ? tiles / sms : kMaxChunk;
-    a.chunk = (int)(per_sm < 1 ? 1 : (per_sm > kMaxChunk ? kMaxChunk : per_sm));
+    while (a.chunk < kMaxChunk && 2 * a.chunk <= per_sm) {
+        a.chunk *= 2;
+        ++a.chunk_log2;
+    }
     int64_t strips = 0;
-    for (int64_t m = 0; m < n_mb; ++m) strips += oz_row_strips(a.n_nb, lower, m, a.chunk);
+    for (int64_t m = 0; m < n_mb; ++m) strips += oz_row_strips(a.n_nb, lower, m, a.chunk_log2);
     if (strips > (1LL << 31) - 1) return cudaErrorInvalidValue;
     if (S == kMaxSlices)
         (k_ozaki_gemm<kMaxSlices><<<(unsigned)strips, kPThreads, ozaki_smem_bytes(), st>>>(ma, mb, a),

@@ -118,4 +118,29 @@ nk_status nk_prof_read(int32_t cls, double *ms, int64_t *launches, double *work)
     return NK_OK;
 }
 
+nk_status nk_prof_trace(int32_t max, int32_t *cls, double *t0_ms, double *t1_ms, int32_t *n_out) {
+    if (!n_out || max < 0 || (max > 0 && (!cls || !t0_ms || !t1_ms))) return NK_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_mu);
+    int32_t n = 0;
+    cudaEvent_t first = nullptr;
+    for (size_t i = 0; i < g_used; ++i) {
+        Slot &s = g_slots[i];
+        if (!s.closed) continue;
+        if (cudaEventSynchronize(s.stop) != cudaSuccess) return NK_ERR_CUDA;
+        if (!first) first = s.start;
+        if (n < max) {
+            float a = 0.f, b = 0.f;
+            if (cudaEventElapsedTime(&a, first, s.start) != cudaSuccess ||
+                cudaEventElapsedTime(&b, first, s.stop) != cudaSuccess)
+                return NK_ERR_CUDA;
+            cls[n] = s.cls;
+            t0_ms[n] = a;
+            t1_ms[n] = b;
+        }
+        ++n;
+    }
+    *n_out = n;
+    return NK_OK;
+}
+
 }  // extern "C"

@@ -152,6 +152,9 @@ def lib():
     L.nk_prof_read.argtypes = [i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                                ctypes.POINTER(ctypes.c_double)]
     L.nk_prof_read.restype = ctypes.c_int32
+    L.nk_prof_trace.argtypes = [i32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]
+    L.nk_prof_trace.restype = ctypes.c_int32
     L.nk_launch_count.argtypes = []
     L.nk_launch_count.restype = ctypes.c_int64
     L.nk_request_bytes.argtypes = [ctypes.POINTER(nk_request)]
@@ -387,6 +390,20 @@ def nk_prof_read(cls):
     c = PROF_CLASSES[cls] if isinstance(cls, str) else int(cls)
     _check(lib().nk_prof_read(c, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(w)))
     return ms.value, n.value, w.value
+
+
+def nk_prof_trace():
+    """[(class name, start ms, end ms)] of the bracketed launches since
+    nk_prof_enable, in enqueue order, on one clock across streams."""
+    n = ctypes.c_int32()
+    _check(lib().nk_prof_trace(0, None, None, None, ctypes.byref(n)))
+    m = n.value
+    cls = (ctypes.c_int32 * max(m, 1))()
+    t0 = (ctypes.c_double * max(m, 1))()
+    t1 = (ctypes.c_double * max(m, 1))()
+    _check(lib().nk_prof_trace(m, cls, t0, t1, ctypes.byref(n)))
+    names = {v: k for k, v in PROF_CLASSES.items()}
+    return [(names.get(cls[i], str(cls[i])), t0[i], t1[i]) for i in range(min(m, n.value))]
 
 
 def nk_launch_count():
