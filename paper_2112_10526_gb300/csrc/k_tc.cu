@@ -974,22 +974,37 @@ namespace {
 
 // Factor panel k (columns k0 .. k0 + kb - 1) whose block column is up to date:
 // diagonal block + inverse, L_panel = A_panel L_kk^-T, slices of L_panel.
+// With an aux stream (cs non-null), the panel rows below the diagonal block
+// are sliced there, beside the diagonal block's factorisation and inverse:
+// the slicing depends only on the narrow update that precedes the panel.
 cudaError_t panel_step(double *A, int64_t n, int64_t k0, int *info, int *err, TcWs &w, __nv_bfloat16 *Lsl,
-                       int *Lexp, cudaStream_t st) {
+                       int *Lexp, cudaStream_t st, const CholStreams *cs) {
     const int S = kMaxSlices;
     const int kb = (int)(n - k0 < kNB ? n - k0 : kNB);
     const int64_t rest = n - k0 - kb;
     double *Linv = w.Linv + (size_t)(k0 / kNB) * kNB * kNB;
+    double *panel = A + (size_t)(k0 + kb) * n + k0;
+    cudaError_t e = cudaSuccess;
+    const bool fork = cs != nullptr && cs->aux != nullptr && rest > 0;
+    if (fork) {
+        e = cudaEventRecord(cs->ev_fork, st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs->aux, cs->ev_fork, 0);
+        if (e != cudaSuccess) return e;
+        const int aslot = prof_begin(NK_PROF_CHOL_PANEL, cs->aux);
+        e = launch_slice_rows(panel, n, rest, kb, S, Lsl, Lexp, cs->aux);
+        prof_end(aslot, cs->aux, 0.0);
+        if (e == cudaSuccess) e = cudaEventRecord(cs->ev_join, cs->aux);
+        if (e != cudaSuccess) return e;
+    }
     // timing classes: the FP64 diagonal-block kernels and the slicing count
     // as the panel, the tensor-core panel product with the trailing updates
     int slot = prof_begin(NK_PROF_CHOL_PANEL, st);
     (k_potrf64<<<1, kPotrfThreads, 0, st>>>(A, n, k0, kb, info), nk::note_launch());
     (k_trtri64<<<kNB / kTrtriWarps, 32 * kTrtriWarps, 0, st>>>(A, n, k0, kb, Linv), nk::note_launch());
-    cudaError_t e = cudaSuccess;
-    double *panel = A + (size_t)(k0 + kb) * n + k0;
     if (rest > 0) {
         e = launch_slice_rows(Linv, kNB, kb, kb, S, w.Bsl, w.expB, st);
-        if (e == cudaSuccess) e = launch_slice_rows(panel, n, rest, kb, S, Lsl, Lexp, st);
+        if (e == cudaSuccess) e = fork ? cudaStreamWaitEvent(st, cs->ev_join, 0)
+                                       : launch_slice_rows(panel, n, rest, kb, S, Lsl, Lexp, st);
     }
     prof_end(slot, st, 2.0 * (double)kb * kb * kb / 3.0);
     if (rest > 0 && e == cudaSuccess) {
@@ -1006,7 +1021,7 @@ cudaError_t panel_step(double *A, int64_t n, int64_t k0, int *info, int *err, Tc
 }  // namespace
 
 cudaError_t launch_cholesky_tc(double *A, int64_t n, int *info, int *err, void *ws, cudaStream_t st,
-                               cudaStream_t side, cudaEvent_t ev_wide, cudaEvent_t ev_panel) {
+                               const CholStreams *cs) {
     // Step k, with panel k factored and sliced:
     //   side stream: the narrow update (block column k+1 by panel k), then
     //     panel k+1 (factor, invert, solve, slice);
@@ -1021,9 +1036,10 @@ cudaError_t launch_cholesky_tc(double *A, int64_t n, int *info, int *err, void *
     __nv_bfloat16 *buf[2] = {w.Asl, w.Asl2};
     int *bexp[2] = {w.expA, w.expA2};
     const int64_t nb = (n + kNB - 1) / kNB;
-    const bool two = side != nullptr;
-    cudaStream_t ps = two ? side : st;
-    e = panel_step(A, n, 0, info, err, w, buf[0], bexp[0], st);
+    const bool two = cs != nullptr && cs->side != nullptr;
+    cudaStream_t side = two ? cs->side : nullptr, ps = two ? cs->side : st;
+    cudaEvent_t ev_wide = two ? cs->ev_wide : nullptr, ev_panel = two ? cs->ev_panel : nullptr;
+    e = panel_step(A, n, 0, info, err, w, buf[0], bexp[0], st, cs);
     if (e != cudaSuccess) return e;
     for (int64_t k = 0; k + 1 < nb; ++k) {
         const int64_t k0 = k * kNB;
@@ -1042,7 +1058,7 @@ cudaError_t launch_cholesky_tc(double *A, int64_t n, int *info, int *err, void *
         e = launch_ozaki_gemm_strided(Lk, Le, rest, rest, Lk, Le, kb1, rest, S, C1, n, 1, true, err, ps);
         prof_end(slot, ps, ozaki_mma_flops(rest, kb1, S, true));
         if (e != cudaSuccess) return e;
-        e = panel_step(A, n, k0 + kNB, info, err, w, buf[(k + 1) & 1], bexp[(k + 1) & 1], ps);
+        e = panel_step(A, n, k0 + kNB, info, err, w, buf[(k + 1) & 1], bexp[(k + 1) & 1], ps, cs);
         if (e != cudaSuccess) return e;
         if (two) {
             e = cudaEventRecord(ev_panel, side);

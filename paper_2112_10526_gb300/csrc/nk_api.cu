@@ -288,6 +288,7 @@ nk_status run_solve(nk_ctx *ctx, int N, int M, int64_t Ns, const int8_t *s, cons
                     cudaStream_t st, int precision = NK_F64, bool sync_check = false) {
     const bool tc = precision == NK_MIXED;
     const int64_t Np = n_params(N, M);
+    const nk::CholStreams cs{ctx->side, ctx->aux, ctx->ev[0], ctx->ev[1], ctx->ev[2], ctx->ev[3]};
     if (host_info) host_info[0] = 0, host_info[1] = 1;
     if (host_resid) *host_resid = 0.0;
     if (solver == NK_SOLVER_CG) {
@@ -347,7 +348,7 @@ nk_status run_solve(nk_ctx *ctx, int N, int M, int64_t Ns, const int8_t *s, cons
         else
             NK_CU(nk::launch_syrk_t(w.dJ, Ns, Np, 1.0 / (double)Ns, eps, w.S, st), "chol syrk");
         if (tc)
-            NK_CU(nk::launch_cholesky_tc(w.S, Np, w.info, w.info + 1, w.tc, st, ctx->side, ctx->ev[0], ctx->ev[1]),
+            NK_CU(nk::launch_cholesky_tc(w.S, Np, w.info, w.info + 1, w.tc, st, &cs),
                   "chol factor");
         else
             NK_CU(nk::launch_cholesky(w.S, Np, w.info, st), "chol factor");
@@ -364,7 +365,7 @@ nk_status run_solve(nk_ctx *ctx, int N, int M, int64_t Ns, const int8_t *s, cons
     if (tc) {
         NK_CU(nk::launch_gram_tc(N, M, Ns, s, T, 7, w.K, w.info + 1, w.tc, st), "ss gram");
         NK_CU(nk::launch_center_gram(Ns, w.K, w.rowmean, eps, st), "ss gram");
-        NK_CU(nk::launch_cholesky_tc(w.K, Ns, w.info, w.info + 1, w.tc, st, ctx->side, ctx->ev[0], ctx->ev[1]),
+        NK_CU(nk::launch_cholesky_tc(w.K, Ns, w.info, w.info + 1, w.tc, st, &cs),
               "ss factor");
     } else {
         NK_CU(nk::launch_gram_samplespace(N, M, Ns, s, T, eps, w.K, w.rowmean, st), "ss gram");
@@ -480,15 +481,18 @@ nk_status nk_ctx_create(int32_t device, nk_ctx **out) {
     int lo_prio = 0, hi_prio = 0;
     if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, hi_prio);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev[0], cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev[1], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->aux, cudaStreamNonBlocking, hi_prio);
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&c->ev[i], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc(&c->tc_err, 256);
     if (e == cudaSuccess) e = cudaMemset(c->tc_err, 0, 256);
     if (e != cudaSuccess) {
         if (c->host_flags) cudaFreeHost(c->host_flags);
         if (c->host_vals) cudaFreeHost(c->host_vals);
         if (c->side) cudaStreamDestroy(c->side);
-        if (c->ev[0]) cudaEventDestroy(c->ev[0]);
+        if (c->aux) cudaStreamDestroy(c->aux);
+        for (int i = 0; i < 4; ++i)
+            if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+        if (c->tc_err) cudaFree(c->tc_err);
         delete c;
         return cuda_fail(e, "context resources");
     }
@@ -503,8 +507,9 @@ nk_status nk_ctx_destroy(nk_ctx *ctx) {
     if (ctx->host_flags) cudaFreeHost(ctx->host_flags);
     if (ctx->host_vals) cudaFreeHost(ctx->host_vals);
     if (ctx->side) cudaStreamDestroy(ctx->side);
-    if (ctx->ev[0]) cudaEventDestroy(ctx->ev[0]);
-    if (ctx->ev[1]) cudaEventDestroy(ctx->ev[1]);
+    if (ctx->aux) cudaStreamDestroy(ctx->aux);
+    for (int i = 0; i < 4; ++i)
+        if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
     if (ctx->tc_err) cudaFree(ctx->tc_err);
     delete ctx;
     return NK_OK;

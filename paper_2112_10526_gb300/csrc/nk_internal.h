@@ -16,7 +16,8 @@ struct nk_ctx {
     int *host_flags;    // pinned: [0] done, [1] iterations, [2..3] factor status, [4] tc error
     double *host_vals;  // pinned
     cudaStream_t side;  // high-priority stream for the Cholesky look-ahead
-    cudaEvent_t ev[2];
+    cudaStream_t aux;   // high-priority stream for work beside the panel chain
+    cudaEvent_t ev[4];
     int *tc_err;        // device: sticky code of the first tensor-core time-out
     size_t plan_bytes;  // workspace counted by plan-only calls
 };
@@ -164,10 +165,15 @@ cudaError_t launch_ozaki_gemm(const __nv_bfloat16 *Asl, const int *expA, int64_t
                               const __nv_bfloat16 *Bsl, const int *expB, int64_t cols, int S, double *C,
                               int64_t ldc, int mode, bool lower, int *err, cudaStream_t st);
 size_t tc_chol_ws_bytes(int64_t n);
-// side / events: a second stream for the panel look-ahead (null: one stream).
+// Streams of the panel look-ahead: `side` carries the panel chain, `aux`
+// the slicing of a panel beside its diagonal block; the events join them.
+struct CholStreams {
+    cudaStream_t side, aux;
+    cudaEvent_t ev_wide, ev_panel, ev_fork, ev_join;
+};
+// cs null: everything on st.
 cudaError_t launch_cholesky_tc(double *A, int64_t n, int *info, int *err, void *ws, cudaStream_t st,
-                               cudaStream_t side = nullptr, cudaEvent_t ev_wide = nullptr,
-                               cudaEvent_t ev_panel = nullptr);
+                               const CholStreams *cs = nullptr);
 // Forward and backward solves with the factor of launch_cholesky_tc (one
 // cooperative launch each); err receives 6 / 7 if a block-row wait timed out.
 cudaError_t launch_cholesky_solve_tc(const double *L, int64_t n, const void *ws, double *b, int *err,
