@@ -312,6 +312,30 @@ __device__ __forceinline__ void slice_value(double x, int e, int SB, __nv_bfloat
     }
 }
 
+// slice_value for two neighbouring values of one row, written as BF16 pairs
+// (4-byte stores, so that a warp writes whole 128-byte lines per plane).
+__device__ __forceinline__ void slice_pair(double x0, double x1, int e, int SB, __nv_bfloat162 *out,
+                                           int64_t plane2) {
+    unsigned long long y[2] = {0ULL, 0ULL};
+    bool neg[2];
+    const double x[2] = {x0, x1};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        int b;
+        unsigned long long m;
+        split_bits(x[h], b, m, neg[h]);
+        if (m) {
+            const int sh = b - 1075 + 8 * SB - e;
+            y[h] = sh >= 0 ? (m << sh) : (sh <= -64 ? 0ULL : m >> (-sh));
+        }
+    }
+    for (int t = 0; t < SB; ++t) {
+        const int d0 = (int)((y[0] >> (8 * (SB - 1 - t))) & 0xFFULL), d1 = (int)((y[1] >> (8 * (SB - 1 - t))) & 0xFFULL);
+        out[(size_t)t * plane2] = __halves2bfloat162(__int2bfloat16_rn(neg[0] ? -d0 : d0),
+                                                     __int2bfloat16_rn(neg[1] ? -d1 : d1));
+    }
+}
+
 // Rows of a row-major FP64 matrix (row r, column k: X[r * ldx + k] for k < K;
 // with augment, column K holds aug[r] and the operand has K + 1 columns) ->
 // SB slices [SB][rows][ld] with one exponent per row.  One block per row.
@@ -372,7 +396,9 @@ __global__ void k_tg_colexp(const double *__restrict__ T, const int *__restrict_
     const int64_t k0 = (int64_t)blockIdx.y * 256;
     int ex = -100000;
     if (j <= M) {
-        for (int64_t k = k0 + threadIdx.y; k < k0 + 256 && k < Ns; k += blockDim.y) {
+        const int64_t kend = k0 + 256 < Ns ? k0 + 256 : Ns;
+#pragma unroll 4
+        for (int64_t k = k0 + threadIdx.y; k < kend; k += blockDim.y) {  // loads of 4 rows in flight
             const int et = j < M ? exp_of(T[(size_t)k * M + j]) : 1, eg = ge[k];
             if (et != -100000 && eg != -100000) ex = max(ex, et + eg);
         }
@@ -386,13 +412,14 @@ __global__ void k_tg_colexp(const double *__restrict__ T, const int *__restrict_
     }
 }
 
-// (T' o g')^T sliced: out [SB][M+1][ld], row j, column k, through 32 x 32 tiles.
+// (T' o g')^T sliced: out [SB][M+1][ld], row j, column k, through tiles of
+// 64 k x 32 j (ld is even: each lane writes a BF16 pair per plane).
 __global__ void k_tg_slice(const double *__restrict__ T, const double *__restrict__ gp, int64_t Ns, int M, int SB,
                            int64_t ld, const int *__restrict__ expo, __nv_bfloat16 *__restrict__ out) {
-    __shared__ double tile[32][33];
-    const int64_t k0 = (int64_t)blockIdx.x * 32;
+    __shared__ double tile[64][33];
+    const int64_t k0 = (int64_t)blockIdx.x * 64;
     const int j0 = blockIdx.y * 32;
-    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    for (int r = threadIdx.y; r < 64; r += blockDim.y) {
         const int64_t k = k0 + r;
         const int j = j0 + threadIdx.x;
         double v = 0.0;
@@ -400,13 +427,14 @@ __global__ void k_tg_slice(const double *__restrict__ T, const double *__restric
         tile[r][threadIdx.x] = v;
     }
     __syncthreads();
-    const int64_t plane = (int64_t)(M + 1) * ld;
+    const int64_t plane2 = (int64_t)(M + 1) * ld / 2;
     for (int r = threadIdx.y; r < 32; r += blockDim.y) {
         const int j = j0 + r;
-        const int64_t k = k0 + threadIdx.x;
+        const int64_t k = k0 + 2 * threadIdx.x;
         if (j > M || k >= ld) continue;
         const int e = expo[j] == -100000 ? 0 : expo[j];
-        slice_value(k < Ns ? tile[threadIdx.x][r] : 0.0, e, SB, out + (size_t)j * ld + k, plane);
+        const double x0 = k < Ns ? tile[2 * threadIdx.x][r] : 0.0, x1 = k + 1 < Ns ? tile[2 * threadIdx.x + 1][r] : 0.0;
+        slice_pair(x0, x1, e, SB, reinterpret_cast<__nv_bfloat162 *>(out + (size_t)j * ld + k), plane2);
     }
 }
 
@@ -613,7 +641,7 @@ cudaError_t launch_vjp_tc(int N, int M, int64_t Ns, const int8_t *s, const doubl
     (k_scale_g<<<nblk(Ns, 256), 256, 0, st>>>(Ns, g, scale, shift, gp, ge), nk::note_launch());
     (k_tg_colexp<<<dim3(nblk(M + 1, 32), nblk(Ns, 256)), dim3(32, 8), 0, st>>>(T, ge, Ns, M, eg),
      nk::note_launch());
-    (k_tg_slice<<<dim3(nblk(ld, 32), nblk(M + 1, 32)), tb, 0, st>>>(T, gp, Ns, M, SB, ld, eg, Gs),
+    (k_tg_slice<<<dim3(nblk(ld, 64), nblk(M + 1, 32)), tb, 0, st>>>(T, gp, Ns, M, SB, ld, eg, Gs),
      nk::note_launch());
     // split the long K = Ns range until the grid covers the SMs twice
     // (every split keeps >= 4 chunks; each split's FP32 levels stay exact)
