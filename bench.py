@@ -424,6 +424,8 @@ def run_ours(args, rank, world):
                    "l2": l2_text(w["solver"], Ns, w["M"], w["N"] + w["M"] + w["M"] * w["N"])},
         "samples_sweeps_per_s": world * K * Ns / (ms_plain / 1e3),
         "proposals_per_s": world * K * Ns * w["N"] / (ms_plain / 1e3),
+        # local-energy evaluations per second of the E_loc kernels alone (CUDA events)
+        "eloc_evals_per_s": (world * K * Ns / (prof["eloc"][0] / 1e3)) if prof.get("eloc", (0,))[0] > 0 else None,
         "energy": stats["energy"], "energy_error": stats["error"], "acceptance": stats["acceptance"],
         "roofline": rf,
         "rooflines_by_class": by_class,

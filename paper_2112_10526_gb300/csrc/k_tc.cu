@@ -55,13 +55,10 @@ constexpr int kABytes = kTileM * kTileK * 2;  // one slice of the A tile
 // from the top, of the fixed-point magnitude floor(|a| 2^(8S - e_r)), with the
 // sign of a: exactly the digits of repeated multiply-by-256-and-truncate,
 // taken from the FP64 bit pattern with integer shifts only.
-__global__ void k_slice_rows(const double *__restrict__ A, int64_t lda, int64_t rows, int kcols, int S,
-                             __nv_bfloat16 *__restrict__ out, int *__restrict__ expo) {
-    const int lane = threadIdx.x & 31;
-    const int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (r >= rows) return;
-    const double x0 = lane < kcols ? A[(size_t)r * lda + lane] : 0.0;
-    const double x1 = lane + 32 < kcols ? A[(size_t)r * lda + lane + 32] : 0.0;
+// The warp's row r, with lane l holding columns l (x0) and l + 32 (x1), as S
+// slices out[q][r][0..63] (plane stride `rows` rows) and the row exponent.
+__device__ __forceinline__ void slice_row_warp(double x0, double x1, int lane, int64_t rows, int64_t r, int S,
+                                               __nv_bfloat16 *__restrict__ out, int *__restrict__ expo) {
     int b0, b1;
     unsigned long long m0, m1;
     bool n0, n1;
@@ -91,6 +88,16 @@ __global__ void k_slice_rows(const double *__restrict__ A, int64_t lda, int64_t 
         o[lane + 32] = __int2bfloat16_rn(n1 ? -d1 : d1);
     }
     if (lane == 0) expo[r] = e;
+}
+
+__global__ void k_slice_rows(const double *__restrict__ A, int64_t lda, int64_t rows, int kcols, int S,
+                             __nv_bfloat16 *__restrict__ out, int *__restrict__ expo) {
+    const int lane = threadIdx.x & 31;
+    const int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (r >= rows) return;
+    const double x0 = lane < kcols ? A[(size_t)r * lda + lane] : 0.0;
+    const double x1 = lane + 32 < kcols ? A[(size_t)r * lda + lane + 32] : 0.0;
+    slice_row_warp(x0, x1, lane, rows, r, S, out, expo);
 }
 
 // Columns p of rows r0 .. r0 + kr - 1 (kr <= 64) of X [.][ldx] -> S BF16
@@ -571,50 +578,52 @@ __global__ void __launch_bounds__(kPotrfThreads) k_potrf64(double *__restrict__ 
 }
 
 // Linv = L^-1 for the factored kb x kb diagonal block at (k, k): a lower-
-// triangular 64 x 64 block, zero above the diagonal and beyond kb.  With
-// L = D U (D = diag(l_ii), U unit lower), column j of L^-1 is U^-1 e_j / l_jj.
-// One warp per column (16 CTAs of 4 warps, one per SM sub-partition, each CTA
-// staging only the rows and columns its columns read, rows divided by their
-// diagonal on load): lanes hold rows lane and lane + 32, and the forward
-// substitution takes per step one shuffle of y_i and one FMA per lane (two
-// while rows below 32 are still open).  A dependent FP64 operation costs
-// about as much as a shuffle on this part, so the unit diagonal keeps the
-// division off the chain.
+// triangular 64 x 64 block, zero above the diagonal and beyond kb, written
+// row by row together with its S slices (out [S][kb][64], exponents expo[kb];
+// the B operand of the panel solve).  Row i of L^-1 solves x^T L = e_i^T;
+// with U'_rc = l_rc / l_cc (columns divided by their diagonal on load) it is
+// x_i = 1 / l_ii and x_c = -sum_{r > c} x_r U'_rc, taken by backward
+// substitution: one warp per row (16 CTAs of 4 warps, one per SM
+// sub-partition, each staging only the rows its rows read), lanes holding
+// columns lane and lane + 32, one shuffle and one FMA per step.  A dependent
+// FP64 operation costs about as much as a shuffle on this part, so the unit
+// diagonal keeps the division off the chain.  The warp then slices its row
+// as k_slice_rows would.
 constexpr int kTrtriWarps = 4;
 
 __global__ void __launch_bounds__(32 * kTrtriWarps) k_trtri64(const double *__restrict__ A, int64_t n, int64_t k,
-                                                              int kb, double *__restrict__ Linv) {
+                                                              int kb, double *__restrict__ Linv, int S,
+                                                              __nv_bfloat16 *__restrict__ out, int *__restrict__ expo) {
     __shared__ double U[kNB * kLd];
     __shared__ double rd[kNB];
     const int t = threadIdx.x, lane = t & 31;
-    const int j = blockIdx.x * kTrtriWarps + (t >> 5);
-    // column j of the inverse reads only rows and columns j .. 63 of L
-    const int j0 = blockIdx.x * kTrtriWarps, w0 = kNB - j0;
-    for (int i = j0 + t; i < kNB; i += 32 * kTrtriWarps) rd[i] = i < kb ? 1.0 / A[(size_t)(k + i) * n + k + i] : 1.0;
+    const int i = blockIdx.x * kTrtriWarps + (t >> 5);
+    // row i of the inverse reads only rows 0 .. i of L
+    const int rows = blockIdx.x * kTrtriWarps + kTrtriWarps;  // rows staged: 0 .. rows - 1
+    for (int c = t; c < kNB; c += 32 * kTrtriWarps) rd[c] = c < kb ? 1.0 / A[(size_t)(k + c) * n + k + c] : 1.0;
     __syncthreads();
-    for (int e = t; e < w0 * w0; e += 32 * kTrtriWarps) {
-        const int r = j0 + e / w0, c = j0 + e % w0;
-        U[r * kLd + c] = (r < kb && c < r) ? A[(size_t)(k + r) * n + k + c] * rd[r] : 0.0;
+    for (int e = t; e < rows * kNB; e += 32 * kTrtriWarps) {
+        const int r = e / kNB, c = e % kNB;
+        U[r * kLd + c] = (r < kb && c < r) ? A[(size_t)(k + r) * n + k + c] * rd[c] : 0.0;
     }
     __syncthreads();
-    // y = U^-1 e_j: y_i is final when step i begins; then row r -= u_ri y_i
-    double acc0 = lane == j ? 1.0 : 0.0, acc1 = lane + 32 == j ? 1.0 : 0.0;
-    double y0 = 0.0, y1 = 0.0;
-    int i = j;
-    for (; i < 32; ++i) {  // warp-uniform bounds; rows above j0 were not staged and stay 0
-        const double yi = __shfl_sync(0xffffffffu, acc0, i);
-        if (lane == i) y0 = yi;
-        acc0 = fma(lane >= j0 ? -U[lane * kLd + i] : 0.0, yi, acc0);
-        acc1 = fma(-U[(lane + 32) * kLd + i], yi, acc1);
+    double x0 = 0.0, x1 = 0.0;  // columns lane, lane + 32 of row i
+    if (i < kb) {
+        // acc holds -sum_{r > c} x_r U'_rc over the rows finished so far; x_c is
+        // final once row c + 1 has been applied
+        double acc0 = lane == i ? rd[i] : 0.0, acc1 = lane + 32 == i ? rd[i] : 0.0;
+        for (int r = i; r >= 1; --r) {  // warp-uniform bounds
+            const double xr = r < 32 ? __shfl_sync(0xffffffffu, acc0, r) : __shfl_sync(0xffffffffu, acc1, r - 32);
+            // columns c < r take -x_r U'_rc (U' is zero on and above the diagonal)
+            acc0 = fma(-xr, U[r * kLd + lane], acc0);
+            if (r > 32) acc1 = fma(-xr, U[r * kLd + lane + 32], acc1);
+        }
+        x0 = acc0;
+        x1 = acc1;
+        slice_row_warp(x0, x1, lane, kb, i, S, out, expo);
     }
-    for (; i < kNB; ++i) {
-        const double yi = __shfl_sync(0xffffffffu, acc1, i - 32);
-        if (lane == i - 32) y1 = yi;
-        acc1 = fma(lane + 32 >= j0 ? -U[(lane + 32) * kLd + i] : 0.0, yi, acc1);
-    }
-    const double s = j < kb ? rd[j] : 0.0;
-    Linv[(size_t)lane * kNB + j] = lane < kb ? y0 * s : 0.0;
-    Linv[(size_t)(lane + 32) * kNB + j] = lane + 32 < kb ? y1 * s : 0.0;
+    Linv[(size_t)i * kNB + lane] = x0;
+    Linv[(size_t)i * kNB + lane + 32] = x1;
 }
 
 // ---------------------------------------------- triangular solves with L ---
@@ -1000,12 +1009,11 @@ cudaError_t panel_step(double *A, int64_t n, int64_t k0, int *info, int *err, Tc
     // as the panel, the tensor-core panel product with the trailing updates
     int slot = prof_begin(NK_PROF_CHOL_PANEL, st);
     (k_potrf64<<<1, kPotrfThreads, 0, st>>>(A, n, k0, kb, info), nk::note_launch());
-    (k_trtri64<<<kNB / kTrtriWarps, 32 * kTrtriWarps, 0, st>>>(A, n, k0, kb, Linv), nk::note_launch());
-    if (rest > 0) {
-        e = launch_slice_rows(Linv, kNB, kb, kb, S, w.Bsl, w.expB, st);
-        if (e == cudaSuccess) e = fork ? cudaStreamWaitEvent(st, cs->ev_join, 0)
-                                       : launch_slice_rows(panel, n, rest, kb, S, Lsl, Lexp, st);
-    }
+    // the inverse and its slices (the B operand of the panel solve)
+    (k_trtri64<<<kNB / kTrtriWarps, 32 * kTrtriWarps, 0, st>>>(A, n, k0, kb, Linv, S, w.Bsl, w.expB),
+     nk::note_launch());
+    if (rest > 0)
+        e = fork ? cudaStreamWaitEvent(st, cs->ev_join, 0) : launch_slice_rows(panel, n, rest, kb, S, Lsl, Lexp, st);
     prof_end(slot, st, 2.0 * (double)kb * kb * kb / 3.0);
     if (rest > 0 && e == cudaSuccess) {
         slot = prof_begin(NK_PROF_CHOL_UPDATE, st);
