@@ -30,7 +30,10 @@ def ctx():
 
 # (rows, cols, k, mode, lower); mode 0 '=', 1 '-=', 2 '+='
 GEMM_CASES = [(300, 130, 64, 0, False), (128, 64, 64, 0, False), (1, 1, 1, 0, False), (257, 65, 37, 1, False),
-              (400, 400, 64, 1, True), (129, 200, 50, 2, True), (64, 300, 64, 0, False)]
+              (400, 400, 64, 1, True), (129, 200, 50, 2, True), (64, 300, 64, 0, False),
+              # enough tiles per SM for strips of 2, 4 and 8 tiles, and more
+              # than 32 tile rows (two rounds of the strip search)
+              (2000, 2000, 64, 1, True), (4200, 640, 64, 2, False), (5000, 5000, 64, 1, True)]
 
 
 @pytest.mark.parametrize("rows,cols,k,mode,lower", GEMM_CASES)
@@ -184,3 +187,36 @@ def test_samplespace_solve_full_size(ctx):
     assert res["f64"] < 1e-9, res
     assert res["mixed"] < 1e-9, res
     assert vec_rel_err(out["mixed"], out["f64"]) < 1e-8
+
+
+def test_prof_trace_orders_the_bracketed_segments(ctx):
+    """nk_prof_trace: every bracketed launch of an NK_MIXED sample-space solve,
+    in enqueue order, with start <= end on one clock from the first start;
+    the Cholesky's classes are there and the trace agrees with nk_prof_read."""
+    N, M, Ns = 16, 16, 1024
+    p = I.rbm_params(N, M, 4, 0.3)
+    s = I.random_configs(Ns, N, 6)
+    Np = N + M + M * N
+    F = np.random.default_rng(2).normal(size=Np) * 0.1
+    d = torch.empty(Np, dtype=torch.float64, device=dev())
+    nk.nk_prof_enable(True)
+    try:
+        nk.nk_sr_solve(ctx, cu(p), N, M, cu(s), cu(F), d, solver="cholesky_samplespace", diag_shift=0.01,
+                       precision="mixed")
+        torch.cuda.synchronize()
+        tr = nk.nk_prof_trace()
+        per_class = {c: nk.nk_prof_read(c) for c in nk.PROF_CLASSES}
+    finally:
+        nk.nk_prof_enable(False)
+    assert tr and tr[0][1] == 0.0
+    assert all(0.0 <= t0 <= t1 for _, t0, t1 in tr)
+    names = {c for c, _, _ in tr}
+    assert {"gram", "chol_update", "chol_panel", "trsv"} <= names
+    for c, (ms, n, _) in per_class.items():
+        seg = [(t0, t1) for k, t0, t1 in tr if k == c]
+        assert n == len(seg)
+        assert ms == pytest.approx(sum(t1 - t0 for t0, t1 in seg), rel=1e-3, abs=1e-3)
+    # a NULL count pointer and a short buffer are argument errors / truncation
+    import ctypes
+    assert nk.lib().nk_prof_trace(0, None, None, None, None) == -1
+    assert nk.lib().nk_prof_trace(1, None, None, None, ctypes.byref(ctypes.c_int32())) == -1
