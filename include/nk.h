@@ -103,8 +103,11 @@ int32_t nk_version(void);
 /*
  * Sticky status of the context's tensor-core products (NK_MIXED paths):
  * waits for the context's work on `stream` and returns in *code 0, or the
- * code of the first tensor-core wait that timed out since the last call
- * (1-5; the results of that call are invalid).  Resets the word.
+ * code of the last bounded wait that timed out since the last call (the
+ * results of that call are invalid): 3-5 the S-GEMM (producer, MMA issuer,
+ * epilogue), 6 / 7 the forward / backward triangular solve, 12-16 the
+ * FP64-accurate product (producer, A slices, B slices, accumulator buffer,
+ * epilogue).  Resets the word.
  */
 nk_status nk_ctx_error(nk_ctx *ctx, int32_t *code /* host */, void *stream);
 
