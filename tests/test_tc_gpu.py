@@ -220,3 +220,42 @@ def test_prof_trace_orders_the_bracketed_segments(ctx):
     import ctypes
     assert nk.lib().nk_prof_trace(0, None, None, None, None) == -1
     assert nk.lib().nk_prof_trace(1, None, None, None, ctypes.byref(ctypes.c_int32())) == -1
+
+
+def test_mixed_jacobian_products_full_size_sampled(ctx):
+    """NK_MIXED J v and J^T g at the 20 x 20 TFIM workload's full size (Ns =
+    16384, N = 400, M = 1600, Np = 642 000), checked on sampled outputs the
+    oracle computes one by one: 64 entries of J v from the Jacobian rows of
+    their samples, and 64 parameters of J^T g (a, b and W entries) as sums
+    over all samples of s, tanh(theta) and their products."""
+    N, M, Ns = 400, 1600, 16384
+    p = I.rbm_params(N, M, 3)
+    s = I.random_configs(Ns, N, 3)
+    Np = N + M + M * N
+    rng = np.random.default_rng(7)
+    pd, sd = cu(p), cu(s)
+    v = rng.normal(size=Np)
+    w = torch.empty(Ns, dtype=torch.float64, device=dev())
+    nk.nk_jvp(ctx, pd, N, M, sd, cu(v), w, precision="mixed")
+    rows = rng.choice(Ns, 64, replace=False)
+    ref_w = oracle.jacobian(p, N, M, s[rows]) @ v
+    assert vec_rel_err(w.cpu().numpy()[rows], ref_w) < 1e-8
+    g = rng.normal(size=Ns)
+    out = torch.empty(Np, dtype=torch.float64, device=dev())
+    nk.nk_vjp(ctx, pd, N, M, sd, cu(g), out, precision="mixed")
+    a, b, W = p[:N], p[N:N + M], p[N + M:].reshape(M, N)
+    sf = s.astype(np.float64)
+    t = np.tanh(b[None, :] + sf @ W.T)
+    idx = np.concatenate([rng.choice(N, 8, replace=False), N + rng.choice(M, 8, replace=False),
+                          N + M + rng.choice(M * N, 48, replace=False)])
+    ref = np.empty(len(idx))
+    for n, q in enumerate(idx):
+        if q < N:
+            ref[n] = sf[:, q] @ g
+        elif q < N + M:
+            ref[n] = t[:, q - N] @ g
+        else:
+            j, i = divmod(q - N - M, N)
+            ref[n] = (t[:, j] * sf[:, i]) @ g
+    assert vec_rel_err(out.cpu().numpy()[idx], ref) < 1e-8
+    assert nk.nk_ctx_error(ctx) == 0
