@@ -404,3 +404,38 @@ def test_metropolis_full_size_local_rule_sampled_chains(ctx, prec):
     np.testing.assert_array_equal(st.cpu().numpy()[:K], ref["state"])
     assert rel_err(lp.cpu().numpy()[:K], ref["logpsi"]) < (1e-10 if prec == "f64" else 1e-4)
     np.testing.assert_array_equal(nacc.cpu().numpy(), (dec.cpu().numpy() == 1).sum(axis=(1, 2)))
+
+
+@pytest.mark.parametrize("prec", ["f64", "mixed"])
+def test_metropolis_full_size_24x24_sampled_chains(ctx, prec):
+    """The sweep configuration of the 24 x 24 Heisenberg workload (8192
+    exchange chains at S_z = 0, N = 576, M = 4608, sigma = 0.01; one
+    discarded and one sampled sweep) run in full on the GPU; the first 4
+    chains are replayed by the oracle with forced-follow."""
+    N, M, C, nd, ns = 576, 4608, 8192, 1, 1
+    p = I.rbm_params(N, M, 5)
+    edges = I.square_edges(24)
+    s0 = oracle.chain_init(N, C, "exchange", 5, 0)
+    st = cu(s0)
+    samples = torch.empty((C, ns, N), dtype=torch.int8, device=dev())
+    lp = torch.empty((C, ns), dtype=torch.float64, device=dev())
+    nacc = torch.zeros(C, dtype=torch.int64, device=dev())
+    dec = torch.empty((C, nd + ns, N), dtype=torch.uint8, device=dev())
+    nk.nk_metropolis_sweep(ctx, cu(p), N, M, "exchange", cu(edges), st, 0, nd, ns, 5, 0, samples, lp, nacc,
+                           dec, precision=prec)
+    K = 4
+    g_dec = dec.cpu().numpy()[:K]
+    ref = oracle.metropolis(p, N, M, "exchange", edges, s0[:K], 0, nd, ns, 5, 0, forced=g_dec)
+    mism = ref["decisions"] != g_dec
+    if prec == "f64":
+        allowed = ref["margin"] < 1e-9
+    else:
+        lu = _lnu(5, 0, K, N, nd + ns, 0)
+        two_d = lu + np.where(ref["decisions"] == 1, 1, -1) * ref["margin"]
+        allowed = ref["margin"] < 1e-4 * np.maximum(1.0, np.abs(two_d))
+    assert not (mism & ~allowed).any()
+    np.testing.assert_array_equal(samples.cpu().numpy()[:K], ref["samples"])
+    np.testing.assert_array_equal(st.cpu().numpy()[:K], ref["state"])
+    assert rel_err(lp.cpu().numpy()[:K], ref["logpsi"]) < (1e-10 if prec == "f64" else 1e-4)
+    assert (st.cpu().numpy().astype(np.int64).sum(axis=1) == 0).all()
+    np.testing.assert_array_equal(nacc.cpu().numpy(), (dec.cpu().numpy() == 1).sum(axis=(1, 2)))
