@@ -259,3 +259,49 @@ def test_mixed_jacobian_products_full_size_sampled(ctx):
             ref[n] = (t[:, j] * sf[:, i]) @ g
     assert vec_rel_err(out.cpu().numpy()[idx], ref) < 1e-8
     assert nk.nk_ctx_error(ctx) == 0
+
+
+def test_mixed_jacobian_products_24x24_full_size_sampled(ctx):
+    """NK_MIXED J v and J^T g at the 24 x 24 Heisenberg workload's full size
+    (Ns = 65536, N = 576, M = 4608, Np = 2 659 392), on sampled outputs
+    computed one by one from the definitions: (J v)_k = s_k.v_a +
+    t_k.v_b + t_k.(V_W s_k) for 48 samples k, and (J^T g)_q for 48
+    parameters q, each a sum over all samples that needs tanh(theta) of one
+    hidden unit only."""
+    N, M, Ns = 576, 4608, 65536
+    p = I.rbm_params(N, M, 5)
+    s = I.random_configs(Ns, N, 5, sz0=True)
+    Np = N + M + M * N
+    rng = np.random.default_rng(11)
+    pd, sd = cu(p), cu(s)
+    a, b, W = p[:N], p[N:N + M], p[N + M:].reshape(M, N)
+    v = rng.normal(size=Np)
+    va, vb, VW = v[:N], v[N:N + M], v[N + M:].reshape(M, N)
+    w = torch.empty(Ns, dtype=torch.float64, device=dev())
+    nk.nk_jvp(ctx, pd, N, M, sd, cu(v), w, precision="mixed")
+    rows = rng.choice(Ns, 48, replace=False)
+    ref_w = np.empty(len(rows))
+    for n, k in enumerate(rows):
+        sk = s[k].astype(np.float64)
+        tk = np.tanh(b + W @ sk)
+        ref_w[n] = sk @ va + tk @ vb + tk @ (VW @ sk)
+    assert vec_rel_err(w.cpu().numpy()[rows], ref_w) < 1e-8
+    g = rng.normal(size=Ns)
+    out = torch.empty(Np, dtype=torch.float64, device=dev())
+    nk.nk_vjp(ctx, pd, N, M, sd, cu(g), out, precision="mixed")
+    sf = s.astype(np.float64)
+    units = rng.choice(M, 8, replace=False)
+    t = {int(j): np.tanh(b[j] + sf @ W[j]) for j in units}
+    idx = [int(i) for i in rng.choice(N, 8, replace=False)] + [N + int(j) for j in units]
+    idx += [N + M + int(j) * N + int(i) for j in units for i in rng.choice(N, 4, replace=False)]
+    ref = np.empty(len(idx))
+    for n, q in enumerate(idx):
+        if q < N:
+            ref[n] = sf[:, q] @ g
+        elif q < N + M:
+            ref[n] = t[q - N] @ g
+        else:
+            j, i = divmod(q - N - M, N)
+            ref[n] = (t[j] * sf[:, i]) @ g
+    assert vec_rel_err(out.cpu().numpy()[idx], ref) < 1e-8
+    assert nk.nk_ctx_error(ctx) == 0
