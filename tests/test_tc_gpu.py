@@ -305,3 +305,42 @@ def test_mixed_jacobian_products_24x24_full_size_sampled(ctx):
             ref[n] = (t[j] * sf[:, i]) @ g
     assert vec_rel_err(out.cpu().numpy()[idx], ref) < 1e-8
     assert nk.nk_ctx_error(ctx) == 0
+
+
+def test_mixed_cg_solve_full_size_sampled_residual(ctx):
+    """The NK_MIXED CG solve of (S + eps I) delta = F at the 20 x 20 TFIM
+    workload's full size (Ns = 16384, Np = 642 000, on-the-fly QGT, 4-slice
+    products), checked by the residual on 64 sampled components computed from
+    the definitions: w = J delta over all samples (Delta w centred), then
+    (S delta)_q = (1/Ns) sum_k O_kq Delta w_k for the sampled q."""
+    N, M, Ns, eps = 400, 1600, 16384, 0.01
+    p = I.rbm_params(N, M, 3)
+    s = I.random_configs(Ns, N, 3)
+    Np = N + M + M * N
+    rng = np.random.default_rng(13)
+    F = rng.normal(size=Np) * 0.1
+    d = torch.empty(Np, dtype=torch.float64, device=dev())
+    info = nk.nk_sr_solve(ctx, cu(p), N, M, cu(s), cu(F), d, solver="cg", diag_shift=eps, cg_tol=1e-9,
+                          cg_maxiter=3000, precision="mixed")
+    assert info["converged"]
+    delta = d.cpu().numpy()
+    a, b, W = p[:N], p[N:N + M], p[N + M:].reshape(M, N)
+    da, db, DW = delta[:N], delta[N:N + M], delta[N + M:].reshape(M, N)
+    sf = s.astype(np.float64)
+    t = np.tanh(b[None, :] + sf @ W.T)
+    w = sf @ da + t @ db + np.einsum("kj,kj->k", t, sf @ DW.T)
+    dw = w - w.mean()
+    idx = np.concatenate([rng.choice(N, 8, replace=False), N + rng.choice(M, 8, replace=False),
+                          N + M + rng.choice(M * N, 48, replace=False)])
+    r = np.empty(len(idx))
+    for n, q in enumerate(idx):
+        if q < N:
+            col = sf[:, q]
+        elif q < N + M:
+            col = t[:, q - N]
+        else:
+            j, i = divmod(q - N - M, N)
+            col = t[:, j] * sf[:, i]
+        r[n] = col @ dw / Ns + eps * delta[q] - F[q]
+    # the CG stops at ||r|| <= 1e-9 ||F||; the 4-slice products add about 2^-32
+    assert np.abs(r).max() <= 1e-8 * np.linalg.norm(F)
