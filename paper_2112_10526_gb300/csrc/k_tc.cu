@@ -640,6 +640,8 @@ __global__ void __launch_bounds__(32 * kTrtriWarps) k_trtri64(const double *__re
 // order, so with all CTAs resident (cooperative launch) every wait ends; each
 // wait is still bounded by the global timer and records error 6 (forward) or
 // 7 (backward), after which the CTA finishes its row without waiting again.
+// (A right-hand side holding a NaN with exactly the sentinel's payload would
+// read as unsolved and end in that time-out error rather than in a NaN.)
 constexpr int kTrsvThreads = 256;
 constexpr unsigned long long kSolveSentinel = 0xFFFFFFFFFFFFFFFFULL;
 
