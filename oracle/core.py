@@ -7,7 +7,9 @@ Conventions shared with the product library (by specification, not by code):
   * parameters theta = [a (N); b (M); W (M x N row-major)], float64;
   * configurations int8 in {-1, +1}, row-major [batch, N];
   * Hamiltonian dict: {"kind": "tfim"|"heis", "J": float, "h": float,
-    "marshall": bool, "edges": int32 [E, 2]};
+    "marshall": bool, "edges": int32 [E, 2]}, optionally with "J2": float
+    and "n_edges2": int, the last n_edges2 edges being the next-nearest
+    neighbours of coupling J2 (Eq. eq: j1 j2 heisenberg);
   * sampler rule: "local" (single-spin flip) or "exchange" (edge swap at
     fixed magnetisation).
 """
@@ -45,7 +47,7 @@ def _load():
     P = ctypes.c_void_p
     i32, i64, u64, u32, f64 = ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double
     lib.oc_logpsi.argtypes = [i32, i32, P, P, i64, P]
-    lib.oc_local_energy.argtypes = [i32, i32, P, i32, f64, f64, i32, i32, P, P, i64, P]
+    lib.oc_local_energy.argtypes = [i32, i32, P, i32, f64, f64, f64, i32, i32, i32, P, P, i64, P]
     lib.oc_jacobian.argtypes = [i32, i32, P, P, i64, P]
     lib.oc_philox4x64_10.argtypes = [P, P, P]
     lib.oc_chain_init.argtypes = [i32, i32, i32, u64, u32, P]
@@ -101,10 +103,12 @@ def local_energy(params, N, M, ham, s):
     s = _cfg(s, N)
     out = np.empty(s.shape[0], dtype=np.float64)
     edges = np.ascontiguousarray(ham["edges"], dtype=np.int32).reshape(-1, 2)
+    E2 = int(ham.get("n_edges2", 0))
+    assert 0 <= E2 <= edges.shape[0]
     pa = _par(params)
-    lib.oc_local_energy(N, M, _p(pa), KIND[ham["kind"]], float(ham["J"]), float(ham.get("h", 0.0)),
-                        int(bool(ham.get("marshall", False))), edges.shape[0], _p(edges), _p(s),
-                        s.shape[0], _p(out))
+    lib.oc_local_energy(N, M, _p(pa), KIND[ham["kind"]], float(ham["J"]), float(ham.get("J2", 0.0)),
+                        float(ham.get("h", 0.0)), int(bool(ham.get("marshall", False))), edges.shape[0], E2,
+                        _p(edges), _p(s), s.shape[0], _p(out))
     return out
 
 

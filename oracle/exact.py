@@ -64,28 +64,31 @@ def two_sublattices(N, edges):
 
 def hamiltonian(N, ham):
     """Sparse H (real, CSR) of the transverse-field Ising model
-    H = J sum_<ik> sz_i sz_k - h sum_i sx_i  (Eq. eq:tf-ising-hamiltonian) or
-    the Heisenberg model H = J sum_<ik> sigma_i . sigma_k  (Eq. eq: j1 j2
-    heisenberg, J2 = 0).  With ham["marshall"], the Heisenberg H is conjugated
-    by U = prod_{i in A} sz_i for a two-colouring A/B of the lattice."""
+    H = sum_e J_e sz_i sz_k - h sum_i sx_i  (Eq. eq:tf-ising-hamiltonian) or
+    the Heisenberg model H = sum_e J_e sigma_i . sigma_k  (Eq. eq: j1 j2
+    heisenberg), J_e = J on the nearest-neighbour edges and J2 on the last
+    ham["n_edges2"] edges (next-nearest neighbours).  With ham["marshall"],
+    the Heisenberg H is conjugated by U = prod_{i in A} sz_i for the
+    two-colouring A/B of the nearest-neighbour graph."""
     edges = np.asarray(ham["edges"]).reshape(-1, 2)
-    J = float(ham["J"])
+    E1 = edges.shape[0] - int(ham.get("n_edges2", 0))
+    coupling = [float(ham["J"]) if q < E1 else float(ham.get("J2", 0.0)) for q in range(edges.shape[0])]
     dim = 2 ** N
     H = sp.csr_matrix((dim, dim), dtype=np.complex128)
     sz = [site_op(_SZ, i, N) for i in range(N)]
     if ham["kind"] == "tfim":
         h = float(ham["h"])
-        for i, k in edges:
-            H = H + J * (sz[i] @ sz[k])
+        for (i, k), Je in zip(edges, coupling):
+            H = H + Je * (sz[i] @ sz[k])
         for i in range(N):
             H = H - h * site_op(_SX, i, N)
     else:
         sx = [site_op(_SX, i, N) for i in range(N)]
         sy = [site_op(_SY, i, N) for i in range(N)]
-        for i, k in edges:
-            H = H + J * (sx[i] @ sx[k] + sy[i] @ sy[k] + sz[i] @ sz[k])
+        for (i, k), Je in zip(edges, coupling):
+            H = H + Je * (sx[i] @ sx[k] + sy[i] @ sy[k] + sz[i] @ sz[k])
         if ham.get("marshall", False):
-            col = two_sublattices(N, edges)
+            col = two_sublattices(N, edges[:E1])
             U = sp.identity(dim, format="csr", dtype=np.complex128)
             for i in range(N):
                 if col[i] == 0:

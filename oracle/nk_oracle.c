@@ -93,30 +93,41 @@ static double oc_log_ratio(int N, int M, const double *params, const int8_t *s,
  * Local energy E_loc(s) = sum_{s'} H_{s s'} psi(s')/psi(s)
  * (Sec. 3.3 "Estimating observables", Eq. "eq:local-estimator").
  *
+ * The E edges form two classes: the first E - E2 are nearest neighbours
+ * <ik> with coupling J, the last E2 next-nearest neighbours <<ik>> with
+ * coupling J2 (Sec. 7, Eq. "eq: j1 j2 heisenberg"; E2 = 0 is the plain
+ * nearest-neighbour model).  J_e below is the coupling of edge e.
+ *
  * kind 0, transverse-field Ising (Sec. 9, Eq. "eq:tf-ising-hamiltonian"):
- *     H = J sum_<ik> sz_i sz_k - h sum_i sx_i
- *     diagonal: J sum_e s_i s_k;  connected: s^(i) (site i flipped), H = -h.
- * kind 1, Heisenberg in Pauli matrices (Sec. 7, Eq. "eq: j1 j2 heisenberg"
- * with J2 = 0):
- *     H = J sum_<ik> (sx sx + sy sy + sz sz)
- *     diagonal: J sum_e s_i s_k;  connected: for each edge with s_i != s_k,
- *     s^(ik) (both flipped), H = 2J, or -2J when `marshall` is set (the
- *     sign rotation prod_{i in A} sz_i applied to a bipartite lattice whose
- *     edges all join the two sublattices).
+ *     H = sum_e J_e sz_i sz_k - h sum_i sx_i
+ *     diagonal: sum_e J_e s_i s_k;  connected: s^(i) (site i flipped), H = -h.
+ * kind 1, Heisenberg in Pauli matrices (Sec. 7, Eq. "eq: j1 j2 heisenberg"):
+ *     H = sum_e J_e (sx sx + sy sy + sz sz)
+ *     diagonal: sum_e J_e s_i s_k;  connected: for each edge with s_i != s_k,
+ *     s^(ik) (both flipped), H = 2 J_e.  With `marshall` set, the sign
+ *     rotation prod_{i in A} sz_i of a two-sublattice lattice is folded in:
+ *     it negates the element of every edge joining the two sublattices and
+ *     keeps that of every edge inside one.  The nearest-neighbour edges are
+ *     taken to join the sublattices and the next-nearest ones to stay inside
+ *     one (the square lattice and the even ring), so the elements are -2J
+ *     and +2 J2.
  * edges: int32 [E, 2].
  */
 void oc_local_energy(int N, int M, const double *params, int kind, double J,
-                     double h, int marshall, int E, const int32_t *edges,
-                     const int8_t *s, int64_t B, double *out)
+                     double J2, double h, int marshall, int E, int E2,
+                     const int32_t *edges, const int8_t *s, int64_t B,
+                     double *out)
 {
     double *theta = (double *)malloc(sizeof(double) * (size_t)(M > 0 ? M : 1));
+    const int E1 = E - E2;
     for (int64_t k = 0; k < B; ++k) {
         const int8_t *sk = s + (size_t)k * N;
         oc_hidden(N, M, params, sk, theta);
         double e = 0.0;
         for (int q = 0; q < E; ++q) {
             int i = edges[2 * q], l = edges[2 * q + 1];
-            e += J * (double)sk[i] * (double)sk[l];
+            double Je = q < E1 ? J : J2;
+            e += Je * (double)sk[i] * (double)sk[l];
         }
         if (kind == 0) {
             for (int i = 0; i < N; ++i) {
@@ -124,10 +135,10 @@ void oc_local_energy(int N, int M, const double *params, int kind, double J,
                 e += -h * exp(oc_log_ratio(N, M, params, sk, theta, site, 1));
             }
         } else {
-            double hoff = marshall ? -2.0 * J : 2.0 * J;
             for (int q = 0; q < E; ++q) {
                 int pair[2] = {edges[2 * q], edges[2 * q + 1]};
                 if (sk[pair[0]] == sk[pair[1]]) continue;
+                double hoff = q < E1 ? (marshall ? -2.0 * J : 2.0 * J) : 2.0 * J2;
                 e += hoff * exp(oc_log_ratio(N, M, params, sk, theta, pair, 2));
             }
         }

@@ -12,6 +12,11 @@ Recipe (matching the workloads of the NetKet 3 paper, Secs. 8-10):
   * periodic L x L square lattice: site i = x L + y, edges (i, right) then
     (i, down) for every site in order, right = ((x+1) mod L) L + y,
     down = x L + (y+1) mod L  (E = 2 L^2);
+  * its next-nearest neighbours (the two diagonals, Sec. 7): edges
+    (i, ((x+1) mod L) L + (y+1) mod L) then (i, ((x+1) mod L) L + (y-1) mod L)
+    for every site in order (2 L^2 more); on the chain (i, i+2 mod L);
+  * J1-J2 models list the nearest-neighbour edges first and the
+    next-nearest ones after them ("n_edges2" of them, coupling "J2");
   * random configurations: i.i.d. +-1 spins, or uniformly random S_z = 0
     configurations (a random permutation of N/2 up and N/2 down spins).
 """
@@ -42,6 +47,20 @@ def square_edges(L: int) -> np.ndarray:
     return np.array(out, dtype=np.int32).reshape(-1, 2)
 
 
+def square_nnn_edges(L: int) -> np.ndarray:
+    out = []
+    for x in range(L):
+        for y in range(L):
+            i = x * L + y
+            out.append([i, ((x + 1) % L) * L + (y + 1) % L])
+            out.append([i, ((x + 1) % L) * L + (y - 1) % L])
+    return np.array(out, dtype=np.int32).reshape(-1, 2)
+
+
+def chain_nnn_edges(L: int) -> np.ndarray:
+    return np.array([[i, (i + 2) % L] for i in range(L)], dtype=np.int32).reshape(-1, 2)
+
+
 def random_configs(B: int, N: int, seed: int, sz0: bool = False) -> np.ndarray:
     rng = np.random.default_rng(seed)
     if not sz0:
@@ -66,7 +85,19 @@ def heis_chain(L: int, J: float = 1.0, marshall: bool = True) -> dict:
     return {"kind": "heis", "J": J, "h": 0.0, "marshall": marshall, "edges": chain_edges(L)}
 
 
-# The five workloads (sizes from the paper's examples and benchmarks).
+def j1j2_square(L: int, J1: float = 1.0, J2: float = 0.5, marshall: bool = True) -> dict:
+    e2 = square_nnn_edges(L)
+    return {"kind": "heis", "J": J1, "J2": J2, "h": 0.0, "marshall": marshall,
+            "edges": np.concatenate([square_edges(L), e2]), "n_edges2": int(e2.shape[0])}
+
+
+def j1j2_chain(L: int, J1: float = 1.0, J2: float = 0.5, marshall: bool = True) -> dict:
+    e2 = chain_nnn_edges(L)
+    return {"kind": "heis", "J": J1, "J2": J2, "h": 0.0, "marshall": marshall,
+            "edges": np.concatenate([chain_edges(L), e2]), "n_edges2": int(e2.shape[0])}
+
+
+# The workloads (sizes from the paper's examples and benchmarks).
 WORKLOADS = {
     "tfim1d_n16": dict(N=16, alpha=1, ham=lambda: tfim_chain(16, 1.0, 1.0), rule="local",
                        chains=16, per_chain=64, discard=16, seed=1, diag_shift=0.01, lr=0.01,
@@ -80,6 +111,12 @@ WORKLOADS = {
     "heis2d_24x24": dict(N=576, alpha=8, ham=lambda: heis_square(24, 1.0, True), rule="exchange",
                          chains=8192, per_chain=8, discard=16, seed=5, diag_shift=0.01, lr=0.01,
                          solver="cg"),
+    # Sec. 7: J1 = 1, J2 = 0.5 on the 10 x 10 square lattice, exchange moves
+    # over both edge classes (d_max = 2), one sample per chain (n_chains =
+    # n_samples = 1024), with the RBM of heis2d_10x10 in place of the GCNN.
+    "j1j2_10x10": dict(N=100, alpha=2, ham=lambda: j1j2_square(10, 1.0, 0.5, True), rule="exchange",
+                       chains=1024, per_chain=1, discard=16, seed=6, diag_shift=0.01, lr=0.02,
+                       solver="cholesky_samplespace"),
 }
 
 

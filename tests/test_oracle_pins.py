@@ -89,6 +89,9 @@ HAMS_SMALL = [
     ("heis-chain8-plain", 8, lambda: I.heis_chain(8, 0.8, False), False),
     ("heis-4x4-marshall", 16, lambda: I.heis_square(4, 1.0, True), True),
     ("tfim-3x3-is-not-bipartite-free", 9, lambda: I.tfim_square(3, 1.0, 2.0), False),
+    ("j1j2-chain8-marshall", 8, lambda: I.j1j2_chain(8, 1.0, 0.5, True), False),
+    ("j1j2-chain10-plain", 10, lambda: I.j1j2_chain(10, 0.8, 0.35, False), False),
+    ("j1j2-4x4-marshall", 16, lambda: I.j1j2_square(4, 1.0, 0.5, True), True),
 ]
 
 
@@ -108,7 +111,10 @@ def test_local_energy_equals_hamiltonian_action(name, N, hf, sz0):
     assert np.max(np.abs(el - ref) / np.maximum(1.0, np.abs(ref))) < 1e-11
 
 
-@pytest.mark.parametrize("name,N,hf,sz0", HAMS_SMALL[:4], ids=[h[0] for h in HAMS_SMALL[:4]])
+EXPECT_CASES = HAMS_SMALL[:4] + HAMS_SMALL[6:8]
+
+
+@pytest.mark.parametrize("name,N,hf,sz0", EXPECT_CASES, ids=[h[0] for h in EXPECT_CASES])
 def test_exact_expectation_identity(name, N, hf, sz0):
     """<H> = sum_s p(s) E_loc(s) with p = |psi|^2/<psi|psi>  (Eq. eq:
     expectation value VMC), and the variational bound <H> >= E0."""
@@ -135,6 +141,10 @@ def test_zero_variance_uniform_state():
     s = I.random_configs(50, 16, 2, sz0=True)
     el = oracle.local_energy(np.zeros(16 + 3 + 48), 16, 3, ham, s)
     np.testing.assert_allclose(el, 0.9 * ham["edges"].shape[0], rtol=1e-15, atol=0)
+    # both edge classes of the J1-J2 model: E_loc = J1 E1 + J2 E2
+    ham = I.j1j2_square(4, 0.9, -0.4, False)
+    el = oracle.local_energy(np.zeros(16 + 3 + 48), 16, 3, ham, s)
+    np.testing.assert_allclose(el, 0.9 * 32 - 0.4 * 32, rtol=1e-14, atol=0)
 
 
 # ---------------------------------------------------- exact ground states ---
@@ -161,6 +171,23 @@ def test_heisenberg_small_closed_forms():
     assert abs(e4 + 8.0 * 1.3) < 1e-12
     e4m, _ = exact.ground_energy(4, I.heis_chain(4, 1.3, True))
     assert abs(e4m + 8.0 * 1.3) < 1e-12
+
+
+@pytest.mark.parametrize("L", [8, 10, 12])
+@pytest.mark.parametrize("marshall", [False, True])
+def test_majumdar_ghosh_closed_form(L, marshall):
+    """At J2 = J1 / 2 the periodic J1-J2 chain (Eq. eq: j1 j2 heisenberg in
+    one dimension, even L) has the nearest-neighbour dimer products as exact
+    ground states (Majumdar and Ghosh, J. Math. Phys. 10, 1388 (1969)), with
+    E0 = -3 J1 L / 8 in spin units, i.e. -3 J1 L / 2 with Pauli matrices.
+    The Marshall rotation of the nearest-neighbour sublattices leaves it
+    unchanged."""
+    J1 = 1.3
+    e0, _ = exact.ground_energy(L, I.j1j2_chain(L, J1, J1 / 2, marshall), sz0=True)
+    assert abs(e0 + 1.5 * J1 * L) < 1e-9 * L
+    # away from that point the dimer energy is no longer the ground energy
+    e1, _ = exact.ground_energy(L, I.j1j2_chain(L, J1, 0.2 * J1, marshall), sz0=True)
+    assert e1 < -1.5 * J1 * L - 0.1
 
 
 def test_marshall_rotation_makes_ground_state_positive():
@@ -355,17 +382,21 @@ def test_metropolis_local_tv_against_exact():
     assert _tv(counts, es.p) < 0.01
 
 
-def test_metropolis_exchange_tv_and_sz():
+@pytest.mark.parametrize("dmax", [1, 2])
+def test_metropolis_exchange_tv_and_sz(dmax):
     """Exchange rule on a 12-site ring at S_z = 0 (924 states): magnetisation
     is conserved and the histogram matches exact |psi|^2 (TV < 0.01).
     Nearest-neighbour swaps on a ring mix slowly once |psi|^2 is peaked, so
-    this variant uses sigma = 0.2 and 2e6 samples (i.i.d. draws: TV ~ 0.004)."""
+    this variant uses sigma = 0.2 and 2e6 samples (i.i.d. draws: TV ~ 0.004).
+    With dmax = 2 the proposals run over the next-nearest-neighbour edges too
+    (the exchange rule of the J1-J2 example of Sec. 7)."""
     N, M = 12, 12
     p = I.rbm_params(N, M, 13, 0.2)
     es = exact.ExactState(p, N, M, sz0=True)
     C, ns = 200, 10000
+    edges = I.chain_edges(N) if dmax == 1 else I.j1j2_chain(N)["edges"]
     s0 = oracle.chain_init(N, C, "exchange", seed=6)
-    mc = oracle.metropolis(p, N, M, "exchange", I.chain_edges(N), s0, 0, 50, ns, seed=6)
+    mc = oracle.metropolis(p, N, M, "exchange", edges, s0, 0, 50, ns, seed=6)
     x = mc["samples"].reshape(-1, N)
     assert (x.astype(np.int64).sum(axis=1) == 0).all()
     full = ((x < 0).astype(np.int64) * (1 << (N - 1 - np.arange(N)))).sum(axis=1)
