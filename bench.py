@@ -188,7 +188,8 @@ def setup(w, precision, rank, dev):
     st["params"] = torch.from_numpy(I.rbm_params(N, M, w["seed"])).to(dev)
     st["edges"] = torch.from_numpy(w["ham"]["edges"]).to(dev)
     st["ham"] = nk.make_ham(w["ham"]["kind"], w["ham"]["J"], w["ham"].get("h", 0.0),
-                            w["ham"].get("marshall", False), st["edges"])
+                            w["ham"].get("marshall", False), st["edges"], w["ham"].get("J2", 0.0),
+                            w["ham"].get("n_edges2", 0))
     st["s"] = torch.empty((C, N), dtype=torch.int8, device=dev)
     st["ctx"] = nk.Ctx(dev.index)
     nk.nk_chains_init(st["ctx"], N, C, w["rule"], w["seed"], rank, st["s"])
@@ -210,6 +211,12 @@ def step(st, first=False):
 def lattice_text(N):
     L = int(round(N ** 0.5))
     return f"{L}x{L} periodic square" if L * L == N else f"{N}-site periodic chain"
+
+
+def ham_text(ham):
+    if ham.get("n_edges2", 0):
+        return f"{ham['kind']} J1-J2 (J1={ham['J']}, J2={ham['J2']}, exchange over both edge classes)"
+    return ham["kind"]
 
 
 def l2_text(solver, Ns, M, Np):
@@ -417,7 +424,7 @@ def run_ours(args, rank, world):
         "dtype": "f64" if args.precision == "f64" else "f32+f64",
         "data": "synthetic (seeded RBM parameters N(0, 0.01^2), Philox chains)",
         "config": {"workload": w["name"], "lattice": lattice_text(w["N"]),
-                   "hamiltonian": w["ham"]["kind"], "N": w["N"], "M": w["M"], "Np": w["N"] + w["M"] + w["M"] * w["N"],
+                   "hamiltonian": ham_text(w["ham"]), "N": w["N"], "M": w["M"], "Np": w["N"] + w["M"] + w["M"] * w["N"],
                    "chains": w["chains"], "samples_per_chain": w["per_chain"], "Ns": Ns, "rule": w["rule"],
                    "solver": w["solver"], "precision": args.precision, "diag_shift": w["diag_shift"],
                    "lr": w["lr"], "parallelism": f"replicas x{world}",

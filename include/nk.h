@@ -62,8 +62,8 @@ typedef int32_t nk_status;
 #define NK_RULE_LOCAL 0    /* MetropolisLocal: flip one spin (Sec. 3.4) */
 #define NK_RULE_EXCHANGE 1 /* MetropolisExchange: swap an edge (Sec. 3.4) */
 
-#define NK_TFIM 0 /* H = J sum_<ik> sz sz - h sum_i sx (Eq. eq:tf-ising-hamiltonian) */
-#define NK_HEIS 1 /* H = J sum_<ik> sigma.sigma (Eq. eq: j1 j2 heisenberg, J2=0) */
+#define NK_TFIM 0 /* H = J sum_<ik> sz sz + J2 sum_<<ik>> sz sz - h sum_i sx (Eq. eq:tf-ising-hamiltonian) */
+#define NK_HEIS 1 /* H = J sum_<ik> sigma.sigma + J2 sum_<<ik>> sigma.sigma (Eq. eq: j1 j2 heisenberg) */
 
 #define NK_SOLVER_CHOLESKY 0             /* dense (S + eps I) in parameter space */
 #define NK_SOLVER_CHOLESKY_SAMPLESPACE 1 /* same solution via an Ns x Ns factor */
@@ -82,14 +82,22 @@ typedef struct {
 
 typedef struct {
     int32_t kind;          /* NK_TFIM or NK_HEIS */
-    double J;              /* coupling */
+    double J;              /* coupling of the nearest-neighbour edges <ik> */
     double h;              /* transverse field (NK_TFIM) */
-    int32_t marshall;      /* NK_HEIS: 1 = off-diagonal element -2J on every
-                              edge (Marshall sign folded in; the lattice must
-                              be bipartite with every edge joining the two
-                              sublattices), 0 = +2J */
-    int32_t n_edges;       /* E >= 1 */
-    const int32_t *edges;  /* device [E, 2], site indices in [0, N) */
+    int32_t marshall;      /* NK_HEIS: 1 = Marshall sign folded in: off-diagonal
+                              element -2J on every nearest-neighbour edge (each
+                              must join the two sublattices of a bipartite
+                              lattice) and +2 J2 on every next-nearest one (each
+                              must stay inside one sublattice); 0 = +2J, +2 J2 */
+    int32_t n_edges;       /* E >= 1, both classes */
+    const int32_t *edges;  /* device [E, 2], site indices in [0, N); the
+                              nearest-neighbour edges first */
+    double J2;             /* coupling of the next-nearest-neighbour edges <<ik>> */
+    int32_t n_edges2;      /* the last n_edges2 of the E edges are next-nearest
+                              neighbours, 0 <= n_edges2 <= E (0: J2 unused; a
+                              zero-initialised tail gives the nearest-neighbour
+                              model).  nk_sr_step's exchange rule draws from all
+                              E edges (d_max = 2 of the J1-J2 example, Sec. 7) */
 } nk_ham;
 
 /* Context: device ordinal, workspace, cached per-parameter tables. */

@@ -444,11 +444,13 @@ __global__ void __launch_bounds__(128) k_eloc(ElocK<R> P) {
         t[j] = (R)tj;
         if (A.t_out) A.t_out[(size_t)k * M + j] = tj;
     }
+    // edges [0, E1) couple with J, the next-nearest ones [E1, E) with J2
+    const int E1 = E - A.E2;
     double diag = 0.0;
     for (int e = lane; e < E; e += 32) {
         const int i = T.edges[2 * e], kk = T.edges[2 * e + 1];
         if ((unsigned)i < (unsigned)N && (unsigned)kk < (unsigned)N)
-            diag += A.J * (double)sv[i] * (double)sv[kk];
+            diag += (e < E1 ? A.J : A.J2) * (double)sv[i] * (double)sv[kk];
     }
     __syncwarp();
     double off = 0.0;
@@ -484,7 +486,9 @@ __global__ void __launch_bounds__(128) k_eloc(ElocK<R> P) {
             n += __popc(mask);
         }
         __syncwarp();
-        const double hoff = A.marshall ? -2.0 * A.J : 2.0 * A.J;
+        // off-diagonal elements; the Marshall sign flips only the edges that
+        // join the two sublattices (the nearest-neighbour class)
+        const double hoff = A.marshall ? -2.0 * A.J : 2.0 * A.J, hoff2 = 2.0 * A.J2;
         if (P.units) {
             for (int idx = 0; idx < n; ++idx) {
                 const int e = list[idx];
@@ -494,7 +498,7 @@ __global__ void __launch_bounds__(128) k_eloc(ElocK<R> P) {
                 pr = warp_prod(pr);
                 const double delta =
                     -2.0 * (double)si * (T.a[i] - T.a[kk]) + (double)(T.K_edge[e] + prod_log(pr));
-                if (lane == 0) off += hoff * exp(delta);
+                if (lane == 0) off += (e < E1 ? hoff : hoff2) * exp(delta);
             }
         } else {
             for (int idx = lane; idx < n; idx += 32) {
@@ -504,7 +508,7 @@ __global__ void __launch_bounds__(128) k_eloc(ElocK<R> P) {
                 Prod<R> pr = strided_product<R>(t, T.tau_edgeT + e, (size_t)E, si, 0, 1, M);
                 const double delta =
                     -2.0 * (double)si * (T.a[i] - T.a[kk]) + (double)(T.K_edge[e] + prod_log(pr));
-                off += hoff * exp(delta);
+                off += (e < E1 ? hoff : hoff2) * exp(delta);
             }
         }
     }
@@ -530,7 +534,7 @@ __global__ void __launch_bounds__(kEW * 32) k_eloc_batched(ElocBK P) {
     extern __shared__ __align__(16) unsigned char sm[];
     const Tables<float> &T = P.t;
     const ElocArgs &A = P.a;
-    const int N = T.N, M = T.M, E = T.E;
+    const int N = T.N, M = T.M, E = T.E, E1 = E - A.E2;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t k0 = (int64_t)blockIdx.x * kEG;
     const int G = (int)(A.Ns - k0 < kEG ? A.Ns - k0 : kEG);
@@ -553,13 +557,14 @@ __global__ void __launch_bounds__(kEW * 32) k_eloc_batched(ElocBK P) {
         t[g * P.t_ld + j] = tv;
     }
     __syncthreads();
-    // diagonal part: warp g sums J s_i s_k over the edges of sample g
+    // diagonal part: warp g sums J_e s_i s_k over the edges of sample g
     if (warp < G) {
         double d = 0.0;
         const int8_t *s = sv + warp * P.s_ld;
         for (int e = lane; e < E; e += 32) {
             const int i = T.edges[2 * e], kk = T.edges[2 * e + 1];
-            if ((unsigned)i < (unsigned)N && (unsigned)kk < (unsigned)N) d += A.J * (double)s[i] * (double)s[kk];
+            if ((unsigned)i < (unsigned)N && (unsigned)kk < (unsigned)N)
+                d += (e < E1 ? A.J : A.J2) * (double)s[i] * (double)s[kk];
         }
         d = warp_sum(d);
         if (lane == 0) diag[warp] = d;
@@ -572,7 +577,8 @@ __global__ void __launch_bounds__(kEW * 32) k_eloc_batched(ElocBK P) {
     for (int g = 0; g < kEG; ++g) off[g] = 0.f;
     const bool tfim = A.kind == NK_TFIM;
     const int nconn = tfim ? N : E;
-    const float hoff = (float)(A.marshall ? -2.0 * A.J : 2.0 * A.J), hfield = (float)(-A.h);
+    const float hoff = (float)(A.marshall ? -2.0 * A.J : 2.0 * A.J), hoff2 = (float)(2.0 * A.J2),
+                hfield = (float)(-A.h);
     for (int c = warp; c < nconn; c += kEW) {
         int i, kk = -1;
         const float *tau;
@@ -632,7 +638,7 @@ __global__ void __launch_bounds__(kEW * 32) k_eloc_batched(ElocBK P) {
             renorm(p);
             p = warp_prod_normalised(p);
             const float delta = -2.f * aa * sg[g] + (K + prod_log(p));
-            off[g] = fmaf(tfim ? hfield : hoff, expf(delta), off[g]);
+            off[g] = fmaf(tfim ? hfield : (c < E1 ? hoff : hoff2), expf(delta), off[g]);
         }
     }
     if (lane == 0) {

@@ -147,6 +147,8 @@ nk_status check_ham(const nk_ham *h, int N) {
         return fail(NK_ERR_INVALID_ARG, "ham->kind %d unknown", h->kind);
     if (h->n_edges < 1 || h->n_edges > 65536)
         return fail(NK_ERR_INVALID_ARG, "ham->n_edges=%d out of [1, 65536]", h->n_edges);
+    if (h->n_edges2 < 0 || h->n_edges2 > h->n_edges)
+        return fail(NK_ERR_INVALID_ARG, "ham->n_edges2=%d out of [0, n_edges]", h->n_edges2);
     NK_DEV(h->edges, "ham->edges");
     (void)N;
     return NK_OK;
@@ -638,7 +640,7 @@ nk_status nk_local_energy(nk_ctx *ctx, const nk_rbm *rbm, int32_t precision, con
     NK_DEV(eloc_out, "eloc_out");
     if (t_out) NK_DEV(t_out, "t_out");
     cudaStream_t st = (cudaStream_t)stream;
-    nk::ElocArgs a{ham->kind, ham->J, ham->h, ham->marshall, s, Ns, eloc_out, t_out};
+    nk::ElocArgs a = nk::eloc_args(ham, s, Ns, eloc_out, t_out);
     const bool site = ham->kind == NK_TFIM, edge = ham->kind == NK_HEIS;
     auto body = [&](auto tag, Carver &c, bool run) -> nk_status {
         using R = decltype(tag);
@@ -977,7 +979,7 @@ nk_status nk_sr_step(nk_ctx *ctx, nk_rbm *rbm, const nk_ham *ham, nk_chains *cha
         if (sw != NK_OK) return sw;
         if (mixed)
             NK_CU(nk::launch_theta_tc(N, M, t.b, t.W, samples, Ns, theta, ctx->tc_err, tcm, st), "theta");
-        nk::ElocArgs ea{ham->kind, ham->J, ham->h, ham->marshall, samples, Ns, eloc, T, theta};
+        nk::ElocArgs ea = nk::eloc_args(ham, samples, Ns, eloc, T, theta);
         NK_CU(nk::launch_eloc(t, ea, st), "local energy");
         NK_CU(nk::launch_stats(eloc, Ns, C, st3, st), "stats");
         NK_CU(nk::launch_make_force_g(Ns, eloc, st3, gv, st), "force g");

@@ -103,7 +103,18 @@ struct ElocArgs {
     double *eloc;
     double *t_out;            // [Ns][M] or null
     const double *theta_in;   // [Ns][M] precomputed theta, or null (rebuilt in the kernel)
+    double J2;                // coupling of the last E2 edges (next-nearest neighbours)
+    int E2;
 };
+
+// Local-energy arguments of a Hamiltonian descriptor.
+inline ElocArgs eloc_args(const nk_ham *h, const int8_t *s, int64_t Ns, double *eloc, double *t_out,
+                          const double *theta_in = nullptr) {
+    ElocArgs a{h->kind, h->J, h->h, h->marshall, s, Ns, eloc, t_out, theta_in};
+    a.J2 = h->J2;
+    a.E2 = h->n_edges2;
+    return a;
+}
 
 template <typename R>
 cudaError_t launch_eloc(const Tables<R> &t, const ElocArgs &a, cudaStream_t st);

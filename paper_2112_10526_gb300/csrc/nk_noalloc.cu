@@ -124,7 +124,7 @@ nk_status run(const nk_rbm *rbm, const nk_ham *ham, const int8_t *s, int64_t Ns,
     const bool site = ham->kind == NK_TFIM, edge = ham->kind == NK_HEIS;
     cudaError_t e = nk::launch_tables(t, site, edge, st);
     if (e == cudaSuccess) {
-        nk::ElocArgs a{ham->kind, ham->J, ham->h, ham->marshall, s, Ns, eloc, t_out};
+        nk::ElocArgs a = nk::eloc_args(ham, s, Ns, eloc, t_out);
         e = nk::launch_eloc(t, a, st);
     }
     if (e != cudaSuccess) return nk::report_error(NK_ERR_CUDA, cudaGetErrorString(e));
@@ -145,6 +145,8 @@ extern "C" nk_status nk_local_energy_noalloc(const nk_rbm *rbm, int32_t precisio
         return nk::report_error(NK_ERR_INVALID_ARG, "ham->kind unknown");
     if (ham->n_edges < 1 || ham->n_edges > 65536)
         return nk::report_error(NK_ERR_INVALID_ARG, "ham->n_edges out of [1, 65536]");
+    if (ham->n_edges2 < 0 || ham->n_edges2 > ham->n_edges)
+        return nk::report_error(NK_ERR_INVALID_ARG, "ham->n_edges2 out of [0, n_edges]");
     if (Ns < 0) return nk::report_error(NK_ERR_INVALID_ARG, "Ns < 0");
     if (Ns == 0) return NK_OK;
     if (!on_device(rbm->params) || !on_device(ham->edges) || !on_device(s) || !on_device(eloc_out) ||

@@ -48,7 +48,8 @@ class nk_rbm(ctypes.Structure):
 
 class nk_ham(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("J", ctypes.c_double), ("h", ctypes.c_double),
-                ("marshall", ctypes.c_int32), ("n_edges", ctypes.c_int32), ("edges", ctypes.c_void_p)]
+                ("marshall", ctypes.c_int32), ("n_edges", ctypes.c_int32), ("edges", ctypes.c_void_p),
+                ("J2", ctypes.c_double), ("n_edges2", ctypes.c_int32)]
 
 
 class nk_qgt(ctypes.Structure):
@@ -219,11 +220,13 @@ def make_rbm(params, N, M):
     return nk_rbm(N, M, params.data_ptr())
 
 
-def make_ham(kind, J, h, marshall, edges):
+def make_ham(kind, J, h, marshall, edges, J2=0.0, n_edges2=0):
+    """edges: device int32 [E, 2], the last n_edges2 of them next-nearest
+    neighbours with coupling J2."""
     assert edges.dtype == torch.int32 and edges.is_cuda
     e = edges.reshape(-1, 2)
     return nk_ham(KIND[kind] if isinstance(kind, str) else int(kind), float(J), float(h), int(bool(marshall)),
-                  int(e.shape[0]), e.data_ptr())
+                  int(e.shape[0]), e.data_ptr(), float(J2), int(n_edges2))
 
 
 # ------------------------------------------------------------ entry points --

@@ -18,7 +18,8 @@ def cu(x, dtype=None):
 
 def ham_to_device(ham):
     edges = cu(np.asarray(ham["edges"], dtype=np.int32).reshape(-1, 2))
-    return nk.make_ham(ham["kind"], ham["J"], ham.get("h", 0.0), ham.get("marshall", False), edges), edges
+    return nk.make_ham(ham["kind"], ham["J"], ham.get("h", 0.0), ham.get("marshall", False), edges,
+                       ham.get("J2", 0.0), ham.get("n_edges2", 0)), edges
 
 
 def rel_err(got, ref, floor=None):
