@@ -10,8 +10,10 @@ Conventions shared with the product library (by specification, not by code):
     "marshall": bool, "edges": int32 [E, 2]}, optionally with "J2": float
     and "n_edges2": int, the last n_edges2 edges being the next-nearest
     neighbours of coupling J2 (Eq. eq: j1 j2 heisenberg);
-  * sampler rule: "local" (single-spin flip) or "exchange" (edge swap at
-    fixed magnetisation).
+  * sampler rule: "local" (single-spin flip), "exchange" (edge swap at
+    fixed magnetisation) or "hamiltonian" (a uniformly chosen configuration
+    connected by an off-diagonal element of a Heisenberg-type Hamiltonian on
+    the given edges, with the Hastings correction).
 """
 from __future__ import annotations
 
@@ -26,7 +28,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
 KIND = {"tfim": 0, "heis": 1}
-RULE = {"local": 0, "exchange": 1}
+RULE = {"local": 0, "exchange": 1, "hamiltonian": 2}
 
 
 def build(force: bool = False) -> str:

@@ -232,7 +232,7 @@ static double oc_uniform(uint64_t y)
  * Random initial chain states (the Hilbert-space random_state of Sec. 2.1).
  * rule 0 (unconstrained spins): s_i = +1 iff bit (i mod 256) of the 256-bit
  *   word y0|y1|y2|y3 (y0 lowest) of block floor(i / 256) is set.
- * rule 1 (total S_z = 0, N even): start from N/2 up spins followed by N/2
+ * rules 1, 2 (total S_z = 0, N even): start from N/2 up spins followed by N/2
  *   down spins and shuffle by Fisher-Yates: for i = N-1 .. 1 swap s_i with
  *   s_j, j = pick(y0 of block i, i + 1).
  * Output s: [C, N].
@@ -272,7 +272,14 @@ void oc_chain_init(int N, int C, int rule, uint64_t seed, uint32_t stream,
  *   rule 0 (MetropolisLocal): flip site i = pick(y0, N);
  *   rule 1 (MetropolisExchange): swap the spins of edge e = pick(y0, E); if
  *     they are equal the proposal leaves s unchanged and is not a move.
- *   u = uniform(y1); accept iff ln u < 2 [ln psi(s') - ln psi(s)].
+ *   rule 2 (MetropolisHamiltonian of a Heisenberg-type H on these edges):
+ *     the configurations connected to s by an off-diagonal element are the
+ *     swaps across its n(s) antiparallel edges; s' is the r-th of them in
+ *     edge-list order, r = pick(y0, n(s)) (n(s) = 0: not a move).  The
+ *     proposal is not symmetric, g(s'|s) = 1/n(s), so the acceptance takes
+ *     the correction L(s, s') = ln g(s|s')/g(s'|s) = ln n(s) - ln n(s').
+ *   u = uniform(y1); accept iff ln u < 2 [ln psi(s') - ln psi(s)] + L(s, s')
+ *   (L = 0 for rules 0 and 1).
  * theta = b + W s is rebuilt from scratch at the start of every sweep and
  * moved by -2 W_:i s_i on each accepted flip.
  *
@@ -288,6 +295,14 @@ void oc_chain_init(int N, int C, int rule, uint64_t seed, uint32_t stream,
  * |2 (ln psi(s') - ln psi(s)) - ln u| to margin_out (may be NULL; 0 for
  * non-moves).  n_accepted[c] counts accepted moves.
  */
+/* Number of edges whose two spins differ. */
+static int oc_antiparallel(int E, const int32_t *edges, const int8_t *s)
+{
+    int n = 0;
+    for (int e = 0; e < E; ++e) n += s[edges[2 * e]] != s[edges[2 * e + 1]];
+    return n;
+}
+
 void oc_metropolis(int N, int M, const double *params, int rule, int E,
                    const int32_t *edges, int C, int8_t *s, int64_t sweep0,
                    int n_discard, int n_samples, uint64_t seed, uint32_t stream,
@@ -310,9 +325,30 @@ void oc_metropolis(int N, int M, const double *params, int rule, int E,
                 size_t slot = ((size_t)c * n_sweeps + w) * N + p;
                 oc_draw(q, (uint64_t)c, stream, 0, seed, y);
                 int sites[2], n;
+                double corr = 0.0;
                 if (rule == 0) {
                     sites[0] = oc_pick(y[0], N);
                     n = 1;
+                } else if (rule == 2) {
+                    int ns = oc_antiparallel(E, edges, sc);
+                    if (ns == 0) {
+                        if (decisions_out) decisions_out[slot] = 2;
+                        if (margin_out) margin_out[slot] = 0.0;
+                        continue;
+                    }
+                    int r = oc_pick(y[0], ns), e = 0;
+                    for (;; ++e)
+                        if (sc[edges[2 * e]] != sc[edges[2 * e + 1]] && r-- == 0) break;
+                    sites[0] = edges[2 * e];
+                    sites[1] = edges[2 * e + 1];
+                    n = 2;
+                    /* n(s') by counting on the swapped configuration */
+                    sc[sites[0]] = (int8_t)-sc[sites[0]];
+                    sc[sites[1]] = (int8_t)-sc[sites[1]];
+                    int nsp = oc_antiparallel(E, edges, sc);
+                    sc[sites[0]] = (int8_t)-sc[sites[0]];
+                    sc[sites[1]] = (int8_t)-sc[sites[1]];
+                    corr = log((double)ns) - log((double)nsp);
                 } else {
                     int e = oc_pick(y[0], E);
                     sites[0] = edges[2 * e];
@@ -326,9 +362,9 @@ void oc_metropolis(int N, int M, const double *params, int rule, int E,
                 }
                 double d = oc_log_ratio(N, M, params, sc, theta, sites, n);
                 double lu = log(oc_uniform(y[1]));
-                int mine = lu < 2.0 * d;
+                int mine = lu < 2.0 * d + corr;
                 if (decisions_out) decisions_out[slot] = (uint8_t)mine;
-                if (margin_out) margin_out[slot] = fabs(2.0 * d - lu);
+                if (margin_out) margin_out[slot] = fabs(2.0 * d + corr - lu);
                 int take = forced ? (forced[slot] == 1) : mine;
                 if (take) {
                     for (int j = 0; j < M; ++j)

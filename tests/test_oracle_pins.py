@@ -406,6 +406,60 @@ def test_metropolis_exchange_tv_and_sz(dmax):
     assert _tv(counts, es.p) < 0.01
 
 
+@pytest.mark.parametrize("lattice", ["ring", "j1j2-ring"])
+def test_metropolis_hamiltonian_rule_tv(lattice):
+    """MetropolisHamiltonian rule (Sec. 3.4) on a 12-site ring at S_z = 0:
+    s' is drawn uniformly from the swaps across the antiparallel edges, so
+    g(s'|s) = 1/n(s) and the acceptance carries L(s, s') = ln n(s) - ln n(s').
+    The histogram matches exact |psi|^2 (TV < 0.01).  Dropping the correction
+    biases the chain towards configurations with many antiparallel edges
+    (TV about 0.07 at these parameters).  Every proposal is a move."""
+    N, M = 12, 12
+    p = I.rbm_params(N, M, 13, 0.2)
+    es = exact.ExactState(p, N, M, sz0=True)
+    C, ns = 200, 10000
+    edges = I.chain_edges(N) if lattice == "ring" else I.j1j2_chain(N)["edges"]
+    s0 = oracle.chain_init(N, C, "hamiltonian", seed=7)
+    mc = oracle.metropolis(p, N, M, "hamiltonian", edges, s0, 0, 50, ns, seed=7)
+    assert set(np.unique(mc["decisions"])) <= {0, 1}
+    x = mc["samples"].reshape(-1, N)
+    assert (x.astype(np.int64).sum(axis=1) == 0).all()
+    full = ((x < 0).astype(np.int64) * (1 << (N - 1 - np.arange(N)))).sum(axis=1)
+    pos = np.full(2 ** N, -1)
+    pos[es.index] = np.arange(es.index.size)
+    counts = np.bincount(pos[full], minlength=es.index.size).astype(np.float64)
+    assert _tv(counts, es.p) < 0.01
+
+
+def test_metropolis_hamiltonian_rule_single_proposal_by_hand():
+    """One proposal of the Hamiltonian rule against its definition, spelled out
+    with numpy: the antiparallel edges of s in list order, the r-th one swapped,
+    and the decision ln u < 2 (ln psi(s') - ln psi(s)) + ln n(s) - ln n(s')."""
+    N, M = 8, 5
+    p = I.rbm_params(N, M, 3, 0.5)
+    edges = I.j1j2_chain(N)["edges"]
+    s0 = np.array([[1, 1, -1, 1, -1, -1, 1, -1]], dtype=np.int8)
+    # the first proposal of sweep 0: Philox block (0, chain 0, stream 3, 0)
+    y = oracle.philox4x64_10(np.array([0, 0, 3, 0], dtype=np.uint64), np.array([11, 0], dtype=np.uint64))
+    anti = [e for e in range(edges.shape[0]) if s0[0, edges[e, 0]] != s0[0, edges[e, 1]]]
+    r = (int(y[0]) >> 32) * len(anti) >> 32
+    i, k = edges[anti[r]]
+    s1 = s0.copy()
+    s1[0, i], s1[0, k] = s1[0, k], s1[0, i]
+    n1 = sum(s1[0, a] != s1[0, b] for a, b in edges)
+    lp0, lp1 = oracle.logpsi(p, N, M, s0)[0], oracle.logpsi(p, N, M, s1)[0]
+    lu = np.log(((int(y[1]) >> 11) + 0.5) * 2.0 ** -53)
+    expect = lu < 2 * (lp1 - lp0) + np.log(len(anti)) - np.log(n1)
+    # a one-proposal run: a sweep is N proposals, so force the other N - 1
+    # proposals to "reject" and read the oracle's own first decision
+    forced = np.zeros((1, 1, N), dtype=np.uint8)
+    forced[0, 0, 0] = 1 if expect else 0
+    mc = oracle.metropolis(p, N, M, "hamiltonian", edges, s0, 0, 0, 1, seed=11, stream=3, forced=forced)
+    assert mc["decisions"][0, 0, 0] == int(expect)
+    assert abs(mc["margin"][0, 0, 0] - abs(2 * (lp1 - lp0) + np.log(len(anti)) - np.log(n1) - lu)) < 1e-12
+    np.testing.assert_array_equal(mc["samples"][0, 0], s1[0] if expect else s0[0])
+
+
 def test_metropolis_forced_follow_and_decisions():
     N, M = 10, 10
     p = I.rbm_params(N, M, 4, 0.3)
