@@ -53,7 +53,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "f64"])
-    ap.add_argument("--workload", default="heis2d_10x10")
+    ap.add_argument("--workload", default="heis2d_10x10",
+                    help="workload name, optionally with @rule to replace its sampler rule "
+                         "(e.g. heis2d_10x10@hamiltonian)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the other-precision timing")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
@@ -66,7 +68,11 @@ def parse():
 
 def workload(name):
     from paper_2112_10526_gb300 import inputs as I
-    w = dict(I.WORKLOADS[name])
+    base, _, rule = name.partition("@")
+    w = dict(I.WORKLOADS[base])
+    if rule:
+        assert rule in ("local", "exchange", "hamiltonian"), rule
+        w["rule"] = rule
     w["name"] = name
     w["M"] = w["alpha"] * w["N"]
     w["ham"] = w["ham"]()

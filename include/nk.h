@@ -61,6 +61,9 @@ typedef int32_t nk_status;
 
 #define NK_RULE_LOCAL 0    /* MetropolisLocal: flip one spin (Sec. 3.4) */
 #define NK_RULE_EXCHANGE 1 /* MetropolisExchange: swap an edge (Sec. 3.4) */
+#define NK_RULE_HAMILTONIAN 2 /* MetropolisHamiltonian: move along an off-diagonal
+                                 element of H (Sec. 3.4), with the Hastings
+                                 correction of the asymmetric proposal */
 
 #define NK_TFIM 0 /* H = J sum_<ik> sz sz + J2 sum_<<ik>> sz sz - h sum_i sx (Eq. eq:tf-ising-hamiltonian) */
 #define NK_HEIS 1 /* H = J sum_<ik> sigma.sigma + J2 sum_<<ik>> sigma.sigma (Eq. eq: j1 j2 heisenberg) */
@@ -132,7 +135,8 @@ nk_status nk_rbm_logpsi(nk_ctx *ctx, const nk_rbm *rbm, int32_t precision, const
 /*
  * Random initial chain states (random_state of Sec. 2.1), from the Philox
  * stream (key (seed, 0), counter (index, chain, stream_id, 1)).
- *   rule NK_RULE_LOCAL: i.i.d. spins; NK_RULE_EXCHANGE: S_z = 0 (N even).
+ *   rule NK_RULE_LOCAL: i.i.d. spins; NK_RULE_EXCHANGE and
+ *   NK_RULE_HAMILTONIAN: S_z = 0 (N even).
  *   s_out [C, N] int8.
  */
 nk_status nk_chains_init(nk_ctx *ctx, int32_t N, int32_t C, int32_t rule, uint64_t seed,
@@ -140,17 +144,24 @@ nk_status nk_chains_init(nk_ctx *ctx, int32_t N, int32_t C, int32_t rule, uint64
 
 /*
  * Metropolis-Hastings sweeps (Sec. 3.4: P_acc = min(1, |psi(s')/psi(s)|^2)
- * for the symmetric local and exchange proposals).  One sweep is N
+ * for the symmetric local and exchange proposals, times g(s|s')/g(s'|s)
+ * for the Hamiltonian rule).  One sweep is N
  * proposals per chain.  Proposal p of sweep w uses the Philox4x64-10 block
  * with key (seed, 0) and counter ((sweep0 + w) N + p, chain, stream_id, 0):
  * the site (local) or edge (exchange) is floor(hi32(y0) * n / 2^32), the
  * uniform is u = ((y1 >> 11) + 0.5) 2^-53, and the move is accepted iff
  * ln u < 2 (ln psi(s') - ln psi(s)).  An exchange proposal on an edge with
- * equal spins is not a move.  Hidden activations theta = b + W s are rebuilt
+ * equal spins is not a move.  NK_RULE_HAMILTONIAN is the rule of a
+ * Heisenberg-type Hamiltonian on `edges`: the configurations connected to s
+ * are the swaps across its n(s) antiparallel edges, s' is the r-th of them
+ * in edge order, r = floor(hi32(y0) n(s) / 2^32), and the move is accepted
+ * iff ln u < 2 (ln psi(s') - ln psi(s)) + ln n(s) - ln n(s') (n(s) = 0: not
+ * a move).  Hidden activations theta = b + W s are rebuilt
  * from scratch (FP64) at the start of every sweep and updated incrementally
  * on every accepted move.
  *   s            [C, N] in/out chain states
- *   n_edges/edges  device [E, 2] edge list (exchange rule only; else 0/NULL)
+ *   n_edges/edges  device [E, 2] edge list (exchange and Hamiltonian rules;
+ *                else 0/NULL)
  *   samples_out  [C, n_samples, N]: the state after each of the n_samples
  *                sweeps that follow n_discard discarded sweeps
  *   logpsi_out   [C, n_samples] float64 or NULL

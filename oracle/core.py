@@ -287,7 +287,14 @@ def sr_step(params, N, M, ham, rule, chains, sweep0, n_discard, n_samples, seed,
     """One VMC iteration with stochastic reconfiguration (Sec. 4.1): sample,
     local energies, force, QGT solve, SGD update.  Returns the new parameters,
     new chain states and the per-step diagnostics."""
-    edges = ham["edges"]
+    edges = np.asarray(ham["edges"]).reshape(-1, 2)
+    if rule == "hamiltonian" and ham["kind"] == "tfim":
+        # the connected configurations of the Ising model are the N single
+        # flips, drawn uniformly: the local rule
+        rule = "local"
+    elif rule == "hamiltonian" and float(ham.get("J2", 0.0)) == 0.0:
+        # edges with a zero coupling connect nothing
+        edges = edges[:edges.shape[0] - int(ham.get("n_edges2", 0))]
     mc = metropolis(params, N, M, rule, edges, chains, sweep0, n_discard, n_samples, seed, stream,
                     forced=forced)
     C = chains.shape[0]

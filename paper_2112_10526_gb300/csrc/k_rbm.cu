@@ -242,6 +242,55 @@ __device__ __forceinline__ Prod<float> unit_lanes_product<float>(const float *t,
 
 // ------------------------------------------------------------------ sweep ---
 
+// Edge e of the list joins two sites of [0, N) holding different spins, after
+// the spins of sites i and k are flipped (i = k = -1: as they are).
+__device__ __forceinline__ bool antiparallel(const int32_t *__restrict__ edges, int e, int N, const int8_t *sv,
+                                             int i, int k) {
+    const int a = edges[2 * e], b = edges[2 * e + 1];
+    if ((unsigned)a >= (unsigned)N || (unsigned)b >= (unsigned)N) return false;
+    const int sa = (a == i || a == k) ? -sv[a] : sv[a], sb = (b == i || b == k) ? -sv[b] : sv[b];
+    return sa != sb;
+}
+
+// MetropolisHamiltonian proposal of a Heisenberg-type Hamiltonian (Sec. 3.4):
+// the connected configurations are the swaps across the n(s) antiparallel
+// edges; the proposal is the r-th of them in edge order, r = floor(hi n(s) /
+// 2^32), and n(s') is counted on the swapped state.  Warp-uniform results;
+// e_sel = -1 when n(s) = 0.
+__device__ __forceinline__ void hamiltonian_pick(const int32_t *__restrict__ edges, int E, int N, const int8_t *sv,
+                                                 unsigned hi, int lane, int &e_sel, int &ns, int &nsp) {
+    ns = 0;
+    nsp = 0;
+    e_sel = -1;
+    for (int e0 = 0; e0 < E; e0 += 32) {
+        const int e = e0 + lane;
+        ns += __popc(__ballot_sync(kFull, e < E && antiparallel(edges, e, N, sv, -1, -1)));
+    }
+    if (ns == 0) return;
+    int r = (int)(((unsigned long long)hi * (unsigned long long)ns) >> 32);  // r < ns
+    for (int e0 = 0; e0 < E; e0 += 32) {
+        const int e = e0 + lane;
+        const bool f = e < E && antiparallel(edges, e, N, sv, -1, -1);
+        const unsigned m = __ballot_sync(kFull, f);
+        const int cnt = __popc(m);
+        if (r < cnt) {  // warp-uniform
+            const bool hit = f && __popc(m & ((1u << lane) - 1u)) == r;
+            e_sel = e0 + __ffs(__ballot_sync(kFull, hit)) - 1;
+            break;
+        }
+        r -= cnt;
+    }
+    if (e_sel < 0) {
+        ns = 0;
+        return;
+    }
+    const int i = edges[2 * e_sel], k = edges[2 * e_sel + 1];
+    for (int e0 = 0; e0 < E; e0 += 32) {
+        const int e = e0 + lane;
+        nsp += __popc(__ballot_sync(kFull, e < E && antiparallel(edges, e, N, sv, i, k)));
+    }
+}
+
 template <typename R>
 struct SweepK {
     Tables<R> t;
@@ -253,8 +302,10 @@ struct SweepK {
 // One warp per chain.  Hidden units are spread over the lanes (j = lane,
 // lane + 32, ...); t = tanh theta and the spins live in shared memory.  The
 // 32 lanes evaluate the Philox blocks of 32 consecutive proposals at once and
-// broadcast them one per proposal.
-template <typename R>
+// broadcast them one per proposal.  kHam: the Hamiltonian rule, whose edge
+// depends on the state (a separate instantiation keeps the registers of the
+// local and exchange rules as they are).
+template <typename R, bool kHam>
 __global__ void __launch_bounds__(128) k_sweep(SweepK<R> P) {
     extern __shared__ __align__(16) unsigned char sm[];
     const Tables<R> &T = P.t;
@@ -304,6 +355,7 @@ __global__ void __launch_bounds__(128) k_sweep(SweepK<R> P) {
         // The FP32 path takes the accept decision in FP32 (ln u and the
         // ratio), the FP64 path in FP64.
         int b_i = 0, b_k = -1, b_row = 0, b_ok = 1;
+        unsigned b_hi = 0;
         R b_K = R(0);
         Acc b_aa = Acc(0), b_lu = Acc(0);
         for (int q = 0; q < N; ++q) {
@@ -320,6 +372,8 @@ __global__ void __launch_bounds__(128) k_sweep(SweepK<R> P) {
                     b_row = b_i;
                     b_K = T.K_site[b_i];
                     b_aa = (Acc)T.a[b_i];
+                } else if (kHam) {
+                    b_hi = (unsigned)(y.v[0] >> 32);  // the edge depends on the state
                 } else {
                     const int e = pick_index(y.v[0], T.E);
                     const int i0 = A.edges[2 * e], k0 = A.edges[2 * e + 1];
@@ -333,14 +387,33 @@ __global__ void __launch_bounds__(128) k_sweep(SweepK<R> P) {
                 }
             }
             const int src = q & 31;
-            const int i = __shfl_sync(kFull, b_i, src), k = __shfl_sync(kFull, b_k, src);
-            const int row = __shfl_sync(kFull, b_row, src);
-            const R K = __shfl_sync(kFull, b_K, src);
-            const Acc aa = __shfl_sync(kFull, b_aa, src), lu = __shfl_sync(kFull, b_lu, src);
+            int i = __shfl_sync(kFull, b_i, src), k = __shfl_sync(kFull, b_k, src);
+            int row = __shfl_sync(kFull, b_row, src);
+            R K = __shfl_sync(kFull, b_K, src);
+            Acc aa = __shfl_sync(kFull, b_aa, src);
+            const Acc lu = __shfl_sync(kFull, b_lu, src);
             const size_t slot = ((size_t)c * A.dec_stride + A.dec_offset + w) * N + q;
             const R *tau;
+            Acc corr = Acc(0);  // ln g(s|s') - ln g(s'|s)
             if (A.rule == NK_RULE_LOCAL) {
                 tau = T.tau_site + (size_t)row * M;
+            } else if (kHam) {
+                int e, ns, nsp;
+                hamiltonian_pick(A.edges, T.E, N, sv, __shfl_sync(kFull, b_hi, src), lane, e, ns, nsp);
+                if (e < 0) {
+                    if (lane == 0 && A.decisions) A.decisions[slot] = 2;
+                    continue;
+                }
+                i = A.edges[2 * e];
+                k = A.edges[2 * e + 1];
+                row = e;
+                K = T.K_edge[e];
+                aa = (Acc)(T.a[i] - T.a[k]);
+                if (kF32)
+                    corr = (Acc)(logf((float)ns) - logf((float)nsp));
+                else
+                    corr = (Acc)(log((double)ns) - log((double)nsp));
+                tau = T.tau_edge + (size_t)row * M;
             } else {
                 if (!__shfl_sync(kFull, b_ok, src) || sv[i] == sv[k]) {
                     if (lane == 0 && A.decisions) A.decisions[slot] = 2;
@@ -353,7 +426,7 @@ __global__ void __launch_bounds__(128) k_sweep(SweepK<R> P) {
             Prod<R> pr = unit_lanes_product<R>(t, tau, si, lane, M, P.vec4);
             pr = warp_prod_normalised(pr);
             const Acc delta = d0 + (Acc)(K + prod_log(pr));
-            const bool accept = lu < Acc(2) * delta;
+            const bool accept = lu < Acc(2) * delta + corr;
             if (lane == 0 && A.decisions) A.decisions[slot] = accept ? 1 : 0;
             if (accept) {
                 if (kF32 && P.vec4) {
@@ -779,11 +852,16 @@ cudaError_t launch_sweep(const Tables<R> &t, const SweepArgs &a, cudaStream_t st
     while (wpb > 1 && (size_t)wpb * P.warp_bytes > 200 * 1024) wpb >>= 1;
     size_t smem = (size_t)wpb * P.warp_bytes;
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
-    cudaError_t err = nk::allow_max_dynamic_smem((const void *)k_sweep<R>);
+    const bool ham = a.rule == NK_RULE_HAMILTONIAN;
+    const void *fn = ham ? (const void *)k_sweep<R, true> : (const void *)k_sweep<R, false>;
+    cudaError_t err = nk::allow_max_dynamic_smem(fn);
     if (err != cudaSuccess) return err;
     unsigned grid = (unsigned)((a.C + wpb - 1) / wpb);
     const int slot = prof_begin(NK_PROF_SWEEP, st);
-    (k_sweep<R><<<grid, 32 * wpb, smem, st>>>(P), nk::note_launch());
+    if (ham)
+        (k_sweep<R, true><<<grid, 32 * wpb, smem, st>>>(P), nk::note_launch());
+    else
+        (k_sweep<R, false><<<grid, 32 * wpb, smem, st>>>(P), nk::note_launch());
     prof_end(slot, st, (double)a.C * (a.n_discard + a.n_samples) * t.N * (double)t.M);
     return cudaGetLastError();
 }

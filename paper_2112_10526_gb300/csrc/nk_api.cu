@@ -554,9 +554,9 @@ nk_status nk_chains_init(nk_ctx *ctx, int32_t N, int32_t C, int32_t rule, uint64
     DeviceGuard g(ctx->device);
     if (N < 1 || N > 4096) return fail(NK_ERR_INVALID_ARG, "N=%d out of [1, 4096]", N);
     if (C < 0) return fail(NK_ERR_INVALID_ARG, "C < 0");
-    if (rule != NK_RULE_LOCAL && rule != NK_RULE_EXCHANGE)
+    if (rule != NK_RULE_LOCAL && rule != NK_RULE_EXCHANGE && rule != NK_RULE_HAMILTONIAN)
         return fail(NK_ERR_INVALID_ARG, "rule %d unknown", rule);
-    if (rule == NK_RULE_EXCHANGE && (N % 2))
+    if (rule != NK_RULE_LOCAL && (N % 2))
         return fail(NK_ERR_INVALID_ARG, "S_z = 0 initial states need an even N");
     if (C == 0) return NK_OK;
     NK_DEV(s_out, "s_out");
@@ -575,14 +575,15 @@ nk_status nk_metropolis_sweep(nk_ctx *ctx, const nk_rbm *rbm, int32_t precision,
     nk_status st0 = check_rbm(rbm);
     if (st0 != NK_OK) return st0;
     if ((st0 = check_precision(precision)) != NK_OK) return st0;
-    if (rule != NK_RULE_LOCAL && rule != NK_RULE_EXCHANGE)
+    if (rule != NK_RULE_LOCAL && rule != NK_RULE_EXCHANGE && rule != NK_RULE_HAMILTONIAN)
         return fail(NK_ERR_INVALID_ARG, "rule %d unknown", rule);
     if (C < 0 || n_discard < 0 || n_samples < 0 || sweep0 < 0)
         return fail(NK_ERR_INVALID_ARG, "negative C, n_discard, n_samples or sweep0");
     if (C == 0 || n_discard + n_samples == 0) return NK_OK;
-    if (rule == NK_RULE_EXCHANGE) {
+    const bool pair = rule != NK_RULE_LOCAL;  // moves along edges
+    if (pair) {
         if (n_edges < 1 || n_edges > 65536)
-            return fail(NK_ERR_INVALID_ARG, "exchange rule needs 1 <= n_edges <= 65536");
+            return fail(NK_ERR_INVALID_ARG, "exchange and Hamiltonian rules need 1 <= n_edges <= 65536");
         NK_DEV(edges, "edges");
     }
     NK_DEV(s, "s");
@@ -591,7 +592,7 @@ nk_status nk_metropolis_sweep(nk_ctx *ctx, const nk_rbm *rbm, int32_t precision,
     if (n_accepted) NK_DEV(n_accepted, "n_accepted");
     if (decisions_out) NK_DEV(decisions_out, "decisions_out");
     cudaStream_t st = (cudaStream_t)stream;
-    const int E = rule == NK_RULE_EXCHANGE ? n_edges : 0;
+    const int E = pair ? n_edges : 0;
     nk::SweepArgs a{};
     a.N = rbm->N;
     a.M = rbm->M;
@@ -612,12 +613,12 @@ nk_status nk_metropolis_sweep(nk_ctx *ctx, const nk_rbm *rbm, int32_t precision,
     auto body = [&](auto tag, Carver &c, bool run) -> nk_status {
         using R = decltype(tag);
         nk::Tables<R> t{};
-        carve_tables(c, t, rbm, E, edges, rule == NK_RULE_LOCAL, rule == NK_RULE_EXCHANGE);
+        carve_tables(c, t, rbm, E, edges, !pair, pair);
         const bool mixed = precision == NK_MIXED;
         double *theta = mixed ? c.take<double>((size_t)C * rbm->M) : nullptr;
         void *tcm = mixed ? c.take<char>(nk::tc_theta_ws_bytes(rbm->N, rbm->M, C)) : nullptr;
         if (!run) return NK_OK;
-        NK_CU(nk::launch_tables(t, rule == NK_RULE_LOCAL, rule == NK_RULE_EXCHANGE, st), "tables");
+        NK_CU(nk::launch_tables(t, !pair, pair, st), "tables");
         return run_sweeps(ctx, t, a, mixed, theta, tcm, st);
     };
     if (precision == NK_F64)
@@ -920,7 +921,7 @@ nk_status nk_sr_step(nk_ctx *ctx, nk_rbm *rbm, const nk_ham *ham, nk_chains *cha
     if ((st0 = check_ham(ham, rbm->N)) != NK_OK) return st0;
     if ((st0 = check_solver(cfg->solver, cfg->diag_shift, cfg->cg_tol, cfg->cg_maxiter)) != NK_OK)
         return st0;
-    if (cfg->rule != NK_RULE_LOCAL && cfg->rule != NK_RULE_EXCHANGE)
+    if (cfg->rule != NK_RULE_LOCAL && cfg->rule != NK_RULE_EXCHANGE && cfg->rule != NK_RULE_HAMILTONIAN)
         return fail(NK_ERR_INVALID_ARG, "rule %d unknown", cfg->rule);
     if (chains->C < 1 || cfg->n_samples < 1 || cfg->n_discard < 0 || chains->sweeps_done < 0)
         return fail(NK_ERR_INVALID_ARG, "need C >= 1, n_samples >= 1, n_discard >= 0");
@@ -932,8 +933,13 @@ nk_status nk_sr_step(nk_ctx *ctx, nk_rbm *rbm, const nk_ham *ham, nk_chains *cha
     cudaStream_t st = (cudaStream_t)stream;
     const int N = rbm->N, M = rbm->M, C = chains->C, E = ham->n_edges;
     const int64_t Ns = (int64_t)C * cfg->n_samples, Np = n_params(N, M);
-    const bool site = cfg->rule == NK_RULE_LOCAL || ham->kind == NK_TFIM;
-    const bool edge = cfg->rule == NK_RULE_EXCHANGE || ham->kind == NK_HEIS;
+    // The Hamiltonian rule of the Ising model draws one of the N single flips
+    // uniformly: the local rule.  For NK_HEIS it moves along the edges with a
+    // nonzero coupling (the next-nearest class drops out when J2 = 0).
+    const int rule = cfg->rule == NK_RULE_HAMILTONIAN && ham->kind == NK_TFIM ? NK_RULE_LOCAL : cfg->rule;
+    const int E_rule = rule == NK_RULE_HAMILTONIAN && ham->J2 == 0.0 ? E - ham->n_edges2 : E;
+    const bool site = rule == NK_RULE_LOCAL || ham->kind == NK_TFIM;
+    const bool edge = rule != NK_RULE_LOCAL || ham->kind == NK_HEIS;
 
     auto body = [&](auto tag, Carver &c, bool run) -> nk_status {
         using R = decltype(tag);
@@ -961,9 +967,9 @@ nk_status nk_sr_step(nk_ctx *ctx, nk_rbm *rbm, const nk_ham *ham, nk_chains *cha
         nk::SweepArgs a{};
         a.N = N;
         a.M = M;
-        a.E = E;
+        a.E = E_rule;
         a.C = C;
-        a.rule = cfg->rule;
+        a.rule = rule;
         a.edges = ham->edges;
         a.s = chains->s;
         a.sweep0 = chains->sweeps_done;
@@ -975,7 +981,9 @@ nk_status nk_sr_step(nk_ctx *ctx, nk_rbm *rbm, const nk_ham *ham, nk_chains *cha
         a.logpsi = nullptr;
         a.n_accepted = acc;
         a.decisions = nullptr;
-        nk_status sw = run_sweeps(ctx, t, a, mixed, theta, tcm, st);
+        nk::Tables<R> ts = t;  // the rule's edges: a prefix of the Hamiltonian's
+        ts.E = E_rule;
+        nk_status sw = run_sweeps(ctx, ts, a, mixed, theta, tcm, st);
         if (sw != NK_OK) return sw;
         if (mixed)
             NK_CU(nk::launch_theta_tc(N, M, t.b, t.W, samples, Ns, theta, ctx->tc_err, tcm, st), "theta");

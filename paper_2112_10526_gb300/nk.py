@@ -24,13 +24,13 @@ NK_ERR_NOT_CONVERGED = -5
 NK_ERR_UNIMPLEMENTED = -6
 
 NK_F64, NK_MIXED = 0, 1
-NK_RULE_LOCAL, NK_RULE_EXCHANGE = 0, 1
+NK_RULE_LOCAL, NK_RULE_EXCHANGE, NK_RULE_HAMILTONIAN = 0, 1, 2
 NK_TFIM, NK_HEIS = 0, 1
 NK_SOLVER_CHOLESKY, NK_SOLVER_CHOLESKY_SAMPLESPACE, NK_SOLVER_CG = 0, 1, 2
 NK_QGT_ONTHEFLY, NK_QGT_JACOBIAN = 0, 1
 
 PRECISION = {"f64": NK_F64, "mixed": NK_MIXED}
-RULE = {"local": NK_RULE_LOCAL, "exchange": NK_RULE_EXCHANGE}
+RULE = {"local": NK_RULE_LOCAL, "exchange": NK_RULE_EXCHANGE, "hamiltonian": NK_RULE_HAMILTONIAN}
 KIND = {"tfim": NK_TFIM, "heis": NK_HEIS}
 SOLVER = {"cholesky": NK_SOLVER_CHOLESKY, "cholesky_samplespace": NK_SOLVER_CHOLESKY_SAMPLESPACE,
           "cg": NK_SOLVER_CG}
