@@ -603,6 +603,10 @@ struct ElocBK {
     int t_ld, s_ld;
 };
 
+// kU tau loads in flight per lane: 4 where M is large enough that the
+// shared-memory t of kEG samples allows one CTA per SM anyway (M >= 4096),
+// else 1 (the extra registers of 4 would halve the resident CTAs).
+template <int kU>
 __global__ void __launch_bounds__(kEW * 32) k_eloc_batched(ElocBK P) {
     extern __shared__ __align__(16) unsigned char sm[];
     const Tables<float> &T = P.t;
@@ -683,25 +687,35 @@ __global__ void __launch_bounds__(kEW * 32) k_eloc_batched(ElocBK P) {
             ex[g] = 0;
             sg[g] = (float)sv[g * P.s_ld + i];
         }
-        int cnt = 0;
-        for (int j = 4 * lane; j < M; j += 128) {
-            const float4 uv = __ldg(reinterpret_cast<const float4 *>(tau + j));
+        // This lane's units j = 4 lane + 128 it, it = j >> 7: the tau loads
+        // of kU iterations are issued together (the row comes from L2), and
+        // the products are renormalised after every odd iteration.
+        for (int j0 = 4 * lane; j0 < M; j0 += kU * 128) {
+            float4 uv[kU];
 #pragma unroll
-            for (int g = 0; g < kEG; ++g) {
-                if (!(active & (1u << g))) continue;
-                const float4 tv = *reinterpret_cast<const float4 *>(t + g * P.t_ld + j);
-                const float ns = -sg[g];
-                m[g] *= fmaf(ns * tv.x, uv.x, 1.f) * fmaf(ns * tv.y, uv.y, 1.f) * fmaf(ns * tv.z, uv.z, 1.f) *
-                        fmaf(ns * tv.w, uv.w, 1.f);
-            }
-            if (++cnt == 2) {
+            for (int u = 0; u < kU; ++u)
+                uv[u] = j0 + u * 128 < M ? __ldg(reinterpret_cast<const float4 *>(tau + j0 + u * 128))
+                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int j = j0 + u * 128;
+                if (j >= M) break;
 #pragma unroll
                 for (int g = 0; g < kEG; ++g) {
-                    int k;
-                    m[g] = frexpf(m[g], &k);
-                    ex[g] += k;
+                    if (!(active & (1u << g))) continue;
+                    const float4 tv = *reinterpret_cast<const float4 *>(t + g * P.t_ld + j);
+                    const float ns = -sg[g];
+                    m[g] *= fmaf(ns * tv.x, uv[u].x, 1.f) * fmaf(ns * tv.y, uv[u].y, 1.f) *
+                            fmaf(ns * tv.z, uv[u].z, 1.f) * fmaf(ns * tv.w, uv[u].w, 1.f);
                 }
-                cnt = 0;
+                if ((j >> 7) & 1) {
+#pragma unroll
+                    for (int g = 0; g < kEG; ++g) {
+                        int k;
+                        m[g] = frexpf(m[g], &k);
+                        ex[g] += k;
+                    }
+                }
             }
         }
 #pragma unroll
@@ -888,11 +902,16 @@ cudaError_t launch_eloc_batched<float>(const Tables<float> &t, const ElocArgs &a
     P.s_ld = (t.N + 15) / 16 * 16;
     const size_t smem = eloc_batched_smem(t.N, t.M);
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
-    cudaError_t err = nk::allow_max_dynamic_smem((const void *)k_eloc_batched);
+    const bool wide = t.M >= 4096;
+    const void *fn = wide ? (const void *)k_eloc_batched<4> : (const void *)k_eloc_batched<1>;
+    cudaError_t err = nk::allow_max_dynamic_smem(fn);
     if (err != cudaSuccess) return err;
     const unsigned grid = (unsigned)((a.Ns + kEG - 1) / kEG);
     const int slot = prof_begin(NK_PROF_ELOC, st);
-    (k_eloc_batched<<<grid, kEW * 32, smem, st>>>(P), nk::note_launch());
+    if (wide)
+        (k_eloc_batched<4><<<grid, kEW * 32, smem, st>>>(P), nk::note_launch());
+    else
+        (k_eloc_batched<1><<<grid, kEW * 32, smem, st>>>(P), nk::note_launch());
     const double conn = a.kind == NK_TFIM ? (double)t.N : 0.5 * (double)t.E;
     prof_end(slot, st, (double)a.Ns * conn * (double)t.M);
     return cudaGetLastError();
