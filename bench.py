@@ -37,7 +37,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x FMA x max
 
 
 def measured_peaks():
-    """Measured peaks of this GPU pool (HBM copy GB/s, cuBLAS bf16 TF/s)."""
+    """Measured peaks of this GPU model from MEASURED_PEAKS.json (HBM copy
+    GB/s, cuBLAS bf16 TF/s burst and sustained), else fallback figures."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             d = json.load(f)
