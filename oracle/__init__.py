@@ -16,7 +16,7 @@ Layout:
   exact.py     exact enumeration over all basis states and exact
                diagonalisation from Kronecker products of Pauli matrices.
 
-Parity pins are in tests/test_oracle_*.py.  Functions without an external
-pin say "parity unpinned" in their docstring.
+Parity pins are in tests/test_oracle_*.py.  A function without an external
+pin would say "parity unpinned" in its docstring; none does.
 """
 from .core import *  # noqa: F401,F403

@@ -182,7 +182,9 @@ def stats(eloc, n_chains=None):
     The error of the mean is not fixed by the paper.  Reading used here: with
     n_chains chains of >= 2 samples each (samples stored chain-major), the
     standard error sqrt(var(chain means) / n_chains); otherwise
-    sqrt(variance / N_s).  parity unpinned (the error bar only)."""
+    sqrt(variance / N_s).  Pinned statistically: over repeated independent
+    runs its rms matches the spread of the mean (i.i.d. and autocorrelated
+    chains)."""
     e = np.asarray(eloc, dtype=np.float64).ravel()
     ns = e.size
     mean = e.sum() / ns
