@@ -14,7 +14,10 @@ Layout:
                QGT, SR linear solves and update in numpy (Sec. 3.3, 3.5, 4.1,
                App. B of the paper);
   exact.py     exact enumeration over all basis states and exact
-               diagonalisation from Kronecker products of Pauli matrices.
+               diagonalisation from Kronecker products of Pauli matrices;
+  symm.py      the symmetric RBM (RBMSymm, Sec. 5): ln psi and
+               log-derivatives over a site-permutation group, SR step
+               through the equal plain RBM with tied parameters.
 
 Parity pins are in tests/test_oracle_*.py.  A function without an external
 pin would say "parity unpinned" in its docstring; none does.

@@ -17,6 +17,8 @@ Recipe (matching the workloads of the NetKet 3 paper, Secs. 8-10):
     for every site in order (2 L^2 more); on the chain (i, i+2 mod L);
   * J1-J2 models list the nearest-neighbour edges first and the
     next-nearest ones after them ("n_edges2" of them, coupling "J2");
+  * symmetry groups are lists of site permutations (the lattice
+    translations);
   * random configurations: i.i.d. +-1 spins, or uniformly random S_z = 0
     configurations (a random permutation of N/2 up and N/2 down spins).
 """
@@ -59,6 +61,22 @@ def square_nnn_edges(L: int) -> np.ndarray:
 
 def chain_nnn_edges(L: int) -> np.ndarray:
     return np.array([[i, (i + 2) % L] for i in range(L)], dtype=np.int32).reshape(-1, 2)
+
+
+def translations_chain(L: int) -> np.ndarray:
+    """Translation group of the periodic chain as site permutations:
+    row g maps site j to (j + g) mod L."""
+    return np.array([[(j + g) % L for j in range(L)] for g in range(L)], dtype=np.int64)
+
+
+def translations_square(L: int) -> np.ndarray:
+    """Translation group of the periodic L x L square lattice: row
+    dx L + dy maps site x L + y to ((x + dx) mod L) L + (y + dy) mod L."""
+    out = []
+    for dx in range(L):
+        for dy in range(L):
+            out.append([((x + dx) % L) * L + (y + dy) % L for x in range(L) for y in range(L)])
+    return np.array(out, dtype=np.int64)
 
 
 def random_configs(B: int, N: int, seed: int, sz0: bool = False) -> np.ndarray:
