@@ -278,6 +278,36 @@ def solve_cg(matvec, F, tol=1e-10, maxiter=1000):
     return x, it, np.sqrt(rr) / fn
 
 
+def solve_svd(S, F, diag_shift=0.0, rcond=1e-12):
+    """(S + eps I) delta = F through the singular value decomposition of the
+    symmetric positive semi-definite S + eps I, suppressing the singular
+    values below rcond times the largest (Sec. 3.5, non-iterative solvers
+    whose stability is controlled by dropping small singular values):
+    delta = sum_{k: sigma_k > rcond sigma_max} v_k (u_k . F) / sigma_k."""
+    A = np.asarray(S, dtype=np.float64) + diag_shift * np.eye(S.shape[0])
+    U, sig, Vt = np.linalg.svd(A)
+    keep = sig > rcond * sig[0] if sig.size else sig > 0
+    coef = (U[:, keep].T @ np.asarray(F, dtype=np.float64)) / sig[keep]
+    return Vt[keep].T @ coef
+
+
+def solve_svd_samplespace(O, F, rcond=1e-12):
+    """The same truncated solve (eps = 0) from the N_s x N_s Gram matrix:
+    with dJ the centred Jacobian and T = dJ dJ^T / N_s = sum_k lambda_k u_k
+    u_k^T, the nonzero spectrum of S = dJ^T dJ / N_s is that of T with
+    singular vectors v_k = dJ^T u_k / sqrt(N_s lambda_k), so
+    delta = sum_{k: lambda_k > rcond lambda_max} v_k (v_k . F) / lambda_k."""
+    O = np.asarray(O, dtype=np.float64)
+    ns = O.shape[0]
+    dJ = O - O.sum(axis=0) / ns
+    lam, U = np.linalg.eigh(dJ @ dJ.T / ns)
+    order = np.argsort(lam)[::-1]
+    lam, U = lam[order], U[:, order]
+    keep = lam > rcond * lam[0]
+    V = dJ.T @ U[:, keep] / np.sqrt(ns * lam[keep])
+    return V @ ((V.T @ np.asarray(F, dtype=np.float64)) / lam[keep])
+
+
 def sgd_update(params, delta, lr):
     """theta_i -> theta_i - eta delta_i  (Sec. 4.1, SGD update rule)."""
     return np.asarray(params, dtype=np.float64) - lr * np.asarray(delta, dtype=np.float64)
@@ -285,7 +315,7 @@ def sgd_update(params, delta, lr):
 
 def sr_step(params, N, M, ham, rule, chains, sweep0, n_discard, n_samples, seed, stream=0,
             diag_shift=0.01, lr=0.01, solver="cholesky", cg_tol=1e-10, cg_maxiter=1000,
-            forced=None):
+            forced=None, svd_rcond=1e-12):
     """One VMC iteration with stochastic reconfiguration (Sec. 4.1): sample,
     local energies, force, QGT solve, SGD update.  Returns the new parameters,
     new chain states and the per-step diagnostics."""
@@ -307,6 +337,9 @@ def sr_step(params, N, M, ham, rule, chains, sweep0, n_discard, n_samples, seed,
     F = force(O, e)
     if solver == "cholesky":
         delta = solve_cholesky(qgt_dense(O), F, diag_shift)
+        iters, res = 0, 0.0
+    elif solver == "svd":
+        delta = solve_svd(qgt_dense(O), F, diag_shift, svd_rcond)
         iters, res = 0, 0.0
     else:
         delta, iters, res = solve_cg(lambda v: qgt_matvec_onthefly(O, v, diag_shift), F,

@@ -320,6 +320,49 @@ def test_cg_matches_cholesky():
     np.testing.assert_allclose(x2, x1, rtol=1e-9, atol=1e-10)
 
 
+def test_svd_solve_on_a_known_spectrum():
+    """S = Q diag(2, 1e-3, 1e-20, 0) Q^T with Q orthogonal: with rcond = 1e-10
+    the truncated solve keeps the first two directions, delta = Q diag(1/2,
+    1e3, 0, 0) Q^T F."""
+    Q, _ = np.linalg.qr(np.random.default_rng(3).normal(size=(4, 4)))
+    S = Q @ np.diag([2.0, 1e-3, 1e-20, 0.0]) @ Q.T
+    F = np.array([0.3, -1.2, 0.7, 2.0])
+    ref = Q @ (np.array([0.5, 1e3, 0.0, 0.0]) * (Q.T @ F))
+    np.testing.assert_allclose(oracle.solve_svd(S, F, 0.0, 1e-10), ref, rtol=1e-9, atol=1e-9)
+    # a diagonal shift moves every singular value by eps and keeps them all
+    ref_eps = Q @ ((Q.T @ F) / (np.array([2.0, 1e-3, 1e-20, 0.0]) + 0.1))
+    np.testing.assert_allclose(oracle.solve_svd(S, F, 0.1, 1e-10), ref_eps, rtol=1e-12, atol=1e-12)
+
+
+def test_svd_solve_equals_cholesky_when_shifted():
+    N, M = 6, 6
+    p = I.rbm_params(N, M, 2, 0.3)
+    s = I.random_configs(128, N, 8)
+    S = oracle.qgt_dense(oracle.jacobian(p, N, M, s))
+    F = np.random.default_rng(4).normal(size=p.size)
+    np.testing.assert_allclose(oracle.solve_svd(S, F, 0.05), oracle.solve_cholesky(S, F, 0.05),
+                               rtol=1e-9, atol=1e-10)
+
+
+def test_svd_solve_rank_deficient_sample_and_parameter_space():
+    """N_s = 30 samples, N_p = 48 parameters: S has rank <= 29.  The truncated
+    solve through the N_s x N_s Gram matrix equals the one through S; the
+    result lies in the row space of the centred Jacobian and solves S delta =
+    F projected on the range of S."""
+    N, M, Ns = 6, 6, 30
+    p = I.rbm_params(N, M, 5, 0.4)
+    O = oracle.jacobian(p, N, M, I.random_configs(Ns, N, 9))
+    S = oracle.qgt_dense(O)
+    F = oracle.force(O, np.random.default_rng(6).normal(size=Ns))
+    d1 = oracle.solve_svd(S, F, 0.0, 1e-10)
+    d2 = oracle.solve_svd_samplespace(O, F, 1e-10)
+    assert np.linalg.norm(d1 - d2) < 1e-8 * np.linalg.norm(d1)
+    dJ = O - O.mean(axis=0)
+    P = np.linalg.pinv(dJ, rcond=1e-10) @ dJ  # projector on the row space
+    assert np.linalg.norm(P @ d1 - d1) < 1e-8 * np.linalg.norm(d1)
+    assert np.linalg.norm(S @ d1 - P @ F) < 1e-8 * np.linalg.norm(F)
+
+
 def test_sr_is_projected_imaginary_time_step():
     """SR (Eq. eq:stochastic-reconfiguration, real case) is the least-squares
     projection of the imaginary-time step (H - E) psi onto the tangent space
