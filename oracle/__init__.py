@@ -17,7 +17,10 @@ Layout:
                diagonalisation from Kronecker products of Pauli matrices;
   symm.py      the symmetric RBM (RBMSymm, Sec. 5): ln psi and
                log-derivatives over a site-permutation group, SR step
-               through the equal plain RBM with tied parameters.
+               through the equal plain RBM with tied parameters;
+  holo.py      the complex holomorphic RBM, its force and QGT (exact or
+               sampled) and the TDVP equation of motion with Euler and Heun
+               steps (Sec. 4.3), in complex128.
 
 Parity pins are in tests/test_oracle_*.py.  A function without an external
 pin would say "parity unpinned" in its docstring; none does.
