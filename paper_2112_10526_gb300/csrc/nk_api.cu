@@ -936,7 +936,7 @@ nk_status nk_sr_step(nk_ctx *ctx, nk_rbm *rbm, const nk_ham *ham, nk_chains *cha
     // The Hamiltonian rule of the Ising model draws one of the N single flips
     // uniformly: the local rule.  For NK_HEIS it moves along the edges with a
     // nonzero coupling (the next-nearest class drops out when J2 = 0).
-    const int rule = cfg->rule == NK_RULE_HAMILTONIAN && ham->kind == NK_TFIM ? NK_RULE_LOCAL : cfg->rule;
+    const int rule = nk::effective_rule(cfg->rule, ham->kind);
     const int E_rule = rule == NK_RULE_HAMILTONIAN && ham->J2 == 0.0 ? E - ham->n_edges2 : E;
     const bool site = rule == NK_RULE_LOCAL || ham->kind == NK_TFIM;
     const bool edge = rule != NK_RULE_LOCAL || ham->kind == NK_HEIS;

@@ -107,6 +107,13 @@ struct ElocArgs {
     int E2;
 };
 
+// The rule NK_RULE_HAMILTONIAN becomes for a Hamiltonian kind: the Ising
+// model's connected configurations are the N single flips, drawn uniformly,
+// which is the local rule.
+inline int effective_rule(int rule, int ham_kind) {
+    return rule == NK_RULE_HAMILTONIAN && ham_kind == NK_TFIM ? NK_RULE_LOCAL : rule;
+}
+
 // Local-energy arguments of a Hamiltonian descriptor.
 inline ElocArgs eloc_args(const nk_ham *h, const int8_t *s, int64_t Ns, double *eloc, double *t_out,
                           const double *theta_in = nullptr) {

@@ -102,7 +102,7 @@ nk_status plan_ws(nk_ctx *planner, const nk_request &r, size_t *out) {
         st = nk_sr_step(planner, &rbm, &ham, &ch, &r.cfg, nullptr, nullptr, nullptr, nullptr);
     } else {
         const int64_t Ns = (int64_t)r.n_chains * r.cfg.n_samples;
-        st = nk_metropolis_sweep(planner, &rbm, r.cfg.precision, r.cfg.rule, r.n_edges,
+        st = nk_metropolis_sweep(planner, &rbm, r.cfg.precision, nk::effective_rule(r.cfg.rule, r.ham_kind), r.n_edges,
                                  reinterpret_cast<const int32_t *>(256), r.n_chains, reinterpret_cast<int8_t *>(256),
                                  0, r.cfg.n_discard, r.cfg.n_samples, r.cfg.seed, r.cfg.stream_id,
                                  reinterpret_cast<int8_t *>(256), nullptr, nullptr, nullptr, nullptr);
@@ -160,7 +160,8 @@ void run_request(nk_server *srv, Slot &slot, Req &q) {
     nk_rbm rbm{N, M, d_params};
     nk_ham ham{r.ham_kind, r.J, r.h, r.marshall, r.n_edges, d_edges};
     if (res.status == NK_OK) {
-        nk_status s0 = nk_chains_init(slot.ctx, N, C, r.cfg.rule, r.cfg.seed, r.cfg.stream_id, d_s, st);
+        nk_status s0 = nk_chains_init(slot.ctx, N, C, nk::effective_rule(r.cfg.rule, r.ham_kind), r.cfg.seed,
+                                      r.cfg.stream_id, d_s, st);
         if (s0 != NK_OK) fail(s0);
     }
     double host_stats[16] = {0};
@@ -170,7 +171,8 @@ void run_request(nk_server *srv, Slot &slot, Req &q) {
                                   d_samples, d_eloc, st);
         if (s1 != NK_OK && s1 != NK_ERR_NOT_CONVERGED) fail(s1);
     } else if (res.status == NK_OK) {
-        nk_status s1 = nk_metropolis_sweep(slot.ctx, &rbm, r.cfg.precision, r.cfg.rule, r.n_edges, d_edges, C, d_s,
+        nk_status s1 = nk_metropolis_sweep(slot.ctx, &rbm, r.cfg.precision, nk::effective_rule(r.cfg.rule, r.ham_kind),
+                                           r.n_edges, d_edges, C, d_s,
                                            0, r.cfg.n_discard, r.cfg.n_samples, r.cfg.seed, r.cfg.stream_id,
                                            d_samples, nullptr, d_acc, nullptr, st);
         if (s1 == NK_OK) s1 = nk_local_energy(slot.ctx, &rbm, r.cfg.precision, &ham, d_samples, Ns, d_eloc, nullptr, st);

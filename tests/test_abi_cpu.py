@@ -90,3 +90,25 @@ def test_request_bytes_plan_only_without_gpu(libnk):
         pytest.skip("no CUDA driver to create the planning context")
     assert b > a > 0
     assert c >= b + 8192 * 8192 * 8
+
+
+@pytest.mark.parametrize("kind", ["expect", "sr_step"])
+def test_request_bytes_hamiltonian_rule_plans_like_its_effective_rule(libnk, kind):
+    """NK_RULE_HAMILTONIAN is the local rule for the Ising model and an
+    edge-swap rule for the Heisenberg model.  The plan-only pass (no GPU)
+    accepts it for both request kinds; an SR step of the Ising model then
+    carves no edge tables, so it plans exactly the bytes of the local rule."""
+    from paper_2112_10526_gb300 import inputs as I
+    from paper_2112_10526_gb300 import nk
+
+    def req(rule, ham, N):
+        M = 2 * N
+        cfg = nk.make_cfg(rule, "mixed", "cg", 0, 4, 0.01, 0.01, 1)
+        return nk.make_request(kind, N, M, I.rbm_params(N, M, 1), ham, 256, cfg)
+
+    tfim, heis = I.tfim_square(8), I.heis_square(8)  # E = 2N: edge tables differ in size from site tables
+    b_loc = nk.nk_request_bytes(req("local", tfim, 64))
+    if b_loc == 0:
+        pytest.skip("no CUDA driver to create the planning context")
+    assert nk.nk_request_bytes(req("hamiltonian", tfim, 64)) == b_loc
+    assert nk.nk_request_bytes(req("hamiltonian", heis, 64)) == nk.nk_request_bytes(req("exchange", heis, 64)) > 0
