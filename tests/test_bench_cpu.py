@@ -1,0 +1,55 @@
+"""Host logic of bench.py without a GPU: workload selection (including the
+@rule override), the roofline arithmetic of the reported line, and the
+descriptive config fields."""
+import pytest
+
+import bench
+
+
+def test_workloads_and_rule_override():
+    w = bench.workload("heis2d_10x10")
+    assert (w["N"], w["M"], w["chains"], w["per_chain"], w["rule"]) == (100, 200, 1024, 8, "exchange")
+    h = bench.workload("heis2d_10x10@hamiltonian")
+    assert h["rule"] == "hamiltonian" and h["name"] == "heis2d_10x10@hamiltonian" and h["M"] == 200
+    j = bench.workload("j1j2_10x10")
+    assert j["ham"]["n_edges2"] == 200 and j["ham"]["edges"].shape == (400, 2)
+    assert "J1-J2" in bench.ham_text(j["ham"]) and bench.ham_text(w["ham"]) == "heis"
+    with pytest.raises(AssertionError):
+        bench.workload("heis2d_10x10@metropolis")
+
+
+def test_roofline_of_an_alu_class():
+    """Ratio terms count one FMA and one multiply: 2 flops each, against the
+    FP32 lanes for the mixed path and the FP64 pipe for the FP64 path."""
+    prof = {"sweep": (20.0, 4, 5e11), "eloc": (5.0, 4, 1e11)}
+    rf, cls = bench.roofline(prof, 2, "mixed")
+    assert cls == "sweep" and rf["bound"] == "alu"
+    assert rf["achieved"] == pytest.approx(2 * 5e11 / 0.020 / 1e12)
+    assert rf["frac"] == pytest.approx(rf["achieved"] / bench.FP32_PEAK_TFLOPS)
+    assert rf["avg_launch_ms"] == pytest.approx(5.0)
+    rf64, _ = bench.roofline(prof, 2, "f64")
+    assert rf64["peak"] == bench.FP64_PEAK_TFLOPS
+
+
+def test_roofline_of_the_tensor_class_with_traffic():
+    """The tensor-core classes are rated against the measured sustained BF16
+    peak, and the Cholesky products carry the captured DRAM bytes per tile
+    scaled to a launch, as long as the kernel source is the captured one."""
+    tiles = 1000.0
+    prof = {"chol_update": (10.0, 5, tiles * bench.OZAKI_TILE_FLOPS), "sweep": (1.0, 1, 1.0)}
+    rf, cls = bench.roofline(prof, 1, "mixed")
+    peaks, _src = bench.measured_peaks()
+    assert cls == "chol_update" and rf["bound"] == "tensor"
+    assert rf["peak"] == peaks["bf16_tflops_sustained"]
+    assert rf["frac"] == pytest.approx(tiles * bench.OZAKI_TILE_FLOPS / 0.010 / 1e12 / rf["peak"])
+    if bench.ozaki_source_hash().startswith(bench.OZAKI_TRAFFIC["source_sha256_prefix"]):
+        assert rf["traffic"] == pytest.approx(tiles * bench.OZAKI_TRAFFIC["bytes_per_tile"] / 5)
+    else:
+        assert rf["traffic"] is None
+
+
+def test_l2_text_names_the_array_that_outgrows_l2():
+    assert "larger" in bench.l2_text("cholesky_samplespace", 8192, 200, 20300)
+    assert "SMALLER" in bench.l2_text("cholesky_samplespace", 1024, 200, 20300)
+    assert "tanh(theta)" in bench.l2_text("cg", 16384, 1600, 642000)
+    assert bench.replica_value(4, 10, 2000.0) == pytest.approx(20.0)
