@@ -380,6 +380,8 @@ typedef struct {
     const int32_t *edges;    /* HOST [E, 2], copied by nk_server_submit */
     int32_t n_chains;        /* chains start from nk_chains_init(cfg.seed, cfg.stream_id) */
     nk_sr_cfg cfg;           /* rule, precision, solver, sweeps, eps, lr, RNG stream */
+    double J2;               /* as nk_ham: coupling of the last n_edges2 edges */
+    int32_t n_edges2;        /* 0 <= n_edges2 <= n_edges (0: nearest neighbours only) */
 } nk_request;
 
 typedef struct {

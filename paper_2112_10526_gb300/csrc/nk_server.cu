@@ -95,7 +95,8 @@ nk_status plan_ws(nk_ctx *planner, const nk_request &r, size_t *out) {
     nk::set_plan_only(true);
     double *fake_d = reinterpret_cast<double *>(256);
     nk_rbm rbm{r.N, r.M, fake_d};
-    nk_ham ham{r.ham_kind, r.J, r.h, r.marshall, r.n_edges, reinterpret_cast<const int32_t *>(256)};
+    nk_ham ham{r.ham_kind, r.J, r.h, r.marshall, r.n_edges, reinterpret_cast<const int32_t *>(256), r.J2,
+               r.n_edges2};
     nk_status st;
     if (r.kind == NK_REQ_SR_STEP) {
         nk_chains ch{r.n_chains, reinterpret_cast<int8_t *>(256), 0, nullptr};
@@ -158,7 +159,7 @@ void run_request(nk_server *srv, Slot &slot, Req &q) {
             fail(NK_ERR_CUDA, "upload of the request state failed");
     }
     nk_rbm rbm{N, M, d_params};
-    nk_ham ham{r.ham_kind, r.J, r.h, r.marshall, r.n_edges, d_edges};
+    nk_ham ham{r.ham_kind, r.J, r.h, r.marshall, r.n_edges, d_edges, r.J2, r.n_edges2};
     if (res.status == NK_OK) {
         nk_status s0 = nk_chains_init(slot.ctx, N, C, nk::effective_rule(r.cfg.rule, r.ham_kind), r.cfg.seed,
                                       r.cfg.stream_id, d_s, st);
@@ -412,7 +413,7 @@ nk_status nk_server_submit(nk_server *srv, const nk_request *req, double *params
     const nk_request &r = *req;
     if (r.kind != NK_REQ_SR_STEP && r.kind != NK_REQ_EXPECT) return nk::report_error(NK_ERR_INVALID_ARG, "request kind");
     if (r.N < 1 || r.N > 4096 || r.M < 1 || r.M > 8192 || r.n_chains < 1 || r.cfg.n_samples < 1 || !r.params ||
-        r.n_edges < 1 || !r.edges)
+        r.n_edges < 1 || !r.edges || r.n_edges2 < 0 || r.n_edges2 > r.n_edges)
         return nk::report_error(NK_ERR_INVALID_ARG, "request sizes or pointers");
     auto q = std::make_unique<Req>();
     q->r = r;

@@ -77,7 +77,8 @@ class nk_request(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("N", ctypes.c_int32), ("M", ctypes.c_int32),
                 ("params", ctypes.c_void_p), ("ham_kind", ctypes.c_int32), ("J", ctypes.c_double),
                 ("h", ctypes.c_double), ("marshall", ctypes.c_int32), ("n_edges", ctypes.c_int32),
-                ("edges", ctypes.c_void_p), ("n_chains", ctypes.c_int32), ("cfg", nk_sr_cfg)]
+                ("edges", ctypes.c_void_p), ("n_chains", ctypes.c_int32), ("cfg", nk_sr_cfg),
+                ("J2", ctypes.c_double), ("n_edges2", ctypes.c_int32)]
 
 
 class nk_result(ctypes.Structure):
@@ -423,7 +424,8 @@ def make_request(kind, N, M, params, ham, n_chains, cfg):
     e = np.ascontiguousarray(ham["edges"], dtype=np.int32).reshape(-1, 2)
     req = nk_request(NK_REQ_SR_STEP if kind in ("sr_step", NK_REQ_SR_STEP) else NK_REQ_EXPECT, int(N), int(M),
                      p.ctypes.data, KIND[ham["kind"]], float(ham["J"]), float(ham.get("h", 0.0)),
-                     int(bool(ham.get("marshall", False))), int(e.shape[0]), e.ctypes.data, int(n_chains), cfg)
+                     int(bool(ham.get("marshall", False))), int(e.shape[0]), e.ctypes.data, int(n_chains), cfg,
+                     float(ham.get("J2", 0.0)), int(ham.get("n_edges2", 0)))
     req._keep = (p, e)
     return req
 

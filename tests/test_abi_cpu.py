@@ -112,3 +112,21 @@ def test_request_bytes_hamiltonian_rule_plans_like_its_effective_rule(libnk, kin
         pytest.skip("no CUDA driver to create the planning context")
     assert nk.nk_request_bytes(req("hamiltonian", tfim, 64)) == b_loc
     assert nk.nk_request_bytes(req("hamiltonian", heis, 64)) == nk.nk_request_bytes(req("exchange", heis, 64)) > 0
+
+
+def test_request_bytes_plans_a_j1j2_request(libnk):
+    """A serving request carries the second edge class (J2, n_edges2) of the
+    J1-J2 model; the plan-only pass sizes it with both classes."""
+    from paper_2112_10526_gb300 import inputs as I
+    from paper_2112_10526_gb300 import nk
+
+    N, M = 100, 200
+    cfg = nk.make_cfg("exchange", "mixed", "cholesky_samplespace", 0, 1, 0.01, 0.02, 6)
+    ham = I.j1j2_square(10)
+    r = nk.make_request("sr_step", N, M, I.rbm_params(N, M, 6), ham, 1024, cfg)
+    assert (r.J2, r.n_edges2, r.n_edges) == (0.5, 200, 400)
+    b = nk.nk_request_bytes(r)
+    if b == 0:
+        pytest.skip("no CUDA driver to create the planning context")
+    r1 = nk.make_request("sr_step", N, M, I.rbm_params(N, M, 6), I.heis_square(10), 1024, cfg)
+    assert b > nk.nk_request_bytes(r1) > 0  # twice the edge tables
