@@ -18,7 +18,8 @@ Layout:
   symm.py      the symmetric RBM (RBMSymm, Sec. 5): ln psi and
                log-derivatives over a site-permutation group, SR step
                through the equal plain RBM with tied parameters;
-  holo.py      the complex holomorphic RBM, its force and QGT (exact or
+  holo.py      the complex holomorphic RBM, its Metropolis chains on the
+               real oracle's Philox streams, its force and QGT (exact or
                sampled) and the TDVP equation of motion with Euler and Heun
                steps (Sec. 4.3), in complex128.
 

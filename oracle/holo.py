@@ -22,6 +22,7 @@ import itertools
 
 import numpy as np
 
+from . import core as _core
 from . import exact as _exact
 
 
@@ -175,3 +176,46 @@ def brute_force_marginal(params, N, M, s):
     for h in itertools.product([-1.0, 1.0], repeat=M):
         out += np.exp(s @ a + th @ np.array(h))
     return out / 2 ** M
+
+
+def metropolis(params, N, M, rule, edges, s, sweep0, n_discard, n_samples, seed, stream=0):
+    """Metropolis-Hastings chains on |psi|^2 of the complex RBM (Sec. 3.4), on
+    the Philox streams of the real-RBM oracle: proposal p of sweep w of chain
+    c draws the block ((sweep0 + w) N + p, c, stream, 0) with key (seed, 0);
+    the site (local) or edge (exchange) is floor(hi32(y0) n / 2^32), u =
+    ((y1 >> 11) + 1/2) 2^-53, and the move is taken iff
+    ln u < 2 Re[ln psi(s') - ln psi(s)] (|psi(s')/psi(s)|^2 = e^{2 Re dlnpsi}).
+    An exchange proposal on an edge with equal spins is not a move.  Each
+    ratio comes from two full evaluations of ln psi.  Returns the new states
+    and the samples [C, n_samples, N]."""
+    s = np.array(s, dtype=np.int8).reshape(-1, N)
+    C = s.shape[0]
+    E = 0 if edges is None else np.asarray(edges).reshape(-1, 2).shape[0]
+    edges = None if edges is None else np.asarray(edges).reshape(-1, 2)
+    key = np.array([seed, 0], dtype=np.uint64)
+    samples = np.empty((C, n_samples, N), dtype=np.int8)
+    for w in range(n_discard + n_samples):
+        for p in range(N):
+            q = (sweep0 + w) * N + p
+            lp = logpsi(params, N, M, s)
+            sp = s.copy()
+            move = np.ones(C, dtype=bool)
+            lu = np.empty(C)
+            for c in range(C):
+                y = _core.philox4x64_10(np.array([q, c, stream, 0], dtype=np.uint64), key)
+                n = N if rule == "local" else E
+                r = int((int(y[0]) >> 32) * n >> 32)
+                lu[c] = np.log(((int(y[1]) >> 11) + 0.5) * 2.0 ** -53)
+                if rule == "local":
+                    sp[c, r] = -sp[c, r]
+                else:
+                    i, k = edges[r]
+                    if s[c, i] == s[c, k]:
+                        move[c] = False
+                    else:
+                        sp[c, i], sp[c, k] = -sp[c, i], -sp[c, k]
+            take = move & (lu < 2.0 * (logpsi(params, N, M, sp) - lp).real)
+            s[take] = sp[take]
+        if w >= n_discard:
+            samples[:, w - n_discard] = s
+    return s, samples

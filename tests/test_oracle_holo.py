@@ -195,3 +195,32 @@ def test_real_time_energy_is_conserved_to_second_order():
         drift.append(abs(H.exact_moments(q, N, M, ham)[2].real - E0))
     assert drift[0] / drift[1] > 3.5, drift
     assert drift[1] < 2e-3, drift
+
+
+@pytest.mark.parametrize("rule", ["local", "exchange"])
+def test_complex_sampler_equals_the_c_oracle_on_real_parameters(rule):
+    """On real parameters the complex sampler draws the same Philox streams
+    and takes the same decisions as the real-RBM C oracle: identical chains."""
+    N, M = 8, 8
+    pr = I.rbm_params(N, M, 3, 0.5)
+    s0 = oracle.chain_init(N, 6, rule, 5, 1)
+    edges = None if rule == "local" else I.chain_edges(N)
+    st, sm = H.metropolis(pr, N, M, rule, edges, s0, 2, 3, 4, 5, 1)
+    ref = oracle.metropolis(pr, N, M, rule, edges, s0, 2, 3, 4, 5, 1)
+    np.testing.assert_array_equal(sm, ref["samples"])
+    np.testing.assert_array_equal(st, ref["state"])
+
+
+def test_complex_sampler_histogram_against_exact():
+    """Complex parameters: the histogram of 200 chains x 300 sweeps (local
+    rule, N = 8) matches |psi|^2 (TV < 0.03; i.i.d. draws of the same size
+    give about 0.012), not |psi| (TV 0.33 between the two here)."""
+    N, M = 8, 6
+    p = _params(N, M, 21, 0.4)
+    P = np.abs(H.exact_state(p, N, M)) ** 2
+    s0 = oracle.chain_init(N, 200, "local", 9, 0)
+    _st, sm = H.metropolis(p, N, M, "local", None, s0, 0, 10, 300, 9, 0)
+    x = sm.reshape(-1, N)
+    idx = ((x < 0).astype(np.int64) * (1 << (N - 1 - np.arange(N)))).sum(axis=1)
+    counts = np.bincount(idx, minlength=2 ** N) / idx.size
+    assert 0.5 * np.abs(counts - P).sum() < 0.03
