@@ -224,3 +224,36 @@ def test_complex_sampler_histogram_against_exact():
     idx = ((x < 0).astype(np.int64) * (1 << (N - 1 - np.arange(N)))).sum(axis=1)
     counts = np.bincount(idx, minlength=2 ** N) / idx.size
     assert 0.5 * np.abs(counts - P).sum() < 0.03
+
+
+def test_sample_moments_converge_to_the_exact_moments():
+    """Force, QGT and energy as sample means (Sec. 3.3) over 2e5 i.i.d. draws
+    from the exact |psi|^2 agree with the exact moments within the sampling
+    error (energy within 4 sigma; force and QGT within 5 % in norm)."""
+    N, M = 6, 3
+    ham = I.tfim_chain(N, 1.0, 0.8)
+    p = _params(N, M, 23, 0.3)
+    f_ex, G_ex, e_ex = H.exact_moments(p, N, M, ham)
+    P = np.abs(H.exact_state(p, N, M)) ** 2
+    basis = exact.basis(N)
+    idx = np.random.default_rng(4).choice(P.size, size=200000, p=P / P.sum())
+    # evaluate per distinct configuration, then weight by the counts
+    counts = np.bincount(idx, minlength=P.size)
+    keep = counts > 0
+    w = counts[keep] / idx.size
+    O = H.jacobian(p, N, M, basis[keep])
+    el = H.local_energy(p, N, M, ham, basis[keep])
+    f_s, G_s, e_s = H._moments(O, el, w)
+    sigma = np.sqrt(np.sum(w * np.abs(el - e_s) ** 2) / idx.size)
+    assert abs(e_s - e_ex) < 4 * sigma
+    assert np.linalg.norm(f_s - f_ex) < 0.05 * np.linalg.norm(f_ex)
+    assert np.linalg.norm(G_s - G_ex) < 0.05 * np.linalg.norm(G_ex)
+    # the sample-mean entry point gives the same numbers on the repeated draws
+    sub = basis[idx[:2000]]
+    f1, G1, e1 = H.sample_moments(p, N, M, ham, sub)
+    c = np.bincount(idx[:2000], minlength=P.size)
+    k = c > 0
+    f2, G2, e2 = H._moments(H.jacobian(p, N, M, basis[k]), H.local_energy(p, N, M, ham, basis[k]), c[k] / 2000)
+    np.testing.assert_allclose(f1, f2, rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(G1, G2, rtol=1e-10, atol=1e-12)
+    assert abs(e1 - e2) < 1e-10
