@@ -74,7 +74,6 @@ def test_request_bytes_plan_only_without_gpu(libnk):
     """The admission estimate is a plan-only pass: it needs no GPU, grows
     with the sample count and counts the Ns x Ns factor of the sample-space
     solve."""
-    import numpy as np
     from paper_2112_10526_gb300 import inputs as I
     from paper_2112_10526_gb300 import nk
 

@@ -10,7 +10,7 @@ from paper_2112_10526_gb300 import autograd as ag
 from paper_2112_10526_gb300 import inputs as I
 from paper_2112_10526_gb300 import nk
 
-from gpu_util import cu, dev, vec_rel_err
+from gpu_util import cu, vec_rel_err
 
 pytestmark = pytest.mark.gpu
 
