@@ -219,3 +219,25 @@ def metropolis(params, N, M, rule, edges, s, sweep0, n_discard, n_samples, seed,
         if w >= n_discard:
             samples[:, w - n_discard] = s
     return s, samples
+
+
+def tvmc_rhs(params, N, M, ham, rule, edges, chains, sweep0, n_discard, n_samples, seed, stream=0,
+             gamma=-1j, diag_shift=0.0, rcond=None):
+    """One evaluation of the t-VMC equation of motion (Sec. 4.3): sample the
+    chains, form the force and QGT as sample means, solve Eq. eq:tvmc.
+    Returns (theta_dot, new chain states, sample-mean energy)."""
+    state, samples = metropolis(params, N, M, rule, edges, chains, sweep0, n_discard, n_samples, seed, stream)
+    f, G, e = sample_moments(params, N, M, ham, samples.reshape(-1, N))
+    return theta_dot(G, f, gamma, diag_shift, rcond), state, e
+
+
+def tvmc_heun(params, N, M, ham, rule, edges, chains, sweep0, n_samples, seed, dt, stream=0, gamma=-1j,
+              diag_shift=0.0, rcond=None):
+    """One Heun step of t-VMC: each of the two slopes is evaluated on fresh
+    samples (the chains continue; the second slope draws the sweeps after the
+    first).  Returns (new parameters, chain states, next sweep index)."""
+    k1, chains, _e = tvmc_rhs(params, N, M, ham, rule, edges, chains, sweep0, 0, n_samples, seed, stream, gamma,
+                              diag_shift, rcond)
+    k2, chains, _e = tvmc_rhs(params + dt * k1, N, M, ham, rule, edges, chains, sweep0 + n_samples, 0, n_samples,
+                              seed, stream, gamma, diag_shift, rcond)
+    return params + 0.5 * dt * (k1 + k2), chains, sweep0 + 2 * n_samples
