@@ -306,7 +306,11 @@ typedef struct {
 } nk_chains;
 
 typedef struct {
-    int32_t rule;        /* NK_RULE_* */
+    int32_t rule;        /* NK_RULE_*; in nk_sr_step NK_RULE_HAMILTONIAN is the
+                            local rule for NK_TFIM (its connected configurations
+                            are the N single flips) and swaps across the
+                            Hamiltonian's edges for NK_HEIS, without the
+                            next-nearest class when J2 = 0 */
     int32_t precision;   /* NK_F64 or NK_MIXED */
     int32_t solver;      /* NK_SOLVER_* */
     int32_t n_discard;   /* sweeps discarded before sampling */
