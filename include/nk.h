@@ -188,19 +188,30 @@ nk_status nk_local_energy(nk_ctx *ctx, const nk_rbm *rbm, int32_t precision, con
                           void *stream);
 
 /*
- * Local energies exactly as nk_local_energy, for callers that cannot let a
- * library allocate device memory (their HBM is owned by another allocator,
- * or they cannot afford cudaMalloc's device-wide synchronisation).  The paper
- * has no counterpart; this is a property of the library, not of the method.
+ * Local energies as nk_local_energy, for callers that cannot let a library
+ * allocate device memory (their HBM is owned by another allocator, or they
+ * cannot afford cudaMalloc's device-wide synchronisation).  The paper has no
+ * counterpart; this is a property of the library, not of the method.
  * No context and no allocation: the flip-ratio tables live in one fixed
  * __device__ array of NK_NOALLOC_SCRATCH_BYTES compiled into libnk.so, held
  * by every GPU that loads the library until the process exits.  Sizes whose
  * tables do not fit (about 8 (3 N M + N) bytes for NK_TFIM, 8 (N M + 2 E M
  * + E) for NK_HEIS in FP64, half the tau part in NK_MIXED) return
- * NK_ERR_INVALID_ARG.  The first call on each device (with it current) looks
- * up the array's device address; make it before any stream capture.  All
- * calls share the array: calls that overlap on the GPU race, so serialise
- * them.  Runs on the current device; arguments as nk_local_energy.
+ * NK_ERR_INVALID_ARG.
+ *   NK_F64: the same kernels on the same tables as nk_local_energy, so the
+ *   results are bit-identical.  NK_MIXED: there is no room for the batch's
+ *   hidden activations, so the local-energy kernel rebuilds theta = b + W s
+ *   per sample in FP64 instead of taking the tensor-core product; the
+ *   results agree with nk_local_energy within the mixed tolerance (1e-4
+ *   relative per sample), not bit for bit.
+ * The first call on each device, with it current, looks up the array's
+ * device address; the address is cached per device and CUDA context and
+ * looked up again when the context changes (after cudaDeviceReset, say).
+ * Make the first call, and the first after a reset, before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU race,
+ * so serialise them.  Runs on the current device; every array must be
+ * memory of that device (or managed memory), else NK_ERR_INVALID_ARG.
+ * Arguments as nk_local_energy.
  */
 #define NK_NOALLOC_SCRATCH_BYTES (8u << 20)
 nk_status nk_local_energy_noalloc(const nk_rbm *rbm, int32_t precision, const nk_ham *ham,

@@ -12,9 +12,14 @@
 // The array is a file-scope __device__ variable of kNoallocScratchBytes.
 // Every GPU that loads libnk.so holds it until the process exits.  Host code
 // cannot use the array's name as a device address (in host code it names a
-// host-side stand-in), so the device address is looked up once per device
-// with cudaGetSymbolAddress, on the first call made with that device
-// current, and cached.  Make that first call before any stream capture.
+// host-side stand-in), so the device address is looked up with
+// cudaGetSymbolAddress on the first call made with a device current, and
+// cached per device together with the identity of the CUDA context it was
+// looked up in.  A call made in another context on that device (after
+// cudaDeviceReset, a primary-context reset, or with a driver-API context
+// current) looks the address up again, since the module, and the array with
+// it, may then live at another address.  Make the first call on a device,
+// and the first call after such a reset, before any stream capture.
 //
 // All calls share the array and it keeps the last call's contents.  Every
 // table a call reads is fully written by that same call first, so nothing
@@ -35,37 +40,78 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[NK_NOALLOC_SCRA
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-char *g_scratch_dev[kMaxDevices] = {};
+struct ScratchSlot {
+    unsigned long long ctx_id;  // identity of the context the address belongs to (0: none yet)
+    char *addr;
+};
+ScratchSlot g_scratch_dev[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device (set-up on the
-// first call per device).
-nk_status scratch_address(char **out) {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return nk::report_error(NK_ERR_CUDA, cudaGetErrorString(e));
+// The driver's cuCtxGetCurrent / cuCtxGetId, reached through the runtime so
+// that the library does not link libcuda directly.
+typedef int (*CtxGetCurrentFn)(void **);
+typedef int (*CtxGetIdFn)(void *, unsigned long long *);
+
+// Identity of the context current on this thread (0 if none can be read).
+unsigned long long current_ctx_id() {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(f);
+        cudaGetLastError();
+    });
+    if (!get_current || !get_id) return 0;
+    void *ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != 0 || !ctx) return 0;
+    if (get_id(ctx, &id) != 0) return 0;
+    return id;
+}
+
+// Device address of the scratch array in the context current on this thread
+// (set-up on the first call per device and again whenever that context
+// changes).
+nk_status scratch_address(int dev, char **out) {
     if (dev < 0 || dev >= kMaxDevices) return nk::report_error(NK_ERR_INVALID_ARG, "device ordinal out of range");
+    unsigned long long id = current_ctx_id();
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_dev[dev]) {
+    ScratchSlot &slot = g_scratch_dev[dev];
+    if (id == 0 || slot.ctx_id != id || !slot.addr) {
         void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        // binds the device's primary context to this thread if none is current
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) {
             cudaGetLastError();
             return nk::report_error(NK_ERR_CUDA, "cudaGetSymbolAddress(scratch) failed");
         }
-        g_scratch_dev[dev] = static_cast<char *>(p);
+        if (id == 0) id = current_ctx_id();
+        slot.ctx_id = id;  // 0 (context identity unreadable): looked up again on every call
+        slot.addr = static_cast<char *>(p);
     }
-    *out = g_scratch_dev[dev];
+    *out = slot.addr;
     return NK_OK;
 }
 
-bool on_device(const void *p) {
+// A device (or managed) pointer that the kernels on device `dev` may use:
+// memory of another GPU is rejected, since this entry point launches on the
+// current device and peer access is not assumed.
+bool on_device(const void *p, int dev) {
     if (!p) return false;
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 // Bump carving of the scratch array (base == nullptr counts bytes only).
@@ -103,7 +149,7 @@ size_t plan_tables(Bump &b, nk::Tables<R> &t, const nk_rbm *rbm, const nk_ham *h
 }
 
 template <typename R>
-nk_status run(const nk_rbm *rbm, const nk_ham *ham, const int8_t *s, int64_t Ns, double *eloc,
+nk_status run(int dev, const nk_rbm *rbm, const nk_ham *ham, const int8_t *s, int64_t Ns, double *eloc,
               double *t_out, cudaStream_t st) {
     nk::Tables<R> t{};
     Bump count{nullptr};
@@ -117,7 +163,7 @@ nk_status run(const nk_rbm *rbm, const nk_ham *ham, const int8_t *s, int64_t Ns,
         return nk::report_error(NK_ERR_INVALID_ARG, msg);
     }
     char *base = nullptr;
-    nk_status stt = scratch_address(&base);
+    nk_status stt = scratch_address(dev, &base);
     if (stt != NK_OK) return stt;
     Bump real{base};
     plan_tables(real, t, rbm, ham);
@@ -149,10 +195,14 @@ extern "C" nk_status nk_local_energy_noalloc(const nk_rbm *rbm, int32_t precisio
         return nk::report_error(NK_ERR_INVALID_ARG, "ham->n_edges2 out of [0, n_edges]");
     if (Ns < 0) return nk::report_error(NK_ERR_INVALID_ARG, "Ns < 0");
     if (Ns == 0) return NK_OK;
-    if (!on_device(rbm->params) || !on_device(ham->edges) || !on_device(s) || !on_device(eloc_out) ||
-        (t_out && !on_device(t_out)))
-        return nk::report_error(NK_ERR_INVALID_ARG, "arrays must be device pointers");
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return nk::report_error(NK_ERR_CUDA, cudaGetErrorString(e));
+    if (!on_device(rbm->params, dev) || !on_device(ham->edges, dev) || !on_device(s, dev) ||
+        !on_device(eloc_out, dev) || (t_out && !on_device(t_out, dev)))
+        return nk::report_error(NK_ERR_INVALID_ARG,
+                                "arrays must be device pointers of the current device");
     cudaStream_t st = (cudaStream_t)stream;
-    if (precision == NK_F64) return run<double>(rbm, ham, s, Ns, eloc_out, t_out, st);
-    return run<float>(rbm, ham, s, Ns, eloc_out, t_out, st);
+    if (precision == NK_F64) return run<double>(dev, rbm, ham, s, Ns, eloc_out, t_out, st);
+    return run<float>(dev, rbm, ham, s, Ns, eloc_out, t_out, st);
 }
