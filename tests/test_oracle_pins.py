@@ -406,6 +406,51 @@ def test_chain_init_rules():
     assert len({tuple(r) for r in e}) == 40
 
 
+def _sz0_histogram(rows, N):
+    """Counts of each S_z = 0 configuration of N sites among `rows`, in the
+    order of itertools.combinations of the up sites."""
+    index = {c: k for k, c in enumerate(itertools.combinations(range(N), N // 2))}
+    counts = np.zeros(len(index))
+    for r in rows:
+        counts[index[tuple(np.flatnonzero(r == 1))]] += 1
+    return counts
+
+
+def _chi2_pvalue(counts):
+    from scipy.stats import chi2
+    exp = counts.sum() / counts.size
+    return float(chi2.sf(((counts - exp) ** 2 / exp).sum(), counts.size - 1))
+
+
+def test_chain_init_sz0_is_uniform_over_the_sector():
+    """The S_z = 0 initial states (random_state of Sec. 2.1 restricted to the
+    zero-magnetisation sector) must be uniform over the C(6, 3) = 20
+    configurations: a chi-square test over 40000 chains.  The same test,
+    run on a shuffle with the plausible off-by-one (the swap partner drawn
+    from [0, i) instead of [0, i]: Sattolo's single-cycle shuffle, which can
+    never return the starting order), must reject it."""
+    N, C = 6, 40000
+    rows = oracle.chain_init(N, C, "exchange", seed=31, stream=5)
+    assert (rows.sum(axis=1) == 0).all()
+    counts = _sz0_histogram(rows, N)
+    assert counts.min() > 0
+    assert _chi2_pvalue(counts) > 1e-6
+
+    def shuffled(c, partner_range):
+        r = np.array([1] * (N // 2) + [-1] * (N // 2), dtype=np.int8)
+        for i in range(N - 1, 0, -1):
+            y = oracle.philox4x64_10(np.array([i, c, 5, 1], dtype=np.uint64), np.array([31, 0], dtype=np.uint64))
+            j = (int(y[0]) >> 32) * partner_range(i) >> 32
+            r[i], r[j] = r[j], r[i]
+        return r
+
+    bad = np.array([shuffled(c, lambda i: i) for c in range(4000)])
+    assert _chi2_pvalue(_sz0_histogram(bad, N)) < 1e-6
+    # with the inclusive range the hand-written shuffle is the oracle's own
+    good = np.array([shuffled(c, lambda i: i + 1) for c in range(200)])
+    np.testing.assert_array_equal(good, rows[:200])
+
+
 def test_metropolis_local_tv_against_exact():
     """Histogram of single-flip Metropolis samples against exact |psi|^2 at
     N = 12 (1e6 samples, TV < 0.01).  Parameters have sigma = 0.3 so that the
