@@ -32,10 +32,16 @@ RULE = {"local": 0, "exchange": 1, "hamiltonian": 2}
 
 
 def build(force: bool = False) -> str:
-    """Compile nk_oracle.c into liboracle.so with plain gcc (no fast-math)."""
+    """Compile nk_oracle.c into liboracle.so with plain gcc (no fast-math),
+    with OpenMP over independent configurations where gcc supports it (the
+    thread count, OMP_NUM_THREADS, does not change any result)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        try:
+            subprocess.check_call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -51,11 +57,12 @@ def _load():
     lib.oc_logpsi.argtypes = [i32, i32, P, P, i64, P]
     lib.oc_local_energy.argtypes = [i32, i32, P, i32, f64, f64, f64, i32, i32, i32, P, P, i64, P]
     lib.oc_jacobian.argtypes = [i32, i32, P, P, i64, P]
+    lib.oc_jacobian_cols.argtypes = [i32, i32, P, P, i64, i32, P, P]
     lib.oc_philox4x64_10.argtypes = [P, P, P]
     lib.oc_chain_init.argtypes = [i32, i32, i32, u64, u32, P]
     lib.oc_metropolis.argtypes = [i32, i32, P, i32, i32, P, i32, P, i64, i32, i32, u64, u32,
                                   P, P, P, P, P, P]
-    for f in ("oc_logpsi", "oc_local_energy", "oc_jacobian", "oc_philox4x64_10",
+    for f in ("oc_logpsi", "oc_local_energy", "oc_jacobian", "oc_jacobian_cols", "oc_philox4x64_10",
               "oc_chain_init", "oc_metropolis"):
         getattr(lib, f).restype = None
     _lib = lib
@@ -121,6 +128,20 @@ def jacobian(params, N, M, s):
     out = np.empty((s.shape[0], n_params(N, M)), dtype=np.float64)
     pa = _par(params)
     lib.oc_jacobian(N, M, _p(pa), _p(s), s.shape[0], _p(out))
+    return out
+
+
+def jacobian_cols(params, N, M, s, cols):
+    """Columns `cols` of the same Jacobian, J[:, cols] (Eq.
+    eq:log-derivative-O): for very large N_p, where the full rows do not fit
+    in memory."""
+    lib = _load()
+    s = _cfg(s, N)
+    cols = np.ascontiguousarray(cols, dtype=np.int64).ravel()
+    assert cols.size == 0 or (cols.min() >= 0 and cols.max() < n_params(N, M))
+    out = np.empty((s.shape[0], cols.size), dtype=np.float64)
+    pa = _par(params)
+    lib.oc_jacobian_cols(N, M, _p(pa), _p(s), s.shape[0], cols.size, _p(cols), _p(out))
     return out
 
 

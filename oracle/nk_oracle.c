@@ -8,6 +8,11 @@
  *
  * Everything here is deliberately slow and written as the definitions read:
  * full FP64, one configuration at a time, no blocking, no identities.
+ * Configurations (and Metropolis chains) are independent of one another, so
+ * when the file is compiled with OpenMP the loop over them may be split over
+ * host threads (OMP_NUM_THREADS); each one is still computed by one thread
+ * in the order written here, so the results do not depend on the thread
+ * count.
  *
  * Parameter vector layout (NetKet 3, Sec. 3.2 "Defining the variational
  * ansatz", Table "tab:nk.models", RBM entry):
@@ -63,10 +68,14 @@ static double oc_logpsi_one(int N, int M, const double *params,
 void oc_logpsi(int N, int M, const double *params, const int8_t *s,
                int64_t B, double *out)
 {
-    double *theta = (double *)malloc(sizeof(double) * (size_t)(M > 0 ? M : 1));
-    for (int64_t k = 0; k < B; ++k)
-        out[k] = oc_logpsi_one(N, M, params, s + (size_t)k * N, theta);
-    free(theta);
+#pragma omp parallel
+    {
+        double *theta = (double *)malloc(sizeof(double) * (size_t)(M > 0 ? M : 1));
+#pragma omp for schedule(static)
+        for (int64_t k = 0; k < B; ++k)
+            out[k] = oc_logpsi_one(N, M, params, s + (size_t)k * N, theta);
+        free(theta);
+    }
 }
 
 /* ln psi(s') - ln psi(s) when the sites in `sites` (n of them) are flipped,
@@ -118,8 +127,11 @@ void oc_local_energy(int N, int M, const double *params, int kind, double J,
                      const int32_t *edges, const int8_t *s, int64_t B,
                      double *out)
 {
-    double *theta = (double *)malloc(sizeof(double) * (size_t)(M > 0 ? M : 1));
     const int E1 = E - E2;
+#pragma omp parallel
+    {
+    double *theta = (double *)malloc(sizeof(double) * (size_t)(M > 0 ? M : 1));
+#pragma omp for schedule(dynamic, 4)
     for (int64_t k = 0; k < B; ++k) {
         const int8_t *sk = s + (size_t)k * N;
         oc_hidden(N, M, params, sk, theta);
@@ -145,6 +157,7 @@ void oc_local_energy(int N, int M, const double *params, int kind, double J,
         out[k] = e;
     }
     free(theta);
+    }
 }
 
 /*
@@ -157,7 +170,10 @@ void oc_jacobian(int N, int M, const double *params, const int8_t *s,
                  int64_t B, double *O)
 {
     size_t Np = (size_t)N + M + (size_t)M * N;
+#pragma omp parallel
+    {
     double *theta = (double *)malloc(sizeof(double) * (size_t)(M > 0 ? M : 1));
+#pragma omp for schedule(static)
     for (int64_t k = 0; k < B; ++k) {
         const int8_t *sk = s + (size_t)k * N;
         double *row = O + (size_t)k * Np;
@@ -171,6 +187,39 @@ void oc_jacobian(int N, int M, const double *params, const int8_t *s,
         }
     }
     free(theta);
+    }
+}
+
+/*
+ * Selected columns of the same Jacobian: O[k][c] = O_{cols[c]}(s_k) for
+ * every configuration k, with the derivatives of Eq. "eq:log-derivative-O"
+ * written out as above.  theta_j is formed, by its definition
+ * b_j + sum_i W_ji s_i, only for the hidden units the columns need.
+ * Output O: [B, ncols].
+ */
+void oc_jacobian_cols(int N, int M, const double *params, const int8_t *s,
+                      int64_t B, int ncols, const int64_t *cols, double *O)
+{
+    const double *b = params + N;
+    const double *W = params + N + M;
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < B; ++k) {
+        const int8_t *sk = s + (size_t)k * N;
+        for (int c = 0; c < ncols; ++c) {
+            int64_t q = cols[c];
+            double v;
+            if (q < N) {
+                v = (double)sk[q];
+            } else {
+                int64_t j = q < N + M ? q - N : (q - N - M) / N;
+                double th = b[j];
+                for (int i = 0; i < N; ++i) th += W[(size_t)j * N + i] * (double)sk[i];
+                v = tanh(th);
+                if (q >= N + M) v *= (double)sk[(q - N - M) % N];
+            }
+            O[(size_t)k * ncols + c] = v;
+        }
+    }
 }
 
 /*
@@ -311,10 +360,13 @@ void oc_metropolis(int N, int M, const double *params, int rule, int E,
                    int64_t *n_accepted)
 {
     const double *W = params + N + M;
+    int n_sweeps = n_discard + n_samples;
+#pragma omp parallel
+    {
     double *theta = (double *)malloc(sizeof(double) * (size_t)(M > 0 ? M : 1));
     double *scratch = (double *)malloc(sizeof(double) * (size_t)(M > 0 ? M : 1));
-    int n_sweeps = n_discard + n_samples;
     uint64_t y[4];
+#pragma omp for schedule(dynamic, 1)
     for (int c = 0; c < C; ++c) {
         int8_t *sc = s + (size_t)c * N;
         int64_t acc = 0;
@@ -387,4 +439,5 @@ void oc_metropolis(int N, int M, const double *params, int rule, int E,
     }
     free(theta);
     free(scratch);
+    }
 }

@@ -224,6 +224,45 @@ def test_jacobian_central_differences():
         np.testing.assert_allclose(O[:, kk], fd, rtol=1e-6, atol=1e-9)
 
 
+def test_jacobian_columns_central_differences_and_thread_count():
+    """The column-restricted Jacobian against central differences of ln psi
+    (step 1e-6, relative 1e-6) for a ragged set of columns of every block
+    (a, b, W), and equal, bit for bit, to the same columns of the full rows;
+    the full rows and the local energies do not depend on the number of
+    OpenMP threads (each configuration is one thread's work)."""
+    N, M = 7, 5
+    p = I.rbm_params(N, M, 22, 0.5)
+    s = I.random_configs(9, N, 5)
+    cols = np.array([0, 6, N, N + 4, N + M, N + M + 3, N + M + 2 * N + 6, N + M + M * N - 1, N + 2])
+    Oc = oracle.jacobian_cols(p, N, M, s, cols)
+    h = 1e-6
+    for c, kk in enumerate(cols):
+        pp, pm = p.copy(), p.copy()
+        pp[kk] += h
+        pm[kk] -= h
+        fd = (oracle.logpsi(pp, N, M, s) - oracle.logpsi(pm, N, M, s)) / (2 * h)
+        np.testing.assert_allclose(Oc[:, c], fd, rtol=1e-6, atol=1e-9)
+    np.testing.assert_array_equal(Oc, oracle.jacobian(p, N, M, s)[:, cols])
+    assert oracle.jacobian_cols(p, N, M, s, []).shape == (9, 0)
+    import subprocess
+    import sys
+    code = ("import hashlib, numpy as np, oracle; from paper_2112_10526_gb300 import inputs as I; "
+            "N, M = 12, 24; p = I.rbm_params(N, M, 3, 0.3); ham = I.heis_chain(N); "
+            "s0 = oracle.chain_init(N, 37, 'exchange', 3); "
+            "r = oracle.metropolis(p, N, M, 'exchange', ham['edges'], s0, 0, 2, 3, 3); "
+            "x = r['samples'].reshape(-1, N); "
+            "e = oracle.local_energy(p, N, M, ham, x); O = oracle.jacobian(p, N, M, x); "
+            "print(hashlib.sha256(b''.join(a.tobytes() for a in (r['samples'], r['decisions'], r['margin'], "
+            "r['logpsi'], e, O, oracle.logpsi(p, N, M, x)))).hexdigest())")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    outs = set()
+    for threads in ("1", "5"):
+        env = dict(os.environ, OMP_NUM_THREADS=threads, PYTHONPATH=root)
+        outs.add(subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                                check=True, cwd=root).stdout.strip())
+    assert len(outs) == 1
+
+
 def test_force_is_gradient_of_exact_energy():
     """f = 2 Re Cov[O, E_loc] is the gradient of <H> (Eqs. eq:force VMC,
     eq:VMC gradient:real), checked by central differences of the exact
