@@ -222,12 +222,23 @@ def test_prof_trace_orders_the_bracketed_segments(ctx):
     assert nk.lib().nk_prof_trace(1, None, None, None, ctypes.byref(ctypes.c_int32())) == -1
 
 
+def _oracle_jv(p, N, M, s, v, chunk):
+    """J v from the oracle's Jacobian rows (Eq. eq:log-derivative-O), a
+    chunk of samples at a time so that the rows fit in memory."""
+    return np.concatenate([oracle.jacobian(p, N, M, s[k:k + chunk]) @ v for k in range(0, s.shape[0], chunk)])
+
+
+def _sampled_params(rng, N, M, n_a, n_b, n_w):
+    return np.concatenate([rng.choice(N, n_a, replace=False), N + rng.choice(M, n_b, replace=False),
+                           N + M + rng.choice(M * N, n_w, replace=False)])
+
+
 def test_mixed_jacobian_products_full_size_sampled(ctx):
     """NK_MIXED J v and J^T g at the 20 x 20 TFIM workload's full size (Ns =
     16384, N = 400, M = 1600, Np = 642 000), checked on sampled outputs the
-    oracle computes one by one: 64 entries of J v from the Jacobian rows of
-    their samples, and 64 parameters of J^T g (a, b and W entries) as sums
-    over all samples of s, tanh(theta) and their products."""
+    oracle computes: 64 entries of J v from the oracle's Jacobian rows of
+    their samples, and 64 parameters of J^T g (a, b and W entries) from the
+    oracle's Jacobian columns of those parameters over all samples."""
     N, M, Ns = 400, 1600, 16384
     p = I.rbm_params(N, M, 3)
     s = I.random_configs(Ns, N, 3)
@@ -243,66 +254,38 @@ def test_mixed_jacobian_products_full_size_sampled(ctx):
     g = rng.normal(size=Ns)
     out = torch.empty(Np, dtype=torch.float64, device=dev())
     nk.nk_vjp(ctx, pd, N, M, sd, cu(g), out, precision="mixed")
-    a, b, W = p[:N], p[N:N + M], p[N + M:].reshape(M, N)
-    sf = s.astype(np.float64)
-    t = np.tanh(b[None, :] + sf @ W.T)
-    idx = np.concatenate([rng.choice(N, 8, replace=False), N + rng.choice(M, 8, replace=False),
-                          N + M + rng.choice(M * N, 48, replace=False)])
-    ref = np.empty(len(idx))
-    for n, q in enumerate(idx):
-        if q < N:
-            ref[n] = sf[:, q] @ g
-        elif q < N + M:
-            ref[n] = t[:, q - N] @ g
-        else:
-            j, i = divmod(q - N - M, N)
-            ref[n] = (t[:, j] * sf[:, i]) @ g
+    idx = _sampled_params(rng, N, M, 8, 8, 48)
+    ref = oracle.jacobian_cols(p, N, M, s, idx).T @ g
     assert vec_rel_err(out.cpu().numpy()[idx], ref) < 1e-8
     assert nk.nk_ctx_error(ctx) == 0
 
 
 def test_mixed_jacobian_products_24x24_full_size_sampled(ctx):
     """NK_MIXED J v and J^T g at the 24 x 24 Heisenberg workload's full size
-    (Ns = 65536, N = 576, M = 4608, Np = 2 659 392), on sampled outputs
-    computed one by one from the definitions: (J v)_k = s_k.v_a +
-    t_k.v_b + t_k.(V_W s_k) for 48 samples k, and (J^T g)_q for 48
-    parameters q, each a sum over all samples that needs tanh(theta) of one
-    hidden unit only."""
+    (Ns = 65536, N = 576, M = 4608, Np = 2 659 392), on sampled outputs the
+    oracle computes: (J v)_k for 48 samples k from the oracle's Jacobian rows,
+    and (J^T g)_q for 48 parameters q (8 hidden units, with their b and four
+    W entries each, and 8 visible biases) from the oracle's Jacobian columns
+    over all samples."""
     N, M, Ns = 576, 4608, 65536
     p = I.rbm_params(N, M, 5)
     s = I.random_configs(Ns, N, 5, sz0=True)
     Np = N + M + M * N
     rng = np.random.default_rng(11)
     pd, sd = cu(p), cu(s)
-    a, b, W = p[:N], p[N:N + M], p[N + M:].reshape(M, N)
     v = rng.normal(size=Np)
-    va, vb, VW = v[:N], v[N:N + M], v[N + M:].reshape(M, N)
     w = torch.empty(Ns, dtype=torch.float64, device=dev())
     nk.nk_jvp(ctx, pd, N, M, sd, cu(v), w, precision="mixed")
     rows = rng.choice(Ns, 48, replace=False)
-    ref_w = np.empty(len(rows))
-    for n, k in enumerate(rows):
-        sk = s[k].astype(np.float64)
-        tk = np.tanh(b + W @ sk)
-        ref_w[n] = sk @ va + tk @ vb + tk @ (VW @ sk)
+    ref_w = _oracle_jv(p, N, M, s[rows], v, 8)
     assert vec_rel_err(w.cpu().numpy()[rows], ref_w) < 1e-8
     g = rng.normal(size=Ns)
     out = torch.empty(Np, dtype=torch.float64, device=dev())
     nk.nk_vjp(ctx, pd, N, M, sd, cu(g), out, precision="mixed")
-    sf = s.astype(np.float64)
     units = rng.choice(M, 8, replace=False)
-    t = {int(j): np.tanh(b[j] + sf @ W[j]) for j in units}
     idx = [int(i) for i in rng.choice(N, 8, replace=False)] + [N + int(j) for j in units]
     idx += [N + M + int(j) * N + int(i) for j in units for i in rng.choice(N, 4, replace=False)]
-    ref = np.empty(len(idx))
-    for n, q in enumerate(idx):
-        if q < N:
-            ref[n] = sf[:, q] @ g
-        elif q < N + M:
-            ref[n] = t[q - N] @ g
-        else:
-            j, i = divmod(q - N - M, N)
-            ref[n] = (t[j] * sf[:, i]) @ g
+    ref = oracle.jacobian_cols(p, N, M, s, idx).T @ g
     assert vec_rel_err(out.cpu().numpy()[idx], ref) < 1e-8
     assert nk.nk_ctx_error(ctx) == 0
 
@@ -310,9 +293,10 @@ def test_mixed_jacobian_products_24x24_full_size_sampled(ctx):
 def test_mixed_cg_solve_full_size_sampled_residual(ctx):
     """The NK_MIXED CG solve of (S + eps I) delta = F at the 20 x 20 TFIM
     workload's full size (Ns = 16384, Np = 642 000, on-the-fly QGT, 4-slice
-    products), checked by the residual on 64 sampled components computed from
-    the definitions: w = J delta over all samples (Delta w centred), then
-    (S delta)_q = (1/Ns) sum_k O_kq Delta w_k for the sampled q."""
+    products), checked by the residual on 64 sampled components, with the
+    QGT product of App. B.3 taken through the oracle's Jacobian: w = J delta
+    over all samples from its rows, Delta w centred, then (S delta)_q =
+    (1/Ns) sum_k O_kq Delta w_k from its columns of the sampled q."""
     N, M, Ns, eps = 400, 1600, 16384, 0.01
     p = I.rbm_params(N, M, 3)
     s = I.random_configs(Ns, N, 3)
@@ -324,23 +308,9 @@ def test_mixed_cg_solve_full_size_sampled_residual(ctx):
                           cg_maxiter=3000, precision="mixed")
     assert info["converged"]
     delta = d.cpu().numpy()
-    a, b, W = p[:N], p[N:N + M], p[N + M:].reshape(M, N)
-    da, db, DW = delta[:N], delta[N:N + M], delta[N + M:].reshape(M, N)
-    sf = s.astype(np.float64)
-    t = np.tanh(b[None, :] + sf @ W.T)
-    w = sf @ da + t @ db + np.einsum("kj,kj->k", t, sf @ DW.T)
+    w = _oracle_jv(p, N, M, s, delta, 256)
     dw = w - w.mean()
-    idx = np.concatenate([rng.choice(N, 8, replace=False), N + rng.choice(M, 8, replace=False),
-                          N + M + rng.choice(M * N, 48, replace=False)])
-    r = np.empty(len(idx))
-    for n, q in enumerate(idx):
-        if q < N:
-            col = sf[:, q]
-        elif q < N + M:
-            col = t[:, q - N]
-        else:
-            j, i = divmod(q - N - M, N)
-            col = t[:, j] * sf[:, i]
-        r[n] = col @ dw / Ns + eps * delta[q] - F[q]
+    idx = _sampled_params(rng, N, M, 8, 8, 48)
+    r = oracle.jacobian_cols(p, N, M, s, idx).T @ dw / Ns + eps * delta[idx] - F[idx]
     # the CG stops at ||r|| <= 1e-9 ||F||; the 4-slice products add about 2^-32
     assert np.abs(r).max() <= 1e-8 * np.linalg.norm(F)
