@@ -1,12 +1,15 @@
 #!/usr/bin/env python
 """Benchmark of one VMC + stochastic-reconfiguration step (the whole hot path).
 
-Workload (default): 10 x 10 periodic Heisenberg antiferromagnet with the
-Marshall sign folded in, real RBM alpha = 2 (M = 200, Np = 20300), spin-
-exchange Metropolis at S_z = 0 with 1024 chains x 8 samples (Ns = 8192),
-eps = 0.01, lr = 0.01, SR solved by an FP64 Cholesky of the Ns x Ns
-sample-space matrix.  A step = sampling (8 sweeps per chain), local energies,
-statistics, force, SR solve and update, all through nk_sr_step.
+Workload (default): 24 x 24 periodic Heisenberg antiferromagnet with the
+Marshall sign folded in, real RBM alpha = 8 (M = 4608, Np = 2 659 392),
+spin-exchange Metropolis at S_z = 0 with 8192 chains x 8 samples (Ns =
+65536), eps = 0.01, lr = 0.01, SR solved by conjugate gradients on the
+on-the-fly QGT (relative residual 1e-6 in NK_MIXED, 1e-10 in NK_F64).  A step
+= sampling (8 sweeps per chain), local energies, statistics, force, SR solve
+and update, all through nk_sr_step.  The same step on the FP64 GPU path
+(fewer steps) and the 10 x 10 Heisenberg workload (sample-space Cholesky)
+are added to the line, then the serving stream.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|f64]
     python bench.py --impl reference ...   # the CPU oracle on a bounded sample
@@ -47,6 +50,15 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "of fallback"
 
 
+# CG stopping rule per precision: relative residual 1e-10 on the FP64 path,
+# 1e-6 on the mixed path (whose 4-slice QGT products carry about 2^-32)
+CG_TOL = {"f64": 1e-10, "mixed": 1e-6}
+# chains of the oracle's bounded sample per workload (about 10-30 s of one
+# host thread per SR step; the default is used for the others)
+ORACLE_CHAINS = {"heis2d_24x24": 4, "tfim2d_20x20": 16, "heis2d_10x10": 128}
+ORACLE_CHAINS_DEFAULT = 64
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -54,13 +66,17 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "f64"])
-    ap.add_argument("--workload", default="heis2d_10x10",
+    ap.add_argument("--workload", default="heis2d_24x24",
                     help="workload name, optionally with @rule to replace its sampler rule "
                          "(e.g. heis2d_10x10@hamiltonian)")
+    ap.add_argument("--extra", default="heis2d_10x10",
+                    help="comma-separated workloads timed after the headline (mixed path, same steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the other-precision timing")
+    ap.add_argument("--compare-steps", type=int, default=2,
+                    help="timed steps of the other-precision arm (after one warm-up step)")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
-    ap.add_argument("--serve", type=int, default=128,
+    ap.add_argument("--serve", type=int, default=512,
                     help="requests of the serving run added to the line (0: none)")
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-budget-gb", type=float, default=64.0)
@@ -82,9 +98,15 @@ def workload(name):
 
 # ----------------------------------------------------------- CPU oracle ----
 
+def oracle_chains(name):
+    return ORACLE_CHAINS.get(name.partition("@")[0], ORACLE_CHAINS_DEFAULT)
+
+
 def oracle_sample(name, chains, steps):
-    """Time the oracle's SR step on `chains` chains of the workload (one host
-    thread), `steps` times.  Runs in a fresh process."""
+    """Time the oracle's SR step on `chains` chains of the workload, `steps`
+    times (the first with the workload's discarded sweeps, untimed when more
+    than one step is asked for).  Runs in a fresh process; the thread count
+    comes from OMP_NUM_THREADS / OPENBLAS_NUM_THREADS."""
     import numpy as np
     import oracle
     from paper_2112_10526_gb300 import inputs as I
@@ -94,21 +116,31 @@ def oracle_sample(name, chains, steps):
     s = oracle.chain_init(N, chains, w["rule"], w["seed"], 0)
     times = []
     sweep0 = 0
-    for _ in range(steps):
+    solver = "cg" if w["solver"] == "cg" else "cholesky"
+    for k in range(steps):
+        nd = w["discard"] if k == 0 else 0
         t0 = time.perf_counter()
-        r = oracle.sr_step(p, N, M, w["ham"], w["rule"], s, sweep0, 0, w["per_chain"], w["seed"], 0,
-                           diag_shift=w["diag_shift"], lr=w["lr"], solver="cg", cg_tol=1e-10,
+        r = oracle.sr_step(p, N, M, w["ham"], w["rule"], s, sweep0, nd, w["per_chain"], w["seed"], 0,
+                           diag_shift=w["diag_shift"], lr=w["lr"], solver=solver, cg_tol=CG_TOL["f64"],
                            cg_maxiter=1000)
         times.append(time.perf_counter() - t0)
         p, s = r["params"], r["state"]
-        sweep0 += w["per_chain"]
-    return {"times": times, "energy": float(r["stats"]["mean"]), "cg_iters": int(r["cg_iters"])}
+        sweep0 += nd + w["per_chain"]
+    return {"times": times, "energy": float(r["stats"]["mean"]), "cg_iters": int(r["cg_iters"]),
+            "solver": solver}
 
 
-def run_oracle_subprocess(name, chains, steps):
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_oracle_subprocess(name, chains, steps, threads):
     env = dict(os.environ)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        env[v] = "1"
+        env[v] = str(threads)
     env["CUDA_VISIBLE_DEVICES"] = ""
     out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample",
                           f"{name}:{chains}:{steps}"], env=env, capture_output=True, text=True,
@@ -116,17 +148,34 @@ def run_oracle_subprocess(name, chains, steps):
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
-def oracle_line_fields(name, chains, res):
+def oracle_line_fields(name, chains, res, threads):
+    """SR steps/s of the whole workload from the oracle's steps on `chains`
+    chains (the work is per chain and per sample: linear extrapolation)."""
     w = workload(name)
     scale = w["chains"] / chains
-    t = statistics.median(res["times"])
+    times = res["times"][1:] if len(res["times"]) > 1 else res["times"]
+    t = statistics.median(times)
     value = 1.0 / (t * scale)
     return value, {
-        "value": value, "unit": "SR steps/s", "cores": 1, "kind": "oracle",
-        "sample": (f"{chains} of {w['chains']} chains x {w['per_chain']} samples, oracle CG solver "
-                   f"(x0 = 0, tol 1e-10), 1 host thread; median of {len(res['times'])} steps, "
-                   f"extrapolated linearly in the number of samples"),
+        "value": value, "unit": "SR steps/s", "cores": threads, "kind": "oracle",
+        "sample": (f"{chains} of {w['chains']} chains x {w['per_chain']} samples, oracle {res['solver']} "
+                   f"solver (CG: x0 = 0, tol {CG_TOL['f64']:g}), {threads} host thread(s); median of "
+                   f"{len(times)} step(s) after the discard step, extrapolated linearly in the number of "
+                   f"samples ({t:.2f} s per sampled step)"),
     }
+
+
+def cpu_baseline(name):
+    """The oracle timed on all host cores (the reported baseline) and on one
+    thread, each on the bounded sample of the workload."""
+    chains = oracle_chains(name)
+    n = host_cores()
+    wide = max(chains, min(n, workload(name)["chains"]))  # a chain per thread at least
+    all_v, all_f = oracle_line_fields(name, wide, run_oracle_subprocess(name, wide, 2, n), n)
+    one_v, one_f = oracle_line_fields(name, chains, run_oracle_subprocess(name, chains, 2, 1), 1)
+    all_f["nproc"] = n
+    all_f["single_thread"] = {"value": one_v, "unit": "SR steps/s", "cores": 1}
+    return all_f
 
 
 # --------------------------------------------------------------- clocks ----
@@ -202,7 +251,7 @@ def setup(w, precision, rank, dev):
     nk.nk_chains_init(st["ctx"], N, C, w["rule"], w["seed"], rank, st["s"])
     st["chains"] = nk.make_chains(st["s"])
     st["cfg"] = nk.make_cfg(w["rule"], precision, w["solver"], w["discard"], w["per_chain"],
-                            w["diag_shift"], w["lr"], w["seed"], stream_id=rank, cg_tol=1e-8,
+                            w["diag_shift"], w["lr"], w["seed"], stream_id=rank, cg_tol=CG_TOL[precision],
                             cg_maxiter=1000)
     st["stats"] = torch.empty(nk.SR_STATS_DOUBLES, dtype=torch.float64, device=dev)
     return st
@@ -261,6 +310,10 @@ def max_over_ranks(x, world, dev):
 
 
 def timed_steps(st, K, world, dev, prof=False):
+    """K steps bracketed by a barrier and a synchronize on both sides, timed
+    with CUDA events on the launching stream.  With prof, every tracked
+    kernel class is also timed by the library's own events (on the streams
+    its kernels run on) and its algorithmic and executed work added up."""
     import torch
     from paper_2112_10526_gb300 import nk
     stream = torch.cuda.current_stream()
@@ -280,7 +333,7 @@ def timed_steps(st, K, world, dev, prof=False):
     ms = e0.elapsed_time(e1)
     prof_out = None
     if prof:
-        prof_out = {c: nk.nk_prof_read(c) for c in nk.PROF_CLASSES}
+        prof_out = {c: nk.nk_prof_read(c) + (nk.nk_prof_read_executed(c),) for c in nk.PROF_CLASSES}
         nk.nk_prof_enable(False)
     return max_over_ranks(ms, world, dev), launches, prof_out
 
@@ -311,11 +364,12 @@ def e2e_steps(st, K, dev):
     return dt, bi, bo
 
 
-# DRAM bytes (read + write) of k_ozaki_gemm per 128 x 32 output tile with 7
-# slices, from the ncu capture summarised in
-# profiles/k_ozaki_gemm_wide_update_heis2d_10x10.md (8064 x 8064 lower
-# update: 472.76 MB over 8064 tiles).  Valid while the kernel's source is the
-# one captured: the hash covers the GEMM section of k_tc.cu and tc_ptx.cuh.
+# DRAM bytes (read + write) per launch of the dominant kernels, from one ncu
+# capture each (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the
+# sha256 of the kernel's source section so that a changed kernel reports no
+# stale figure.  k_ozaki_gemm: per 128 x 32 output tile with 7 slices (the
+# 8064 x 8064 lower update of the 10 x 10 workload: 472.76 MB over 8064
+# tiles).
 OZAKI_TRAFFIC = {"bytes_per_tile": 59062.3, "source_sha256_prefix": "dadcb0eb2cc3d6e5"}
 OZAKI_TILE_FLOPS = 28 * 4 * 2.0 * 128 * 32 * 16  # executed BF16 flops per tile (7 slices)
 
@@ -332,97 +386,135 @@ def ozaki_source_hash():
         return ""
 
 
+TENSOR_CLASSES = ("chol_update", "gram", "jvp_vjp")
+
+
+def class_roofline(cls, ms, launches, work, executed, precision):
+    """One kernel class against the roofline that bounds it.  `work` is the
+    method's algorithmic work (ratio terms for the sweep and the local
+    energies, FP64-operation flops for the products and factorisations);
+    `executed` what the hardware ran (BF16 slice-product flops of the
+    tensor-core paths)."""
+    peaks, src = measured_peaks()
+    secs = ms / 1e3
+    out = {"kernel_class": cls, "launches": launches, "avg_launch_ms": ms / launches}
+    if cls in ("sweep", "eloc"):
+        # one FMA and one multiply per ratio term
+        out.update(bound="alu", unit="TFLOP/s", achieved=2.0 * work / secs / 1e12,
+                   algorithmic_work="2 flops per ratio term")
+        if precision == "f64":
+            out.update(peak=FP64_PEAK_TFLOPS, peak_source="FP64 pipe, nominal 1.25 TFLOP/s (of nominal)")
+        else:
+            out.update(peak=FP32_PEAK_TFLOPS,
+                       peak_source="FP32 lanes: 152 SMs x 128 x 2 x 2.07 GHz (of nominal)")
+    elif cls in TENSOR_CLASSES and precision == "mixed":
+        out.update(bound="tensor", unit="TFLOP/s", achieved=work / secs / 1e12,
+                   peak=peaks["bf16_tflops_sustained"],
+                   peak_source=f"bf16 dense, sustained ({src}); the FP64-accurate products run as "
+                               f"BF16 slice products",
+                   algorithmic_work="flops of the FP64 operation",
+                   executed_tflops=executed / secs / 1e12,
+                   executed_frac=executed / secs / 1e12 / peaks["bf16_tflops_sustained"])
+    elif cls == "trsv":
+        # two solves read the lower factor once each: n^2 / 2 x 8 bytes per solve, work = 2 n^2
+        out.update(bound="hbm", unit="GB/s", achieved=(work / 2.0) * 8.0 / secs / 1e9, peak=peaks["hbm_gbs"],
+                   peak_source=f"HBM copy ({src})", algorithmic_work="the lower factor read once per solve")
+    else:
+        out.update(bound="alu", unit="TFLOP/s", achieved=work / secs / 1e12, peak=FP64_PEAK_TFLOPS,
+                   peak_source="FP64 pipe, nominal 1.25 TFLOP/s (of nominal; no measured FP64 peak)",
+                   algorithmic_work="FP64 flops")
+    out["frac"] = out["achieved"] / out["peak"]
+    return out
+
+
 def roofline(prof, K, precision):
-    # dominant tracked kernel class by time
+    """The dominant tracked kernel class by time, with its DRAM traffic per
+    launch where a capture of the same kernel source exists."""
     cls = max(prof, key=lambda c: prof[c][0])
-    ms, launches, work = prof[cls]
+    ms, launches, work = prof[cls][:3]
+    executed = prof[cls][3] if len(prof[cls]) > 3 else work
     if launches == 0 or ms <= 0:
         return None, cls
-    secs = ms / 1e3
-    bound = "alu"
-    if cls in ("sweep", "eloc"):
-        flops = 2.0 * work  # one FMA + one multiply per ratio term
-        peak = FP64_PEAK_TFLOPS if precision == "f64" else FP32_PEAK_TFLOPS
-        note = ("FP64 pipe, nominal 1.25 TFLOP/s (of nominal)" if precision == "f64"
-                else "FP32 lanes: 152 SMs x 128 x 2 x 2.07 GHz (of nominal)")
-    elif cls in ("chol_update", "gram", "jvp_vjp") and precision == "mixed":
-        # executed BF16 tcgen05 MMA flops (sliced FP64-accurate products) vs the measured bf16 peak
-        flops = work
-        peaks, src = measured_peaks()
-        peak = peaks["bf16_tflops_sustained"]
-        bound = "tensor"
-        note = f"bf16 dense, sustained ({src})"
-    else:
-        flops = work
-        peak = FP64_PEAK_TFLOPS
-        note = "FP64 pipe, nominal 1.25 TFLOP/s (of nominal; no measured FP64 peak)"
-    achieved = flops / secs / 1e12
+    rf = class_roofline(cls, ms, launches, work, executed, precision)
     traffic = None
     if cls == "chol_update" and precision == "mixed" and \
             ozaki_source_hash().startswith(OZAKI_TRAFFIC["source_sha256_prefix"]):
         # bytes per launch, like achieved: the class's tiles x the captured bytes per tile
-        traffic = work / OZAKI_TILE_FLOPS * OZAKI_TRAFFIC["bytes_per_tile"] / launches
-    return {"kernel_class": cls, "bound": bound, "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic, "traffic_unit": "DRAM bytes per launch",
-            "peak_source": note, "launches": launches, "avg_launch_ms": ms / launches,
-            "share_of_step": ms / 1.0}, cls
+        traffic = executed / OZAKI_TILE_FLOPS * OZAKI_TRAFFIC["bytes_per_tile"] / launches
+    rf["traffic"] = traffic
+    rf["traffic_unit"] = "DRAM bytes per launch"
+    return rf, cls
 
 
 def rooflines_by_class(prof, step_ms, precision):
-    """Every tracked kernel class against the roofline that bounds it (the
-    same conventions as the dominant-class roofline)."""
-    peaks, src = measured_peaks()
+    """Every tracked kernel class per step against its roofline."""
     out = {}
-    for cls, (ms, launches, work) in prof.items():
+    for cls, v in prof.items():
+        ms, launches, work = v[:3]
+        executed = v[3] if len(v) > 3 else work
         if launches == 0 or ms <= 0:
             continue
-        secs = ms / 1e3
-        if cls in ("sweep", "eloc"):
-            val, unit, bound = 2.0 * work / secs / 1e12, "TFLOP/s", "alu"
-            peak = FP64_PEAK_TFLOPS if precision == "f64" else FP32_PEAK_TFLOPS
-            note = "FP64 pipe, nominal" if precision == "f64" else "FP32 lanes, nominal"
-        elif cls in ("chol_update", "gram", "jvp_vjp") and precision == "mixed":
-            val, unit, bound = work / secs / 1e12, "TFLOP/s", "tensor"
-            peak, note = peaks["bf16_tflops_sustained"], f"bf16 dense, sustained ({src})"
-        elif cls == "trsv":
-            # two solves read the lower factor once each: n^2 / 2 x 8 bytes per solve, work = 2 n^2
-            val, unit, bound = (work / 2.0) * 8.0 / secs / 1e9, "GB/s", "hbm"
-            peak, note = peaks["hbm_gbs"], f"HBM copy ({src})"
-        else:
-            val, unit, bound = work / secs / 1e12, "TFLOP/s", "alu"
-            peak, note = FP64_PEAK_TFLOPS, "FP64 pipe, nominal"
-        out[cls] = {"bound": bound, "achieved": val, "peak": peak, "unit": unit, "frac": val / peak,
-                    "ms_per_step": ms, "share_of_step": ms / step_ms, "launches": launches, "peak_source": note}
+        r = class_roofline(cls, ms, launches, work, executed, precision)
+        r.update(ms_per_step=ms, share_of_step=ms / step_ms)
+        out[cls] = r
     return out
+
+
+def measure(w, precision, K, warmup, rank, world, dev, prof=True, e2e=True):
+    """Warm-up, a profiled timing (per-class events), the plain timing (the
+    headline number) and the end-to-end timing of one workload."""
+    from paper_2112_10526_gb300 import nk
+    st = setup(w, precision, rank, dev)
+    for i in range(warmup):
+        step(st, first=(i == 0))
+    import torch
+    torch.cuda.synchronize()
+    res = {}
+    if prof:
+        ms_p, _, pr = timed_steps(st, K, world, dev, prof=True)
+        res["prof"], res["ms_prof"] = pr, ms_p
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    ms, launches, _ = timed_steps(st, K, world, dev, prof=False)
+    res["clocks"] = clocks.stop()
+    res["ms"], res["launches"] = ms, launches
+    res["stats"] = nk.sr_stats_dict(st["stats"])
+    if e2e:
+        dt, bi, bo = e2e_steps(st, K, dev)
+        res["e2e"] = (max_over_ranks(dt, world, dev), bi, bo)
+    st["ctx"].close()
+    return res
+
+
+def workload_config(w, precision, world):
+    Ns = w["chains"] * w["per_chain"]
+    Np = w["N"] + w["M"] + w["M"] * w["N"]
+    cfg = {"workload": w["name"], "lattice": lattice_text(w["N"]), "hamiltonian": ham_text(w["ham"]),
+           "N": w["N"], "M": w["M"], "Np": Np, "chains": w["chains"], "samples_per_chain": w["per_chain"],
+           "Ns": Ns, "rule": w["rule"], "solver": w["solver"], "precision": precision,
+           "diag_shift": w["diag_shift"], "lr": w["lr"], "parallelism": f"replicas x{world}",
+           "l2": l2_text(w["solver"], Ns, w["M"], Np)}
+    if w["solver"] == "cg":
+        cfg["cg_tol"] = CG_TOL[precision]
+    return cfg
 
 
 def run_ours(args, rank, world):
     import torch
-    from paper_2112_10526_gb300 import nk
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     w = workload(args.workload)
-    st = setup(w, args.precision, rank, dev)
-    for i in range(args.warmup):
-        step(st, first=(i == 0))
-    torch.cuda.synchronize()
-    clocks = Clocks(local)
-    clocks.start()
-    ms, launches, prof = timed_steps(st, args.steps, world, dev, prof=True)
-    clk = clocks.stop()
-    # a second timing without the event brackets (the headline number)
-    ms_plain, launches, _ = timed_steps(st, args.steps, world, dev, prof=False)
     K = args.steps
+    r = measure(w, args.precision, K, args.warmup, rank, world, dev)
+    ms_plain, prof = r["ms"], r["prof"]
     value = replica_value(world, K, ms_plain)
-    stats = nk.sr_stats_dict(st["stats"])
+    stats = r["stats"]
+    prof_step = {c: (v[0] / K, v[1] / K, v[2] / K, v[3] / K) for c, v in prof.items()}
     rf, dom = roofline(prof, K, args.precision)
     if rf is not None:
-        rf["share_of_step"] = prof[dom][0] / ms
-    by_class = rooflines_by_class({c: (v[0] / K, v[1] / K, v[2] / K) for c, v in prof.items()}, ms / K,
-                                  args.precision)
-    e2e_dt, bi, bo = e2e_steps(st, K, dev)
-    e2e_dt = max_over_ranks(e2e_dt, world, dev)
+        rf["share_of_step"] = prof[dom][0] / r["ms_prof"]
+    e2e_dt, bi, bo = r["e2e"]
     Ns = w["chains"] * w["per_chain"]
     line = {
         "metric": METRIC, "value": value, "unit": "SR steps/s", "n_gpus": world, "steps": K,
@@ -430,36 +522,45 @@ def run_ours(args, rank, world):
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "f64" else "f32+f64",
         "data": "synthetic (seeded RBM parameters N(0, 0.01^2), Philox chains)",
-        "config": {"workload": w["name"], "lattice": lattice_text(w["N"]),
-                   "hamiltonian": ham_text(w["ham"]), "N": w["N"], "M": w["M"], "Np": w["N"] + w["M"] + w["M"] * w["N"],
-                   "chains": w["chains"], "samples_per_chain": w["per_chain"], "Ns": Ns, "rule": w["rule"],
-                   "solver": w["solver"], "precision": args.precision, "diag_shift": w["diag_shift"],
-                   "lr": w["lr"], "parallelism": f"replicas x{world}",
-                   "l2": l2_text(w["solver"], Ns, w["M"], w["N"] + w["M"] + w["M"] * w["N"])},
+        "config": workload_config(w, args.precision, world),
         "samples_sweeps_per_s": world * K * Ns / (ms_plain / 1e3),
         "proposals_per_s": world * K * Ns * w["N"] / (ms_plain / 1e3),
         # local-energy evaluations per second of the E_loc kernels alone (CUDA events)
         "eloc_evals_per_s": (world * K * Ns / (prof["eloc"][0] / 1e3)) if prof.get("eloc", (0,))[0] > 0 else None,
         "energy": stats["energy"], "energy_error": stats["error"], "acceptance": stats["acceptance"],
+        "cg_iters": stats["cg_iters"],
         "roofline": rf,
-        "rooflines_by_class": by_class,
+        "rooflines_by_class": rooflines_by_class(prof_step, r["ms_prof"] / K, args.precision),
         "kernel_ms_per_step": {c: prof[c][0] / K for c in prof if prof[c][1] > 0},
         "e2e": {"value": world * K / e2e_dt, "unit": "SR steps/s", "h2d_bytes_per_step": bi,
                 "d2h_bytes_per_step": bo},
-        "gpu_launches": int(launches),
-        "clocks": clk,
+        "gpu_launches": int(r["launches"]),
+        "clocks": r["clocks"],
     }
     if not args.no_compare and world == 1:
         other = "f64" if args.precision == "mixed" else "mixed"
-        st2 = setup(w, other, rank, dev)
-        for i in range(args.warmup):
-            step(st2, first=(i == 0))
-        ms2, _, _ = timed_steps(st2, K, world, dev)
-        s2 = nk.sr_stats_dict(st2["stats"])
-        line[f"{other}_path"] = {"value": K / (ms2 / 1e3), "unit": "SR steps/s", "ms_per_step": ms2 / K,
-                                 "energy": s2["energy"], "energy_error": s2["error"]}
-        st2["ctx"].close()
-    st["ctx"].close()
+        Kc = max(1, args.compare_steps)
+        r2 = measure(w, other, Kc, 1, rank, world, dev, prof=False, e2e=False)
+        s2 = r2["stats"]
+        line[f"{other}_path"] = {"value": Kc / (r2["ms"] / 1e3), "unit": "SR steps/s",
+                                 "ms_per_step": r2["ms"] / Kc, "steps": Kc, "warmup": 1,
+                                 "energy": s2["energy"], "energy_error": s2["error"],
+                                 "cg_iters": s2["cg_iters"], "clocks": r2["clocks"],
+                                 "config": workload_config(w, other, world)}
+    extra = {}
+    for name in [x for x in args.extra.split(",") if x] if world == 1 else []:
+        we = workload(name)
+        re_ = measure(we, args.precision, K, args.warmup, rank, world, dev)
+        Ke = K
+        dom_rf, _ = roofline(re_["prof"], Ke, args.precision)
+        extra[name] = {"value": Ke / (re_["ms"] / 1e3), "unit": "SR steps/s", "ms_per_step": re_["ms"] / Ke,
+                       "e2e": {"value": Ke / re_["e2e"][0], "unit": "SR steps/s",
+                               "h2d_bytes_per_step": re_["e2e"][1], "d2h_bytes_per_step": re_["e2e"][2]},
+                       "energy": re_["stats"]["energy"], "energy_error": re_["stats"]["error"],
+                       "kernel_ms_per_step": {c: v[0] / Ke for c, v in re_["prof"].items() if v[1] > 0},
+                       "roofline": dom_rf, "config": workload_config(we, args.precision, world)}
+    if extra:
+        line["other_workloads"] = extra
     return line
 
 
@@ -537,17 +638,18 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        chains = 128
-        res = run_oracle_subprocess(args.workload, chains, args.steps + args.warmup)
+        n = host_cores()
+        chains = max(oracle_chains(args.workload), min(n, workload(args.workload)["chains"]))
+        res = run_oracle_subprocess(args.workload, chains, args.steps + args.warmup, n)
         res["times"] = res["times"][args.warmup:] or res["times"]
-        value, cpu = oracle_line_fields(args.workload, chains, res)
+        value, cpu = oracle_line_fields(args.workload, chains, {**res, "times": [0.0] + res["times"]}, n)
+        cpu["nproc"] = n
         w = workload(args.workload)
         line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "SR steps/s",
                 "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": w["name"], "N": w["N"], "M": w["M"], "chains": w["chains"],
-                           "samples_per_chain": w["per_chain"]},
+                "config": workload_config(w, "f64", 1),
                 "cpu_baseline": cpu,
                 "e2e": {"value": value, "unit": "SR steps/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
@@ -555,10 +657,8 @@ def main():
         return
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        # the oracle runs in a fresh process before any CUDA work in this one
-        chains = 128
-        res = run_oracle_subprocess(args.workload, chains, 1)
-        _, cpu = oracle_line_fields(args.workload, chains, res)
+        # the oracle runs in fresh processes before any CUDA work in this one
+        cpu = cpu_baseline(args.workload)
     if world > 1:
         import torch
         import torch.distributed as dist

@@ -433,32 +433,37 @@ size_t nk_request_bytes(const nk_request *req);
 /*
  * Kernel timing for measurement tools (not part of the method).  When
  * enabled, every launch of a tracked kernel class is bracketed by CUDA
- * events recorded on the stream it is launched on, and its algorithmic work
- * (flops or bytes, per class) is added up.  nk_prof_read waits for those
- * events and returns the total milliseconds, the number of launches and the
- * total work since the last nk_prof_enable.  Process-wide; thread-safe.
+ * events recorded on the stream it is launched on, and its work is added
+ * up.  nk_prof_read waits for those events and returns the total
+ * milliseconds, the number of launches and the total ALGORITHMIC work since
+ * the last nk_prof_enable: the method's own count (ratio terms, or the flops
+ * of the FP64 operation a launch stands for, whatever precision runs it).
+ * nk_prof_read_executed returns what the hardware executed for the same
+ * launches: for the NK_MIXED tensor-core products the BF16 MMA flops of all
+ * slice products (several times the algorithmic flops), else the same as
+ * the algorithmic work.  Process-wide; thread-safe.
  */
-#define NK_PROF_SWEEP 0       /* Metropolis sweeps: work = ratio terms (proposals x M) */
-#define NK_PROF_ELOC 1        /* local energies: work = ratio terms (connections x M) */
-#define NK_PROF_GRAM 2        /* sample-space Gram: work = flops (NK_MIXED: BF16 tensor-core
-                                 MMA flops executed) */
-#define NK_PROF_CHOL_UPDATE 3 /* Cholesky products: NK_F64 trailing updates, work = FP64
-                                 flops; NK_MIXED every tensor-core product of the
-                                 factorisation (trailing updates and panel solves),
-                                 work = BF16 MMA flops executed */
-#define NK_PROF_CHOL_PANEL 4  /* Cholesky panels: NK_F64 diagonal blocks and panel solves,
-                                 work = FP64 flops; NK_MIXED diagonal blocks, their
-                                 inverses and the operand slicing, work = FP64 flops
-                                 of the diagonal blocks */
-#define NK_PROF_TRSV 5        /* triangular solves: work = flops */
-#define NK_PROF_JVP_VJP 6     /* Jacobian products and the batched theta: work = flops
-                                 (NK_MIXED: BF16 tensor-core MMA flops executed) */
+#define NK_PROF_SWEEP 0       /* Metropolis sweeps: ratio terms (proposals x M) */
+#define NK_PROF_ELOC 1        /* local energies: ratio terms (connections x M) */
+#define NK_PROF_GRAM 2        /* Gram matrices: lower-triangle flops, (N + M) per entry of the
+                                 sample-space Jacobian-row Gram s.s + t.t + (t.t)(s.s), 2 Ns
+                                 per entry of the parameter-space S */
+#define NK_PROF_CHOL_UPDATE 3 /* Cholesky products: the FP64 flops of the trailing updates
+                                 (lower triangle) and, in NK_MIXED, of the panel solves run as
+                                 tensor-core products with the inverted diagonal block; summed
+                                 over a factorisation of order n, about n^3 / 3 */
+#define NK_PROF_CHOL_PANEL 4  /* Cholesky panels: FP64 flops of the diagonal blocks (and their
+                                 inverses in NK_MIXED); NK_F64 panel solves; operand slicing */
+#define NK_PROF_TRSV 5        /* triangular solves: flops */
+#define NK_PROF_JVP_VJP 6     /* Jacobian products J v, J^T g (2 Ns (N + 1)(M + 1) flops each)
+                                 and the batched theta = b + W s (2 B N M) */
 #define NK_PROF_N 8
 nk_status nk_prof_enable(int32_t on);
 /* Number of CUDA kernels this library has launched in this process. */
 int64_t nk_launch_count(void);
 nk_status nk_prof_read(int32_t cls, double *ms /* host */, int64_t *launches /* host */,
                        double *work /* host */);
+nk_status nk_prof_read_executed(int32_t cls, double *executed /* host */);
 /* The bracketed launches since the last nk_prof_enable, in the order they
  * were enqueued: for entry i (i < max) the class cls[i] and the start and
  * end times t0_ms[i], t1_ms[i] in milliseconds from the start of the first

@@ -568,7 +568,7 @@ cudaError_t launch_theta_tc(int N, int M, const double *b, const double *W, cons
     (k_slice_long_rows<<<M, 128, 0, st>>>(W, N, M, N, nullptr, kMaxSB, ld, Ws, ew), nk::note_launch());
     const int slot = prof_begin(NK_PROF_JVP_VJP, st);
     cudaError_t e = sgemm(As, B, ld, Ws, ew, M, ld, N, kMaxSB, theta, M, 0, b, err, st);
-    prof_end(slot, st, sgemm_flops(B, M, N, kMaxSB));
+    prof_end(slot, st, 2.0 * (double)B * N * (double)M, sgemm_flops(B, M, N, kMaxSB));
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
@@ -602,7 +602,7 @@ cudaError_t launch_jvp_tc(int N, int M, int64_t Ns, const int8_t *s, const doubl
     (k_slice_long_rows<<<M + 1, 128, 0, st>>>(Vp, N + 1, M + 1, N + 1, nullptr, SB, ld, Vs, ev), nk::note_launch());
     const int slot = prof_begin(NK_PROF_JVP_VJP, st);
     cudaError_t e = sgemm(As, Ns, ld, Vs, ev, M + 1, ld, N + 1, SB, P, ntc, 3, nullptr, err, st, T, M);
-    prof_end(slot, st, sgemm_flops(Ns, M + 1, N + 1, SB));
+    prof_end(slot, st, 2.0 * (double)Ns * (N + 1) * (double)(M + 1), sgemm_flops(Ns, M + 1, N + 1, SB));
     if (e != cudaSuccess) return e;
     (k_rowsum_partials<<<nblk(Ns, 256), 256, 0, st>>>(Ns, ntc, P, out), nk::note_launch());
     return cudaGetLastError();
@@ -659,7 +659,7 @@ cudaError_t launch_vjp_tc(int N, int M, int64_t Ns, const int8_t *s, const doubl
     const int64_t tot = (int64_t)(N + 1) * (M + 1);
     const int slot = prof_begin(NK_PROF_JVP_VJP, st);
     e = sgemm(St, N + 1, ld, Gs, eg, M + 1, ld, Ns, SB, PT, M + 1, 0, nullptr, err, st, nullptr, 0, ks, tot);
-    prof_end(slot, st, sgemm_flops(N + 1, M + 1, Ns, SB));
+    prof_end(slot, st, 2.0 * (double)Ns * (N + 1) * (double)(M + 1), sgemm_flops(N + 1, M + 1, Ns, SB));
     if (e != cudaSuccess) return e;
     (k_scatter_vjp<<<nblk(tot, 256), 256, 0, st>>>(N, M, ks, PT, out), nk::note_launch());
     return cudaGetLastError();

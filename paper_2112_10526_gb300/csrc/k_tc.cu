@@ -1020,7 +1020,8 @@ cudaError_t panel_step(double *A, int64_t n, int64_t k0, int *info, int *err, Tc
     if (rest > 0 && e == cudaSuccess) {
         slot = prof_begin(NK_PROF_CHOL_UPDATE, st);
         e = launch_ozaki_gemm(Lsl, Lexp, rest, w.Bsl, w.expB, kb, S, panel, n, 0, false, err, st);
-        prof_end(slot, st, ozaki_mma_flops(rest, kb, S, false));
+        // the triangular solve L21 = A21 L11^-T: rest kb^2 flops in FP64
+        prof_end(slot, st, (double)rest * kb * kb, ozaki_mma_flops(rest, kb, S, false));
         slot = prof_begin(NK_PROF_CHOL_PANEL, st);
         if (e == cudaSuccess) e = launch_slice_rows(panel, n, rest, kb, S, Lsl, Lexp, st);
         prof_end(slot, st, 0.0);
@@ -1066,7 +1067,9 @@ cudaError_t launch_cholesky_tc(double *A, int64_t n, int *info, int *err, void *
         // narrow: block column k + 1 (all rows below panel k)
         int slot = prof_begin(NK_PROF_CHOL_UPDATE, ps);
         e = launch_ozaki_gemm_strided(Lk, Le, rest, rest, Lk, Le, kb1, rest, S, C1, n, 1, true, err, ps);
-        prof_end(slot, ps, ozaki_mma_flops(rest, kb1, S, true));
+        // FP64 flops of the lower part of the rest x kb1 block column, K = kNB
+        prof_end(slot, ps, 2.0 * kNB * ((double)rest * kb1 - 0.5 * (double)kb1 * (kb1 - 1)),
+                 ozaki_mma_flops(rest, kb1, S, true));
         if (e != cudaSuccess) return e;
         e = panel_step(A, n, k0 + kNB, info, err, w, buf[(k + 1) & 1], bexp[(k + 1) & 1], ps, cs);
         if (e != cudaSuccess) return e;
@@ -1080,7 +1083,8 @@ cudaError_t launch_cholesky_tc(double *A, int64_t n, int *info, int *err, void *
             slot = prof_begin(NK_PROF_CHOL_UPDATE, st);
             e = launch_ozaki_gemm_strided(Lk + (size_t)kb1 * kTileK, Le + kb1, rest2, rest, Lk + (size_t)kb1 * kTileK,
                                           Le + kb1, rest2, rest, S, C1 + (size_t)kb1 * n + kb1, n, 1, true, err, st);
-            prof_end(slot, st, ozaki_mma_flops(rest2, rest2, S, true));
+            // FP64 flops of the lower rest2 x rest2 trailing update, K = kNB
+            prof_end(slot, st, (double)kNB * rest2 * (double)(rest2 + 1), ozaki_mma_flops(rest2, rest2, S, true));
             if (e != cudaSuccess) return e;
         }
         if (two) {
@@ -1143,7 +1147,8 @@ cudaError_t launch_gram_cols_tc(const double *X, int64_t rows, int64_t ncols, do
         const dim3 grid(nblk(ncols, 256), (unsigned)(ncols < 65535 ? ncols : 65535));
         (k_scale_shift_lower<<<grid, 256, 0, st>>>(C, ncols, scale, eps), nk::note_launch());
     }
-    prof_end(slot, st, (double)((rows + kTileK - 1) / kTileK) * ozaki_mma_flops(ncols, ncols, S, true));
+    prof_end(slot, st, (double)rows * ncols * (double)(ncols + 1),
+             (double)((rows + kTileK - 1) / kTileK) * ozaki_mma_flops(ncols, ncols, S, true));
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
@@ -1160,7 +1165,10 @@ cudaError_t launch_gram_tc(int N, int M, int64_t Ns, const int8_t *s, const doub
     }
     dim3 grid(nblk(Ns, 64), nblk(Ns, 64));
     (k_gram_combine<<<grid, 256, 0, st>>>(N, Ns, s, K), nk::note_launch());
-    prof_end(slot, st, (double)((M + kTileK - 1) / kTileK) * ozaki_mma_flops(Ns, Ns, S, true));
+    // the lower triangle of the Jacobian-row Gram through s.s + t.t + (t.t)(s.s):
+    // (N + M) flops per entry, the count of the FP64 path
+    prof_end(slot, st, (double)Ns * (Ns + 1) * (double)(N + M),
+             (double)((M + kTileK - 1) / kTileK) * ozaki_mma_flops(Ns, Ns, S, true));
     return cudaGetLastError();
 }
 

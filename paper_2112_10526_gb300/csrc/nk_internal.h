@@ -28,7 +28,10 @@ namespace nk {
 void set_plan_only(bool on);
 
 // Kernel timing hooks (prof.cu).  prof_begin returns a slot (or -1 when
-// timing is off); prof_end closes it and adds `work` to the class.
+// timing is off); prof_end closes it and adds `work` (the method's
+// algorithmic work: ratio terms, or the flops of the FP64 operation) and
+// `executed` (what the hardware ran, e.g. BF16 slice-product flops; < 0:
+// equal to work) to the class.
 int prof_begin(int cls, cudaStream_t st);
 // Sets the message returned by nk_last_error on this thread; returns code.
 nk_status report_error(nk_status code, const char *msg);
@@ -40,7 +43,7 @@ void note_launch(long long n = 1);
 // with different sizes; a constant maximum does not (occupancy follows the
 // size given at launch, not this limit).
 cudaError_t allow_max_dynamic_smem(const void *func);
-void prof_end(int slot, cudaStream_t st, double work);
+void prof_end(int slot, cudaStream_t st, double work, double executed = -1.0);
 
 // Per-parameter tables of the flip-ratio identity (see k_rbm.cu).  All
 // pointers are device workspace.  R = double (NK_F64) or float (NK_MIXED).

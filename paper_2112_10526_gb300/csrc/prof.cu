@@ -15,7 +15,7 @@ namespace {
 struct Slot {
     cudaEvent_t start, stop;
     int cls;
-    double work;
+    double work, exec;
     bool closed;
 };
 
@@ -63,6 +63,7 @@ int prof_begin(int cls, cudaStream_t st) {
     Slot &s = g_slots[g_used];
     s.cls = cls;
     s.work = 0.0;
+    s.exec = 0.0;
     s.closed = false;
     if (cudaEventRecord(s.start, st) != cudaSuccess) {
         cudaGetLastError();
@@ -71,7 +72,7 @@ int prof_begin(int cls, cudaStream_t st) {
     return (int)g_used++;
 }
 
-void prof_end(int slot, cudaStream_t st, double work) {
+void prof_end(int slot, cudaStream_t st, double work, double executed) {
     if (slot < 0) return;
     std::lock_guard<std::mutex> lk(g_mu);
     if ((size_t)slot >= g_used) return;
@@ -81,6 +82,7 @@ void prof_end(int slot, cudaStream_t st, double work) {
         return;
     }
     s.work = work;
+    s.exec = executed < 0.0 ? work : executed;
     s.closed = true;
 }
 
@@ -115,6 +117,16 @@ nk_status nk_prof_read(int32_t cls, double *ms, int64_t *launches, double *work)
     *ms = t;
     *launches = n;
     *work = w;
+    return NK_OK;
+}
+
+nk_status nk_prof_read_executed(int32_t cls, double *executed) {
+    if (cls < 0 || cls >= NK_PROF_N || !executed) return NK_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_mu);
+    double x = 0.0;
+    for (size_t i = 0; i < g_used; ++i)
+        if (g_slots[i].cls == cls && g_slots[i].closed) x += g_slots[i].exec;
+    *executed = x;
     return NK_OK;
 }
 

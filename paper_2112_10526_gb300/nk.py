@@ -154,6 +154,8 @@ def lib():
     L.nk_prof_read.argtypes = [i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                                ctypes.POINTER(ctypes.c_double)]
     L.nk_prof_read.restype = ctypes.c_int32
+    L.nk_prof_read_executed.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
+    L.nk_prof_read_executed.restype = ctypes.c_int32
     L.nk_prof_trace.argtypes = [i32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double),
                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]
     L.nk_prof_trace.restype = ctypes.c_int32
@@ -389,11 +391,21 @@ def nk_prof_enable(on=True):
 
 
 def nk_prof_read(cls):
-    """(milliseconds, launches, work) of a tracked kernel class since nk_prof_enable."""
+    """(milliseconds, launches, algorithmic work) of a tracked kernel class
+    since nk_prof_enable."""
     ms, n, w = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
     c = PROF_CLASSES[cls] if isinstance(cls, str) else int(cls)
     _check(lib().nk_prof_read(c, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(w)))
     return ms.value, n.value, w.value
+
+
+def nk_prof_read_executed(cls):
+    """Work the hardware executed for the same launches (BF16 slice-product
+    flops of the tensor-core paths)."""
+    x = ctypes.c_double()
+    c = PROF_CLASSES[cls] if isinstance(cls, str) else int(cls)
+    _check(lib().nk_prof_read_executed(c, ctypes.byref(x)))
+    return x.value
 
 
 def nk_prof_trace():

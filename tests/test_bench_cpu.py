@@ -21,7 +21,7 @@ def test_workloads_and_rule_override():
 def test_roofline_of_an_alu_class():
     """Ratio terms count one FMA and one multiply: 2 flops each, against the
     FP32 lanes for the mixed path and the FP64 pipe for the FP64 path."""
-    prof = {"sweep": (20.0, 4, 5e11), "eloc": (5.0, 4, 1e11)}
+    prof = {"sweep": (20.0, 4, 5e11, 5e11), "eloc": (5.0, 4, 1e11, 1e11)}
     rf, cls = bench.roofline(prof, 2, "mixed")
     assert cls == "sweep" and rf["bound"] == "alu"
     assert rf["achieved"] == pytest.approx(2 * 5e11 / 0.020 / 1e12)
@@ -32,20 +32,46 @@ def test_roofline_of_an_alu_class():
 
 
 def test_roofline_of_the_tensor_class_with_traffic():
-    """The tensor-core classes are rated against the measured sustained BF16
-    peak, and the Cholesky products carry the captured DRAM bytes per tile
+    """The tensor-core classes are rated by the method's algorithmic flops
+    (the FP64 operation) against the measured sustained BF16 peak; the BF16
+    slice-product flops they executed are reported beside, not in, the
+    fraction.  The Cholesky products carry the captured DRAM bytes per tile
     scaled to a launch, as long as the kernel source is the captured one."""
     tiles = 1000.0
-    prof = {"chol_update": (10.0, 5, tiles * bench.OZAKI_TILE_FLOPS), "sweep": (1.0, 1, 1.0)}
+    n = 8192.0
+    algo = n ** 3 / 3
+    prof = {"chol_update": (10.0, 5, algo, tiles * bench.OZAKI_TILE_FLOPS), "sweep": (1.0, 1, 1.0, 1.0)}
     rf, cls = bench.roofline(prof, 1, "mixed")
     peaks, _src = bench.measured_peaks()
     assert cls == "chol_update" and rf["bound"] == "tensor"
     assert rf["peak"] == peaks["bf16_tflops_sustained"]
-    assert rf["frac"] == pytest.approx(tiles * bench.OZAKI_TILE_FLOPS / 0.010 / 1e12 / rf["peak"])
+    assert rf["achieved"] == pytest.approx(algo / 0.010 / 1e12)
+    assert rf["frac"] == pytest.approx(algo / 0.010 / 1e12 / rf["peak"])
+    assert rf["executed_tflops"] == pytest.approx(tiles * bench.OZAKI_TILE_FLOPS / 0.010 / 1e12)
     if bench.ozaki_source_hash().startswith(bench.OZAKI_TRAFFIC["source_sha256_prefix"]):
         assert rf["traffic"] == pytest.approx(tiles * bench.OZAKI_TRAFFIC["bytes_per_tile"] / 5)
     else:
         assert rf["traffic"] is None
+
+
+def test_headline_defaults_and_oracle_sample():
+    """The default workload is the largest single-GPU configuration (24 x 24
+    Heisenberg, Ns = 65536, CG), with the FP64 arm and the serving stream of
+    512 requests; the oracle's bounded sample is a few chains of it."""
+    import sys
+    argv = sys.argv
+    try:
+        sys.argv = ["bench.py"]
+        a = bench.parse()
+    finally:
+        sys.argv = argv
+    assert a.workload == "heis2d_24x24" and a.serve == 512 and not a.no_compare
+    w = bench.workload(a.workload)
+    assert (w["N"], w["M"], w["chains"] * w["per_chain"], w["solver"]) == (576, 4608, 65536, "cg")
+    cfg = bench.workload_config(w, "mixed", 1)
+    assert cfg["cg_tol"] == 1e-6 and bench.workload_config(w, "f64", 1)["cg_tol"] == 1e-10
+    assert 1 <= bench.oracle_chains(a.workload) < w["chains"]
+    assert bench.host_cores() >= 1
 
 
 def test_l2_text_names_the_array_that_outgrows_l2():
