@@ -35,6 +35,13 @@ def rbm_params(N: int, M: int, seed: int, sigma: float = 0.01) -> np.ndarray:
     return np.concatenate([a, b, W.ravel()]).astype(np.float64)
 
 
+def symm_params(N: int, alpha: int, seed: int, sigma: float = 0.01) -> np.ndarray:
+    """Symmetric-RBM parameters [a (1); b (alpha); W (alpha x N)] i.i.d.
+    N(0, sigma^2), drawn in that order from default_rng(seed)."""
+    rng = np.random.default_rng(seed)
+    return rng.normal(0.0, sigma, size=1 + alpha + alpha * N)
+
+
 def chain_edges(L: int) -> np.ndarray:
     return np.array([[i, (i + 1) % L] for i in range(L)], dtype=np.int32).reshape(-1, 2)
 
@@ -129,6 +136,12 @@ WORKLOADS = {
     "heis2d_24x24": dict(N=576, alpha=8, ham=lambda: heis_square(24, 1.0, True), rule="exchange",
                          chains=8192, per_chain=8, discard=16, seed=5, diag_shift=0.01, lr=0.01,
                          solver="cg"),
+    # Sec. 5: the symmetric RBM (RBMSymm) on the 10 x 10 Heisenberg lattice,
+    # alpha = 4 features over the 100 translations (400 tied hidden units,
+    # 405 parameters), dense Cholesky in the symmetric parameters.
+    "heis2d_10x10_symm": dict(N=100, alpha=4, symm="translations_square", ham=lambda: heis_square(10, 1.0, True),
+                              rule="exchange", chains=1024, per_chain=8, discard=16, seed=7, diag_shift=0.01,
+                              lr=0.01, solver="cholesky"),
     # Sec. 7: J1 = 1, J2 = 0.5 on the 10 x 10 square lattice, exchange moves
     # over both edge classes (d_max = 2), one sample per chain (n_chains =
     # n_samples = 1024), with the RBM of heis2d_10x10 in place of the GCNN.
