@@ -69,7 +69,7 @@ def parse():
     ap.add_argument("--workload", default="heis2d_24x24",
                     help="workload name, optionally with @rule to replace its sampler rule "
                          "(e.g. heis2d_10x10@hamiltonian)")
-    ap.add_argument("--extra", default="heis2d_10x10",
+    ap.add_argument("--extra", default="heis2d_10x10,heis2d_10x10_symm",
                     help="comma-separated workloads timed after the headline (mixed path, same steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the other-precision timing")
@@ -91,8 +91,15 @@ def workload(name):
         assert rule in ("local", "exchange", "hamiltonian"), rule
         w["rule"] = rule
     w["name"] = name
-    w["M"] = w["alpha"] * w["N"]
     w["ham"] = w["ham"]()
+    if "symm" in w:
+        w["perms"] = getattr(I, w["symm"])(int(round(w["N"] ** 0.5))) if w["symm"] == "translations_square" \
+            else getattr(I, w["symm"])(w["N"])
+        w["M"] = w["alpha"] * w["perms"].shape[0]  # expanded hidden units
+        w["Np"] = 1 + w["alpha"] + w["alpha"] * w["N"]
+    else:
+        w["M"] = w["alpha"] * w["N"]
+        w["Np"] = w["N"] + w["M"] + w["M"] * w["N"]
     return w
 
 
@@ -241,7 +248,11 @@ def setup(w, precision, rank, dev):
     from paper_2112_10526_gb300 import nk
     N, M, C = w["N"], w["M"], w["chains"]
     st = {"N": N, "M": M, "C": C, "ns": w["per_chain"]}
-    st["params"] = torch.from_numpy(I.rbm_params(N, M, w["seed"])).to(dev)
+    if "symm" in w:
+        st["symm"] = (w["alpha"], torch.from_numpy(w["perms"].astype("int32")).to(dev))
+        st["params"] = torch.from_numpy(I.symm_params(N, w["alpha"], w["seed"])).to(dev)
+    else:
+        st["params"] = torch.from_numpy(I.rbm_params(N, M, w["seed"])).to(dev)
     st["edges"] = torch.from_numpy(w["ham"]["edges"]).to(dev)
     st["ham"] = nk.make_ham(w["ham"]["kind"], w["ham"]["J"], w["ham"].get("h", 0.0),
                             w["ham"].get("marshall", False), st["edges"], w["ham"].get("J2", 0.0),
@@ -260,6 +271,11 @@ def setup(w, precision, rank, dev):
 def step(st, first=False):
     from paper_2112_10526_gb300 import nk
     st["cfg"].n_discard = st["cfg"].n_discard if first else 0
+    if "symm" in st:
+        alpha, perms = st["symm"]
+        nk.nk_symm_sr_step(st["ctx"], st["params"], st["N"], alpha, perms, st["ham"], st["chains"], st["cfg"],
+                           st["stats"])
+        return
     nk.nk_sr_step(st["ctx"], st["params"], st["N"], st["M"], st["ham"], st["chains"], st["cfg"],
                   st["stats"])
 
@@ -488,8 +504,10 @@ def measure(w, precision, K, warmup, rank, world, dev, prof=True, e2e=True):
 
 def workload_config(w, precision, world):
     Ns = w["chains"] * w["per_chain"]
-    Np = w["N"] + w["M"] + w["M"] * w["N"]
+    Np = w["Np"]
     cfg = {"workload": w["name"], "lattice": lattice_text(w["N"]), "hamiltonian": ham_text(w["ham"]),
+           "model": (f"symmetric RBM, alpha = {w['alpha']} over {w['perms'].shape[0]} translations"
+                     if "symm" in w else f"RBM, alpha = {w['alpha']}"),
            "N": w["N"], "M": w["M"], "Np": Np, "chains": w["chains"], "samples_per_chain": w["per_chain"],
            "Ns": Ns, "rule": w["rule"], "solver": w["solver"], "precision": precision,
            "diag_shift": w["diag_shift"], "lr": w["lr"], "parallelism": f"replicas x{world}",

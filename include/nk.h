@@ -71,6 +71,10 @@ typedef int32_t nk_status;
 #define NK_SOLVER_CHOLESKY 0             /* dense (S + eps I) in parameter space */
 #define NK_SOLVER_CHOLESKY_SAMPLESPACE 1 /* same solution via an Ns x Ns factor */
 #define NK_SOLVER_CG 2                   /* CG on on-the-fly QGT products */
+#define NK_SOLVER_SVD 3                  /* pseudo-inverse of the dense (S + eps I) in parameter
+                                            space, eigenvalues below rcond x the largest dropped */
+#define NK_SOLVER_SVD_SAMPLESPACE 4      /* the same truncated solve (eps = 0) from the
+                                            eigenpairs of the Ns x Ns sample-space Gram */
 
 #define NK_QGT_ONTHEFLY 0 /* QGTOnTheFly (App. B.3) */
 #define NK_QGT_JACOBIAN 1 /* QGTJacobianDense on a stored centred Jacobian (App. B.2) */
@@ -293,16 +297,26 @@ nk_status nk_tc_gemm(nk_ctx *ctx, int64_t rows, int64_t cols, int32_t k, const d
  * systems").  solver: NK_SOLVER_CHOLESKY (dense Np x Np FP64 Cholesky),
  * NK_SOLVER_CHOLESKY_SAMPLESPACE (FP64 Cholesky of the Ns x Ns matrix
  * dJ dJ^T / Ns + diag_shift I and delta = (F - dJ^T y / sqrt(Ns)) /
- * diag_shift, equal in exact arithmetic), NK_SOLVER_CG (x0 = 0, stops at
- * ||r|| <= cg_tol ||F|| or cg_maxiter; reads the residual back to the host
- * every 8 iterations, which synchronises the stream).  With NK_MIXED the
- * Cholesky factorisations run their panel and trailing products on the
- * tensor cores at FP64-level accuracy (see nk_tc_gemm), and so does the
- * sample-space Gram; the call then synchronises the stream and returns
- * NK_ERR_CUDA on a failed factorisation (NK_ERR_TIMEOUT on a tensor-core
- * time-out).
- *   info_out host int32[2] or NULL: iterations, converged flag.
- *   resid_out host double or NULL: final relative residual (CG).
+ * diag_shift, equal in exact arithmetic), NK_SOLVER_CG (Jacobi-preconditioned
+ * conjugate gradients, x0 = 0, stops at ||r|| <= cg_tol ||F|| or cg_maxiter;
+ * reads the residual back to the host every 8 iterations, which
+ * synchronises the stream), NK_SOLVER_SVD (the pseudo-inverse of the dense
+ * Np x Np matrix S + diag_shift I, keeping the eigenvalues above rcond times
+ * the largest) and NK_SOLVER_SVD_SAMPLESPACE (the same truncated solve at
+ * diag_shift = 0 from the eigenpairs (lambda_k, u_k) of X X^T, X = dJ /
+ * sqrt(Ns): delta = X^T sum_{lambda_k > rcond max lambda} u_k lambda_k^-2
+ * u_k^T X F).  For the two SVD solvers cg_tol is rcond (0: 1e-12); their
+ * eigendecomposition is cyclic Jacobi in FP64 on CUDA cores, which reads
+ * its convergence back once per sweep (synchronises the stream); n = Np or
+ * Ns at most 8192.  With NK_MIXED the Cholesky factorisations run their
+ * panel and trailing products on the tensor cores at FP64-level accuracy
+ * (see nk_tc_gemm), and so do the Gram matrices; the call then synchronises
+ * the stream and returns NK_ERR_CUDA on a failed factorisation
+ * (NK_ERR_TIMEOUT on a tensor-core time-out).
+ *   info_out host int32[2] or NULL: iterations (CG) or Jacobi sweeps (SVD),
+ *   converged flag.
+ *   resid_out host double or NULL: final relative residual (CG), or the
+ *   relative off-diagonal norm left by the sweeps (SVD).
  */
 nk_status nk_sr_solve(nk_ctx *ctx, const nk_rbm *rbm, int32_t precision, const int8_t *s,
                       int64_t Ns, const double *F, int32_t solver, double diag_shift,
@@ -332,6 +346,7 @@ typedef struct {
     double cg_tol;
     uint64_t seed;
     uint32_t stream_id;
+    double svd_rcond;    /* NK_SOLVER_SVD*: relative cutoff of the eigenvalues (0: 1e-12) */
 } nk_sr_cfg;
 
 /* Diagnostics of one step, written to DEVICE memory (float64 fields). */
@@ -363,6 +378,60 @@ nk_status nk_sr_step(nk_ctx *ctx, nk_rbm *rbm, const nk_ham *ham, nk_chains *cha
                      const nk_sr_cfg *cfg, nk_sr_stats *stats_out, int8_t *samples_out,
                      double *eloc_out, void *stream);
 
+
+/* ------------------------------------------------------ symmetric RBM ---
+ * RBMSymm (Sec. 5, "fully symmetric RBMs"): a permutation group G of the
+ * sites, given as rows perms[g][j] = pi_g(j) (each a permutation of [0, N);
+ * the identity need not come first), and alpha features whose activation at
+ * group element g is the embedding layer of Eq. eq: equivariant: embedding,
+ *     theta_{f,g}(s) = b_f + sum_j W_{f,j} s_{pi_g(j)},
+ * with ln psi(s) = a sum_j s_j + sum_{f,g} ln cosh theta_{f,g}(s).  The
+ * printed form has no biases; a hidden bias per feature and one visible bias
+ * (the symmetric restriction of the RBM's) are kept, and vanish at zero.
+ * Parameters: one float64 device vector [a (1); b (alpha); W (alpha x N,
+ * row-major)], Np = 1 + alpha + alpha N.  psi is invariant under G.
+ * The model equals a plain RBM with M = alpha |G| hidden units and tied
+ * parameters (unit f |G| + g: bias b_f, weight W_{f,j} on site pi_g(j), every
+ * visible bias a); the sampler and the local energies run on those expanded
+ * parameters.  Limits: N <= 4096, alpha |G| <= 8192.
+ */
+typedef struct {
+    int32_t N;             /* sites */
+    int32_t alpha;         /* features */
+    int32_t n_group;       /* |G| */
+    const int32_t *perms;  /* device [n_group, N] */
+    double *params;        /* device [1 + alpha + alpha N]; only nk_symm_sr_step writes it */
+} nk_rbm_symm;
+
+/* The equal plain RBM's parameters: plain_out device [N + M + M N], M =
+ * alpha n_group.  Checks first that every row of perms is a permutation of
+ * [0, N) (NK_ERR_INVALID_ARG otherwise); the check reads one flag back and
+ * synchronises the stream. */
+nk_status nk_symm_expand(nk_ctx *ctx, const nk_rbm_symm *symm, double *plain_out, void *stream);
+
+/* Log-derivatives in the symmetric parameters (Eq. eq:log-derivative-O by
+ * the chain rule through the tying): O_a = sum_j s_j, O_{b_f} = sum_g
+ * tanh theta_{f,g}, O_{W_{f,j}} = sum_g tanh theta_{f,g} s_{pi_g(j)}.
+ *   s [Ns, N];  O_out [Ns, Np] float64, uncentred.
+ * theta in FP64 (NK_F64) or by the FP64-exact tensor-core product (NK_MIXED);
+ * the sums in FP64.  Synchronises the stream (permutation check). */
+nk_status nk_symm_jacobian(nk_ctx *ctx, const nk_rbm_symm *symm, int32_t precision, const int8_t *s,
+                           int64_t Ns, double *O_out, void *stream);
+
+/* One VMC iteration with stochastic reconfiguration (Sec. 4.1) for the
+ * symmetric RBM: the chains and local energies of the expanded RBM (the same
+ * psi), then the centred Jacobian in the Np symmetric parameters, the force
+ * F = (2/Ns) dJ^T (E_loc - mean), S = dJ^T dJ / Ns + diag_shift I, its
+ * Cholesky factor, two triangular solves, and params <- params - lr delta.
+ * cfg->solver must be NK_SOLVER_CHOLESKY (NK_ERR_UNIMPLEMENTED otherwise):
+ * Np is small enough for the dense factor.  NK_MIXED runs the sweeps and
+ * local energies in FP32 as nk_sr_step does, and builds and factors S with
+ * the FP64-accurate tensor-core products.  The other arguments, and the
+ * diagnostics, as nk_sr_step.  Synchronises the stream (permutation check;
+ * NK_MIXED also reads the factorisation status). */
+nk_status nk_symm_sr_step(nk_ctx *ctx, nk_rbm_symm *symm, const nk_ham *ham, nk_chains *chains,
+                          const nk_sr_cfg *cfg, nk_sr_stats *stats_out, int8_t *samples_out, double *eloc_out,
+                          void *stream);
 
 /* ------------------------------------------------------------- serving ---
  * A persistent request loop on one GPU for VMC expectation values and SR

@@ -198,6 +198,10 @@ struct SolveWs {
     double *dJ, *S, *mean, *ones;
     int *info;  // [0] breakdown pivot, [1] tensor-core time-out code
     double *K, *rowmean;
+    // SVD solvers: eigenvectors, eigenvalues, their largest, Jacobi workspace
+    double *V, *ev, *evmax, *z, *gpart;
+    void *eig;
+    int *kept;
     void *tc;   // tensor-core slices and inverted diagonal blocks (NK_MIXED)
     void *tcm;  // tensor-core Jacobian-product workspace (NK_MIXED)
     int *tcerr; // sticky tensor-core error word of the context
@@ -230,6 +234,30 @@ void carve_solve(Carver &c, SolveWs &w, int N, int M, int64_t Ns, int solver, in
         w.ones = c.take<double>(Ns);
         w.info = c.take<int>(2);
         if (precision == NK_MIXED) w.tc = c.take<char>(nk::tc_chol_ws_bytes(Np));
+    } else if (solver == NK_SOLVER_SVD || solver == NK_SOLVER_SVD_SAMPLESPACE) {
+        const bool ss = solver == NK_SOLVER_SVD_SAMPLESPACE;
+        const int64_t n = ss ? Ns : Np;
+        if (ss) {
+            w.U = c.take<double>((size_t)Ns * (M + 1));
+            w.w = c.take<double>(Ns);
+            w.rowmean = c.take<double>(2 * Ns + 1);
+            w.tmp = c.take<double>(Np);
+            if (precision == NK_MIXED) w.tc = c.take<char>(nk::tc_chol_ws_bytes(Ns));
+        } else {
+            w.dJ = c.take<double>((size_t)Ns * Np);
+            w.mean = c.take<double>(Np);
+            w.ones = c.take<double>(Ns);
+            if (precision == NK_MIXED) w.tc = c.take<char>(nk::tc_chol_ws_bytes(Np));
+        }
+        w.K = c.take<double>((size_t)n * n);
+        w.V = c.take<double>((size_t)n * n);
+        w.ev = c.take<double>(n);
+        w.evmax = c.take<double>(4);
+        w.z = c.take<double>(n);
+        w.gpart = c.take<double>(nk::gemv_t_partial_doubles(n, n));
+        w.eig = c.take<char>(nk::eig_ws_bytes(n));
+        w.kept = c.take<int>(4);
+        w.info = c.take<int>(2);
     } else {
         w.U = c.take<double>((size_t)Ns * (M + 1));
         w.w = c.take<double>(Ns);
@@ -246,6 +274,10 @@ void carve_solve(Carver &c, SolveWs &w, int N, int M, int64_t Ns, int solver, in
 // (2^-32 of the row maximum), 7 (FP64 level) where the sample-space solve
 // subtracts nearly equal vectors.
 constexpr int kMatvecSlices = 4, kExactSlices = 7;
+// Jacobi sweeps of the SVD solvers: stop at a relative off-diagonal norm of
+// 1e-14 (the rounding level of FP64 rotations), at most 60 sweeps.
+constexpr int kMaxJacobiSweeps = 60;
+constexpr double kJacobiTol = 1e-14;
 
 cudaError_t jvp_any(int N, int M, int64_t Ns, const int8_t *s, const double *T, const double *v, SolveWs &w,
                     double *out, int precision, int slices, cudaStream_t st) {
@@ -338,6 +370,79 @@ nk_status run_solve(nk_ctx *ctx, int N, int M, int64_t Ns, const int8_t *s, cons
                         tol, maxiter, res);
         return NK_OK;
     }
+    if (solver == NK_SOLVER_SVD || solver == NK_SOLVER_SVD_SAMPLESPACE) {
+        const bool ss = solver == NK_SOLVER_SVD_SAMPLESPACE;
+        const int64_t n = ss ? Ns : Np;
+        const double rcond = tol > 0.0 ? tol : 1e-12;
+        NK_CU(cudaMemsetAsync(w.info, 0, 2 * sizeof(int), st), "svd");
+        if (ss) {
+            // the centred sample-space Gram X X^T, X = dJ / sqrt(Ns), no shift
+            if (tc) {
+                NK_CU(nk::launch_gram_tc(N, M, Ns, s, T, 7, w.K, w.info + 1, w.tc, st), "svd gram");
+                NK_CU(nk::launch_center_gram(Ns, w.K, w.rowmean, 0.0, st), "svd gram");
+            } else {
+                NK_CU(nk::launch_gram_samplespace(N, M, Ns, s, T, 0.0, w.K, w.rowmean, st), "svd gram");
+            }
+        } else {
+            // the dense S + eps I from the centred Jacobian
+            NK_CU(nk::launch_fill(Ns, 1.0, w.ones, st), "svd mean");
+            NK_CU(nk::launch_vjp(N, M, Ns, s, T, w.ones, 1.0 / (double)Ns, nullptr, w.partial, w.mean, st),
+                  "svd mean");
+            NK_CU(nk::launch_jacobian_rows(N, M, s, T, 0, Ns, w.mean, w.dJ, st), "svd dJ");
+            if (tc)
+                NK_CU(nk::launch_gram_cols_tc(w.dJ, Ns, Np, 1.0 / (double)Ns, eps, w.K, w.info + 1, w.tc, st),
+                      "svd S");
+            else
+                NK_CU(nk::launch_syrk_t(w.dJ, Ns, Np, 1.0 / (double)Ns, eps, w.K, st), "svd S");
+        }
+        NK_CU(nk::launch_symmetrize_lower(n, w.K, st), "svd");
+        NK_CU(nk::launch_identity(n, w.V, st), "svd");
+        // cyclic Jacobi sweeps until the off-diagonal part is at the rounding level
+        int sweeps = 0;
+        bool converged = false;
+        double rel = 0.0;
+        for (; sweeps < kMaxJacobiSweeps; ++sweeps) {
+            NK_CU(nk::launch_offdiag_norms(w.K, n, w.eig, w.evmax + 2, st), "svd norms");
+            NK_CU(cudaMemcpyAsync(ctx->host_vals, w.evmax + 2, 2 * sizeof(double), cudaMemcpyDeviceToHost, st),
+                  "svd norms");
+            NK_CU(cudaStreamSynchronize(st), "svd norms");
+            const double off = ctx->host_vals[0], tot = ctx->host_vals[0] + ctx->host_vals[1];
+            rel = tot > 0.0 ? std::sqrt(off / tot) : 0.0;
+            if (rel <= kJacobiTol) {
+                converged = true;
+                break;
+            }
+            NK_CU(nk::launch_jacobi_sweep(w.K, w.V, n, w.eig, st), "svd sweep");
+        }
+        NK_CU(nk::launch_eig_diag(n, w.K, w.ev, w.evmax, st), "svd eigenvalues");
+        NK_CU(cudaMemsetAsync(w.kept, 0, sizeof(int), st), "svd");
+        if (ss) {
+            // y = X F, z = U^T y / lambda^2 (kept), y = U z, delta = X^T y
+            const double isq = 1.0 / std::sqrt((double)Ns);
+            NK_CU(jvp_any(N, M, Ns, s, T, F, w, w.w, precision, kExactSlices, st), "svd XF");
+            NK_CU(nk::launch_center(Ns, w.w, w.dotp, isq, st), "svd XF");
+            NK_CU(nk::launch_gemv_t(w.V, n, n, w.w, 1.0, w.gpart, w.z, st), "svd U^T y");
+            NK_CU(nk::launch_spectral_filter(n, w.ev, w.evmax, rcond, 2, w.z, w.kept, st), "svd filter");
+            NK_CU(nk::launch_gemv_rows(w.V, n, n, w.z, w.w, st), "svd U z");
+            NK_CU(nk::launch_center(Ns, w.w, w.dotp, isq, st), "svd X^T y");
+            NK_CU(vjp_any(N, M, Ns, s, T, w.w, 1.0, nullptr, w, delta, precision, kExactSlices, st), "svd X^T y");
+        } else {
+            // delta = V diag(1 / lambda, kept) V^T F
+            NK_CU(nk::launch_gemv_t(w.V, n, n, F, 1.0, w.gpart, w.z, st), "svd V^T F");
+            NK_CU(nk::launch_spectral_filter(n, w.ev, w.evmax, rcond, 1, w.z, w.kept, st), "svd filter");
+            NK_CU(nk::launch_gemv_rows(w.V, n, n, w.z, delta, st), "svd V z");
+        }
+        if (host_info) host_info[0] = sweeps, host_info[1] = converged ? 1 : 0;
+        if (host_resid) *host_resid = rel;
+        if (tc) {
+            nk_status f = check_factor(ctx, w.info, st);
+            if (f != NK_OK) return f;
+        }
+        if (!converged)
+            return fail(NK_ERR_NOT_CONVERGED, "Jacobi sweeps left a relative off-diagonal norm %g after %d sweeps",
+                        rel, sweeps);
+        return NK_OK;
+    }
     if (solver == NK_SOLVER_CHOLESKY) {
         NK_CU(nk::launch_fill(Ns, 1.0, w.ones, st), "chol");
         NK_CU(nk::launch_vjp(N, M, Ns, s, T, w.ones, 1.0 / (double)Ns, nullptr, w.partial, w.mean, st),
@@ -428,15 +533,89 @@ nk_status batch_T(nk_ctx *ctx, const nk_rbm *rbm, const int8_t *s, int64_t B, do
     return NK_OK;
 }
 
+// The sampling half of a VMC step, shared by the plain and the symmetric
+// RBM: the flip-ratio tables of `rbm`, the sweeps of the chains (rule and
+// its edge count already mapped), T = tanh theta of every sample, the local
+// energies and their statistics (mean, variance, error) in st3.
+struct StepBufs {
+    int8_t *samples;
+    double *eloc, *T, *st3, *theta;
+    unsigned long long *acc;
+    void *tcm;
+};
+
+template <typename R>
+void carve_step(Carver &c, nk::Tables<R> &t, StepBufs &b, const nk_rbm *rbm, const nk_ham *ham, int C,
+                int64_t Ns, bool site, bool edge, bool mixed, int8_t *samples_out, double *eloc_out) {
+    const int N = rbm->N, M = rbm->M;
+    carve_tables(c, t, rbm, ham->n_edges, ham->edges, site, edge);
+    b.samples = samples_out ? samples_out : c.take<int8_t>((size_t)Ns * N);
+    b.eloc = eloc_out ? eloc_out : c.take<double>(Ns);
+    b.T = c.take<double>((size_t)Ns * M);
+    b.st3 = c.take<double>(4);
+    b.acc = c.take<unsigned long long>(C);
+    const int64_t TB = Ns > C ? Ns : C;
+    b.theta = mixed ? c.take<double>((size_t)TB * M) : nullptr;
+    b.tcm = mixed ? c.take<char>(tcm_bytes(N, M, TB)) : nullptr;
+}
+
+template <typename R>
+nk_status run_sample_measure(nk_ctx *ctx, const nk::Tables<R> &t, const StepBufs &b, const nk_ham *ham,
+                             const nk_chains *chains, const nk_sr_cfg *cfg, int rule, int E_rule, bool site,
+                             bool edge, bool mixed, cudaStream_t st) {
+    const int N = t.N, M = t.M, C = chains->C;
+    const int64_t Ns = (int64_t)C * cfg->n_samples;
+    NK_CU(nk::launch_tables(t, site, edge, st), "tables");
+    NK_CU(cudaMemsetAsync(b.acc, 0, sizeof(unsigned long long) * C, st), "memset");
+    nk::SweepArgs a{};
+    a.N = N;
+    a.M = M;
+    a.E = E_rule;
+    a.C = C;
+    a.rule = rule;
+    a.edges = ham->edges;
+    a.s = chains->s;
+    a.sweep0 = chains->sweeps_done;
+    a.n_discard = cfg->n_discard;
+    a.n_samples = cfg->n_samples;
+    a.seed = cfg->seed;
+    a.stream_id = cfg->stream_id;
+    a.samples = b.samples;
+    a.logpsi = nullptr;
+    a.n_accepted = b.acc;
+    a.decisions = nullptr;
+    nk::Tables<R> ts = t;  // the rule's edges: a prefix of the Hamiltonian's
+    ts.E = E_rule;
+    nk_status sw = run_sweeps(ctx, ts, a, mixed, b.theta, b.tcm, st);
+    if (sw != NK_OK) return sw;
+    if (mixed)
+        NK_CU(nk::launch_theta_tc(N, M, t.b, t.W, b.samples, Ns, b.theta, ctx->tc_err, b.tcm, st), "theta");
+    nk::ElocArgs ea = nk::eloc_args(ham, b.samples, Ns, b.eloc, b.T, b.theta);
+    NK_CU(nk::launch_eloc(t, ea, st), "local energy");
+    NK_CU(nk::launch_stats(b.eloc, Ns, C, b.st3, st), "stats");
+    return NK_OK;
+}
+
 nk_status check_solver(int solver, double eps, double tol, int maxiter) {
-    if (solver != NK_SOLVER_CG && solver != NK_SOLVER_CHOLESKY &&
-        solver != NK_SOLVER_CHOLESKY_SAMPLESPACE)
+    if (solver != NK_SOLVER_CG && solver != NK_SOLVER_CHOLESKY && solver != NK_SOLVER_CHOLESKY_SAMPLESPACE &&
+        solver != NK_SOLVER_SVD && solver != NK_SOLVER_SVD_SAMPLESPACE)
         return fail(NK_ERR_INVALID_ARG, "solver %d unknown", solver);
+    if ((solver == NK_SOLVER_SVD || solver == NK_SOLVER_SVD_SAMPLESPACE) && !(tol >= 0.0 && tol < 1.0))
+        return fail(NK_ERR_INVALID_ARG, "the SVD cutoff rcond must be in [0, 1)");
     if (!(eps > 0.0) && solver == NK_SOLVER_CHOLESKY_SAMPLESPACE)
         return fail(NK_ERR_INVALID_ARG, "the sample-space solve needs diag_shift > 0");
     if (!(eps >= 0.0)) return fail(NK_ERR_INVALID_ARG, "diag_shift must be >= 0");
     if (solver == NK_SOLVER_CG && (maxiter < 1 || !(tol > 0.0)))
         return fail(NK_ERR_INVALID_ARG, "CG needs cg_maxiter >= 1 and cg_tol > 0");
+    return NK_OK;
+}
+
+// The SVD solvers hold two n x n FP64 matrices (n = Np or Ns).
+nk_status check_svd_size(int solver, int N, int M, int64_t Ns) {
+    const int64_t n = solver == NK_SOLVER_SVD ? n_params(N, M) : Ns;
+    if ((solver == NK_SOLVER_SVD || solver == NK_SOLVER_SVD_SAMPLESPACE) && n > 8192)
+        return fail(NK_ERR_INVALID_ARG, "the SVD solvers need %s <= 8192 (got %lld)",
+                    solver == NK_SOLVER_SVD ? "Np" : "Ns", (long long)n);
     return NK_OK;
 }
 
@@ -891,6 +1070,7 @@ nk_status nk_sr_solve(nk_ctx *ctx, const nk_rbm *rbm, int32_t precision, const i
     if ((st0 = check_precision(precision)) != NK_OK) return st0;
     if ((st0 = check_solver(solver, diag_shift, cg_tol, cg_maxiter)) != NK_OK) return st0;
     if (Ns < 1) return fail(NK_ERR_INVALID_ARG, "Ns must be >= 1");
+    if ((st0 = check_svd_size(solver, rbm->N, rbm->M, Ns)) != NK_OK) return st0;
     NK_DEV(s, "s");
     NK_DEV(F, "F");
     NK_DEV(delta_out, "delta_out");
@@ -919,12 +1099,16 @@ nk_status nk_sr_step(nk_ctx *ctx, nk_rbm *rbm, const nk_ham *ham, nk_chains *cha
     if (!cfg || !chains) return fail(NK_ERR_INVALID_ARG, "cfg or chains is NULL");
     if ((st0 = check_precision(cfg->precision)) != NK_OK) return st0;
     if ((st0 = check_ham(ham, rbm->N)) != NK_OK) return st0;
-    if ((st0 = check_solver(cfg->solver, cfg->diag_shift, cfg->cg_tol, cfg->cg_maxiter)) != NK_OK)
+    const bool svd_solver = cfg->solver == NK_SOLVER_SVD || cfg->solver == NK_SOLVER_SVD_SAMPLESPACE;
+    if ((st0 = check_solver(cfg->solver, cfg->diag_shift, svd_solver ? cfg->svd_rcond : cfg->cg_tol,
+                            cfg->cg_maxiter)) != NK_OK)
         return st0;
     if (cfg->rule != NK_RULE_LOCAL && cfg->rule != NK_RULE_EXCHANGE && cfg->rule != NK_RULE_HAMILTONIAN)
         return fail(NK_ERR_INVALID_ARG, "rule %d unknown", cfg->rule);
     if (chains->C < 1 || cfg->n_samples < 1 || cfg->n_discard < 0 || chains->sweeps_done < 0)
         return fail(NK_ERR_INVALID_ARG, "need C >= 1, n_samples >= 1, n_discard >= 0");
+    if ((st0 = check_svd_size(cfg->solver, rbm->N, rbm->M, (int64_t)chains->C * cfg->n_samples)) != NK_OK)
+        return st0;
     NK_DEV(chains->s, "chains->s");
     if (chains->n_accepted) NK_DEV(chains->n_accepted, "chains->n_accepted");
     if (stats_out) NK_DEV(stats_out, "stats_out");
@@ -943,59 +1127,30 @@ nk_status nk_sr_step(nk_ctx *ctx, nk_rbm *rbm, const nk_ham *ham, nk_chains *cha
 
     auto body = [&](auto tag, Carver &c, bool run) -> nk_status {
         using R = decltype(tag);
+        const bool mixed = cfg->precision == NK_MIXED;
         nk::Tables<R> t{};
-        carve_tables(c, t, rbm, E, ham->edges, site, edge);
-        int8_t *samples = samples_out ? samples_out : c.take<int8_t>((size_t)Ns * N);
-        double *eloc = eloc_out ? eloc_out : c.take<double>(Ns);
-        double *T = c.take<double>((size_t)Ns * M);
-        double *st3 = c.take<double>(4);
+        StepBufs sb{};
+        carve_step(c, t, sb, rbm, ham, C, Ns, site, edge, mixed, samples_out, eloc_out);
         double *gv = c.take<double>(Ns);
         double *F = c.take<double>(Np);
         double *delta = c.take<double>(Np);
         double *nrm = c.take<double>(2);
-        unsigned long long *acc = c.take<unsigned long long>(C);
         SolveWs w;
         carve_solve(c, w, N, M, Ns, cfg->solver, cfg->precision);
         w.tcerr = ctx->tc_err;
-        const bool mixed = cfg->precision == NK_MIXED;
-        const int64_t TB = Ns > C ? Ns : C;
-        double *theta = mixed ? c.take<double>((size_t)TB * M) : nullptr;
-        void *tcm = mixed ? c.take<char>(tcm_bytes(N, M, TB)) : nullptr;
         if (!run) return NK_OK;
-        NK_CU(nk::launch_tables(t, site, edge, st), "tables");
-        NK_CU(cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * C, st), "memset");
-        nk::SweepArgs a{};
-        a.N = N;
-        a.M = M;
-        a.E = E_rule;
-        a.C = C;
-        a.rule = rule;
-        a.edges = ham->edges;
-        a.s = chains->s;
-        a.sweep0 = chains->sweeps_done;
-        a.n_discard = cfg->n_discard;
-        a.n_samples = cfg->n_samples;
-        a.seed = cfg->seed;
-        a.stream_id = cfg->stream_id;
-        a.samples = samples;
-        a.logpsi = nullptr;
-        a.n_accepted = acc;
-        a.decisions = nullptr;
-        nk::Tables<R> ts = t;  // the rule's edges: a prefix of the Hamiltonian's
-        ts.E = E_rule;
-        nk_status sw = run_sweeps(ctx, ts, a, mixed, theta, tcm, st);
-        if (sw != NK_OK) return sw;
-        if (mixed)
-            NK_CU(nk::launch_theta_tc(N, M, t.b, t.W, samples, Ns, theta, ctx->tc_err, tcm, st), "theta");
-        nk::ElocArgs ea = nk::eloc_args(ham, samples, Ns, eloc, T, theta);
-        NK_CU(nk::launch_eloc(t, ea, st), "local energy");
-        NK_CU(nk::launch_stats(eloc, Ns, C, st3, st), "stats");
+        nk_status sm = run_sample_measure(ctx, t, sb, ham, chains, cfg, rule, E_rule, site, edge, mixed, st);
+        if (sm != NK_OK) return sm;
+        int8_t *samples = sb.samples;
+        double *eloc = sb.eloc, *T = sb.T, *st3 = sb.st3;
+        unsigned long long *acc = sb.acc;
         NK_CU(nk::launch_make_force_g(Ns, eloc, st3, gv, st), "force g");
         NK_CU(vjp_any(N, M, Ns, samples, T, gv, 1.0, nullptr, w, F, cfg->precision, kExactSlices, st), "force");
         int info[2] = {0, 0};
         double resid = 0.0;
+        const bool svd = cfg->solver == NK_SOLVER_SVD || cfg->solver == NK_SOLVER_SVD_SAMPLESPACE;
         nk_status ss = run_solve(ctx, N, M, Ns, samples, T, F, cfg->solver, cfg->diag_shift,
-                                 cfg->cg_tol, cfg->cg_maxiter, w, delta, info, &resid, st,
+                                 svd ? cfg->svd_rcond : cfg->cg_tol, cfg->cg_maxiter, w, delta, info, &resid, st,
                                  cfg->precision, false);
         if (ss != NK_OK && ss != NK_ERR_NOT_CONVERGED) return ss;
         NK_CU(nk::launch_dot(Np, F, F, w.dotp, nrm, st), "norm");
@@ -1019,6 +1174,191 @@ nk_status nk_sr_step(nk_ctx *ctx, nk_rbm *rbm, const nk_ham *ham, nk_chains *cha
     };
     if (cfg->precision == NK_F64)
         return with_workspace(ctx, [&](Carver &c, bool run) { return body(double{}, c, run); });
+    return with_workspace(ctx, [&](Carver &c, bool run) { return body(float{}, c, run); });
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------ symmetric RBM ---
+
+namespace {
+
+nk_status check_symm(const nk_rbm_symm *m) {
+    if (!m) return fail(NK_ERR_INVALID_ARG, "symmetric RBM is NULL");
+    if (m->N < 1 || m->N > 4096) return fail(NK_ERR_INVALID_ARG, "N=%d out of [1, 4096]", m->N);
+    if (m->alpha < 1 || m->n_group < 1 || (int64_t)m->alpha * m->n_group > 8192)
+        return fail(NK_ERR_INVALID_ARG, "alpha=%d, n_group=%d: need alpha >= 1, n_group >= 1, alpha n_group <= 8192",
+                    m->alpha, m->n_group);
+    NK_DEV(m->perms, "symm->perms");
+    NK_DEV(m->params, "symm->params");
+    return NK_OK;
+}
+
+inline int64_t symm_params(const nk_rbm_symm *m) { return 1 + m->alpha + (int64_t)m->alpha * m->N; }
+
+// int offset, in the context's 256-byte device status block (tc_err), of the
+// flag of the permutation check
+constexpr int kPermsFlag = 16;
+
+// Checks that every row of perms is a permutation of [0, N) (reads one flag
+// back: synchronises the stream), then writes the expanded plain-RBM
+// parameters.
+nk_status symm_expand_checked(nk_ctx *ctx, const nk_rbm_symm *m, double *plain, cudaStream_t st) {
+    int *flag = ctx->tc_err + kPermsFlag;
+    NK_CU(cudaMemsetAsync(flag, 0, sizeof(int), st), "perms");
+    NK_CU(nk::launch_symm_check_perms(m->N, m->n_group, m->perms, flag, st), "perms");
+    NK_CU(cudaMemcpyAsync(ctx->host_flags + 5, flag, sizeof(int), cudaMemcpyDeviceToHost, st), "perms");
+    NK_CU(cudaStreamSynchronize(st), "perms");
+    if (ctx->host_flags[5])
+        return fail(NK_ERR_INVALID_ARG, "symm->perms: a row is not a permutation of [0, %d)", m->N);
+    NK_CU(nk::launch_symm_expand(m->N, m->alpha, m->n_group, m->perms, m->params, plain, st), "expand");
+    return NK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+nk_status nk_symm_expand(nk_ctx *ctx, const nk_rbm_symm *symm, double *plain_out, void *stream) {
+    if (!ctx) return fail(NK_ERR_INVALID_ARG, "ctx is NULL");
+    DeviceGuard g(ctx->device);
+    nk_status st0 = check_symm(symm);
+    if (st0 != NK_OK) return st0;
+    NK_DEV(plain_out, "plain_out");
+    if (g_plan_only) return NK_OK;
+    return symm_expand_checked(ctx, symm, plain_out, (cudaStream_t)stream);
+}
+
+nk_status nk_symm_jacobian(nk_ctx *ctx, const nk_rbm_symm *symm, int32_t precision, const int8_t *s, int64_t Ns,
+                           double *O_out, void *stream) {
+    if (!ctx) return fail(NK_ERR_INVALID_ARG, "ctx is NULL");
+    DeviceGuard g(ctx->device);
+    nk_status st0 = check_symm(symm);
+    if (st0 != NK_OK) return st0;
+    if ((st0 = check_precision(precision)) != NK_OK) return st0;
+    if (Ns < 0) return fail(NK_ERR_INVALID_ARG, "Ns < 0");
+    if (Ns == 0) return NK_OK;
+    NK_DEV(s, "s");
+    NK_DEV(O_out, "O_out");
+    if (nk::symm_jacobian_smem(symm->N, symm->alpha, symm->n_group) > 227 * 1024)
+        return fail(NK_ERR_INVALID_ARG, "alpha n_group too large for one sample's activations in shared memory");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int N = symm->N, M = symm->alpha * symm->n_group;
+    return with_workspace(ctx, [&](Carver &c, bool run) -> nk_status {
+        double *plain = c.take<double>((size_t)n_params(N, M));
+        double *T = c.take<double>((size_t)Ns * M);
+        const bool mixed = precision == NK_MIXED;
+        void *tcm = mixed ? c.take<char>(nk::tc_theta_ws_bytes(N, M, Ns)) : nullptr;
+        if (!run) return NK_OK;
+        nk_status e = symm_expand_checked(ctx, symm, plain, st);
+        if (e != NK_OK) return e;
+        nk_rbm r{N, M, plain};
+        if ((e = batch_T(ctx, &r, s, Ns, T, mixed, tcm, st)) != NK_OK) return e;
+        NK_CU(nk::launch_symm_jacobian(N, symm->alpha, symm->n_group, symm->perms, s, T, Ns, O_out, st),
+              "symmetric jacobian");
+        return NK_OK;
+    });
+}
+
+nk_status nk_symm_sr_step(nk_ctx *ctx, nk_rbm_symm *symm, const nk_ham *ham, nk_chains *chains,
+                          const nk_sr_cfg *cfg, nk_sr_stats *stats_out, int8_t *samples_out, double *eloc_out,
+                          void *stream) {
+    if (!ctx) return fail(NK_ERR_INVALID_ARG, "ctx is NULL");
+    DeviceGuard g(ctx->device);
+    nk_status st0 = check_symm(symm);
+    if (st0 != NK_OK) return st0;
+    if (!cfg || !chains) return fail(NK_ERR_INVALID_ARG, "cfg or chains is NULL");
+    if ((st0 = check_precision(cfg->precision)) != NK_OK) return st0;
+    if ((st0 = check_ham(ham, symm->N)) != NK_OK) return st0;
+    if (cfg->solver != NK_SOLVER_CHOLESKY)
+        return fail(NK_ERR_UNIMPLEMENTED,
+                    "the symmetric RBM solves its 1 + alpha + alpha N parameters by the dense Cholesky only");
+    if ((st0 = check_solver(cfg->solver, cfg->diag_shift, cfg->cg_tol, cfg->cg_maxiter)) != NK_OK) return st0;
+    if (cfg->rule != NK_RULE_LOCAL && cfg->rule != NK_RULE_EXCHANGE && cfg->rule != NK_RULE_HAMILTONIAN)
+        return fail(NK_ERR_INVALID_ARG, "rule %d unknown", cfg->rule);
+    if (chains->C < 1 || cfg->n_samples < 1 || cfg->n_discard < 0 || chains->sweeps_done < 0)
+        return fail(NK_ERR_INVALID_ARG, "need C >= 1, n_samples >= 1, n_discard >= 0");
+    if (nk::symm_jacobian_smem(symm->N, symm->alpha, symm->n_group) > 227 * 1024)
+        return fail(NK_ERR_INVALID_ARG, "alpha n_group too large for one sample's activations in shared memory");
+    NK_DEV(chains->s, "chains->s");
+    if (chains->n_accepted) NK_DEV(chains->n_accepted, "chains->n_accepted");
+    if (stats_out) NK_DEV(stats_out, "stats_out");
+    if (samples_out) NK_DEV(samples_out, "samples_out");
+    if (eloc_out) NK_DEV(eloc_out, "eloc_out");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int N = symm->N, alpha = symm->alpha, G = symm->n_group, M = alpha * G, C = chains->C,
+              E = ham->n_edges;
+    const int64_t Ns = (int64_t)C * cfg->n_samples, Np = symm_params(symm);
+    const int rule = nk::effective_rule(cfg->rule, ham->kind);
+    const int E_rule = rule == NK_RULE_HAMILTONIAN && ham->J2 == 0.0 ? E - ham->n_edges2 : E;
+    const bool site = rule == NK_RULE_LOCAL || ham->kind == NK_TFIM;
+    const bool edge = rule != NK_RULE_LOCAL || ham->kind == NK_HEIS;
+    const bool mixed = cfg->precision == NK_MIXED;
+    const nk::CholStreams cs{ctx->side, ctx->aux, ctx->ev[0], ctx->ev[1], ctx->ev[2], ctx->ev[3]};
+
+    auto body = [&](auto tag, Carver &c, bool run) -> nk_status {
+        using R = decltype(tag);
+        double *plain = c.take<double>((size_t)n_params(N, M));
+        nk_rbm r{N, M, plain};
+        nk::Tables<R> t{};
+        StepBufs sb{};
+        carve_step(c, t, sb, &r, ham, C, Ns, site, edge, mixed, samples_out, eloc_out);
+        double *O = c.take<double>((size_t)Ns * Np);
+        double *ones = c.take<double>(Ns);
+        double *mean = c.take<double>(Np);
+        double *partial = c.take<double>(nk::gemv_t_partial_doubles(Ns, Np));
+        double *gv = c.take<double>(Ns);
+        double *F = c.take<double>(Np);
+        double *S = c.take<double>((size_t)Np * Np);
+        double *nrm = c.take<double>(2);
+        double *dotp = c.take<double>(nk::dot_partial_doubles(Np) + 8);
+        int *info = c.take<int>(2);
+        void *tc = mixed ? c.take<char>(nk::tc_chol_ws_bytes(Np)) : nullptr;
+        if (!run) return NK_OK;
+        nk_status e = symm_expand_checked(ctx, symm, plain, st);
+        if (e != NK_OK) return e;
+        e = run_sample_measure(ctx, t, sb, ham, chains, cfg, rule, E_rule, site, edge, mixed, st);
+        if (e != NK_OK) return e;
+        // the Jacobian in the symmetric parameters, centred
+        NK_CU(nk::launch_symm_jacobian(N, alpha, G, symm->perms, sb.samples, sb.T, Ns, O, st), "jacobian");
+        NK_CU(nk::launch_fill(Ns, 1.0, ones, st), "mean");
+        NK_CU(nk::launch_gemv_t(O, Ns, Np, ones, 1.0 / (double)Ns, partial, mean, st), "mean");
+        NK_CU(nk::launch_sub_colmean(Ns, Np, mean, O, st), "centre");
+        // force F = (2/Ns) dJ^T (E_loc - mean E_loc)
+        NK_CU(nk::launch_make_force_g(Ns, sb.eloc, sb.st3, gv, st), "force g");
+        NK_CU(nk::launch_gemv_t(O, Ns, Np, gv, 1.0, partial, F, st), "force");
+        // S + eps I = dJ^T dJ / Ns + eps I, Cholesky, two triangular solves
+        NK_CU(cudaMemsetAsync(info, 0, 2 * sizeof(int), st), "chol");
+        if (mixed) {
+            NK_CU(nk::launch_gram_cols_tc(O, Ns, Np, 1.0 / (double)Ns, cfg->diag_shift, S, info + 1, tc, st), "gram");
+            NK_CU(nk::launch_cholesky_tc(S, Np, info, info + 1, tc, st, &cs), "factor");
+        } else {
+            NK_CU(nk::launch_syrk_t(O, Ns, Np, 1.0 / (double)Ns, cfg->diag_shift, S, st), "syrk");
+            NK_CU(nk::launch_cholesky(S, Np, info, st), "factor");
+        }
+        NK_CU(nk::launch_axpby(Np, 1.0, F, 0.0, mean, st), "solve");  // mean <- F, solved in place
+        if (mixed)
+            NK_CU(nk::launch_cholesky_solve_tc(S, Np, tc, mean, info + 1, st), "solve");
+        else
+            NK_CU(nk::launch_cholesky_solve(S, Np, mean, st), "solve");
+        NK_CU(nk::launch_dot(Np, F, F, dotp, nrm, st), "norm");
+        NK_CU(nk::launch_dot(Np, mean, mean, dotp, nrm + 1, st), "norm");
+        NK_CU(nk::launch_sgd(Np, cfg->lr, mean, symm->params, st), "update");
+        if (stats_out) {
+            const double nprop = (double)C * (cfg->n_discard + cfg->n_samples) * N;
+            NK_CU(nk::launch_write_sr_stats(sb.st3, sb.acc, C, nprop, nrm, nrm + 1, nullptr, nullptr, info,
+                                            stats_out, st),
+                  "stats out");
+        }
+        if (chains->n_accepted) {
+            (k_add_u64<<<(C + 255) / 256, 256, 0, st>>>(
+                C, sb.acc, reinterpret_cast<unsigned long long *>(chains->n_accepted)), nk::note_launch());
+            NK_CU(cudaGetLastError(), "acc");
+        }
+        chains->sweeps_done += cfg->n_discard + cfg->n_samples;
+        return mixed ? check_factor(ctx, info, st) : NK_OK;
+    };
+    if (!mixed) return with_workspace(ctx, [&](Carver &c, bool run) { return body(double{}, c, run); });
     return with_workspace(ctx, [&](Carver &c, bool run) { return body(float{}, c, run); });
 }
 

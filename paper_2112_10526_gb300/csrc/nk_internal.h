@@ -13,12 +13,14 @@ struct nk_ctx {
     int device;
     char *ws;
     size_t ws_size;
-    int *host_flags;    // pinned: [0] done, [1] iterations, [2..3] factor status, [4] tc error
+    int *host_flags;    // pinned: [0] done, [1] iterations, [2..3] factor status, [4] tc error,
+                        // [5] permutation check
     double *host_vals;  // pinned
     cudaStream_t side;  // high-priority stream for the Cholesky look-ahead
     cudaStream_t aux;   // high-priority stream for work beside the panel chain
     cudaEvent_t ev[4];
-    int *tc_err;        // device: sticky code of the first tensor-core time-out
+    int *tc_err;        // device, 256 bytes: [0] sticky code of the first tensor-core
+                        // time-out; [16] flag of the symmetric RBM's permutation check
     size_t plan_bytes;  // workspace counted by plan-only calls
 };
 
@@ -236,6 +238,33 @@ cudaError_t launch_cg_update_p(int64_t n, const double *rr_new, const double *rr
                                const double *r, double *p, const int *done, cudaStream_t st);
 cudaError_t launch_cg_check(const double *rr, const double *ff, double tol, int *done,
                             int *iters, double *rr_keep, cudaStream_t st);
+
+// Symmetric RBM (k_symm.cu): perms [G][N] device; err |= 1 when a row is not
+// a permutation of [0, N); expanded plain-RBM parameters [N + M + M N],
+// M = alpha G; uncentred symmetric Jacobian rows O [Ns][1 + alpha + alpha N]
+// from t = tanh theta of the expanded units [Ns][M]; O -= column means.
+cudaError_t launch_symm_check_perms(int N, int G, const int32_t *perms, int *err, cudaStream_t st);
+cudaError_t launch_symm_expand(int N, int alpha, int G, const int32_t *perms, const double *p, double *out,
+                               cudaStream_t st);
+size_t symm_jacobian_smem(int N, int alpha, int G);
+cudaError_t launch_symm_jacobian(int N, int alpha, int G, const int32_t *perms, const int8_t *s, const double *T,
+                                 int64_t Ns, double *O, cudaStream_t st);
+cudaError_t launch_sub_colmean(int64_t rows, int64_t cols, const double *mean, double *O, cudaStream_t st);
+
+// Symmetric eigensolver (k_eig.cu): cyclic two-sided Jacobi sweeps with the
+// round-robin parallel ordering on a full symmetric A [n][n] (diagonalised
+// in place) and V [n][n] (V <- V J; start from the identity: columns are the
+// eigenvectors); ws of eig_ws_bytes(n).  out2 = (sum of squares off the
+// diagonal, on it).  w = diag A, wmax = max w.  The filter: z_k <- z_k /
+// w_k^power for w_k > rcond wmax, else 0; kept counts the kept ones.
+size_t eig_ws_bytes(int64_t n);
+cudaError_t launch_symmetrize_lower(int64_t n, double *A, cudaStream_t st);
+cudaError_t launch_identity(int64_t n, double *V, cudaStream_t st);
+cudaError_t launch_jacobi_sweep(double *A, double *V, int64_t n, void *ws, cudaStream_t st);
+cudaError_t launch_offdiag_norms(const double *A, int64_t n, void *ws, double *out2, cudaStream_t st);
+cudaError_t launch_eig_diag(int64_t n, const double *A, double *w, double *wmax, cudaStream_t st);
+cudaError_t launch_spectral_filter(int64_t n, const double *w, const double *wmax, double rcond, int power,
+                                   double *z, int *kept, cudaStream_t st);
 
 // params -= lr * delta; norms into stats.
 cudaError_t launch_sgd(int64_t n, double lr, const double *delta, double *params,

@@ -27,13 +27,14 @@ NK_F64, NK_MIXED = 0, 1
 NK_RULE_LOCAL, NK_RULE_EXCHANGE, NK_RULE_HAMILTONIAN = 0, 1, 2
 NK_TFIM, NK_HEIS = 0, 1
 NK_SOLVER_CHOLESKY, NK_SOLVER_CHOLESKY_SAMPLESPACE, NK_SOLVER_CG = 0, 1, 2
+NK_SOLVER_SVD, NK_SOLVER_SVD_SAMPLESPACE = 3, 4
 NK_QGT_ONTHEFLY, NK_QGT_JACOBIAN = 0, 1
 
 PRECISION = {"f64": NK_F64, "mixed": NK_MIXED}
 RULE = {"local": NK_RULE_LOCAL, "exchange": NK_RULE_EXCHANGE, "hamiltonian": NK_RULE_HAMILTONIAN}
 KIND = {"tfim": NK_TFIM, "heis": NK_HEIS}
 SOLVER = {"cholesky": NK_SOLVER_CHOLESKY, "cholesky_samplespace": NK_SOLVER_CHOLESKY_SAMPLESPACE,
-          "cg": NK_SOLVER_CG}
+          "cg": NK_SOLVER_CG, "svd": NK_SOLVER_SVD, "svd_samplespace": NK_SOLVER_SVD_SAMPLESPACE}
 
 
 class NkError(RuntimeError):
@@ -58,6 +59,11 @@ class nk_qgt(ctypes.Structure):
                 ("Np", ctypes.c_int32)]
 
 
+class nk_rbm_symm(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int32), ("alpha", ctypes.c_int32), ("n_group", ctypes.c_int32),
+                ("perms", ctypes.c_void_p), ("params", ctypes.c_void_p)]
+
+
 class nk_chains(ctypes.Structure):
     _fields_ = [("C", ctypes.c_int32), ("s", ctypes.c_void_p), ("sweeps_done", ctypes.c_int64),
                 ("n_accepted", ctypes.c_void_p)]
@@ -67,7 +73,8 @@ class nk_sr_cfg(ctypes.Structure):
     _fields_ = [("rule", ctypes.c_int32), ("precision", ctypes.c_int32), ("solver", ctypes.c_int32),
                 ("n_discard", ctypes.c_int32), ("n_samples", ctypes.c_int32),
                 ("cg_maxiter", ctypes.c_int32), ("diag_shift", ctypes.c_double), ("lr", ctypes.c_double),
-                ("cg_tol", ctypes.c_double), ("seed", ctypes.c_uint64), ("stream_id", ctypes.c_uint32)]
+                ("cg_tol", ctypes.c_double), ("seed", ctypes.c_uint64), ("stream_id", ctypes.c_uint32),
+                ("svd_rcond", ctypes.c_double)]
 
 
 NK_REQ_EXPECT, NK_REQ_SR_STEP = 0, 1
@@ -140,6 +147,10 @@ def lib():
                         ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double), P],
         "nk_sr_step": [P, ctypes.POINTER(nk_rbm), ctypes.POINTER(nk_ham), ctypes.POINTER(nk_chains),
                        ctypes.POINTER(nk_sr_cfg), P, P, P, P],
+        "nk_symm_expand": [P, ctypes.POINTER(nk_rbm_symm), P, P],
+        "nk_symm_jacobian": [P, ctypes.POINTER(nk_rbm_symm), i32, P, i64, P, P],
+        "nk_symm_sr_step": [P, ctypes.POINTER(nk_rbm_symm), ctypes.POINTER(nk_ham), ctypes.POINTER(nk_chains),
+                            ctypes.POINTER(nk_sr_cfg), P, P, P, P],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -364,6 +375,36 @@ def nk_sr_step(ctx, params, N, M, ham, chains, cfg, stats_out=None, samples_out=
     return code
 
 
+def make_symm(params, N, alpha, perms):
+    """nk_rbm_symm over device tensors: params float64 [1 + alpha + alpha N],
+    perms int32 [|G|, N]."""
+    assert perms.dtype == torch.int32 and perms.is_contiguous() and perms.shape[1] == N
+    assert params.dtype == torch.float64 and params.numel() == 1 + alpha + alpha * N
+    return nk_rbm_symm(N, alpha, perms.shape[0], perms.data_ptr(), params.data_ptr())
+
+
+def nk_symm_expand(ctx, params, N, alpha, perms, plain_out, stream=None):
+    m = make_symm(params, N, alpha, perms)
+    _check(lib().nk_symm_expand(ctx.handle, ctypes.byref(m), _ptr(plain_out), _stream(stream)))
+    return plain_out
+
+
+def nk_symm_jacobian(ctx, params, N, alpha, perms, s, O_out, precision="f64", stream=None):
+    m = make_symm(params, N, alpha, perms)
+    _check(lib().nk_symm_jacobian(ctx.handle, ctypes.byref(m), _prec(precision), _ptr(s), s.shape[0], _ptr(O_out),
+                                  _stream(stream)))
+    return O_out
+
+
+def nk_symm_sr_step(ctx, params, N, alpha, perms, ham, chains, cfg, stats_out=None, samples_out=None,
+                    eloc_out=None, stream=None):
+    """One SR step of the symmetric RBM; params (device float64) updated in place."""
+    m = make_symm(params, N, alpha, perms)
+    _check(lib().nk_symm_sr_step(ctx.handle, ctypes.byref(m), ctypes.byref(ham), ctypes.byref(chains),
+                                 ctypes.byref(cfg), _ptr(stats_out), _ptr(samples_out), _ptr(eloc_out),
+                                 _stream(stream)))
+
+
 def sr_stats_dict(t):
     """Read an nk_sr_stats device buffer (float64 [8]) into a dict."""
     v = t.detach().cpu().tolist()
@@ -371,10 +412,11 @@ def sr_stats_dict(t):
 
 
 def make_cfg(rule, precision, solver, n_discard, n_samples, diag_shift, lr, seed, stream_id=0,
-             cg_tol=1e-10, cg_maxiter=1000):
+             cg_tol=1e-10, cg_maxiter=1000, svd_rcond=0.0):
     return nk_sr_cfg(RULE[rule] if isinstance(rule, str) else rule, _prec(precision),
                      SOLVER[solver] if isinstance(solver, str) else solver, int(n_discard), int(n_samples),
-                     int(cg_maxiter), float(diag_shift), float(lr), float(cg_tol), int(seed), int(stream_id))
+                     int(cg_maxiter), float(diag_shift), float(lr), float(cg_tol), int(seed), int(stream_id),
+                     float(svd_rcond))
 
 
 def make_chains(s, sweeps_done=0, n_accepted=None):
