@@ -433,6 +433,89 @@ nk_status nk_symm_sr_step(nk_ctx *ctx, nk_rbm_symm *symm, const nk_ham *ham, nk_
                           const nk_sr_cfg *cfg, nk_sr_stats *stats_out, int8_t *samples_out, double *eloc_out,
                           void *stream);
 
+/* ---------------------------------------- complex RBM and time evolution ---
+ * The RBM of Sec. 3.2 with complex parameters a, b, W (the holomorphic ansatz
+ * of the time-evolution examples, Sec. 9): ln psi(s) = a.s + sum_j
+ * ln cosh(b_j + W_j.s) is complex, psi(s) need not be positive, and the map
+ * theta -> ln psi(s) is holomorphic, so O_k = d ln psi / d theta_k is the
+ * complex O_a = s, O_b = tanh theta, O_W = tanh theta s^T.
+ * Complex arrays are interleaved (re, im) float64 pairs and must be 16-byte
+ * aligned (NK_ERR_INVALID_ARG otherwise).  Parameters: [a (N); b (M); W (M x
+ * N, row-major)] complex, 2 Np doubles.  Everything is FP64 on CUDA cores.
+ * Limits: N <= 4096, M <= 4096.
+ */
+typedef struct {
+    int32_t N, M;
+    double *params;  /* device, 2 Np doubles; only nk_tdvp_step writes it */
+} nk_crbm;
+
+/* Complex ln psi of a batch: s [B, N]; out [B] complex (2 B doubles). */
+nk_status nk_crbm_logpsi(nk_ctx *ctx, const nk_crbm *rbm, const int8_t *s, int64_t B, double *out, void *stream);
+
+/* Metropolis-Hastings chains on |psi|^2 (Sec. 3.4), on the Philox streams and
+ * proposal rules of nk_metropolis_sweep (NK_RULE_LOCAL or NK_RULE_EXCHANGE):
+ * the move is accepted iff ln u < 2 Re[ln psi(s') - ln psi(s)]; each
+ * log-ratio is summed term by term over the hidden units from the moved
+ * activations.  s [C, N] in/out; samples_out [C, n_samples, N]; n_accepted
+ * [C] or NULL. */
+nk_status nk_crbm_metropolis(nk_ctx *ctx, const nk_crbm *rbm, int32_t rule, int32_t n_edges, const int32_t *edges,
+                             int32_t C, int8_t *s, int64_t sweep0, int32_t n_discard, int32_t n_samples,
+                             uint64_t seed, uint32_t stream_id, int8_t *samples_out, uint64_t *n_accepted,
+                             void *stream);
+
+/* Complex local energies (Eq. eq:local-estimator): eloc_out [Ns] complex. */
+nk_status nk_crbm_local_energy(nk_ctx *ctx, const nk_crbm *rbm, const nk_ham *ham, const int8_t *s, int64_t Ns,
+                               double *eloc_out, void *stream);
+
+/* Complex log-derivatives: O_out [Ns, Np] complex, uncentred. */
+nk_status nk_crbm_jacobian(nk_ctx *ctx, const nk_crbm *rbm, const int8_t *s, int64_t Ns, double *O_out,
+                           void *stream);
+
+#define NK_TDVP_EULER 1 /* theta(t + dt) = theta + dt k1 */
+#define NK_TDVP_HEUN 2  /* k2 at theta + dt k1 on fresh samples; theta + dt (k1 + k2) / 2 */
+
+typedef struct {
+    int32_t rule;        /* NK_RULE_LOCAL or NK_RULE_EXCHANGE */
+    int32_t integrator;  /* NK_TDVP_EULER or NK_TDVP_HEUN */
+    int32_t real_time;   /* 1: gamma = -i (unitary dynamics); 0: gamma = -1 (imaginary time) */
+    int32_t solver;      /* NK_SOLVER_CHOLESKY ((G + eps I), eps > 0) or NK_SOLVER_SVD (its
+                            pseudo-inverse: eigenvalues above rcond x the largest) */
+    int32_t n_discard;   /* sweeps discarded before the first slope's samples */
+    int32_t n_samples;   /* samples (sweeps) per chain for each slope */
+    double dt;
+    double diag_shift;   /* eps */
+    double rcond;        /* NK_SOLVER_SVD (0: 1e-12) */
+    uint64_t seed;
+    uint32_t stream_id;
+} nk_tdvp_cfg;
+
+/* Diagnostics of one time step (DEVICE float64 fields), from the first
+ * slope's samples. */
+typedef struct {
+    double energy_re, energy_im;  /* mean E_loc */
+    double variance;              /* mean |E_loc - mean|^2 */
+    double error;                 /* sqrt(variance / Ns) */
+} nk_tdvp_stats;
+
+/*
+ * One step of time-dependent variational Monte Carlo (Sec. 4.3): each slope
+ * samples the chains (continuing them; the second slope of Heun draws the
+ * sweeps after the first's, with no discards), forms the sample-mean force
+ * f~ = E[O^* (E_loc - E[E_loc])] and QGT G = E[O^* O] - E[O^*] E[O] (Sec.
+ * 3.5, Eq. eq:force VMC) and solves (G + eps I) theta_dot = gamma f~ (Eq.
+ * eq:tvmc); then the explicit Runge-Kutta update of Eq. eq:rk-step.  The
+ * Hermitian system is solved through its real embedding [[Re G, -Im G],
+ * [Im G, Re G]] of order 2 Np, built as R^T R / Ns from the realified
+ * centred Jacobian R (2 Ns x 2 Np): by the FP64 Cholesky, or by the cyclic
+ * Jacobi eigensolver of the SVD solvers (2 Np <= 8192; synchronises the
+ * stream once per sweep).
+ *   rbm->params updated in place; chains advanced (sweeps_done on the host).
+ *   stats_out: device nk_tdvp_stats or NULL; theta_dot_out: device [Np]
+ *   complex, the first slope, or NULL.
+ */
+nk_status nk_tdvp_step(nk_ctx *ctx, nk_crbm *rbm, const nk_ham *ham, nk_chains *chains, const nk_tdvp_cfg *cfg,
+                       nk_tdvp_stats *stats_out, double *theta_dot_out, void *stream);
+
 /* ------------------------------------------------------------- serving ---
  * A persistent request loop on one GPU for VMC expectation values and SR
  * steps (the serving use of this library; the paper has no counterpart).

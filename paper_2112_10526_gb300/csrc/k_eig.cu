@@ -204,18 +204,42 @@ __global__ void k_spectral_filter(int64_t n, const double *__restrict__ w, const
     if (keep && kept) atomicAdd(kept, 1);
 }
 
+// The workspace: rotation (c, s) and index pair per pair of a round, and the
+// per-row partial norms, each sub-array starting on a 256-byte boundary (the
+// double2 arrays need 16-byte alignment for their vector loads and stores).
+struct EigWs {
+    double2 *cs;
+    int2 *pq;
+    double2 *partial;
+};
+
+inline size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+EigWs carve_eig(void *ws, int64_t n) {
+    const int64_t m = n + (n & 1);
+    char *p = static_cast<char *>(ws);
+    EigWs w;
+    w.cs = reinterpret_cast<double2 *>(p);
+    p += align256((size_t)(m / 2) * sizeof(double2));
+    w.pq = reinterpret_cast<int2 *>(p);
+    p += align256((size_t)(m / 2) * sizeof(int2));
+    w.partial = reinterpret_cast<double2 *>(p);
+    return w;
+}
+
 }  // namespace
 
 size_t eig_ws_bytes(int64_t n) {
     const int64_t m = n + (n & 1);
-    return (size_t)(m / 2) * (sizeof(double2) + sizeof(int2)) + (size_t)n * sizeof(double2) + 8 * sizeof(double) + 1024;
+    return align256((size_t)(m / 2) * sizeof(double2)) + align256((size_t)(m / 2) * sizeof(int2)) +
+           align256((size_t)n * sizeof(double2)) + 256;
 }
 
 cudaError_t launch_jacobi_sweep(double *A, double *V, int64_t n, void *ws, cudaStream_t st) {
     const int m = (int)(n + (n & 1));
-    char *p = static_cast<char *>(ws);
-    auto *cs = reinterpret_cast<double2 *>(p);
-    auto *pq = reinterpret_cast<int2 *>(p + (size_t)(m / 2) * sizeof(double2));
+    const EigWs w = carve_eig(ws, n);
+    double2 *cs = w.cs;
+    int2 *pq = w.pq;
     const unsigned tx = (unsigned)(n < 256 ? 128 : 256);
     const unsigned gx = (unsigned)((n + tx - 1) / tx);
     for (int r = 0; r < m - 1; ++r) {
@@ -237,8 +261,7 @@ cudaError_t launch_identity(int64_t n, double *V, cudaStream_t st) {
 }
 
 cudaError_t launch_offdiag_norms(const double *A, int64_t n, void *ws, double *out2, cudaStream_t st) {
-    const int64_t m = n + (n & 1);
-    auto *partial = reinterpret_cast<double2 *>(static_cast<char *>(ws) + (size_t)(m / 2) * (sizeof(double2) + sizeof(int2)));
+    double2 *partial = carve_eig(ws, n).partial;
     (k_offdiag_partial<<<(unsigned)n, 256, 0, st>>>(A, n, partial), nk::note_launch());
     (k_offdiag_final<<<1, 1024, 0, st>>>(n, partial, out2), nk::note_launch());
     return cudaGetLastError();

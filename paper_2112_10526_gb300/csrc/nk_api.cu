@@ -316,6 +316,30 @@ nk_status check_factor(nk_ctx *ctx, const int *info, cudaStream_t st) {
     return NK_OK;
 }
 
+// Cyclic Jacobi sweeps on the full symmetric K [n][n] (diagonalised in
+// place; V <- V J from the identity) until the relative off-diagonal norm is
+// at the rounding level or kMaxJacobiSweeps; reads the norms back once per
+// sweep.  norms: 2 device doubles of scratch.
+nk_status jacobi_eigen(nk_ctx *ctx, double *K, double *V, int64_t n, void *eig_ws, double *norms, cudaStream_t st,
+                       int *sweeps_out, double *rel_out) {
+    NK_CU(nk::launch_symmetrize_lower(n, K, st), "eig");
+    NK_CU(nk::launch_identity(n, V, st), "eig");
+    int sweeps = 0;
+    double rel = 0.0;
+    for (; sweeps <= kMaxJacobiSweeps; ++sweeps) {
+        NK_CU(nk::launch_offdiag_norms(K, n, eig_ws, norms, st), "eig norms");
+        NK_CU(cudaMemcpyAsync(ctx->host_vals, norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, st), "eig norms");
+        NK_CU(cudaStreamSynchronize(st), "eig norms");
+        const double off = ctx->host_vals[0], tot = ctx->host_vals[0] + ctx->host_vals[1];
+        rel = tot > 0.0 ? std::sqrt(off / tot) : 0.0;
+        if (rel <= kJacobiTol || sweeps == kMaxJacobiSweeps) break;
+        NK_CU(nk::launch_jacobi_sweep(K, V, n, eig_ws, st), "eig sweep");
+    }
+    *sweeps_out = sweeps;
+    *rel_out = rel;
+    return NK_OK;
+}
+
 nk_status run_solve(nk_ctx *ctx, int N, int M, int64_t Ns, const int8_t *s, const double *T,
                     const double *F, int solver, double eps, double tol, int maxiter,
                     SolveWs &w, double *delta, int *host_info, double *host_resid,
@@ -395,25 +419,11 @@ nk_status run_solve(nk_ctx *ctx, int N, int M, int64_t Ns, const int8_t *s, cons
             else
                 NK_CU(nk::launch_syrk_t(w.dJ, Ns, Np, 1.0 / (double)Ns, eps, w.K, st), "svd S");
         }
-        NK_CU(nk::launch_symmetrize_lower(n, w.K, st), "svd");
-        NK_CU(nk::launch_identity(n, w.V, st), "svd");
-        // cyclic Jacobi sweeps until the off-diagonal part is at the rounding level
         int sweeps = 0;
-        bool converged = false;
         double rel = 0.0;
-        for (; sweeps < kMaxJacobiSweeps; ++sweeps) {
-            NK_CU(nk::launch_offdiag_norms(w.K, n, w.eig, w.evmax + 2, st), "svd norms");
-            NK_CU(cudaMemcpyAsync(ctx->host_vals, w.evmax + 2, 2 * sizeof(double), cudaMemcpyDeviceToHost, st),
-                  "svd norms");
-            NK_CU(cudaStreamSynchronize(st), "svd norms");
-            const double off = ctx->host_vals[0], tot = ctx->host_vals[0] + ctx->host_vals[1];
-            rel = tot > 0.0 ? std::sqrt(off / tot) : 0.0;
-            if (rel <= kJacobiTol) {
-                converged = true;
-                break;
-            }
-            NK_CU(nk::launch_jacobi_sweep(w.K, w.V, n, w.eig, st), "svd sweep");
-        }
+        nk_status js = jacobi_eigen(ctx, w.K, w.V, n, w.eig, w.evmax + 2, st, &sweeps, &rel);
+        if (js != NK_OK) return js;
+        const bool converged = rel <= kJacobiTol;
         NK_CU(nk::launch_eig_diag(n, w.K, w.ev, w.evmax, st), "svd eigenvalues");
         NK_CU(cudaMemsetAsync(w.kept, 0, sizeof(int), st), "svd");
         if (ss) {
@@ -1360,6 +1370,240 @@ nk_status nk_symm_sr_step(nk_ctx *ctx, nk_rbm_symm *symm, const nk_ham *ham, nk_
     };
     if (!mixed) return with_workspace(ctx, [&](Carver &c, bool run) { return body(double{}, c, run); });
     return with_workspace(ctx, [&](Carver &c, bool run) { return body(float{}, c, run); });
+}
+
+}  // extern "C"
+
+// ------------------------------------------ complex RBM and time evolution ---
+
+namespace {
+
+nk_status check_crbm(const nk_crbm *r) {
+    if (!r) return fail(NK_ERR_INVALID_ARG, "complex RBM is NULL");
+    if (r->N < 1 || r->N > 4096) return fail(NK_ERR_INVALID_ARG, "N=%d out of [1, 4096]", r->N);
+    if (r->M < 1 || r->M > 4096) return fail(NK_ERR_INVALID_ARG, "M=%d out of [1, 4096]", r->M);
+    NK_DEV(r->params, "rbm->params");
+    if (reinterpret_cast<uintptr_t>(r->params) % 16)
+        return fail(NK_ERR_INVALID_ARG, "rbm->params must be 16-byte aligned (complex pairs)");
+    if (4 * nk::crbm_smem_per_warp(r->N, r->M) > 227 * 1024)
+        return fail(NK_ERR_INVALID_ARG, "N, M too large for the activations of 4 chains in shared memory");
+    return NK_OK;
+}
+
+nk_status check_complex_out(const double *p, const char *name) {
+    NK_DEV(p, name);
+    if (reinterpret_cast<uintptr_t>(p) % 16) return fail(NK_ERR_INVALID_ARG, "%s must be 16-byte aligned", name);
+    return NK_OK;
+}
+
+// One slope of the t-VMC equation of motion at parameters p: sample, local
+// energies and their statistics, the realified centred Jacobian R, the force
+// R^T g = [Re f; Im f], the real embedding of G + eps I and its solve for
+// gamma f.  x: the slope, realified [Re; Im] (2 Np doubles).
+struct TdvpWs {
+    int8_t *samples;
+    double *eloc, *stats4, *O, *mean, *R, *g, *F, *rhs, *S, *V, *ev, *evmax, *z, *gpart, *partial;
+    void *eig;
+    int *info, *kept;
+    unsigned long long *acc;
+};
+
+nk_status tdvp_slope(nk_ctx *ctx, int N, int M, const double *p, const nk_ham *ham, nk_chains *chains,
+                     const nk_tdvp_cfg *cfg, int n_discard, TdvpWs &w, double *x, cudaStream_t st) {
+    const int C = chains->C;
+    const int64_t Ns = (int64_t)C * cfg->n_samples, Np = n_params(N, M), n = 2 * Np;
+    NK_CU(nk::launch_crbm_sweep(N, M, p, cfg->rule, ham->n_edges, ham->edges, C, chains->s, chains->sweeps_done,
+                                n_discard, cfg->n_samples, cfg->seed, cfg->stream_id, w.samples, w.acc, st),
+          "sweep");
+    chains->sweeps_done += n_discard + cfg->n_samples;
+    NK_CU(nk::launch_crbm_eloc(N, M, p, ham, w.samples, Ns, w.eloc, st), "local energy");
+    NK_CU(nk::launch_cstats(Ns, w.eloc, w.stats4, st), "stats");
+    NK_CU(nk::launch_crbm_jacobian(N, M, p, w.samples, Ns, w.O, st), "jacobian");
+    NK_CU(nk::launch_crealify(Ns, Np, w.O, w.mean, w.R, st), "realify");
+    NK_CU(nk::launch_cforce_g(Ns, w.eloc, w.stats4, w.g, st), "force g");
+    NK_CU(nk::launch_gemv_t(w.R, 2 * Ns, n, w.g, 1.0, w.partial, w.F, st), "force");
+    NK_CU(nk::launch_tdvp_rhs(Np, w.F, cfg->real_time, w.rhs, st), "rhs");
+    NK_CU(nk::launch_syrk_t(w.R, 2 * Ns, n, 1.0 / (double)Ns, cfg->diag_shift, w.S, st), "qgt");
+    if (cfg->solver == NK_SOLVER_CHOLESKY) {
+        NK_CU(cudaMemsetAsync(w.info, 0, 2 * sizeof(int), st), "chol");
+        NK_CU(nk::launch_cholesky(w.S, n, w.info, st), "chol");
+        NK_CU(nk::launch_axpby(n, 1.0, w.rhs, 0.0, x, st), "chol");
+        NK_CU(nk::launch_cholesky_solve(w.S, n, x, st), "chol solve");
+        return check_factor(ctx, w.info, st);
+    }
+    int sweeps = 0;
+    double rel = 0.0;
+    nk_status js = jacobi_eigen(ctx, w.S, w.V, n, w.eig, w.evmax + 2, st, &sweeps, &rel);
+    if (js != NK_OK) return js;
+    if (rel > kJacobiTol)
+        return fail(NK_ERR_NOT_CONVERGED, "Jacobi sweeps left a relative off-diagonal norm %g", rel);
+    NK_CU(nk::launch_eig_diag(n, w.S, w.ev, w.evmax, st), "eigenvalues");
+    NK_CU(nk::launch_gemv_t(w.V, n, n, w.rhs, 1.0, w.gpart, w.z, st), "V^T rhs");
+    NK_CU(nk::launch_spectral_filter(n, w.ev, w.evmax, cfg->rcond > 0.0 ? cfg->rcond : 1e-12, 1, w.z, w.kept, st),
+          "filter");
+    NK_CU(nk::launch_gemv_rows(w.V, n, n, w.z, x, st), "V z");
+    return NK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+nk_status nk_crbm_logpsi(nk_ctx *ctx, const nk_crbm *rbm, const int8_t *s, int64_t B, double *out, void *stream) {
+    if (!ctx) return fail(NK_ERR_INVALID_ARG, "ctx is NULL");
+    DeviceGuard g(ctx->device);
+    nk_status st0 = check_crbm(rbm);
+    if (st0 != NK_OK) return st0;
+    if (B < 0) return fail(NK_ERR_INVALID_ARG, "B < 0");
+    if (B == 0) return NK_OK;
+    NK_DEV(s, "s");
+    if ((st0 = check_complex_out(out, "out")) != NK_OK) return st0;
+    if (g_plan_only) return NK_OK;
+    NK_CU(nk::launch_crbm_logpsi(rbm->N, rbm->M, rbm->params, s, B, out, (cudaStream_t)stream), "logpsi");
+    return NK_OK;
+}
+
+nk_status nk_crbm_metropolis(nk_ctx *ctx, const nk_crbm *rbm, int32_t rule, int32_t n_edges, const int32_t *edges,
+                             int32_t C, int8_t *s, int64_t sweep0, int32_t n_discard, int32_t n_samples,
+                             uint64_t seed, uint32_t stream_id, int8_t *samples_out, uint64_t *n_accepted,
+                             void *stream) {
+    if (!ctx) return fail(NK_ERR_INVALID_ARG, "ctx is NULL");
+    DeviceGuard g(ctx->device);
+    nk_status st0 = check_crbm(rbm);
+    if (st0 != NK_OK) return st0;
+    if (rule != NK_RULE_LOCAL && rule != NK_RULE_EXCHANGE)
+        return fail(NK_ERR_INVALID_ARG, "rule %d: the complex RBM samples with the local or exchange rule", rule);
+    if (C < 0 || n_discard < 0 || n_samples < 1 || sweep0 < 0)
+        return fail(NK_ERR_INVALID_ARG, "need C >= 0, n_discard >= 0, n_samples >= 1, sweep0 >= 0");
+    if (rule == NK_RULE_EXCHANGE) {
+        if (n_edges < 1 || n_edges > 65536) return fail(NK_ERR_INVALID_ARG, "n_edges out of [1, 65536]");
+        NK_DEV(edges, "edges");
+    }
+    if (C == 0) return NK_OK;
+    NK_DEV(s, "s");
+    NK_DEV(samples_out, "samples_out");
+    if (n_accepted) NK_DEV(n_accepted, "n_accepted");
+    if (g_plan_only) return NK_OK;
+    NK_CU(nk::launch_crbm_sweep(rbm->N, rbm->M, rbm->params, rule, n_edges, edges, C, s, sweep0, n_discard,
+                                n_samples, seed, stream_id, samples_out,
+                                reinterpret_cast<unsigned long long *>(n_accepted), (cudaStream_t)stream),
+          "sweep");
+    return NK_OK;
+}
+
+nk_status nk_crbm_local_energy(nk_ctx *ctx, const nk_crbm *rbm, const nk_ham *ham, const int8_t *s, int64_t Ns,
+                               double *eloc_out, void *stream) {
+    if (!ctx) return fail(NK_ERR_INVALID_ARG, "ctx is NULL");
+    DeviceGuard g(ctx->device);
+    nk_status st0 = check_crbm(rbm);
+    if (st0 != NK_OK) return st0;
+    if ((st0 = check_ham(ham, rbm->N)) != NK_OK) return st0;
+    if (Ns < 0) return fail(NK_ERR_INVALID_ARG, "Ns < 0");
+    if (Ns == 0) return NK_OK;
+    NK_DEV(s, "s");
+    if ((st0 = check_complex_out(eloc_out, "eloc_out")) != NK_OK) return st0;
+    if (g_plan_only) return NK_OK;
+    NK_CU(nk::launch_crbm_eloc(rbm->N, rbm->M, rbm->params, ham, s, Ns, eloc_out, (cudaStream_t)stream),
+          "local energy");
+    return NK_OK;
+}
+
+nk_status nk_crbm_jacobian(nk_ctx *ctx, const nk_crbm *rbm, const int8_t *s, int64_t Ns, double *O_out,
+                           void *stream) {
+    if (!ctx) return fail(NK_ERR_INVALID_ARG, "ctx is NULL");
+    DeviceGuard g(ctx->device);
+    nk_status st0 = check_crbm(rbm);
+    if (st0 != NK_OK) return st0;
+    if (Ns < 0) return fail(NK_ERR_INVALID_ARG, "Ns < 0");
+    if (Ns == 0) return NK_OK;
+    NK_DEV(s, "s");
+    if ((st0 = check_complex_out(O_out, "O_out")) != NK_OK) return st0;
+    if (g_plan_only) return NK_OK;
+    NK_CU(nk::launch_crbm_jacobian(rbm->N, rbm->M, rbm->params, s, Ns, O_out, (cudaStream_t)stream), "jacobian");
+    return NK_OK;
+}
+
+nk_status nk_tdvp_step(nk_ctx *ctx, nk_crbm *rbm, const nk_ham *ham, nk_chains *chains, const nk_tdvp_cfg *cfg,
+                       nk_tdvp_stats *stats_out, double *theta_dot_out, void *stream) {
+    if (!ctx) return fail(NK_ERR_INVALID_ARG, "ctx is NULL");
+    DeviceGuard g(ctx->device);
+    nk_status st0 = check_crbm(rbm);
+    if (st0 != NK_OK) return st0;
+    if (!cfg || !chains) return fail(NK_ERR_INVALID_ARG, "cfg or chains is NULL");
+    if ((st0 = check_ham(ham, rbm->N)) != NK_OK) return st0;
+    if (cfg->rule != NK_RULE_LOCAL && cfg->rule != NK_RULE_EXCHANGE)
+        return fail(NK_ERR_INVALID_ARG, "rule %d: the local or exchange rule", cfg->rule);
+    if (cfg->integrator != NK_TDVP_EULER && cfg->integrator != NK_TDVP_HEUN)
+        return fail(NK_ERR_INVALID_ARG, "integrator %d unknown", cfg->integrator);
+    if (cfg->solver != NK_SOLVER_CHOLESKY && cfg->solver != NK_SOLVER_SVD)
+        return fail(NK_ERR_INVALID_ARG, "solver %d: NK_SOLVER_CHOLESKY or NK_SOLVER_SVD", cfg->solver);
+    if (cfg->solver == NK_SOLVER_CHOLESKY && !(cfg->diag_shift > 0.0))
+        return fail(NK_ERR_INVALID_ARG, "the Cholesky solve needs diag_shift > 0");
+    if (!(cfg->diag_shift >= 0.0) || !(cfg->rcond >= 0.0 && cfg->rcond < 1.0) || !std::isfinite(cfg->dt))
+        return fail(NK_ERR_INVALID_ARG, "need diag_shift >= 0, 0 <= rcond < 1 and a finite dt");
+    if (chains->C < 1 || cfg->n_samples < 1 || cfg->n_discard < 0 || chains->sweeps_done < 0)
+        return fail(NK_ERR_INVALID_ARG, "need C >= 1, n_samples >= 1, n_discard >= 0");
+    const int N = rbm->N, M = rbm->M, C = chains->C;
+    const int64_t Ns = (int64_t)C * cfg->n_samples, Np = n_params(N, M), n = 2 * Np;
+    if (cfg->solver == NK_SOLVER_SVD && n > 8192)
+        return fail(NK_ERR_INVALID_ARG, "the SVD solve needs 2 Np <= 8192 (got %lld)", (long long)n);
+    if (cfg->rule == NK_RULE_EXCHANGE && ham->n_edges < 1) return fail(NK_ERR_INVALID_ARG, "no edges");
+    NK_DEV(chains->s, "chains->s");
+    if (chains->n_accepted) NK_DEV(chains->n_accepted, "chains->n_accepted");
+    if (stats_out) NK_DEV(stats_out, "stats_out");
+    if (theta_dot_out && (st0 = check_complex_out(theta_dot_out, "theta_dot_out")) != NK_OK) return st0;
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool svd = cfg->solver == NK_SOLVER_SVD;
+    return with_workspace(ctx, [&](Carver &c, bool run) -> nk_status {
+        TdvpWs w{};
+        w.samples = c.take<int8_t>((size_t)Ns * N);
+        w.eloc = c.take<double>(2 * Ns);
+        w.stats4 = c.take<double>(4);
+        w.O = c.take<double>((size_t)2 * Ns * Np);
+        w.mean = c.take<double>(2 * Np);
+        w.R = c.take<double>((size_t)4 * Ns * Np);
+        w.g = c.take<double>(2 * Ns);
+        w.F = c.take<double>(n);
+        w.rhs = c.take<double>(n);
+        w.S = c.take<double>((size_t)n * n);
+        w.partial = c.take<double>(nk::gemv_t_partial_doubles(2 * Ns, n));
+        w.info = c.take<int>(2);
+        w.acc = c.take<unsigned long long>(C);
+        if (svd) {
+            w.V = c.take<double>((size_t)n * n);
+            w.ev = c.take<double>(n);
+            w.evmax = c.take<double>(4);
+            w.z = c.take<double>(n);
+            w.gpart = c.take<double>(nk::gemv_t_partial_doubles(n, n));
+            w.eig = c.take<char>(nk::eig_ws_bytes(n));
+            w.kept = c.take<int>(4);
+        }
+        double *k1 = c.take<double>(n);
+        double *k2 = c.take<double>(n);
+        double *ptmp = c.take<double>(2 * Np);
+        if (!run) return NK_OK;
+        NK_CU(cudaMemsetAsync(w.acc, 0, sizeof(unsigned long long) * C, st), "acc");
+        nk_status e = tdvp_slope(ctx, N, M, rbm->params, ham, chains, cfg, cfg->n_discard, w, k1, st);
+        if (e != NK_OK) return e;
+        if (stats_out)
+            NK_CU(cudaMemcpyAsync(stats_out, w.stats4, 4 * sizeof(double), cudaMemcpyDeviceToDevice, st), "stats");
+        if (theta_dot_out) NK_CU(nk::launch_caxpy_realified(Np, nullptr, 1.0, k1, theta_dot_out, st), "theta dot");
+        if (cfg->integrator == NK_TDVP_EULER) {
+            NK_CU(nk::launch_caxpy_realified(Np, rbm->params, cfg->dt, k1, rbm->params, st), "euler");
+        } else {
+            NK_CU(nk::launch_caxpy_realified(Np, rbm->params, cfg->dt, k1, ptmp, st), "heun");
+            e = tdvp_slope(ctx, N, M, ptmp, ham, chains, cfg, 0, w, k2, st);
+            if (e != NK_OK) return e;
+            NK_CU(nk::launch_caxpy_realified(Np, rbm->params, 0.5 * cfg->dt, k1, rbm->params, st), "heun");
+            NK_CU(nk::launch_caxpy_realified(Np, rbm->params, 0.5 * cfg->dt, k2, rbm->params, st), "heun");
+        }
+        if (chains->n_accepted) {
+            (k_add_u64<<<(C + 255) / 256, 256, 0, st>>>(
+                C, w.acc, reinterpret_cast<unsigned long long *>(chains->n_accepted)), nk::note_launch());
+            NK_CU(cudaGetLastError(), "acc");
+        }
+        return NK_OK;
+    });
 }
 
 }  // extern "C"

@@ -266,6 +266,28 @@ cudaError_t launch_eig_diag(int64_t n, const double *A, double *w, double *wmax,
 cudaError_t launch_spectral_filter(int64_t n, const double *w, const double *wmax, double rcond, int power,
                                    double *z, int *kept, cudaStream_t st);
 
+// Complex holomorphic RBM (k_complex.cu); complex arrays are interleaved
+// (re, im) doubles, 16-byte aligned.  Shared memory per warp of the one-
+// warp-per-chain kernels: crbm_smem_per_warp (4 warps per block).
+size_t crbm_smem_per_warp(int N, int M);
+cudaError_t launch_crbm_logpsi(int N, int M, const double *p, const int8_t *s, int64_t B, double *out,
+                               cudaStream_t st);
+cudaError_t launch_crbm_sweep(int N, int M, const double *p, int rule, int E, const int32_t *edges, int C, int8_t *s,
+                              int64_t sweep0, int n_discard, int n_samples, uint64_t seed, uint32_t stream_id,
+                              int8_t *samples, unsigned long long *n_accepted, cudaStream_t st);
+cudaError_t launch_crbm_eloc(int N, int M, const double *p, const nk_ham *ham, const int8_t *s, int64_t Ns,
+                             double *eloc, cudaStream_t st);
+cudaError_t launch_crbm_jacobian(int N, int M, const double *p, const int8_t *s, int64_t Ns, double *O,
+                                 cudaStream_t st);
+// mean: complex [cols] scratch; R [2 rows][2 cols] the realified centred O.
+cudaError_t launch_crealify(int64_t rows, int64_t cols, const double *O, double *mean, double *R, cudaStream_t st);
+// out4 = [Re mean, Im mean, variance, error] of complex local energies.
+cudaError_t launch_cstats(int64_t Ns, const double *e, double *out4, cudaStream_t st);
+cudaError_t launch_cforce_g(int64_t Ns, const double *e, const double *stats4, double *g, cudaStream_t st);
+cudaError_t launch_tdvp_rhs(int64_t n, const double *f, int real_time, double *rhs, cudaStream_t st);
+cudaError_t launch_caxpy_realified(int64_t n, const double *base, double h, const double *x, double *out,
+                                   cudaStream_t st);
+
 // params -= lr * delta; norms into stats.
 cudaError_t launch_sgd(int64_t n, double lr, const double *delta, double *params,
                        cudaStream_t st);

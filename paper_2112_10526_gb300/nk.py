@@ -64,6 +64,21 @@ class nk_rbm_symm(ctypes.Structure):
                 ("perms", ctypes.c_void_p), ("params", ctypes.c_void_p)]
 
 
+class nk_crbm(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int32), ("M", ctypes.c_int32), ("params", ctypes.c_void_p)]
+
+
+class nk_tdvp_cfg(ctypes.Structure):
+    _fields_ = [("rule", ctypes.c_int32), ("integrator", ctypes.c_int32), ("real_time", ctypes.c_int32),
+                ("solver", ctypes.c_int32), ("n_discard", ctypes.c_int32), ("n_samples", ctypes.c_int32),
+                ("dt", ctypes.c_double), ("diag_shift", ctypes.c_double), ("rcond", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("stream_id", ctypes.c_uint32)]
+
+
+NK_TDVP_EULER, NK_TDVP_HEUN = 1, 2
+TDVP_STATS_FIELDS = ["energy_re", "energy_im", "variance", "error"]
+
+
 class nk_chains(ctypes.Structure):
     _fields_ = [("C", ctypes.c_int32), ("s", ctypes.c_void_p), ("sweeps_done", ctypes.c_int64),
                 ("n_accepted", ctypes.c_void_p)]
@@ -148,6 +163,12 @@ def lib():
         "nk_sr_step": [P, ctypes.POINTER(nk_rbm), ctypes.POINTER(nk_ham), ctypes.POINTER(nk_chains),
                        ctypes.POINTER(nk_sr_cfg), P, P, P, P],
         "nk_symm_expand": [P, ctypes.POINTER(nk_rbm_symm), P, P],
+        "nk_crbm_logpsi": [P, ctypes.POINTER(nk_crbm), P, i64, P, P],
+        "nk_crbm_metropolis": [P, ctypes.POINTER(nk_crbm), i32, i32, P, i32, P, i64, i32, i32, u64, u32, P, P, P],
+        "nk_crbm_local_energy": [P, ctypes.POINTER(nk_crbm), ctypes.POINTER(nk_ham), P, i64, P, P],
+        "nk_crbm_jacobian": [P, ctypes.POINTER(nk_crbm), P, i64, P, P],
+        "nk_tdvp_step": [P, ctypes.POINTER(nk_crbm), ctypes.POINTER(nk_ham), ctypes.POINTER(nk_chains),
+                         ctypes.POINTER(nk_tdvp_cfg), P, P, P],
         "nk_symm_jacobian": [P, ctypes.POINTER(nk_rbm_symm), i32, P, i64, P, P],
         "nk_symm_sr_step": [P, ctypes.POINTER(nk_rbm_symm), ctypes.POINTER(nk_ham), ctypes.POINTER(nk_chains),
                             ctypes.POINTER(nk_sr_cfg), P, P, P, P],
@@ -403,6 +424,56 @@ def nk_symm_sr_step(ctx, params, N, alpha, perms, ham, chains, cfg, stats_out=No
     _check(lib().nk_symm_sr_step(ctx.handle, ctypes.byref(m), ctypes.byref(ham), ctypes.byref(chains),
                                  ctypes.byref(cfg), _ptr(stats_out), _ptr(samples_out), _ptr(eloc_out),
                                  _stream(stream)))
+
+
+def make_crbm(params, N, M):
+    """nk_crbm over a device complex128 tensor [N + M + M N]."""
+    assert params.dtype == torch.complex128 and params.is_cuda and params.numel() == N + M + M * N
+    return nk_crbm(N, M, params.data_ptr())
+
+
+def nk_crbm_logpsi(ctx, params, N, M, s, out, stream=None):
+    r = make_crbm(params, N, M)
+    _check(lib().nk_crbm_logpsi(ctx.handle, ctypes.byref(r), _ptr(s), s.shape[0], _ptr(out), _stream(stream)))
+    return out
+
+
+def nk_crbm_metropolis(ctx, params, N, M, rule, edges, s, sweep0, n_discard, n_samples, seed, stream_id, samples_out,
+                       n_accepted=None, stream=None):
+    r = make_crbm(params, N, M)
+    ne = 0 if edges is None else edges.shape[0]
+    _check(lib().nk_crbm_metropolis(ctx.handle, ctypes.byref(r), RULE[rule] if isinstance(rule, str) else rule, ne,
+                                    _ptr(edges), s.shape[0], _ptr(s), int(sweep0), int(n_discard), int(n_samples),
+                                    int(seed), int(stream_id), _ptr(samples_out), _ptr(n_accepted), _stream(stream)))
+    return samples_out
+
+
+def nk_crbm_local_energy(ctx, params, N, M, ham, s, out, stream=None):
+    r = make_crbm(params, N, M)
+    _check(lib().nk_crbm_local_energy(ctx.handle, ctypes.byref(r), ctypes.byref(ham), _ptr(s), s.shape[0], _ptr(out),
+                                      _stream(stream)))
+    return out
+
+
+def nk_crbm_jacobian(ctx, params, N, M, s, O_out, stream=None):
+    r = make_crbm(params, N, M)
+    _check(lib().nk_crbm_jacobian(ctx.handle, ctypes.byref(r), _ptr(s), s.shape[0], _ptr(O_out), _stream(stream)))
+    return O_out
+
+
+def make_tdvp_cfg(rule, integrator, real_time, solver, n_discard, n_samples, dt, diag_shift, seed, stream_id=0,
+                  rcond=0.0):
+    return nk_tdvp_cfg(RULE[rule] if isinstance(rule, str) else rule,
+                       {"euler": NK_TDVP_EULER, "heun": NK_TDVP_HEUN}.get(integrator, integrator), int(bool(real_time)),
+                       SOLVER[solver] if isinstance(solver, str) else solver, int(n_discard), int(n_samples),
+                       float(dt), float(diag_shift), float(rcond), int(seed), int(stream_id))
+
+
+def nk_tdvp_step(ctx, params, N, M, ham, chains, cfg, stats_out=None, theta_dot_out=None, stream=None):
+    """One t-VMC step of the complex RBM; params (device complex128) updated in place."""
+    r = make_crbm(params, N, M)
+    _check(lib().nk_tdvp_step(ctx.handle, ctypes.byref(r), ctypes.byref(ham), ctypes.byref(chains), ctypes.byref(cfg),
+                              _ptr(stats_out), _ptr(theta_dot_out), _stream(stream)))
 
 
 def sr_stats_dict(t):

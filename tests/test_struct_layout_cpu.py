@@ -17,7 +17,7 @@ from paper_2112_10526_gb300 import nk
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 INCLUDE = os.path.join(ROOT, "include")
 
-STRUCTS = ["nk_rbm", "nk_ham", "nk_qgt", "nk_rbm_symm", "nk_chains", "nk_sr_cfg", "nk_request", "nk_result", "nk_server_stats"]
+STRUCTS = ["nk_rbm", "nk_ham", "nk_qgt", "nk_rbm_symm", "nk_crbm", "nk_tdvp_cfg", "nk_chains", "nk_sr_cfg", "nk_request", "nk_result", "nk_server_stats"]
 
 CONSTANTS = {
     "NK_OK": nk.NK_OK, "NK_ERR_INVALID_ARG": nk.NK_ERR_INVALID_ARG, "NK_ERR_CUDA": nk.NK_ERR_CUDA,
@@ -30,6 +30,7 @@ CONSTANTS = {
     "NK_SOLVER_CHOLESKY": nk.NK_SOLVER_CHOLESKY, "NK_SOLVER_CHOLESKY_SAMPLESPACE": nk.NK_SOLVER_CHOLESKY_SAMPLESPACE,
     "NK_SOLVER_CG": nk.NK_SOLVER_CG, "NK_SOLVER_SVD": nk.NK_SOLVER_SVD,
     "NK_SOLVER_SVD_SAMPLESPACE": nk.NK_SOLVER_SVD_SAMPLESPACE, "NK_QGT_ONTHEFLY": nk.NK_QGT_ONTHEFLY, "NK_QGT_JACOBIAN": nk.NK_QGT_JACOBIAN,
+    "NK_TDVP_EULER": nk.NK_TDVP_EULER, "NK_TDVP_HEUN": nk.NK_TDVP_HEUN,
     "NK_REQ_EXPECT": nk.NK_REQ_EXPECT, "NK_REQ_SR_STEP": nk.NK_REQ_SR_STEP,
     "NK_PROF_SWEEP": nk.PROF_CLASSES["sweep"], "NK_PROF_ELOC": nk.PROF_CLASSES["eloc"],
     "NK_PROF_GRAM": nk.PROF_CLASSES["gram"], "NK_PROF_CHOL_UPDATE": nk.PROF_CLASSES["chol_update"],
