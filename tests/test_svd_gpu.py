@@ -70,8 +70,9 @@ def test_sample_space_svd_matches_oracle(ctx, N, M, Ns, sig, prec):
     got, info = _solve(ctx, p, N, M, s, F, "svd_samplespace", 0.0, 1e-12, prec)
     ref = oracle.solve_svd_samplespace(O, F, 1e-12)
     assert vec_rel_err(got, ref) < 1e-8, info
-    if Ns < N + M + M * N:
-        # the two spaces give the same truncated solve
+    if Ns < N + M + M * N <= 2000:
+        # the two spaces give the same truncated solve (the dense Np x Np
+        # check only where the oracle's host SVD of S stays small)
         assert vec_rel_err(got, oracle.solve_svd(oracle.qgt_dense(O), F, 0.0, 1e-12)) < 1e-8
 
 
