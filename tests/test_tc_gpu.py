@@ -290,13 +290,16 @@ def test_mixed_jacobian_products_24x24_full_size_sampled(ctx):
     assert nk.nk_ctx_error(ctx) == 0
 
 
-def test_mixed_cg_solve_full_size_sampled_residual(ctx):
+@pytest.mark.parametrize("tol,bound", [(1e-9, 1e-8), (1e-6, 5e-6)])
+def test_mixed_cg_solve_full_size_sampled_residual(ctx, tol, bound):
     """The NK_MIXED CG solve of (S + eps I) delta = F at the 20 x 20 TFIM
-    workload's full size (Ns = 16384, Np = 642 000, on-the-fly QGT, 4-slice
-    products), checked by the residual on 64 sampled components, with the
-    QGT product of App. B.3 taken through the oracle's Jacobian: w = J delta
-    over all samples from its rows, Delta w centred, then (S delta)_q =
-    (1/Ns) sum_k O_kq Delta w_k from its columns of the sampled q."""
+    workload's full size (Ns = 16384, Np = 642 000, on-the-fly QGT), checked
+    by the residual on 64 sampled components, with the QGT product of App.
+    B.3 taken through the oracle's Jacobian: w = J delta over all samples from
+    its rows, Delta w centred, then (S delta)_q = (1/Ns) sum_k O_kq Delta w_k
+    from its columns of the sampled q.  At tol 1e-9 the products have 4
+    slices (2^-32); at tol 1e-6 3 slices on an FP32 tanh(theta) (2^-24), and
+    the residual bound leaves room for that product error."""
     N, M, Ns, eps = 400, 1600, 16384, 0.01
     p = I.rbm_params(N, M, 3)
     s = I.random_configs(Ns, N, 3)
@@ -304,7 +307,7 @@ def test_mixed_cg_solve_full_size_sampled_residual(ctx):
     rng = np.random.default_rng(13)
     F = rng.normal(size=Np) * 0.1
     d = torch.empty(Np, dtype=torch.float64, device=dev())
-    info = nk.nk_sr_solve(ctx, cu(p), N, M, cu(s), cu(F), d, solver="cg", diag_shift=eps, cg_tol=1e-9,
+    info = nk.nk_sr_solve(ctx, cu(p), N, M, cu(s), cu(F), d, solver="cg", diag_shift=eps, cg_tol=tol,
                           cg_maxiter=3000, precision="mixed")
     assert info["converged"]
     delta = d.cpu().numpy()
@@ -312,5 +315,4 @@ def test_mixed_cg_solve_full_size_sampled_residual(ctx):
     dw = w - w.mean()
     idx = _sampled_params(rng, N, M, 8, 8, 48)
     r = oracle.jacobian_cols(p, N, M, s, idx).T @ dw / Ns + eps * delta[idx] - F[idx]
-    # the CG stops at ||r|| <= 1e-9 ||F||; the 4-slice products add about 2^-32
-    assert np.abs(r).max() <= 1e-8 * np.linalg.norm(F)
+    assert np.abs(r).max() <= bound * np.linalg.norm(F)
