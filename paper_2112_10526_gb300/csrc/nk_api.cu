@@ -272,12 +272,13 @@ void carve_solve(Carver &c, SolveWs &w, int N, int M, int64_t Ns, int solver, in
 }
 
 // Slices per operand row of the NK_MIXED Jacobian products: 4 in CG matvecs
-// (2^-32 of the row maximum; 3, 2^-24, when the CG tolerance is 1e-6 or
-// looser: a product error near 5e-7 relative, below what that tolerance
-// resolves), 7 (FP64 level) where the sample-space solve subtracts nearly
-// equal vectors.
+// (2^-32 of the row maximum), 7 (FP64 level) where the sample-space solve
+// subtracts nearly equal vectors.  When the CG tolerance is 1e-6 or looser
+// the CG products read tanh(theta) in FP32 (a product error near 6e-8
+// relative, well below what that tolerance resolves; 3 slices, at ~5e-7,
+// measured more iterations than they saved).
 constexpr int kMatvecSlices = 4, kExactSlices = 7;
-inline int cg_slices(double tol) { return tol >= 1e-6 ? 3 : kMatvecSlices; }
+inline bool cg_fp32_t(double tol) { return tol >= 1e-6; }
 // Jacobi sweeps of the SVD solvers: stop at a relative off-diagonal norm of
 // 1e-14 (the rounding level of FP64 rotations), at most 60 sweeps.
 constexpr int kMaxJacobiSweeps = 60;
@@ -359,8 +360,8 @@ nk_status run_solve(nk_ctx *ctx, int N, int M, int64_t Ns, const int8_t *s, cons
         double *rr = w.sc, *rr_new = w.sc + 1, *pAp = w.sc + 2, *ff = w.sc + 3, *rr_keep = w.sc + 4;
         int *done = w.flags, *iters = w.flags + 1;
         nk::JacPrep jp{};
-        const int slices = cg_slices(tol);
-        if (tc) NK_CU(nk::launch_jac_prep(N, M, Ns, s, T, w.prep, &jp, st, slices < kMatvecSlices), "cg operands");
+        const int slices = kMatvecSlices;
+        if (tc) NK_CU(nk::launch_jac_prep(N, M, Ns, s, T, w.prep, &jp, st, cg_fp32_t(tol)), "cg operands");
         NK_CU(nk::launch_fill(Np, 0.0, w.x, st), "cg init");
         NK_CU(nk::launch_axpby(Np, 1.0, F, 0.0, w.r, st), "cg init");
         NK_CU(nk::launch_axpby(Np, 1.0, F, 0.0, w.p, st), "cg init");

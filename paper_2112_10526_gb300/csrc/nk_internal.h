@@ -217,7 +217,7 @@ cudaError_t launch_theta_tc(int N, int M, const double *b, const double *W, cons
 // (the CG iterations): S' = [S, 1] as BF16 rows [Ns][pad8(N + 1)], its
 // transpose as BF16 columns [N + 1][pad8(Ns)], and, with fp32_t, tanh theta
 // in FP32 [Ns][M] (T32; null otherwise), which the products then read in
-// place of the FP64 T: its 24 bits match 3-slice products, not 4.
+// place of the FP64 T (a relative error of 2^-24 per entry).
 struct JacPrep {
     const __nv_bfloat16 *As, *St;
     const float *T32;

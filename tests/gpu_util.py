@@ -33,8 +33,9 @@ def rel_err(got, ref, floor=None):
 
 
 def vec_rel_err(got, ref):
-    """||got - ref|| / ||ref||."""
-    got = np.asarray(got, dtype=np.float64).ravel()
-    ref = np.asarray(ref, dtype=np.float64).ravel()
+    """||got - ref|| / ||ref|| (real or complex vectors)."""
+    cplx = np.iscomplexobj(got) or np.iscomplexobj(ref)
+    got = np.asarray(got, dtype=np.complex128 if cplx else np.float64).ravel()
+    ref = np.asarray(ref, dtype=np.complex128 if cplx else np.float64).ravel()
     n = np.linalg.norm(ref)
     return float(np.linalg.norm(got - ref) / (n if n > 0 else 1.0))
