@@ -70,11 +70,13 @@ def parse():
                     help="workload name, optionally with @rule to replace its sampler rule "
                          "(e.g. heis2d_10x10@hamiltonian)")
     ap.add_argument("--extra", default="heis2d_10x10,heis2d_10x10_symm",
-                    help="comma-separated workloads timed after the headline (mixed path, same steps)")
+                    help="comma-separated workloads timed after the headline (mixed path, same steps); none: no others")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the other-precision timing")
     ap.add_argument("--compare-steps", type=int, default=2,
                     help="timed steps of the other-precision arm (after one warm-up step)")
+    ap.add_argument("--chains", type=int, default=0,
+                    help="override the workload's chain count (a smaller case of the same kernels, for profilers)")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--serve", type=int, default=512,
                     help="requests of the serving run added to the line (0: none)")
@@ -523,6 +525,9 @@ def run_ours(args, rank, world):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     w = workload(args.workload)
+    if args.chains > 0:
+        w["chains"] = args.chains
+        w["name"] += f"@chains={args.chains}"
     K = args.steps
     r = measure(w, args.precision, K, args.warmup, rank, world, dev)
     ms_plain, prof = r["ms"], r["prof"]
@@ -566,7 +571,7 @@ def run_ours(args, rank, world):
                                  "cg_iters": s2["cg_iters"], "clocks": r2["clocks"],
                                  "config": workload_config(w, other, world)}
     extra = {}
-    for name in [x for x in args.extra.split(",") if x] if world == 1 else []:
+    for name in [x for x in args.extra.split(",") if x and x != "none"] if world == 1 else []:
         we = workload(name)
         re_ = measure(we, args.precision, K, args.warmup, rank, world, dev)
         Ke = K

@@ -59,7 +59,6 @@ struct SgArgs {
     int mode;             // 0: C = R (+ bias), 1: C -= R, 2: C += R, 3: C[row][bx] = sum_col R t'
     const double *bias;   // [cols] or null
     const double *T;      // mode 3: T [rows][Mt]; t'_col = T[col] for col < Mt, 1 at col = Mt
-    const float *T32;     // mode 3: the same in FP32 (read instead of T when set)
     int Mt;
     int *err;
 };
@@ -166,8 +165,7 @@ __global__ void __launch_bounds__(kSgThreads, 2)
             tc_fence_after();
             const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
             const bool row_ok = row < a.rows;
-            const double *trow = (a.mode == 3 && row_ok && !a.T32) ? a.T + (size_t)row * a.Mt : nullptr;
-            const float *trow32 = (a.mode == 3 && row_ok && a.T32) ? a.T32 + (size_t)row * a.Mt : nullptr;
+            const double *trow = (a.mode == 3 && row_ok) ? a.T + (size_t)row * a.Mt : nullptr;
             double racc = 0.0;
 #pragma unroll 1
             for (int c8 = 0; c8 < kBN; c8 += 8) {
@@ -180,10 +178,7 @@ __global__ void __launch_bounds__(kSgThreads, 2)
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
                         const int64_t col = n0 + c8 + j;
-                        const bool have = trow != nullptr || trow32 != nullptr;
-                        tv[j] = !have ? 0.0
-                                      : (col < a.Mt ? (trow32 ? (double)trow32[col] : trow[col])
-                                                    : (col == a.Mt ? 1.0 : 0.0));
+                        tv[j] = trow == nullptr ? 0.0 : (col < a.Mt ? trow[col] : (col == a.Mt ? 1.0 : 0.0));
                     }
                 }
                 uint32_t r[kMaxSB][8];
@@ -395,8 +390,7 @@ __global__ void k_scale_g(int64_t Ns, const double *__restrict__ g, double scale
 // Column exponents of T' o g' (column j of (T' o g')^T): an upper bound
 // max_k (exp(T'_kj) + exp(g'_k)) of the exact exponent, at most one above it,
 // taken with integer operations only.
-template <typename TT>
-__global__ void k_tg_colexp(const TT *__restrict__ T, const int *__restrict__ ge, int64_t Ns, int M,
+__global__ void k_tg_colexp(const double *__restrict__ T, const int *__restrict__ ge, int64_t Ns, int M,
                             int *__restrict__ expo) {
     const int j = blockIdx.x * 32 + threadIdx.x;
     const int64_t k0 = (int64_t)blockIdx.y * 256;
@@ -405,7 +399,7 @@ __global__ void k_tg_colexp(const TT *__restrict__ T, const int *__restrict__ ge
         const int64_t kend = k0 + 256 < Ns ? k0 + 256 : Ns;
 #pragma unroll 4
         for (int64_t k = k0 + threadIdx.y; k < kend; k += blockDim.y) {  // loads of 4 rows in flight
-            const int et = j < M ? exp_of((double)T[(size_t)k * M + j]) : 1, eg = ge[k];
+            const int et = j < M ? exp_of(T[(size_t)k * M + j]) : 1, eg = ge[k];
             if (et != -100000 && eg != -100000) ex = max(ex, et + eg);
         }
     }
@@ -420,8 +414,7 @@ __global__ void k_tg_colexp(const TT *__restrict__ T, const int *__restrict__ ge
 
 // (T' o g')^T sliced: out [SB][M+1][ld], row j, column k, through tiles of
 // 64 k x 32 j (ld is even: each lane writes a BF16 pair per plane).
-template <typename TT>
-__global__ void k_tg_slice(const TT *__restrict__ T, const double *__restrict__ gp, int64_t Ns, int M, int SB,
+__global__ void k_tg_slice(const double *__restrict__ T, const double *__restrict__ gp, int64_t Ns, int M, int SB,
                            int64_t ld, const int *__restrict__ expo, __nv_bfloat16 *__restrict__ out) {
     __shared__ double tile[64][33];
     const int64_t k0 = (int64_t)blockIdx.x * 64;
@@ -430,7 +423,7 @@ __global__ void k_tg_slice(const TT *__restrict__ T, const double *__restrict__ 
         const int64_t k = k0 + r;
         const int j = j0 + threadIdx.x;
         double v = 0.0;
-        if (k < Ns && j <= M) v = (j < M ? (double)T[(size_t)k * M + j] : 1.0) * gp[k];
+        if (k < Ns && j <= M) v = (j < M ? T[(size_t)k * M + j] : 1.0) * gp[k];
         tile[r][threadIdx.x] = v;
     }
     __syncthreads();
@@ -522,11 +515,10 @@ bool make_sliced_map(CUtensorMap *map, const __nv_bfloat16 *p, int64_t rows, int
 cudaError_t sgemm(const __nv_bfloat16 *A, int64_t rows, int64_t ldA, const __nv_bfloat16 *Bsl, const int *expB,
                   int64_t cols, int64_t ldB, int64_t K, int SB, double *C, int64_t ldc, int mode,
                   const double *bias, int *err, cudaStream_t st, const double *T = nullptr, int Mt = 0,
-                  int ksplit = 1, int64_t split_stride = 0, const float *T32 = nullptr) {
+                  int ksplit = 1, int64_t split_stride = 0) {
     if (rows <= 0 || cols <= 0 || K <= 0) return cudaSuccess;
     if (SB < 1 || SB > kMaxSB || rows > (1LL << 31) - kBM || cols > (1LL << 31) - kBN) return cudaErrorInvalidValue;
-    if (ksplit < 1 || (ksplit > 1 && mode != 0) || (mode == 3 && T == nullptr && T32 == nullptr))
-        return cudaErrorInvalidValue;
+    if (ksplit < 1 || (ksplit > 1 && mode != 0) || (mode == 3 && T == nullptr)) return cudaErrorInvalidValue;
     CUtensorMap ma, mb;
     if (!make_rows_map(&ma, A, rows, K, ldA, kBM) || !make_sliced_map(&mb, Bsl, cols, K, ldB, SB, kBN))
         return cudaErrorInvalidValue;
@@ -537,7 +529,7 @@ cudaError_t sgemm(const __nv_bfloat16 *A, int64_t rows, int64_t ldA, const __nv_
     uint32_t tcols = 32;
     while (tcols < (uint32_t)(SB * kBN)) tcols <<= 1;
     SgArgs a{rows, cols, kchunks, SB, kc_split, sgemm_stages(SB), kAB + SB * kBB, tcols, expB, C, ldc,
-             split_stride, mode, bias, T, T32, Mt, err};
+             split_stride, mode, bias, T, Mt, err};
     dim3 grid(nblk(cols, kBN), nblk(rows, kBM), (unsigned)((kchunks + kc_split - 1) / kc_split));
     (k_sgemm<<<grid, kSgThreads, sgemm_smem_bytes(SB), st>>>(ma, mb, a), nk::note_launch());
     return cudaGetLastError();
@@ -580,35 +572,6 @@ cudaError_t launch_theta_tc(int N, int M, const double *b, const double *W, cons
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
-__global__ void k_to_float(int64_t n, const double *__restrict__ x, float *__restrict__ y) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) y[i] = (float)x[i];
-}
-
-size_t jac_prep_bytes(int N, int M, int64_t Ns) {
-    return ((size_t)Ns * pad8(N + 1) * 2 + 255) / 256 * 256 + ((size_t)(N + 1) * pad8(Ns) * 2 + 255) / 256 * 256 +
-           ((size_t)Ns * M * 4 + 255) / 256 * 256 + 256;
-}
-
-cudaError_t launch_jac_prep(int N, int M, int64_t Ns, const int8_t *s, const double *T, void *ws, JacPrep *out,
-                            cudaStream_t st, bool fp32_t) {
-    char *p = static_cast<char *>(ws);
-    auto take = [&](size_t bytes) {
-        char *q = p;
-        p += (bytes + 255) / 256 * 256;
-        return q;
-    };
-    const int64_t lda = pad8(N + 1), ldt = pad8(Ns);
-    auto *As = reinterpret_cast<__nv_bfloat16 *>(take((size_t)Ns * lda * 2));
-    auto *St = reinterpret_cast<__nv_bfloat16 *>(take((size_t)(N + 1) * ldt * 2));
-    auto *T32 = reinterpret_cast<float *>(take((size_t)Ns * M * 4));
-    (k_pm1_rows<<<nblk(Ns * lda, 256), 256, 0, st>>>(s, Ns, N, 1, lda, As), nk::note_launch());
-    (k_pm1_cols<<<dim3(nblk(ldt, 32), nblk(N + 1, 32)), dim3(32, 8), 0, st>>>(s, Ns, N, ldt, St), nk::note_launch());
-    if (fp32_t) (k_to_float<<<nblk(Ns * M, 256), 256, 0, st>>>(Ns * M, T, T32), nk::note_launch());
-    *out = JacPrep{As, St, fp32_t ? T32 : nullptr};
-    return cudaGetLastError();
-}
-
 size_t tc_jvp_ws_bytes(int N, int M, int64_t Ns) {
     const int64_t ld = pad8(N + 1), ntc = (M + 1 + kBN - 1) / kBN;
     return ((size_t)Ns * ld * 2 + 255) / 256 * 256 + ((size_t)kMaxSB * (M + 1) * ld * 2 + 255) / 256 * 256 +
@@ -619,7 +582,7 @@ size_t tc_jvp_ws_bytes(int N, int M, int64_t Ns) {
 // out = J v with V' cut into SB slices: w = rowdot(T', S' V'^T), the row
 // products taken in the S-GEMM epilogue per 64-column tile and summed after.
 cudaError_t launch_jvp_tc(int N, int M, int64_t Ns, const int8_t *s, const double *T, const double *v,
-                          double *out, int SB, int *err, void *ws, cudaStream_t st, const JacPrep *prep) {
+                          double *out, int SB, int *err, void *ws, cudaStream_t st) {
     const int64_t ld = pad8(N + 1);
     char *p = static_cast<char *>(ws);
     auto take = [&](size_t bytes) {
@@ -628,21 +591,17 @@ cudaError_t launch_jvp_tc(int N, int M, int64_t Ns, const int8_t *s, const doubl
         return q;
     };
     auto *As = reinterpret_cast<__nv_bfloat16 *>(take((size_t)Ns * ld * 2));
-    if (prep) As = const_cast<__nv_bfloat16 *>(prep->As);
     auto *Vs = reinterpret_cast<__nv_bfloat16 *>(take((size_t)kMaxSB * (M + 1) * ld * 2));
     auto *Vp = reinterpret_cast<double *>(take((size_t)(M + 1) * (N + 1) * 8));
     auto *ev = reinterpret_cast<int *>(take((size_t)(M + 1) * 4));
     const int ntc = (M + 1 + kBN - 1) / kBN;
     auto *P = reinterpret_cast<double *>(take((size_t)Ns * ntc * 8));
     const int64_t tot = (int64_t)(M + 1) * (N + 1);
-    if (!prep) (k_pm1_rows<<<nblk(Ns * ld, 256), 256, 0, st>>>(s, Ns, N, 1, ld, As), nk::note_launch());
+    (k_pm1_rows<<<nblk(Ns * ld, 256), 256, 0, st>>>(s, Ns, N, 1, ld, As), nk::note_launch());
     (k_build_vaug<<<nblk(tot, 256), 256, 0, st>>>(N, M, v, Vp), nk::note_launch());
     (k_slice_long_rows<<<M + 1, 128, 0, st>>>(Vp, N + 1, M + 1, N + 1, nullptr, SB, ld, Vs, ev), nk::note_launch());
     const int slot = prof_begin(NK_PROF_JVP_VJP, st);
-    cudaError_t e = (prep && prep->T32)
-                        ? sgemm(As, Ns, ld, Vs, ev, M + 1, ld, N + 1, SB, P, ntc, 3, nullptr, err, st, nullptr, M, 1, 0,
-                                prep->T32)
-                        : sgemm(As, Ns, ld, Vs, ev, M + 1, ld, N + 1, SB, P, ntc, 3, nullptr, err, st, T, M);
+    cudaError_t e = sgemm(As, Ns, ld, Vs, ev, M + 1, ld, N + 1, SB, P, ntc, 3, nullptr, err, st, T, M);
     prof_end(slot, st, 2.0 * (double)Ns * (N + 1) * (double)(M + 1), sgemm_flops(Ns, M + 1, N + 1, SB));
     if (e != cudaSuccess) return e;
     (k_rowsum_partials<<<nblk(Ns, 256), 256, 0, st>>>(Ns, ntc, P, out), nk::note_launch());
@@ -662,7 +621,7 @@ size_t tc_vjp_ws_bytes(int N, int M, int64_t Ns) {
 // out = J^T g' with g' = scale (g - shift), (T' o g')^T cut into SB slices.
 cudaError_t launch_vjp_tc(int N, int M, int64_t Ns, const int8_t *s, const double *T, const double *g,
                           double scale, const double *shift, double *out, int SB, int *err, void *ws,
-                          cudaStream_t st, const JacPrep *prep) {
+                          cudaStream_t st) {
     const int64_t ld = pad8(Ns);
     char *p = static_cast<char *>(ws);
     auto take = [&](size_t bytes) {
@@ -671,28 +630,19 @@ cudaError_t launch_vjp_tc(int N, int M, int64_t Ns, const int8_t *s, const doubl
         return q;
     };
     auto *St = reinterpret_cast<__nv_bfloat16 *>(take((size_t)(N + 1) * ld * 2));
-    if (prep) St = const_cast<__nv_bfloat16 *>(prep->St);
     auto *Gs = reinterpret_cast<__nv_bfloat16 *>(take((size_t)kMaxSB * (M + 1) * ld * 2));
     auto *eg = reinterpret_cast<int *>(take((size_t)(M + 1) * 4));
     auto *PT = reinterpret_cast<double *>(take((size_t)kMaxKSplit * (N + 1) * (M + 1) * 8));
     auto *gp = reinterpret_cast<double *>(take((size_t)Ns * 8));
     auto *ge = reinterpret_cast<int *>(take((size_t)Ns * 4));
     dim3 tb(32, 8);
-    if (!prep)
-        (k_pm1_cols<<<dim3(nblk(ld, 32), nblk(N + 1, 32)), tb, 0, st>>>(s, Ns, N, ld, St), nk::note_launch());
+    (k_pm1_cols<<<dim3(nblk(ld, 32), nblk(N + 1, 32)), tb, 0, st>>>(s, Ns, N, ld, St), nk::note_launch());
     (k_fill_int<<<nblk(M + 1, 256), 256, 0, st>>>(M + 1, -100000, eg), nk::note_launch());
     (k_scale_g<<<nblk(Ns, 256), 256, 0, st>>>(Ns, g, scale, shift, gp, ge), nk::note_launch());
-    if (prep && prep->T32) {
-        (k_tg_colexp<float><<<dim3(nblk(M + 1, 32), nblk(Ns, 256)), dim3(32, 8), 0, st>>>(prep->T32, ge, Ns, M, eg),
-         nk::note_launch());
-        (k_tg_slice<float><<<dim3(nblk(ld, 64), nblk(M + 1, 32)), tb, 0, st>>>(prep->T32, gp, Ns, M, SB, ld, eg, Gs),
-         nk::note_launch());
-    } else {
-        (k_tg_colexp<double><<<dim3(nblk(M + 1, 32), nblk(Ns, 256)), dim3(32, 8), 0, st>>>(T, ge, Ns, M, eg),
-         nk::note_launch());
-        (k_tg_slice<double><<<dim3(nblk(ld, 64), nblk(M + 1, 32)), tb, 0, st>>>(T, gp, Ns, M, SB, ld, eg, Gs),
-         nk::note_launch());
-    }
+    (k_tg_colexp<<<dim3(nblk(M + 1, 32), nblk(Ns, 256)), dim3(32, 8), 0, st>>>(T, ge, Ns, M, eg),
+     nk::note_launch());
+    (k_tg_slice<<<dim3(nblk(ld, 64), nblk(M + 1, 32)), tb, 0, st>>>(T, gp, Ns, M, SB, ld, eg, Gs),
+     nk::note_launch());
     // split the long K = Ns range until the grid covers the SMs twice
     // (every split keeps >= 4 chunks; each split's FP32 levels stay exact)
     int dev = 0, sms = 0;

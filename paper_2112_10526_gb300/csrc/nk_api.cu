@@ -204,7 +204,6 @@ struct SolveWs {
     int *kept;
     void *tc;   // tensor-core slices and inverted diagonal blocks (NK_MIXED)
     void *tcm;  // tensor-core Jacobian-product workspace (NK_MIXED)
-    void *prep; // NK_MIXED CG: the products' fixed operands (nk::JacPrep)
     int *tcerr; // sticky tensor-core error word of the context
 };
 
@@ -228,7 +227,6 @@ void carve_solve(Carver &c, SolveWs &w, int N, int M, int64_t Ns, int solver, in
         w.r = c.take<double>(Np);
         w.p = c.take<double>(Np);
         w.Ap = c.take<double>(Np);
-        if (precision == NK_MIXED) w.prep = c.take<char>(nk::jac_prep_bytes(N, M, Ns));
     } else if (solver == NK_SOLVER_CHOLESKY) {
         w.dJ = c.take<double>((size_t)Ns * Np);
         w.S = c.take<double>((size_t)Np * Np);
@@ -271,43 +269,38 @@ void carve_solve(Carver &c, SolveWs &w, int N, int M, int64_t Ns, int solver, in
     }
 }
 
+// (G + eps I) v for the on-the-fly QGT (App. B.3).
 // Slices per operand row of the NK_MIXED Jacobian products: 4 in CG matvecs
 // (2^-32 of the row maximum), 7 (FP64 level) where the sample-space solve
-// subtracts nearly equal vectors.  When the CG tolerance is 1e-6 or looser
-// the CG products read tanh(theta) in FP32 (a product error near 6e-8
-// relative, well below what that tolerance resolves; 3 slices, at ~5e-7,
-// measured more iterations than they saved).
+// subtracts nearly equal vectors.
 constexpr int kMatvecSlices = 4, kExactSlices = 7;
-inline bool cg_fp32_t(double tol) { return tol >= 1e-6; }
 // Jacobi sweeps of the SVD solvers: stop at a relative off-diagonal norm of
 // 1e-14 (the rounding level of FP64 rotations), at most 60 sweeps.
 constexpr int kMaxJacobiSweeps = 60;
 constexpr double kJacobiTol = 1e-14;
 
 cudaError_t jvp_any(int N, int M, int64_t Ns, const int8_t *s, const double *T, const double *v, SolveWs &w,
-                    double *out, int precision, int slices, cudaStream_t st, const nk::JacPrep *prep = nullptr) {
-    if (precision == NK_MIXED) return nk::launch_jvp_tc(N, M, Ns, s, T, v, out, slices, w.tcerr, w.tcm, st, prep);
+                    double *out, int precision, int slices, cudaStream_t st) {
+    if (precision == NK_MIXED) return nk::launch_jvp_tc(N, M, Ns, s, T, v, out, slices, w.tcerr, w.tcm, st);
     return nk::launch_jvp(N, M, Ns, s, T, v, w.U, out, st);
 }
 
 cudaError_t vjp_any(int N, int M, int64_t Ns, const int8_t *s, const double *T, const double *g, double scale,
-                    const double *shift, SolveWs &w, double *out, int precision, int slices, cudaStream_t st,
-                    const nk::JacPrep *prep = nullptr) {
+                    const double *shift, SolveWs &w, double *out, int precision, int slices, cudaStream_t st) {
     if (precision == NK_MIXED)
-        return nk::launch_vjp_tc(N, M, Ns, s, T, g, scale, shift, out, slices, w.tcerr, w.tcm, st, prep);
+        return nk::launch_vjp_tc(N, M, Ns, s, T, g, scale, shift, out, slices, w.tcerr, w.tcm, st);
     return nk::launch_vjp(N, M, Ns, s, T, g, scale, shift, w.partial, out, st);
 }
 
-// (G + eps I) v for the on-the-fly QGT (App. B.3).  NK_MIXED: `slices`
-// slices per product operand row, prep the operands fixed through the solve.
+// (G + eps I) v for the on-the-fly QGT (App. B.3).
 cudaError_t qgt_onthefly(int N, int M, int64_t Ns, const int8_t *s, const double *T,
                          const double *v, double eps, SolveWs &w, double *out, cudaStream_t st,
-                         int precision = NK_F64, int slices = kMatvecSlices, const nk::JacPrep *prep = nullptr) {
-    cudaError_t e = jvp_any(N, M, Ns, s, T, v, w, w.w, precision, slices, st, prep);
+                         int precision = NK_F64) {
+    cudaError_t e = jvp_any(N, M, Ns, s, T, v, w, w.w, precision, kMatvecSlices, st);
     if (e != cudaSuccess) return e;
     e = nk::launch_center(Ns, w.w, w.dotp, 1.0 / (double)Ns, st);
     if (e != cudaSuccess) return e;
-    e = vjp_any(N, M, Ns, s, T, w.w, 1.0, nullptr, w, out, precision, slices, st, prep);
+    e = vjp_any(N, M, Ns, s, T, w.w, 1.0, nullptr, w, out, precision, kMatvecSlices, st);
     if (e != cudaSuccess) return e;
     return nk::launch_axpby(n_params(N, M), eps, v, 1.0, out, st);
 }
@@ -359,9 +352,6 @@ nk_status run_solve(nk_ctx *ctx, int N, int M, int64_t Ns, const int8_t *s, cons
     if (solver == NK_SOLVER_CG) {
         double *rr = w.sc, *rr_new = w.sc + 1, *pAp = w.sc + 2, *ff = w.sc + 3, *rr_keep = w.sc + 4;
         int *done = w.flags, *iters = w.flags + 1;
-        nk::JacPrep jp{};
-        const int slices = kMatvecSlices;
-        if (tc) NK_CU(nk::launch_jac_prep(N, M, Ns, s, T, w.prep, &jp, st, cg_fp32_t(tol)), "cg operands");
         NK_CU(nk::launch_fill(Np, 0.0, w.x, st), "cg init");
         NK_CU(nk::launch_axpby(Np, 1.0, F, 0.0, w.r, st), "cg init");
         NK_CU(nk::launch_axpby(Np, 1.0, F, 0.0, w.p, st), "cg init");
@@ -371,8 +361,7 @@ nk_status run_solve(nk_ctx *ctx, int N, int M, int64_t Ns, const int8_t *s, cons
         int it = 0;
         bool converged = false;
         while (it < maxiter) {
-            NK_CU(qgt_onthefly(N, M, Ns, s, T, w.p, eps, w, w.Ap, st, precision, slices, tc ? &jp : nullptr),
-                  "cg matvec");
+            NK_CU(qgt_onthefly(N, M, Ns, s, T, w.p, eps, w, w.Ap, st, precision), "cg matvec");
             NK_CU(nk::launch_dot(Np, w.p, w.Ap, w.dotp, pAp, st), "cg dot");
             NK_CU(nk::launch_cg_update_xr(Np, rr_keep, pAp, w.p, w.Ap, w.x, w.r, done, st), "cg xr");
             NK_CU(nk::launch_dot(Np, w.r, w.r, w.dotp, rr_new, st), "cg dot");

@@ -213,25 +213,13 @@ cudaError_t launch_gram_cols_tc(const double *X, int64_t rows, int64_t ncols, do
 size_t tc_theta_ws_bytes(int N, int M, int64_t B);
 cudaError_t launch_theta_tc(int N, int M, const double *b, const double *W, const int8_t *s, int64_t B,
                             double *theta, int *err, void *ws, cudaStream_t st);
-// Operands of the Jacobian products that stay fixed through one SR solve
-// (the CG iterations): S' = [S, 1] as BF16 rows [Ns][pad8(N + 1)], its
-// transpose as BF16 columns [N + 1][pad8(Ns)], and, with fp32_t, tanh theta
-// in FP32 [Ns][M] (T32; null otherwise), which the products then read in
-// place of the FP64 T (a relative error of 2^-24 per entry).
-struct JacPrep {
-    const __nv_bfloat16 *As, *St;
-    const float *T32;
-};
-size_t jac_prep_bytes(int N, int M, int64_t Ns);
-cudaError_t launch_jac_prep(int N, int M, int64_t Ns, const int8_t *s, const double *T, void *ws, JacPrep *out,
-                            cudaStream_t st, bool fp32_t);
 size_t tc_jvp_ws_bytes(int N, int M, int64_t Ns);
 cudaError_t launch_jvp_tc(int N, int M, int64_t Ns, const int8_t *s, const double *T, const double *v,
-                          double *out, int SB, int *err, void *ws, cudaStream_t st, const JacPrep *prep = nullptr);
+                          double *out, int SB, int *err, void *ws, cudaStream_t st);
 size_t tc_vjp_ws_bytes(int N, int M, int64_t Ns);
 cudaError_t launch_vjp_tc(int N, int M, int64_t Ns, const int8_t *s, const double *T, const double *g,
                           double scale, const double *shift, double *out, int SB, int *err, void *ws,
-                          cudaStream_t st, const JacPrep *prep = nullptr);
+                          cudaStream_t st);
 
 // vector helpers
 cudaError_t launch_axpby(int64_t n, double alpha, const double *x, double beta, double *y,

@@ -297,9 +297,8 @@ def test_mixed_cg_solve_full_size_sampled_residual(ctx, tol, bound):
     by the residual on 64 sampled components, with the QGT product of App.
     B.3 taken through the oracle's Jacobian: w = J delta over all samples from
     its rows, Delta w centred, then (S delta)_q = (1/Ns) sum_k O_kq Delta w_k
-    from its columns of the sampled q.  The products have 4 slices (2^-32);
-    at tol 1e-6 they read tanh(theta) in FP32 (2^-24 per entry), and the
-    residual bound leaves room for that product error."""
+    from its columns of the sampled q, at the two CG tolerances of the tests
+    and of the bench (the 4-slice products carry about 2^-32)."""
     N, M, Ns, eps = 400, 1600, 16384, 0.01
     p = I.rbm_params(N, M, 3)
     s = I.random_configs(Ns, N, 3)
