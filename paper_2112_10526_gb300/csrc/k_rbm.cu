@@ -193,7 +193,16 @@ __device__ __forceinline__ Prod<R> strided_product(const R *__restrict__ t, cons
 
 // Lanes over hidden units, four consecutive units per lane (16-byte loads of
 // t and tau): prod over this lane's units of (1 - si t_j tau_j).  Needs
-// M % 4 == 0 and 16-byte aligned rows.
+// M % 4 == 0 and 16-byte aligned rows.  kSharedTau: the tau row is in shared
+// memory (plain loads instead of the read-only global path); the arithmetic
+// is the same either way.
+template <bool kSharedTau>
+__device__ __forceinline__ float4 load_tau4(const float *tau) {
+    if (kSharedTau) return *reinterpret_cast<const float4 *>(tau);
+    return __ldg(reinterpret_cast<const float4 *>(tau));
+}
+
+template <bool kSharedTau = false>
 __device__ __forceinline__ Prod<float> lane_product4(const float *__restrict__ t, const float *__restrict__ tau,
                                                      float si, int lane, int M) {
     float m0 = 1.f, m1 = 1.f;
@@ -204,7 +213,7 @@ __device__ __forceinline__ Prod<float> lane_product4(const float *__restrict__ t
     for (; j + 3 * 128 < M; j += 4 * 128) {
         float4 uv[4], tv[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) uv[u] = __ldg(reinterpret_cast<const float4 *>(tau + j + u * 128));
+        for (int u = 0; u < 4; ++u) uv[u] = load_tau4<kSharedTau>(tau + j + u * 128);
 #pragma unroll
         for (int u = 0; u < 4; ++u) tv[u] = *reinterpret_cast<const float4 *>(t + j + u * 128);
 #pragma unroll
@@ -219,7 +228,7 @@ __device__ __forceinline__ Prod<float> lane_product4(const float *__restrict__ t
     }
     for (; j < M; j += 128) {
         const float4 tv = *reinterpret_cast<const float4 *>(t + j);
-        const float4 uv = __ldg(reinterpret_cast<const float4 *>(tau + j));
+        const float4 uv = load_tau4<kSharedTau>(tau + j);
         m0 *= fmaf(-si * tv.x, uv.x, 1.f) * fmaf(-si * tv.y, uv.y, 1.f);
         m1 *= fmaf(-si * tv.z, uv.z, 1.f) * fmaf(-si * tv.w, uv.w, 1.f);
     }
@@ -238,6 +247,23 @@ template <>
 __device__ __forceinline__ Prod<float> unit_lanes_product<float>(const float *t, const float *tau, float si, int lane,
                                                                  int M, bool vec4) {
     return vec4 ? lane_product4(t, tau, si, lane, M) : strided_product<float>(t, tau, 1, si, lane, 32, M);
+}
+
+// Asynchronous 16-byte global -> shared copies (cp.async, cache-global): a
+// lane copies the float4 chunks j = 4 lane + 128 u of a row, the same chunks
+// lane_product4 reads, so that each lane waits only for its own copies.
+__device__ __forceinline__ void copy_row_async(float *dst, const float *src, int lane, int M) {
+    for (int j = 4 * lane; j < M; j += 128) {
+        const unsigned d = (unsigned)__cvta_generic_to_shared(dst + j);
+        const size_t g = __cvta_generic_to_global(src + j);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(g) : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+// Waits until at most n of this thread's copy groups are still in flight.
+template <int n>
+__device__ __forceinline__ void copy_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(n) : "memory");
 }
 
 // ------------------------------------------------------------------ sweep ---
@@ -450,6 +476,138 @@ __global__ void __launch_bounds__(128) k_sweep(SweepK<R> P) {
                         const R tj = t[j], tv = si * tau[j];
                         t[j] = (tj - tv) / (R(1) - tj * tv);
                     }
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    sv[i] = (int8_t)-sv[i];
+                    if (k >= 0) sv[k] = (int8_t)-sv[k];
+                }
+                lp += (double)delta;
+                ++acc;
+            }
+            __syncwarp();
+        }
+        if (w >= A.n_discard) {
+            const size_t row = (size_t)c * A.out_stride + A.out_offset + (w - A.n_discard);
+            for (int i = lane; i < N; i += 32) A.samples[row * N + i] = sv[i];
+            if (lane == 0 && A.logpsi) A.logpsi[row] = lp;
+        }
+        __syncwarp();
+    }
+    for (int i = lane; i < N; i += 32) A.s[(size_t)c * N + i] = sv[i];
+    if (lane == 0 && A.n_accepted) A.n_accepted[c] += acc;
+}
+
+// FP32 sweeps of the local and exchange rules with the flip-ratio row of the
+// next proposal prefetched.  The site (local) or edge (exchange) of every
+// proposal comes from its Philox block alone, not from the chain state, so
+// while proposal q is evaluated from one shared-memory buffer, the tau row of
+// proposal q + 1 streams into the other (cp.async); the rows of a large M
+// (18 KB at M = 4608) otherwise arrive from L2 one dependent batch of loads
+// at a time.  The arithmetic and the order of every product are those of
+// k_sweep<float, false>, so the decisions are identical.  Proposals are drawn
+// 32 at a time, one per lane; the first of each batch is fetched without
+// overlap.  Shared memory per warp: t [M], two rows [M], spins [N].
+__global__ void __launch_bounds__(128) k_sweep_pf(SweepK<float> P) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const Tables<float> &T = P.t;
+    const SweepArgs &A = P.a;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (c >= A.C) return;
+    const int N = T.N, M = T.M;
+    unsigned char *base = sm + (size_t)warp * P.warp_bytes;
+    float *t = reinterpret_cast<float *>(base);
+    float *buf0 = reinterpret_cast<float *>(base + P.t_bytes);
+    float *buf1 = reinterpret_cast<float *>(base + 2 * (size_t)P.t_bytes);
+    int8_t *sv = reinterpret_cast<int8_t *>(base + 3 * (size_t)P.t_bytes);
+    const bool local = A.rule == NK_RULE_LOCAL;
+    const float *tab = local ? T.tau_site : T.tau_edge;
+    for (int i = lane; i < N; i += 32) sv[i] = A.s[(size_t)c * N + i];
+    __syncwarp();
+    unsigned long long acc = 0;
+    const int n_sweeps = A.n_discard + A.n_samples;
+    for (int w = 0; w < n_sweeps; ++w) {
+        double lp = 0.0;
+        for (int j = lane; j < M; j += 32) {
+            double th;
+            if (A.theta_in) {
+                th = A.theta_in[(size_t)c * M + j];
+            } else {
+                th = T.b[j];
+                for (int i = 0; i < N; ++i) th = fma(T.Wt[(size_t)i * M + j], (double)sv[i], th);
+            }
+            const float thf = (float)th;
+            t[j] = tanhf(thf);
+            lp += (double)lncosh(thf);
+        }
+        for (int i = lane; i < N; i += 32) lp += T.a[i] * (double)sv[i];
+        lp = warp_sum(lp);
+        __syncwarp();
+        const unsigned long long qbase = (unsigned long long)(A.sweep0 + w) * (unsigned long long)N;
+        int b_i = 0, b_k = -1, b_row = 0, b_ok = 1;
+        float b_K = 0.f, b_aa = 0.f, b_lu = 0.f;
+        for (int q = 0; q < N; ++q) {
+            const int src = q & 31;
+            if (src == 0) {
+                Philox4 y = philox4x64_10(qbase + (unsigned long long)(q + lane), (unsigned long long)c,
+                                          (unsigned long long)A.stream_id, 0ULL, A.seed, 0ULL);
+                b_lu = logf((float)uniform53(y.v[1]));
+                if (local) {
+                    b_i = pick_index(y.v[0], N);
+                    b_k = -1;
+                    b_row = b_i;
+                    b_K = T.K_site[b_i];
+                    b_aa = (float)T.a[b_i];
+                } else {
+                    const int e = pick_index(y.v[0], T.E);
+                    const int i0 = A.edges[2 * e], k0 = A.edges[2 * e + 1];
+                    // an edge outside [0, N) is never a move (bounds guard)
+                    b_ok = (unsigned)i0 < (unsigned)N && (unsigned)k0 < (unsigned)N;
+                    b_i = b_ok ? i0 : 0;
+                    b_k = b_ok ? k0 : 0;
+                    b_row = e;
+                    b_K = T.K_edge[e];
+                    b_aa = b_ok ? (float)(T.a[b_i] - T.a[b_k]) : 0.f;
+                }
+            }
+            const int i = __shfl_sync(kFull, b_i, src), k = __shfl_sync(kFull, b_k, src);
+            const int row = __shfl_sync(kFull, b_row, src);
+            const float K = __shfl_sync(kFull, b_K, src), aa = __shfl_sync(kFull, b_aa, src);
+            const float lu = __shfl_sync(kFull, b_lu, src);
+            const int ok = __shfl_sync(kFull, b_ok, src);
+            float *cur = (q & 1) ? buf1 : buf0;
+            if (src == 0) copy_row_async(cur, tab + (size_t)row * M, lane, M);  // not prefetched
+            if (src + 1 < 32 && q + 1 < N) {
+                const int nrow = __shfl_sync(kFull, b_row, src + 1);
+                copy_row_async((q & 1) ? buf0 : buf1, tab + (size_t)nrow * M, lane, M);
+                copy_wait<1>();  // this proposal's row has landed; the next one is in flight
+            } else {
+                copy_wait<0>();
+            }
+            __syncwarp();
+            const size_t slot = ((size_t)c * A.dec_stride + A.dec_offset + w) * N + q;
+            if (!local && (!ok || sv[i] == sv[k])) {
+                if (lane == 0 && A.decisions) A.decisions[slot] = 2;
+                continue;
+            }
+            const float d0 = -2.f * aa * (float)sv[i];
+            const float si = (float)sv[i];
+            Prod<float> pr = lane_product4<true>(t, cur, si, lane, M);
+            pr = warp_prod_normalised(pr);
+            const float delta = d0 + (K + prod_log(pr));
+            const bool accept = lu < 2.f * delta;
+            if (lane == 0 && A.decisions) A.decisions[slot] = accept ? 1 : 0;
+            if (accept) {
+                for (int j = 4 * lane; j < M; j += 128) {
+                    float4 tv = *reinterpret_cast<const float4 *>(t + j);
+                    const float4 uv = *reinterpret_cast<const float4 *>(cur + j);
+                    const float v0 = si * uv.x, v1 = si * uv.y, v2 = si * uv.z, v3 = si * uv.w;
+                    tv.x = __fdividef(tv.x - v0, fmaf(-tv.x, v0, 1.f));
+                    tv.y = __fdividef(tv.y - v1, fmaf(-tv.y, v1, 1.f));
+                    tv.z = __fdividef(tv.z - v2, fmaf(-tv.z, v2, 1.f));
+                    tv.w = __fdividef(tv.w - v3, fmaf(-tv.w, v3, 1.f));
+                    *reinterpret_cast<float4 *>(t + j) = tv;
                 }
                 __syncwarp();
                 if (lane == 0) {
@@ -845,6 +1003,20 @@ cudaError_t launch_chain_init(int N, int C, int rule, uint64_t seed, uint32_t st
     return cudaGetLastError();
 }
 
+cudaError_t launch_sweep_pf(SweepK<float> P, int warp_bytes, cudaStream_t st) {
+    P.warp_bytes = warp_bytes;
+    int wpb = 4;
+    while (wpb > 1 && (size_t)wpb * warp_bytes > 227 * 1024) wpb >>= 1;
+    const size_t smem = (size_t)wpb * warp_bytes;
+    cudaError_t err = nk::allow_max_dynamic_smem((const void *)k_sweep_pf);
+    if (err != cudaSuccess) return err;
+    const unsigned grid = (unsigned)((P.a.C + wpb - 1) / wpb);
+    const int slot = prof_begin(NK_PROF_SWEEP, st);
+    (k_sweep_pf<<<grid, 32 * wpb, smem, st>>>(P), nk::note_launch());
+    prof_end(slot, st, (double)P.a.C * (P.a.n_discard + P.a.n_samples) * P.t.N * (double)P.t.M);
+    return cudaGetLastError();
+}
+
 template <typename R>
 cudaError_t launch_sweep(const Tables<R> &t, const SweepArgs &a, cudaStream_t st) {
     if (a.C <= 0 || a.n_discard + a.n_samples <= 0) return cudaSuccess;
@@ -862,6 +1034,13 @@ cudaError_t launch_sweep(const Tables<R> &t, const SweepArgs &a, cudaStream_t st
     P.t_bytes = align16<R>(t.M * (int)sizeof(R));
     P.warp_bytes = P.t_bytes + align16<R>(t.N);
     P.vec4 = sizeof(R) == 4 && (t.M % 4) == 0;
+    // FP32 local and exchange rules: the prefetching kernel, when two more
+    // rows per warp fit in shared memory
+    if constexpr (sizeof(R) == 4) {
+        const size_t pf_bytes = 3 * (size_t)P.t_bytes + align16<R>(t.N);
+        if (P.vec4 && a.rule != NK_RULE_HAMILTONIAN && pf_bytes <= 227 * 1024)
+            return launch_sweep_pf(P, (int)pf_bytes, st);
+    }
     int wpb = 4;
     while (wpb > 1 && (size_t)wpb * P.warp_bytes > 200 * 1024) wpb >>= 1;
     size_t smem = (size_t)wpb * P.warp_bytes;
