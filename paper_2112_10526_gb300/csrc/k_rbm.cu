@@ -249,21 +249,51 @@ __device__ __forceinline__ Prod<float> unit_lanes_product<float>(const float *t,
     return vec4 ? lane_product4(t, tau, si, lane, M) : strided_product<float>(t, tau, 1, si, lane, 32, M);
 }
 
-// Asynchronous 16-byte global -> shared copies (cp.async, cache-global): a
-// lane copies the float4 chunks j = 4 lane + 128 u of a row, the same chunks
-// lane_product4 reads, so that each lane waits only for its own copies.
-__device__ __forceinline__ void copy_row_async(float *dst, const float *src, int lane, int M) {
-    for (int j = 4 * lane; j < M; j += 128) {
-        const unsigned d = (unsigned)__cvta_generic_to_shared(dst + j);
-        const size_t g = __cvta_generic_to_global(src + j);
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(g) : "memory");
+// lane_product4 on a tau row already held in registers: uv[u] is the chunk j
+// = 4 lane + 128 u (zero past M).  The groups, renormalisations and tail are
+// those of lane_product4, in the same order, so the result is identical; only
+// the loads are gone (the caller issues all of them at once, one L2 round
+// trip per row instead of one per group of four).
+template <int kC>
+__device__ __forceinline__ Prod<float> lane_product4_regs(const float *__restrict__ t, const float4 (&uv)[kC],
+                                                          float si, int lane, int M) {
+    float m0 = 1.f, m1 = 1.f;
+    int e = 0;
+    int j = 4 * lane, G = 0;
+#pragma unroll
+    for (int g = 0; g < kC / 4; ++g) {
+        if (j + 3 * 128 < M) {
+            float4 tv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) tv[u] = *reinterpret_cast<const float4 *>(t + j + u * 128);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float4 w = uv[4 * g + u];
+                m0 *= fmaf(-si * tv[u].x, w.x, 1.f) * fmaf(-si * tv[u].y, w.y, 1.f);
+                m1 *= fmaf(-si * tv[u].z, w.z, 1.f) * fmaf(-si * tv[u].w, w.w, 1.f);
+            }
+            int k0, k1;
+            m0 = frexpf(m0, &k0);
+            m1 = frexpf(m1, &k1);
+            e += k0 + k1;
+            j += 4 * 128;
+            ++G;
+        }
     }
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-// Waits until at most n of this thread's copy groups are still in flight.
-template <int n>
-__device__ __forceinline__ void copy_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(n) : "memory");
+#pragma unroll
+    for (int u = 0; u < kC; ++u) {
+        if (u >= 4 * G && 4 * lane + 128 * u < M) {
+            const float4 tv = *reinterpret_cast<const float4 *>(t + 4 * lane + 128 * u);
+            const float4 w = uv[u];
+            m0 *= fmaf(-si * tv.x, w.x, 1.f) * fmaf(-si * tv.y, w.y, 1.f);
+            m1 *= fmaf(-si * tv.z, w.z, 1.f) * fmaf(-si * tv.w, w.w, 1.f);
+        }
+    }
+    Prod<float> p{m0, e};
+    renorm(p);
+    p.m *= m1;
+    renorm(p);
+    return p;
 }
 
 // ------------------------------------------------------------------ sweep ---
@@ -498,17 +528,16 @@ __global__ void __launch_bounds__(128) k_sweep(SweepK<R> P) {
     if (lane == 0 && A.n_accepted) A.n_accepted[c] += acc;
 }
 
-// FP32 sweeps of the local and exchange rules with the flip-ratio row of the
-// next proposal prefetched.  The site (local) or edge (exchange) of every
-// proposal comes from its Philox block alone, not from the chain state, so
-// while proposal q is evaluated from one shared-memory buffer, the tau row of
-// proposal q + 1 streams into the other (cp.async); the rows of a large M
-// (18 KB at M = 4608) otherwise arrive from L2 one dependent batch of loads
-// at a time.  The arithmetic and the order of every product are those of
-// k_sweep<float, false>, so the decisions are identical.  Proposals are drawn
-// 32 at a time, one per lane; the first of each batch is fetched without
-// overlap.  Shared memory per warp: t [M], two rows [M], spins [N].
-__global__ void __launch_bounds__(128) k_sweep_pf(SweepK<float> P) {
+// FP32 sweeps of the local and exchange rules with the flip-ratio row of a
+// proposal held in registers: every lane issues the loads of all its kC
+// chunks of the row at once, so a proposal waits for one L2 round trip
+// (k_sweep<float, false> waits for one per group of four chunks: nine at M =
+// 4608).  The accepted move's update of t reuses the registers.  The
+// arithmetic and the order of every product are those of
+// k_sweep<float, false>, so the decisions are identical.  Needs M % 4 == 0 and
+// M <= 128 kC.
+template <int kC>
+__global__ void __launch_bounds__(128) k_sweep_rows(SweepK<float> P) {
     extern __shared__ __align__(16) unsigned char sm[];
     const Tables<float> &T = P.t;
     const SweepArgs &A = P.a;
@@ -518,9 +547,7 @@ __global__ void __launch_bounds__(128) k_sweep_pf(SweepK<float> P) {
     const int N = T.N, M = T.M;
     unsigned char *base = sm + (size_t)warp * P.warp_bytes;
     float *t = reinterpret_cast<float *>(base);
-    float *buf0 = reinterpret_cast<float *>(base + P.t_bytes);
-    float *buf1 = reinterpret_cast<float *>(base + 2 * (size_t)P.t_bytes);
-    int8_t *sv = reinterpret_cast<int8_t *>(base + 3 * (size_t)P.t_bytes);
+    int8_t *sv = reinterpret_cast<int8_t *>(base + P.t_bytes);
     const bool local = A.rule == NK_RULE_LOCAL;
     const float *tab = local ? T.tau_site : T.tau_edge;
     for (int i = lane; i < N; i += 32) sv[i] = A.s[(size_t)c * N + i];
@@ -576,16 +603,6 @@ __global__ void __launch_bounds__(128) k_sweep_pf(SweepK<float> P) {
             const float K = __shfl_sync(kFull, b_K, src), aa = __shfl_sync(kFull, b_aa, src);
             const float lu = __shfl_sync(kFull, b_lu, src);
             const int ok = __shfl_sync(kFull, b_ok, src);
-            float *cur = (q & 1) ? buf1 : buf0;
-            if (src == 0) copy_row_async(cur, tab + (size_t)row * M, lane, M);  // not prefetched
-            if (src + 1 < 32 && q + 1 < N) {
-                const int nrow = __shfl_sync(kFull, b_row, src + 1);
-                copy_row_async((q & 1) ? buf0 : buf1, tab + (size_t)nrow * M, lane, M);
-                copy_wait<1>();  // this proposal's row has landed; the next one is in flight
-            } else {
-                copy_wait<0>();
-            }
-            __syncwarp();
             const size_t slot = ((size_t)c * A.dec_stride + A.dec_offset + w) * N + q;
             if (!local && (!ok || sv[i] == sv[k])) {
                 if (lane == 0 && A.decisions) A.decisions[slot] = 2;
@@ -593,16 +610,25 @@ __global__ void __launch_bounds__(128) k_sweep_pf(SweepK<float> P) {
             }
             const float d0 = -2.f * aa * (float)sv[i];
             const float si = (float)sv[i];
-            Prod<float> pr = lane_product4<true>(t, cur, si, lane, M);
+            float4 uv[kC];
+            const float *row_p = tab + (size_t)row * M;
+#pragma unroll
+            for (int u = 0; u < kC; ++u) {
+                const int j = 4 * lane + 128 * u;
+                uv[u] = j < M ? __ldg(reinterpret_cast<const float4 *>(row_p + j)) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            Prod<float> pr = lane_product4_regs<kC>(t, uv, si, lane, M);
             pr = warp_prod_normalised(pr);
             const float delta = d0 + (K + prod_log(pr));
             const bool accept = lu < 2.f * delta;
             if (lane == 0 && A.decisions) A.decisions[slot] = accept ? 1 : 0;
             if (accept) {
-                for (int j = 4 * lane; j < M; j += 128) {
+#pragma unroll
+                for (int u = 0; u < kC; ++u) {
+                    const int j = 4 * lane + 128 * u;
+                    if (j >= M) continue;
                     float4 tv = *reinterpret_cast<const float4 *>(t + j);
-                    const float4 uv = *reinterpret_cast<const float4 *>(cur + j);
-                    const float v0 = si * uv.x, v1 = si * uv.y, v2 = si * uv.z, v3 = si * uv.w;
+                    const float v0 = si * uv[u].x, v1 = si * uv[u].y, v2 = si * uv[u].z, v3 = si * uv[u].w;
                     tv.x = __fdividef(tv.x - v0, fmaf(-tv.x, v0, 1.f));
                     tv.y = __fdividef(tv.y - v1, fmaf(-tv.y, v1, 1.f));
                     tv.z = __fdividef(tv.z - v2, fmaf(-tv.z, v2, 1.f));
@@ -1003,18 +1029,31 @@ cudaError_t launch_chain_init(int N, int C, int rule, uint64_t seed, uint32_t st
     return cudaGetLastError();
 }
 
-cudaError_t launch_sweep_pf(SweepK<float> P, int warp_bytes, cudaStream_t st) {
-    P.warp_bytes = warp_bytes;
+// The register-row sweep for kC chunks of 128 floats per lane.
+template <int kC>
+cudaError_t launch_sweep_rows_kc(const SweepK<float> &P, cudaStream_t st) {
     int wpb = 4;
-    while (wpb > 1 && (size_t)wpb * warp_bytes > 227 * 1024) wpb >>= 1;
-    const size_t smem = (size_t)wpb * warp_bytes;
-    cudaError_t err = nk::allow_max_dynamic_smem((const void *)k_sweep_pf);
+    while (wpb > 1 && (size_t)wpb * P.warp_bytes > 200 * 1024) wpb >>= 1;
+    const size_t smem = (size_t)wpb * P.warp_bytes;
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
+    cudaError_t err = nk::allow_max_dynamic_smem((const void *)k_sweep_rows<kC>);
     if (err != cudaSuccess) return err;
     const unsigned grid = (unsigned)((P.a.C + wpb - 1) / wpb);
     const int slot = prof_begin(NK_PROF_SWEEP, st);
-    (k_sweep_pf<<<grid, 32 * wpb, smem, st>>>(P), nk::note_launch());
+    (k_sweep_rows<kC><<<grid, 32 * wpb, smem, st>>>(P), nk::note_launch());
     prof_end(slot, st, (double)P.a.C * (P.a.n_discard + P.a.n_samples) * P.t.N * (double)P.t.M);
     return cudaGetLastError();
+}
+
+// FP32 local and exchange rules with M % 4 == 0 and M <= 4608: the
+// register-row kernel with the smallest chunk count that holds a row (36
+// chunks take 254 registers a thread, no spills).
+cudaError_t launch_sweep_rows(const SweepK<float> &P, cudaStream_t st) {
+    const int M = P.t.M;
+    if (M <= 512) return launch_sweep_rows_kc<4>(P, st);
+    if (M <= 1024) return launch_sweep_rows_kc<8>(P, st);
+    if (M <= 2048) return launch_sweep_rows_kc<16>(P, st);
+    return launch_sweep_rows_kc<36>(P, st);
 }
 
 template <typename R>
@@ -1037,9 +1076,7 @@ cudaError_t launch_sweep(const Tables<R> &t, const SweepArgs &a, cudaStream_t st
     // FP32 local and exchange rules: the prefetching kernel, when two more
     // rows per warp fit in shared memory
     if constexpr (sizeof(R) == 4) {
-        const size_t pf_bytes = 3 * (size_t)P.t_bytes + align16<R>(t.N);
-        if (P.vec4 && a.rule != NK_RULE_HAMILTONIAN && pf_bytes <= 227 * 1024)
-            return launch_sweep_pf(P, (int)pf_bytes, st);
+        if (P.vec4 && a.rule != NK_RULE_HAMILTONIAN && t.M <= 36 * 128) return launch_sweep_rows(P, st);
     }
     int wpb = 4;
     while (wpb > 1 && (size_t)wpb * P.warp_bytes > 200 * 1024) wpb >>= 1;
