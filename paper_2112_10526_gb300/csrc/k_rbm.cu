@@ -1045,16 +1045,13 @@ cudaError_t launch_sweep_rows_kc(const SweepK<float> &P, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-// FP32 local and exchange rules with M % 4 == 0 and M <= 4608: the
-// register-row kernel with the smallest chunk count that holds a row (36
-// chunks take 254 registers a thread, no spills).
-cudaError_t launch_sweep_rows(const SweepK<float> &P, cudaStream_t st) {
-    const int M = P.t.M;
-    if (M <= 512) return launch_sweep_rows_kc<4>(P, st);
-    if (M <= 1024) return launch_sweep_rows_kc<8>(P, st);
-    if (M <= 2048) return launch_sweep_rows_kc<16>(P, st);
-    return launch_sweep_rows_kc<36>(P, st);
-}
+// FP32 local and exchange rules with M % 4 == 0 and M <= 512: the
+// register-row kernel (4 chunks a lane, 72 registers, the occupancy of
+// k_sweep).  Measured on GB300: 0.62 against 0.71 ms a step at M = 200; at
+// M = 1600 (16 chunks, 161 registers) and M = 4608 (36 chunks, 254
+// registers) the larger register footprint made it slower than k_sweep
+// (10.9 against 8.4 ms, 140 against 125 ms), so those sizes keep k_sweep.
+cudaError_t launch_sweep_rows(const SweepK<float> &P, cudaStream_t st) { return launch_sweep_rows_kc<4>(P, st); }
 
 template <typename R>
 cudaError_t launch_sweep(const Tables<R> &t, const SweepArgs &a, cudaStream_t st) {
@@ -1076,7 +1073,7 @@ cudaError_t launch_sweep(const Tables<R> &t, const SweepArgs &a, cudaStream_t st
     // FP32 local and exchange rules: the prefetching kernel, when two more
     // rows per warp fit in shared memory
     if constexpr (sizeof(R) == 4) {
-        if (P.vec4 && a.rule != NK_RULE_HAMILTONIAN && t.M <= 36 * 128) return launch_sweep_rows(P, st);
+        if (P.vec4 && a.rule != NK_RULE_HAMILTONIAN && t.M <= 4 * 128) return launch_sweep_rows(P, st);
     }
     int wpb = 4;
     while (wpb > 1 && (size_t)wpb * P.warp_bytes > 200 * 1024) wpb >>= 1;
