@@ -78,6 +78,8 @@ def parse():
     ap.add_argument("--chains", type=int, default=0,
                     help="override the workload's chain count (a smaller case of the same kernels, for profilers)")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--tdvp", default="tdvp_tfim1d_l20",
+                    help="t-VMC workload added to the line (none: skip)")
     ap.add_argument("--serve", type=int, default=512,
                     help="requests of the serving run added to the line (0: none)")
     ap.add_argument("--serve-slots", type=int, default=8)
@@ -587,6 +589,49 @@ def run_ours(args, rank, world):
     return line
 
 
+# ------------------------------------------------------------------ t-VMC ----
+
+def run_tdvp(name, K, warmup, dev):
+    """Time evolution of the complex RBM: K t-VMC steps (nk_tdvp_step, two
+    slopes each for Heun) after `warmup` steps; CUDA events on the stream."""
+    import numpy as np
+    import torch
+    from paper_2112_10526_gb300 import inputs as I
+    from paper_2112_10526_gb300 import nk
+    w = dict(I.TDVP_WORKLOADS[name])
+    N, M, C = w["N"], w["alpha"] * w["N"], w["chains"]
+    ham = w["ham"]()
+    params = torch.from_numpy(I.complex_rbm_params(N, M, w["seed"], w["sigma"])).to(dev)
+    edges = torch.from_numpy(ham["edges"]).to(dev)
+    h = nk.make_ham(ham["kind"], ham["J"], ham.get("h", 0.0), ham.get("marshall", False), edges)
+    s = torch.from_numpy(I.random_configs(C, N, w["seed"])).to(dev)
+    ch = nk.make_chains(s)
+    cfg = nk.make_tdvp_cfg(w["rule"], w["integrator"], w["real_time"], w["solver"], w["discard"], w["per_chain"],
+                           w["dt"], w["diag_shift"], w["seed"], rcond=w["rcond"])
+    stats = torch.empty(4, dtype=torch.float64, device=dev)
+    with nk.Ctx(dev.index) as ctx:
+        for i in range(max(1, warmup)):
+            nk.nk_tdvp_step(ctx, params, N, M, h, ch, cfg, stats)
+            cfg.n_discard = 0
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(K):
+            nk.nk_tdvp_step(ctx, params, N, M, h, ch, cfg, stats)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+    st = stats.cpu().numpy()
+    Ns = C * w["per_chain"]
+    return {"value": K / (ms / 1e3), "unit": "t-VMC steps/s", "ms_per_step": ms / K, "steps": K,
+            "energy": complex(st[0], st[1]).real, "energy_imag": float(st[1]), "energy_error": float(st[3]),
+            "config": {"workload": name, "lattice": lattice_text(N), "hamiltonian": "tfim (h = 1 quench)",
+                       "model": "complex RBM, alpha = 1", "N": N, "M": M, "Np_complex": N + M + M * N,
+                       "chains": C, "samples_per_chain": w["per_chain"], "Ns": Ns, "integrator": w["integrator"],
+                       "dt": w["dt"], "time": "real", "solver": f"pseudo-inverse (rcond {w['rcond']:g}), "
+                       f"Jacobi on the {2 * (N + M + M * N)}-dim real embedding", "precision": "f64"}}
+
+
 # ---------------------------------------------------------------- serving ----
 
 def run_serve(n_requests, slots, budget_gb, device=0):
@@ -688,6 +733,10 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     line = run_ours(args, rank, world)
     line["cpu_baseline"] = cpu
+    if args.tdvp and args.tdvp != "none" and world == 1:
+        import torch
+        line["tdvp"] = run_tdvp(args.tdvp, args.steps, args.warmup,
+                                torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0"))))
     if args.serve > 0 and world == 1:
         line["serve"] = run_serve(args.serve, args.serve_slots, args.serve_budget_gb,
                                   int(os.environ.get("LOCAL_RANK", "0")))

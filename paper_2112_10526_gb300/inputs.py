@@ -151,6 +151,29 @@ WORKLOADS = {
 }
 
 
+# Sec. 9 (unitary dynamics): the quench of the periodic transverse-field
+# Ising chain L = 20 to h = 1 with a complex RBM, alpha = 1, 4096 samples,
+# the local rule and the Heun scheme; the truncated pseudo-inverse solves
+# Eq. eq:tvmc (the default SVD-based solver of the time-evolution driver,
+# eps = 0).  The paper starts from an optimised ground state; here the
+# parameters are seeded: complex, real and imaginary parts N(0, sigma^2).
+TDVP_WORKLOADS = {
+    "tdvp_tfim1d_l20": dict(N=20, alpha=1, ham=lambda: tfim_chain(20, 1.0, 1.0), rule="local", chains=1024,
+                            per_chain=4, discard=16, seed=8, sigma=0.05, dt=0.01, integrator="heun", real_time=True,
+                            solver="svd", rcond=1e-12, diag_shift=0.0),
+}
+
+
+def complex_rbm_params(N: int, M: int, seed: int, sigma: float = 0.01) -> np.ndarray:
+    """Complex RBM parameters [a (N); b (M); W (M x N)]: real parts, then
+    imaginary parts, i.i.d. N(0, sigma^2) from default_rng(seed)."""
+    rng = np.random.default_rng(seed)
+    n = N + M + M * N
+    re = rng.normal(0.0, sigma, n)
+    im = rng.normal(0.0, sigma, n)
+    return re + 1j * im
+
+
 def serve_requests(n: int = 512, seed: int = 4) -> list:
     """Seeded serving mix (each request: local-energy expectation + one SR
     step): lattice uniform over the periodic Ising chains N in {16, 32, 64,
