@@ -572,6 +572,15 @@ def run_ours(args, rank, world):
                                  "energy": s2["energy"], "energy_error": s2["error"],
                                  "cg_iters": s2["cg_iters"], "clocks": r2["clocks"],
                                  "config": workload_config(w, other, world)}
+        # the energies of both precisions after the same 1 + Kc steps from the
+        # same parameters, chains and Philox streams
+        r3 = measure(w, args.precision, Kc, 1, rank, world, dev, prof=False, e2e=False)
+        s3 = r3["stats"]
+        line["energy_after_equal_steps"] = {
+            "steps": 1 + Kc, args.precision: {"energy": s3["energy"], "error": s3["error"]},
+            other: {"energy": s2["energy"], "error": s2["error"]},
+            "difference_in_combined_errors": abs(s3["energy"] - s2["energy"]) /
+            max(1e-300, (s3["error"] ** 2 + s2["error"] ** 2) ** 0.5)}
     extra = {}
     for name in [x for x in args.extra.split(",") if x and x != "none"] if world == 1 else []:
         we = workload(name)
