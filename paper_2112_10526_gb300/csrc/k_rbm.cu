@@ -803,6 +803,7 @@ __global__ void __launch_bounds__(kEW * 32) k_eloc_batched(ElocBK P) {
     int8_t *sv = reinterpret_cast<int8_t *>(sm + (size_t)kEG * P.t_ld * 4);      // [kEG][s_ld]
     double *part = reinterpret_cast<double *>(sm + (size_t)kEG * P.t_ld * 4 + (size_t)kEG * P.s_ld);  // [kEW][kEG]
     double *diag = part + kEW * kEG;                                              // [kEG]
+    float *offw = reinterpret_cast<float *>(diag + kEG);                          // [kEW][kEG]
     for (int x = threadIdx.x; x < kEG * N; x += blockDim.x) {
         const int g = x / N, i = x % N;
         sv[g * P.s_ld + i] = g < G ? A.s[(size_t)(k0 + g) * N + i] : (int8_t)1;
@@ -833,9 +834,8 @@ __global__ void __launch_bounds__(kEW * 32) k_eloc_batched(ElocBK P) {
     // FP32 path: ratios, exponentials and the per-warp partial sums in FP32
     // lanes (each warp adds about nconn / kEW terms); the diagonal part and
     // the final sum stay in FP64.
-    float off[kEG];
-#pragma unroll
-    for (int g = 0; g < kEG; ++g) off[g] = 0.f;
+    if (lane < kEG) offw[warp * kEG + lane] = 0.f;
+    __syncwarp();
     const bool tfim = A.kind == NK_TFIM;
     const int nconn = tfim ? N : E;
     const float hoff = (float)(A.marshall ? -2.0 * A.J : 2.0 * A.J), hoff2 = (float)(2.0 * A.J2),
@@ -862,14 +862,25 @@ __global__ void __launch_bounds__(kEW * 32) k_eloc_batched(ElocBK P) {
         for (int g = 0; g < kEG; ++g)
             if (g < G && (tfim || sv[g * P.s_ld + i] != sv[g * P.s_ld + kk])) active |= 1u << g;
         if (!active) continue;
+        // The active samples of this connection as slots 0 .. cnt - 1 (in
+        // increasing sample order, so every product is formed as before):
+        // the loops below stop at cnt, so inactive samples cost nothing.
+        const int cnt = __popc(active);
         float m[kEG];
         int ex[kEG];
         float sg[kEG];
+        const float *tg[kEG];
+        int gs[kEG];
+        unsigned rest = active;
 #pragma unroll
-        for (int g = 0; g < kEG; ++g) {
-            m[g] = 1.f;
-            ex[g] = 0;
-            sg[g] = (float)sv[g * P.s_ld + i];
+        for (int q = 0; q < kEG; ++q) {
+            const int g = rest ? __ffs(rest) - 1 : 0;
+            rest &= rest - 1u;
+            gs[q] = g;
+            m[q] = 1.f;
+            ex[q] = 0;
+            sg[q] = (float)sv[g * P.s_ld + i];
+            tg[q] = t + (size_t)g * P.t_ld;
         }
         // This lane's units j = 4 lane + 128 it, it = j >> 7: the tau loads
         // of kU iterations are issued together (the row comes from L2), and
@@ -885,36 +896,41 @@ __global__ void __launch_bounds__(kEW * 32) k_eloc_batched(ElocBK P) {
                 const int j = j0 + u * 128;
                 if (j >= M) break;
 #pragma unroll
-                for (int g = 0; g < kEG; ++g) {
-                    if (!(active & (1u << g))) continue;
-                    const float4 tv = *reinterpret_cast<const float4 *>(t + g * P.t_ld + j);
-                    const float ns = -sg[g];
-                    m[g] *= fmaf(ns * tv.x, uv[u].x, 1.f) * fmaf(ns * tv.y, uv[u].y, 1.f) *
+                for (int q = 0; q < kEG; ++q) {
+                    if (q >= cnt) break;
+                    const float4 tv = *reinterpret_cast<const float4 *>(tg[q] + j);
+                    const float ns = -sg[q];
+                    m[q] *= fmaf(ns * tv.x, uv[u].x, 1.f) * fmaf(ns * tv.y, uv[u].y, 1.f) *
                             fmaf(ns * tv.z, uv[u].z, 1.f) * fmaf(ns * tv.w, uv[u].w, 1.f);
                 }
                 if ((j >> 7) & 1) {
 #pragma unroll
-                    for (int g = 0; g < kEG; ++g) {
+                    for (int q = 0; q < kEG; ++q) {
+                        if (q >= cnt) break;
                         int k;
-                        m[g] = frexpf(m[g], &k);
-                        ex[g] += k;
+                        m[q] = frexpf(m[q], &k);
+                        ex[q] += k;
                     }
                 }
             }
         }
 #pragma unroll
-        for (int g = 0; g < kEG; ++g) {
-            if (!(active & (1u << g))) continue;
-            Prod<float> p{m[g], ex[g]};
+        for (int q = 0; q < kEG; ++q) {
+            if (q >= cnt) break;
+            Prod<float> p{m[q], ex[q]};
             renorm(p);
             p = warp_prod_normalised(p);
-            const float delta = -2.f * aa * sg[g] + (K + prod_log(p));
-            off[g] = fmaf(tfim ? hfield : (c < E1 ? hoff : hoff2), expf(delta), off[g]);
+            const float delta = -2.f * aa * sg[q] + (K + prod_log(p));
+            if (lane == 0) {
+                float &o = offw[warp * kEG + gs[q]];
+                o = fmaf(tfim ? hfield : (c < E1 ? hoff : hoff2), expf(delta), o);
+            }
         }
     }
+    __syncwarp();
     if (lane == 0) {
 #pragma unroll
-        for (int g = 0; g < kEG; ++g) part[warp * kEG + g] = (double)off[g];
+        for (int g = 0; g < kEG; ++g) part[warp * kEG + g] = (double)offw[warp * kEG + g];
     }
     __syncthreads();
     if (threadIdx.x < G) {
@@ -1098,7 +1114,7 @@ template cudaError_t launch_sweep<float>(const Tables<float> &, const SweepArgs 
 
 size_t eloc_batched_smem(int N, int M) {
     const size_t t_ld = (size_t)(M + 3) / 4 * 4, s_ld = (size_t)(N + 15) / 16 * 16;
-    return (size_t)kEG * t_ld * 4 + (size_t)kEG * s_ld + (size_t)(kEW * kEG + kEG) * 8;
+    return (size_t)kEG * t_ld * 4 + (size_t)kEG * s_ld + (size_t)(kEW * kEG + kEG) * 8 + (size_t)kEW * kEG * 4;
 }
 
 template <typename R>
