@@ -412,6 +412,33 @@ __global__ void k_tg_colexp(const double *__restrict__ T, const int *__restrict_
     }
 }
 
+// max over k of ge[k] (-100000 marks zero): one block.
+__global__ void k_max_exp(int64_t n, const int *__restrict__ ge, int *__restrict__ out) {
+    __shared__ int red[32];
+    int m = -100000;
+    for (int64_t k = threadIdx.x; k < n; k += blockDim.x) m = max(m, ge[k]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : -100000;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, off));
+        if (threadIdx.x == 0) *out = v;
+    }
+}
+
+// Column exponents of T' o g' from the bound max_k |t'_kj| max_k |g'_k|:
+// expo[j] = colexpT[j] + gmax (an upper bound of the per-entry exponents).
+__global__ void k_colexp_bound(int M, const int *__restrict__ colexpT, const int *__restrict__ gmax,
+                               int *__restrict__ expo) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j > M) return;
+    const int a = colexpT[j], b = *gmax;
+    expo[j] = (a == -100000 || b == -100000) ? -100000 : a + b;
+}
+
 // (T' o g')^T sliced: out [SB][M+1][ld], row j, column k, through tiles of
 // 64 k x 32 j (ld is even: each lane writes a BF16 pair per plane).
 __global__ void k_tg_slice(const double *__restrict__ T, const double *__restrict__ gp, int64_t Ns, int M, int SB,
@@ -613,15 +640,27 @@ constexpr int kMaxKSplit = 8;
 size_t tc_vjp_ws_bytes(int N, int M, int64_t Ns) {
     const int64_t ld = pad8(Ns);
     return ((size_t)(N + 1) * ld * 2 + 255) / 256 * 256 + ((size_t)kMaxSB * (M + 1) * ld * 2 + 255) / 256 * 256 +
-           ((size_t)(M + 1) * 4 + 255) / 256 * 256 +
+           ((size_t)(M + 2) * 4 + 255) / 256 * 256 +
            ((size_t)kMaxKSplit * (N + 1) * (M + 1) * 8 + 255) / 256 * 256 + ((size_t)Ns * 8 + 255) / 256 * 256 +
            ((size_t)Ns * 4 + 255) / 256 * 256 + 256;
 }
 
 // out = J^T g' with g' = scale (g - shift), (T' o g')^T cut into SB slices.
+size_t tc_colexp_ws_bytes(int M, int64_t Ns) { return ((size_t)Ns * 4 + 255) / 256 * 256 + (size_t)(M + 1) * 4; }
+
+// colexpT[j] = exponent of max_k |t'_kj| (t'_kM = 1), once per T.
+cudaError_t launch_colexp_t(int M, int64_t Ns, const double *T, int *colexpT, void *ws, cudaStream_t st) {
+    int *zero = static_cast<int *>(ws);
+    (k_fill_int<<<nblk(Ns, 256), 256, 0, st>>>(Ns, 0, zero), nk::note_launch());
+    (k_fill_int<<<nblk(M + 1, 256), 256, 0, st>>>(M + 1, -100000, colexpT), nk::note_launch());
+    (k_tg_colexp<<<dim3(nblk(M + 1, 32), nblk(Ns, 256)), dim3(32, 8), 0, st>>>(T, zero, Ns, M, colexpT),
+     nk::note_launch());
+    return cudaGetLastError();
+}
+
 cudaError_t launch_vjp_tc(int N, int M, int64_t Ns, const int8_t *s, const double *T, const double *g,
                           double scale, const double *shift, double *out, int SB, int *err, void *ws,
-                          cudaStream_t st) {
+                          cudaStream_t st, const int *colexpT) {
     const int64_t ld = pad8(Ns);
     char *p = static_cast<char *>(ws);
     auto take = [&](size_t bytes) {
@@ -631,16 +670,22 @@ cudaError_t launch_vjp_tc(int N, int M, int64_t Ns, const int8_t *s, const doubl
     };
     auto *St = reinterpret_cast<__nv_bfloat16 *>(take((size_t)(N + 1) * ld * 2));
     auto *Gs = reinterpret_cast<__nv_bfloat16 *>(take((size_t)kMaxSB * (M + 1) * ld * 2));
-    auto *eg = reinterpret_cast<int *>(take((size_t)(M + 1) * 4));
+    auto *eg = reinterpret_cast<int *>(take((size_t)(M + 2) * 4));
     auto *PT = reinterpret_cast<double *>(take((size_t)kMaxKSplit * (N + 1) * (M + 1) * 8));
     auto *gp = reinterpret_cast<double *>(take((size_t)Ns * 8));
     auto *ge = reinterpret_cast<int *>(take((size_t)Ns * 4));
     dim3 tb(32, 8);
     (k_pm1_cols<<<dim3(nblk(ld, 32), nblk(N + 1, 32)), tb, 0, st>>>(s, Ns, N, ld, St), nk::note_launch());
-    (k_fill_int<<<nblk(M + 1, 256), 256, 0, st>>>(M + 1, -100000, eg), nk::note_launch());
     (k_scale_g<<<nblk(Ns, 256), 256, 0, st>>>(Ns, g, scale, shift, gp, ge), nk::note_launch());
-    (k_tg_colexp<<<dim3(nblk(M + 1, 32), nblk(Ns, 256)), dim3(32, 8), 0, st>>>(T, ge, Ns, M, eg),
-     nk::note_launch());
+    if (colexpT) {
+        // the column bound: no pass over T (eg[M + 1] holds max_k ge[k])
+        (k_max_exp<<<1, 1024, 0, st>>>(Ns, ge, eg + M + 1), nk::note_launch());
+        (k_colexp_bound<<<nblk(M + 1, 256), 256, 0, st>>>(M, colexpT, eg + M + 1, eg), nk::note_launch());
+    } else {
+        (k_fill_int<<<nblk(M + 1, 256), 256, 0, st>>>(M + 1, -100000, eg), nk::note_launch());
+        (k_tg_colexp<<<dim3(nblk(M + 1, 32), nblk(Ns, 256)), dim3(32, 8), 0, st>>>(T, ge, Ns, M, eg),
+         nk::note_launch());
+    }
     (k_tg_slice<<<dim3(nblk(ld, 64), nblk(M + 1, 32)), tb, 0, st>>>(T, gp, Ns, M, SB, ld, eg, Gs),
      nk::note_launch());
     // split the long K = Ns range until the grid covers the SMs twice

@@ -204,6 +204,8 @@ struct SolveWs {
     int *kept;
     void *tc;   // tensor-core slices and inverted diagonal blocks (NK_MIXED)
     void *tcm;  // tensor-core Jacobian-product workspace (NK_MIXED)
+    int *colexpT;     // NK_MIXED CG: column exponents of tanh(theta), [M + 1]
+    void *colexp_ws;
     int *tcerr; // sticky tensor-core error word of the context
 };
 
@@ -227,6 +229,10 @@ void carve_solve(Carver &c, SolveWs &w, int N, int M, int64_t Ns, int solver, in
         w.r = c.take<double>(Np);
         w.p = c.take<double>(Np);
         w.Ap = c.take<double>(Np);
+        if (precision == NK_MIXED) {
+            w.colexpT = c.take<int>(M + 1);
+            w.colexp_ws = c.take<char>(nk::tc_colexp_ws_bytes(M, Ns));
+        }
     } else if (solver == NK_SOLVER_CHOLESKY) {
         w.dJ = c.take<double>((size_t)Ns * Np);
         w.S = c.take<double>((size_t)Np * Np);
@@ -286,21 +292,23 @@ cudaError_t jvp_any(int N, int M, int64_t Ns, const int8_t *s, const double *T, 
 }
 
 cudaError_t vjp_any(int N, int M, int64_t Ns, const int8_t *s, const double *T, const double *g, double scale,
-                    const double *shift, SolveWs &w, double *out, int precision, int slices, cudaStream_t st) {
+                    const double *shift, SolveWs &w, double *out, int precision, int slices, cudaStream_t st,
+                    const int *colexpT = nullptr) {
     if (precision == NK_MIXED)
-        return nk::launch_vjp_tc(N, M, Ns, s, T, g, scale, shift, out, slices, w.tcerr, w.tcm, st);
+        return nk::launch_vjp_tc(N, M, Ns, s, T, g, scale, shift, out, slices, w.tcerr, w.tcm, st, colexpT);
     return nk::launch_vjp(N, M, Ns, s, T, g, scale, shift, w.partial, out, st);
 }
 
 // (G + eps I) v for the on-the-fly QGT (App. B.3).
+// NK_MIXED CG passes the column exponents of T (colexpT) for the J^T g slices.
 cudaError_t qgt_onthefly(int N, int M, int64_t Ns, const int8_t *s, const double *T,
                          const double *v, double eps, SolveWs &w, double *out, cudaStream_t st,
-                         int precision = NK_F64) {
+                         int precision = NK_F64, const int *colexpT = nullptr) {
     cudaError_t e = jvp_any(N, M, Ns, s, T, v, w, w.w, precision, kMatvecSlices, st);
     if (e != cudaSuccess) return e;
     e = nk::launch_center(Ns, w.w, w.dotp, 1.0 / (double)Ns, st);
     if (e != cudaSuccess) return e;
-    e = vjp_any(N, M, Ns, s, T, w.w, 1.0, nullptr, w, out, precision, kMatvecSlices, st);
+    e = vjp_any(N, M, Ns, s, T, w.w, 1.0, nullptr, w, out, precision, kMatvecSlices, st, colexpT);
     if (e != cudaSuccess) return e;
     return nk::launch_axpby(n_params(N, M), eps, v, 1.0, out, st);
 }
@@ -352,6 +360,7 @@ nk_status run_solve(nk_ctx *ctx, int N, int M, int64_t Ns, const int8_t *s, cons
     if (solver == NK_SOLVER_CG) {
         double *rr = w.sc, *rr_new = w.sc + 1, *pAp = w.sc + 2, *ff = w.sc + 3, *rr_keep = w.sc + 4;
         int *done = w.flags, *iters = w.flags + 1;
+        if (tc) NK_CU(nk::launch_colexp_t(M, Ns, T, w.colexpT, w.colexp_ws, st), "cg exponents");
         NK_CU(nk::launch_fill(Np, 0.0, w.x, st), "cg init");
         NK_CU(nk::launch_axpby(Np, 1.0, F, 0.0, w.r, st), "cg init");
         NK_CU(nk::launch_axpby(Np, 1.0, F, 0.0, w.p, st), "cg init");
@@ -361,7 +370,8 @@ nk_status run_solve(nk_ctx *ctx, int N, int M, int64_t Ns, const int8_t *s, cons
         int it = 0;
         bool converged = false;
         while (it < maxiter) {
-            NK_CU(qgt_onthefly(N, M, Ns, s, T, w.p, eps, w, w.Ap, st, precision), "cg matvec");
+            NK_CU(qgt_onthefly(N, M, Ns, s, T, w.p, eps, w, w.Ap, st, precision, tc ? w.colexpT : nullptr),
+                  "cg matvec");
             NK_CU(nk::launch_dot(Np, w.p, w.Ap, w.dotp, pAp, st), "cg dot");
             NK_CU(nk::launch_cg_update_xr(Np, rr_keep, pAp, w.p, w.Ap, w.x, w.r, done, st), "cg xr");
             NK_CU(nk::launch_dot(Np, w.r, w.r, w.dotp, rr_new, st), "cg dot");

@@ -217,9 +217,14 @@ size_t tc_jvp_ws_bytes(int N, int M, int64_t Ns);
 cudaError_t launch_jvp_tc(int N, int M, int64_t Ns, const int8_t *s, const double *T, const double *v,
                           double *out, int SB, int *err, void *ws, cudaStream_t st);
 size_t tc_vjp_ws_bytes(int N, int M, int64_t Ns);
+// colexpT (optional, [M + 1], from launch_colexp_t): the column exponents of
+// tanh(theta), so that the slices of (T' o g')^T take their exponents from
+// the bound max_k |t'_kj| max_k |g'_k| instead of a pass over T.
 cudaError_t launch_vjp_tc(int N, int M, int64_t Ns, const int8_t *s, const double *T, const double *g,
                           double scale, const double *shift, double *out, int SB, int *err, void *ws,
-                          cudaStream_t st);
+                          cudaStream_t st, const int *colexpT = nullptr);
+size_t tc_colexp_ws_bytes(int M, int64_t Ns);
+cudaError_t launch_colexp_t(int M, int64_t Ns, const double *T, int *colexpT, void *ws, cudaStream_t st);
 
 // vector helpers
 cudaError_t launch_axpby(int64_t n, double alpha, const double *x, double beta, double *y,
