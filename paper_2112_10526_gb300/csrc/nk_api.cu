@@ -326,25 +326,18 @@ nk_status check_factor(nk_ctx *ctx, const int *info, cudaStream_t st) {
 
 // Cyclic Jacobi sweeps on the full symmetric K [n][n] (diagonalised in
 // place; V <- V J from the identity) until the relative off-diagonal norm is
-// at the rounding level or kMaxJacobiSweeps; reads the norms back once per
-// sweep.  norms: 2 device doubles of scratch.
+// at the rounding level or kMaxJacobiSweeps: one cooperative launch, whose
+// sweep count and final norm are read back once (synchronises the stream).
+// norms: 2 device doubles of scratch.
 nk_status jacobi_eigen(nk_ctx *ctx, double *K, double *V, int64_t n, void *eig_ws, double *norms, cudaStream_t st,
                        int *sweeps_out, double *rel_out) {
     NK_CU(nk::launch_symmetrize_lower(n, K, st), "eig");
     NK_CU(nk::launch_identity(n, V, st), "eig");
-    int sweeps = 0;
-    double rel = 0.0;
-    for (; sweeps <= kMaxJacobiSweeps; ++sweeps) {
-        NK_CU(nk::launch_offdiag_norms(K, n, eig_ws, norms, st), "eig norms");
-        NK_CU(cudaMemcpyAsync(ctx->host_vals, norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, st), "eig norms");
-        NK_CU(cudaStreamSynchronize(st), "eig norms");
-        const double off = ctx->host_vals[0], tot = ctx->host_vals[0] + ctx->host_vals[1];
-        rel = tot > 0.0 ? std::sqrt(off / tot) : 0.0;
-        if (rel <= kJacobiTol || sweeps == kMaxJacobiSweeps) break;
-        NK_CU(nk::launch_jacobi_sweep(K, V, n, eig_ws, st), "eig sweep");
-    }
-    *sweeps_out = sweeps;
-    *rel_out = rel;
+    NK_CU(nk::launch_jacobi_coop(K, V, n, kMaxJacobiSweeps, kJacobiTol, eig_ws, norms, st), "eig sweeps");
+    NK_CU(cudaMemcpyAsync(ctx->host_vals, norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, st), "eig sweeps");
+    NK_CU(cudaStreamSynchronize(st), "eig sweeps");
+    *sweeps_out = (int)ctx->host_vals[0];
+    *rel_out = ctx->host_vals[1];
     return NK_OK;
 }
 

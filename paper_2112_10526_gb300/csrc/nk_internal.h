@@ -259,14 +259,15 @@ cudaError_t launch_sub_colmean(int64_t rows, int64_t cols, const double *mean, d
 // Symmetric eigensolver (k_eig.cu): cyclic two-sided Jacobi sweeps with the
 // round-robin parallel ordering on a full symmetric A [n][n] (diagonalised
 // in place) and V [n][n] (V <- V J; start from the identity: columns are the
-// eigenvectors); ws of eig_ws_bytes(n).  out2 = (sum of squares off the
-// diagonal, on it).  w = diag A, wmax = max w.  The filter: z_k <- z_k /
+// eigenvectors); ws of eig_ws_bytes(n).  w = diag A, wmax = max w.  The filter: z_k <- z_k /
 // w_k^power for w_k > rcond wmax, else 0; kept counts the kept ones.
 size_t eig_ws_bytes(int64_t n);
 cudaError_t launch_symmetrize_lower(int64_t n, double *A, cudaStream_t st);
 cudaError_t launch_identity(int64_t n, double *V, cudaStream_t st);
-cudaError_t launch_jacobi_sweep(double *A, double *V, int64_t n, void *ws, cudaStream_t st);
-cudaError_t launch_offdiag_norms(const double *A, int64_t n, void *ws, double *out2, cudaStream_t st);
+// All sweeps in one cooperative launch, until the relative off-diagonal
+// norm is <= tol or max_sweeps; out2 = (sweeps taken, final norm).
+cudaError_t launch_jacobi_coop(double *A, double *V, int64_t n, int max_sweeps, double tol, void *ws, double *out2,
+                               cudaStream_t st);
 cudaError_t launch_eig_diag(int64_t n, const double *A, double *w, double *wmax, cudaStream_t st);
 cudaError_t launch_spectral_filter(int64_t n, const double *w, const double *wmax, double rcond, int power,
                                    double *z, int *kept, cudaStream_t st);

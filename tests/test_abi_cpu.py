@@ -129,3 +129,17 @@ def test_request_bytes_plans_a_j1j2_request(libnk):
         pytest.skip("no CUDA driver to create the planning context")
     r1 = nk.make_request("sr_step", N, M, I.rbm_params(N, M, 6), I.heis_square(10), 1024, cfg)
     assert b > nk.nk_request_bytes(r1) > 0  # twice the edge tables
+
+
+def test_library_leaves_no_internal_symbol_undefined():
+    """A shared library links even when one of its own functions is missing;
+    every nk:: symbol the library uses must be defined in it."""
+    import shutil
+    import subprocess
+    from paper_2112_10526_gb300 import build
+    if shutil.which("nm") is None:
+        pytest.skip("no nm")
+    lib = build.build()
+    out = subprocess.run(["nm", "-D", "--undefined-only", lib], capture_output=True, text=True, check=True).stdout
+    missing = [ln.split()[-1] for ln in out.splitlines() if "_ZN2nk" in ln or " nk_" in ln]
+    assert not missing, missing
