@@ -238,6 +238,259 @@ __global__ void __launch_bounds__(kSgThreads, 2)
     }
 }
 
+// ------------------------------------------- J v: persistent, 4 slices ---
+//
+// The CG products of NK_MIXED (4 slices) as one persistent kernel per SM:
+// warp 0 streams A / B K-chunks through a 4-stage TMA ring, warp 1 issues the
+// MMAs of a 128 x 64 tile (4 slices side by side, N = 256) into one of two
+// TMEM accumulator sets (512 columns), and 16 epilogue warps drain the other
+// set meanwhile: warp (q, g) owns TMEM lane quarter q (tile rows 32q ..
+// 32q + 31) and the 16 tile columns 16g .. 16g + 15.  Per entry the epilogue
+// forms the exact integer V of the 4 levels (levels4_to_i64), its FP64 value
+// V 2^(f_n - 32) (exact_to_double; |V| < 2^46 needs no rounding) and one FP64
+// FMA with t'; tanh(theta) for the warp's columns is loaded before the wait
+// on the accumulators.  The four column groups of a row meet in shared
+// memory (a ring of 4 tiles, an mbarrier per quarter and slot), and warp
+// (q, 0) writes the tile's row partial P[nt][row].  Tiles go round robin over
+// the CTAs.  Every wait is bounded; a time-out sets err and drains the copies
+// and MMAs in flight before the TMEM is released.
+constexpr int kJvEpiWarps = 16;
+constexpr int kJvThreads = 64 + 32 * kJvEpiWarps;
+constexpr int kJvStages = 4;
+constexpr int kJvSB = 4;
+constexpr int kJvStageBytes = kAB + kJvSB * kBB;  // 48 KB
+constexpr int kJvRing = 4;                          // row-partial slots
+constexpr uint32_t kJvAccCols = kJvSB * kBN;        // 256
+
+struct JvArgs {
+    int64_t rows;         // Ns
+    int64_t cols;         // M + 1
+    int kchunks;
+    int n_nt;             // column tiles
+    int64_t tiles;
+    const int *expB;      // [n_nt * 64] (read up to the tile end; columns >= cols unused)
+    const double *T;      // [rows][M]
+    int M;
+    bool vec;             // T rows 16-byte aligned: M even, T 16-byte aligned
+    double *P;            // [n_nt][rows]
+    int *err;
+};
+
+constexpr size_t jv_smem_bytes() {
+    return 1024 + (size_t)kJvStages * kJvStageBytes + (size_t)kJvRing * 4 * kBM * 8 +
+           (size_t)(2 * kJvStages + 4 + kJvRing * 4) * 8 + 16;
+}
+
+__global__ void __launch_bounds__(kJvThreads, 1)
+    k_jvp4(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, JvArgs a) {
+    extern __shared__ unsigned char smem_raw[];
+    const uint32_t base = smem_u32(smem_raw);
+    unsigned char *ops = smem_raw + ((1024 - (base & 1023)) & 1023);
+    double *red = reinterpret_cast<double *>(ops + (size_t)kJvStages * kJvStageBytes);  // [ring][4 groups][128]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(red + (size_t)kJvRing * 4 * kBM);
+    uint64_t *full = bars, *empty = bars + kJvStages;
+    uint64_t *acc_full = bars + 2 * kJvStages, *acc_empty = acc_full + 2;
+    uint64_t *red_full = acc_empty + 2;  // [ring][quarter]
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(red_full + kJvRing * 4);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tslot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t ntiles = a.tiles > (int64_t)blockIdx.x ? (a.tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kJvStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], kJvEpiWarps);
+        }
+        for (int i = 0; i < kJvRing * 4; ++i) mbar_init(&red_full[i], 4);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc(tslot, 2 * kJvAccCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    auto fail = [&](int code) {
+        *abort_flag = 1;
+        atomicExch(a.err, code);
+    };
+
+    if (warp == 0 && lane == 0) {
+        // ---------------------------------------------------------- producer
+        int64_t g = 0;  // K-chunks issued (all tiles)
+        for (int64_t li = 0; li < ntiles && !*abort_flag; ++li) {
+            const int64_t tile = blockIdx.x + li * gridDim.x;
+            const int m0 = (int)(tile / a.n_nt) * kBM, n0 = (int)(tile % a.n_nt) * kBN;
+            for (int kc = 0; kc < a.kchunks; ++kc, ++g) {
+                const int s = (int)(g % kJvStages);
+                if (g >= kJvStages &&
+                    !mbar_wait_or_abort(&empty[s], (uint32_t)((g / kJvStages - 1) & 1), abort_flag)) {
+                    fail(20);
+                    break;
+                }
+                unsigned char *sp = ops + (size_t)s * kJvStageBytes;
+                mbar_expect_tx(&full[s], (uint32_t)kJvStageBytes);
+                tma_load_2d(sp, &mapA, &full[s], kc * kBK, m0);
+#pragma unroll
+                for (int t = 0; t < kJvSB; ++t) tma_load_3d(sp + kAB + t * kBB, &mapB, &full[s], kc * kBK, n0, t);
+            }
+        }
+        if (*abort_flag) {
+            // the copies in flight land before the CTA exits
+            for (int64_t h = g - kJvStages > 0 ? g - kJvStages : 0; h < g; ++h)
+                mbar_wait(&full[h % kJvStages], (uint32_t)((h / kJvStages) & 1));
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ------------------------------------------------------- MMA issuer
+        const uint32_t idesc = idesc_bf16(kBM, kBN * kJvSB);
+        int64_t g = 0;
+        int64_t committed = -1;  // last tile whose accumulator commit was issued
+        bool any = false;
+        for (int64_t li = 0; li < ntiles && !*abort_flag; ++li) {
+            const int b = (int)(li & 1);
+            const uint32_t use = (uint32_t)(li >> 1);
+            if (use > 0 && !mbar_wait_or_abort(&acc_empty[b], (use - 1) & 1, abort_flag)) {
+                fail(21);
+                break;
+            }
+            tc_fence_after();
+            bool ok = true;
+            for (int kc = 0; kc < a.kchunks; ++kc, ++g) {
+                const int s = (int)(g % kJvStages);
+                if (!mbar_wait_or_abort(&full[s], (uint32_t)((g / kJvStages) & 1), abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                unsigned char *sp = ops + (size_t)s * kJvStageBytes;
+                const uint64_t da = sw128_desc(sp), db = sw128_desc(sp + kAB);
+#pragma unroll
+                for (int kk = 0; kk < kBK / 16; ++kk)
+                    umma_bf16(tmem + (uint32_t)b * kJvAccCols, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2),
+                              idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+                umma_commit(&empty[s]);
+                any = true;
+            }
+            umma_commit(&acc_full[b]);
+            committed = li;
+            if (!ok) {
+                fail(22);
+                break;
+            }
+        }
+        if (*abort_flag && any && committed >= 0) {
+            // the MMAs in flight finish before the TMEM is released
+            mbar_wait(&acc_full[committed & 1], (uint32_t)((committed >> 1) & 1));
+        }
+    } else if (warp >= 2) {
+        // --------------------------------------------------------- epilogue
+        const int q = warp & 3, grp = (warp - 2) >> 2, c0 = grp * 16;
+        const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+        for (int64_t li = 0; li < ntiles; ++li) {
+            const int64_t tile = blockIdx.x + li * gridDim.x;
+            const int64_t m0 = (tile / a.n_nt) * kBM;
+            const int n0 = (int)(tile % a.n_nt) * kBN;
+            const int64_t row = m0 + q * 32 + lane;
+            const bool row_ok = row < a.rows;
+            // t' of the warp's 16 columns and their exponents, in flight while the MMAs run
+            double tv[16];
+            int fe[16];
+            const int col0 = n0 + c0;
+            if (row_ok && a.vec && col0 + 16 <= a.M) {
+                const double2 *src = reinterpret_cast<const double2 *>(a.T + (size_t)row * a.M + col0);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const double2 v2 = __ldcs(src + j);
+                    tv[2 * j] = v2.x;
+                    tv[2 * j + 1] = v2.y;
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int col = col0 + j;
+                    tv[j] = !row_ok ? 0.0 : (col < a.M ? a.T[(size_t)row * a.M + col] : (col == a.M ? 1.0 : 0.0));
+                }
+            }
+            {
+                const int4 *ep = reinterpret_cast<const int4 *>(a.expB + col0);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int4 e4 = __ldg(ep + j);
+                    fe[4 * j] = e4.x;
+                    fe[4 * j + 1] = e4.y;
+                    fe[4 * j + 2] = e4.z;
+                    fe[4 * j + 3] = e4.w;
+                }
+#pragma unroll
+                for (int j = 0; j < 16; ++j) fe[j] = col0 + j < a.cols ? fe[j] - 8 * kJvSB : -100000;
+            }
+            const int b = (int)(li & 1);
+            const uint32_t use = (uint32_t)(li >> 1);
+            int ok = 1;
+            if (lane == 0) ok = mbar_wait_or_abort(&acc_full[b], use & 1, abort_flag) ? 1 : 0;
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) {
+                if (lane == 0) fail(23);
+                break;
+            }
+            tc_fence_after();
+            double r0 = 0.0, r1 = 0.0;
+#pragma unroll
+            for (int c8 = 0; c8 < 16; c8 += 8) {
+                uint32_t r[kJvSB][8];
+#pragma unroll
+                for (int t = 0; t < kJvSB; ++t)
+                    tmem_ld8(tmem + (uint32_t)b * kJvAccCols + lane_base + (uint32_t)(t * kBN + c0 + c8), r[t]);
+                tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 8; j += 2) {
+                    const long long V0 = levels4_to_i64(__uint_as_float(r[0][j]), __uint_as_float(r[1][j]),
+                                                        __uint_as_float(r[2][j]), __uint_as_float(r[3][j]));
+                    const long long V1 =
+                        levels4_to_i64(__uint_as_float(r[0][j + 1]), __uint_as_float(r[1][j + 1]),
+                                       __uint_as_float(r[2][j + 1]), __uint_as_float(r[3][j + 1]));
+                    r0 = fma(exact_to_double(V0, fe[c8 + j]), tv[c8 + j], r0);
+                    r1 = fma(exact_to_double(V1, fe[c8 + j + 1]), tv[c8 + j + 1], r1);
+                }
+            }
+            // the accumulator set is drained: hand it back to the MMA warp
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[b]);
+            // the four column groups of each row meet in the ring slot of this tile
+            const int slot = (int)(li % kJvRing);
+            red[((size_t)slot * 4 + grp) * kBM + q * 32 + lane] = r0 + r1;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&red_full[slot * 4 + q]);
+            if (grp == 0) {
+                int rok = 1;
+                if (lane == 0)
+                    rok = mbar_wait_or_abort(&red_full[slot * 4 + q], (uint32_t)((li / kJvRing) & 1), abort_flag)
+                              ? 1
+                              : 0;
+                rok = __shfl_sync(0xffffffffu, rok, 0);
+                if (!rok) {
+                    if (lane == 0) fail(24);
+                    break;
+                }
+                const double *rs = red + (size_t)slot * 4 * kBM + q * 32 + lane;
+                const double sum = ((rs[0] + rs[kBM]) + rs[2 * kBM]) + rs[3 * kBM];
+                if (row_ok) a.P[(size_t)(n0 / kBN) * a.rows + row] = sum;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 2 * kJvAccCols);
+    }
+}
+
 int sgemm_stages(int SB) { return SB <= 4 ? 2 : 3; }
 
 size_t sgemm_smem_bytes(int SB) {
@@ -465,7 +718,15 @@ __global__ void k_tg_slice(const double *__restrict__ T, const double *__restric
     }
 }
 
-// P^T [N+1][M+1] (row i, column j) -> J^T g in the parameter layout.
+// w[r] = sum_t P[t][r] (tile-major partials of k_jvp4), in tile order.
+__global__ void k_rowsum_tiles(int64_t rows, int ntc, const double *__restrict__ P, double *__restrict__ w) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    double acc = 0.0;
+    for (int t = 0; t < ntc; ++t) acc += P[(size_t)t * rows + r];
+    w[r] = acc;
+}
+
 // w[row] = sum over the ntc column tiles of P[row][t], in tile order.
 __global__ void k_rowsum_partials(int64_t rows, int ntc, const double *__restrict__ P, double *__restrict__ w) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -475,7 +736,8 @@ __global__ void k_rowsum_partials(int64_t rows, int ntc, const double *__restric
     w[r] = acc;
 }
 
-// PT holds ks K-split partial products [ks][(N+1)][(M+1)], summed in order.
+// P^T [N+1][M+1] (row i, column j) -> J^T g in the parameter layout; PT
+// holds ks K-split partial products [ks][(N+1)][(M+1)], summed in order.
 __global__ void k_scatter_vjp(int N, int M, int ks, const double *__restrict__ PT, double *__restrict__ out) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t tot = (int64_t)(N + 1) * (M + 1);
@@ -562,6 +824,31 @@ cudaError_t sgemm(const __nv_bfloat16 *A, int64_t rows, int64_t ldA, const __nv_
     return cudaGetLastError();
 }
 
+// J v partials P [n_nt][rows] = per 64-column tile, sum_col (A B^T)[row][col]
+// t'_col by k_jvp4 (4 slices; K <= 16448 so that |D_t| <= 255 K < 2^22).
+cudaError_t jvp4(const __nv_bfloat16 *A, int64_t rows, int64_t ldA, const __nv_bfloat16 *Bsl, const int *expB,
+                 int64_t cols, int64_t ldB, int64_t K, const double *T, int Mt, double *P, int *err,
+                 cudaStream_t st) {
+    if (rows <= 0 || cols <= 0 || K <= 0) return cudaSuccess;
+    if (K > 16448 || rows > (1LL << 31) - kBM || cols > (1LL << 31) - kBN || T == nullptr)
+        return cudaErrorInvalidValue;
+    CUtensorMap ma, mb;
+    if (!make_rows_map(&ma, A, rows, K, ldA, kBM) || !make_sliced_map(&mb, Bsl, cols, K, ldB, kJvSB, kBN))
+        return cudaErrorInvalidValue;
+    cudaError_t e = nk::allow_max_dynamic_smem((const void *)k_jvp4);
+    int dev = 0, sms = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int n_nt = (int)((cols + kBN - 1) / kBN);
+    const int64_t tiles = (int64_t)n_nt * ((rows + kBM - 1) / kBM);
+    JvArgs a{rows, cols, (int)((K + kBK - 1) / kBK), n_nt, tiles, expB, T, Mt,
+             (Mt % 2 == 0) && ((reinterpret_cast<uintptr_t>(T) & 15) == 0), P, err};
+    const int grid = (int)(tiles < sms ? tiles : sms);
+    (k_jvp4<<<grid, kJvThreads, jv_smem_bytes(), st>>>(ma, mb, a), nk::note_launch());
+    return cudaGetLastError();
+}
+
 double sgemm_flops(int64_t rows, int64_t cols, int64_t K, int SB) {
     return 2.0 * (double)((rows + kBM - 1) / kBM * kBM) * (double)((cols + kBN - 1) / kBN * kBN) *
            (double)((K + kBK - 1) / kBK * kBK) * SB;
@@ -606,10 +893,24 @@ size_t tc_jvp_ws_bytes(int N, int M, int64_t Ns) {
            ((size_t)Ns * ntc * 8 + 255) / 256 * 256 + 256;
 }
 
+size_t tc_jvp_operand_bytes(int N, int64_t Ns) { return (size_t)Ns * pad8(N + 1) * 2; }
+size_t tc_vjp_operand_bytes(int N, int64_t Ns) { return (size_t)(N + 1) * pad8(Ns) * 2; }
+
+cudaError_t launch_jacobian_operands(int N, int64_t Ns, const int8_t *s, void *opA, void *opT, cudaStream_t st) {
+    if (Ns <= 0) return cudaSuccess;
+    const int64_t lda = pad8(N + 1), ldt = pad8(Ns);
+    (k_pm1_rows<<<nblk(Ns * lda, 256), 256, 0, st>>>(s, Ns, N, 1, lda, static_cast<__nv_bfloat16 *>(opA)),
+     nk::note_launch());
+    (k_pm1_cols<<<dim3(nblk(ldt, 32), nblk(N + 1, 32)), dim3(32, 8), 0, st>>>(s, Ns, N, ldt,
+                                                                              static_cast<__nv_bfloat16 *>(opT)),
+     nk::note_launch());
+    return cudaGetLastError();
+}
+
 // out = J v with V' cut into SB slices: w = rowdot(T', S' V'^T), the row
 // products taken in the S-GEMM epilogue per 64-column tile and summed after.
 cudaError_t launch_jvp_tc(int N, int M, int64_t Ns, const int8_t *s, const double *T, const double *v,
-                          double *out, int SB, int *err, void *ws, cudaStream_t st) {
+                          double *out, int SB, int *err, void *ws, cudaStream_t st, const void *opA) {
     const int64_t ld = pad8(N + 1);
     char *p = static_cast<char *>(ws);
     auto take = [&](size_t bytes) {
@@ -624,18 +925,42 @@ cudaError_t launch_jvp_tc(int N, int M, int64_t Ns, const int8_t *s, const doubl
     const int ntc = (M + 1 + kBN - 1) / kBN;
     auto *P = reinterpret_cast<double *>(take((size_t)Ns * ntc * 8));
     const int64_t tot = (int64_t)(M + 1) * (N + 1);
-    (k_pm1_rows<<<nblk(Ns * ld, 256), 256, 0, st>>>(s, Ns, N, 1, ld, As), nk::note_launch());
+    if (opA)
+        As = static_cast<__nv_bfloat16 *>(const_cast<void *>(opA));
+    else
+        (k_pm1_rows<<<nblk(Ns * ld, 256), 256, 0, st>>>(s, Ns, N, 1, ld, As), nk::note_launch());
     (k_build_vaug<<<nblk(tot, 256), 256, 0, st>>>(N, M, v, Vp), nk::note_launch());
     (k_slice_long_rows<<<M + 1, 128, 0, st>>>(Vp, N + 1, M + 1, N + 1, nullptr, SB, ld, Vs, ev), nk::note_launch());
+    const bool persistent = SB == kJvSB && N + 1 <= 16448;
     const int slot = prof_begin(NK_PROF_JVP_VJP, st);
-    cudaError_t e = sgemm(As, Ns, ld, Vs, ev, M + 1, ld, N + 1, SB, P, ntc, 3, nullptr, err, st, T, M);
+    cudaError_t e = persistent ? jvp4(As, Ns, ld, Vs, ev, M + 1, ld, N + 1, T, M, P, err, st)
+                               : sgemm(As, Ns, ld, Vs, ev, M + 1, ld, N + 1, SB, P, ntc, 3, nullptr, err, st, T, M);
     prof_end(slot, st, 2.0 * (double)Ns * (N + 1) * (double)(M + 1), sgemm_flops(Ns, M + 1, N + 1, SB));
     if (e != cudaSuccess) return e;
-    (k_rowsum_partials<<<nblk(Ns, 256), 256, 0, st>>>(Ns, ntc, P, out), nk::note_launch());
+    if (persistent)
+        (k_rowsum_tiles<<<nblk(Ns, 256), 256, 0, st>>>(Ns, ntc, P, out), nk::note_launch());
+    else
+        (k_rowsum_partials<<<nblk(Ns, 256), 256, 0, st>>>(Ns, ntc, P, out), nk::note_launch());
     return cudaGetLastError();
 }
 
 constexpr int kMaxKSplit = 8;
+
+// K-split count for a grid of `tiles` output tiles over `slots` resident
+// CTAs: the share of the last wave's slots that hold work, less 1 % per extra
+// split (its partial output is written and summed), best over 1 .. 8 splits
+// of at least 4 K-chunks each.
+static int pick_ksplit(int64_t tiles, int64_t kchunks, int64_t slots) {
+    int best = 1;
+    double best_score = -1.0;
+    for (int ks = 1; ks <= kMaxKSplit; ++ks) {
+        if (ks > 1 && kchunks / ks < 4) break;
+        const int64_t ctas = tiles * ks, waves = (ctas + slots - 1) / slots;
+        const double score = (double)ctas / (double)(waves * slots) - 0.01 * (ks - 1);
+        if (score > best_score + 1e-12) best_score = score, best = ks;
+    }
+    return best;
+}
 
 size_t tc_vjp_ws_bytes(int N, int M, int64_t Ns) {
     const int64_t ld = pad8(Ns);
@@ -660,7 +985,7 @@ cudaError_t launch_colexp_t(int M, int64_t Ns, const double *T, int *colexpT, vo
 
 cudaError_t launch_vjp_tc(int N, int M, int64_t Ns, const int8_t *s, const double *T, const double *g,
                           double scale, const double *shift, double *out, int SB, int *err, void *ws,
-                          cudaStream_t st, const int *colexpT) {
+                          cudaStream_t st, const int *colexpT, const void *opT) {
     const int64_t ld = pad8(Ns);
     char *p = static_cast<char *>(ws);
     auto take = [&](size_t bytes) {
@@ -675,7 +1000,10 @@ cudaError_t launch_vjp_tc(int N, int M, int64_t Ns, const int8_t *s, const doubl
     auto *gp = reinterpret_cast<double *>(take((size_t)Ns * 8));
     auto *ge = reinterpret_cast<int *>(take((size_t)Ns * 4));
     dim3 tb(32, 8);
-    (k_pm1_cols<<<dim3(nblk(ld, 32), nblk(N + 1, 32)), tb, 0, st>>>(s, Ns, N, ld, St), nk::note_launch());
+    if (opT)
+        St = static_cast<__nv_bfloat16 *>(const_cast<void *>(opT));
+    else
+        (k_pm1_cols<<<dim3(nblk(ld, 32), nblk(N + 1, 32)), tb, 0, st>>>(s, Ns, N, ld, St), nk::note_launch());
     (k_scale_g<<<nblk(Ns, 256), 256, 0, st>>>(Ns, g, scale, shift, gp, ge), nk::note_launch());
     if (colexpT) {
         // the column bound: no pass over T (eg[M + 1] holds max_k ge[k])
@@ -688,17 +1016,17 @@ cudaError_t launch_vjp_tc(int N, int M, int64_t Ns, const int8_t *s, const doubl
     }
     (k_tg_slice<<<dim3(nblk(ld, 64), nblk(M + 1, 32)), tb, 0, st>>>(T, gp, Ns, M, SB, ld, eg, Gs),
      nk::note_launch());
-    // split the long K = Ns range until the grid covers the SMs twice
-    // (every split keeps >= 4 chunks; each split's FP32 levels stay exact)
-    int dev = 0, sms = 0;
+    // split the long K = Ns range so that the last wave of CTAs is nearly
+    // full (every split keeps >= 4 chunks; each split's FP32 levels stay exact)
+    int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = nk::allow_max_dynamic_smem((const void *)k_sgemm);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sgemm, kSgThreads, sgemm_smem_bytes(SB));
     if (e != cudaSuccess) return e;
     const int64_t tiles = (int64_t)nblk(M + 1, kBN) * nblk(N + 1, kBM), kchunks = (Ns + kBK - 1) / kBK;
-    int ks = (int)((2 * (int64_t)sms + tiles - 1) / tiles);
-    if (ks > kMaxKSplit) ks = kMaxKSplit;
-    if (ks > kchunks / 4) ks = (int)(kchunks / 4);
-    if (ks < 1) ks = 1;
+    int ks = pick_ksplit(tiles, kchunks, (int64_t)sms * (per_sm > 0 ? per_sm : 1));
     const int kc_split = (int)((kchunks + ks - 1) / ks);
     ks = (int)((kchunks + kc_split - 1) / kc_split);  // splits the kernel launches
     const int64_t tot = (int64_t)(N + 1) * (M + 1);

@@ -206,6 +206,8 @@ struct SolveWs {
     void *tcm;  // tensor-core Jacobian-product workspace (NK_MIXED)
     int *colexpT;     // NK_MIXED CG: column exponents of tanh(theta), [M + 1]
     void *colexp_ws;
+    void *opA, *opT;  // NK_MIXED CG: the +-1 product operands, built once per solve
+    bool ops_ready;   // opA / opT hold the operands of the samples being solved for
     int *tcerr; // sticky tensor-core error word of the context
 };
 
@@ -232,6 +234,8 @@ void carve_solve(Carver &c, SolveWs &w, int N, int M, int64_t Ns, int solver, in
         if (precision == NK_MIXED) {
             w.colexpT = c.take<int>(M + 1);
             w.colexp_ws = c.take<char>(nk::tc_colexp_ws_bytes(M, Ns));
+            w.opA = c.take<char>(nk::tc_jvp_operand_bytes(N, Ns));
+            w.opT = c.take<char>(nk::tc_vjp_operand_bytes(N, Ns));
         }
     } else if (solver == NK_SOLVER_CHOLESKY) {
         w.dJ = c.take<double>((size_t)Ns * Np);
@@ -287,7 +291,8 @@ constexpr double kJacobiTol = 1e-14;
 
 cudaError_t jvp_any(int N, int M, int64_t Ns, const int8_t *s, const double *T, const double *v, SolveWs &w,
                     double *out, int precision, int slices, cudaStream_t st) {
-    if (precision == NK_MIXED) return nk::launch_jvp_tc(N, M, Ns, s, T, v, out, slices, w.tcerr, w.tcm, st);
+    if (precision == NK_MIXED)
+        return nk::launch_jvp_tc(N, M, Ns, s, T, v, out, slices, w.tcerr, w.tcm, st, w.ops_ready ? w.opA : nullptr);
     return nk::launch_jvp(N, M, Ns, s, T, v, w.U, out, st);
 }
 
@@ -295,7 +300,8 @@ cudaError_t vjp_any(int N, int M, int64_t Ns, const int8_t *s, const double *T, 
                     const double *shift, SolveWs &w, double *out, int precision, int slices, cudaStream_t st,
                     const int *colexpT = nullptr) {
     if (precision == NK_MIXED)
-        return nk::launch_vjp_tc(N, M, Ns, s, T, g, scale, shift, out, slices, w.tcerr, w.tcm, st, colexpT);
+        return nk::launch_vjp_tc(N, M, Ns, s, T, g, scale, shift, out, slices, w.tcerr, w.tcm, st, colexpT,
+                                 w.ops_ready ? w.opT : nullptr);
     return nk::launch_vjp(N, M, Ns, s, T, g, scale, shift, w.partial, out, st);
 }
 
@@ -353,7 +359,16 @@ nk_status run_solve(nk_ctx *ctx, int N, int M, int64_t Ns, const int8_t *s, cons
     if (solver == NK_SOLVER_CG) {
         double *rr = w.sc, *rr_new = w.sc + 1, *pAp = w.sc + 2, *ff = w.sc + 3, *rr_keep = w.sc + 4;
         int *done = w.flags, *iters = w.flags + 1;
-        if (tc) NK_CU(nk::launch_colexp_t(M, Ns, T, w.colexpT, w.colexp_ws, st), "cg exponents");
+        if (tc) {
+            NK_CU(nk::launch_colexp_t(M, Ns, T, w.colexpT, w.colexp_ws, st), "cg exponents");
+            NK_CU(nk::launch_jacobian_operands(N, Ns, s, w.opA, w.opT, st), "cg operands");
+        }
+        // the operands stay valid for this solve's samples only
+        struct OpsReady {
+            SolveWs &w;
+            ~OpsReady() { w.ops_ready = false; }
+        } ops_guard{w};
+        w.ops_ready = tc;
         NK_CU(nk::launch_fill(Np, 0.0, w.x, st), "cg init");
         NK_CU(nk::launch_axpby(Np, 1.0, F, 0.0, w.r, st), "cg init");
         NK_CU(nk::launch_axpby(Np, 1.0, F, 0.0, w.p, st), "cg init");

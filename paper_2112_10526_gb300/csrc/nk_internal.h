@@ -213,16 +213,24 @@ cudaError_t launch_gram_cols_tc(const double *X, int64_t rows, int64_t ncols, do
 size_t tc_theta_ws_bytes(int N, int M, int64_t B);
 cudaError_t launch_theta_tc(int N, int M, const double *b, const double *W, const int8_t *s, int64_t B,
                             double *theta, int *err, void *ws, cudaStream_t st);
+// The +-1 operands of the two Jacobian products depend on the samples only:
+// a solve that repeats the products (CG) builds them once.  opA: [S, 1] as
+// BF16 [Ns][pad8(N + 1)] (J v); opT: [S, 1]^T as BF16 [N + 1][pad8(Ns)] (J^T g).
+size_t tc_jvp_operand_bytes(int N, int64_t Ns);
+size_t tc_vjp_operand_bytes(int N, int64_t Ns);
+cudaError_t launch_jacobian_operands(int N, int64_t Ns, const int8_t *s, void *opA, void *opT, cudaStream_t st);
 size_t tc_jvp_ws_bytes(int N, int M, int64_t Ns);
+// opA (optional): the prebuilt J v operand of launch_jacobian_operands.
 cudaError_t launch_jvp_tc(int N, int M, int64_t Ns, const int8_t *s, const double *T, const double *v,
-                          double *out, int SB, int *err, void *ws, cudaStream_t st);
+                          double *out, int SB, int *err, void *ws, cudaStream_t st, const void *opA = nullptr);
 size_t tc_vjp_ws_bytes(int N, int M, int64_t Ns);
 // colexpT (optional, [M + 1], from launch_colexp_t): the column exponents of
 // tanh(theta), so that the slices of (T' o g')^T take their exponents from
-// the bound max_k |t'_kj| max_k |g'_k| instead of a pass over T.
+// the bound max_k |t'_kj| max_k |g'_k| instead of a pass over T.  opT
+// (optional): the prebuilt J^T g operand of launch_jacobian_operands.
 cudaError_t launch_vjp_tc(int N, int M, int64_t Ns, const int8_t *s, const double *T, const double *g,
                           double scale, const double *shift, double *out, int SB, int *err, void *ws,
-                          cudaStream_t st, const int *colexpT = nullptr);
+                          cudaStream_t st, const int *colexpT = nullptr, const void *opT = nullptr);
 size_t tc_colexp_ws_bytes(int M, int64_t Ns);
 cudaError_t launch_colexp_t(int M, int64_t Ns, const double *T, int *colexpT, void *ws, cudaStream_t st);
 

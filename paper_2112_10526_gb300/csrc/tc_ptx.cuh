@@ -253,6 +253,52 @@ __host__ __device__ __forceinline__ double window_to_double(long long x, int sc)
     return v;
 }
 
+// The four FP32 levels of a 4-slice product (exact integers, |D_t| < 2^22)
+// as the signed 64-bit V = D_0 2^24 + D_1 2^16 + D_2 2^8 + D_3.  One FP32 add
+// of 1.5 2^23 turns a level into the bit pattern 0x4B400000 + D_t (ulp 1 in
+// [2^23, 2^24)); the pairs D_0 2^8 + D_1 and D_2 2^8 + D_3 follow in 32-bit
+// arithmetic modulo 2^32 (exact: both below 2^31 in magnitude), and V in one
+// 64-bit multiply-add.
+__host__ __device__ __forceinline__ unsigned int biased_level_bits(float d) {
+#ifdef __CUDA_ARCH__
+    return __float_as_uint(__fadd_rn(d, 12582912.0f));
+#else
+    const float x = d + 12582912.0f;
+    unsigned int u;
+    __builtin_memcpy(&u, &x, 4);
+    return u;
+#endif
+}
+
+__host__ __device__ __forceinline__ long long levels4_to_i64(float d0, float d1, float d2, float d3) {
+    const unsigned int bias = 257u * 0x4B400000u;  // mod 2^32
+    const int hi = (int)(biased_level_bits(d0) * 256u + biased_level_bits(d1) - bias);
+    const int lo = (int)(biased_level_bits(d2) * 256u + biased_level_bits(d3) - bias);
+    return (long long)hi * 65536 + lo;
+}
+
+// V 2^sc as FP64 for |V| < 2^53, where the value needs no rounding: the
+// leading one of |V| moves to bit 52 and (exponent - 1) 2^52 is added, as in
+// window_to_double.  A signed zero for V = 0 or a result below 2^-1022, an
+// infinity from 2^1024 on.
+__host__ __device__ __forceinline__ double exact_to_double(long long V, int sc) {
+    const unsigned long long sgn = (unsigned long long)V & 0x8000000000000000ULL;
+    const unsigned long long m = sgn ? 0ULL - (unsigned long long)V : (unsigned long long)V;
+    const int z = clz64_any(m);                              // 11 .. 64
+    const unsigned long long n = m << ((z - 11) & 63);       // leading one at bit 52 (m != 0)
+    const int eb = 1086 - z + sc;                            // biased exponent
+    unsigned long long bits = sgn | (((unsigned long long)(eb - 1) << 52) + n);  // mod 2^64
+    bits = eb > 2046 ? (sgn | 0x7FF0000000000000ULL) : bits;
+    bits = (m == 0ULL || eb < 1) ? sgn : bits;
+    double v;
+#ifdef __CUDA_ARCH__
+    v = __longlong_as_double((long long)bits);
+#else
+    __builtin_memcpy(&v, &bits, 8);
+#endif
+    return v;
+}
+
 // ------------------------------------------------------ host: tensor maps ---
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,

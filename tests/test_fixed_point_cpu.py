@@ -5,7 +5,10 @@ host, against exact 128-bit integer arithmetic:
   the fixed-point recombination V of the slice levels, for levels up to the
   bounds the kernels guarantee;
 * window_to_double(x, sc) is x 2^sc rounded to nearest with ties away from
-  zero, a signed zero below 2^-1022 and an infinity from 2^1024 on.
+  zero, a signed zero below 2^-1022 and an infinity from 2^1024 on;
+* levels4_to_i64 is D_0 2^24 + D_1 2^16 + D_2 2^8 + D_3 for FP32 levels up
+  to 2^22 in magnitude, and exact_to_double(V, sc) is V 2^sc (no rounding for
+  |V| < 2^53) with the same flush and saturation.
 
 The routines are __host__ __device__; the test compiles them with g++ from
 the header itself."""
@@ -124,8 +127,37 @@ int main() {
             ++bad;
         }
     }
+    // 4. the 4-level combination: |D_t| < 2^22, exact FP32 integers
+    for (long it = 0; it < 1000000; ++it) {
+        long long d[4];
+        for (int i = 0; i < 4; ++i) d[i] = rnd_bound((1LL << 22) - 1);
+        const long long want = (d[0] << 24) + (d[1] << 16) + (d[2] << 8) + d[3];
+        ++n;
+        if (levels4_to_i64((float)d[0], (float)d[1], (float)d[2], (float)d[3]) != want) {
+            if (bad < 5) printf("levels4 %%ld\n", it);
+            ++bad;
+        }
+    }
+    // 5. the exact conversion: |V| < 2^53 at every scale
+    for (long it = 0; it < 1000000; ++it) {
+        const int bl = (int)(g() %% 54);
+        unsigned long long m = bl == 0 ? 0ULL : ((g() >> (64 - bl)) | (1ULL << (bl - 1)));
+        const long long x = (g() & 1) ? -(long long)m : (long long)m;
+        int sc;
+        switch (g() %% 3) {
+            case 0: sc = (int)(g() %% 200) - 100; break;
+            case 1: sc = -1075 + (int)(g() %% 80); break;
+            default: sc = 960 + (int)(g() %% 80);
+        }
+        ++n;
+        const double got = exact_to_double(x, sc), ref = ref_round(x, sc);
+        if (!same(got, ref) && !(m == 0 && got == 0.0 && ref == 0.0)) {
+            if (bad < 5) printf("exact x=%%lld sc=%%d got %%a ref %%a\n", x, sc, got, ref);
+            ++bad;
+        }
+    }
     printf("checked %%ld bad %%ld\n", n, bad);
-    return bad != 0 || n < 4000000;
+    return bad != 0 || n < 6000000;
 }
 """
 
@@ -133,12 +165,12 @@ int main() {
 def _extract():
     src = open(HEADER).read()
     a = src.index("__host__ __device__ __forceinline__ int clz64_any")
-    b = src.index("\n}\n", src.index("double window_to_double(")) + 3
+    b = src.index("\n}\n", src.index("double exact_to_double(")) + 3
     return src[a:b]
 
 
 @pytest.mark.skipif(shutil.which("g++") is None, reason="needs g++")
-def test_epilogue_windows_and_rounding_match_exact_int128():
+def test_epilogue_windows_rounding_and_exact_conversion_match_int128():
     with tempfile.TemporaryDirectory() as d:
         cpp = os.path.join(d, "f2b.cpp")
         exe = os.path.join(d, "f2b")
