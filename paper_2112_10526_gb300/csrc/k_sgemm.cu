@@ -245,15 +245,23 @@ __global__ void __launch_bounds__(kSgThreads, 2)
 // MMAs of a 128 x 64 tile (4 slices side by side, N = 256) into one of two
 // TMEM accumulator sets (512 columns), and 16 epilogue warps drain the other
 // set meanwhile: warp (q, g) owns TMEM lane quarter q (tile rows 32q ..
-// 32q + 31) and the 16 tile columns 16g .. 16g + 15.  Per entry the epilogue
-// forms the exact integer V of the 4 levels (levels4_to_i64), its FP64 value
-// V 2^(f_n - 32) (exact_to_double; |V| < 2^46 needs no rounding) and one FP64
-// FMA with t'; tanh(theta) for the warp's columns is loaded before the wait
-// on the accumulators.  The four column groups of a row meet in shared
-// memory (a ring of 4 tiles, an mbarrier per quarter and slot), and warp
-// (q, 0) writes the tile's row partial P[nt][row].  Tiles go round robin over
-// the CTAs.  Every wait is bounded; a time-out sets err and drains the copies
-// and MMAs in flight before the TMEM is released.
+// 32q + 31) and the 16 tile columns 16g .. 16g + 15.
+//
+// The epilogue needs sum_j t'_j V_j 2^(f_j - 32) per row, V_j = D_0 2^24 +
+// D_1 2^16 + D_2 2^8 + D_3 from the exact FP32 levels.  It runs in FP32 on
+// tanh(theta) stored as an FP32 pair t = th + tl (|tl| <= 2^-24 |th|, built
+// once per solve): with u = th 2^(f_j - F) and ul = tl 2^(f_j - F) (F the
+// largest column exponent of the tile, so that the scale is a power of two
+// <= 1), the row sum is 2^(F - 8) sum_j (D_0 + D_1 2^-8 + D_2 2^-16 +
+// D_3 2^-24)(u + ul).  The products D_0 u and D_1 u are split exactly by FMA
+// (p + e), p is summed exactly by two-sum into FP32 pairs, and the terms
+// below 2^-24 of the leading one go to a plain FP32 sum: about 2^-44 of the
+// summed magnitudes, below the 2^-32 of the slicing, with no FP64 work per
+// entry.  The four column groups of a row meet as FP32 pairs in shared memory
+// (a ring of 4 tiles, an mbarrier per quarter and slot), and warp (q, 0)
+// writes the tile's row partial P[nt][row] in FP64.  Tiles go round robin
+// over the CTAs.  Every wait is bounded; a time-out sets err and drains the
+// copies and MMAs in flight before the TMEM is released.
 constexpr int kJvEpiWarps = 16;
 constexpr int kJvThreads = 64 + 32 * kJvEpiWarps;
 constexpr int kJvStages = 4;
@@ -261,32 +269,67 @@ constexpr int kJvSB = 4;
 constexpr int kJvStageBytes = kAB + kJvSB * kBB;  // 48 KB
 constexpr int kJvRing = 4;                          // row-partial slots
 constexpr uint32_t kJvAccCols = kJvSB * kBN;        // 256
+constexpr int kTcRowDot = 0, kTcStoreT = 1;         // epilogue modes of k_tc4
 
-struct JvArgs {
-    int64_t rows;         // Ns
-    int64_t cols;         // M + 1
-    int kchunks;
-    int n_nt;             // column tiles
-    int64_t tiles;
+struct Tc4Args {
+    int64_t rows, cols;
+    int kchunks;          // K-chunks of the whole product
+    int kc_split;         // K-chunks per unit (mode 1; kchunks in mode 0)
+    int ks;               // K splits
+    int n_nt, n_mg;       // column tiles; row-tile groups of C tiles
+    int C;                // CTAs per cluster (1, 2, 4): B slices multicast across them
+    int64_t groups;       // n_mg * n_nt * ks
     const int *expB;      // [n_nt * 64] (read up to the tile end; columns >= cols unused)
-    const double *T;      // [rows][M]
-    int M;
-    bool vec;             // T rows 16-byte aligned: M even, T 16-byte aligned
-    double *P;            // [n_nt][rows]
+    const float4 *Thl;    // mode 0: t' as FP32 pairs, tile-major (launch_split_t)
+    double *P;            // mode 0: [n_nt][rows]; mode 1: [ks][cols][ldp] (column-major tiles)
+    int64_t ldp, split_stride;
     int *err;
 };
+
+// s + e = a + b exactly (Knuth's two-sum, no ordering of |a|, |b| needed)
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
 
 constexpr size_t jv_smem_bytes() {
     return 1024 + (size_t)kJvStages * kJvStageBytes + (size_t)kJvRing * 4 * kBM * 8 +
            (size_t)(2 * kJvStages + 4 + kJvRing * 4) * 8 + 16;
 }
 
+// Unit li of cluster slot `cl` (of ncl): the cluster's row-tile group mg,
+// column tile nt and K split z, this CTA's row tile mt = mg C + rank.
+// Mode 0 walks the column tiles fastest (the A tiles of a group are reused),
+// mode 1 the row-tile groups (the B range of (nt, z) is reused from L2).
+struct Tc4Unit {
+    int64_t mt;
+    int nt, z;
+};
+template <int kMode>
+__device__ __forceinline__ Tc4Unit tc4_unit(const Tc4Args &a, int64_t g, uint32_t rank) {
+    Tc4Unit u;
+    int64_t mg;
+    if (kMode == kTcRowDot) {
+        mg = g / a.n_nt;
+        u.nt = (int)(g % a.n_nt);
+        u.z = 0;
+    } else {
+        mg = g % a.n_mg;
+        const int64_t r = g / a.n_mg;
+        u.nt = (int)(r % a.n_nt);
+        u.z = (int)(r / a.n_nt);
+    }
+    u.mt = mg * a.C + rank;
+    return u;
+}
+template <int kMode>
 __global__ void __launch_bounds__(kJvThreads, 1)
-    k_jvp4(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, JvArgs a) {
+    k_tc4(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, Tc4Args a) {
     extern __shared__ unsigned char smem_raw[];
     const uint32_t base = smem_u32(smem_raw);
     unsigned char *ops = smem_raw + ((1024 - (base & 1023)) & 1023);
-    double *red = reinterpret_cast<double *>(ops + (size_t)kJvStages * kJvStageBytes);  // [ring][4 groups][128]
+    float2 *red = reinterpret_cast<float2 *>(ops + (size_t)kJvStages * kJvStageBytes);  // [ring][4 groups][128]
     uint64_t *bars = reinterpret_cast<uint64_t *>(red + (size_t)kJvRing * 4 * kBM);
     uint64_t *full = bars, *empty = bars + kJvStages;
     uint64_t *acc_full = bars + 2 * kJvStages, *acc_empty = acc_full + 2;
@@ -294,12 +337,17 @@ __global__ void __launch_bounds__(kJvThreads, 1)
     uint32_t *tslot = reinterpret_cast<uint32_t *>(red_full + kJvRing * 4);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tslot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t ntiles = a.tiles > (int64_t)blockIdx.x ? (a.tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int C = a.C;
+    const uint32_t rank = C > 1 ? cluster_rank() : 0u;
+    const uint16_t mask = (uint16_t)((1u << C) - 1u);
+    const int64_t cl = blockIdx.x / C, ncl = gridDim.x / C;
+    const int64_t nunits = a.groups > cl ? (a.groups - 1 - cl) / ncl + 1 : 0;
+    const int64_t n_mt = (a.rows + kBM - 1) / kBM;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kJvStages; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
+            mbar_init(&empty[s], (uint32_t)C);  // one commit from every CTA of the cluster
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&acc_full[b], 1);
@@ -311,7 +359,10 @@ __global__ void __launch_bounds__(kJvThreads, 1)
     }
     if (warp == 0) tmem_alloc(tslot, 2 * kJvAccCols);
     tc_fence_before();
-    __syncthreads();
+    if (C > 1)
+        cluster_sync_all();  // the peers' barriers exist before any multicast reaches them
+    else
+        __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
     auto fail = [&](int code) {
@@ -321,11 +372,15 @@ __global__ void __launch_bounds__(kJvThreads, 1)
 
     if (warp == 0 && lane == 0) {
         // ---------------------------------------------------------- producer
-        int64_t g = 0;  // K-chunks issued (all tiles)
-        for (int64_t li = 0; li < ntiles && !*abort_flag; ++li) {
-            const int64_t tile = blockIdx.x + li * gridDim.x;
-            const int m0 = (int)(tile / a.n_nt) * kBM, n0 = (int)(tile % a.n_nt) * kBN;
-            for (int kc = 0; kc < a.kchunks; ++kc, ++g) {
+        // own A tile; B slices rank * 4 / C .. (rank + 1) * 4 / C - 1 to every CTA
+        const int per = kJvSB / C, t0 = (int)rank * per;
+        int64_t g = 0;  // K-chunks issued (all units)
+        for (int64_t li = 0; li < nunits && !*abort_flag; ++li) {
+            const Tc4Unit u = tc4_unit<kMode>(a, cl + li * ncl, rank);
+            const int m0 = (int)(u.mt * kBM), n0 = u.nt * kBN;
+            const int kc0 = u.z * a.kc_split;
+            const int kc1 = kc0 + a.kc_split < a.kchunks ? kc0 + a.kc_split : a.kchunks;
+            for (int kc = kc0; kc < kc1; ++kc, ++g) {
                 const int s = (int)(g % kJvStages);
                 if (g >= kJvStages &&
                     !mbar_wait_or_abort(&empty[s], (uint32_t)((g / kJvStages - 1) & 1), abort_flag)) {
@@ -335,8 +390,12 @@ __global__ void __launch_bounds__(kJvThreads, 1)
                 unsigned char *sp = ops + (size_t)s * kJvStageBytes;
                 mbar_expect_tx(&full[s], (uint32_t)kJvStageBytes);
                 tma_load_2d(sp, &mapA, &full[s], kc * kBK, m0);
-#pragma unroll
-                for (int t = 0; t < kJvSB; ++t) tma_load_3d(sp + kAB + t * kBB, &mapB, &full[s], kc * kBK, n0, t);
+                for (int t = t0; t < t0 + per; ++t) {
+                    if (C > 1)
+                        tma_load_3d_mc(sp + kAB + t * kBB, &mapB, &full[s], kc * kBK, n0, t, mask);
+                    else
+                        tma_load_3d(sp + kAB + t * kBB, &mapB, &full[s], kc * kBK, n0, t);
+                }
             }
         }
         if (*abort_flag) {
@@ -348,9 +407,11 @@ __global__ void __launch_bounds__(kJvThreads, 1)
         // ------------------------------------------------------- MMA issuer
         const uint32_t idesc = idesc_bf16(kBM, kBN * kJvSB);
         int64_t g = 0;
-        int64_t committed = -1;  // last tile whose accumulator commit was issued
-        bool any = false;
-        for (int64_t li = 0; li < ntiles && !*abort_flag; ++li) {
+        int64_t committed = -1;  // last unit whose accumulator commit was issued
+        for (int64_t li = 0; li < nunits && !*abort_flag; ++li) {
+            const Tc4Unit u = tc4_unit<kMode>(a, cl + li * ncl, rank);
+            const int kc0 = u.z * a.kc_split;
+            const int kc1 = kc0 + a.kc_split < a.kchunks ? kc0 + a.kc_split : a.kchunks;
             const int b = (int)(li & 1);
             const uint32_t use = (uint32_t)(li >> 1);
             if (use > 0 && !mbar_wait_or_abort(&acc_empty[b], (use - 1) & 1, abort_flag)) {
@@ -359,7 +420,7 @@ __global__ void __launch_bounds__(kJvThreads, 1)
             }
             tc_fence_after();
             bool ok = true;
-            for (int kc = 0; kc < a.kchunks; ++kc, ++g) {
+            for (int kc = kc0; kc < kc1; ++kc, ++g) {
                 const int s = (int)(g % kJvStages);
                 if (!mbar_wait_or_abort(&full[s], (uint32_t)((g / kJvStages) & 1), abort_flag)) {
                     ok = false;
@@ -371,9 +432,12 @@ __global__ void __launch_bounds__(kJvThreads, 1)
 #pragma unroll
                 for (int kk = 0; kk < kBK / 16; ++kk)
                     umma_bf16(tmem + (uint32_t)b * kJvAccCols, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2),
-                              idesc, (kc > 0 || kk > 0) ? 1u : 0u);
-                umma_commit(&empty[s]);
-                any = true;
+                              idesc, (kc > kc0 || kk > 0) ? 1u : 0u);
+                // the stage is free once every CTA of the cluster has read it
+                if (C > 1)
+                    umma_commit_mc(&empty[s], mask);
+                else
+                    umma_commit(&empty[s]);
             }
             umma_commit(&acc_full[b]);
             committed = li;
@@ -382,7 +446,7 @@ __global__ void __launch_bounds__(kJvThreads, 1)
                 break;
             }
         }
-        if (*abort_flag && any && committed >= 0) {
+        if (*abort_flag && committed >= 0) {
             // the MMAs in flight finish before the TMEM is released
             mbar_wait(&acc_full[committed & 1], (uint32_t)((committed >> 1) & 1));
         }
@@ -390,31 +454,35 @@ __global__ void __launch_bounds__(kJvThreads, 1)
         // --------------------------------------------------------- epilogue
         const int q = warp & 3, grp = (warp - 2) >> 2, c0 = grp * 16;
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-        for (int64_t li = 0; li < ntiles; ++li) {
-            const int64_t tile = blockIdx.x + li * gridDim.x;
-            const int64_t m0 = (tile / a.n_nt) * kBM;
-            const int n0 = (int)(tile % a.n_nt) * kBN;
+        for (int64_t li = 0; li < nunits; ++li) {
+            const Tc4Unit u = tc4_unit<kMode>(a, cl + li * ncl, rank);
+            const int64_t m0 = u.mt * kBM;
+            const int n0 = u.nt * kBN;
             const int64_t row = m0 + q * 32 + lane;
             const bool row_ok = row < a.rows;
-            // t' of the warp's 16 columns and their exponents, in flight while the MMAs run
-            double tv[16];
-            int fe[16];
             const int col0 = n0 + c0;
-            if (row_ok && a.vec && col0 + 16 <= a.M) {
-                const double2 *src = reinterpret_cast<const double2 *>(a.T + (size_t)row * a.M + col0);
+            // mode 0: t' of the warp's 16 columns, in flight while the MMAs
+            // run (tile-major pairs: a warp's 32 rows of a column pair are 512
+            // contiguous bytes, one 16-byte load per lane and column pair)
+            float2 tv[16];
+            if (kMode == kTcRowDot) {
+                if (u.mt < n_mt) {
+                    const float4 *src =
+                        a.Thl + (((size_t)u.mt * a.n_nt + u.nt) * (kBN / 2) + (c0 >> 1)) * kBM + q * 32 + lane;
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const double2 v2 = __ldcs(src + j);
-                    tv[2 * j] = v2.x;
-                    tv[2 * j + 1] = v2.y;
-                }
-            } else {
+                    for (int j = 0; j < 8; ++j) {
+                        const float4 v4 = __ldcs(src + (size_t)j * kBM);
+                        tv[2 * j] = make_float2(v4.x, v4.y);
+                        tv[2 * j + 1] = make_float2(v4.z, v4.w);
+                    }
+                } else {
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int col = col0 + j;
-                    tv[j] = !row_ok ? 0.0 : (col < a.M ? a.T[(size_t)row * a.M + col] : (col == a.M ? 1.0 : 0.0));
+                    for (int j = 0; j < 16; ++j) tv[j] = make_float2(0.f, 0.f);
                 }
             }
+            // the warp's column exponents; mode 0 scales them against the
+            // tile's largest one F (lanes cover its 64 columns): 2^(f_j - F)
+            int fe[16];
             {
                 const int4 *ep = reinterpret_cast<const int4 *>(a.expB + col0);
 #pragma unroll
@@ -426,7 +494,21 @@ __global__ void __launch_bounds__(kJvThreads, 1)
                     fe[4 * j + 3] = e4.w;
                 }
 #pragma unroll
-                for (int j = 0; j < 16; ++j) fe[j] = col0 + j < a.cols ? fe[j] - 8 * kJvSB : -100000;
+                for (int j = 0; j < 16; ++j) fe[j] = col0 + j < a.cols ? fe[j] : -100000;
+            }
+            int F = 0;
+            float cs[16];
+            if (kMode == kTcRowDot) {
+                const int ca = n0 + lane, cb = n0 + 32 + lane;
+                const int ea = ca < a.cols ? __ldg(a.expB + ca) : -100000;
+                const int eb = cb < a.cols ? __ldg(a.expB + cb) : -100000;
+                F = __reduce_max_sync(0xffffffffu, ea > eb ? ea : eb);
+                if (F == -100000) F = 0;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int e = fe[j] - F + 127;
+                    cs[j] = e >= 1 ? __int_as_float(e << 23) : 0.f;
+                }
             }
             const int b = (int)(li & 1);
             const uint32_t use = (uint32_t)(li >> 1);
@@ -438,7 +520,31 @@ __global__ void __launch_bounds__(kJvThreads, 1)
                 break;
             }
             tc_fence_after();
-            double r0 = 0.0, r1 = 0.0;
+            if (kMode == kTcStoreT) {
+                // P^T[z][col][row] = V 2^(f_col - 32), exact (|V| < 2^48: K per unit <= 16448)
+                double *dst = a.P + (size_t)u.z * a.split_stride + row;
+#pragma unroll
+                for (int c8 = 0; c8 < 16; c8 += 8) {
+                    uint32_t r[kJvSB][8];
+#pragma unroll
+                    for (int t = 0; t < kJvSB; ++t)
+                        tmem_ld8(tmem + (uint32_t)b * kJvAccCols + lane_base + (uint32_t)(t * kBN + c0 + c8), r[t]);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const long long V = levels4_to_i64(__uint_as_float(r[0][j]), __uint_as_float(r[1][j]),
+                                                           __uint_as_float(r[2][j]), __uint_as_float(r[3][j]));
+                        const int col = col0 + c8 + j;
+                        if (row_ok && col < a.cols) dst[(size_t)col * a.ldp] = exact_to_double(V, fe[c8 + j] - 32);
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acc_empty[b]);
+                continue;
+            }
+            // mode 0.  A: sum of D_0 u (exact pairs); B: sum of D_1 u; sm: the terms below 2^-24
+            float ah = 0.f, al = 0.f, bh = 0.f, bl = 0.f, sm = 0.f;
 #pragma unroll
             for (int c8 = 0; c8 < 16; c8 += 8) {
                 uint32_t r[kJvSB][8];
@@ -447,23 +553,37 @@ __global__ void __launch_bounds__(kJvThreads, 1)
                     tmem_ld8(tmem + (uint32_t)b * kJvAccCols + lane_base + (uint32_t)(t * kBN + c0 + c8), r[t]);
                 tmem_wait_ld();
 #pragma unroll
-                for (int j = 0; j < 8; j += 2) {
-                    const long long V0 = levels4_to_i64(__uint_as_float(r[0][j]), __uint_as_float(r[1][j]),
-                                                        __uint_as_float(r[2][j]), __uint_as_float(r[3][j]));
-                    const long long V1 =
-                        levels4_to_i64(__uint_as_float(r[0][j + 1]), __uint_as_float(r[1][j + 1]),
-                                       __uint_as_float(r[2][j + 1]), __uint_as_float(r[3][j + 1]));
-                    r0 = fma(exact_to_double(V0, fe[c8 + j]), tv[c8 + j], r0);
-                    r1 = fma(exact_to_double(V1, fe[c8 + j + 1]), tv[c8 + j + 1], r1);
+                for (int j = 0; j < 8; ++j) {
+                    const float d0 = __uint_as_float(r[0][j]), d1 = __uint_as_float(r[1][j]);
+                    const float d2 = __uint_as_float(r[2][j]), d3 = __uint_as_float(r[3][j]);
+                    const float u0 = __fmul_rn(tv[c8 + j].x, cs[c8 + j]), ul = __fmul_rn(tv[c8 + j].y, cs[c8 + j]);
+                    const float p0 = __fmul_rn(d0, u0), e0 = __fmaf_rn(d0, u0, -p0);
+                    const float p1 = __fmul_rn(d1, u0), e1 = __fmaf_rn(d1, u0, -p1);
+                    // 2^-24-level: e0 + D_0 ul; 2^-32: (e1 + D_1 ul) 2^-8; 2^-40: (D_2 + D_3 2^-8) u 2^-16
+                    float lo = __fmaf_rn(d0, ul, e0);
+                    lo = __fmaf_rn(__fmaf_rn(d1, ul, e1), 0.00390625f, lo);
+                    lo = __fmaf_rn(__fmaf_rn(d3, 0.00390625f, d2), __fmul_rn(u0, 1.52587890625e-05f), lo);
+                    sm = __fadd_rn(sm, lo);
+                    float s, e;
+                    two_sum(ah, p0, s, e);
+                    ah = s;
+                    al = __fadd_rn(al, e);
+                    two_sum(bh, p1, s, e);
+                    bh = s;
+                    bl = __fadd_rn(bl, e);
                 }
             }
             // the accumulator set is drained: hand it back to the MMA warp
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[b]);
-            // the four column groups of each row meet in the ring slot of this tile
+            // (H, L) = A + B 2^-8 + sm as one FP32 pair
+            float H, L;
+            two_sum(ah, __fmul_rn(bh, 0.00390625f), H, L);
+            L = __fadd_rn(L, __fadd_rn(al, __fmaf_rn(bl, 0.00390625f, sm)));
+            // the four column groups of each row meet in the ring slot of this unit
             const int slot = (int)(li % kJvRing);
-            red[((size_t)slot * 4 + grp) * kBM + q * 32 + lane] = r0 + r1;
+            red[((size_t)slot * 4 + grp) * kBM + q * 32 + lane] = make_float2(H, L);
             __syncwarp();
             if (lane == 0) mbar_arrive(&red_full[slot * 4 + q]);
             if (grp == 0) {
@@ -477,14 +597,30 @@ __global__ void __launch_bounds__(kJvThreads, 1)
                     if (lane == 0) fail(24);
                     break;
                 }
-                const double *rs = red + (size_t)slot * 4 * kBM + q * 32 + lane;
-                const double sum = ((rs[0] + rs[kBM]) + rs[2 * kBM]) + rs[3 * kBM];
-                if (row_ok) a.P[(size_t)(n0 / kBN) * a.rows + row] = sum;
+                const float2 *rs = red + (size_t)slot * 4 * kBM + q * 32 + lane;
+                float sh = rs[0].x, sl = rs[0].y;
+#pragma unroll
+                for (int g2 = 1; g2 < 4; ++g2) {
+                    float s, e;
+                    two_sum(sh, rs[g2 * kBM].x, s, e);
+                    sh = s;
+                    sl = __fadd_rn(sl, __fadd_rn(e, rs[g2 * kBM].y));
+                }
+                // 2^(F - 8) (sh + sl) in FP64 (the power of two by its exponent bits)
+                const int ebias = F - 8 + 1023;
+                const double scale = __longlong_as_double(
+                    ebias < 1 ? 0LL : (ebias > 2046 ? 0x7FF0000000000000LL : (long long)ebias << 52));
+                if (row_ok) a.P[(size_t)u.nt * a.rows + row] = ((double)sh + (double)sl) * scale;
             }
         }
     }
     tc_fence_before();
-    __syncthreads();
+    // no peer multicasts into this CTA's shared memory or arrives on its
+    // barriers after the cluster barrier; then the TMEM goes back
+    if (C > 1)
+        cluster_sync_all();
+    else
+        __syncthreads();
     if (warp == 0) {
         tc_fence_after();
         tmem_dealloc(tmem, 2 * kJvAccCols);
@@ -693,32 +829,85 @@ __global__ void k_colexp_bound(int M, const int *__restrict__ colexpT, const int
 }
 
 // (T' o g')^T sliced: out [SB][M+1][ld], row j, column k, through tiles of
-// 64 k x 32 j (ld is even: each lane writes a BF16 pair per plane).
-__global__ void k_tg_slice(const double *__restrict__ T, const double *__restrict__ gp, int64_t Ns, int M, int SB,
-                           int64_t ld, const int *__restrict__ expo, __nv_bfloat16 *__restrict__ out) {
-    __shared__ double tile[64][33];
+// 64 k x 64 j in shared memory (FP64, row pitch 65).  A warp reads rows of T
+// as 512 contiguous bytes (one 16-byte load per lane), all eight of a
+// thread's loads issued before their first use; it writes BF16 pairs, 128
+// contiguous bytes per plane and row j (ld is even).
+constexpr int kTgPitch = 65;
+__global__ void __launch_bounds__(256) k_tg_slice(const double *__restrict__ T, const double *__restrict__ gp,
+                                                  int64_t Ns, int M, int SB, int64_t ld, int vec,
+                                                  const int *__restrict__ expo, __nv_bfloat16 *__restrict__ out) {
+    __shared__ double tile[64 * kTgPitch];  // [k][j]
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t k0 = (int64_t)blockIdx.x * 64;
-    const int j0 = blockIdx.y * 32;
-    for (int r = threadIdx.y; r < 64; r += blockDim.y) {
-        const int64_t k = k0 + r;
-        const int j = j0 + threadIdx.x;
-        double v = 0.0;
-        if (k < Ns && j <= M) v = (j < M ? T[(size_t)k * M + j] : 1.0) * gp[k];
-        tile[r][threadIdx.x] = v;
+    const int j0 = blockIdx.y * 64;
+    const int jl = 2 * lane, j = j0 + jl;
+    double2 v[8];
+    double gk[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int64_t k = k0 + w + 8 * i;
+        gk[i] = k < Ns ? gp[k] : 0.0;
+        if (k < Ns && vec && j + 1 < M) {
+            v[i] = __ldcs(reinterpret_cast<const double2 *>(T + (size_t)k * M + j));
+        } else {
+            v[i].x = (k < Ns && j < M) ? T[(size_t)k * M + j] : (j == M ? 1.0 : 0.0);
+            v[i].y = (k < Ns && j + 1 < M) ? T[(size_t)k * M + j + 1] : (j + 1 == M ? 1.0 : 0.0);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int r = w + 8 * i;
+        tile[r * kTgPitch + jl] = v[i].x * gk[i];
+        tile[r * kTgPitch + jl + 1] = v[i].y * gk[i];
     }
     __syncthreads();
     const int64_t plane2 = (int64_t)(M + 1) * ld / 2;
-    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-        const int j = j0 + r;
-        const int64_t k = k0 + 2 * threadIdx.x;
-        if (j > M || k >= ld) continue;
-        const int e = expo[j] == -100000 ? 0 : expo[j];
-        const double x0 = k < Ns ? tile[2 * threadIdx.x][r] : 0.0, x1 = k + 1 < Ns ? tile[2 * threadIdx.x + 1][r] : 0.0;
-        slice_pair(x0, x1, e, SB, reinterpret_cast<__nv_bfloat162 *>(out + (size_t)j * ld + k), plane2);
+    const int64_t k = k0 + 2 * lane;
+#pragma unroll 2
+    for (int i = 0; i < 8; ++i) {
+        const int jr = w + 8 * i, jj = j0 + jr;
+        if (jj > M || k >= ld) continue;
+        const int e = expo[jj] == -100000 ? 0 : expo[jj];
+        const double x0 = k < Ns ? tile[(2 * lane) * kTgPitch + jr] : 0.0;
+        const double x1 = k + 1 < Ns ? tile[(2 * lane + 1) * kTgPitch + jr] : 0.0;
+        slice_pair(x0, x1, e, SB, reinterpret_cast<__nv_bfloat162 *>(out + (size_t)jj * ld + k), plane2);
     }
 }
 
-// w[r] = sum_t P[t][r] (tile-major partials of k_jvp4), in tile order.
+// t' = [tanh(theta), 1] as FP32 pairs th = fl32(t), tl = fl32(t - th) (t - th
+// is exact in FP64: th + tl = t within 2^-48 |t|), in the tile order of
+// k_tc4 (mode 0): one block per 128 x 64 tile (row tile mt, column tile nt), stored
+// at ((mt n_nt + nt) 32 + column pair) 128 + row as float4 (th, tl) of the
+// pair's two columns.  Rows >= Ns and columns > M hold 0, column M holds 1.
+// The tile passes through shared memory in FP64 (row pitch 65).
+constexpr int kSplitPitch = kBN + 1;
+__global__ void __launch_bounds__(256) k_split_t(int64_t Ns, int M, int n_nt, const double *__restrict__ T,
+                                                 float4 *__restrict__ out) {
+    extern __shared__ double tile[];  // [128][65]
+    const int nt = blockIdx.x;
+    const int64_t mt = blockIdx.y;
+    const int64_t m0 = mt * kBM;
+    const int n0 = nt * kBN;
+    for (int e = threadIdx.x; e < kBM * kBN; e += blockDim.x) {
+        const int r = e / kBN, c = e % kBN;
+        const int64_t row = m0 + r;
+        const int col = n0 + c;
+        double v = 0.0;
+        if (row < Ns) v = col < M ? __ldcs(T + (size_t)row * M + col) : (col == M ? 1.0 : 0.0);
+        tile[r * kSplitPitch + c] = v;
+    }
+    __syncthreads();
+    float4 *dst = out + ((size_t)mt * n_nt + nt) * (kBN / 2) * kBM;
+    for (int e = threadIdx.x; e < kBM * (kBN / 2); e += blockDim.x) {
+        const int cp = e / kBM, r = e % kBM;
+        const double t0 = tile[r * kSplitPitch + 2 * cp], t1 = tile[r * kSplitPitch + 2 * cp + 1];
+        const float h0 = __double2float_rn(t0), h1 = __double2float_rn(t1);
+        dst[e] = make_float4(h0, __double2float_rn(t0 - (double)h0), h1, __double2float_rn(t1 - (double)h1));
+    }
+}
+
+// w[r] = sum_t P[t][r] (tile-major partials of k_tc4 mode 0), in tile order.
 __global__ void k_rowsum_tiles(int64_t rows, int ntc, const double *__restrict__ P, double *__restrict__ w) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= rows) return;
@@ -734,6 +923,24 @@ __global__ void k_rowsum_partials(int64_t rows, int ntc, const double *__restric
     double acc = 0.0;
     for (int t = 0; t < ntc; ++t) acc += P[(size_t)r * ntc + t];
     w[r] = acc;
+}
+
+// P^T as [ks][M+1][N+1] (column j, row i: k_tc4 mode 1) -> J^T g in the
+// parameter layout, the ks partials summed in order.
+__global__ void k_scatter_vjp_t(int N, int M, int ks, const double *__restrict__ PT, double *__restrict__ out) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t tot = (int64_t)(N + 1) * (M + 1);
+    if (idx >= tot) return;
+    const int j = (int)(idx / (N + 1)), i = (int)(idx % (N + 1));
+    double v = PT[idx];
+    for (int z = 1; z < ks; ++z) v += PT[(size_t)z * tot + idx];
+    if (i == N && j == M) return;
+    if (j == M)
+        out[i] = v;
+    else if (i == N)
+        out[N + j] = v;
+    else
+        out[N + M + (size_t)j * N + i] = v;
 }
 
 // P^T [N+1][M+1] (row i, column j) -> J^T g in the parameter layout; PT
@@ -824,29 +1031,99 @@ cudaError_t sgemm(const __nv_bfloat16 *A, int64_t rows, int64_t ldA, const __nv_
     return cudaGetLastError();
 }
 
-// J v partials P [n_nt][rows] = per 64-column tile, sum_col (A B^T)[row][col]
-// t'_col by k_jvp4 (4 slices; K <= 16448 so that |D_t| <= 255 K < 2^22).
-cudaError_t jvp4(const __nv_bfloat16 *A, int64_t rows, int64_t ldA, const __nv_bfloat16 *Bsl, const int *expB,
-                 int64_t cols, int64_t ldB, int64_t K, const double *T, int Mt, double *P, int *err,
-                 cudaStream_t st) {
-    if (rows <= 0 || cols <= 0 || K <= 0) return cudaSuccess;
-    if (K > 16448 || rows > (1LL << 31) - kBM || cols > (1LL << 31) - kBN || T == nullptr)
-        return cudaErrorInvalidValue;
-    CUtensorMap ma, mb;
-    if (!make_rows_map(&ma, A, rows, K, ldA, kBM) || !make_sliced_map(&mb, Bsl, cols, K, ldB, kJvSB, kBN))
-        return cudaErrorInvalidValue;
-    cudaError_t e = nk::allow_max_dynamic_smem((const void *)k_jvp4);
+// One launch of k_tc4: as many clusters of a.C CTAs as fit at once (one CTA
+// per SM), each walking its units round robin.
+template <int kMode>
+cudaError_t launch_tc4(const CUtensorMap &ma, const CUtensorMap &mb, const Tc4Args &a, cudaStream_t st) {
+    cudaError_t e = nk::allow_max_dynamic_smem((const void *)k_tc4<kMode>);
     int dev = 0, sms = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)a.C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(kJvThreads);
+    cfg.dynamicSmemBytes = jv_smem_bytes();
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int64_t ncl = sms / a.C;
+    if (a.C > 1) {
+        int fit = 0;
+        cfg.gridDim = dim3((unsigned)(ncl * a.C));
+        e = cudaOccupancyMaxActiveClusters(&fit, (const void *)k_tc4<kMode>, &cfg);
+        if (e != cudaSuccess) return e;
+        if (fit >= 1 && fit < ncl) ncl = fit;
+    }
+    if (ncl > a.groups) ncl = a.groups;
+    cfg.gridDim = dim3((unsigned)(ncl * a.C));
+    e = cudaLaunchKernelEx(&cfg, k_tc4<kMode>, ma, mb, a);
+    nk::note_launch();
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+// CTAs per cluster of the J v product (B slices multicast across row tiles).
+constexpr int kJvCluster = 2;
+
+// J v partials P [n_nt][rows] = per 64-column tile, sum_col (A B^T)[row][col]
+// t'_col by k_tc4 mode 0 (4 slices; K <= 65792 keeps the FP32 levels exact).
+cudaError_t jvp4(const __nv_bfloat16 *A, int64_t rows, int64_t ldA, const __nv_bfloat16 *Bsl, const int *expB,
+                 int64_t cols, int64_t ldB, int64_t K, const void *Thl, int Mt, double *P, int *err,
+                 cudaStream_t st) {
+    if (rows <= 0 || cols <= 0 || K <= 0) return cudaSuccess;
+    if (K > 65792 || rows > (1LL << 31) - kBM || cols > (1LL << 31) - kBN || Thl == nullptr)
+        return cudaErrorInvalidValue;
+    if ((reinterpret_cast<uintptr_t>(Thl) & 15) != 0 || Mt + 1 != cols) return cudaErrorInvalidValue;
+    CUtensorMap ma, mb;
+    if (!make_rows_map(&ma, A, rows, K, ldA, kBM) || !make_sliced_map(&mb, Bsl, cols, K, ldB, kJvSB, kBN))
+        return cudaErrorInvalidValue;
     const int n_nt = (int)((cols + kBN - 1) / kBN);
-    const int64_t tiles = (int64_t)n_nt * ((rows + kBM - 1) / kBM);
-    JvArgs a{rows, cols, (int)((K + kBK - 1) / kBK), n_nt, tiles, expB, T, Mt,
-             (Mt % 2 == 0) && ((reinterpret_cast<uintptr_t>(T) & 15) == 0), P, err};
-    const int grid = (int)(tiles < sms ? tiles : sms);
-    (k_jvp4<<<grid, kJvThreads, jv_smem_bytes(), st>>>(ma, mb, a), nk::note_launch());
-    return cudaGetLastError();
+    const int64_t n_mt = (rows + kBM - 1) / kBM;
+    const int C = n_mt >= 2 * kJvCluster ? kJvCluster : 1;
+    const int n_mg = (int)((n_mt + C - 1) / C);
+    const int kchunks = (int)((K + kBK - 1) / kBK);
+    Tc4Args a{rows, cols, kchunks, kchunks, 1, n_nt, n_mg, C, (int64_t)n_mg * n_nt, expB,
+              reinterpret_cast<const float4 *>(Thl), P, 0, 0, err};
+    return launch_tc4<kTcRowDot>(ma, mb, a, st);
+}
+
+// P^T [ks][cols][ldp] (column-major split-K partial products) = A B^T by
+// k_tc4 mode 1, with ks such that a unit is at most 257 K-chunks (|D_t| <=
+// 255 K < 2^22) and the last round of units is nearly full.
+cudaError_t vjp4(const __nv_bfloat16 *A, int64_t rows, int64_t ldA, const __nv_bfloat16 *Bsl, const int *expB,
+                 int64_t cols, int64_t ldB, int64_t K, double *P, int64_t ldp, int64_t split_stride, int max_ks,
+                 int *ks_out, int *err, cudaStream_t st) {
+    if (rows <= 0 || cols <= 0 || K <= 0) return cudaSuccess;
+    if (rows > (1LL << 31) - kBM || cols > (1LL << 31) - kBN || ldp < rows) return cudaErrorInvalidValue;
+    CUtensorMap ma, mb;
+    if (!make_rows_map(&ma, A, rows, K, ldA, kBM) || !make_sliced_map(&mb, Bsl, cols, K, ldB, kJvSB, kBN))
+        return cudaErrorInvalidValue;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int n_nt = (int)((cols + kBN - 1) / kBN);
+    const int n_mt = (int)((rows + kBM - 1) / kBM);
+    const int kchunks = (int)((K + kBK - 1) / kBK);
+    const int ks_min = (kchunks + 256) / 257;
+    if (ks_min > max_ks) return cudaErrorInvalidValue;
+    int ks = ks_min;
+    double best = -1.0;
+    for (int k = ks_min; k <= max_ks; ++k) {
+        const int64_t units = (int64_t)n_mt * n_nt * k, rounds = (units + sms - 1) / sms;
+        const double score = (double)units / (double)(rounds * sms) - 0.01 * (k - ks_min);
+        if (score > best + 1e-12) best = score, ks = k;
+    }
+    const int kc_split = (kchunks + ks - 1) / ks;
+    ks = (kchunks + kc_split - 1) / kc_split;
+    *ks_out = ks;
+    Tc4Args a{rows, cols, kchunks, kc_split, ks, n_nt, n_mt, 1, (int64_t)n_mt * n_nt * ks, expB, nullptr, P, ldp,
+              split_stride, err};
+    return launch_tc4<kTcStoreT>(ma, mb, a, st);
 }
 
 double sgemm_flops(int64_t rows, int64_t cols, int64_t K, int SB) {
@@ -890,7 +1167,24 @@ size_t tc_jvp_ws_bytes(int N, int M, int64_t Ns) {
     const int64_t ld = pad8(N + 1), ntc = (M + 1 + kBN - 1) / kBN;
     return ((size_t)Ns * ld * 2 + 255) / 256 * 256 + ((size_t)kMaxSB * (M + 1) * ld * 2 + 255) / 256 * 256 +
            ((size_t)(M + 1) * (N + 1) * 8 + 255) / 256 * 256 + ((size_t)(M + 1) * 4 + 255) / 256 * 256 +
-           ((size_t)Ns * ntc * 8 + 255) / 256 * 256 + 256;
+           ((size_t)Ns * ntc * 8 + 255) / 256 * 256 + tc_split_t_bytes(M, Ns) + 256;
+}
+
+size_t tc_split_t_bytes(int M, int64_t Ns) {
+    return (size_t)((Ns + kBM - 1) / kBM) * kBM * (size_t)((M + 1 + kBN - 1) / kBN) * kBN * sizeof(float2);
+}
+
+cudaError_t launch_split_t(int M, int64_t Ns, const double *T, void *Thl, cudaStream_t st) {
+    if (Ns <= 0) return cudaSuccess;
+    const int n_nt = (M + 1 + kBN - 1) / kBN;
+    const int64_t n_mt = (Ns + kBM - 1) / kBM;
+    if (n_mt > 65535) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)kBM * kSplitPitch * sizeof(double);
+    cudaError_t e = nk::allow_max_dynamic_smem((const void *)k_split_t);
+    if (e != cudaSuccess) return e;
+    (k_split_t<<<dim3(n_nt, (unsigned)n_mt), 256, smem, st>>>(Ns, M, n_nt, T, static_cast<float4 *>(Thl)),
+     nk::note_launch());
+    return cudaGetLastError();
 }
 
 size_t tc_jvp_operand_bytes(int N, int64_t Ns) { return (size_t)Ns * pad8(N + 1) * 2; }
@@ -910,7 +1204,8 @@ cudaError_t launch_jacobian_operands(int N, int64_t Ns, const int8_t *s, void *o
 // out = J v with V' cut into SB slices: w = rowdot(T', S' V'^T), the row
 // products taken in the S-GEMM epilogue per 64-column tile and summed after.
 cudaError_t launch_jvp_tc(int N, int M, int64_t Ns, const int8_t *s, const double *T, const double *v,
-                          double *out, int SB, int *err, void *ws, cudaStream_t st, const void *opA) {
+                          double *out, int SB, int *err, void *ws, cudaStream_t st, const void *opA,
+                          const void *Thl) {
     const int64_t ld = pad8(N + 1);
     char *p = static_cast<char *>(ws);
     auto take = [&](size_t bytes) {
@@ -931,9 +1226,15 @@ cudaError_t launch_jvp_tc(int N, int M, int64_t Ns, const int8_t *s, const doubl
         (k_pm1_rows<<<nblk(Ns * ld, 256), 256, 0, st>>>(s, Ns, N, 1, ld, As), nk::note_launch());
     (k_build_vaug<<<nblk(tot, 256), 256, 0, st>>>(N, M, v, Vp), nk::note_launch());
     (k_slice_long_rows<<<M + 1, 128, 0, st>>>(Vp, N + 1, M + 1, N + 1, nullptr, SB, ld, Vs, ev), nk::note_launch());
-    const bool persistent = SB == kJvSB && N + 1 <= 16448;
+    const bool persistent = SB == kJvSB && N + 1 <= 65792;
+    if (persistent && Thl == nullptr) {
+        void *own = take(tc_split_t_bytes(M, Ns));
+        cudaError_t es = launch_split_t(M, Ns, T, own, st);
+        if (es != cudaSuccess) return es;
+        Thl = own;
+    }
     const int slot = prof_begin(NK_PROF_JVP_VJP, st);
-    cudaError_t e = persistent ? jvp4(As, Ns, ld, Vs, ev, M + 1, ld, N + 1, T, M, P, err, st)
+    cudaError_t e = persistent ? jvp4(As, Ns, ld, Vs, ev, M + 1, ld, N + 1, Thl, M, P, err, st)
                                : sgemm(As, Ns, ld, Vs, ev, M + 1, ld, N + 1, SB, P, ntc, 3, nullptr, err, st, T, M);
     prof_end(slot, st, 2.0 * (double)Ns * (N + 1) * (double)(M + 1), sgemm_flops(Ns, M + 1, N + 1, SB));
     if (e != cudaSuccess) return e;
@@ -1014,7 +1315,8 @@ cudaError_t launch_vjp_tc(int N, int M, int64_t Ns, const int8_t *s, const doubl
         (k_tg_colexp<<<dim3(nblk(M + 1, 32), nblk(Ns, 256)), dim3(32, 8), 0, st>>>(T, ge, Ns, M, eg),
          nk::note_launch());
     }
-    (k_tg_slice<<<dim3(nblk(ld, 64), nblk(M + 1, 32)), tb, 0, st>>>(T, gp, Ns, M, SB, ld, eg, Gs),
+    const int vec = (M % 2 == 0) && ((reinterpret_cast<uintptr_t>(T) & 15) == 0);
+    (k_tg_slice<<<dim3(nblk(ld, 64), nblk(M + 1, 64)), 256, 0, st>>>(T, gp, Ns, M, SB, ld, vec, eg, Gs),
      nk::note_launch());
     // split the long K = Ns range so that the last wave of CTAs is nearly
     // full (every split keeps >= 4 chunks; each split's FP32 levels stay exact)
@@ -1026,10 +1328,20 @@ cudaError_t launch_vjp_tc(int N, int M, int64_t Ns, const int8_t *s, const doubl
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sgemm, kSgThreads, sgemm_smem_bytes(SB));
     if (e != cudaSuccess) return e;
     const int64_t tiles = (int64_t)nblk(M + 1, kBN) * nblk(N + 1, kBM), kchunks = (Ns + kBK - 1) / kBK;
+    const int64_t tot = (int64_t)(N + 1) * (M + 1);
+    if (SB == kJvSB && (kchunks + 256) / 257 <= kMaxKSplit) {
+        // the persistent 4-slice kernel, P^T column-major
+        int ks4 = 1;
+        const int slot = prof_begin(NK_PROF_JVP_VJP, st);
+        e = vjp4(St, N + 1, ld, Gs, eg, M + 1, ld, Ns, PT, N + 1, tot, kMaxKSplit, &ks4, err, st);
+        prof_end(slot, st, 2.0 * (double)Ns * (N + 1) * (double)(M + 1), sgemm_flops(N + 1, M + 1, Ns, SB));
+        if (e != cudaSuccess) return e;
+        (k_scatter_vjp_t<<<nblk(tot, 256), 256, 0, st>>>(N, M, ks4, PT, out), nk::note_launch());
+        return cudaGetLastError();
+    }
     int ks = pick_ksplit(tiles, kchunks, (int64_t)sms * (per_sm > 0 ? per_sm : 1));
     const int kc_split = (int)((kchunks + ks - 1) / ks);
     ks = (int)((kchunks + kc_split - 1) / kc_split);  // splits the kernel launches
-    const int64_t tot = (int64_t)(N + 1) * (M + 1);
     const int slot = prof_begin(NK_PROF_JVP_VJP, st);
     e = sgemm(St, N + 1, ld, Gs, eg, M + 1, ld, Ns, SB, PT, M + 1, 0, nullptr, err, st, nullptr, 0, ks, tot);
     prof_end(slot, st, 2.0 * (double)Ns * (N + 1) * (double)(M + 1), sgemm_flops(N + 1, M + 1, Ns, SB));

@@ -207,7 +207,8 @@ struct SolveWs {
     int *colexpT;     // NK_MIXED CG: column exponents of tanh(theta), [M + 1]
     void *colexp_ws;
     void *opA, *opT;  // NK_MIXED CG: the +-1 product operands, built once per solve
-    bool ops_ready;   // opA / opT hold the operands of the samples being solved for
+    void *thl;        // NK_MIXED CG: tanh(theta) as FP32 pairs, built once per solve
+    bool ops_ready;   // opA / opT / thl hold the operands of the samples being solved for
     int *tcerr; // sticky tensor-core error word of the context
 };
 
@@ -236,6 +237,7 @@ void carve_solve(Carver &c, SolveWs &w, int N, int M, int64_t Ns, int solver, in
             w.colexp_ws = c.take<char>(nk::tc_colexp_ws_bytes(M, Ns));
             w.opA = c.take<char>(nk::tc_jvp_operand_bytes(N, Ns));
             w.opT = c.take<char>(nk::tc_vjp_operand_bytes(N, Ns));
+            w.thl = c.take<char>(nk::tc_split_t_bytes(M, Ns));
         }
     } else if (solver == NK_SOLVER_CHOLESKY) {
         w.dJ = c.take<double>((size_t)Ns * Np);
@@ -292,7 +294,8 @@ constexpr double kJacobiTol = 1e-14;
 cudaError_t jvp_any(int N, int M, int64_t Ns, const int8_t *s, const double *T, const double *v, SolveWs &w,
                     double *out, int precision, int slices, cudaStream_t st) {
     if (precision == NK_MIXED)
-        return nk::launch_jvp_tc(N, M, Ns, s, T, v, out, slices, w.tcerr, w.tcm, st, w.ops_ready ? w.opA : nullptr);
+        return nk::launch_jvp_tc(N, M, Ns, s, T, v, out, slices, w.tcerr, w.tcm, st, w.ops_ready ? w.opA : nullptr,
+                                 w.ops_ready ? w.thl : nullptr);
     return nk::launch_jvp(N, M, Ns, s, T, v, w.U, out, st);
 }
 
@@ -362,6 +365,7 @@ nk_status run_solve(nk_ctx *ctx, int N, int M, int64_t Ns, const int8_t *s, cons
         if (tc) {
             NK_CU(nk::launch_colexp_t(M, Ns, T, w.colexpT, w.colexp_ws, st), "cg exponents");
             NK_CU(nk::launch_jacobian_operands(N, Ns, s, w.opA, w.opT, st), "cg operands");
+            NK_CU(nk::launch_split_t(M, Ns, T, w.thl, st), "cg operands");
         }
         // the operands stay valid for this solve's samples only
         struct OpsReady {

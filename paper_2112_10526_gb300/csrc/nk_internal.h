@@ -219,10 +219,16 @@ cudaError_t launch_theta_tc(int N, int M, const double *b, const double *W, cons
 size_t tc_jvp_operand_bytes(int N, int64_t Ns);
 size_t tc_vjp_operand_bytes(int N, int64_t Ns);
 cudaError_t launch_jacobian_operands(int N, int64_t Ns, const int8_t *s, void *opA, void *opT, cudaStream_t st);
+// t' = [tanh(theta), 1] as FP32 pairs (hi, lo) in the tile order of the
+// 4-slice J v kernel; fixed during a solve, so CG builds it once.
+size_t tc_split_t_bytes(int M, int64_t Ns);
+cudaError_t launch_split_t(int M, int64_t Ns, const double *T, void *Thl, cudaStream_t st);
 size_t tc_jvp_ws_bytes(int N, int M, int64_t Ns);
-// opA (optional): the prebuilt J v operand of launch_jacobian_operands.
+// opA (optional): the prebuilt J v operand of launch_jacobian_operands;
+// Thl (optional): the pairs of launch_split_t for T (else built in ws).
 cudaError_t launch_jvp_tc(int N, int M, int64_t Ns, const int8_t *s, const double *T, const double *v,
-                          double *out, int SB, int *err, void *ws, cudaStream_t st, const void *opA = nullptr);
+                          double *out, int SB, int *err, void *ws, cudaStream_t st, const void *opA = nullptr,
+                          const void *Thl = nullptr);
 size_t tc_vjp_ws_bytes(int N, int M, int64_t Ns);
 // colexpT (optional, [M + 1], from launch_colexp_t): the column exponents of
 // tanh(theta), so that the slices of (T' o g')^T take their exponents from
