@@ -725,6 +725,15 @@ __device__ __forceinline__ void slice_pair(double x0, double x1, int e, int SB, 
     }
 }
 
+// The 4-slice case of slice_pair (grid32 and bf16_digit_pair, tc_ptx.cuh).
+__device__ __forceinline__ void slice_pair4(double x0, double x1, int e, uint32_t *out, int64_t plane2) {
+    uint32_t s0, s1;
+    const uint32_t y0 = grid32(x0, e, s0), y1 = grid32(x1, e, s1);
+    const uint32_t sg = (s0 << 15) | (s1 << 31);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) out[(size_t)t * plane2] = bf16_digit_pair(y0, y1, 3u - (uint32_t)t, sg);
+}
+
 // Rows of a row-major FP64 matrix (row r, column k: X[r * ldx + k] for k < K;
 // with augment, column K holds aug[r] and the operand has K + 1 columns) ->
 // SB slices [SB][rows][ld] with one exponent per row.  One block per row.
@@ -871,7 +880,10 @@ __global__ void __launch_bounds__(256) k_tg_slice(const double *__restrict__ T, 
         const int e = expo[jj] == -100000 ? 0 : expo[jj];
         const double x0 = k < Ns ? tile[(2 * lane) * kTgPitch + jr] : 0.0;
         const double x1 = k + 1 < Ns ? tile[(2 * lane + 1) * kTgPitch + jr] : 0.0;
-        slice_pair(x0, x1, e, SB, reinterpret_cast<__nv_bfloat162 *>(out + (size_t)jj * ld + k), plane2);
+        if (SB == 4)
+            slice_pair4(x0, x1, e, reinterpret_cast<uint32_t *>(out + (size_t)jj * ld + k), plane2);
+        else
+            slice_pair(x0, x1, e, SB, reinterpret_cast<__nv_bfloat162 *>(out + (size_t)jj * ld + k), plane2);
     }
 }
 

@@ -335,6 +335,60 @@ __host__ __device__ __forceinline__ double exact_to_double(long long V, int sc) 
     return v;
 }
 
+// 4-slice digits with 32-bit integer operations.  grid32: y = trunc(|x|
+// 2^(32 - e)) for |x| < 2^e is the top 32 bits of the mantissa (implicit one
+// included) shifted right by 1022 + e - (biased exponent); the 21 dropped
+// mantissa bits cannot carry into the truncated value.  Subnormal x give 0.
+// bf16_digit_pair: byte `byte` of y0 and of y1 as the low and high BF16 of a
+// pair, exactly (a byte d becomes the float 2^23 + d by its bit pattern,
+// minus 2^23, whose upper 16 bits are the BF16 of d), signs OR-ed in.
+__host__ __device__ __forceinline__ uint32_t byte_perm_any(uint32_t x, uint32_t y, uint32_t s) {
+#ifdef __CUDA_ARCH__
+    return __byte_perm(x, y, s);
+#else
+    const unsigned long long v = ((unsigned long long)y << 32) | x;
+    uint32_t r = 0;
+    for (int i = 0; i < 4; ++i) r |= (uint32_t)((v >> (8 * ((s >> (4 * i)) & 7))) & 0xFFu) << (8 * i);
+    return r;
+#endif
+}
+
+__host__ __device__ __forceinline__ uint32_t grid32(double x, int e, uint32_t &sgn) {
+    unsigned long long b;
+#ifdef __CUDA_ARCH__
+    b = (unsigned long long)__double_as_longlong(x);
+#else
+    __builtin_memcpy(&b, &x, 8);
+#endif
+    const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+    sgn = hi >> 31;
+    const int be = (int)((hi >> 20) & 0x7FFu);
+    const uint32_t top = (((hi & 0xFFFFFu) | 0x100000u) << 11) | (lo >> 21);
+    const int rs = 1022 + e - be;  // >= 0 for |x| < 2^e
+    return (be == 0 || rs >= 32) ? 0u : (rs <= 0 ? top : top >> rs);
+}
+
+__host__ __device__ __forceinline__ uint32_t bf16_digit_pair(uint32_t y0, uint32_t y1, uint32_t byte,
+                                                             uint32_t sgnmask) {
+    const uint32_t sel = 0x7540u | byte;  // bytes: y.b[byte], 0, 0, 0x4B
+    const uint32_t u0 = byte_perm_any(y0, 0x4B000000u, sel), u1 = byte_perm_any(y1, 0x4B000000u, sel);
+    float f0, f1;
+#ifdef __CUDA_ARCH__
+    f0 = __fsub_rn(__uint_as_float(u0), 8388608.0f);
+    f1 = __fsub_rn(__uint_as_float(u1), 8388608.0f);
+    return __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632u) | sgnmask;
+#else
+    __builtin_memcpy(&f0, &u0, 4);
+    __builtin_memcpy(&f1, &u1, 4);
+    f0 -= 8388608.0f;
+    f1 -= 8388608.0f;
+    uint32_t v0, v1;
+    __builtin_memcpy(&v0, &f0, 4);
+    __builtin_memcpy(&v1, &f1, 4);
+    return byte_perm_any(v0, v1, 0x7632u) | sgnmask;
+#endif
+}
+
 // ------------------------------------------------------ host: tensor maps ---
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,

@@ -8,7 +8,9 @@ host, against exact 128-bit integer arithmetic:
   zero, a signed zero below 2^-1022 and an infinity from 2^1024 on;
 * levels4_to_i64 is D_0 2^24 + D_1 2^16 + D_2 2^8 + D_3 for FP32 levels up
   to 2^22 in magnitude, and exact_to_double(V, sc) is V 2^sc (no rounding for
-  |V| < 2^53) with the same flush and saturation.
+  |V| < 2^53) with the same flush and saturation;
+* grid32(x, e) is trunc(|x| 2^(32 - e)) for |x| < 2^e, and bf16_digit_pair
+  the exact BF16 of one byte of each of two such values.
 
 The routines are __host__ __device__; the test compiles them with g++ from
 the header itself."""
@@ -156,8 +158,38 @@ int main() {
             ++bad;
         }
     }
+    // 6. the 4-slice digits: grid32 is trunc(|x| 2^(32 - e)) (ldexp is exact
+    //    here), bf16_digit_pair the BF16 of a byte of each of two such values
+    for (long it = 0; it < 1000000; ++it) {
+        const int e = (int)(g() %% 200) - 100;
+        const int bl = (int)(g() %% 70);  // |x| / 2^e from 2^-70 up to just below 1
+        double x = ldexp((double)(g() >> 11) / 9007199254740992.0, e - bl);
+        if (g() & 1) x = -x;
+        if (!(fabs(x) < ldexp(1.0, e))) continue;
+        uint32_t sg;
+        const uint32_t y = grid32(x, e, sg);
+        const uint32_t want = (uint32_t)floor(ldexp(fabs(x), 32 - e));
+        ++n;
+        if (y != want || sg != (std::signbit(x) ? 1u : 0u)) {
+            if (bad < 5) printf("grid32 x=%%a e=%%d got %%u want %%u\n", x, e, y, want);
+            ++bad;
+        }
+        const uint32_t y1 = (uint32_t)(g() >> 32);
+        for (uint32_t byte = 0; byte < 4; ++byte) {
+            const uint32_t pr = bf16_digit_pair(y, y1, byte, 0x80000000u);
+            const uint32_t lo = pr & 0xFFFFu, hi2 = pr >> 16;
+            float flo, fhi;
+            const uint32_t blo = lo << 16, bhi = hi2 << 16;
+            memcpy(&flo, &blo, 4);
+            memcpy(&fhi, &bhi, 4);
+            if (flo != (float)((y >> (8 * byte)) & 255u) || fhi != -(float)((y1 >> (8 * byte)) & 255u)) {
+                if (bad < 5) printf("digit pair byte %%u of %%u %%u\n", byte, y, y1);
+                ++bad;
+            }
+        }
+    }
     printf("checked %%ld bad %%ld\n", n, bad);
-    return bad != 0 || n < 6000000;
+    return bad != 0 || n < 6900000;
 }
 """
 
@@ -165,7 +197,7 @@ int main() {
 def _extract():
     src = open(HEADER).read()
     a = src.index("__host__ __device__ __forceinline__ int clz64_any")
-    b = src.index("\n}\n", src.index("double exact_to_double(")) + 3
+    b = src.index("\n}\n", src.index("uint32_t bf16_digit_pair(")) + 3
     return src[a:b]
 
 
