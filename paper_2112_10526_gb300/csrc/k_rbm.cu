@@ -208,6 +208,48 @@ __device__ __forceinline__ Prod<float> lane_product4(const float *__restrict__ t
     float m0 = 1.f, m1 = 1.f;
     int e = 0;
     int j = 4 * lane;
+    // Large M reads the tau row from L2, one round trip per group of four
+    // 16-byte loads: a ring of three groups keeps the loads of the next two
+    // in flight while one is multiplied (software pipelining; the products
+    // and renormalisations run in the order of the plain loop below, so the
+    // result is the same).
+    if (!kSharedTau && M >= 6 * 512) {
+        const int full = (M - 4 * lane - 3 * 128 + 511) / 512;  // groups with j + 384 < M (>= 5 here)
+        float4 r0[4], r1[4], r2[4];
+        auto load = [&](float4 (&r)[4], int g) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) r[u] = load_tau4<kSharedTau>(tau + j + g * 512 + u * 128);
+        };
+        auto mul = [&](const float4 (&uv)[4], int g) {
+            float4 tv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) tv[u] = *reinterpret_cast<const float4 *>(t + j + g * 512 + u * 128);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                m0 *= fmaf(-si * tv[u].x, uv[u].x, 1.f) * fmaf(-si * tv[u].y, uv[u].y, 1.f);
+                m1 *= fmaf(-si * tv[u].z, uv[u].z, 1.f) * fmaf(-si * tv[u].w, uv[u].w, 1.f);
+            }
+            int k0, k1;
+            m0 = frexpf(m0, &k0);
+            m1 = frexpf(m1, &k1);
+            e += k0 + k1;
+        };
+        load(r0, 0);
+        load(r1, 1);
+        int g = 0;
+        for (; g + 2 < full; g += 3) {
+            load(r2, g + 2);
+            mul(r0, g);
+            if (g + 3 < full) load(r0, g + 3);
+            mul(r1, g + 1);
+            if (g + 4 < full) load(r1, g + 4);
+            mul(r2, g + 2);
+        }
+        // one or two groups left, already in r0 / r1
+        if (g < full) mul(r0, g++);
+        if (g < full) mul(r1, g++);
+        j += g * 512;
+    }
     // groups of four 16-byte loads in flight (large M reads the tau row from L2),
     // renormalised after each group as before
     for (; j + 3 * 128 < M; j += 4 * 128) {
