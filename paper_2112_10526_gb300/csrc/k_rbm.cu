@@ -202,20 +202,20 @@ __device__ __forceinline__ float4 load_tau4(const float *tau) {
     return __ldg(reinterpret_cast<const float4 *>(tau));
 }
 
-template <bool kSharedTau = false>
+template <bool kSharedTau = false, bool kRing = false>
 __device__ __forceinline__ Prod<float> lane_product4(const float *__restrict__ t, const float *__restrict__ tau,
                                                      float si, int lane, int M) {
     float m0 = 1.f, m1 = 1.f;
     int e = 0;
     int j = 4 * lane;
     // Large M reads the tau row from L2, one round trip per group of four
-    // 16-byte loads: a ring of three groups keeps the loads of the next two
+    // 16-byte loads: a ring of four groups keeps the loads of the next three
     // in flight while one is multiplied (software pipelining; the products
     // and renormalisations run in the order of the plain loop below, so the
     // result is the same).
-    if (!kSharedTau && M >= 6 * 512) {
+    if (kRing && !kSharedTau && M >= 6 * 512) {
         const int full = (M - 4 * lane - 3 * 128 + 511) / 512;  // groups with j + 384 < M (>= 5 here)
-        float4 r0[4], r1[4], r2[4];
+        float4 r0[4], r1[4], r2[4], r3[4];
         auto load = [&](float4 (&r)[4], int g) {
 #pragma unroll
             for (int u = 0; u < 4; ++u) r[u] = load_tau4<kSharedTau>(tau + j + g * 512 + u * 128);
@@ -236,18 +236,22 @@ __device__ __forceinline__ Prod<float> lane_product4(const float *__restrict__ t
         };
         load(r0, 0);
         load(r1, 1);
+        load(r2, 2);
         int g = 0;
-        for (; g + 2 < full; g += 3) {
-            load(r2, g + 2);
+        for (; g + 3 < full; g += 4) {
+            load(r3, g + 3);
             mul(r0, g);
-            if (g + 3 < full) load(r0, g + 3);
+            if (g + 4 < full) load(r0, g + 4);
             mul(r1, g + 1);
-            if (g + 4 < full) load(r1, g + 4);
+            if (g + 5 < full) load(r1, g + 5);
             mul(r2, g + 2);
+            if (g + 6 < full) load(r2, g + 6);
+            mul(r3, g + 3);
         }
-        // one or two groups left, already in r0 / r1
+        // up to three groups left, already in r0 / r1 / r2
         if (g < full) mul(r0, g++);
         if (g < full) mul(r1, g++);
+        if (g < full) mul(r2, g++);
         j += g * 512;
     }
     // groups of four 16-byte loads in flight (large M reads the tau row from L2),
@@ -281,14 +285,16 @@ __device__ __forceinline__ Prod<float> lane_product4(const float *__restrict__ t
     return p;
 }
 
-template <typename R>
-__device__ __forceinline__ Prod<R> unit_lanes_product(const R *t, const R *tau, R si, int lane, int M, bool vec4) {
-    return strided_product<R>(t, tau, 1, si, lane, 32, M);
+template <bool kRing>
+__device__ __forceinline__ Prod<double> unit_lanes_product(const double *t, const double *tau, double si, int lane,
+                                                           int M, bool vec4) {
+    return strided_product<double>(t, tau, 1, si, lane, 32, M);
 }
-template <>
-__device__ __forceinline__ Prod<float> unit_lanes_product<float>(const float *t, const float *tau, float si, int lane,
-                                                                 int M, bool vec4) {
-    return vec4 ? lane_product4(t, tau, si, lane, M) : strided_product<float>(t, tau, 1, si, lane, 32, M);
+template <bool kRing>
+__device__ __forceinline__ Prod<float> unit_lanes_product(const float *t, const float *tau, float si, int lane, int M,
+                                                          bool vec4) {
+    return vec4 ? lane_product4<false, kRing>(t, tau, si, lane, M)
+                : strided_product<float>(t, tau, 1, si, lane, 32, M);
 }
 
 // lane_product4 on a tau row already held in registers: uv[u] is the chunk j
@@ -403,8 +409,11 @@ struct SweepK {
 // broadcast them one per proposal.  kHam: the Hamiltonian rule, whose edge
 // depends on the state (a separate instantiation keeps the registers of the
 // local and exchange rules as they are).
-template <typename R, bool kHam>
-__global__ void __launch_bounds__(128) k_sweep(SweepK<R> P) {
+// kRing: the FP32 form with the pipelined tau loads (M >= 3072), given the
+// registers of 3 blocks of 4 warps per SM (what shared memory allows there);
+// otherwise the registers of 7 blocks, for the small-M occupancy.
+template <typename R, bool kHam, bool kRing>
+__global__ void __launch_bounds__(128, kRing ? 3 : 7) k_sweep(SweepK<R> P) {
     extern __shared__ __align__(16) unsigned char sm[];
     const Tables<R> &T = P.t;
     const SweepArgs &A = P.a;
@@ -521,7 +530,7 @@ __global__ void __launch_bounds__(128) k_sweep(SweepK<R> P) {
             }
             const Acc d0 = Acc(-2) * aa * (Acc)sv[i];
             const R si = (R)sv[i];
-            Prod<R> pr = unit_lanes_product<R>(t, tau, si, lane, M, P.vec4);
+            Prod<R> pr = unit_lanes_product<kRing>(t, tau, si, lane, M, P.vec4);
             pr = warp_prod_normalised(pr);
             const Acc delta = d0 + (Acc)(K + prod_log(pr));
             const bool accept = lu < Acc(2) * delta + corr;
@@ -1138,15 +1147,21 @@ cudaError_t launch_sweep(const Tables<R> &t, const SweepArgs &a, cudaStream_t st
     size_t smem = (size_t)wpb * P.warp_bytes;
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
     const bool ham = a.rule == NK_RULE_HAMILTONIAN;
-    const void *fn = ham ? (const void *)k_sweep<R, true> : (const void *)k_sweep<R, false>;
+    const bool ring = sizeof(R) == 4 && P.vec4 && t.M >= 6 * 512;
+    const void *fn = ham ? (ring ? (const void *)k_sweep<R, true, true> : (const void *)k_sweep<R, true, false>)
+                         : (ring ? (const void *)k_sweep<R, false, true> : (const void *)k_sweep<R, false, false>);
     cudaError_t err = nk::allow_max_dynamic_smem(fn);
     if (err != cudaSuccess) return err;
     unsigned grid = (unsigned)((a.C + wpb - 1) / wpb);
     const int slot = prof_begin(NK_PROF_SWEEP, st);
-    if (ham)
-        (k_sweep<R, true><<<grid, 32 * wpb, smem, st>>>(P), nk::note_launch());
+    if (ham && ring)
+        (k_sweep<R, true, true><<<grid, 32 * wpb, smem, st>>>(P), nk::note_launch());
+    else if (ham)
+        (k_sweep<R, true, false><<<grid, 32 * wpb, smem, st>>>(P), nk::note_launch());
+    else if (ring)
+        (k_sweep<R, false, true><<<grid, 32 * wpb, smem, st>>>(P), nk::note_launch());
     else
-        (k_sweep<R, false><<<grid, 32 * wpb, smem, st>>>(P), nk::note_launch());
+        (k_sweep<R, false, false><<<grid, 32 * wpb, smem, st>>>(P), nk::note_launch());
     prof_end(slot, st, (double)a.C * (a.n_discard + a.n_samples) * t.N * (double)t.M);
     return cudaGetLastError();
 }
