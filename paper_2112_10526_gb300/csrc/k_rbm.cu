@@ -542,16 +542,28 @@ __global__ void __launch_bounds__(128, kRing ? 3 : 7) k_sweep(SweepK<R> P) {
                     float *tf = reinterpret_cast<float *>(t);
                     const float *uf = reinterpret_cast<const float *>(tau);
                     const float sf = (float)si;
-                    for (int j = 4 * lane; j < M; j += 128) {
-                        float4 tv = *reinterpret_cast<const float4 *>(tf + j);
-                        const float4 uv = __ldg(reinterpret_cast<const float4 *>(uf + j));
+                    auto upd = [&](float4 tv, const float4 &uv, int j) {
                         const float v0 = sf * uv.x, v1 = sf * uv.y, v2 = sf * uv.z, v3 = sf * uv.w;
                         tv.x = __fdividef(tv.x - v0, fmaf(-tv.x, v0, 1.f));
                         tv.y = __fdividef(tv.y - v1, fmaf(-tv.y, v1, 1.f));
                         tv.z = __fdividef(tv.z - v2, fmaf(-tv.z, v2, 1.f));
                         tv.w = __fdividef(tv.w - v3, fmaf(-tv.w, v3, 1.f));
                         *reinterpret_cast<float4 *>(tf + j) = tv;
+                    };
+                    // the row again in groups of four 16-byte loads (one round
+                    // trip per group where it has left L1)
+                    int j = 4 * lane;
+                    for (; j + 3 * 128 < M; j += 4 * 128) {
+                        float4 uv[4], tv[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) uv[u] = __ldg(reinterpret_cast<const float4 *>(uf + j + u * 128));
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) tv[u] = *reinterpret_cast<const float4 *>(tf + j + u * 128);
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) upd(tv[u], uv[u], j + u * 128);
                     }
+                    for (; j < M; j += 128)
+                        upd(*reinterpret_cast<const float4 *>(tf + j), __ldg(reinterpret_cast<const float4 *>(uf + j)), j);
                 } else {
                     for (int j = lane; j < M; j += 32) {
                         const R tj = t[j], tv = si * tau[j];
