@@ -202,28 +202,56 @@ __device__ __forceinline__ float4 load_tau4(const float *tau) {
     return __ldg(reinterpret_cast<const float4 *>(tau));
 }
 
+// A lane's tau row in groups g of four 16-byte loads (units j0 + 512 g + 128
+// u, u < 4), for g = 0 .. full - 1: f(uv, g) runs on each group in order,
+// while a ring of four keeps the loads of the next three groups in flight
+// (large M reads the row from L2, one round trip per group otherwise).
+// Returns full.
+template <class F>
+__device__ __forceinline__ int tau_ring4(const float *__restrict__ tau, int j0, int full, F &&f) {
+    float4 r0[4], r1[4], r2[4], r3[4];
+    auto load = [&](float4 (&r)[4], int g) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) r[u] = __ldg(reinterpret_cast<const float4 *>(tau + j0 + g * 512 + u * 128));
+    };
+    if (0 < full) load(r0, 0);
+    if (1 < full) load(r1, 1);
+    if (2 < full) load(r2, 2);
+    int g = 0;
+    for (; g + 3 < full; g += 4) {
+        load(r3, g + 3);
+        f(r0, g);
+        if (g + 4 < full) load(r0, g + 4);
+        f(r1, g + 1);
+        if (g + 5 < full) load(r1, g + 5);
+        f(r2, g + 2);
+        if (g + 6 < full) load(r2, g + 6);
+        f(r3, g + 3);
+    }
+    // up to three groups left, already in r0 / r1 / r2
+    if (g < full) f(r0, g++);
+    if (g < full) f(r1, g++);
+    if (g < full) f(r2, g++);
+    return g;
+}
+
+// groups of four units (j + 384 < M) of the lane starting at unit j
+__device__ __forceinline__ int lane_groups(int M, int j) { return M - j - 3 * 128 > 0 ? (M - j - 3 * 128 + 511) / 512 : 0; }
+
 template <bool kSharedTau = false, bool kRing = false>
 __device__ __forceinline__ Prod<float> lane_product4(const float *__restrict__ t, const float *__restrict__ tau,
                                                      float si, int lane, int M) {
     float m0 = 1.f, m1 = 1.f;
     int e = 0;
     int j = 4 * lane;
-    // Large M reads the tau row from L2, one round trip per group of four
-    // 16-byte loads: a ring of four groups keeps the loads of the next three
-    // in flight while one is multiplied (software pipelining; the products
-    // and renormalisations run in the order of the plain loop below, so the
-    // result is the same).
+    // Large M: the ring of tau_ring4 (the products and renormalisations run
+    // in the order of the plain loop below, so the result is the same).
     if (kRing && !kSharedTau && M >= 6 * 512) {
-        const int full = (M - 4 * lane - 3 * 128 + 511) / 512;  // groups with j + 384 < M (>= 5 here)
-        float4 r0[4], r1[4], r2[4], r3[4];
-        auto load = [&](float4 (&r)[4], int g) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) r[u] = load_tau4<kSharedTau>(tau + j + g * 512 + u * 128);
-        };
-        auto mul = [&](const float4 (&uv)[4], int g) {
+        const int j0 = j;
+        j += 512 * tau_ring4(tau, j0, lane_groups(M, j0), [&](const float4 (&uv)[4], int g) {
             float4 tv[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) tv[u] = *reinterpret_cast<const float4 *>(t + j + g * 512 + u * 128);
+            for (int u = 0; u < 4; ++u) tv[u] = *reinterpret_cast<const float4 *>(t + j0 + g * 512 + u * 128);
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 m0 *= fmaf(-si * tv[u].x, uv[u].x, 1.f) * fmaf(-si * tv[u].y, uv[u].y, 1.f);
@@ -233,26 +261,7 @@ __device__ __forceinline__ Prod<float> lane_product4(const float *__restrict__ t
             m0 = frexpf(m0, &k0);
             m1 = frexpf(m1, &k1);
             e += k0 + k1;
-        };
-        load(r0, 0);
-        load(r1, 1);
-        load(r2, 2);
-        int g = 0;
-        for (; g + 3 < full; g += 4) {
-            load(r3, g + 3);
-            mul(r0, g);
-            if (g + 4 < full) load(r0, g + 4);
-            mul(r1, g + 1);
-            if (g + 5 < full) load(r1, g + 5);
-            mul(r2, g + 2);
-            if (g + 6 < full) load(r2, g + 6);
-            mul(r3, g + 3);
-        }
-        // up to three groups left, already in r0 / r1 / r2
-        if (g < full) mul(r0, g++);
-        if (g < full) mul(r1, g++);
-        if (g < full) mul(r2, g++);
-        j += g * 512;
+        });
     }
     // groups of four 16-byte loads in flight (large M reads the tau row from L2),
     // renormalised after each group as before
