@@ -202,6 +202,16 @@ __device__ __forceinline__ float4 load_tau4(const float *tau) {
     return __ldg(reinterpret_cast<const float4 *>(tau));
 }
 
+// frexp of a positive running product: m = f 2^k, f in [0.5, 1), from the
+// exponent bits (zero and subnormal m are left as they are, k = 0; the
+// products here are renormalised every 8 factors in (0, 2)).
+__device__ __forceinline__ float renorm_bits(float m, int &e) {
+    const int b = __float_as_int(m);
+    const int be = (b >> 23) & 0xFF;
+    e += be ? be - 126 : 0;
+    return be ? __int_as_float((b & 0x807FFFFF) | 0x3F000000) : m;
+}
+
 // A lane's tau row in groups g of four 16-byte loads (units j0 + 512 g + 128
 // u, u < 4), for g = 0 .. full - 1: f(uv, g) runs on each group in order,
 // while a ring of four keeps the loads of the next three groups in flight
@@ -238,9 +248,12 @@ __device__ __forceinline__ int tau_ring4(const float *__restrict__ tau, int j0, 
 // groups of four units (j + 384 < M) of the lane starting at unit j
 __device__ __forceinline__ int lane_groups(int M, int j) { return M - j - 3 * 128 > 0 ? (M - j - 3 * 128 + 511) / 512 : 0; }
 
-template <bool kSharedTau = false, bool kRing = false>
-__device__ __forceinline__ Prod<float> lane_product4(const float *__restrict__ t, const float *__restrict__ tau,
-                                                     float si, int lane, int M) {
+// kPos: s_i = +1 (factors 1 - t tau), else s_i = -1 (1 + t tau), the sign
+// in the FMA operand; the running products are renormalised by their
+// exponent bits.
+template <bool kSharedTau, bool kRing, bool kPos>
+__device__ __forceinline__ Prod<float> lane_product4_signed(const float *__restrict__ t, const float *__restrict__ tau,
+                                                            int lane, int M) {
     float m0 = 1.f, m1 = 1.f;
     int e = 0;
     int j = 4 * lane;
@@ -254,13 +267,11 @@ __device__ __forceinline__ Prod<float> lane_product4(const float *__restrict__ t
             for (int u = 0; u < 4; ++u) tv[u] = *reinterpret_cast<const float4 *>(t + j0 + g * 512 + u * 128);
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                m0 *= fmaf(-si * tv[u].x, uv[u].x, 1.f) * fmaf(-si * tv[u].y, uv[u].y, 1.f);
-                m1 *= fmaf(-si * tv[u].z, uv[u].z, 1.f) * fmaf(-si * tv[u].w, uv[u].w, 1.f);
+                m0 *= fmaf(kPos ? -tv[u].x : tv[u].x, uv[u].x, 1.f) * fmaf(kPos ? -tv[u].y : tv[u].y, uv[u].y, 1.f);
+                m1 *= fmaf(kPos ? -tv[u].z : tv[u].z, uv[u].z, 1.f) * fmaf(kPos ? -tv[u].w : tv[u].w, uv[u].w, 1.f);
             }
-            int k0, k1;
-            m0 = frexpf(m0, &k0);
-            m1 = frexpf(m1, &k1);
-            e += k0 + k1;
+            m0 = renorm_bits(m0, e);
+            m1 = renorm_bits(m1, e);
         });
     }
     // groups of four 16-byte loads in flight (large M reads the tau row from L2),
@@ -273,25 +284,30 @@ __device__ __forceinline__ Prod<float> lane_product4(const float *__restrict__ t
         for (int u = 0; u < 4; ++u) tv[u] = *reinterpret_cast<const float4 *>(t + j + u * 128);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            m0 *= fmaf(-si * tv[u].x, uv[u].x, 1.f) * fmaf(-si * tv[u].y, uv[u].y, 1.f);
-            m1 *= fmaf(-si * tv[u].z, uv[u].z, 1.f) * fmaf(-si * tv[u].w, uv[u].w, 1.f);
+            m0 *= fmaf(kPos ? -tv[u].x : tv[u].x, uv[u].x, 1.f) * fmaf(kPos ? -tv[u].y : tv[u].y, uv[u].y, 1.f);
+            m1 *= fmaf(kPos ? -tv[u].z : tv[u].z, uv[u].z, 1.f) * fmaf(kPos ? -tv[u].w : tv[u].w, uv[u].w, 1.f);
         }
-        int k0, k1;
-        m0 = frexpf(m0, &k0);
-        m1 = frexpf(m1, &k1);
-        e += k0 + k1;
+        m0 = renorm_bits(m0, e);
+        m1 = renorm_bits(m1, e);
     }
     for (; j < M; j += 128) {
         const float4 tv = *reinterpret_cast<const float4 *>(t + j);
         const float4 uv = load_tau4<kSharedTau>(tau + j);
-        m0 *= fmaf(-si * tv.x, uv.x, 1.f) * fmaf(-si * tv.y, uv.y, 1.f);
-        m1 *= fmaf(-si * tv.z, uv.z, 1.f) * fmaf(-si * tv.w, uv.w, 1.f);
+        m0 *= fmaf(kPos ? -tv.x : tv.x, uv.x, 1.f) * fmaf(kPos ? -tv.y : tv.y, uv.y, 1.f);
+        m1 *= fmaf(kPos ? -tv.z : tv.z, uv.z, 1.f) * fmaf(kPos ? -tv.w : tv.w, uv.w, 1.f);
     }
     Prod<float> p{m0, e};
     renorm(p);
     p.m *= m1;
     renorm(p);
     return p;
+}
+
+template <bool kSharedTau = false, bool kRing = false>
+__device__ __forceinline__ Prod<float> lane_product4(const float *__restrict__ t, const float *__restrict__ tau,
+                                                     float si, int lane, int M) {
+    return si > 0.f ? lane_product4_signed<kSharedTau, kRing, true>(t, tau, lane, M)
+                    : lane_product4_signed<kSharedTau, kRing, false>(t, tau, lane, M);
 }
 
 template <bool kRing>
@@ -329,10 +345,8 @@ __device__ __forceinline__ Prod<float> lane_product4_regs(const float *__restric
                 m0 *= fmaf(-si * tv[u].x, w.x, 1.f) * fmaf(-si * tv[u].y, w.y, 1.f);
                 m1 *= fmaf(-si * tv[u].z, w.z, 1.f) * fmaf(-si * tv[u].w, w.w, 1.f);
             }
-            int k0, k1;
-            m0 = frexpf(m0, &k0);
-            m1 = frexpf(m1, &k1);
-            e += k0 + k1;
+            m0 = renorm_bits(m0, e);
+            m1 = renorm_bits(m1, e);
             j += 4 * 128;
             ++G;
         }
@@ -979,9 +993,7 @@ __global__ void __launch_bounds__(kEW * 32) k_eloc_batched(ElocBK P) {
 #pragma unroll
                     for (int q = 0; q < kEG; ++q) {
                         if (q >= cnt) break;
-                        int k;
-                        m[q] = frexpf(m[q], &k);
-                        ex[q] += k;
+                        m[q] = renorm_bits(m[q], ex[q]);
                     }
                 }
             }
