@@ -240,35 +240,41 @@ __global__ void __launch_bounds__(kSgThreads, 2)
 
 // ------------------------------------------- J v: persistent, 4 slices ---
 //
-// The CG products of NK_MIXED (4 slices) as one persistent kernel per SM:
-// warp 0 streams A / B K-chunks through a 4-stage TMA ring, warp 1 issues the
-// MMAs of a 128 x 64 tile (4 slices side by side, N = 256) into one of two
-// TMEM accumulator sets (512 columns), and 16 epilogue warps drain the other
-// set meanwhile: warp (q, g) owns TMEM lane quarter q (tile rows 32q ..
+// The CG products of NK_MIXED as one persistent kernel per SM, on FP16
+// slices: B (V' for J v, (T' o g')^T for J^T g) is cut into 3 slices of
+// 11-bit digits on a 33-bit grid per operand row (FP16 holds every integer up
+// to 2048 exactly), A is the +-1 operand in FP16, and each FP32 level sums
+// K products below 2^11, exact while K 2047 < 2^24 (K <= 8192 per unit).
+// Warp 0 streams A / B K-chunks through a 5-stage TMA ring (40 KB a stage),
+// warp 1 issues the MMAs of a 128 x 64 tile (3 slices side by side, N = 192)
+// into one of two TMEM accumulator sets, and 16 epilogue warps drain the
+// other set meanwhile: warp (q, g) owns TMEM lane quarter q (tile rows 32q ..
 // 32q + 31) and the 16 tile columns 16g .. 16g + 15.
 //
-// The epilogue needs sum_j t'_j V_j 2^(f_j - 32) per row, V_j = D_0 2^24 +
-// D_1 2^16 + D_2 2^8 + D_3 from the exact FP32 levels.  It runs in FP32 on
-// tanh(theta) stored as an FP32 pair t = th + tl (|tl| <= 2^-24 |th|, built
-// once per solve): with u = th 2^(f_j - F) and ul = tl 2^(f_j - F) (F the
-// largest column exponent of the tile, so that the scale is a power of two
-// <= 1), the row sum is 2^(F - 8) sum_j (D_0 + D_1 2^-8 + D_2 2^-16 +
-// D_3 2^-24)(u + ul).  The products D_0 u and D_1 u are split exactly by FMA
-// (p + e), p is summed exactly by two-sum into FP32 pairs, and the terms
-// below 2^-24 of the leading one go to a plain FP32 sum: about 2^-44 of the
-// summed magnitudes, below the 2^-32 of the slicing, with no FP64 work per
-// entry.  The four column groups of a row meet as FP32 pairs in shared memory
-// (a ring of 4 tiles, an mbarrier per quarter and slot), and warp (q, 0)
-// writes the tile's row partial P[nt][row] in FP64.  Tiles go round robin
-// over the CTAs.  Every wait is bounded; a time-out sets err and drains the
-// copies and MMAs in flight before the TMEM is released.
+// J v (mode 0) needs sum_j t'_j V_j 2^(f_j - 33) per row, V_j = D_0 2^22 +
+// D_1 2^11 + D_2 from the exact FP32 levels.  It runs in FP32 on tanh(theta)
+// stored as an FP32 pair t = th + tl (|tl| <= 2^-24 |th|, built once per
+// solve): with u = th 2^(f_j - F) and ul = tl 2^(f_j - F) (F the largest
+// column exponent of the tile, so that the scale is a power of two <= 1),
+// the row sum is 2^(F - 11) sum_j (D_0 + D_1 2^-11 + D_2 2^-22)(u + ul).  The
+// products D_0 u and D_1 u are split exactly by FMA (p + e), p is summed
+// exactly by two-sum into FP32 pairs, and the smaller terms go to a plain
+// FP32 sum: about 2^-44 of the summed magnitudes, below the 2^-33 of the
+// slicing, with no FP64 work per entry.  The four column groups of a row meet
+// as FP32 pairs in shared memory (a ring of 4 tiles, an mbarrier per quarter
+// and slot), and warp (q, 0) writes the tile's row partial P[nt][row] in
+// FP64.  J^T g (mode 1) recombines V exactly in int64 and writes FP64 split-K
+// partials.  Units go round robin over the clusters.  Every wait is bounded;
+// a time-out sets err and drains the copies and MMAs in flight before the
+// TMEM is released.
 constexpr int kJvEpiWarps = 16;
 constexpr int kJvThreads = 64 + 32 * kJvEpiWarps;
-constexpr int kJvStages = 4;
-constexpr int kJvSB = 4;
-constexpr int kJvStageBytes = kAB + kJvSB * kBB;  // 48 KB
+constexpr int kJvStages = 5;
+constexpr int kJvSB = 3;                            // FP16 slices of 11-bit digits
+constexpr int kJvStageBytes = kAB + kJvSB * kBB;  // 40 KB
 constexpr int kJvRing = 4;                          // row-partial slots
-constexpr uint32_t kJvAccCols = kJvSB * kBN;        // 256
+constexpr uint32_t kJvAccCols = kJvSB * kBN;        // 192 per accumulator set
+constexpr uint32_t kJvTmemCols = 512;               // two sets, rounded up to a power of two
 constexpr int kTcRowDot = 0, kTcStoreT = 1;         // epilogue modes of k_tc4
 
 struct Tc4Args {
@@ -357,7 +363,7 @@ __global__ void __launch_bounds__(kJvThreads, 1)
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) tmem_alloc(tslot, 2 * kJvAccCols);
+    if (warp == 0) tmem_alloc(tslot, kJvTmemCols);
     tc_fence_before();
     if (C > 1)
         cluster_sync_all();  // the peers' barriers exist before any multicast reaches them
@@ -372,8 +378,8 @@ __global__ void __launch_bounds__(kJvThreads, 1)
 
     if (warp == 0 && lane == 0) {
         // ---------------------------------------------------------- producer
-        // own A tile; B slices rank * 4 / C .. (rank + 1) * 4 / C - 1 to every CTA
-        const int per = kJvSB / C, t0 = (int)rank * per;
+        // own A tile; B slices rank * 3 / C .. (rank + 1) * 3 / C - 1 to every CTA
+        const int t0 = (int)rank * kJvSB / C, t1 = ((int)rank + 1) * kJvSB / C;
         int64_t g = 0;  // K-chunks issued (all units)
         for (int64_t li = 0; li < nunits && !*abort_flag; ++li) {
             const Tc4Unit u = tc4_unit<kMode>(a, cl + li * ncl, rank);
@@ -390,7 +396,7 @@ __global__ void __launch_bounds__(kJvThreads, 1)
                 unsigned char *sp = ops + (size_t)s * kJvStageBytes;
                 mbar_expect_tx(&full[s], (uint32_t)kJvStageBytes);
                 tma_load_2d(sp, &mapA, &full[s], kc * kBK, m0);
-                for (int t = t0; t < t0 + per; ++t) {
+                for (int t = t0; t < t1; ++t) {
                     if (C > 1)
                         tma_load_3d_mc(sp + kAB + t * kBB, &mapB, &full[s], kc * kBK, n0, t, mask);
                     else
@@ -405,7 +411,7 @@ __global__ void __launch_bounds__(kJvThreads, 1)
         }
     } else if (warp == 1 && lane == 0) {
         // ------------------------------------------------------- MMA issuer
-        const uint32_t idesc = idesc_bf16(kBM, kBN * kJvSB);
+        const uint32_t idesc = idesc_f16(kBM, kBN * kJvSB);
         int64_t g = 0;
         int64_t committed = -1;  // last unit whose accumulator commit was issued
         for (int64_t li = 0; li < nunits && !*abort_flag; ++li) {
@@ -521,7 +527,8 @@ __global__ void __launch_bounds__(kJvThreads, 1)
             }
             tc_fence_after();
             if (kMode == kTcStoreT) {
-                // P^T[z][col][row] = V 2^(f_col - 32), exact (|V| < 2^48: K per unit <= 16448)
+                // P^T[z][col][row] = V 2^(f_col - 33), V = D_0 2^22 + D_1 2^11 + D_2 exact
+                // (|D_t| < 2^24: K per unit <= 8192)
                 double *dst = a.P + (size_t)u.z * a.split_stride + row;
 #pragma unroll
                 for (int c8 = 0; c8 < 16; c8 += 8) {
@@ -532,10 +539,11 @@ __global__ void __launch_bounds__(kJvThreads, 1)
                     tmem_wait_ld();
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
-                        const long long V = levels4_to_i64(__uint_as_float(r[0][j]), __uint_as_float(r[1][j]),
-                                                           __uint_as_float(r[2][j]), __uint_as_float(r[3][j]));
+                        const long long V = ((long long)__float2int_rn(__uint_as_float(r[0][j])) << 22) +
+                                            ((long long)__float2int_rn(__uint_as_float(r[1][j])) << 11) +
+                                            (long long)__float2int_rn(__uint_as_float(r[2][j]));
                         const int col = col0 + c8 + j;
-                        if (row_ok && col < a.cols) dst[(size_t)col * a.ldp] = exact_to_double(V, fe[c8 + j] - 32);
+                        if (row_ok && col < a.cols) dst[(size_t)col * a.ldp] = exact_to_double(V, fe[c8 + j] - 33);
                     }
                 }
                 tc_fence_before();
@@ -543,7 +551,7 @@ __global__ void __launch_bounds__(kJvThreads, 1)
                 if (lane == 0) mbar_arrive(&acc_empty[b]);
                 continue;
             }
-            // mode 0.  A: sum of D_0 u (exact pairs); B: sum of D_1 u; sm: the terms below 2^-24
+            // mode 0.  A: sum of D_0 u (exact pairs); B: sum of D_1 u; sm: the smaller terms
             float ah = 0.f, al = 0.f, bh = 0.f, bl = 0.f, sm = 0.f;
 #pragma unroll
             for (int c8 = 0; c8 < 16; c8 += 8) {
@@ -555,14 +563,14 @@ __global__ void __launch_bounds__(kJvThreads, 1)
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const float d0 = __uint_as_float(r[0][j]), d1 = __uint_as_float(r[1][j]);
-                    const float d2 = __uint_as_float(r[2][j]), d3 = __uint_as_float(r[3][j]);
+                    const float d2 = __uint_as_float(r[2][j]);
                     const float u0 = __fmul_rn(tv[c8 + j].x, cs[c8 + j]), ul = __fmul_rn(tv[c8 + j].y, cs[c8 + j]);
                     const float p0 = __fmul_rn(d0, u0), e0 = __fmaf_rn(d0, u0, -p0);
                     const float p1 = __fmul_rn(d1, u0), e1 = __fmaf_rn(d1, u0, -p1);
-                    // 2^-24-level: e0 + D_0 ul; 2^-32: (e1 + D_1 ul) 2^-8; 2^-40: (D_2 + D_3 2^-8) u 2^-16
+                    // 2^-24-level: e0 + D_0 ul; 2^-35: (e1 + D_1 ul) 2^-11; 2^-22: D_2 u 2^-22
                     float lo = __fmaf_rn(d0, ul, e0);
-                    lo = __fmaf_rn(__fmaf_rn(d1, ul, e1), 0.00390625f, lo);
-                    lo = __fmaf_rn(__fmaf_rn(d3, 0.00390625f, d2), __fmul_rn(u0, 1.52587890625e-05f), lo);
+                    lo = __fmaf_rn(__fmaf_rn(d1, ul, e1), 4.8828125e-04f, lo);
+                    lo = __fmaf_rn(d2, __fmul_rn(u0, 2.384185791015625e-07f), lo);
                     sm = __fadd_rn(sm, lo);
                     float s, e;
                     two_sum(ah, p0, s, e);
@@ -577,10 +585,10 @@ __global__ void __launch_bounds__(kJvThreads, 1)
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[b]);
-            // (H, L) = A + B 2^-8 + sm as one FP32 pair
+            // (H, L) = A + B 2^-11 + sm as one FP32 pair
             float H, L;
-            two_sum(ah, __fmul_rn(bh, 0.00390625f), H, L);
-            L = __fadd_rn(L, __fadd_rn(al, __fmaf_rn(bl, 0.00390625f, sm)));
+            two_sum(ah, __fmul_rn(bh, 4.8828125e-04f), H, L);
+            L = __fadd_rn(L, __fadd_rn(al, __fmaf_rn(bl, 4.8828125e-04f, sm)));
             // the four column groups of each row meet in the ring slot of this unit
             const int slot = (int)(li % kJvRing);
             red[((size_t)slot * 4 + grp) * kBM + q * 32 + lane] = make_float2(H, L);
@@ -606,8 +614,8 @@ __global__ void __launch_bounds__(kJvThreads, 1)
                     sh = s;
                     sl = __fadd_rn(sl, __fadd_rn(e, rs[g2 * kBM].y));
                 }
-                // 2^(F - 8) (sh + sl) in FP64 (the power of two by its exponent bits)
-                const int ebias = F - 8 + 1023;
+                // 2^(F - 11) (sh + sl) in FP64 (the power of two by its exponent bits)
+                const int ebias = F - 11 + 1023;
                 const double scale = __longlong_as_double(
                     ebias < 1 ? 0LL : (ebias > 2046 ? 0x7FF0000000000000LL : (long long)ebias << 52));
                 if (row_ok) a.P[(size_t)u.nt * a.rows + row] = ((double)sh + (double)sl) * scale;
@@ -623,7 +631,7 @@ __global__ void __launch_bounds__(kJvThreads, 1)
         __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        tmem_dealloc(tmem, 2 * kJvAccCols);
+        tmem_dealloc(tmem, kJvTmemCols);
     }
 }
 
@@ -639,8 +647,22 @@ size_t sgemm_smem_bytes(int SB) {
 
 // S [B][N] int8 -> BF16 [B][ld]; column N holds 1.0 when augment, the rest of
 // the padding 0.
+// +-1, 1 and 0 as 16-bit operands: BF16 (the k_sgemm products) or FP16 (the
+// 3-slice products of k_tc4); all three values are exact in both.
+template <typename H>
+__device__ __forceinline__ H to16(float v);
+template <>
+__device__ __forceinline__ __nv_bfloat16 to16<__nv_bfloat16>(float v) {
+    return __float2bfloat16_rn(v);
+}
+template <>
+__device__ __forceinline__ __half to16<__half>(float v) {
+    return __float2half_rn(v);
+}
+
+template <typename H>
 __global__ void k_pm1_rows(const int8_t *__restrict__ s, int64_t B, int N, int augment, int64_t ld,
-                           __nv_bfloat16 *__restrict__ out) {
+                           H *__restrict__ out) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= B * ld) return;
     const int64_t k = idx / ld;
@@ -650,12 +672,12 @@ __global__ void k_pm1_rows(const int8_t *__restrict__ s, int64_t B, int N, int a
         v = (float)s[(size_t)k * N + i];
     else if (augment && i == N)
         v = 1.f;
-    out[idx] = __float2bfloat16_rn(v);
+    out[idx] = to16<H>(v);
 }
 
 // S^T with a row of ones: out [N+1][ld] (row i, column k) = s_ki (i < N) or 1.
-__global__ void k_pm1_cols(const int8_t *__restrict__ s, int64_t Ns, int N, int64_t ld,
-                           __nv_bfloat16 *__restrict__ out) {
+template <typename H>
+__global__ void k_pm1_cols(const int8_t *__restrict__ s, int64_t Ns, int N, int64_t ld, H *__restrict__ out) {
     __shared__ int8_t tile[32][33];
     const int64_t k0 = (int64_t)blockIdx.x * 32;
     const int i0 = blockIdx.y * 32;
@@ -671,7 +693,7 @@ __global__ void k_pm1_cols(const int8_t *__restrict__ s, int64_t Ns, int N, int6
         if (i > N || k >= ld) continue;
         float v = 0.f;
         if (k < Ns) v = i < N ? (float)tile[threadIdx.x][r] : 1.f;
-        out[(size_t)i * ld + k] = __float2bfloat16_rn(v);
+        out[(size_t)i * ld + k] = to16<H>(v);
     }
 }
 
@@ -725,6 +747,15 @@ __device__ __forceinline__ void slice_pair(double x0, double x1, int e, int SB, 
     }
 }
 
+// The 3-slice FP16 form (11-bit digits on the 33-bit grid, tc_ptx.cuh).
+__device__ __forceinline__ void slice_pair_h3(double x0, double x1, int e, uint32_t *out, int64_t plane2) {
+    uint32_t s0, s1;
+    const unsigned long long y0 = grid33(x0, e, s0), y1 = grid33(x1, e, s1);
+    const uint32_t sg = (s0 << 15) | (s1 << 31);
+#pragma unroll
+    for (int t = 0; t < 3; ++t) out[(size_t)t * plane2] = f16_digit_pair(y0, y1, 22 - 11 * t, sg);
+}
+
 // The 4-slice case of slice_pair (grid32 and bf16_digit_pair, tc_ptx.cuh).
 __device__ __forceinline__ void slice_pair4(double x0, double x1, int e, uint32_t *out, int64_t plane2) {
     uint32_t s0, s1;
@@ -732,6 +763,40 @@ __device__ __forceinline__ void slice_pair4(double x0, double x1, int e, uint32_
     const uint32_t sg = (s0 << 15) | (s1 << 31);
 #pragma unroll
     for (int t = 0; t < 4; ++t) out[(size_t)t * plane2] = bf16_digit_pair(y0, y1, 3u - (uint32_t)t, sg);
+}
+
+// Rows of a row-major FP64 matrix into 3 FP16 slices of 11-bit digits (the
+// 33-bit grid of the row's exponent): out [3][rows][ld], one block per row.
+__global__ void k_slice_rows_h3(const double *__restrict__ X, int64_t ldx, int64_t rows, int64_t K, int64_t ld,
+                                uint32_t *__restrict__ out, int *__restrict__ expo) {
+    const int64_t r = blockIdx.x;
+    if (r >= rows) return;
+    int ex = -100000;
+    for (int64_t k = threadIdx.x; k < K; k += blockDim.x) ex = max(ex, exp_of(X[(size_t)r * ldx + k]));
+    __shared__ int red[32];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) ex = max(ex, __shfl_xor_sync(0xffffffffu, ex, off));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ex;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : -100000;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, off));
+        if (threadIdx.x == 0) red[0] = v;
+    }
+    __syncthreads();
+    const int e = red[0] == -100000 ? 0 : red[0];
+    const int64_t plane2 = rows * ld / 2;  // in FP16 pairs (ld even)
+    for (int64_t k = 2 * threadIdx.x; k < ld; k += 2 * blockDim.x) {
+        const double x0 = k < K ? X[(size_t)r * ldx + k] : 0.0, x1 = k + 1 < K ? X[(size_t)r * ldx + k + 1] : 0.0;
+        uint32_t s0, s1;
+        const unsigned long long y0 = grid33(x0, e, s0), y1 = grid33(x1, e, s1);
+        const uint32_t sg = (s0 << 15) | (s1 << 31);
+        uint32_t *o = out + ((size_t)r * ld + k) / 2;
+#pragma unroll
+        for (int t = 0; t < 3; ++t) o[(size_t)t * plane2] = f16_digit_pair(y0, y1, 22 - 11 * t, sg);
+    }
+    if (threadIdx.x == 0) expo[r] = e;
 }
 
 // Rows of a row-major FP64 matrix (row r, column k: X[r * ldx + k] for k < K;
@@ -844,7 +909,7 @@ __global__ void k_colexp_bound(int M, const int *__restrict__ colexpT, const int
 // contiguous bytes per plane and row j (ld is even).
 constexpr int kTgPitch = 65;
 __global__ void __launch_bounds__(256) k_tg_slice(const double *__restrict__ T, const double *__restrict__ gp,
-                                                  int64_t Ns, int M, int SB, int64_t ld, int vec,
+                                                  int64_t Ns, int M, int SB, int f16, int64_t ld, int vec,
                                                   const int *__restrict__ expo, __nv_bfloat16 *__restrict__ out) {
     __shared__ double tile[64 * kTgPitch];  // [k][j]
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -880,7 +945,9 @@ __global__ void __launch_bounds__(256) k_tg_slice(const double *__restrict__ T, 
         const int e = expo[jj] == -100000 ? 0 : expo[jj];
         const double x0 = k < Ns ? tile[(2 * lane) * kTgPitch + jr] : 0.0;
         const double x1 = k + 1 < Ns ? tile[(2 * lane + 1) * kTgPitch + jr] : 0.0;
-        if (SB == 4)
+        if (f16)
+            slice_pair_h3(x0, x1, e, reinterpret_cast<uint32_t *>(out + (size_t)jj * ld + k), plane2);
+        else if (SB == 4)
             slice_pair4(x0, x1, e, reinterpret_cast<uint32_t *>(out + (size_t)jj * ld + k), plane2);
         else
             slice_pair(x0, x1, e, SB, reinterpret_cast<__nv_bfloat162 *>(out + (size_t)jj * ld + k), plane2);
@@ -1081,17 +1148,20 @@ cudaError_t launch_tc4(const CUtensorMap &ma, const CUtensorMap &mb, const Tc4Ar
 // CTAs per cluster of the J v product (B slices multicast across row tiles).
 constexpr int kJvCluster = 2;
 
+// The largest K whose FP32 levels stay exact with 11-bit digits (K 2047 < 2^24).
+constexpr int kH3MaxK = 8192;
+
 // J v partials P [n_nt][rows] = per 64-column tile, sum_col (A B^T)[row][col]
-// t'_col by k_tc4 mode 0 (4 slices; K <= 65792 keeps the FP32 levels exact).
-cudaError_t jvp4(const __nv_bfloat16 *A, int64_t rows, int64_t ldA, const __nv_bfloat16 *Bsl, const int *expB,
-                 int64_t cols, int64_t ldB, int64_t K, const void *Thl, int Mt, double *P, int *err,
-                 cudaStream_t st) {
+// t'_col by k_tc4 mode 0 (A FP16 +-1, B 3 FP16 slices; K <= 8192).
+cudaError_t jvp4(const void *A, int64_t rows, int64_t ldA, const void *Bsl, const int *expB, int64_t cols,
+                 int64_t ldB, int64_t K, const void *Thl, int Mt, double *P, int *err, cudaStream_t st) {
     if (rows <= 0 || cols <= 0 || K <= 0) return cudaSuccess;
-    if (K > 65792 || rows > (1LL << 31) - kBM || cols > (1LL << 31) - kBN || Thl == nullptr)
+    if (K > kH3MaxK || rows > (1LL << 31) - kBM || cols > (1LL << 31) - kBN || Thl == nullptr)
         return cudaErrorInvalidValue;
     if ((reinterpret_cast<uintptr_t>(Thl) & 15) != 0 || Mt + 1 != cols) return cudaErrorInvalidValue;
     CUtensorMap ma, mb;
-    if (!make_rows_map(&ma, A, rows, K, ldA, kBM) || !make_sliced_map(&mb, Bsl, cols, K, ldB, kJvSB, kBN))
+    if (!make_rows_map(&ma, static_cast<const __nv_bfloat16 *>(A), rows, K, ldA, kBM) ||
+        !make_sliced_map(&mb, static_cast<const __nv_bfloat16 *>(Bsl), cols, K, ldB, kJvSB, kBN))
         return cudaErrorInvalidValue;
     const int n_nt = (int)((cols + kBN - 1) / kBN);
     const int64_t n_mt = (rows + kBM - 1) / kBM;
@@ -1104,15 +1174,17 @@ cudaError_t jvp4(const __nv_bfloat16 *A, int64_t rows, int64_t ldA, const __nv_b
 }
 
 // P^T [ks][cols][ldp] (column-major split-K partial products) = A B^T by
-// k_tc4 mode 1, with ks such that a unit is at most 257 K-chunks (|D_t| <=
-// 255 K < 2^22) and the last round of units is nearly full.
-cudaError_t vjp4(const __nv_bfloat16 *A, int64_t rows, int64_t ldA, const __nv_bfloat16 *Bsl, const int *expB,
-                 int64_t cols, int64_t ldB, int64_t K, double *P, int64_t ldp, int64_t split_stride, int max_ks,
-                 int *ks_out, int *err, cudaStream_t st) {
+// k_tc4 mode 1 (A FP16 +-1, B 3 FP16 slices), with ks such that a unit is at
+// most 128 K-chunks (K <= 8192: exact FP32 levels) and the last round of
+// units is nearly full.
+cudaError_t vjp4(const void *A, int64_t rows, int64_t ldA, const void *Bsl, const int *expB, int64_t cols,
+                 int64_t ldB, int64_t K, double *P, int64_t ldp, int64_t split_stride, int max_ks, int *ks_out,
+                 int *err, cudaStream_t st) {
     if (rows <= 0 || cols <= 0 || K <= 0) return cudaSuccess;
     if (rows > (1LL << 31) - kBM || cols > (1LL << 31) - kBN || ldp < rows) return cudaErrorInvalidValue;
     CUtensorMap ma, mb;
-    if (!make_rows_map(&ma, A, rows, K, ldA, kBM) || !make_sliced_map(&mb, Bsl, cols, K, ldB, kJvSB, kBN))
+    if (!make_rows_map(&ma, static_cast<const __nv_bfloat16 *>(A), rows, K, ldA, kBM) ||
+        !make_sliced_map(&mb, static_cast<const __nv_bfloat16 *>(Bsl), cols, K, ldB, kJvSB, kBN))
         return cudaErrorInvalidValue;
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -1121,7 +1193,7 @@ cudaError_t vjp4(const __nv_bfloat16 *A, int64_t rows, int64_t ldA, const __nv_b
     const int n_nt = (int)((cols + kBN - 1) / kBN);
     const int n_mt = (int)((rows + kBM - 1) / kBM);
     const int kchunks = (int)((K + kBK - 1) / kBK);
-    const int ks_min = (kchunks + 256) / 257;
+    const int ks_min = (kchunks + kH3MaxK / kBK - 1) / (kH3MaxK / kBK);
     if (ks_min > max_ks) return cudaErrorInvalidValue;
     int ks = ks_min;
     double best = -1.0;
@@ -1205,10 +1277,9 @@ size_t tc_vjp_operand_bytes(int N, int64_t Ns) { return (size_t)(N + 1) * pad8(N
 cudaError_t launch_jacobian_operands(int N, int64_t Ns, const int8_t *s, void *opA, void *opT, cudaStream_t st) {
     if (Ns <= 0) return cudaSuccess;
     const int64_t lda = pad8(N + 1), ldt = pad8(Ns);
-    (k_pm1_rows<<<nblk(Ns * lda, 256), 256, 0, st>>>(s, Ns, N, 1, lda, static_cast<__nv_bfloat16 *>(opA)),
+    (k_pm1_rows<<<nblk(Ns * lda, 256), 256, 0, st>>>(s, Ns, N, 1, lda, static_cast<__half *>(opA)),
      nk::note_launch());
-    (k_pm1_cols<<<dim3(nblk(ldt, 32), nblk(N + 1, 32)), dim3(32, 8), 0, st>>>(s, Ns, N, ldt,
-                                                                              static_cast<__nv_bfloat16 *>(opT)),
+    (k_pm1_cols<<<dim3(nblk(ldt, 32), nblk(N + 1, 32)), dim3(32, 8), 0, st>>>(s, Ns, N, ldt, static_cast<__half *>(opT)),
      nk::note_launch());
     return cudaGetLastError();
 }
@@ -1232,13 +1303,23 @@ cudaError_t launch_jvp_tc(int N, int M, int64_t Ns, const int8_t *s, const doubl
     const int ntc = (M + 1 + kBN - 1) / kBN;
     auto *P = reinterpret_cast<double *>(take((size_t)Ns * ntc * 8));
     const int64_t tot = (int64_t)(M + 1) * (N + 1);
-    if (opA)
-        As = static_cast<__nv_bfloat16 *>(const_cast<void *>(opA));
+    // 4 slices' accuracy (the CG products) through the persistent kernel on 3
+    // FP16 slices of 11-bit digits (33 bits), where K = N + 1 allows it
+    const bool persistent = SB == 4 && N + 1 <= kH3MaxK;
+    if (persistent && opA)
+        As = static_cast<__nv_bfloat16 *>(const_cast<void *>(opA));  // FP16 bits
+    else if (persistent)
+        (k_pm1_rows<<<nblk(Ns * ld, 256), 256, 0, st>>>(s, Ns, N, 1, ld, reinterpret_cast<__half *>(As)),
+         nk::note_launch());
     else
         (k_pm1_rows<<<nblk(Ns * ld, 256), 256, 0, st>>>(s, Ns, N, 1, ld, As), nk::note_launch());
     (k_build_vaug<<<nblk(tot, 256), 256, 0, st>>>(N, M, v, Vp), nk::note_launch());
-    (k_slice_long_rows<<<M + 1, 128, 0, st>>>(Vp, N + 1, M + 1, N + 1, nullptr, SB, ld, Vs, ev), nk::note_launch());
-    const bool persistent = SB == kJvSB && N + 1 <= 65792;
+    if (persistent)
+        (k_slice_rows_h3<<<M + 1, 128, 0, st>>>(Vp, N + 1, M + 1, N + 1, ld, reinterpret_cast<uint32_t *>(Vs), ev),
+         nk::note_launch());
+    else
+        (k_slice_long_rows<<<M + 1, 128, 0, st>>>(Vp, N + 1, M + 1, N + 1, nullptr, SB, ld, Vs, ev),
+         nk::note_launch());
     if (persistent && Thl == nullptr) {
         void *own = take(tc_split_t_bytes(M, Ns));
         cudaError_t es = launch_split_t(M, Ns, T, own, st);
@@ -1248,7 +1329,8 @@ cudaError_t launch_jvp_tc(int N, int M, int64_t Ns, const int8_t *s, const doubl
     const int slot = prof_begin(NK_PROF_JVP_VJP, st);
     cudaError_t e = persistent ? jvp4(As, Ns, ld, Vs, ev, M + 1, ld, N + 1, Thl, M, P, err, st)
                                : sgemm(As, Ns, ld, Vs, ev, M + 1, ld, N + 1, SB, P, ntc, 3, nullptr, err, st, T, M);
-    prof_end(slot, st, 2.0 * (double)Ns * (N + 1) * (double)(M + 1), sgemm_flops(Ns, M + 1, N + 1, SB));
+    prof_end(slot, st, 2.0 * (double)Ns * (N + 1) * (double)(M + 1),
+             sgemm_flops(Ns, M + 1, N + 1, persistent ? kJvSB : SB));
     if (e != cudaSuccess) return e;
     if (persistent)
         (k_rowsum_tiles<<<nblk(Ns, 256), 256, 0, st>>>(Ns, ntc, P, out), nk::note_launch());
@@ -1257,7 +1339,7 @@ cudaError_t launch_jvp_tc(int N, int M, int64_t Ns, const int8_t *s, const doubl
     return cudaGetLastError();
 }
 
-constexpr int kMaxKSplit = 8;
+constexpr int kMaxKSplit = 16;
 
 // K-split count for a grid of `tiles` output tiles over `slots` resident
 // CTAs: the share of the last wave's slots that hold work, less 1 % per extra
@@ -1313,8 +1395,15 @@ cudaError_t launch_vjp_tc(int N, int M, int64_t Ns, const int8_t *s, const doubl
     auto *gp = reinterpret_cast<double *>(take((size_t)Ns * 8));
     auto *ge = reinterpret_cast<int *>(take((size_t)Ns * 4));
     dim3 tb(32, 8);
-    if (opT)
-        St = static_cast<__nv_bfloat16 *>(const_cast<void *>(opT));
+    const int64_t kchunks = (Ns + kBK - 1) / kBK;
+    // 4 slices' accuracy (the CG products) through the persistent kernel on 3
+    // FP16 slices of 11-bit digits (33 bits), in units of at most 8192 samples
+    const bool h3 = SB == 4 && (kchunks + kH3MaxK / kBK - 1) / (kH3MaxK / kBK) <= kMaxKSplit;
+    if (h3 && opT)
+        St = static_cast<__nv_bfloat16 *>(const_cast<void *>(opT));  // FP16 bits
+    else if (h3)
+        (k_pm1_cols<<<dim3(nblk(ld, 32), nblk(N + 1, 32)), tb, 0, st>>>(s, Ns, N, ld, reinterpret_cast<__half *>(St)),
+         nk::note_launch());
     else
         (k_pm1_cols<<<dim3(nblk(ld, 32), nblk(N + 1, 32)), tb, 0, st>>>(s, Ns, N, ld, St), nk::note_launch());
     (k_scale_g<<<nblk(Ns, 256), 256, 0, st>>>(Ns, g, scale, shift, gp, ge), nk::note_launch());
@@ -1328,7 +1417,8 @@ cudaError_t launch_vjp_tc(int N, int M, int64_t Ns, const int8_t *s, const doubl
          nk::note_launch());
     }
     const int vec = (M % 2 == 0) && ((reinterpret_cast<uintptr_t>(T) & 15) == 0);
-    (k_tg_slice<<<dim3(nblk(ld, 64), nblk(M + 1, 64)), 256, 0, st>>>(T, gp, Ns, M, SB, ld, vec, eg, Gs),
+    (k_tg_slice<<<dim3(nblk(ld, 64), nblk(M + 1, 64)), 256, 0, st>>>(T, gp, Ns, M, h3 ? kJvSB : SB, h3 ? 1 : 0, ld,
+                                                                        vec, eg, Gs),
      nk::note_launch());
     // split the long K = Ns range so that the last wave of CTAs is nearly
     // full (every split keeps >= 4 chunks; each split's FP32 levels stay exact)
@@ -1339,14 +1429,14 @@ cudaError_t launch_vjp_tc(int N, int M, int64_t Ns, const int8_t *s, const doubl
     if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sgemm, kSgThreads, sgemm_smem_bytes(SB));
     if (e != cudaSuccess) return e;
-    const int64_t tiles = (int64_t)nblk(M + 1, kBN) * nblk(N + 1, kBM), kchunks = (Ns + kBK - 1) / kBK;
+    const int64_t tiles = (int64_t)nblk(M + 1, kBN) * nblk(N + 1, kBM);
     const int64_t tot = (int64_t)(N + 1) * (M + 1);
-    if (SB == kJvSB && (kchunks + 256) / 257 <= kMaxKSplit) {
-        // the persistent 4-slice kernel, P^T column-major
+    if (h3) {
+        // the persistent kernel, P^T column-major
         int ks4 = 1;
         const int slot = prof_begin(NK_PROF_JVP_VJP, st);
         e = vjp4(St, N + 1, ld, Gs, eg, M + 1, ld, Ns, PT, N + 1, tot, kMaxKSplit, &ks4, err, st);
-        prof_end(slot, st, 2.0 * (double)Ns * (N + 1) * (double)(M + 1), sgemm_flops(N + 1, M + 1, Ns, SB));
+        prof_end(slot, st, 2.0 * (double)Ns * (N + 1) * (double)(M + 1), sgemm_flops(N + 1, M + 1, Ns, kJvSB));
         if (e != cudaSuccess) return e;
         (k_scatter_vjp_t<<<nblk(tot, 256), 256, 0, st>>>(N, M, ks4, PT, out), nk::note_launch());
         return cudaGetLastError();

@@ -6,6 +6,7 @@
 
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -101,6 +102,11 @@ __device__ __forceinline__ uint64_t sw128_desc(const void *p) {
 // Instruction descriptor of kind::f16: BF16 A and B (K-major), FP32 D.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// The same with FP16 A and B (format field 0).
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
@@ -386,6 +392,46 @@ __host__ __device__ __forceinline__ uint32_t bf16_digit_pair(uint32_t y0, uint32
     __builtin_memcpy(&v0, &f0, 4);
     __builtin_memcpy(&v1, &f1, 4);
     return byte_perm_any(v0, v1, 0x7632u) | sgnmask;
+#endif
+}
+
+// 3-slice FP16 digits (11 bits each, exact in FP16 up to 2047).  grid33: y =
+// trunc(|x| 2^(33 - e)) for |x| < 2^e, the mantissa (implicit one included)
+// shifted right by 1042 + e - (biased exponent) >= 20; subnormal x give 0.
+// f16_digit_pair: the 11-bit digit at bit `shift` of y0 and of y1 as the low
+// and high FP16 of a pair (the float 2^23 + d from its bit pattern, minus
+// 2^23, converted exactly), signs OR-ed in.
+__host__ __device__ __forceinline__ unsigned long long grid33(double x, int e, uint32_t &sgn) {
+    unsigned long long b;
+#ifdef __CUDA_ARCH__
+    b = (unsigned long long)__double_as_longlong(x);
+#else
+    __builtin_memcpy(&b, &x, 8);
+#endif
+    sgn = (uint32_t)(b >> 63);
+    const int be = (int)((b >> 52) & 0x7FFu);
+    const unsigned long long m = (b & 0xFFFFFFFFFFFFFULL) | (1ULL << 52);
+    const int rs = 1042 + e - be;  // >= 20 for |x| < 2^e
+    return (be == 0 || rs >= 64) ? 0ULL : (rs <= 0 ? m : m >> rs);
+}
+
+// The FP16 bit pattern of an integer 0 <= d < 2048 (exact), for the host.
+__host__ __device__ __forceinline__ uint32_t f16_of_digit_bits(uint32_t d) {
+    if (d == 0) return 0u;
+    const int E = 63 - clz64_any((unsigned long long)d);  // floor(log2 d)
+    return ((uint32_t)(E + 15) << 10) | ((d << (10 - E)) & 0x3FFu);
+}
+
+__host__ __device__ __forceinline__ uint32_t f16_digit_pair(unsigned long long y0, unsigned long long y1, int shift,
+                                                            uint32_t sgnmask) {
+    const uint32_t d0 = (uint32_t)(y0 >> shift) & 0x7FFu, d1 = (uint32_t)(y1 >> shift) & 0x7FFu;
+#ifdef __CUDA_ARCH__
+    const float f0 = __fsub_rn(__uint_as_float(0x4B000000u | d0), 8388608.0f);
+    const float f1 = __fsub_rn(__uint_as_float(0x4B000000u | d1), 8388608.0f);
+    const __half2 h = __floats2half2_rn(f0, f1);
+    return *reinterpret_cast<const uint32_t *>(&h) | sgnmask;
+#else
+    return (f16_of_digit_bits(d0) | (f16_of_digit_bits(d1) << 16)) | sgnmask;
 #endif
 }
 

@@ -10,7 +10,8 @@ host, against exact 128-bit integer arithmetic:
   to 2^22 in magnitude, and exact_to_double(V, sc) is V 2^sc (no rounding for
   |V| < 2^53) with the same flush and saturation;
 * grid32(x, e) is trunc(|x| 2^(32 - e)) for |x| < 2^e, and bf16_digit_pair
-  the exact BF16 of one byte of each of two such values.
+  the exact BF16 of one byte of each of two such values; grid33 and
+  f16_digit_pair the same for 33 bits and 11-bit FP16 digits.
 
 The routines are __host__ __device__; the test compiles them with g++ from
 the header itself."""
@@ -188,8 +189,40 @@ int main() {
             }
         }
     }
+    // 7. the 3-slice FP16 digits: grid33 is trunc(|x| 2^(33 - e)); the FP16
+    //    digit pairs hold the 11-bit fields of two such values exactly
+    for (long it = 0; it < 1000000; ++it) {
+        const int e = (int)(g() %% 200) - 100;
+        const int bl = (int)(g() %% 70);
+        double x = ldexp((double)(g() >> 11) / 9007199254740992.0, e - bl);
+        if (g() & 1) x = -x;
+        if (!(fabs(x) < ldexp(1.0, e))) continue;
+        uint32_t sg;
+        const unsigned long long y = grid33(x, e, sg);
+        const unsigned long long want = (unsigned long long)floor(ldexp(fabs(x), 33 - e));
+        ++n;
+        if (y != want || sg != (std::signbit(x) ? 1u : 0u)) {
+            if (bad < 5) printf("grid33 x=%%a e=%%d got %%llu want %%llu\n", x, e, y, want);
+            ++bad;
+        }
+        const unsigned long long y1 = g() >> 31;
+        for (int sh = 0; sh <= 22; sh += 11) {
+            const uint32_t pr = f16_digit_pair(y, y1, sh, 0x80000000u);
+            const uint32_t d0 = (uint32_t)(y >> sh) & 0x7FFu, d1 = (uint32_t)(y1 >> sh) & 0x7FFu;
+            // decode the two FP16 halves
+            auto dec = [](uint32_t hb) {
+                const int ex = (int)((hb >> 10) & 0x1F), mt = (int)(hb & 0x3FF);
+                const double v = ex == 0 ? ldexp((double)mt, -24) : ldexp(1.0 + mt / 1024.0, ex - 15);
+                return (hb & 0x8000u) ? -v : v;
+            };
+            if (dec(pr & 0xFFFFu) != (double)d0 || dec(pr >> 16) != -(double)d1) {
+                if (bad < 5) printf("f16 digit pair shift %%d of %%llu %%llu\n", sh, y, y1);
+                ++bad;
+            }
+        }
+    }
     printf("checked %%ld bad %%ld\n", n, bad);
-    return bad != 0 || n < 6900000;
+    return bad != 0 || n < 7800000;
 }
 """
 
@@ -197,7 +230,7 @@ int main() {
 def _extract():
     src = open(HEADER).read()
     a = src.index("__host__ __device__ __forceinline__ int clz64_any")
-    b = src.index("\n}\n", src.index("uint32_t bf16_digit_pair(")) + 3
+    b = src.index("\n}\n", src.index("uint32_t f16_digit_pair(")) + 3
     return src[a:b]
 
 
