@@ -33,8 +33,9 @@
  *     rebuilds the hidden activations from scratch at every sweep with an
  *     FP64-exact tensor-core product (configurations x W cut into 7 BF16
  *     integer slices, FP32 accumulation), runs the Jacobian products on the
- *     tensor cores (4 slices in CG matvecs, 7 where the sample-space solve
- *     needs FP64-level products) and keeps FP64 for sample means, centring,
+ *     tensor cores (in CG matvecs 3 FP16 slices of 11-bit digits, 33 bits of
+ *     each operand row; 7 BF16 slices where the sample-space solve needs
+ *     FP64-level products) and keeps FP64 for sample means, centring,
  *     the SR factorisation (tensor-core products at FP64 level) and update.
  */
 #ifndef NK_H

@@ -282,8 +282,9 @@ void carve_solve(Carver &c, SolveWs &w, int N, int M, int64_t Ns, int solver, in
 }
 
 // (G + eps I) v for the on-the-fly QGT (App. B.3).
-// Slices per operand row of the NK_MIXED Jacobian products: 4 in CG matvecs
-// (2^-32 of the row maximum), 7 (FP64 level) where the sample-space solve
+// Accuracy of the NK_MIXED Jacobian products, in 8-bit slices per operand
+// row: 4 in CG matvecs (at least 2^-32 of the row maximum; run as 3 FP16
+// slices of 11 bits, 2^-33), 7 (FP64 level) where the sample-space solve
 // subtracts nearly equal vectors.
 constexpr int kMatvecSlices = 4, kExactSlices = 7;
 // Jacobi sweeps of the SVD solvers: stop at a relative off-diagonal norm of
