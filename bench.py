@@ -51,7 +51,7 @@ def measured_peaks():
 
 
 # CG stopping rule per precision: relative residual 1e-10 on the FP64 path,
-# 1e-6 on the mixed path (whose 4-slice QGT products carry about 2^-32)
+# 1e-6 on the mixed path (whose 3-slice FP16 QGT products carry about 2^-33)
 CG_TOL = {"f64": 1e-10, "mixed": 1e-6}
 # chains of the oracle's bounded sample per workload (about 10-30 s of one
 # host thread per SR step; the default is used for the others)

@@ -298,7 +298,7 @@ nk_status nk_tc_gemm(nk_ctx *ctx, int64_t rows, int64_t cols, int32_t k, const d
  * systems").  solver: NK_SOLVER_CHOLESKY (dense Np x Np FP64 Cholesky),
  * NK_SOLVER_CHOLESKY_SAMPLESPACE (FP64 Cholesky of the Ns x Ns matrix
  * dJ dJ^T / Ns + diag_shift I and delta = (F - dJ^T y / sqrt(Ns)) /
- * diag_shift, equal in exact arithmetic), NK_SOLVER_CG (Jacobi-preconditioned
+ * diag_shift, equal in exact arithmetic), NK_SOLVER_CG (unpreconditioned
  * conjugate gradients, x0 = 0, stops at ||r|| <= cg_tol ||F|| or cg_maxiter;
  * reads the residual back to the host every 8 iterations, which
  * synchronises the stream), NK_SOLVER_SVD (the pseudo-inverse of the dense

@@ -290,6 +290,7 @@ struct Tc4Args {
     double *P;            // mode 0: [n_nt][rows]; mode 1: [ks][cols][ldp] (column-major tiles)
     int64_t ldp, split_stride;
     int *err;
+    const int *skip;      // optional: nothing is done while *skip is set (a converged CG)
 };
 
 // s + e = a + b exactly (Knuth's two-sum, no ordering of |a|, |b| needed)
@@ -332,6 +333,8 @@ __device__ __forceinline__ Tc4Unit tc4_unit(const Tc4Args &a, int64_t g, uint32_
 template <int kMode>
 __global__ void __launch_bounds__(kJvThreads, 1)
     k_tc4(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, Tc4Args a) {
+    // every thread of every CTA reads the same word, written before the launch
+    if (a.skip && *a.skip) return;
     extern __shared__ unsigned char smem_raw[];
     const uint32_t base = smem_u32(smem_raw);
     unsigned char *ops = smem_raw + ((1024 - (base & 1023)) & 1023);
@@ -747,15 +750,6 @@ __device__ __forceinline__ void slice_pair(double x0, double x1, int e, int SB, 
     }
 }
 
-// The 3-slice FP16 form (11-bit digits on the 33-bit grid, tc_ptx.cuh).
-__device__ __forceinline__ void slice_pair_h3(double x0, double x1, int e, uint32_t *out, int64_t plane2) {
-    uint32_t s0, s1;
-    const unsigned long long y0 = grid33(x0, e, s0), y1 = grid33(x1, e, s1);
-    const uint32_t sg = (s0 << 15) | (s1 << 31);
-#pragma unroll
-    for (int t = 0; t < 3; ++t) out[(size_t)t * plane2] = f16_digit_pair(y0, y1, 22 - 11 * t, sg);
-}
-
 // The 4-slice case of slice_pair (grid32 and bf16_digit_pair, tc_ptx.cuh).
 __device__ __forceinline__ void slice_pair4(double x0, double x1, int e, uint32_t *out, int64_t plane2) {
     uint32_t s0, s1;
@@ -909,7 +903,7 @@ __global__ void k_colexp_bound(int M, const int *__restrict__ colexpT, const int
 // contiguous bytes per plane and row j (ld is even).
 constexpr int kTgPitch = 65;
 __global__ void __launch_bounds__(256) k_tg_slice(const double *__restrict__ T, const double *__restrict__ gp,
-                                                  int64_t Ns, int M, int SB, int f16, int64_t ld, int vec,
+                                                  int64_t Ns, int M, int SB, int64_t ld, int vec,
                                                   const int *__restrict__ expo, __nv_bfloat16 *__restrict__ out) {
     __shared__ double tile[64 * kTgPitch];  // [k][j]
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -945,12 +939,95 @@ __global__ void __launch_bounds__(256) k_tg_slice(const double *__restrict__ T, 
         const int e = expo[jj] == -100000 ? 0 : expo[jj];
         const double x0 = k < Ns ? tile[(2 * lane) * kTgPitch + jr] : 0.0;
         const double x1 = k + 1 < Ns ? tile[(2 * lane + 1) * kTgPitch + jr] : 0.0;
-        if (f16)
-            slice_pair_h3(x0, x1, e, reinterpret_cast<uint32_t *>(out + (size_t)jj * ld + k), plane2);
-        else if (SB == 4)
+        if (SB == 4)
             slice_pair4(x0, x1, e, reinterpret_cast<uint32_t *>(out + (size_t)jj * ld + k), plane2);
         else
             slice_pair(x0, x1, e, SB, reinterpret_cast<__nv_bfloat162 *>(out + (size_t)jj * ld + k), plane2);
+    }
+}
+
+// g'' = 2^-G g' as FP32 pairs (gh = fl32(g''), gl = fl32(g'' - gh): g'' - gh
+// is exact in FP64), G = *gmax (|g'_k| < 2^G for every k, so |g''| < 1);
+// an all-zero g' (G = -100000) gives zero pairs.
+__global__ void k_g_pairs(int64_t Ns, const double *__restrict__ gp, const int *__restrict__ gmax,
+                          float2 *__restrict__ g2) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= Ns) return;
+    const int G = *gmax;
+    float2 v = make_float2(0.f, 0.f);
+    if (G != -100000) {
+        const double x = ldexp(gp[k], -G);
+        const float h = __double2float_rn(x);
+        v = make_float2(h, __double2float_rn(x - (double)h));
+    }
+    g2[k] = v;
+}
+
+// (T' o g')^T as 3 FP16 slices of signed 11-bit digits on the 33-bit grid of
+// the column exponent e_j = colexpT[j] + G, from FP32 pairs only (no FP64
+// arithmetic): t' from the tile-major pairs of k_split_t, g'' = 2^-G g' from
+// k_g_pairs.  Per entry, x = t' g'' 2^(11 - colexpT[j]) (|x| <= 2^11) is
+// formed as a pair by mul_pairs and scaled exactly, then cut by
+// h3_signed_digits: x 2^22 = d0 2^22 + d1 2^11 + d2 within 1.25 units, the
+// recombination V 2^(e_j - 33) of the J^T g epilogue.  Columns whose
+// |t'| stays below 2^-100 (or are all zero) get zero digits.
+// out [3][M+1][ld] FP16, four samples per 8-byte store.  One block per 128 x
+// 64 tile of t' (the tile order of k_split_t): warp w takes column pairs 4w
+// .. 4w + 3, lane l samples 4l .. 4l + 3 of the tile.  With skip set (the CG
+// has converged) the kernel does nothing.
+__global__ void __launch_bounds__(256) k_tg_slice_hl(int64_t Ns, int M, int n_nt, int64_t ld,
+                                                     const float4 *__restrict__ Thl, const float2 *__restrict__ g2,
+                                                     const int *__restrict__ colexpT, const int *__restrict__ skip,
+                                                     uint2 *__restrict__ out) {
+    if (skip && *skip) return;
+    const int nt = blockIdx.x;
+    const int64_t mt = blockIdx.y;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t k0 = mt * kBM + 4 * lane;
+    if (k0 >= ld) return;  // ld is a multiple of 8: a lane's four samples are all in or all out
+    float gh[4], gl[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float2 v = k0 + i < Ns ? __ldg(g2 + k0 + i) : make_float2(0.f, 0.f);
+        gh[i] = v.x;
+        gl[i] = v.y;
+    }
+    const float4 *src = Thl + ((size_t)mt * n_nt + nt) * (kBN / 2) * kBM + 4 * lane;
+    const int64_t plane = (int64_t)(M + 1) * ld / 4;  // uint2 per plane
+#pragma unroll 2
+    for (int c = 0; c < 4; ++c) {
+        const int cp = 4 * w + c;
+        const int j0 = nt * kBN + 2 * cp;
+        if (j0 > M) break;
+        float4 v[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v[i] = __ldcs(src + (size_t)cp * kBM + i);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int j = j0 + h;
+            if (j > M) break;
+            const int cT = __ldg(colexpT + j);
+            float d[3][4];
+            if (cT < -100) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) d[0][i] = d[1][i] = d[2][i] = 0.f;
+            } else {
+                // 2^(11 - cT) in two exact factors (11 - cT <= 111 here)
+                const int a1 = 11 - cT > 64 ? 64 : 11 - cT, a2 = 11 - cT - a1;
+                const float s1 = __int_as_float((127 + a1) << 23), s2 = __int_as_float((127 + a2) << 23);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    float ph, pl;
+                    mul_pairs(h ? v[i].z : v[i].x, h ? v[i].w : v[i].y, gh[i], gl[i], ph, pl);
+                    h3_signed_digits(__fmul_rn(__fmul_rn(ph, s1), s2), __fmul_rn(__fmul_rn(pl, s1), s2), d[0][i],
+                                     d[1][i], d[2][i]);
+                }
+            }
+            uint2 *dst = out + ((size_t)j * ld + k0) / 4;
+#pragma unroll
+            for (int t = 0; t < 3; ++t)
+                dst[(size_t)t * plane] = make_uint2(f16_int_pair(d[t][0], d[t][1]), f16_int_pair(d[t][2], d[t][3]));
+        }
     }
 }
 
@@ -1154,7 +1231,8 @@ constexpr int kH3MaxK = 8192;
 // J v partials P [n_nt][rows] = per 64-column tile, sum_col (A B^T)[row][col]
 // t'_col by k_tc4 mode 0 (A FP16 +-1, B 3 FP16 slices; K <= 8192).
 cudaError_t jvp4(const void *A, int64_t rows, int64_t ldA, const void *Bsl, const int *expB, int64_t cols,
-                 int64_t ldB, int64_t K, const void *Thl, int Mt, double *P, int *err, cudaStream_t st) {
+                 int64_t ldB, int64_t K, const void *Thl, int Mt, double *P, int *err, cudaStream_t st,
+                 const int *skip) {
     if (rows <= 0 || cols <= 0 || K <= 0) return cudaSuccess;
     if (K > kH3MaxK || rows > (1LL << 31) - kBM || cols > (1LL << 31) - kBN || Thl == nullptr)
         return cudaErrorInvalidValue;
@@ -1169,7 +1247,7 @@ cudaError_t jvp4(const void *A, int64_t rows, int64_t ldA, const void *Bsl, cons
     const int n_mg = (int)((n_mt + C - 1) / C);
     const int kchunks = (int)((K + kBK - 1) / kBK);
     Tc4Args a{rows, cols, kchunks, kchunks, 1, n_nt, n_mg, C, (int64_t)n_mg * n_nt, expB,
-              reinterpret_cast<const float4 *>(Thl), P, 0, 0, err};
+              reinterpret_cast<const float4 *>(Thl), P, 0, 0, err, skip};
     return launch_tc4<kTcRowDot>(ma, mb, a, st);
 }
 
@@ -1179,7 +1257,7 @@ cudaError_t jvp4(const void *A, int64_t rows, int64_t ldA, const void *Bsl, cons
 // units is nearly full.
 cudaError_t vjp4(const void *A, int64_t rows, int64_t ldA, const void *Bsl, const int *expB, int64_t cols,
                  int64_t ldB, int64_t K, double *P, int64_t ldp, int64_t split_stride, int max_ks, int *ks_out,
-                 int *err, cudaStream_t st) {
+                 int *err, cudaStream_t st, const int *skip) {
     if (rows <= 0 || cols <= 0 || K <= 0) return cudaSuccess;
     if (rows > (1LL << 31) - kBM || cols > (1LL << 31) - kBN || ldp < rows) return cudaErrorInvalidValue;
     CUtensorMap ma, mb;
@@ -1206,7 +1284,7 @@ cudaError_t vjp4(const void *A, int64_t rows, int64_t ldA, const void *Bsl, cons
     ks = (kchunks + kc_split - 1) / kc_split;
     *ks_out = ks;
     Tc4Args a{rows, cols, kchunks, kc_split, ks, n_nt, n_mt, 1, (int64_t)n_mt * n_nt * ks, expB, nullptr, P, ldp,
-              split_stride, err};
+              split_stride, err, skip};
     return launch_tc4<kTcStoreT>(ma, mb, a, st);
 }
 
@@ -1288,7 +1366,7 @@ cudaError_t launch_jacobian_operands(int N, int64_t Ns, const int8_t *s, void *o
 // products taken in the S-GEMM epilogue per 64-column tile and summed after.
 cudaError_t launch_jvp_tc(int N, int M, int64_t Ns, const int8_t *s, const double *T, const double *v,
                           double *out, int SB, int *err, void *ws, cudaStream_t st, const void *opA,
-                          const void *Thl) {
+                          const void *Thl, const int *skip) {
     const int64_t ld = pad8(N + 1);
     char *p = static_cast<char *>(ws);
     auto take = [&](size_t bytes) {
@@ -1327,7 +1405,7 @@ cudaError_t launch_jvp_tc(int N, int M, int64_t Ns, const int8_t *s, const doubl
         Thl = own;
     }
     const int slot = prof_begin(NK_PROF_JVP_VJP, st);
-    cudaError_t e = persistent ? jvp4(As, Ns, ld, Vs, ev, M + 1, ld, N + 1, Thl, M, P, err, st)
+    cudaError_t e = persistent ? jvp4(As, Ns, ld, Vs, ev, M + 1, ld, N + 1, Thl, M, P, err, st, skip)
                                : sgemm(As, Ns, ld, Vs, ev, M + 1, ld, N + 1, SB, P, ntc, 3, nullptr, err, st, T, M);
     prof_end(slot, st, 2.0 * (double)Ns * (N + 1) * (double)(M + 1),
              sgemm_flops(Ns, M + 1, N + 1, persistent ? kJvSB : SB));
@@ -1362,7 +1440,11 @@ size_t tc_vjp_ws_bytes(int N, int M, int64_t Ns) {
     return ((size_t)(N + 1) * ld * 2 + 255) / 256 * 256 + ((size_t)kMaxSB * (M + 1) * ld * 2 + 255) / 256 * 256 +
            ((size_t)(M + 2) * 4 + 255) / 256 * 256 +
            ((size_t)kMaxKSplit * (N + 1) * (M + 1) * 8 + 255) / 256 * 256 + ((size_t)Ns * 8 + 255) / 256 * 256 +
-           ((size_t)Ns * 4 + 255) / 256 * 256 + 256;
+           ((size_t)Ns * 4 + 255) / 256 * 256 + 256 +
+           // the 3-slice path: g'' pairs, and the column exponents and t'
+           // pairs of T when the caller does not pass them
+           ((size_t)Ns * 8 + 255) / 256 * 256 + ((size_t)(M + 1) * 4 + 255) / 256 * 256 +
+           (tc_colexp_ws_bytes(M, Ns) + 255) / 256 * 256 + (tc_split_t_bytes(M, Ns) + 255) / 256 * 256;
 }
 
 // out = J^T g' with g' = scale (g - shift), (T' o g')^T cut into SB slices.
@@ -1380,7 +1462,8 @@ cudaError_t launch_colexp_t(int M, int64_t Ns, const double *T, int *colexpT, vo
 
 cudaError_t launch_vjp_tc(int N, int M, int64_t Ns, const int8_t *s, const double *T, const double *g,
                           double scale, const double *shift, double *out, int SB, int *err, void *ws,
-                          cudaStream_t st, const int *colexpT, const void *opT) {
+                          cudaStream_t st, const int *colexpT, const void *opT, const void *Thl,
+                          const int *skip) {
     const int64_t ld = pad8(Ns);
     char *p = static_cast<char *>(ws);
     auto take = [&](size_t bytes) {
@@ -1407,19 +1490,41 @@ cudaError_t launch_vjp_tc(int N, int M, int64_t Ns, const int8_t *s, const doubl
     else
         (k_pm1_cols<<<dim3(nblk(ld, 32), nblk(N + 1, 32)), tb, 0, st>>>(s, Ns, N, ld, St), nk::note_launch());
     (k_scale_g<<<nblk(Ns, 256), 256, 0, st>>>(Ns, g, scale, shift, gp, ge), nk::note_launch());
-    if (colexpT) {
-        // the column bound: no pass over T (eg[M + 1] holds max_k ge[k])
+    if (h3) {
+        // 3 FP16 slices from FP32 pairs: the column exponents of T and its
+        // tile-major pairs (given once per solve by the CG, else built here),
+        // the bound e_j = colexpT[j] + max_k exp(g'_k), g'' = 2^-G g' as pairs
+        const int *cT = colexpT;
+        if (cT == nullptr) {
+            int *own = reinterpret_cast<int *>(take((size_t)(M + 1) * 4));
+            cudaError_t ec = launch_colexp_t(M, Ns, T, own, take(tc_colexp_ws_bytes(M, Ns)), st);
+            if (ec != cudaSuccess) return ec;
+            cT = own;
+        }
+        if (Thl == nullptr) {
+            void *own = take(tc_split_t_bytes(M, Ns));
+            cudaError_t es = launch_split_t(M, Ns, T, own, st);
+            if (es != cudaSuccess) return es;
+            Thl = own;
+        }
+        auto *g2 = reinterpret_cast<float2 *>(take((size_t)Ns * 8));
         (k_max_exp<<<1, 1024, 0, st>>>(Ns, ge, eg + M + 1), nk::note_launch());
-        (k_colexp_bound<<<nblk(M + 1, 256), 256, 0, st>>>(M, colexpT, eg + M + 1, eg), nk::note_launch());
+        (k_colexp_bound<<<nblk(M + 1, 256), 256, 0, st>>>(M, cT, eg + M + 1, eg), nk::note_launch());
+        (k_g_pairs<<<nblk(Ns, 256), 256, 0, st>>>(Ns, gp, eg + M + 1, g2), nk::note_launch());
+        const int n_nt = (M + 1 + kBN - 1) / kBN;
+        const int64_t n_mt = (Ns + kBM - 1) / kBM;
+        if (n_mt > 65535) return cudaErrorInvalidValue;
+        (k_tg_slice_hl<<<dim3(n_nt, (unsigned)n_mt), 256, 0, st>>>(Ns, M, n_nt, ld, static_cast<const float4 *>(Thl),
+                                                                   g2, cT, skip, reinterpret_cast<uint2 *>(Gs)),
+         nk::note_launch());
     } else {
         (k_fill_int<<<nblk(M + 1, 256), 256, 0, st>>>(M + 1, -100000, eg), nk::note_launch());
         (k_tg_colexp<<<dim3(nblk(M + 1, 32), nblk(Ns, 256)), dim3(32, 8), 0, st>>>(T, ge, Ns, M, eg),
          nk::note_launch());
+        const int vec = (M % 2 == 0) && ((reinterpret_cast<uintptr_t>(T) & 15) == 0);
+        (k_tg_slice<<<dim3(nblk(ld, 64), nblk(M + 1, 64)), 256, 0, st>>>(T, gp, Ns, M, SB, ld, vec, eg, Gs),
+         nk::note_launch());
     }
-    const int vec = (M % 2 == 0) && ((reinterpret_cast<uintptr_t>(T) & 15) == 0);
-    (k_tg_slice<<<dim3(nblk(ld, 64), nblk(M + 1, 64)), 256, 0, st>>>(T, gp, Ns, M, h3 ? kJvSB : SB, h3 ? 1 : 0, ld,
-                                                                        vec, eg, Gs),
-     nk::note_launch());
     // split the long K = Ns range so that the last wave of CTAs is nearly
     // full (every split keeps >= 4 chunks; each split's FP32 levels stay exact)
     int dev = 0, sms = 0, per_sm = 0;
@@ -1435,7 +1540,7 @@ cudaError_t launch_vjp_tc(int N, int M, int64_t Ns, const int8_t *s, const doubl
         // the persistent kernel, P^T column-major
         int ks4 = 1;
         const int slot = prof_begin(NK_PROF_JVP_VJP, st);
-        e = vjp4(St, N + 1, ld, Gs, eg, M + 1, ld, Ns, PT, N + 1, tot, kMaxKSplit, &ks4, err, st);
+        e = vjp4(St, N + 1, ld, Gs, eg, M + 1, ld, Ns, PT, N + 1, tot, kMaxKSplit, &ks4, err, st, skip);
         prof_end(slot, st, 2.0 * (double)Ns * (N + 1) * (double)(M + 1), sgemm_flops(N + 1, M + 1, Ns, kJvSB));
         if (e != cudaSuccess) return e;
         (k_scatter_vjp_t<<<nblk(tot, 256), 256, 0, st>>>(N, M, ks4, PT, out), nk::note_launch());

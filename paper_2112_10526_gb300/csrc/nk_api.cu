@@ -209,6 +209,7 @@ struct SolveWs {
     void *opA, *opT;  // NK_MIXED CG: the +-1 product operands, built once per solve
     void *thl;        // NK_MIXED CG: tanh(theta) as FP32 pairs, built once per solve
     bool ops_ready;   // opA / opT / thl hold the operands of the samples being solved for
+    const int *skip;  // NK_MIXED CG: its converged flag (the products then do nothing)
     int *tcerr; // sticky tensor-core error word of the context
 };
 
@@ -296,7 +297,7 @@ cudaError_t jvp_any(int N, int M, int64_t Ns, const int8_t *s, const double *T, 
                     double *out, int precision, int slices, cudaStream_t st) {
     if (precision == NK_MIXED)
         return nk::launch_jvp_tc(N, M, Ns, s, T, v, out, slices, w.tcerr, w.tcm, st, w.ops_ready ? w.opA : nullptr,
-                                 w.ops_ready ? w.thl : nullptr);
+                                 w.ops_ready ? w.thl : nullptr, w.ops_ready ? w.skip : nullptr);
     return nk::launch_jvp(N, M, Ns, s, T, v, w.U, out, st);
 }
 
@@ -305,7 +306,8 @@ cudaError_t vjp_any(int N, int M, int64_t Ns, const int8_t *s, const double *T, 
                     const int *colexpT = nullptr) {
     if (precision == NK_MIXED)
         return nk::launch_vjp_tc(N, M, Ns, s, T, g, scale, shift, out, slices, w.tcerr, w.tcm, st, colexpT,
-                                 w.ops_ready ? w.opT : nullptr);
+                                 w.ops_ready ? w.opT : nullptr, w.ops_ready ? w.thl : nullptr,
+                                 w.ops_ready ? w.skip : nullptr);
     return nk::launch_vjp(N, M, Ns, s, T, g, scale, shift, w.partial, out, st);
 }
 
@@ -371,9 +373,15 @@ nk_status run_solve(nk_ctx *ctx, int N, int M, int64_t Ns, const int8_t *s, cons
         // the operands stay valid for this solve's samples only
         struct OpsReady {
             SolveWs &w;
-            ~OpsReady() { w.ops_ready = false; }
+            ~OpsReady() {
+                w.ops_ready = false;
+                w.skip = nullptr;
+            }
         } ops_guard{w};
         w.ops_ready = tc;
+        // the iterations after convergence, up to the next poll, skip the
+        // products (their results are discarded by the update kernels)
+        w.skip = tc ? done : nullptr;
         NK_CU(nk::launch_fill(Np, 0.0, w.x, st), "cg init");
         NK_CU(nk::launch_axpby(Np, 1.0, F, 0.0, w.r, st), "cg init");
         NK_CU(nk::launch_axpby(Np, 1.0, F, 0.0, w.p, st), "cg init");

@@ -225,18 +225,23 @@ size_t tc_split_t_bytes(int M, int64_t Ns);
 cudaError_t launch_split_t(int M, int64_t Ns, const double *T, void *Thl, cudaStream_t st);
 size_t tc_jvp_ws_bytes(int N, int M, int64_t Ns);
 // opA (optional): the prebuilt J v operand of launch_jacobian_operands;
-// Thl (optional): the pairs of launch_split_t for T (else built in ws).
+// Thl (optional): the pairs of launch_split_t for T (else built in ws);
+// skip (optional, device int): the product kernel does nothing while *skip
+// is set (the converged flag of a CG whose loop still runs to its next poll).
 cudaError_t launch_jvp_tc(int N, int M, int64_t Ns, const int8_t *s, const double *T, const double *v,
                           double *out, int SB, int *err, void *ws, cudaStream_t st, const void *opA = nullptr,
-                          const void *Thl = nullptr);
+                          const void *Thl = nullptr, const int *skip = nullptr);
 size_t tc_vjp_ws_bytes(int N, int M, int64_t Ns);
 // colexpT (optional, [M + 1], from launch_colexp_t): the column exponents of
 // tanh(theta), so that the slices of (T' o g')^T take their exponents from
 // the bound max_k |t'_kj| max_k |g'_k| instead of a pass over T.  opT
-// (optional): the prebuilt J^T g operand of launch_jacobian_operands.
+// (optional): the prebuilt J^T g operand of launch_jacobian_operands.  Thl
+// and skip as for launch_jvp_tc (the 3-slice path slices (T' o g')^T from
+// the FP32 pairs of T; without Thl or colexpT it builds them in ws).
 cudaError_t launch_vjp_tc(int N, int M, int64_t Ns, const int8_t *s, const double *T, const double *g,
                           double scale, const double *shift, double *out, int SB, int *err, void *ws,
-                          cudaStream_t st, const int *colexpT = nullptr, const void *opT = nullptr);
+                          cudaStream_t st, const int *colexpT = nullptr, const void *opT = nullptr,
+                          const void *Thl = nullptr, const int *skip = nullptr);
 size_t tc_colexp_ws_bytes(int M, int64_t Ns);
 cudaError_t launch_colexp_t(int M, int64_t Ns, const double *T, int *colexpT, void *ws, cudaStream_t st);
 

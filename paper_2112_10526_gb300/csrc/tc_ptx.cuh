@@ -435,6 +435,62 @@ __host__ __device__ __forceinline__ uint32_t f16_digit_pair(unsigned long long y
 #endif
 }
 
+// The product t g of two FP32 pairs (t = th + tl, g = gh + gl, |tl| <=
+// 2^-24 |th|, |gl| <= 2^-24 |gh|) as an unevaluated FP32 pair (ph, pl):
+// ph = fl(th gh), whose rounding error th gh - ph the FMA gives exactly, and
+// pl = fl(th gl + fl(tl gh + (th gh - ph))).  tl gl is dropped; |t g - ph -
+// pl| stays below about 2^-44 |t g|.
+__host__ __device__ __forceinline__ void mul_pairs(float th, float tl, float gh, float gl, float &ph, float &pl) {
+#ifdef __CUDA_ARCH__
+    ph = __fmul_rn(th, gh);
+    pl = __fmaf_rn(th, gl, __fmaf_rn(tl, gh, __fmaf_rn(th, gh, -ph)));
+#else
+    ph = th * gh;
+    pl = fmaf(th, gl, fmaf(tl, gh, fmaf(th, gh, -ph)));
+#endif
+}
+
+// Three signed 11-bit digits of x = xh + xl (|xh| <= 2^11, |xl| <= 2^-22
+// |xh|, FP32), rounded to nearest:
+//     d0 = rint(xh),  s1 = fl(2^11 (xh - d0) + 2^11 xl),  d1 = rint(s1),
+//     d2 = rint(2^11 (s1 - d1)).
+// xh - d0 and s1 - d1 are exact (an FP32 value minus its nearest integer),
+// and the scalings by 2^11 are exact, so the only roundings are the sum s1
+// (at most 2^-14, |s1| <= 1024.5) and the last digit: |x - (d0 + 2^-11 d1 +
+// 2^-22 d2)| <= 2^-23 + 2^-25.  |d0| <= 2048, |d1| <= 1025, |d2| <= 1024:
+// integers that FP16 holds exactly.
+__host__ __device__ __forceinline__ void h3_signed_digits(float xh, float xl, float &d0, float &d1, float &d2) {
+#ifdef __CUDA_ARCH__
+    d0 = rintf(xh);
+    const float s1 = __fmaf_rn(__fsub_rn(xh, d0), 2048.0f, __fmul_rn(xl, 2048.0f));
+    d1 = rintf(s1);
+    d2 = rintf(__fmul_rn(__fsub_rn(s1, d1), 2048.0f));
+#else
+    d0 = rintf(xh);
+    const float s1 = fmaf(xh - d0, 2048.0f, xl * 2048.0f);
+    d1 = rintf(s1);
+    d2 = rintf((s1 - d1) * 2048.0f);
+#endif
+}
+
+// Two integer-valued floats |a|, |b| <= 2048 as the low and high FP16 of a
+// pair (exact).
+__host__ __device__ __forceinline__ uint32_t f16_int_pair(float a, float b) {
+#ifdef __CUDA_ARCH__
+    const __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<const uint32_t *>(&h);
+#else
+    auto one = [](float v) -> uint32_t {
+        uint32_t bits;
+        __builtin_memcpy(&bits, &v, 4);
+        const uint32_t sg = (bits >> 16) & 0x8000u;  // -0 keeps its sign, as on the device
+        const uint32_t d = (uint32_t)(v < 0.0f ? -v : v);
+        return sg | (d == 2048u ? 0x6800u : f16_of_digit_bits(d));
+    };
+    return one(a) | (one(b) << 16);
+#endif
+}
+
 // ------------------------------------------------------ host: tensor maps ---
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,

@@ -11,7 +11,10 @@ host, against exact 128-bit integer arithmetic:
   |V| < 2^53) with the same flush and saturation;
 * grid32(x, e) is trunc(|x| 2^(32 - e)) for |x| < 2^e, and bf16_digit_pair
   the exact BF16 of one byte of each of two such values; grid33 and
-  f16_digit_pair the same for 33 bits and 11-bit FP16 digits.
+  f16_digit_pair the same for 33 bits and 11-bit FP16 digits;
+* mul_pairs and h3_signed_digits give the signed 11-bit digits of a product
+  of two FP32 pairs within 2^-23 + 2^-25 of the exact product (in units of
+  the leading digit), and f16_int_pair encodes them exactly.
 
 The routines are __host__ __device__; the test compiles them with g++ from
 the header itself."""
@@ -221,8 +224,57 @@ int main() {
             }
         }
     }
+    // 8. the 3-slice digits of the CG's J^T g operand, from FP32 pairs: t and
+    //    g'' as pairs (hi = fl32(x), lo = fl32(x - hi)), x = t g'' 2^(11 - cT)
+    //    with |t| < 2^cT and |g''| < 1.  d0 + 2^-11 d1 + 2^-22 d2 must lie
+    //    within 2^-23 + 2^-25 of x (plus 2^-40 for the dropped lo x lo term
+    //    and the pair product's roundings), the digits must be integers with
+    //    |d0| <= 2048, |d1| <= 1025, |d2| <= 1024, and the FP16 pairs must
+    //    hold them exactly.
+    auto dec16 = [](uint32_t hb) {
+        const int ex = (int)((hb >> 10) & 0x1F), mt = (int)(hb & 0x3FF);
+        const double v = ex == 0 ? ldexp((double)mt, -24) : ldexp(1.0 + mt / 1024.0, ex - 15);
+        return (hb & 0x8000u) ? -v : v;
+    };
+    long near_edge = 0;
+    for (long it = 0; it < 1000000; ++it) {
+        const int cT = -(int)(g() %% 60);
+        const int drop = (g() %% 4 == 0) ? (int)(g() %% 40) : 0;  // entries far below the column bound
+        double t = ldexp((double)(g() >> 11) / 9007199254740992.0, cT - drop);
+        if (it %% 7 == 3) t = ldexp(1.0 - ldexp(1.0, -53), cT);  // just below the bound
+        if (g() %% 50 == 0) t = 0.0;
+        if (g() & 1) t = -t;
+        double gg = (double)(g() >> 11) / 9007199254740992.0;
+        if (g() %% 4 == 0) gg = ldexp(gg, -(int)(g() %% 30));
+        if (it %% 7 == 3) gg = 1.0 - ldexp(1.0, -53);
+        if (g() & 1) gg = -gg;
+        const float th = (float)t, tl = (float)(t - (double)th);
+        const float gh = (float)gg, gl = (float)(gg - (double)gh);
+        float ph, pl, d0, d1, d2;
+        mul_pairs(th, tl, gh, gl, ph, pl);
+        const float sc = ldexpf(1.0f, 11 - cT);
+        h3_signed_digits(ph * sc, pl * sc, d0, d1, d2);
+        const long double x = (long double)t * (long double)gg * ldexpl(1.0L, 11 - cT);
+        const long double approx = (long double)d0 + ldexpl((long double)d1, -11) + ldexpl((long double)d2, -22);
+        const long double err = fabsl(approx - x);
+        const bool ints = d0 == rintf(d0) && d1 == rintf(d1) && d2 == rintf(d2);
+        const bool range = fabsf(d0) <= 2048.f && fabsf(d1) <= 1025.f && fabsf(d2) <= 1024.f;
+        if (fabsl(x) > 2047.0L) ++near_edge;
+        ++n;
+        if (!ints || !range || !(err <= ldexpl(1.0L, -23) + ldexpl(1.0L, -25) + ldexpl(1.0L, -40))) {
+            if (bad < 5) printf("h3 digits t=%%a g=%%a cT=%%d: %%g %%g %%g err %%Lg\n", t, gg, cT, d0, d1, d2, err);
+            ++bad;
+        }
+        const uint32_t p01 = f16_int_pair(d0, d1), p2 = f16_int_pair(d2, -d0);
+        if (dec16(p01 & 0xFFFFu) != (double)d0 || dec16(p01 >> 16) != (double)d1 ||
+            dec16(p2 & 0xFFFFu) != (double)d2 || dec16(p2 >> 16) != -(double)d0) {
+            if (bad < 5) printf("f16 int pair %%g %%g %%g\n", d0, d1, d2);
+            ++bad;
+        }
+    }
+    if (near_edge < 1000) { printf("too few cases near |x| = 2^11: %%ld\n", near_edge); ++bad; }
     printf("checked %%ld bad %%ld\n", n, bad);
-    return bad != 0 || n < 7800000;
+    return bad != 0 || n < 8800000;
 }
 """
 
@@ -230,7 +282,7 @@ int main() {
 def _extract():
     src = open(HEADER).read()
     a = src.index("__host__ __device__ __forceinline__ int clz64_any")
-    b = src.index("\n}\n", src.index("uint32_t f16_digit_pair(")) + 3
+    b = src.index("\n}\n", src.index("uint32_t f16_int_pair(")) + 3
     return src[a:b]
 
 
