@@ -386,24 +386,38 @@ def e2e_steps(st, K, dev):
 
 # DRAM bytes (read + write) per launch of the dominant kernels, from one ncu
 # capture each (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the
-# sha256 of the kernel's source section so that a changed kernel reports no
-# stale figure.  k_ozaki_gemm: per 128 x 32 output tile with 7 slices (the
-# 8064 x 8064 lower update of the 10 x 10 workload: 472.76 MB over 8064
-# tiles).
-OZAKI_TRAFFIC = {"bytes_per_tile": 59062.3, "source_sha256_prefix": "dadcb0eb2cc3d6e5"}
+# sha256 of the kernel's own source section so that a changed kernel reports
+# no stale figure.
+# k_ozaki_gemm: per 128 x 32 output tile with 7 slices (the 8064 x 8064
+# lower update of the 10 x 10 workload: 472.76 MB over 8064 tiles).
+OZAKI_TRAFFIC = {"bytes_per_tile": 59062.3, "source_sha256_prefix": "393611d8bf30c3e9"}
 OZAKI_TILE_FLOPS = 28 * 4 * 2.0 * 128 * 32 * 16  # executed BF16 flops per tile (7 slices)
+# k_tc4 (the CG's J v and J^T g products): bytes per launch captured on the
+# 24 x 24 workload at 1024 chains (Ns = 8192): J v 331.97 MB read + 3.73 MB
+# written, J^T g 243.35 + 27.45 MB.  Both read their operands once, which
+# grow with Ns (the tanh(theta) pairs, the +-1 operand, the (T' o g')^T
+# digits), so a launch at Ns samples moves about Ns / 8192 times as much.
+TC4_TRAFFIC = {"ns": 8192, "jv": 335692544, "jtg": 270804736, "source_sha256_prefix": "67e6beb986482524"}
 
 
-def ozaki_source_hash():
+def _section_hash(fname, start, end):
     import hashlib
     here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2112_10526_gb300", "csrc")
     try:
-        s = open(os.path.join(here, "k_tc.cu")).read()
-        a = s.index("// ------------------------------------------------------------- the GEMM ---")
-        b = s.index("// ------------------------------------------------- Cholesky building blocks ---")
-        return hashlib.sha256((s[a:b] + open(os.path.join(here, "tc_ptx.cuh")).read()).encode()).hexdigest()
+        s = open(os.path.join(here, fname)).read()
+        return hashlib.sha256(s[s.index(start):s.index(end)].encode()).hexdigest()
     except (OSError, ValueError):
         return ""
+
+
+def ozaki_source_hash():
+    return _section_hash("k_tc.cu", "// ------------------------------------------------------------- the GEMM ---",
+                         "// ------------------------------------------------- Cholesky building blocks ---")
+
+
+def tc4_source_hash():
+    return _section_hash("k_sgemm.cu", "// ------------------------------ J v and J^T g: persistent, 3 FP16 slices ---",
+                         "// ------------------------------------------------------- operand staging ---")
 
 
 TENSOR_CLASSES = ("chol_update", "gram", "jvp_vjp")
@@ -430,8 +444,8 @@ def class_roofline(cls, ms, launches, work, executed, precision):
     elif cls in TENSOR_CLASSES and precision == "mixed":
         out.update(bound="tensor", unit="TFLOP/s", achieved=work / secs / 1e12,
                    peak=peaks["bf16_tflops_sustained"],
-                   peak_source=f"bf16 dense, sustained ({src}); the FP64-accurate products run as "
-                               f"BF16 slice products",
+                   peak_source=f"bf16 dense, sustained ({src}); the products run as BF16 / FP16 integer-slice "
+                               f"products (FP16 at the BF16 rate)",
                    algorithmic_work="flops of the FP64 operation",
                    executed_tflops=executed / secs / 1e12,
                    executed_frac=executed / secs / 1e12 / peaks["bf16_tflops_sustained"])
@@ -447,9 +461,10 @@ def class_roofline(cls, ms, launches, work, executed, precision):
     return out
 
 
-def roofline(prof, K, precision):
+def roofline(prof, K, precision, ns=None):
     """The dominant tracked kernel class by time, with its DRAM traffic per
-    launch where a capture of the same kernel source exists."""
+    launch where a capture of the same kernel source exists (ns: the
+    workload's samples, for the Jacobian products)."""
     cls = max(prof, key=lambda c: prof[c][0])
     ms, launches, work = prof[cls][:3]
     executed = prof[cls][3] if len(prof[cls]) > 3 else work
@@ -461,6 +476,11 @@ def roofline(prof, K, precision):
             ozaki_source_hash().startswith(OZAKI_TRAFFIC["source_sha256_prefix"]):
         # bytes per launch, like achieved: the class's tiles x the captured bytes per tile
         traffic = executed / OZAKI_TILE_FLOPS * OZAKI_TRAFFIC["bytes_per_tile"] / launches
+    if cls == "jvp_vjp" and precision == "mixed" and ns and \
+            tc4_source_hash().startswith(TC4_TRAFFIC["source_sha256_prefix"]):
+        # the mean of a J v and a J^T g launch of k_tc4, scaled to the workload's Ns
+        traffic = 0.5 * (TC4_TRAFFIC["jv"] + TC4_TRAFFIC["jtg"]) * ns / TC4_TRAFFIC["ns"]
+        rf["traffic_kernel"] = "k_tc4 (mean of J v and J^T g), captured at Ns = 8192 and scaled by Ns"
     rf["traffic"] = traffic
     rf["traffic_unit"] = "DRAM bytes per launch"
     return rf, cls
@@ -536,11 +556,11 @@ def run_ours(args, rank, world):
     value = replica_value(world, K, ms_plain)
     stats = r["stats"]
     prof_step = {c: (v[0] / K, v[1] / K, v[2] / K, v[3] / K) for c, v in prof.items()}
-    rf, dom = roofline(prof, K, args.precision)
+    Ns = w["chains"] * w["per_chain"]
+    rf, dom = roofline(prof, K, args.precision, ns=Ns)
     if rf is not None:
         rf["share_of_step"] = prof[dom][0] / r["ms_prof"]
     e2e_dt, bi, bo = r["e2e"]
-    Ns = w["chains"] * w["per_chain"]
     line = {
         "metric": METRIC, "value": value, "unit": "SR steps/s", "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms_plain / K, "higher_is_better": True,
@@ -586,7 +606,7 @@ def run_ours(args, rank, world):
         we = workload(name)
         re_ = measure(we, args.precision, K, args.warmup, rank, world, dev)
         Ke = K
-        dom_rf, _ = roofline(re_["prof"], Ke, args.precision)
+        dom_rf, _ = roofline(re_["prof"], Ke, args.precision, ns=we["chains"] * we["per_chain"])
         extra[name] = {"value": Ke / (re_["ms"] / 1e3), "unit": "SR steps/s", "ms_per_step": re_["ms"] / Ke,
                        "e2e": {"value": Ke / re_["e2e"][0], "unit": "SR steps/s",
                                "h2d_bytes_per_step": re_["e2e"][1], "d2h_bytes_per_step": re_["e2e"][2]},

@@ -238,13 +238,14 @@ __global__ void __launch_bounds__(kSgThreads, 2)
     }
 }
 
-// ------------------------------------------- J v: persistent, 4 slices ---
+// ------------------------------ J v and J^T g: persistent, 3 FP16 slices ---
 //
 // The CG products of NK_MIXED as one persistent kernel per SM, on FP16
 // slices: B (V' for J v, (T' o g')^T for J^T g) is cut into 3 slices of
 // 11-bit digits on a 33-bit grid per operand row (FP16 holds every integer up
 // to 2048 exactly), A is the +-1 operand in FP16, and each FP32 level sums
-// K products below 2^11, exact while K 2047 < 2^24 (K <= 8192 per unit).
+// K products of at most 2^11 in magnitude, exact while K 2^11 <= 2^24 (K <=
+// 8192 per unit).
 // Warp 0 streams A / B K-chunks through a 5-stage TMA ring (40 KB a stage),
 // warp 1 issues the MMAs of a 128 x 64 tile (3 slices side by side, N = 192)
 // into one of two TMEM accumulator sets, and 16 epilogue warps drain the
