@@ -860,12 +860,17 @@ __global__ void __launch_bounds__(128) k_eloc(ElocK<R> P) {
 }
 
 // ------------------------------------------- sample-batched local energy ---
-// Large M (NK_MIXED, theta given): one CTA of kEW warps holds tanh(theta) of
-// kEG samples in shared memory; every warp takes connections (sites, or
-// edges) in turn, loads each tau row once (16-byte loads, lanes over units)
-// and applies it to all kEG samples, so the tau traffic per ratio term drops
-// kEG-fold.  One warp reduction per (connection, sample).
-constexpr int kEG = 8, kEW = 16;
+// Large M (NK_MIXED, theta given): one CTA of eloc_warps(kU) warps holds
+// tanh(theta) of kEG samples in shared memory; every warp takes connections
+// (sites, or edges) in turn, loads each tau row once (16-byte loads, lanes
+// over units) and applies it to all kEG samples, so the tau traffic per ratio
+// term drops kEG-fold.  One warp reduction per (connection, sample).
+constexpr int kEG = 8;
+// Warps per CTA.  At M >= 4096 the t of kEG samples (147 KB at M = 4608)
+// leaves room for one CTA per SM, and the kernel waits on shared-memory and
+// fixed latencies: 32 warps instead of 16 took the 24 x 24 local energies
+// from 62.1 to 52.1 ms a step.
+__host__ __device__ constexpr int eloc_warps(int kU) { return kU == 4 ? 32 : 16; }
 
 struct ElocBK {
     Tables<float> t;
@@ -877,7 +882,8 @@ struct ElocBK {
 // shared-memory t of kEG samples allows one CTA per SM anyway (M >= 4096),
 // else 1 (the extra registers of 4 would halve the resident CTAs).
 template <int kU>
-__global__ void __launch_bounds__(kEW * 32) k_eloc_batched(ElocBK P) {
+__global__ void __launch_bounds__(eloc_warps(kU) * 32) k_eloc_batched(ElocBK P) {
+    constexpr int kEW = eloc_warps(kU);
     extern __shared__ __align__(16) unsigned char sm[];
     const Tables<float> &T = P.t;
     const ElocArgs &A = P.a;
@@ -1202,9 +1208,9 @@ cudaError_t launch_sweep(const Tables<R> &t, const SweepArgs &a, cudaStream_t st
 template cudaError_t launch_sweep<double>(const Tables<double> &, const SweepArgs &, cudaStream_t);
 template cudaError_t launch_sweep<float>(const Tables<float> &, const SweepArgs &, cudaStream_t);
 
-size_t eloc_batched_smem(int N, int M) {
+size_t eloc_batched_smem(int N, int M, int warps) {
     const size_t t_ld = (size_t)(M + 3) / 4 * 4, s_ld = (size_t)(N + 15) / 16 * 16;
-    return (size_t)kEG * t_ld * 4 + (size_t)kEG * s_ld + (size_t)(kEW * kEG + kEG) * 8 + (size_t)kEW * kEG * 4;
+    return (size_t)kEG * t_ld * 4 + (size_t)kEG * s_ld + (size_t)(warps * kEG + kEG) * 8 + (size_t)warps * kEG * 4;
 }
 
 template <typename R>
@@ -1219,18 +1225,19 @@ cudaError_t launch_eloc_batched<float>(const Tables<float> &t, const ElocArgs &a
     P.a = a;
     P.t_ld = (t.M + 3) / 4 * 4;
     P.s_ld = (t.N + 15) / 16 * 16;
-    const size_t smem = eloc_batched_smem(t.N, t.M);
-    if (smem > 227 * 1024) return cudaErrorInvalidValue;
     const bool wide = t.M >= 4096;
+    const int warps = wide ? eloc_warps(4) : eloc_warps(1);
+    const size_t smem = eloc_batched_smem(t.N, t.M, warps);
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
     const void *fn = wide ? (const void *)k_eloc_batched<4> : (const void *)k_eloc_batched<1>;
     cudaError_t err = nk::allow_max_dynamic_smem(fn);
     if (err != cudaSuccess) return err;
     const unsigned grid = (unsigned)((a.Ns + kEG - 1) / kEG);
     const int slot = prof_begin(NK_PROF_ELOC, st);
     if (wide)
-        (k_eloc_batched<4><<<grid, kEW * 32, smem, st>>>(P), nk::note_launch());
+        (k_eloc_batched<4><<<grid, warps * 32, smem, st>>>(P), nk::note_launch());
     else
-        (k_eloc_batched<1><<<grid, kEW * 32, smem, st>>>(P), nk::note_launch());
+        (k_eloc_batched<1><<<grid, warps * 32, smem, st>>>(P), nk::note_launch());
     const double conn = a.kind == NK_TFIM ? (double)t.N : 0.5 * (double)t.E;
     prof_end(slot, st, (double)a.Ns * conn * (double)t.M);
     return cudaGetLastError();
@@ -1240,7 +1247,7 @@ template <typename R>
 cudaError_t launch_eloc(const Tables<R> &t, const ElocArgs &a, cudaStream_t st) {
     if (a.Ns <= 0) return cudaSuccess;
     if (sizeof(R) == 4 && a.theta_in && t.M >= kUnitsMappingM && (t.M % 4) == 0 &&
-        eloc_batched_smem(t.N, t.M) <= 227 * 1024)
+        eloc_batched_smem(t.N, t.M, t.M >= 4096 ? eloc_warps(4) : eloc_warps(1)) <= 227 * 1024)
         return launch_eloc_batched<R>(t, a, st);
     ElocK<R> P;
     P.t = t;
