@@ -509,10 +509,23 @@ def measure(w, precision, K, warmup, rank, world, dev, prof=True, e2e=True):
         step(st, first=(i == 0))
     import torch
     torch.cuda.synchronize()
+    # The profiled, plain and end-to-end timings replay the same K steps: the
+    # state after the warm-up (parameters, chains, sweep counter) is restored
+    # before each, and the steps are deterministic, so the per-class split and
+    # the CG iteration counts belong to the steps the headline times.
+    snap = (st["params"].clone(), st["s"].clone(), st["chains"].sweeps_done)
+
+    def restore():
+        st["params"].copy_(snap[0])
+        st["s"].copy_(snap[1])
+        st["chains"].sweeps_done = snap[2]
+        torch.cuda.synchronize()
+
     res = {}
     if prof:
         ms_p, _, pr = timed_steps(st, K, world, dev, prof=True)
         res["prof"], res["ms_prof"] = pr, ms_p
+        restore()
     clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
     clocks.start()
     ms, launches, _ = timed_steps(st, K, world, dev, prof=False)
@@ -520,6 +533,7 @@ def measure(w, precision, K, warmup, rank, world, dev, prof=True, e2e=True):
     res["ms"], res["launches"] = ms, launches
     res["stats"] = nk.sr_stats_dict(st["stats"])
     if e2e:
+        restore()
         dt, bi, bo = e2e_steps(st, K, dev)
         res["e2e"] = (max_over_ranks(dt, world, dev), bi, bo)
     st["ctx"].close()
