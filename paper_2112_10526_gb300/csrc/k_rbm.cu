@@ -459,7 +459,7 @@ __global__ void __launch_bounds__(128, kRing ? 3 : 7) k_sweep(SweepK<R> P) {
         for (int j = lane; j < M; j += 32) {
             double th;
             if (A.theta_in) {
-                th = A.theta_in[(size_t)c * M + j];
+                th = A.theta_in[(size_t)c * (A.theta_ld > 0 ? A.theta_ld : M) + j];
             } else {
                 th = T.b[j];
                 for (int i = 0; i < N; ++i) th = fma(T.Wt[(size_t)i * M + j], (double)sv[i], th);
@@ -645,7 +645,7 @@ __global__ void __launch_bounds__(128) k_sweep_rows(SweepK<float> P) {
         for (int j = lane; j < M; j += 32) {
             double th;
             if (A.theta_in) {
-                th = A.theta_in[(size_t)c * M + j];
+                th = A.theta_in[(size_t)c * (A.theta_ld > 0 ? A.theta_ld : M) + j];
             } else {
                 th = T.b[j];
                 for (int i = 0; i < N; ++i) th = fma(T.Wt[(size_t)i * M + j], (double)sv[i], th);

@@ -1306,7 +1306,7 @@ size_t tc_theta_ws_bytes(int N, int M, int64_t B) {
 
 // theta [B][M] = S W^T + b with W sliced 7 ways: exact up to 2^-56 of max|W_j|.
 cudaError_t launch_theta_tc(int N, int M, const double *b, const double *W, const int8_t *s, int64_t B,
-                            double *theta, int *err, void *ws, cudaStream_t st) {
+                            double *theta, int *err, void *ws, cudaStream_t st, int64_t ldtheta) {
     if (B <= 0) return cudaSuccess;
     const int64_t ld = pad8(N);
     char *p = static_cast<char *>(ws);
@@ -1321,7 +1321,7 @@ cudaError_t launch_theta_tc(int N, int M, const double *b, const double *W, cons
     (k_pm1_rows<<<nblk(B * ld, 256), 256, 0, st>>>(s, B, N, 0, ld, As), nk::note_launch());
     (k_slice_long_rows<<<M, 128, 0, st>>>(W, N, M, N, nullptr, kMaxSB, ld, Ws, ew), nk::note_launch());
     const int slot = prof_begin(NK_PROF_JVP_VJP, st);
-    cudaError_t e = sgemm(As, B, ld, Ws, ew, M, ld, N, kMaxSB, theta, M, 0, b, err, st);
+    cudaError_t e = sgemm(As, B, ld, Ws, ew, M, ld, N, kMaxSB, theta, ldtheta > 0 ? ldtheta : M, 0, b, err, st);
     prof_end(slot, st, 2.0 * (double)B * N * (double)M, sgemm_flops(B, M, N, kMaxSB));
     return e != cudaSuccess ? e : cudaGetLastError();
 }

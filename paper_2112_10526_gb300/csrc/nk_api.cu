@@ -600,6 +600,42 @@ void carve_step(Carver &c, nk::Tables<R> &t, StepBufs &b, const nk_rbm *rbm, con
     b.tcm = mixed ? c.take<char>(tcm_bytes(N, M, TB)) : nullptr;
 }
 
+// NK_MIXED sweeps that leave the theta of every sample behind.  The theta of
+// the chains after a sampling sweep is the theta of that sweep's samples, so
+// the tensor-core product before each sweep writes it straight into those
+// samples' rows of the batch's theta buffer (row stride n_samples M), and one
+// more product after the last sweep gives the last samples' theta.  The
+// product over the whole batch that the local energies would otherwise need
+// is not run.  (Running the local energies of each sweep's samples on a
+// second stream beside the next sweep was measured too: the two kernels
+// slowed each other down and the step gained nothing beyond this.)
+template <typename R>
+nk_status run_sweeps_theta(nk_ctx *ctx, const nk::Tables<R> &t, const nk::Tables<R> &ts, const nk::SweepArgs &a,
+                           const StepBufs &b, cudaStream_t st) {
+    const int N = t.N, M = t.M, C = a.C;
+    const int nd = a.n_discard, ns = a.n_samples, total = nd + ns;
+    for (int w = 0; w <= total; ++w) {
+        // the chains now hold sample q = w - 1 - nd (q < 0: still discarding;
+        // sample 0's rows serve as scratch until its own theta arrives)
+        const int q = w - 1 - nd;
+        double *th = b.theta + (size_t)(q > 0 ? q : 0) * M;
+        NK_CU(nk::launch_theta_tc(N, M, t.b, t.W, a.s, C, th, ctx->tc_err, b.tcm, st, (int64_t)ns * M), "theta");
+        if (w == total) break;
+        nk::SweepArgs sa = a;
+        sa.sweep0 = a.sweep0 + w;
+        sa.n_discard = w < nd ? 1 : 0;
+        sa.n_samples = w < nd ? 0 : 1;
+        sa.theta_in = th;
+        sa.theta_ld = (int64_t)ns * M;
+        sa.out_stride = ns;
+        sa.out_offset = w < nd ? 0 : w - nd;
+        sa.dec_stride = total;
+        sa.dec_offset = w;
+        NK_CU(nk::launch_sweep(ts, sa, st), "sweep");
+    }
+    return NK_OK;
+}
+
 template <typename R>
 nk_status run_sample_measure(nk_ctx *ctx, const nk::Tables<R> &t, const StepBufs &b, const nk_ham *ham,
                              const nk_chains *chains, const nk_sr_cfg *cfg, int rule, int E_rule, bool site,
@@ -627,10 +663,8 @@ nk_status run_sample_measure(nk_ctx *ctx, const nk::Tables<R> &t, const StepBufs
     a.decisions = nullptr;
     nk::Tables<R> ts = t;  // the rule's edges: a prefix of the Hamiltonian's
     ts.E = E_rule;
-    nk_status sw = run_sweeps(ctx, ts, a, mixed, b.theta, b.tcm, st);
+    nk_status sw = mixed ? run_sweeps_theta(ctx, t, ts, a, b, st) : run_sweeps(ctx, ts, a, false, nullptr, nullptr, st);
     if (sw != NK_OK) return sw;
-    if (mixed)
-        NK_CU(nk::launch_theta_tc(N, M, t.b, t.W, b.samples, Ns, b.theta, ctx->tc_err, b.tcm, st), "theta");
     nk::ElocArgs ea = nk::eloc_args(ham, b.samples, Ns, b.eloc, b.T, b.theta);
     NK_CU(nk::launch_eloc(t, ea, st), "local energy");
     NK_CU(nk::launch_stats(b.eloc, Ns, C, b.st3, st), "stats");

@@ -94,6 +94,7 @@ struct SweepArgs {
     // c * dec_stride + dec_offset + sweep.
     const double *theta_in;
     int out_stride, out_offset, dec_stride, dec_offset;
+    int64_t theta_ld;  // row stride of theta_in in doubles (0: M)
 };
 
 template <typename R>
@@ -211,8 +212,10 @@ cudaError_t launch_gram_cols_tc(const double *X, int64_t rows, int64_t ncols, do
 
 // ---- tensor-core products with the configurations (k_sgemm.cu) -------------
 size_t tc_theta_ws_bytes(int N, int M, int64_t B);
+// theta [B][M] = S W^T + b, exact to 2^-56 of max|W_j| (7 slices); row r of
+// theta at theta + r * ldtheta (0: M).
 cudaError_t launch_theta_tc(int N, int M, const double *b, const double *W, const int8_t *s, int64_t B,
-                            double *theta, int *err, void *ws, cudaStream_t st);
+                            double *theta, int *err, void *ws, cudaStream_t st, int64_t ldtheta = 0);
 // The +-1 operands of the two Jacobian products depend on the samples only:
 // a solve that repeats the products (CG) builds them once.  opA: [S, 1] as
 // BF16 [Ns][pad8(N + 1)] (J v); opT: [S, 1]^T as BF16 [N + 1][pad8(Ns)] (J^T g).
