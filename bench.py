@@ -8,8 +8,10 @@ spin-exchange Metropolis at S_z = 0 with 8192 chains x 8 samples (Ns =
 on-the-fly QGT (relative residual 1e-6 in NK_MIXED, 1e-10 in NK_F64).  A step
 = sampling (8 sweeps per chain), local energies, statistics, force, SR solve
 and update, all through nk_sr_step.  The same step on the FP64 GPU path
-(fewer steps) and the 10 x 10 Heisenberg workload (sample-space Cholesky)
-are added to the line, then the serving stream.
+(fewer steps) and the other workloads are added to the line: the 10 x 10
+Heisenberg (sample-space Cholesky), its symmetric RBM, the 20 x 20 Ising
+(CG), J1-J2 on 10 x 10 and the 16-site Ising chain; then the t-VMC leg and
+the serving stream.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|f64]
     python bench.py --impl reference ...   # the CPU oracle on a bounded sample
@@ -69,7 +71,7 @@ def parse():
     ap.add_argument("--workload", default="heis2d_24x24",
                     help="workload name, optionally with @rule to replace its sampler rule "
                          "(e.g. heis2d_10x10@hamiltonian)")
-    ap.add_argument("--extra", default="heis2d_10x10,heis2d_10x10_symm",
+    ap.add_argument("--extra", default="heis2d_10x10,heis2d_10x10_symm,tfim2d_20x20,j1j2_10x10,tfim1d_n16",
                     help="comma-separated workloads timed after the headline (mixed path, same steps); none: no others")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the other-precision timing")
