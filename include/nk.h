@@ -243,7 +243,12 @@ nk_status nk_jacobian(nk_ctx *ctx, const nk_rbm *rbm, int32_t precision, const i
                       int64_t Ns, int32_t centered, int64_t row0, int64_t rows, double *O_out,
                       void *stream);
 
-/* Vector-Jacobian product out = J^T g (App. B.1), g [Ns], out [Np]. */
+/* Vector-Jacobian product out = J^T g (App. B.1), g [Ns], out [Np].  With
+ * NK_MIXED both products run on the tensor cores with the sliced operand
+ * (v, or T o g) cut into 3 FP16 slices of 11-bit digits per row (a 33-bit
+ * grid on each row's largest entry, about 2^-33 relative) and exact FP32
+ * accumulation; nk_vjp builds the FP32 pairs of tanh(theta) it slices from
+ * in the context workspace. */
 nk_status nk_vjp(nk_ctx *ctx, const nk_rbm *rbm, int32_t precision, const int8_t *s, int64_t Ns,
                  const double *g, double *out, void *stream);
 

@@ -223,7 +223,7 @@ size_t tc_jvp_operand_bytes(int N, int64_t Ns);
 size_t tc_vjp_operand_bytes(int N, int64_t Ns);
 cudaError_t launch_jacobian_operands(int N, int64_t Ns, const int8_t *s, void *opA, void *opT, cudaStream_t st);
 // t' = [tanh(theta), 1] as FP32 pairs (hi, lo) in the tile order of the
-// 4-slice J v kernel; fixed during a solve, so CG builds it once.
+// persistent J v kernel (k_tc4); fixed during a solve, so CG builds it once.
 size_t tc_split_t_bytes(int M, int64_t Ns);
 cudaError_t launch_split_t(int M, int64_t Ns, const double *T, void *Thl, cudaStream_t st);
 size_t tc_jvp_ws_bytes(int N, int M, int64_t Ns);
