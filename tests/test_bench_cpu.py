@@ -79,3 +79,27 @@ def test_l2_text_names_the_array_that_outgrows_l2():
     assert "SMALLER" in bench.l2_text("cholesky_samplespace", 1024, 200, 20300)
     assert "tanh(theta)" in bench.l2_text("cg", 16384, 1600, 642000)
     assert bench.replica_value(4, 10, 2000.0) == pytest.approx(20.0)
+
+
+def test_jacobian_product_traffic_follows_the_captured_kernel(monkeypatch):
+    """The CG products report the captured DRAM bytes of k_tc4 (the mean of a
+    J v and a J^T g launch) scaled by the workload's samples, only while the
+    kernel's source section is the one the capture was taken from."""
+    prof = {"jvp_vjp": (100.0, 100, 3.49e13, 1e14), "sweep": (50.0, 8, 1e10, 1e10)}
+    cap = bench.TC4_TRAFFIC
+    monkeypatch.setattr(bench, "tc4_source_hash", lambda: cap["source_sha256_prefix"] + "0" * 48)
+    rf, cls = bench.roofline(prof, 1, "mixed", ns=65536)
+    assert cls == "jvp_vjp"
+    assert rf["traffic"] == pytest.approx(0.5 * (cap["jv"] + cap["jtg"]) * 65536 / cap["ns"])
+    rf_none, _ = bench.roofline(prof, 1, "mixed")  # no sample count: no scaled figure
+    assert rf_none["traffic"] is None
+    monkeypatch.setattr(bench, "tc4_source_hash", lambda: "f" * 64)  # the kernel has changed
+    rf_stale, _ = bench.roofline(prof, 1, "mixed", ns=65536)
+    assert rf_stale["traffic"] is None
+
+
+def test_captured_sources_are_the_current_kernels():
+    """The traffic constants belong to the kernels in the tree (a kernel
+    change without a new capture turns the figure off, and this flags it)."""
+    assert bench.tc4_source_hash().startswith(bench.TC4_TRAFFIC["source_sha256_prefix"])
+    assert bench.ozaki_source_hash().startswith(bench.OZAKI_TRAFFIC["source_sha256_prefix"])
