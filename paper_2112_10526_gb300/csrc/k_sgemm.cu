@@ -523,7 +523,7 @@ __global__ void __launch_bounds__(kJvThreads, 1)
             const int b = (int)(li & 1);
             const uint32_t use = (uint32_t)(li >> 1);
             int ok = 1;
-            if (lane == 0) ok = mbar_wait_or_abort(&acc_full[b], use & 1, abort_flag) ? 1 : 0;
+            if (lane == 0) ok = mbar_wait_or_abort_sleep(&acc_full[b], use & 1, abort_flag) ? 1 : 0;
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) {
                 if (lane == 0) fail(23);

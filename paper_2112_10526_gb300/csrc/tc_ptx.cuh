@@ -172,6 +172,36 @@ __device__ bool mbar_wait_or_abort(uint64_t *bar, uint32_t parity, const volatil
     return false;
 }
 
+// A poll of the mbarrier phase that may suspend the thread for up to ns
+// nanoseconds; it resumes as soon as the phase completes.
+__device__ __forceinline__ bool mbar_try_wait_hint(uint64_t *bar, uint32_t parity, uint32_t ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
+        : "memory");
+    return ok != 0;
+}
+
+// mbar_wait_or_abort for many waiting warps (an epilogue waiting for its
+// accumulators): each poll may sleep up to 1 us, so that the waiting warps
+// do not take issue slots from the producer and MMA threads.  The same
+// bounds: false after kWaitNs or once *abort is set (checked every 16 polls).
+__device__ bool mbar_wait_or_abort_sleep(uint64_t *bar, uint32_t parity, const volatile int *abort) {
+    const unsigned long long t0 = global_ns();
+    for (long long it = 0; it < (1LL << 40); ++it) {
+        if (mbar_try_wait_hint(bar, parity, 1000U)) return true;
+        if ((it & 15) == 15) {
+            if (*abort) return false;
+            if (global_ns() - t0 > kWaitNs) return false;
+        }
+    }
+    return false;
+}
+
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 
