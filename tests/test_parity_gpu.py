@@ -439,3 +439,36 @@ def test_metropolis_full_size_24x24_sampled_chains(ctx, prec):
     assert rel_err(lp.cpu().numpy()[:K], ref["logpsi"]) < (1e-10 if prec == "f64" else 1e-4)
     assert (st.cpu().numpy().astype(np.int64).sum(axis=1) == 0).all()
     np.testing.assert_array_equal(nacc.cpu().numpy(), (dec.cpu().numpy() == 1).sum(axis=(1, 2)))
+
+
+def test_sr_step_sampling_gives_the_samples_of_nk_metropolis_sweep(ctx):
+    """NK_MIXED sampling inside nk_sr_step writes each sweep's theta product
+    into the rows of the samples it belongs to and hands those to the local
+    energies.  On the 24 x 24 sizes (2000 chains, one discarded and two
+    sampled sweeps) it must give, bit for bit, the samples and chain states
+    of nk_metropolis_sweep from the same start (the same Philox streams, the
+    same exact theta products), and local energies equal to nk_local_energy
+    on those samples."""
+    N, M, C, nd, ns, seed = 576, 4608, 2000, 1, 2, 5
+    ham = I.heis_square(24)
+    p = cu(I.rbm_params(N, M, seed))
+    s0 = oracle.chain_init(N, C, "exchange", seed, 0)
+    h, edges = ham_to_device(ham)
+    # the step
+    sd = cu(s0)
+    ch = nk.make_chains(sd)
+    cfg = nk.make_cfg("exchange", "mixed", "cholesky_samplespace", nd, ns, 0.01, 0.0, seed)
+    stats = torch.empty(nk.SR_STATS_DOUBLES, dtype=torch.float64, device=dev())
+    samples = torch.empty((C * ns, N), dtype=torch.int8, device=dev())
+    eloc = torch.empty(C * ns, dtype=torch.float64, device=dev())
+    nk.nk_sr_step(ctx, p, N, M, h, ch, cfg, stats, samples, eloc)
+    # the same sweeps as one launch sequence over all chains
+    st2 = cu(s0)
+    samples2 = torch.empty((C, ns, N), dtype=torch.int8, device=dev())
+    nk.nk_metropolis_sweep(ctx, p, N, M, "exchange", edges, st2, 0, nd, ns, seed, 0, samples2, precision="mixed")
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(samples.cpu().numpy(), samples2.cpu().numpy().reshape(C * ns, N))
+    np.testing.assert_array_equal(sd.cpu().numpy(), st2.cpu().numpy())
+    e2 = torch.empty(C * ns, dtype=torch.float64, device=dev())
+    nk.nk_local_energy(ctx, p, N, M, h, samples2.reshape(C * ns, N), e2, precision="mixed")
+    assert rel_err(eloc.cpu().numpy(), e2.cpu().numpy()) <= 1e-12
