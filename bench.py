@@ -395,11 +395,11 @@ def e2e_steps(st, K, dev):
 OZAKI_TRAFFIC = {"bytes_per_tile": 59062.3, "source_sha256_prefix": "393611d8bf30c3e9"}
 OZAKI_TILE_FLOPS = 28 * 4 * 2.0 * 128 * 32 * 16  # executed BF16 flops per tile (7 slices)
 # k_tc4 (the CG's J v and J^T g products): bytes per launch captured on the
-# 24 x 24 workload at 1024 chains (Ns = 8192): J v 332.02 MB read + 3.57 MB
-# written, J^T g 243.75 + 27.34 MB.  Both read their operands once, which
+# 24 x 24 workload at 1024 chains (Ns = 8192): J v 331.97 MB read + 3.59 MB
+# written, J^T g 243.31 + 27.24 MB.  Both read their operands once, which
 # grow with Ns (the tanh(theta) pairs, the +-1 operand, the (T' o g')^T
 # digits), so a launch at Ns samples moves about Ns / 8192 times as much.
-TC4_TRAFFIC = {"ns": 8192, "jv": 335587840, "jtg": 271083776, "source_sha256_prefix": "e109f779dcbde5e3"}
+TC4_TRAFFIC = {"ns": 8192, "jv": 335554304, "jtg": 270545664, "source_sha256_prefix": "5e16dbda6876423f"}
 
 
 def _section_hash(fname, start, end):

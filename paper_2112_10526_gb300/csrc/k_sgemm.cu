@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(kJvThreads, 1)
             for (int kc = kc0; kc < kc1; ++kc, ++g) {
                 const int s = (int)(g % kJvStages);
                 if (g >= kJvStages &&
-                    !mbar_wait_or_abort(&empty[s], (uint32_t)((g / kJvStages - 1) & 1), abort_flag)) {
+                    !mbar_wait_or_abort_sleep(&empty[s], (uint32_t)((g / kJvStages - 1) & 1), abort_flag)) {
                     fail(20);
                     break;
                 }
@@ -432,7 +432,7 @@ __global__ void __launch_bounds__(kJvThreads, 1)
             bool ok = true;
             for (int kc = kc0; kc < kc1; ++kc, ++g) {
                 const int s = (int)(g % kJvStages);
-                if (!mbar_wait_or_abort(&full[s], (uint32_t)((g / kJvStages) & 1), abort_flag)) {
+                if (!mbar_wait_or_abort_sleep(&full[s], (uint32_t)((g / kJvStages) & 1), abort_flag)) {
                     ok = false;
                     break;
                 }
@@ -601,7 +601,7 @@ __global__ void __launch_bounds__(kJvThreads, 1)
             if (grp == 0) {
                 int rok = 1;
                 if (lane == 0)
-                    rok = mbar_wait_or_abort(&red_full[slot * 4 + q], (uint32_t)((li / kJvRing) & 1), abort_flag)
+                    rok = mbar_wait_or_abort_sleep(&red_full[slot * 4 + q], (uint32_t)((li / kJvRing) & 1), abort_flag)
                               ? 1
                               : 0;
                 rok = __shfl_sync(0xffffffffu, rok, 0);

@@ -186,10 +186,11 @@ __device__ __forceinline__ bool mbar_try_wait_hint(uint64_t *bar, uint32_t parit
     return ok != 0;
 }
 
-// mbar_wait_or_abort for many waiting warps (an epilogue waiting for its
-// accumulators): each poll may sleep up to 1 us, so that the waiting warps
-// do not take issue slots from the producer and MMA threads.  The same
-// bounds: false after kWaitNs or once *abort is set (checked every 16 polls).
+// mbar_wait_or_abort whose polls may sleep up to 1 us each: a waiting warp
+// (an epilogue waiting for its accumulators, a producer or MMA thread
+// waiting for a stage) then gives its issue slots to the warps that have
+// work.  The same bounds: false after kWaitNs or once *abort is set
+// (checked every 16 polls).
 __device__ bool mbar_wait_or_abort_sleep(uint64_t *bar, uint32_t parity, const volatile int *abort) {
     const unsigned long long t0 = global_ns();
     for (long long it = 0; it < (1LL << 40); ++it) {
