@@ -1214,7 +1214,8 @@ cudaError_t launch_tc4(const CUtensorMap &ma, const CUtensorMap &mb, const Tc4Ar
         cfg.gridDim = dim3((unsigned)(ncl * a.C));
         e = cudaOccupancyMaxActiveClusters(&fit, (const void *)k_tc4<kMode>, &cfg);
         if (e != cudaSuccess) return e;
-        if (fit >= 1 && fit < ncl) ncl = fit;
+        if (fit < 1) return cudaErrorInvalidConfiguration;  // the caller falls back to single CTAs
+        if (fit < ncl) ncl = fit;
     }
     if (ncl > a.groups) ncl = a.groups;
     cfg.gridDim = dim3((unsigned)(ncl * a.C));
@@ -1244,12 +1245,15 @@ cudaError_t jvp4(const void *A, int64_t rows, int64_t ldA, const void *Bsl, cons
         return cudaErrorInvalidValue;
     const int n_nt = (int)((cols + kBN - 1) / kBN);
     const int64_t n_mt = (rows + kBM - 1) / kBM;
-    const int C = n_mt >= 2 * kJvCluster ? kJvCluster : 1;
-    const int n_mg = (int)((n_mt + C - 1) / C);
     const int kchunks = (int)((K + kBK - 1) / kBK);
-    Tc4Args a{rows, cols, kchunks, kchunks, 1, n_nt, n_mg, C, (int64_t)n_mg * n_nt, expB,
-              reinterpret_cast<const float4 *>(Thl), P, 0, 0, err, skip};
-    return launch_tc4<kTcRowDot>(ma, mb, a, st);
+    for (int C = n_mt >= 2 * kJvCluster ? kJvCluster : 1;; C = 1) {
+        const int n_mg = (int)((n_mt + C - 1) / C);
+        Tc4Args a{rows, cols, kchunks, kchunks, 1, n_nt, n_mg, C, (int64_t)n_mg * n_nt, expB,
+                  reinterpret_cast<const float4 *>(Thl), P, 0, 0, err, skip};
+        const cudaError_t e = launch_tc4<kTcRowDot>(ma, mb, a, st);
+        if (e == cudaErrorInvalidConfiguration && C > 1) continue;  // no cluster fits: single CTAs
+        return e;
+    }
 }
 
 // P^T [ks][cols][ldp] (column-major split-K partial products) = A B^T by
@@ -1274,19 +1278,29 @@ cudaError_t vjp4(const void *A, int64_t rows, int64_t ldA, const void *Bsl, cons
     const int kchunks = (int)((K + kBK - 1) / kBK);
     const int ks_min = (kchunks + kH3MaxK / kBK - 1) / (kH3MaxK / kBK);
     if (ks_min > max_ks) return cudaErrorInvalidValue;
-    int ks = ks_min;
-    double best = -1.0;
-    for (int k = ks_min; k <= max_ks; ++k) {
-        const int64_t units = (int64_t)n_mt * n_nt * k, rounds = (units + sms - 1) / sms;
-        const double score = (double)units / (double)(rounds * sms) - 0.01 * (k - ks_min);
-        if (score > best + 1e-12) best = score, ks = k;
+    // All row tiles of a unit in one cluster when there are 2 to 8 of them
+    // (N + 1 <= 1024): each tile of digits is then read from L2 once and
+    // multicast to every row tile (on the 24 x 24 workload, 5 row tiles:
+    // 100.5 against 102.4 ms of products a step).  Single CTAs otherwise, or
+    // where no cluster of that size fits.
+    for (int C = n_mt >= 2 && n_mt <= 8 ? n_mt : 1;; C = 1) {
+        const int n_mg = (n_mt + C - 1) / C, slots = sms / C;
+        int ks = ks_min;
+        double best = -1.0;
+        for (int k = ks_min; k <= max_ks; ++k) {
+            const int64_t units = (int64_t)n_mg * n_nt * k, rounds = (units + slots - 1) / slots;
+            const double score = (double)units / (double)(rounds * slots) - 0.01 * (k - ks_min);
+            if (score > best + 1e-12) best = score, ks = k;
+        }
+        const int kc_split = (kchunks + ks - 1) / ks;
+        ks = (kchunks + kc_split - 1) / kc_split;
+        *ks_out = ks;
+        Tc4Args a{rows, cols, kchunks, kc_split, ks, n_nt, n_mg, C, (int64_t)n_mg * n_nt * ks, expB, nullptr, P,
+                  ldp, split_stride, err, skip};
+        e = launch_tc4<kTcStoreT>(ma, mb, a, st);
+        if (e == cudaErrorInvalidConfiguration && C > 1) continue;
+        return e;
     }
-    const int kc_split = (kchunks + ks - 1) / ks;
-    ks = (kchunks + kc_split - 1) / kc_split;
-    *ks_out = ks;
-    Tc4Args a{rows, cols, kchunks, kc_split, ks, n_nt, n_mt, 1, (int64_t)n_mt * n_nt * ks, expB, nullptr, P, ldp,
-              split_stride, err, skip};
-    return launch_tc4<kTcStoreT>(ma, mb, a, st);
 }
 
 double sgemm_flops(int64_t rows, int64_t cols, int64_t K, int SB) {
